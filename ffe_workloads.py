@@ -1,0 +1,82 @@
+"""Synthetic workload definitions shared by the tests, the benchmark and the
+oracle: mesh sizes, orders, physical parameters and seeded draws.  This module
+holds no arithmetic of the method; it only says which problem to set up.
+
+Workloads (the five problem setups the library is exercised on):
+  fast_wave   flat periodic cube [-1,1]^3, 4^3 elements, P=5, smooth fast wave
+  breakdown   flat box [-2,2]x[-0.25,0.25]^2, 64x8x8 elements, P=5, current
+              sheet that drives DG<->FD switching and the E<B clamp
+  wald        Kerr-Schild M=1, a=0.9, shell r in [1.5, 50], 6 wedges x 8x8x16
+  pulsars     32 rotating-dipole shells with seeded sizes and orders
+  adjoint     one rotating-dipole shell, 6 wedges x 6x6x12, luminosity at r=20
+"""
+import math
+
+# boundary kinds and enumerations (mirrored by integer codes of the C ABI)
+PERIODIC, DIRICHLET, NO_INCOMING, STAR = "periodic", "dirichlet", "no_incoming", "star"
+RELAX, HARD, RELAX_THEN_HARD = 0, 1, 2
+
+
+def base_params(**kw):
+    p = dict(eta=0.0, kappa_psi=1.0, kappa_phi=1.0, cfl=0.5, c_over_D=0.4186,
+             filter_on=1, filter_a=36.0, filter_b=50.0, tci_on=1, tci_M=3, tci_alpha=4.0,
+             weno_eps=1e-40, fd_corrector=0, constraint_mode=RELAX, omega_star=0.0)
+    p.update(kw)
+    return p
+
+
+def fast_wave(n=4, P=5, steps=100):
+    """Smooth fast wave in a periodic cube; exact solution U(x - t)."""
+    return dict(name="fast_wave", kind="box", lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0),
+                n=(n, n, n), bc=(PERIODIC, PERIODIC, PERIODIC), P=P,
+                metric=("minkowski", 0.0, 0.0),
+                params=base_params(eta=1e3, cfl=0.5),
+                initial=("fast_wave", dict(amp=0.5)), steps=steps)
+
+
+def breakdown(nx=64, ny=8, nz=8, P=5, steps=400, mode=RELAX, x_half=2.0):
+    """FFE breakdown / current sheet: B=(1,By,0), By = 1 | -10x | -1 across
+    |x|<0.1, E=(0,0,0.5) inside |x|<0.1 and (0,0,1) outside; x ends Dirichlet to
+    the initial state, y and z periodic; element width 4/64 in every direction.
+    Smaller variants keep the element width and shrink the box."""
+    h = 2 * x_half / nx
+    return dict(name="breakdown", kind="box", lo=(-x_half, -0.5 * h * ny, -0.5 * h * nz),
+                hi=(x_half, 0.5 * h * ny, 0.5 * h * nz), n=(nx, ny, nz),
+                bc=(DIRICHLET, PERIODIC, PERIODIC), P=P, metric=("minkowski", 0.0, 0.0),
+                params=base_params(eta=1e3, cfl=0.3, fd_corrector=1, constraint_mode=mode),
+                initial=("breakdown", dict()), steps=steps)
+
+
+def cleaning_mode(n=4, P=5, eps=1e-3, kappa=1.0, steps=20):
+    """Divergence-cleaning telegraph mode: B=(1+eps sin(pi x),0,0), E=psi=phi=q=0."""
+    return dict(name="cleaning_mode", kind="box", lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0),
+                n=(n, n, n), bc=(PERIODIC, PERIODIC, PERIODIC), P=P,
+                metric=("minkowski", 0.0, 0.0),
+                params=base_params(eta=0.0, cfl=0.5, kappa_psi=kappa, kappa_phi=kappa, tci_on=0),
+                initial=("cleaning_mode", dict(eps=eps)), steps=steps)
+
+
+def splitmix64(seed):
+    """splitmix64 stream -> uniform doubles in [0,1) (53-bit mantissa)."""
+    state = seed & 0xFFFFFFFFFFFFFFFF
+    while True:
+        state = (state + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+        z = z ^ (z >> 31)
+        yield (z >> 11) * (1.0 / 9007199254740992.0)
+
+
+def pulsar_draws(n_inst=32, seed=1531):
+    """Per-instance draws, in order R_LC, chi, N_Omega, N_r, P."""
+    g = splitmix64(seed)
+    out = []
+    for _ in range(n_inst):
+        r_lc = 3.0 + 5.0 * next(g)
+        chi = math.radians(60.0) * next(g)
+        n_ang = 4 + int(5 * next(g))
+        n_rad = 8 + int(9 * next(g))
+        P = 4 + int(2 * next(g))
+        out.append(dict(r_lc=r_lc, chi=chi, n_ang=n_ang, n_rad=n_rad, P=P))
+    return out

@@ -1,0 +1,177 @@
+"""Conservative finite-difference subcell right-hand side (Sec. III.C.2).
+Test infrastructure only.
+
+On an FD element with (2N+1)^3 cells of width dxi = 2/(2N+1):
+  dU_i/dt = - sum_k sum_j (d xi^k/d x^j)_i (F^j_{i+1/2} - F^j_{i-1/2}) / dxi + S(U_i)
+Face values of the nine evolved variables and of the densitised current J~
+(Sec. III.C.2: J~ is reconstructed to form the q~ flux) come from WENO5-Z with
+exponent q = 2 (Borges et al. 2008, the paper's choice) in point-value
+interpolation form (see `weno5z`).  The face flux is
+Rusanov; optionally (Cartesian meshes) the 4th-order derivative corrector with
+cell-centred fluxes is subtracted:  F = F* - (1/6)(F_i - 2 F* + F_{i+1}).
+Three ghost layers per face come from the neighbour (its cells, or its DG
+polynomial evaluated at its subcell centres) or from the boundary state.
+"""
+import numpy as np
+
+from . import physics as ph
+from .dg import DG, FD, _met_at
+from .geometry import BC_DIRICHLET, BC_NO_INCOMING, BC_STAR, layer_slice, axis_of
+from .ops import apply_3d
+
+NG = 3
+
+
+def weno5z(v0, v1, v2, v3, v4, eps, q=2):
+    """WENO5-Z value at the face between v2 and v3 from the left-biased stencil
+    (v0..v4 = point values v_{i-2}..v_{i+2}).
+
+    [reading] The subcell data are point values (conservative FD in the
+    Shu-Osher sense, Sec. III.C.2) and the face states feed a flux that the
+    4th-order corrector then turns into the Shu-Osher numerical flux; for the
+    corrected scheme to be high order (as the paper reports, and as its
+    uncorrected variant is not) the face states must be point-value
+    interpolants.  So the three candidates are the quadratic interpolants at
+    x_{i+1/2}, combined with the ideal weights (1, 10, 5)/16 of the 5-point
+    interpolant; smoothness indicators are Jiang-Shu's, and the Z weights are
+    alpha_k = d_k (1 + (tau_5/(beta_k + eps))^q), tau_5 = |beta_0 - beta_2|
+    (Borges et al. 2008).  |.| branches on the real part (complex-step safe)."""
+    p0 = 0.375 * v0 - 1.25 * v1 + 1.875 * v2
+    p1 = -0.125 * v1 + 0.75 * v2 + 0.375 * v3
+    p2 = 0.375 * v2 + 0.75 * v3 - 0.125 * v4
+    b0 = 13.0 / 12.0 * (v0 - 2 * v1 + v2) ** 2 + 0.25 * (v0 - 4 * v1 + 3 * v2) ** 2
+    b1 = 13.0 / 12.0 * (v1 - 2 * v2 + v3) ** 2 + 0.25 * (v1 - v3) ** 2
+    b2 = 13.0 / 12.0 * (v2 - 2 * v3 + v4) ** 2 + 0.25 * (3 * v2 - 4 * v3 + v4) ** 2
+    t = b0 - b2
+    tau = np.where(np.real(t) < 0, -t, t)
+    a0 = (1.0 / 16.0) * (1 + (tau / (b0 + eps)) ** q)
+    a1 = (10.0 / 16.0) * (1 + (tau / (b1 + eps)) ** q)
+    a2 = (5.0 / 16.0) * (1 + (tau / (b2 + eps)) ** q)
+    return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2)
+
+
+def fill_ghosts(st, disc, sel, met_fn, prm):
+    """Extended cell arrays (9, n, Nc+6, Nc+6, Nc+6) for FD elements `sel`, and
+    the coordinates of every filled cell (for the metric).  Corner/edge ghost
+    regions are never read by the dimension-split scheme and stay NaN."""
+    T = disc.T
+    Nc = T.nc
+    n = len(sel)
+    ext = np.full((9, n, Nc + 2 * NG, Nc + 2 * NG, Nc + 2 * NG), np.nan, dtype=st["ufd"].dtype)
+    xyz = np.full((3, n) + ext.shape[2:], np.nan)
+    inner = (slice(NG, NG + Nc),) * 3
+    ext[(slice(None), slice(None)) + inner] = st["ufd"][:, sel]
+    xyz[(slice(None), slice(None)) + inner] = disc.xyz_fd[:, sel]
+    dxi = 2.0 / Nc
+    for a, e in enumerate(sel):
+        for f in range(6):
+            d, s = f // 2, f % 2
+            nb, kind = disc.nbr[e, f], disc.bc[e, f]
+            for g in range(NG):
+                # ghost layer g (0 = adjacent to the face) in extended indexing
+                pos = NG - 1 - g if s == 0 else NG + Nc + g
+                idx = [slice(NG, NG + Nc)] * 3
+                idx[2 - d] = pos
+                tgt = (slice(None), a) + tuple(idx)
+                if nb >= 0:
+                    src = st["ufd"][:, nb] if st["mask"][nb] == FD else apply_3d(T.P, st["udg"][:, nb])
+                    ext[tgt] = src.reshape(9, -1)[:, disc.fd_map[e, f, g]]
+                    xyz[tgt] = disc.xyz_fd[:, nb].reshape(3, -1)[:, disc.fd_map[e, f, g]]
+                else:
+                    # ghost centre from the element map continued past the face
+                    xi_n = -(1 + (g + 0.5) * dxi) if s == 0 else 1 + (g + 0.5) * dxi
+                    Z, Y, X = np.meshgrid(T.xc, T.xc, T.xc, indexing="ij")
+                    pts = np.stack([X, Y, Z])
+                    lay = layer_slice(d, s, Nc, 0)
+                    pts = pts[(slice(None),) + lay].copy()
+                    pts[d] = xi_n
+                    gx = disc.mesh.map(e, pts)
+                    xyz[tgt] = gx
+                    outer = st["ufd"][:, e][(slice(None),) + lay]
+                    if kind == BC_DIRICHLET:
+                        ext[tgt] = prm["dirichlet"](gx)
+                    elif kind == BC_NO_INCOMING:
+                        mf = _met_at(met_fn["fdface"][d], np.array([e]), layer_slice(d, s, Nc + 1, 0))
+                        ijf = disc.ijac_ff[d][:, :, e][(slice(None), slice(None)) + layer_slice(d, s, Nc + 1, 0)]
+                        nrm = ijf[d] * (1.0 if s == 1 else -1.0)
+                        gu = ph._bc(mf.gu, 2, nrm.ndim - 1)
+                        nrm = nrm / np.sqrt(np.einsum('ij...,i...,j...->...', gu, nrm, nrm))
+                        mo = _met_at(met_fn["fd"], np.array([e]), lay)
+                        ext[tgt] = ph.bc_no_incoming_poynting(outer[:, None], mo, nrm[:, None])[:, 0]
+                    elif kind == BC_STAR:
+                        ext[tgt] = ph.bc_star(outer, disc.xyz_fd[:, e][(slice(None),) + lay], prm["omega"])
+                    else:
+                        raise ValueError("face without neighbour or boundary condition")
+    return ext, xyz
+
+
+def rhs_fd(st, disc, met, prm):
+    """Explicit FD right-hand side for all elements with mask == FD.
+
+    met: dict with 'fd' (Metric at cell centres), 'fdface' (list over face
+    direction of Metric at face points) and 'at' (callable xyz -> Metric) for
+    ghost cells.  prm: dict(eta, weno_eps, fd_corrector, dirichlet, omega).
+    Returns dudt with the FD-element blocks filled (zeros elsewhere)."""
+    T = disc.T
+    Nc = T.nc
+    sel = np.nonzero(st["mask"] == FD)[0]
+    out = np.zeros_like(st["ufd"])
+    if len(sel) == 0:
+        return out
+    ext, xyz = fill_ghosts(st, disc, sel, met, prm)
+    mext = met["at"](np.nan_to_num(xyz))
+    jd, jp = ph.current(np.nan_to_num(ext), mext, prm["eta"])
+    W = np.concatenate([ext, jd + jp], axis=0)  # 12 reconstructed quantities
+    mc = _met_at(met["fd"], sel, ())
+    ijac = disc.ijac_fd[:, :, sel]
+    U = st["ufd"][:, sel]
+    jdc, _ = ph.current(U, mc, prm["eta"])
+    dudt = np.zeros_like(U)
+    eps = prm["weno_eps"]
+    for k in range(3):
+        ax = 1 + axis_of(k)  # axis of W (12, n, z, y, x)
+
+        def sl(lo, hi):
+            idx = [slice(None), slice(None), slice(NG, NG + Nc), slice(NG, NG + Nc), slice(NG, NG + Nc)]
+            idx[ax] = slice(lo, hi)
+            return tuple(idx)
+        # face m (0..Nc) between interior cells m-1 and m; extended index of cell c is c + NG
+        # v[o+3][m] = cell m+o (o = -3..2) for each face m
+        v = [W[sl(NG + o, NG + o + Nc + 1)] for o in range(-3, 3)]
+        WL = weno5z(v[0], v[1], v[2], v[3], v[4], eps)
+        WR = weno5z(v[5], v[4], v[3], v[2], v[1], eps)
+        UL, UR = WL[:9], WR[:9]
+        JL, JR = WL[9:], WR[9:]
+        mf = _met_at(met["fdface"][k], sel, ())
+        FL = ph.fluxes(UL, JL, mf)
+        FR = ph.fluxes(UR, JR, mf)
+        ijf = disc.ijac_ff[k][:, :, sel]
+        nrm = ijf[k]
+        sp = nrm.ndim - 1
+        gu = ph._bc(mf.gu, 2, sp)
+        nrm = nrm / np.sqrt(np.einsum('ij...,i...,j...->...', gu, nrm, nrm))
+        nup = np.einsum('jl...,l...->j...', gu, nrm)
+        lam = ph._bc(mf.alpha, 0, sp) + np.abs(np.einsum('j...,j...->...', ph._bc(mf.beta, 1, sp), nrm))
+        Fs = 0.5 * (FL + FR) - 0.5 * (lam * nup)[:, None] * (UR - UL)[None]
+        if prm["fd_corrector"]:
+            # cell-centred fluxes either side of each interior face; the
+            # element-boundary faces use the ghost cells' fluxes
+            mg = met["at"](np.nan_to_num(xyz))
+            Fg = ph.fluxes(np.nan_to_num(ext), jd + jp, mg)
+            def slc(lo, hi):
+                idx = [slice(None), slice(None), slice(None), slice(NG, NG + Nc), slice(NG, NG + Nc), slice(NG, NG + Nc)]
+                idx[ax + 1] = slice(lo, hi)
+                return tuple(idx)
+            Fm = Fg[slc(NG - 1, NG + Nc)]
+            Fp = Fg[slc(NG, NG + Nc + 1)]
+            Fs = Fs - (1.0 / 6.0) * (Fm - 2 * Fs + Fp)
+        lo = [slice(None)] * 6
+        hi = [slice(None)] * 6
+        lo[ax + 1] = slice(0, Nc)
+        hi[ax + 1] = slice(1, Nc + 1)
+        diff = (Fs[tuple(hi)] - Fs[tuple(lo)]) * (Nc / 2.0)
+        for j in range(3):
+            dudt -= ijac[k, j][None] * diff[j]
+    dudt += ph.sources_explicit(U, jdc, mc)
+    out[:, sel] = dudt
+    return out

@@ -1,0 +1,55 @@
+"""Set up an oracle problem from a workload description.  Test infrastructure only."""
+import numpy as np
+
+from . import initial, physics as ph
+from .basis import Tables
+from .geometry import BoxMesh, Discretisation, BC_PERIODIC, BC_DIRICHLET, BC_NO_INCOMING, BC_STAR
+
+_BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "no_incoming": BC_NO_INCOMING, "star": BC_STAR}
+
+
+class Problem:
+    def __init__(self, cfg):
+        self.cfg = cfg
+        p = cfg["params"]
+        self.T = Tables(cfg["P"], p["filter_a"], p["filter_b"], p["tci_M"])
+        if cfg["kind"] == "box":
+            self.mesh = BoxMesh(cfg["lo"], cfg["hi"], cfg["n"], [_BC[b] for b in cfg["bc"]])
+        else:
+            raise NotImplementedError(cfg["kind"])
+        self.disc = Discretisation(self.mesh, self.T)
+        mkind = cfg["metric"][0]
+        if mkind == "minkowski":
+            at = lambda xyz: ph.flat_metric()
+            self.lam_max = 1.0
+        else:
+            raise NotImplementedError(mkind)
+        d = self.disc
+        self.met = {"dg": at(d.xyz), "fd": at(d.xyz_fd), "fdface": [at(x) for x in d.xyz_ff], "at": at}
+        ikind, ikw = cfg["initial"]
+        self.initial = lambda xyz: initial.evaluate(ikind, xyz, **ikw)
+        self.prm = dict(eta=p["eta"], kappa_psi=p["kappa_psi"], kappa_phi=p["kappa_phi"],
+                        weno_eps=p["weno_eps"], fd_corrector=p["fd_corrector"],
+                        dirichlet=self.initial, omega=p["omega_star"],
+                        mode=p["constraint_mode"], filter_on=p["filter_on"], tci_on=p["tci_on"],
+                        tci_alpha=p["tci_alpha"], tci_M=p["tci_M"])
+        self.dxmin = d.min_spacing()
+        self.dt = p["cfl"] * self.dxmin / self.lam_max * p["c_over_D"]
+
+    def initial_state(self):
+        """Initial data on the LGL nodes, then the TCI (alpha) on every element;
+        flagged elements take the initial data at their subcell centres.
+        [reading] the paper initialises on the FD grid (Sec. III.C.1); here the
+        nodal start is the default, as the FD start only matters for Gibbs-prone data."""
+        from .stepper import tci_ratio, tci_threshold
+        d, T = self.disc, self.T
+        udg = self.initial(d.xyz.reshape(3, -1)).reshape((9,) + d.xyz.shape[1:])
+        ufd = np.zeros((9, d.E, T.nc, T.nc, T.nc))
+        mask = np.zeros(d.E, dtype=np.uint8)
+        if self.prm["tci_on"]:
+            r = tci_ratio(udg[3:6], self.met["dg"], T, np.arange(d.E))
+            flag = r > tci_threshold(T.N, self.prm["tci_M"], self.prm["tci_alpha"])
+            for e in np.nonzero(flag)[0]:
+                mask[e] = 1
+                ufd[:, e] = self.initial(d.xyz_fd[:, e].reshape(3, -1)).reshape((9,) + d.xyz_fd.shape[2:])
+        return dict(mask=mask, udg=udg, ufd=ufd, t=0.0)

@@ -1,0 +1,130 @@
+"""Pins of the oracle's pointwise physics against identities of Sec. II and III.B."""
+import numpy as np
+import pytest
+
+from oracle import physics as ph
+
+
+def random_metric(rng, shape):
+    """A positive-definite spatial metric with lapse and shift (derivatives zero)."""
+    A = rng.normal(size=(3, 3) + shape) * 0.3
+    gl = np.einsum('ik...,jk...->ij...', A, A) + np.eye(3).reshape((3, 3) + (1,) * len(shape))
+    gu = np.moveaxis(np.linalg.inv(np.moveaxis(gl, (0, 1), (-2, -1))), (-2, -1), (0, 1))
+    sqrtg = np.sqrt(np.linalg.det(np.moveaxis(gl, (0, 1), (-2, -1))))
+    alpha = 0.5 + rng.random(shape)
+    beta = rng.normal(size=(3,) + shape) * 0.2
+    z3 = np.zeros((3,) + shape)
+    return ph.Metric(alpha, beta, gl, gu, sqrtg, z3, np.zeros((3, 3) + shape), z3, np.zeros(shape))
+
+
+def test_drift_current_is_force_free():
+    """q E^i + eps^{ijk} J_j B_k = 0 for the drift current when E.B = 0 (Sec. II.B)."""
+    rng = np.random.default_rng(1)
+    shape = (50,)
+    m = random_metric(rng, shape)
+    U = rng.normal(size=(9,) + shape)
+    B = U[3:6]
+    Bl = ph.lower(B, m, 1)
+    # remove the part of E along B so that E.B = 0
+    U[0:3] -= np.sum(ph.lower(U[0:3], m, 1) * B, 0) / np.sum(Bl * B, 0) * B
+    jd, jp = ph.current(U, m, eta=7.0)
+    # undensitise: E = E~/sqrtg, B = B~/sqrtg, q = q~/sqrtg, J = J~/(alpha sqrtg)
+    sg = m.sqrtg
+    E, Bv, q, J = U[0:3] / sg, U[3:6] / sg, U[8] / sg, jd / (m.alpha * sg)
+    Jl, Bvl = ph.lower(J, m, 1), ph.lower(Bv, m, 1)
+    lorentz = q * E + ph.cross_lower(Jl, Bvl) / sg
+    assert np.abs(lorentz).max() < 1e-12 * (1 + np.abs(q * E).max())
+    # drift current is orthogonal to E and B
+    assert np.abs(np.sum(ph.lower(J, m, 1) * E, 0)).max() < 1e-12
+    assert np.abs(np.sum(Jl * Bv, 0)).max() < 1e-12
+
+
+def test_parallel_current_terms():
+    """J~_eta = alpha eta [(E.B)/B^2 B + R(E^2-B^2)/B^2 E]: vanishes when E.B = 0 and
+    E^2 < B^2; along B it equals alpha eta (E.B)(1 + R/B^2)."""
+    rng = np.random.default_rng(2)
+    m = random_metric(rng, (40,))
+    U = rng.normal(size=(9, 40))
+    U[3:6] *= 3.0
+    jd, jp = ph.current(U, m, eta=5.0)
+    E, B = U[0:3], U[3:6]
+    El, Bl = ph.lower(E, m, 1), ph.lower(B, m, 1)
+    EB, B2, E2 = np.sum(El * B, 0), np.sum(Bl * B, 0), np.sum(El * E, 0)
+    lhs = np.sum(ph.lower(jp, m, 1) * B, 0)
+    rhs = m.alpha * 5.0 * EB * (1 + np.maximum(E2 - B2, 0) / B2)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
+
+
+def test_flat_sources():
+    rng = np.random.default_rng(3)
+    U = rng.normal(size=(9, 30))
+    m = ph.flat_metric()
+    jd, _ = ph.current(U, m, 2.0)
+    S = ph.sources_explicit(U, jd, m)
+    np.testing.assert_allclose(S[0:3], -jd)
+    assert np.all(S[3:6] == 0) and np.all(S[7:9] == 0)
+    np.testing.assert_allclose(S[6], U[8])
+
+
+@pytest.mark.parametrize("scale", [0.3, 3.0])
+def test_stiff_solve_residual_and_branches(scale):
+    rng = np.random.default_rng(4)
+    m = random_metric(rng, (200,))
+    R = rng.normal(size=(9, 200))
+    R[0:3] *= scale
+    dta, eta = 0.01, 1e3
+    U = ph.stiff_solve(R, m, eta, 1.0, 2.0, dta)
+    G = ph.implicit_G(U, m, eta, 1.0, 2.0)
+    res = U - (R + dta * G)
+    assert np.abs(res).max() < 1e-13 * (1 + np.abs(R).max())
+    np.testing.assert_allclose(U[6], R[6] / (1 + m.alpha * dta), rtol=1e-15)
+    np.testing.assert_allclose(U[7], R[7] / (1 + 2 * m.alpha * dta), rtol=1e-15)
+    # analytic branch: E.B scaled by exactly 1/(1+c), c = alpha eta dta
+    E, B = U[0:3], U[3:6]
+    sub = np.sum(ph.lower(E, m, 1) * E, 0) <= np.sum(ph.lower(B, m, 1) * B, 0)
+    EB = np.sum(ph.lower(E, m, 1) * B, 0)
+    EB0 = np.sum(ph.lower(R[0:3], m, 1) * B, 0)
+    c = m.alpha * eta * dta
+    np.testing.assert_allclose(EB[sub], (EB0 / (1 + c))[sub], rtol=1e-12, atol=1e-15)
+    if scale > 1:
+        assert (~sub).sum() > 10  # the nonlinear branch was exercised
+
+
+def test_hard_clamp_invariants():
+    rng = np.random.default_rng(5)
+    m = random_metric(rng, (300,))
+    U = rng.normal(size=(9, 300)) * 2
+    H = ph.hard_clamp(U, m)
+    E, B = H[0:3], H[3:6]
+    El, Bl = ph.lower(E, m, 1), ph.lower(B, m, 1)
+    nE = np.sqrt(np.sum(El * E, 0))
+    nB = np.sqrt(np.sum(Bl * B, 0))
+    assert np.all(np.abs(np.sum(El * B, 0)) <= 1e-14 * nE * nB + 1e-300)
+    assert np.all(nE ** 2 <= nB ** 2 * (1 + 8 * 2.0 ** -52))
+    # an already admissible field is left alone
+    U2 = U.copy()
+    U2[0:3] = H[0:3] * 0.5
+    np.testing.assert_allclose(ph.hard_clamp(U2, m)[0:3], U2[0:3], atol=1e-14)
+
+
+def test_no_incoming_poynting_state():
+    rng = np.random.default_rng(6)
+    m = ph.flat_metric()
+    U = rng.normal(size=(9, 100))
+    n = np.zeros((3, 100))
+    n[0] = 1.0
+    out = ph.bc_no_incoming_poynting(U, m, n)
+    Sx = U[1] * U[5] - U[2] * U[4]
+    assert np.all(out[0:3][:, Sx < 0] == 0) and np.all(out[0:3][:, Sx > 0] == U[0:3][:, Sx > 0])
+    assert np.all(out[6:8] == 0) and np.all(out[8] == U[8]) and np.all(out[3:6] == U[3:6])
+
+
+def test_star_state_is_ideal_mhd():
+    """E + v x B = 0 with v = Omega z^ x x, so E.B = 0 and E.v = 0."""
+    rng = np.random.default_rng(7)
+    U = rng.normal(size=(9, 50))
+    xyz = rng.normal(size=(3, 50))
+    out = ph.bc_star(U, xyz, 0.3)
+    v = np.stack([-0.3 * xyz[1], 0.3 * xyz[0], 0 * xyz[0]])
+    np.testing.assert_allclose(out[0:3] + np.cross(v.T, U[3:6].T).T, 0, atol=1e-14)
+    assert np.abs(np.sum(out[0:3] * U[3:6], 0)).max() < 1e-13

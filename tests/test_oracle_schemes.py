@@ -1,0 +1,209 @@
+"""Pins of the oracle's DG, FD and time-stepping schemes against closed forms,
+conservation and convergence (Sec. III, IV.A)."""
+import math
+
+import numpy as np
+import pytest
+
+import ffe_workloads as W
+from oracle import initial
+from oracle.dg import rhs_dg
+from oracle.fd import rhs_fd, weno5z
+from oracle.problem import Problem
+from oracle.stepper import A_IM, B_IM, H_IM, Stepper, tci_ratio, tci_threshold
+
+
+def _box(n, P=5, bc="periodic", **prm):
+    cfg = W.fast_wave(n=n, P=P)
+    cfg["n"] = n if isinstance(n, tuple) else (n, n, n)
+    cfg["bc"] = (bc, bc, bc)
+    cfg["params"].update(prm)
+    return cfg
+
+
+def test_dg_rhs_exact_on_linear_fields_matches_maxwell():
+    """Linear fields, eta = 0, q = 0: DG is exact and the right-hand side is the
+    flat Maxwell system  dE/dt = curl B - grad psi,  dB/dt = -curl E - grad phi,
+    dpsi/dt = -div E,  dphi/dt = -div B  (pins the flux signs and eps^{ijk})."""
+    rng = np.random.default_rng(11)
+    A = rng.normal(size=(9, 3))
+    A[8] = 0
+    U0 = rng.normal(size=9)
+    U0[8] = 0
+    fn = lambda xyz: U0.reshape((9,) + (1,) * (xyz.ndim - 1)) + np.einsum('vd,d...->v...', A, xyz)
+    cfg = _box((2, 1, 1), bc="dirichlet", eta=0.0)
+    cfg["params"]["tci_on"] = 0
+    pr = Problem(cfg)
+    pr.prm["dirichlet"] = fn
+    st = dict(mask=np.zeros(pr.disc.E, np.uint8),
+              udg=fn(pr.disc.xyz.reshape(3, -1)).reshape((9,) + pr.disc.xyz.shape[1:]),
+              ufd=np.zeros((9, pr.disc.E, 11, 11, 11)))
+    r = rhs_dg(st, pr.disc, pr.met, pr.prm)
+    dE, dB = A[0:3], A[3:6]   # dE[i, j] = d_j E^i
+    curl = lambda g: np.array([g[2, 1] - g[1, 2], g[0, 2] - g[2, 0], g[1, 0] - g[0, 1]])
+    exp = np.concatenate([curl(dB) - A[6], -curl(dE) - A[7], [-np.trace(dE), -np.trace(dB), 0.0]])
+    np.testing.assert_allclose(r.reshape(9, -1), np.broadcast_to(exp[:, None], (9, r[0].size)), atol=1e-11)
+
+
+@pytest.mark.parametrize("which", ["dg", "fd"])
+def test_conservation_periodic(which):
+    """Linear Maxwell (eta = 0, q = 0) on a periodic box: the LGL-quadrature
+    (DG) or cell sum (FD) of dU/dt vanishes for every variable (strong-form DG
+    with the lumped lift and Rusanov fluxes is conservative; FD telescopes)."""
+    rng = np.random.default_rng(12)
+    cfg = _box(2, eta=0.0)
+    pr = Problem(cfg)
+    E = pr.disc.E
+    st = dict(mask=np.zeros(E, np.uint8), udg=rng.normal(size=(9, E, 6, 6, 6)), ufd=rng.normal(size=(9, E, 11, 11, 11)))
+    st["udg"][8] = 0
+    st["ufd"][8] = 0
+    if which == "dg":
+        r = rhs_dg(st, pr.disc, pr.met, pr.prm)
+        w = pr.T.w
+        W3 = np.einsum('k,j,i->kji', w, w, w)
+        tot = np.einsum('veijk,ijk->v', r, W3)
+    else:
+        st["mask"][:] = 1
+        pr.prm["fd_corrector"] = 1
+        r = rhs_fd(st, pr.disc, pr.met, pr.prm)
+        tot = r.reshape(9, -1).sum(axis=1)
+    assert np.abs(tot).max() < 1e-10 * np.abs(r).max() * r[0].size ** 0.5
+
+
+def _fast_wave_error(n, filter_on, t_end=0.2):
+    cfg = _box((n, 1, 1), filter_on=filter_on)
+    cfg["params"]["tci_on"] = 0
+    cfg["params"]["cfl"] = 0.25
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    S = Stepper(pr)
+    steps = int(round(t_end / pr.dt))
+    for _ in range(steps):
+        st = S.step(st)
+    ex = initial.fast_wave(pr.disc.xyz.reshape(3, -1), t=st["t"]).reshape(st["udg"].shape)
+    return np.abs(st["udg"] - ex).max()
+
+
+def test_fast_wave_translation_convergence():
+    """Exact translation Q(x,t) = Q(x-t,0) (Sec. IV.A.1); error falls like
+    h^(N+1) without the filter and h^N with it (Sec. III.A)."""
+    e_nf = [_fast_wave_error(n, 0) for n in (4, 8)]
+    e_f = [_fast_wave_error(n, 1) for n in (4, 8)]
+    o_nf = math.log2(e_nf[0] / e_nf[1])
+    o_f = math.log2(e_f[0] / e_f[1])
+    assert e_nf[1] < 2e-6
+    assert o_nf > 5.6, o_nf
+    assert 4.3 < o_f < 5.4, o_f
+
+
+def test_cleaning_telegraph_mode():
+    """B = (1 + eps sin(pi x), 0, 0): the pair (B_x, phi) obeys
+    A'' + kappa A' + k^2 A = 0 (damped divergence cleaning, Sec. II.A), so
+    B_x = 1 + eps sin(kx) e^{-kappa t/2}(cos wt + kappa/(2w) sin wt), w^2 = k^2 - kappa^2/4."""
+    cfg = W.cleaning_mode(n=8, kappa=1.0)
+    cfg["n"] = (8, 1, 1)
+    cfg["params"]["cfl"] = 0.25
+    cfg["params"]["filter_on"] = 0  # the filter's O(h^N) projection error would dominate
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    S = Stepper(pr)
+    for _ in range(int(round(0.5 / pr.dt))):
+        st = S.step(st)
+    t, k, kap, eps = st["t"], math.pi, 1.0, 1e-3
+    w = math.sqrt(k * k - kap * kap / 4)
+    Aa = math.exp(-kap * t / 2) * (math.cos(w * t) + kap / (2 * w) * math.sin(w * t))
+    x = pr.disc.xyz[0]
+    Bx = 1 + eps * np.sin(k * x) * Aa
+    assert np.abs(st["udg"][3] - Bx).max() < 2e-6 * eps
+    assert abs(Aa) < 0.9  # the mode actually evolved
+    assert np.abs(st["udg"][0:3]).max() < 1e-12 and np.abs(st["udg"][4:6]).max() < 1e-12
+
+
+def test_weno5z_reconstruction():
+    rng = np.random.default_rng(13)
+    # quadratics: every candidate is exact, so the scheme is exact whatever the weights
+    for _ in range(20):
+        c = rng.normal(size=3)
+        f = lambda x: c[0] + c[1] * x + c[2] * x * x
+        v = [f(x) for x in (-2.0, -1.0, 0.0, 1.0, 2.0)]
+        assert abs(weno5z(*v, 1e-40) - f(0.5)) < 1e-13
+    # smooth data: 5th-order interpolation of point values at the face
+    errs = []
+    for h in (0.1, 0.05):
+        xs = 0.3 + h * np.arange(-2, 3)
+        errs.append(abs(weno5z(*np.sin(xs), 1e-40) - math.sin(0.3 + 0.5 * h)))
+    assert math.log2(errs[0] / errs[1]) > 4.5
+    # a jump: no new extremum (essentially non-oscillatory)
+    v = [0.0, 0.0, 0.0, 1.0, 1.0]
+    assert -1e-12 <= weno5z(*v, 1e-40) <= 1.0 + 1e-12
+
+
+@pytest.mark.parametrize("corr,order", [(1, 3.8), (0, 1.9)])
+def test_fd_rhs_convergence(corr, order):
+    """Corrected FD flux difference converges at 4th order, uncorrected at 2nd (Sec. III.C.2)."""
+    errs = []
+    for n in (4, 8):
+        cfg = _box((n, 1, 1), fd_corrector=corr)
+        pr = Problem(cfg)
+        st = pr.initial_state()
+        st["mask"][:] = 1
+        st["ufd"] = initial.fast_wave(pr.disc.xyz_fd.reshape(3, -1)).reshape(st["ufd"].shape)
+        r = rhs_fd(st, pr.disc, pr.met, pr.prm)
+        bp = 0.5 * np.pi * np.cos(np.pi * pr.disc.xyz_fd[0])
+        ex = np.zeros_like(r)
+        ex[4], ex[2] = -bp, bp
+        errs.append(np.abs(r - ex).max())
+    assert math.log2(errs[0] / errs[1]) > order
+
+
+def test_imex_tableau_order_conditions():
+    """IMEX-SSP3(4,3,3): both tables are third order and satisfy the coupling
+    conditions; with G = 0 the explicit part is Shu-Osher SSP-RK3."""
+    a, b, h = A_IM, B_IM, H_IM
+    Ae = np.array([[0, 0, 0, 0], [0, 0, 0, 0], [0, 1, 0, 0], [0, .25, .25, 0]])
+    Ai = np.array([[a, 0, 0, 0], [-a, a, 0, 0], [0, 1 - a, a, 0], [b, h, .5 - b - h - a, a]])
+    w = np.array([0, 1 / 6, 1 / 6, 2 / 3])
+    ce, ci = Ae.sum(1), Ai.sum(1)
+    for A, c in ((Ae, ce), (Ai, ci)):
+        assert abs(w.sum() - 1) < 1e-14 and abs(w @ c - 0.5) < 1e-14
+        assert abs(w @ c ** 2 - 1 / 3) < 1e-13 and abs(w @ A @ c - 1 / 6) < 1e-13
+    for x, y in ((ce, ci), (ci, ce)):
+        assert abs(w @ (x * y) - 1 / 3) < 1e-13
+    for A, c in ((Ae, ci), (Ai, ce)):
+        assert abs(w @ A @ c - 1 / 6) < 1e-13
+    # explicit stages 2..4 with c = (0, 1, 1/2) and weights (1/6, 1/6, 2/3): SSP-RK3
+    np.testing.assert_allclose(ce[1:], [0, 1, 0.5])
+
+
+def test_tci_threshold_and_flags():
+    assert abs(tci_threshold(5, 3, 4.0) - 3.0 ** -4) < 1e-18
+    assert abs(tci_threshold(4, 3, 5.0) - 2.0 ** -5) < 1e-18
+    cfg = _box((4, 1, 1))
+    pr = Problem(cfg)
+    x = pr.disc.xyz[0]
+    smooth = np.stack([1 + 0.5 * np.sin(np.pi * x), 0 * x, 0 * x])
+    jump = np.stack([np.where(x > 0.1, 2.0, 1.0), 0 * x, 0 * x])
+    sel = np.arange(pr.disc.E)
+    thr = tci_threshold(5, 3, 4.0)
+    assert np.all(tci_ratio(smooth, pr.met["dg"], pr.T, sel) < thr)
+    flags = tci_ratio(jump, pr.met["dg"], pr.T, sel) > thr
+    xe = pr.disc.xyz[0].reshape(pr.disc.E, -1)
+    has_jump = (xe.min(1) < 0.1) & (xe.max(1) > 0.1)
+    assert np.array_equal(flags, has_jump)
+
+
+def test_breakdown_hard_mode_invariants_and_switching():
+    """Small breakdown box: elements at the current sheet switch to FD; with the
+    algebraic clamp every stored state has E.B ~ 0 and E^2 <= B^2 (up to the filter)."""
+    cfg = W.breakdown(nx=16, ny=1, nz=1, x_half=0.5, mode=W.RELAX_THEN_HARD)
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    S = Stepper(pr)
+    for _ in range(3):
+        st = S.step(st)
+    fd = np.nonzero(st["mask"])[0]
+    assert set(fd.tolist()) >= {6, 9}
+    U = st["ufd"][:, fd]
+    E, B = U[0:3], U[3:6]
+    assert np.abs(np.sum(E * B, 0)).max() < 1e-12
+    assert (np.sum(E * E, 0) - np.sum(B * B, 0)).max() < 1e-12
