@@ -1,0 +1,285 @@
+#!/usr/bin/env python3
+"""Benchmark of the GRFFE DG-FD hybrid step on GB300.
+
+Workload: the FFE breakdown / current-sheet problem, box [-2,2]x[-0.25,0.25]^2,
+64x8x8 elements at P=5 (884,736 LGL nodes; troubled elements on 11^3 subcells),
+eta = 1e3, FP64.  A step is one IMEX-SSP3(4,3,3) step of the whole hybrid path:
+3 right-hand sides + 4 stage solves, filter, indicator, rollback and FD<->DG
+switching.  Metric: element-node updates per second (one DG node or FD cell
+advanced through one explicit RHS and its stage update).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun every rank advances its own
+replica (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ffe_workloads as W  # noqa: E402
+
+METRIC = "RHS element-node updates/s FP64 at 1 GB300, % roofline; adjoint/forward time"
+UNIT = "element-node updates/s"
+# dram bytes (read + write) per launch of the dominant kernel from an ncu capture
+# (profiles/ summary of the same kernel); None until measured on the current kernel
+TRAFFIC_PER_LAUNCH = {}
+
+CPU_SAMPLE = dict(nx=16, ny=2, nz=2, x_half=0.5)
+CPU_SAMPLE_TEXT = ("oracle (numpy fp64, 1 thread) on a 16x2x2-element slab of the breakdown "
+                   "workload (same element width, order and current sheet), whole hybrid steps")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(steps, budget_s=None):
+    """Time the oracle, as it stands, on the bounded sample (1 thread)."""
+    from oracle.problem import Problem
+    from oracle.stepper import Stepper
+    import numpy as np
+    cfg = W.breakdown(**CPU_SAMPLE)
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    S = Stepper(pr)
+    nn, nc = (cfg["P"] + 1) ** 3, (2 * cfg["P"] + 1) ** 3
+    units, t0, done = 0, time.perf_counter(), 0
+    for _ in range(steps):
+        fd = int(st["mask"].sum())
+        st = S.step(st)
+        units += 3 * ((pr.disc.E - fd) * nn + fd * nc)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return units / dt, dt, done
+
+
+def cpu_baseline_subprocess(steps, budget_s):
+    """Run the oracle timing in a fresh single-threaded interpreter (spawned, no CUDA)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "r, dt, n = bench.cpu_oracle_rate(%d, %r); print(json.dumps([r, dt, n]))" % (ROOT, steps, budget_s))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    r, dt, n = json.loads(out.stdout.strip().splitlines()[-1])
+    return r, dt, n
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nme, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nme)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    per_step_budget = None
+    for _ in range(args.warmup):
+        pass
+    r, dt, n = cpu_baseline_subprocess(args.steps + args.warmup, per_step_budget)
+    line = {"impl": "reference", "metric": METRIC, "value": r, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "breakdown 16x2x2 slab (oracle sample)", "P": 5},
+            "cpu_baseline": {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": CPU_SAMPLE_TEXT + f", {n} steps in {dt:.1f} s"},
+            "e2e": {"value": r, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2404_01531_gb300 import ffe
+    from paper_2404_01531_gb300.roofline import (FP64_PEAK_TFLOPS, FD_FLUX_FLOPS, dg_flops_per_node,
+                                                 fd_faces_per_element)
+
+    cfg = W.breakdown()
+    stream = torch.cuda.current_stream()
+    ctx = ffe.Context(cfg, stream=stream)
+    ctx.set_initial()
+    ctx.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    # ---- timed region: graph replays, inputs resident in HBM (working set >> L2)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    u0 = ctx.info().node_updates
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    inf = ctx.info()
+    units = inf.node_updates - u0
+    n_fd_end = inf.n_fd_elem
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    u = torch.tensor([float(units)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max, units_all = t.item(), u.item()
+    value = units_all / (ms_max / 1e3)
+    launches = None
+    n0 = ctx.launch_count()
+    ctx.step(1)
+    torch.cuda.synchronize()
+    per_step_launches = ctx.launch_count() - n0
+    launches = per_step_launches * args.steps
+
+    # ---- per-kernel event timing of the same steps (eager launches)
+    ctx.set_profiling(True)
+    fd_before = ctx.info().n_fd_elem
+    ctx.step(args.steps)
+    fd_after = ctx.info().n_fd_elem
+    ctx.set_profiling(False)
+    prof = ctx.profile_read()
+    total_ms = sum(v[1] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][1])
+    dom_launches, dom_ms = prof[dom]
+    fd_mean = 0.5 * (fd_before + fd_after)
+    E, P = ctx.n_elem, ctx.P
+    nn = (P + 1) ** 3
+    if dom == "dg_substep":
+        flops = (E - fd_mean) * nn * sum(dg_flops_per_node(P, s) for s in range(3)) / 3.0
+    elif dom == "fd_flux":
+        flops = fd_mean * fd_faces_per_element(P) * FD_FLUX_FLOPS
+    else:
+        flops = None
+    avg_ms = dom_ms / dom_launches
+    roof = None
+    if flops is not None:
+        ach = flops / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+                "kernel": dom, "peak_source": "derived: 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz",
+                "share": dom_ms / total_ms}
+
+    # ---- end to end through the C ABI with host buffers
+    pin = torch.empty(ctx.n_state, dtype=torch.float64, pin_memory=True)
+    pmask = torch.empty(ctx.n_elem, dtype=torch.uint8, pin_memory=True)
+    ctx.download_into(pin.data_ptr(), pmask.data_ptr())
+    ke = max(3, args.steps // 5)
+    u0 = ctx.info().node_updates
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(ke):
+        ctx.upload_from(pin.data_ptr(), pmask.data_ptr())
+        ctx.step(1)
+        ctx.download_into(pin.data_ptr(), pmask.data_ptr())
+    w1 = time.perf_counter()
+    ue = ctx.info().node_updates - u0
+    e2e = {"value": ue * ws / (w1 - w0), "unit": UNIT, "h2d_bytes_per_step": ctx.n_state * 8 + ctx.n_elem,
+           "d2h_bytes_per_step": ctx.n_state * 8 + ctx.n_elem}
+    status = ctx.status()
+    ctx.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            r, dt, n = cpu_baseline_subprocess(40, 20.0)
+            cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": CPU_SAMPLE_TEXT + f", {n} steps in {dt:.1f} s"}
+        except Exception as ex:  # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "breakdown 64x8x8 P=5 (FFE breakdown / current sheet, eta=1e3)",
+                       "elements": E, "P": P, "dg_nodes": E * nn, "fd_elements_end": n_fd_end,
+                       "parallelism": f"replicas x{ws}", "l2": "working set > L2 (no flush needed)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
+            "status_bits": status}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

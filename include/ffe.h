@@ -1,0 +1,182 @@
+/*
+ * ffe.h - C ABI of the GB300 library for the general-relativistic force-free
+ * electrodynamics (GRFFE) DG-FD hybrid scheme of arXiv:2404.01531.
+ *
+ * What the library computes (section numbers are the paper's):
+ *   - the conservative 3+1 force-free system in densitised variables
+ *     U = (E~^i, B~^i, psi~, phi~, q~), fluxes F^j and sources S (Sec. II.A),
+ *     with the driver-term current (drift + eta parallel/rectifier) (Sec. II.B);
+ *   - nodal DG-SEM on Legendre-Gauss-Lobatto points with mass lumping,
+ *     Rusanov face fluxes and the exponential filter (Sec. III.A);
+ *   - conservative FD on (2P+1)^3 subcells with WENO5-Z, Rusanov and the
+ *     4th-order derivative corrector (Sec. III.C.2);
+ *   - IMEX-SSP3(4,3,3) stepping with the stiff current and the cleaning damping
+ *     implicit (Sec. III.B), and the algebraic E.B = 0 / E < B clamp
+ *     (Sec. II.B, conventional approach) as an option;
+ *   - the modal troubled-cell indicator on |B~| with DG<->FD switching and
+ *     rollback of a troubled DG substep (Sec. III.C.1, III.C.3).
+ *
+ * Conventions for every entry point:
+ *   - Every function returns ffe_status.  FFE_OK = 0.  On error a thread-local
+ *     message is available from ffe_last_error(); no exception, longjmp or
+ *     device trap crosses the ABI.
+ *   - Arguments are validated before anything is enqueued (FFE_EINVAL).
+ *   - "_dev" pointers are device pointers owned by the caller (for example a
+ *     torch tensor's data_ptr()); "_host" pointers are host memory owned by the
+ *     caller.  The library owns the context and everything it allocates.
+ *   - All work is enqueued on the CUDA stream given to ffe_create (NULL = the
+ *     legacy default stream).  Functions that return host data synchronise
+ *     that stream.
+ *   - State layout ("state vector", doubles): the DG block [9][n_dg] followed
+ *     by the FD block [9][n_fd].  Element e owns DG nodes
+ *     [e*(P+1)^3, (e+1)*(P+1)^3) with node index i + (P+1)(j + (P+1) k), i along
+ *     xi^1 (fastest), and FD cells [e*(2P+1)^3, (e+1)*(2P+1)^3) ordered the same
+ *     way.  Variable order: E~x E~y E~z B~x B~y B~z psi~ phi~ q~.  Only the block
+ *     matching an element's mask (0 = DG, 1 = FD) is meaningful.
+ */
+#ifndef FFE_H
+#define FFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FFE_OK = 0,
+    FFE_EINVAL = 1,     /* invalid argument or configuration                   */
+    FFE_ENOMEM = 2,     /* device or host allocation failed                    */
+    FFE_ECUDA = 3,      /* a CUDA runtime call failed                          */
+    FFE_ETIMEOUT = 4,   /* a bounded device wait gave up                       */
+    FFE_ENUMERIC = 5,   /* NaN/Inf produced or the stiff solve did not converge */
+    FFE_ESTATE = 6,     /* call not valid in the context's current state       */
+    FFE_ENOTIMPL = 7    /* combination not implemented                         */
+} ffe_status;
+
+typedef struct ffe_ctx ffe_ctx;
+
+/* domain kinds, boundary kinds, metric kinds, initial data, constraint modes */
+enum { FFE_DOMAIN_BOX = 0, FFE_DOMAIN_SHELL6 = 1 };
+enum { FFE_BC_PERIODIC = 1, FFE_BC_DIRICHLET = 2, FFE_BC_NO_INCOMING = 3, FFE_BC_STAR = 4 };
+enum { FFE_METRIC_MINKOWSKI = 0, FFE_METRIC_KERR_SCHILD = 1 };
+enum { FFE_ID_FAST_WAVE = 0, FFE_ID_BREAKDOWN = 1, FFE_ID_CLEANING_MODE = 2,
+       FFE_ID_WALD = 3, FFE_ID_DIPOLE = 4 };
+enum { FFE_RELAX = 0, FFE_HARD = 1, FFE_RELAX_THEN_HARD = 2 };
+
+/* Domain (Sec. III.A; shell: Sec. IV.B).  BOX: [lo, hi], boundary kind per axis
+ * (periodic or a physical kind applied at both ends).  SHELL6: six cubed-sphere
+ * wedges between r_in and r_out, equiangular angular map, logarithmic radial map;
+ * bc_lo[0] applies at r_in, bc_hi[0] at r_out. */
+typedef struct {
+    int kind;
+    double lo[3], hi[3];
+    int bc_lo[3], bc_hi[3];
+    double r_in, r_out;
+} ffe_domain;
+
+/* Elements: BOX n[0] x n[1] x n[2]; SHELL6 n[0] = n[1] angular, n[2] radial per wedge. */
+typedef struct { int n[3]; } ffe_elements;
+
+/* Background metric (Sec. II.A; Kerr-Schild: App. B): mass M, spin a. */
+typedef struct { int kind; double M, a; } ffe_metric;
+
+/* Scheme parameters.  dt = 0 selects the CFL step
+ * dt = cfl (dx)_min / lambda_max * c_over_D (Sec. III.B). */
+typedef struct {
+    double eta, kappa_psi, kappa_phi;   /* driver-term conductivity, cleaning damping  */
+    double cfl, c_over_D, dt;
+    int filter_on; double filter_a, filter_b;        /* exponential filter (Sec. III.A) */
+    int tci_on, tci_M; double tci_alpha;             /* troubled-cell indicator          */
+    double weno_eps; int fd_corrector;               /* FD subcell scheme                */
+    int constraint_mode;                             /* FFE_RELAX | FFE_HARD | ...        */
+    double omega_star;                               /* star rotation (FFE_BC_STAR)       */
+} ffe_params;
+
+/* Sizes of the state vector. */
+typedef struct {
+    int n_elem, P, np1, nc;       /* elements, order, DG points and FD cells per direction */
+    int64_t n_dg, n_fd;           /* DG nodes, FD cells in the whole context              */
+    int64_t n_state;              /* doubles in a state vector: 9 (n_dg + n_fd)           */
+    double dt, dxmin, t;          /* time step, (dx)_min, current time                    */
+    int64_t steps;                /* steps taken                                          */
+    int n_fd_elem;                /* elements currently on FD                             */
+    int64_t node_updates;         /* DG nodes + FD cells advanced through an explicit RHS
+                                     and its stage update, summed since ffe_set_initial     */
+} ffe_info;
+
+/* Create a context: builds the mesh, operator tables and geometry, allocates
+ * the state and work buffers on the current device and binds `cuda_stream`
+ * (a cudaStream_t, or NULL).  *out receives the context on success. */
+ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, int P,
+                      const ffe_metric* metric, const ffe_params* params,
+                      void* cuda_stream, ffe_ctx** out);
+
+/* Set analytic initial data.  id_params (may be NULL when n_params = 0):
+ *   FAST_WAVE      {amp}                 B=(1,b,0), E=(0,0,-b), b = 1 + amp sin(pi x)
+ *   BREAKDOWN      {}                    current sheet of the breakdown workload
+ *   CLEANING_MODE  {eps}                 B=(1+eps sin(pi x),0,0)
+ * The data are set on the LGL nodes, then the troubled-cell indicator runs and
+ * flagged elements take the data at their subcell centres (Sec. III.C.1/III.C.3).
+ * Resets time and step counters. */
+ffe_status ffe_set_initial(ffe_ctx* ctx, int id_kind, const double* id_params, int n_params, int flags);
+
+/* Explicit right-hand side F(U) (volume + boundary correction + explicit
+ * sources; no stiff part) of the state vector U_dev under the context's
+ * current mask, written to dUdt_dev (state-vector layout).  No state change. */
+ffe_status ffe_rhs(ffe_ctx* ctx, const double* U_dev, double* dUdt_dev);
+
+/* Advance the internal state by nsteps IMEX-SSP3(4,3,3) steps including the
+ * troubled-cell indicator, rollback and FD->DG switching. */
+ffe_status ffe_step(ffe_ctx* ctx, int nsteps);
+
+/* Borrowed device view of the current state vector and mask (uint8 per element,
+ * 0 = DG, 1 = FD); valid until the next mutating call. */
+ffe_status ffe_get_state(ffe_ctx* ctx, double** U_dev, unsigned char** mask_dev);
+
+/* Replace the state and mask from caller device buffers (state-vector layout). */
+ffe_status ffe_set_state(ffe_ctx* ctx, const double* U_dev, const unsigned char* mask_dev);
+
+/* Host copies of the state (synchronising); either pointer may be NULL. */
+ffe_status ffe_download(ffe_ctx* ctx, double* U_host, unsigned char* mask_host);
+ffe_status ffe_upload(ffe_ctx* ctx, const double* U_host, const unsigned char* mask_host);
+
+/* Sizes, time step and counters. */
+ffe_status ffe_get_info(ffe_ctx* ctx, ffe_info* info);
+
+/* Device-side status bits accumulated since the last call (synchronising):
+ * bit 0 NaN/Inf seen, bit 1 stiff solve hit its iteration cap.  Cleared on read. */
+ffe_status ffe_get_status(ffe_ctx* ctx, int* status_bits);
+
+/* Troubled-cell indicator ratio sqrt(sum u^2 / sum u^) per element for the DG
+ * data of U_dev (all elements, whatever the mask), written to ratio_dev[n_elem]. */
+ffe_status ffe_tci_ratio(ffe_ctx* ctx, const double* U_dev, double* ratio_dev);
+
+/* Elements whose last indicator ratio was within 1e-12 (relative) of the
+ * threshold during the last ffe_step call: copies up to `cap` indices to
+ * idx_host and the count to *n (synchronising). */
+ffe_status ffe_near_threshold(ffe_ctx* ctx, int* idx_host, int cap, int* n);
+
+/* Kernel launches enqueued by the library since creation (for accounting);
+ * graph replays count the kernel nodes of the captured step. */
+ffe_status ffe_launch_count(ffe_ctx* ctx, int64_t* n);
+
+/* Per-kernel timing.  With on = 1, ffe_step launches eagerly (no graph) and
+ * brackets every kernel with CUDA events on the context stream, synchronising
+ * once per step; totals accumulate until read.  ffe_profile_read writes a JSON
+ * object {"kernel": [launches, total_ms], ...} into buf (NUL-terminated,
+ * truncated to cap) and clears the totals. */
+ffe_status ffe_set_profiling(ffe_ctx* ctx, int on);
+ffe_status ffe_profile_read(ffe_ctx* ctx, char* buf, size_t cap);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* ffe_last_error(void);
+
+/* Free the context and everything it owns (synchronises its stream). */
+void ffe_destroy(ffe_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFE_H */

@@ -28,7 +28,8 @@ class Problem:
         self.met = {"dg": at(d.xyz), "fd": at(d.xyz_fd), "fdface": [at(x) for x in d.xyz_ff], "at": at}
         ikind, ikw = cfg["initial"]
         self.initial = lambda xyz: initial.evaluate(ikind, xyz, **ikw)
-        self.prm = dict(eta=p["eta"], kappa_psi=p["kappa_psi"], kappa_phi=p["kappa_phi"],
+        # the algebraic-only mode has no driver current
+        self.prm = dict(eta=p["eta"] if p["constraint_mode"] != 1 else 0.0, kappa_psi=p["kappa_psi"], kappa_phi=p["kappa_phi"],
                         weno_eps=p["weno_eps"], fd_corrector=p["fd_corrector"],
                         dirichlet=self.initial, omega=p["omega_star"],
                         mode=p["constraint_mode"], filter_on=p["filter_on"], tci_on=p["tci_on"],

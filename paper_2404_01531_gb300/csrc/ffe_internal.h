@@ -1,0 +1,100 @@
+// Internal types shared by the host driver and the CUDA kernels of libffe.
+// Nothing here is part of the public ABI (see include/ffe.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ffe.h"
+
+namespace ffe {
+
+constexpr int NV = 9;          // E~x E~y E~z B~x B~y B~z psi~ phi~ q~
+constexpr int NG = 5;          // components of the stiff operator: E~ (3), psi~, phi~
+constexpr int NJ = 6;          // stored currents: drift (3), full = drift + eta part (3)
+constexpr int MAXNP = 8;       // P <= 7
+constexpr int MAXNC = 15;      // 2P+1
+constexpr int GH = 3;          // FD ghost layers
+
+// IMEX-SSP3(4,3,3) coefficients (Pareschi & Russo 2005).
+constexpr double IM_A = 0.24169426078821;
+constexpr double IM_B = 0.06042356519705;
+constexpr double IM_H = 0.12915286960590;
+
+// substep kinds of the device stage kernels
+enum Sub : int { SUB_A = 0, SUB_B = 1, SUB_C = 2, SUB_RHS = 3 };
+
+// 1-D operator tables of one order P (built on the host in long double).
+struct Tables {
+    int P, np1, nc;
+    double x[MAXNP], w[MAXNP], w0;
+    double D[MAXNP][MAXNP];        // D_ij = l_j'(x_i)
+    double Filt[MAXNP][MAXNP];     // V diag(sigma) V^-1
+    double Pi[MAXNP][MAXNP];       // projection on Legendre modes p <= P - M
+    double P2F[MAXNC][MAXNP];      // DG -> FD (Lagrange evaluation at subcell centres)
+    double F2D[MAXNP][MAXNC];      // FD -> DG (6-point Lagrange, shifted inside)
+    int f2d_lo[MAXNP];             // first subcell of the 6-point stencil of node i
+};
+
+// A field buffer in state-vector layout: [nv][n_dg] then [nv][n_fd].
+struct Field {
+    double* p;
+    int nv;
+    int64_t ndg, nfd;
+    __host__ __device__ double* dg(int v) const { return p + (int64_t)v * ndg; }
+    __host__ __device__ double* fd(int v) const { return p + (int64_t)nv * ndg + (int64_t)v * nfd; }
+};
+
+// Everything a kernel needs to know about the context (passed by value).
+struct Dev {
+    int E, P, np1, nn, nc, ncell;   // elements, order, 1-D sizes, nodes/cells per element
+    int64_t ndg, nfd;
+    // physics and scheme parameters
+    double eta, kpsi, kphi, dt, weno_eps, omega;
+    int mode, filter_on, tci_on, fd_corr;
+    double thr_dg, thr_fd;          // (P+1-M)^-alpha and (P+1-M)^-(alpha+1)
+    // geometry of the affine box: d xi / d x per element and axis
+    const double* ijac;             // [E][3]
+    const double* xyz_dg;           // [3][ndg] node coordinates
+    const double* xyz_fd;           // [3][nfd] subcell-centre coordinates
+    // connectivity
+    const int* nbr;                 // [E][6] neighbour element or -1
+    const int* nbr_face;            // [E][6] the neighbour's face touching mine
+    const int* bc;                  // [E][6] boundary kind when nbr < 0
+    const int* bface;               // [E][6] boundary-face slot (Dirichlet data) or -1
+    const double* bdg;              // [nbf][9][np1*np1] Dirichlet states at face nodes
+    const double* bfd;              // [nbf][9][GH][nc*nc] Dirichlet states in ghost cells
+    const Tables* tab;              // tables of order P
+    // mask, lists and counters (device)
+    unsigned char* mask;            // [E] 0 = DG, 1 = FD
+    unsigned char* switched;        // [E] switched to FD during the current step
+    int* dg_list; int* fd_list; int* flag_list; int* near_list;
+    int* counts;                    // [0] n_dg, [1] n_fd, [2] n_flag, [3] n_near, [4] status bits
+    unsigned long long* units;      // element-node updates (DG nodes + FD cells per substep)
+    // FD scratch: extended cells [12][E][(nc+6)^3], face fluxes [3][9][E][(nc+1) nc^2]
+    double* ext;
+    double* flux;
+};
+
+// kernel launchers (kernels_*.cu); all enqueue on `st`
+void launch_build_lists(const Dev& d, cudaStream_t st);
+void launch_current(const Dev& d, Field U, Field J, const int* list_or_null, int which_count, cudaStream_t st);
+void launch_stage12(const Dev& d, Field un, Field Ua, Field G1, Field G2, cudaStream_t st);
+void launch_dg_substep(const Dev& d, int sub, Field Uin, Field J, Field un, Field F2, Field F3,
+                       Field G1, Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout,
+                       cudaStream_t st);
+void launch_fd_substep(const Dev& d, int sub, const int* list, int count_index, Field Uin, Field J,
+                       Field un, Field F2, Field F3, Field G1, Field G2, Field G3, Field G4,
+                       Field Fout, Field Uout, Field Gout, cudaStream_t st);
+void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F2, Field F3,
+                             Field G1, Field G2, Field G3, Field G4, cudaStream_t st);
+void launch_fd2dg(const Dev& d, Field un, cudaStream_t st);
+void launch_tci_ratio(const Dev& d, const double* Udg, double* ratio, cudaStream_t st);
+void launch_project_init(const Dev& d, Field U, cudaStream_t st);
+
+extern thread_local int64_t g_launch_counter;
+
+// optional per-kernel event timing (host.cu); no-ops unless profiling is on
+void prof_begin(const char* name, cudaStream_t st);
+void prof_end(cudaStream_t st);
+
+}  // namespace ffe

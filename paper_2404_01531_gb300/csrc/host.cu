@@ -1,0 +1,780 @@
+// Host side of libffe: operator tables, mesh and geometry, initial data,
+// context lifetime, the IMEX step driver (captured once into a CUDA graph) and
+// the C ABI declared in include/ffe.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ffe_internal.h"
+
+using namespace ffe;
+
+namespace {
+
+thread_local std::string g_err;
+
+ffe_status fail(ffe_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t _e = (call);                                                          \
+        if (_e != cudaSuccess)                                                            \
+            return fail(FFE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(_e));       \
+    } while (0)
+
+// ---------------------------------------------------------------- tables ----
+typedef long double ld;
+
+void legendre(int n, ld x, ld& L, ld& dL) {
+    ld p0 = 1.0L, p1 = x;
+    if (n == 0) { L = 1.0L; dL = 0.0L; return; }
+    for (int k = 1; k < n; ++k) {
+        ld p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+        p0 = p1;
+        p1 = p2;
+    }
+    L = p1;
+    if (fabsl(x) == 1.0L) dL = (x > 0 ? 1.0L : ((n + 1) % 2 ? -1.0L : 1.0L)) * n * (n + 1) / 2.0L;
+    else dL = n * (p0 - x * p1) / (1.0L - x * x);
+}
+
+// LGL points: +-1 and the zeros of L_N', by Newton from Chebyshev-Lobatto guesses.
+void lgl(int N, std::vector<ld>& x, std::vector<ld>& w) {
+    x.assign(N + 1, 0.0L);
+    w.assign(N + 1, 0.0L);
+    x[0] = -1.0L;
+    x[N] = 1.0L;
+    for (int j = 1; j < N; ++j) {
+        ld t = -cosl(3.14159265358979323846264338327950288L * j / N);
+        for (int it = 0; it < 100; ++it) {
+            ld L, dL;
+            legendre(N, t, L, dL);
+            ld d2 = (2 * t * dL - N * (N + 1) * L) / (1 - t * t);
+            ld dt = dL / d2;
+            t -= dt;
+            if (fabsl(dt) < 1e-19L) break;
+        }
+        x[j] = t;
+    }
+    for (int j = 0; j <= N / 2; ++j) {   // symmetrise
+        ld m = 0.5L * (x[N - j] - x[j]);
+        x[j] = -m;
+        x[N - j] = m;
+    }
+    for (int j = 0; j <= N; ++j) {
+        ld L, dL;
+        legendre(N, x[j], L, dL);
+        w[j] = 2.0L / (N * (N + 1) * L * L);
+    }
+}
+
+bool invert(std::vector<ld>& A, int n) {   // Gauss-Jordan with partial pivoting, in place
+    std::vector<ld> I(n * n, 0.0L);
+    for (int i = 0; i < n; ++i) I[i * n + i] = 1.0L;
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabsl(A[r * n + c]) > fabsl(A[p * n + c])) p = r;
+        if (A[p * n + c] == 0.0L) return false;
+        for (int k = 0; k < n; ++k) { std::swap(A[c * n + k], A[p * n + k]); std::swap(I[c * n + k], I[p * n + k]); }
+        ld piv = A[c * n + c];
+        for (int k = 0; k < n; ++k) { A[c * n + k] /= piv; I[c * n + k] /= piv; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            ld f = A[r * n + c];
+            for (int k = 0; k < n; ++k) { A[r * n + k] -= f * A[c * n + k]; I[r * n + k] -= f * I[c * n + k]; }
+        }
+    }
+    A = I;
+    return true;
+}
+
+ld lagrange(const std::vector<ld>& xs, int j, ld y) {
+    ld r = 1.0L;
+    for (size_t m = 0; m < xs.size(); ++m)
+        if ((int)m != j) r *= (y - xs[m]) / (xs[j] - xs[m]);
+    return r;
+}
+
+void build_tables(int P, double fa, double fb, int M, Tables& T) {
+    memset(&T, 0, sizeof T);
+    const int np1 = P + 1, nc = 2 * P + 1;
+    T.P = P;
+    T.np1 = np1;
+    T.nc = nc;
+    std::vector<ld> x, w;
+    lgl(P, x, w);
+    for (int i = 0; i < np1; ++i) { T.x[i] = (double)x[i]; T.w[i] = (double)w[i]; }
+    T.w0 = (double)w[0];
+    std::vector<ld> L(np1);
+    for (int i = 0; i < np1; ++i) { ld dl; legendre(P, x[i], L[i], dl); }
+    for (int i = 0; i < np1; ++i)
+        for (int j = 0; j < np1; ++j)
+            T.D[i][j] = (i != j) ? (double)(L[i] / (L[j] * (x[i] - x[j]))) : 0.0;
+    T.D[0][0] = -P * (P + 1) / 4.0;
+    T.D[P][P] = P * (P + 1) / 4.0;
+    std::vector<ld> V(np1 * np1), Vi;
+    for (int i = 0; i < np1; ++i)
+        for (int j = 0; j < np1; ++j) { ld l, dl; legendre(j, x[i], l, dl); V[i * np1 + j] = l; }
+    Vi = V;
+    invert(Vi, np1);
+    for (int i = 0; i < np1; ++i)
+        for (int j = 0; j < np1; ++j) {
+            ld sf = 0.0L, sp = 0.0L;
+            for (int m = 0; m < np1; ++m) {
+                ld sig = expl(-(ld)fa * powl((ld)m / P, 2.0L * (ld)fb));
+                ld keep = (m <= P - M) ? 1.0L : 0.0L;
+                sf += V[i * np1 + m] * sig * Vi[m * np1 + j];
+                sp += V[i * np1 + m] * keep * Vi[m * np1 + j];
+            }
+            T.Filt[i][j] = (double)sf;
+            T.Pi[i][j] = (double)sp;
+        }
+    std::vector<ld> xc(nc);
+    const ld dxi = 2.0L / nc;
+    for (int c = 0; c < nc; ++c) xc[c] = -1.0L + (c + 0.5L) * dxi;
+    for (int c = 0; c < nc; ++c)
+        for (int j = 0; j < np1; ++j) T.P2F[c][j] = (double)lagrange(x, j, xc[c]);
+    if (nc >= 6) {
+        for (int i = 0; i < np1; ++i) {
+            ld pos = (x[i] + 1.0L) / dxi - 0.5L;
+            int lo = (int)floorl(pos) - 2;
+            lo = lo < 0 ? 0 : (lo > nc - 6 ? nc - 6 : lo);
+            T.f2d_lo[i] = lo;
+            std::vector<ld> st(xc.begin() + lo, xc.begin() + lo + 6);
+            for (int m = 0; m < 6; ++m) T.F2D[i][lo + m] = (double)lagrange(st, m, x[i]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ initial data --
+void initial_point(int kind, const double* prm, int nprm, const double* X, double* U) {
+    for (int v = 0; v < NV; ++v) U[v] = 0.0;
+    const double x = X[0];
+    if (kind == FFE_ID_FAST_WAVE) {
+        double amp = nprm > 0 ? prm[0] : 0.5;
+        double b = 1.0 + amp * sin(M_PI * x);
+        U[3] = 1.0;
+        U[4] = b;
+        U[2] = -b;
+    } else if (kind == FFE_ID_BREAKDOWN) {
+        U[3] = 1.0;
+        U[4] = x < -0.1 ? 1.0 : (x > 0.1 ? -1.0 : -10.0 * x);
+        U[2] = fabs(x) < 0.1 ? 0.5 : 1.0;
+    } else if (kind == FFE_ID_CLEANING_MODE) {
+        double eps = nprm > 0 ? prm[0] : 1e-3;
+        U[3] = 1.0 + eps * sin(M_PI * x);
+    }
+}
+
+// ---------------------------------------------------------------- profiler --
+struct ProfRec { std::string name; cudaEvent_t a, b; };
+struct Profiler {
+    bool on = false;
+    std::vector<ProfRec> pending;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+    size_t used = 0;
+    std::vector<std::pair<std::string, std::pair<long, double>>> totals;
+    void add(const std::string& n, double ms) {
+        for (auto& t : totals)
+            if (t.first == n) { t.second.first += 1; t.second.second += ms; return; }
+        totals.push_back({n, {1, ms}});
+    }
+};
+thread_local Profiler g_prof;
+
+}  // namespace
+
+namespace ffe {
+void prof_begin(const char* name, cudaStream_t st) {
+    if (!g_prof.on) return;
+    if (g_prof.used == g_prof.pool.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        g_prof.pool.push_back({a, b});
+    }
+    auto& ev = g_prof.pool[g_prof.used++];
+    g_prof.pending.push_back({name, ev.first, ev.second});
+    cudaEventRecord(ev.first, st);
+}
+void prof_end(cudaStream_t st) {
+    if (!g_prof.on || g_prof.pending.empty()) return;
+    cudaEventRecord(g_prof.pending.back().b, st);
+}
+}  // namespace ffe
+
+namespace {
+void prof_collect(cudaStream_t st) {
+    if (!g_prof.on) return;
+    cudaStreamSynchronize(st);
+    for (auto& r : g_prof.pending) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        g_prof.add(r.name, ms);
+    }
+    g_prof.pending.clear();
+    g_prof.used = 0;
+}
+}  // namespace
+
+// ------------------------------------------------------------- context ------
+struct ffe_ctx {
+    ffe_domain dom;
+    ffe_elements el;
+    ffe_metric met;
+    ffe_params prm;
+    cudaStream_t st = nullptr;
+    Dev d{};
+    Tables tab{};
+    int nx = 0, ny = 0, nz = 0;
+    double h[3] = {0, 0, 0};
+    double dxmin = 0.0, t = 0.0;
+    int64_t steps = 0;
+    int id_kind = -1;
+    std::vector<double> id_prm;
+    std::vector<void*> allocs;
+    Field un{}, Ua{}, Ub{}, F2{}, F3{}, G1{}, G2{}, G3{}, G4{}, J{}, Fs{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = true;
+    int graph_kernels = 0;
+    int nbf = 0;                     // boundary faces with Dirichlet data
+    std::vector<int> h_bface;
+};
+
+namespace {
+
+template <typename T>
+ffe_status dalloc(ffe_ctx* c, T** p, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 1);
+    if (e != cudaSuccess) return fail(FFE_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    cudaMemset(q, 0, n * sizeof(T));
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return FFE_OK;
+}
+
+ffe_status alloc_field(ffe_ctx* c, Field& f, int nv) {
+    f.nv = nv;
+    f.ndg = c->d.ndg;
+    f.nfd = c->d.nfd;
+    return dalloc(c, &f.p, (size_t)nv * (f.ndg + f.nfd));
+}
+
+int elem_id(const ffe_ctx* c, int ex, int ey, int ez) { return ex + c->nx * (ey + c->ny * ez); }
+
+// Build the affine box mesh, connectivity and coordinates on the host and upload.
+ffe_status build_box(ffe_ctx* c) {
+    const int E = c->d.E, np1 = c->d.np1, nc = c->d.nc, nn = c->d.nn, ncell = c->d.ncell;
+    const int n[3] = {c->nx, c->ny, c->nz};
+    std::vector<double> ijac(3 * E), xdg(3 * (size_t)c->d.ndg), xfd(3 * (size_t)c->d.nfd);
+    std::vector<int> nbr(6 * E, -1), nbf(6 * E, -1), bc(6 * E, 0), bface(6 * E, -1);
+    int nbfd = 0;
+    for (int ez = 0; ez < c->nz; ++ez)
+        for (int ey = 0; ey < c->ny; ++ey)
+            for (int ex = 0; ex < c->nx; ++ex) {
+                const int e = elem_id(c, ex, ey, ez);
+                const int ix[3] = {ex, ey, ez};
+                for (int dd = 0; dd < 3; ++dd) ijac[3 * e + dd] = 2.0 / c->h[dd];
+                for (int f = 0; f < 6; ++f) {
+                    const int dd = f >> 1, s = f & 1;
+                    int jx[3] = {ix[0], ix[1], ix[2]};
+                    jx[dd] += s ? 1 : -1;
+                    const int kind = s ? c->dom.bc_hi[dd] : c->dom.bc_lo[dd];
+                    if (jx[dd] < 0 || jx[dd] >= n[dd]) {
+                        if (kind == FFE_BC_PERIODIC) jx[dd] = (jx[dd] + n[dd]) % n[dd];
+                        else {
+                            bc[6 * e + f] = kind;
+                            if (kind == FFE_BC_DIRICHLET) bface[6 * e + f] = nbfd++;
+                            continue;
+                        }
+                    }
+                    nbr[6 * e + f] = elem_id(c, jx[0], jx[1], jx[2]);
+                    nbf[6 * e + f] = 2 * dd + (1 - s);
+                }
+                for (int k = 0; k < np1; ++k)
+                    for (int j = 0; j < np1; ++j)
+                        for (int i = 0; i < np1; ++i) {
+                            const int64_t p = (int64_t)e * nn + i + np1 * (j + np1 * k);
+                            const double xi[3] = {c->tab.x[i], c->tab.x[j], c->tab.x[k]};
+                            for (int dd = 0; dd < 3; ++dd)
+                                xdg[dd * c->d.ndg + p] = c->dom.lo[dd] + (ix[dd] + 0.5 * (xi[dd] + 1.0)) * c->h[dd];
+                        }
+                for (int z = 0; z < nc; ++z)
+                    for (int y = 0; y < nc; ++y)
+                        for (int x = 0; x < nc; ++x) {
+                            const int64_t p = (int64_t)e * ncell + x + nc * (y + nc * z);
+                            const int cc[3] = {x, y, z};
+                            for (int dd = 0; dd < 3; ++dd) {
+                                const double xi = -1.0 + (cc[dd] + 0.5) * 2.0 / nc;
+                                xfd[dd * c->d.nfd + p] = c->dom.lo[dd] + (ix[dd] + 0.5 * (xi + 1.0)) * c->h[dd];
+                            }
+                        }
+            }
+    c->nbf = nbfd;
+    c->h_bface = bface;
+    double *d_ijac, *d_xdg, *d_xfd, *d_bdg, *d_bfd;
+    int *d_nbr, *d_nbf, *d_bc, *d_bface;
+    ffe_status s;
+    if ((s = dalloc(c, &d_ijac, ijac.size()))) return s;
+    if ((s = dalloc(c, &d_xdg, xdg.size()))) return s;
+    if ((s = dalloc(c, &d_xfd, xfd.size()))) return s;
+    if ((s = dalloc(c, &d_nbr, nbr.size()))) return s;
+    if ((s = dalloc(c, &d_nbf, nbf.size()))) return s;
+    if ((s = dalloc(c, &d_bc, bc.size()))) return s;
+    if ((s = dalloc(c, &d_bface, bface.size()))) return s;
+    if ((s = dalloc(c, &d_bdg, (size_t)(nbfd > 0 ? nbfd : 1) * NV * np1 * np1))) return s;
+    if ((s = dalloc(c, &d_bfd, (size_t)(nbfd > 0 ? nbfd : 1) * NV * GH * nc * nc))) return s;
+    CK(cudaMemcpy(d_ijac, ijac.data(), ijac.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_xdg, xdg.data(), xdg.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_xfd, xfd.data(), xfd.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_nbf, nbf.data(), nbf.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_bc, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_bface, bface.data(), bface.size() * 4, cudaMemcpyHostToDevice));
+    c->d.ijac = d_ijac;
+    c->d.xyz_dg = d_xdg;
+    c->d.xyz_fd = d_xfd;
+    c->d.nbr = d_nbr;
+    c->d.nbr_face = d_nbf;
+    c->d.bc = d_bc;
+    c->d.bface = d_bface;
+    c->d.bdg = d_bdg;
+    c->d.bfd = d_bfd;
+    // (dx)_min: smallest gap between adjacent LGL nodes along any element line
+    double gap = 1e300;
+    for (int i = 0; i < np1 - 1; ++i) gap = fmin(gap, c->tab.x[i + 1] - c->tab.x[i]);
+    c->dxmin = 1e300;
+    for (int dd = 0; dd < 3; ++dd) c->dxmin = fmin(c->dxmin, 0.5 * c->h[dd] * gap);
+    return FFE_OK;
+}
+
+// Dirichlet boundary data = the initial data at face nodes and ghost-cell centres.
+ffe_status fill_dirichlet(ffe_ctx* c) {
+    if (c->nbf == 0) return FFE_OK;
+    const int np1 = c->d.np1, nc = c->d.nc, E = c->d.E;
+    std::vector<double> bdg((size_t)c->nbf * NV * np1 * np1), bfd((size_t)c->nbf * NV * GH * nc * nc);
+    for (int e = 0; e < E; ++e) {
+        const int ix[3] = {e % c->nx, (e / c->nx) % c->ny, e / (c->nx * c->ny)};
+        for (int f = 0; f < 6; ++f) {
+            const int slot = c->h_bface[6 * e + f];
+            if (slot < 0) continue;
+            const int dd = f >> 1, s = f & 1;
+            const int t1 = dd == 0 ? 1 : 0, t2 = dd == 2 ? 1 : 2;
+            for (int b = 0; b < np1; ++b)
+                for (int a = 0; a < np1; ++a) {
+                    double xi[3];
+                    xi[dd] = s ? 1.0 : -1.0;
+                    xi[t1] = c->tab.x[a];
+                    xi[t2] = c->tab.x[b];
+                    double X[3], U[NV];
+                    for (int q = 0; q < 3; ++q) X[q] = c->dom.lo[q] + (ix[q] + 0.5 * (xi[q] + 1.0)) * c->h[q];
+                    initial_point(c->id_kind, c->id_prm.data(), (int)c->id_prm.size(), X, U);
+                    for (int v = 0; v < NV; ++v) bdg[((size_t)slot * NV + v) * np1 * np1 + a + np1 * b] = U[v];
+                }
+            for (int g = 0; g < GH; ++g)
+                for (int b = 0; b < nc; ++b)
+                    for (int a = 0; a < nc; ++a) {
+                        double xi[3];
+                        const double dxi = 2.0 / nc;
+                        xi[dd] = s ? 1.0 + (g + 0.5) * dxi : -(1.0 + (g + 0.5) * dxi);
+                        xi[t1] = -1.0 + (a + 0.5) * dxi;
+                        xi[t2] = -1.0 + (b + 0.5) * dxi;
+                        double X[3], U[NV];
+                        for (int q = 0; q < 3; ++q) X[q] = c->dom.lo[q] + (ix[q] + 0.5 * (xi[q] + 1.0)) * c->h[q];
+                        initial_point(c->id_kind, c->id_prm.data(), (int)c->id_prm.size(), X, U);
+                        for (int v = 0; v < NV; ++v)
+                            bfd[(((size_t)slot * NV + v) * GH + g) * nc * nc + a + nc * b] = U[v];
+                    }
+        }
+    }
+    CK(cudaMemcpy((void*)c->d.bdg, bdg.data(), bdg.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)c->d.bfd, bfd.data(), bfd.size() * 8, cudaMemcpyHostToDevice));
+    return FFE_OK;
+}
+
+// One IMEX-SSP3(4,3,3) step with the hybrid control loop, enqueued on c->st.
+void enqueue_step(ffe_ctx* c) {
+    const Dev& d = c->d;
+    cudaStream_t st = c->st;
+    cudaMemsetAsync(d.counts + 2, 0, 2 * sizeof(int), st);
+    cudaMemsetAsync(d.switched, 0, d.E, st);
+    launch_build_lists(d, st);
+    launch_stage12(d, c->un, c->Ua, c->G1, c->G2, st);
+    struct S { int sub; Field Uin, Fout, Uout, Gout; };
+    const S subs[3] = {{SUB_A, c->Ua, c->F2, c->Ub, c->G3},
+                       {SUB_B, c->Ub, c->F3, c->Ua, c->G4},
+                       {SUB_C, c->Ua, c->Fs, c->un, c->G4}};
+    for (const S& s : subs) {
+        launch_current(d, s.Uin, c->J, nullptr, 0, st);
+        launch_dg_substep(d, s.sub, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, s.Fout, s.Uout,
+                          s.Gout, st);
+        launch_fd_substep(d, s.sub, d.fd_list, 1, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4,
+                          s.Fout, s.Uout, s.Gout, st);
+        if (d.tci_on) {
+            launch_rollback_project(d, s.sub, c->un, s.Uin, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, st);
+            launch_current(d, s.Uin, c->J, d.flag_list, 2, st);
+            launch_fd_substep(d, s.sub, d.flag_list, 2, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3,
+                              c->G4, s.Fout, s.Uout, s.Gout, st);
+            cudaMemsetAsync(d.counts + 2, 0, sizeof(int), st);
+            launch_build_lists(d, st);
+        }
+    }
+    if (d.tci_on) launch_fd2dg(d, c->un, st);
+}
+
+ffe_status run_steps(ffe_ctx* c, int nsteps) {
+    static const bool no_graph = getenv("FFE_NO_GRAPH") != nullptr;
+    for (int n = 0; n < nsteps; ++n) {
+        if (g_prof.on) {
+            enqueue_step(c);
+            prof_collect(c->st);
+            CK(cudaGetLastError());
+            c->t += c->d.dt;
+            c->steps += 1;
+            continue;
+        }
+        if (!no_graph && c->graph_ok && c->gexec == nullptr && c->steps > 0) {
+            // capture one step (kernels were launched eagerly once, so attributes are set)
+            cudaGraph_t g;
+            if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                enqueue_step(c);
+                if (cudaStreamEndCapture(c->st, &g) == cudaSuccess &&
+                    cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess) {
+                    c->graph = g;
+                    size_t nn = 0;
+                    cudaGraphGetNodes(g, nullptr, &nn);
+                    std::vector<cudaGraphNode_t> nodes(nn);
+                    cudaGraphGetNodes(g, nodes.data(), &nn);
+                    c->graph_kernels = 0;
+                    for (auto& nd : nodes) {
+                        cudaGraphNodeType ty;
+                        cudaGraphNodeGetType(nd, &ty);
+                        c->graph_kernels += ty == cudaGraphNodeTypeKernel;
+                    }
+                } else {
+                    c->graph_ok = false;
+                    c->gexec = nullptr;
+                    cudaGetLastError();
+                }
+            } else {
+                c->graph_ok = false;
+                cudaGetLastError();
+            }
+        }
+        if (c->gexec) {
+            CK(cudaGraphLaunch(c->gexec, c->st));
+            g_launch_counter += c->graph_kernels;
+        } else {
+            enqueue_step(c);
+        }
+        CK(cudaGetLastError());
+        c->t += c->d.dt;
+        c->steps += 1;
+    }
+    return FFE_OK;
+}
+
+}  // namespace
+
+
+// ------------------------------------------------------------------ C ABI ---
+extern "C" {
+
+const char* ffe_last_error(void) { return g_err.c_str(); }
+
+ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, int P, const ffe_metric* metric,
+                      const ffe_params* params, void* cuda_stream, ffe_ctx** out) {
+    g_err.clear();
+    if (!domain || !elements || !metric || !params || !out) return fail(FFE_EINVAL, "null argument");
+    *out = nullptr;
+    if (P < 2 || P > 6) return fail(FFE_EINVAL, "order P=%d outside [2, 6]", P);
+    if (params->tci_on && P < 3) return fail(FFE_EINVAL, "FD subcells need P >= 3 (6-point projection stencil)");
+    if (domain->kind != FFE_DOMAIN_BOX) return fail(FFE_ENOTIMPL, "domain kind %d not implemented", domain->kind);
+    if (metric->kind != FFE_METRIC_MINKOWSKI) return fail(FFE_ENOTIMPL, "metric kind %d not implemented", metric->kind);
+    for (int dd = 0; dd < 3; ++dd) {
+        if (elements->n[dd] < 1) return fail(FFE_EINVAL, "elements n[%d] = %d", dd, elements->n[dd]);
+        if (!(domain->hi[dd] > domain->lo[dd])) return fail(FFE_EINVAL, "empty box along axis %d", dd);
+        for (int k : {domain->bc_lo[dd], domain->bc_hi[dd]})
+            if (k < FFE_BC_PERIODIC || k > FFE_BC_STAR) return fail(FFE_EINVAL, "boundary kind %d", k);
+        if ((domain->bc_lo[dd] == FFE_BC_PERIODIC) != (domain->bc_hi[dd] == FFE_BC_PERIODIC))
+            return fail(FFE_EINVAL, "periodic axis %d needs periodic at both ends", dd);
+    }
+    if (params->constraint_mode < FFE_RELAX || params->constraint_mode > FFE_RELAX_THEN_HARD)
+        return fail(FFE_EINVAL, "constraint mode %d", params->constraint_mode);
+    if (params->eta < 0 || params->kappa_psi < 0 || params->kappa_phi < 0) return fail(FFE_EINVAL, "negative damping");
+    if (params->tci_on && (params->tci_M < 1 || params->tci_M > P)) return fail(FFE_EINVAL, "tci_M=%d", params->tci_M);
+    if (params->dt < 0 || (params->dt == 0 && !(params->cfl > 0 && params->c_over_D > 0)))
+        return fail(FFE_EINVAL, "need dt > 0 or cfl > 0 and c_over_D > 0");
+
+    ffe_ctx* c = new ffe_ctx();
+    c->dom = *domain;
+    c->el = *elements;
+    c->met = *metric;
+    c->prm = *params;
+    c->st = (cudaStream_t)cuda_stream;
+    c->nx = elements->n[0];
+    c->ny = elements->n[1];
+    c->nz = elements->n[2];
+    for (int dd = 0; dd < 3; ++dd) c->h[dd] = (domain->hi[dd] - domain->lo[dd]) / elements->n[dd];
+    Dev& d = c->d;
+    d.E = c->nx * c->ny * c->nz;
+    d.P = P;
+    d.np1 = P + 1;
+    d.nn = d.np1 * d.np1 * d.np1;
+    d.nc = 2 * P + 1;
+    d.ncell = d.nc * d.nc * d.nc;
+    d.ndg = (int64_t)d.E * d.nn;
+    d.nfd = (int64_t)d.E * d.ncell;
+    d.eta = params->constraint_mode == FFE_HARD ? 0.0 : params->eta;
+    d.kpsi = params->kappa_psi;
+    d.kphi = params->kappa_phi;
+    d.weno_eps = params->weno_eps;
+    d.omega = params->omega_star;
+    d.mode = params->constraint_mode;
+    d.filter_on = params->filter_on;
+    d.tci_on = params->tci_on;
+    d.fd_corr = params->fd_corrector;
+    d.thr_dg = pow((double)(P + 1 - params->tci_M), -params->tci_alpha);
+    d.thr_fd = pow((double)(P + 1 - params->tci_M), -(params->tci_alpha + 1.0));
+    build_tables(P, params->filter_a, params->filter_b, params->tci_M, c->tab);
+    ffe_status s;
+    Tables* dtab;
+    auto bail = [&](ffe_status s) { ffe_destroy(c); return s; };
+    if ((s = dalloc(c, &dtab, 1))) return bail(s);
+    if (cudaMemcpy(dtab, &c->tab, sizeof(Tables), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(FFE_ECUDA, "table upload"));
+    d.tab = dtab;
+    if ((s = build_box(c))) return bail(s);
+    d.dt = params->dt > 0 ? params->dt : params->cfl * c->dxmin / 1.0 * params->c_over_D;
+    if ((s = dalloc(c, &d.mask, d.E))) return bail(s);
+    if ((s = dalloc(c, &d.switched, d.E))) return bail(s);
+    if ((s = dalloc(c, &d.dg_list, d.E))) return bail(s);
+    if ((s = dalloc(c, &d.fd_list, d.E))) return bail(s);
+    if ((s = dalloc(c, &d.flag_list, d.E))) return bail(s);
+    if ((s = dalloc(c, &d.near_list, 4096))) return bail(s);
+    if ((s = dalloc(c, &d.counts, 8))) return bail(s);
+    if ((s = dalloc(c, &d.units, 1))) return bail(s);
+    for (Field* f : {&c->un, &c->Ua, &c->Ub, &c->F2, &c->F3, &c->Fs})
+        if ((s = alloc_field(c, *f, NV))) return bail(s);
+    for (Field* f : {&c->G1, &c->G2, &c->G3, &c->G4})
+        if ((s = alloc_field(c, *f, NG))) return bail(s);
+    if ((s = alloc_field(c, c->J, NJ))) return bail(s);
+    const int64_t ne = d.nc + 2 * GH;
+    if ((s = dalloc(c, &d.ext, (size_t)12 * d.E * ne * ne * ne))) return bail(s);
+    if ((s = dalloc(c, &d.flux, (size_t)3 * NV * d.E * (d.nc + 1) * d.nc * d.nc))) return bail(s);
+    *out = c;
+    return FFE_OK;
+}
+
+ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) {
+    g_err.clear();
+    if (!c) return fail(FFE_EINVAL, "null context");
+    if (id_kind != FFE_ID_FAST_WAVE && id_kind != FFE_ID_BREAKDOWN && id_kind != FFE_ID_CLEANING_MODE)
+        return fail(FFE_ENOTIMPL, "initial data kind %d not implemented", id_kind);
+    if (n_params < 0 || (n_params > 0 && !id_params)) return fail(FFE_EINVAL, "bad initial-data parameters");
+    (void)flags;
+    c->id_kind = id_kind;
+    c->id_prm.assign(id_params, id_params + n_params);
+    const Dev& d = c->d;
+    std::vector<double> xdg(3 * (size_t)d.ndg), U(NV * (size_t)(d.ndg + d.nfd), 0.0);
+    CK(cudaMemcpy(xdg.data(), d.xyz_dg, xdg.size() * 8, cudaMemcpyDeviceToHost));
+    for (int64_t p = 0; p < d.ndg; ++p) {
+        double X[3] = {xdg[p], xdg[d.ndg + p], xdg[2 * d.ndg + p]}, u[NV];
+        initial_point(id_kind, id_params, n_params, X, u);
+        for (int v = 0; v < NV; ++v) U[v * d.ndg + p] = u[v];
+    }
+    std::vector<unsigned char> mask(d.E, 0);
+    if (d.tci_on) {
+        double* ratio;
+        ffe_status s;
+        if ((s = dalloc(c, &ratio, d.E))) return s;
+        CK(cudaMemcpy(c->un.p, U.data(), NV * d.ndg * 8, cudaMemcpyHostToDevice));
+        launch_tci_ratio(d, c->un.p, ratio, c->st);
+        std::vector<double> r(d.E);
+        CK(cudaMemcpyAsync(r.data(), ratio, d.E * 8, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        std::vector<double> xfd(3 * (size_t)d.nfd);
+        CK(cudaMemcpy(xfd.data(), d.xyz_fd, xfd.size() * 8, cudaMemcpyDeviceToHost));
+        for (int e = 0; e < d.E; ++e) {
+            if (!(r[e] > d.thr_dg)) continue;
+            mask[e] = 1;
+            for (int q = 0; q < d.ncell; ++q) {
+                const int64_t p = (int64_t)e * d.ncell + q;
+                double X[3] = {xfd[p], xfd[d.nfd + p], xfd[2 * d.nfd + p]}, u[NV];
+                initial_point(id_kind, id_params, n_params, X, u);
+                for (int v = 0; v < NV; ++v) U[NV * d.ndg + v * d.nfd + p] = u[v];
+            }
+        }
+    }
+    CK(cudaMemcpy(c->un.p, U.data(), U.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.mask, mask.data(), d.E, cudaMemcpyHostToDevice));
+    ffe_status s;
+    if ((s = fill_dirichlet(c))) return s;
+    CK(cudaMemset(d.units, 0, sizeof(unsigned long long)));
+    c->t = 0.0;
+    c->steps = 0;
+    return FFE_OK;
+}
+
+ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) {
+    g_err.clear();
+    if (!c || !U_dev || !dUdt_dev) return fail(FFE_EINVAL, "null argument");
+    if (c->id_kind < 0) return fail(FFE_ESTATE, "no initial data set (boundary data undefined)");
+    const Dev& d = c->d;
+    Field U{(double*)U_dev, NV, d.ndg, d.nfd}, R{dUdt_dev, NV, d.ndg, d.nfd};
+    launch_build_lists(d, c->st);
+    launch_current(d, U, c->J, nullptr, 0, c->st);
+    launch_dg_substep(d, SUB_RHS, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R, c->G1, c->st);
+    launch_fd_substep(d, SUB_RHS, d.fd_list, 1, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R,
+                      c->G1, c->st);
+    CK(cudaGetLastError());
+    return FFE_OK;
+}
+
+ffe_status ffe_step(ffe_ctx* c, int nsteps) {
+    g_err.clear();
+    if (!c || nsteps < 0) return fail(FFE_EINVAL, "bad argument");
+    if (c->id_kind < 0) return fail(FFE_ESTATE, "no initial data set");
+    return run_steps(c, nsteps);
+}
+
+ffe_status ffe_get_state(ffe_ctx* c, double** U_dev, unsigned char** mask_dev) {
+    if (!c) return fail(FFE_EINVAL, "null context");
+    if (U_dev) *U_dev = c->un.p;
+    if (mask_dev) *mask_dev = c->d.mask;
+    return FFE_OK;
+}
+
+ffe_status ffe_set_state(ffe_ctx* c, const double* U_dev, const unsigned char* mask_dev) {
+    if (!c) return fail(FFE_EINVAL, "null context");
+    const Dev& d = c->d;
+    if (U_dev) CK(cudaMemcpyAsync(c->un.p, U_dev, NV * (d.ndg + d.nfd) * 8, cudaMemcpyDeviceToDevice, c->st));
+    if (mask_dev) CK(cudaMemcpyAsync(d.mask, mask_dev, d.E, cudaMemcpyDeviceToDevice, c->st));
+    return FFE_OK;
+}
+
+ffe_status ffe_download(ffe_ctx* c, double* U_host, unsigned char* mask_host) {
+    if (!c) return fail(FFE_EINVAL, "null context");
+    const Dev& d = c->d;
+    if (U_host) CK(cudaMemcpyAsync(U_host, c->un.p, NV * (d.ndg + d.nfd) * 8, cudaMemcpyDeviceToHost, c->st));
+    if (mask_host) CK(cudaMemcpyAsync(mask_host, d.mask, d.E, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return FFE_OK;
+}
+
+ffe_status ffe_upload(ffe_ctx* c, const double* U_host, const unsigned char* mask_host) {
+    if (!c) return fail(FFE_EINVAL, "null context");
+    const Dev& d = c->d;
+    if (U_host) CK(cudaMemcpyAsync(c->un.p, U_host, NV * (d.ndg + d.nfd) * 8, cudaMemcpyHostToDevice, c->st));
+    if (mask_host) CK(cudaMemcpyAsync(d.mask, mask_host, d.E, cudaMemcpyHostToDevice, c->st));
+    return FFE_OK;
+}
+
+ffe_status ffe_get_info(ffe_ctx* c, ffe_info* info) {
+    if (!c || !info) return fail(FFE_EINVAL, "null argument");
+    const Dev& d = c->d;
+    info->n_elem = d.E;
+    info->P = d.P;
+    info->np1 = d.np1;
+    info->nc = d.nc;
+    info->n_dg = d.ndg;
+    info->n_fd = d.nfd;
+    info->n_state = NV * (d.ndg + d.nfd);
+    info->dt = d.dt;
+    info->dxmin = c->dxmin;
+    info->t = c->t;
+    info->steps = c->steps;
+    std::vector<unsigned char> m(d.E);
+    CK(cudaMemcpyAsync(m.data(), d.mask, d.E, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    int n = 0;
+    for (unsigned char x : m) n += x;
+    info->n_fd_elem = n;
+    unsigned long long u = 0;
+    CK(cudaMemcpy(&u, d.units, sizeof u, cudaMemcpyDeviceToHost));
+    info->node_updates = (int64_t)u;
+    return FFE_OK;
+}
+
+ffe_status ffe_get_status(ffe_ctx* c, int* bits) {
+    if (!c || !bits) return fail(FFE_EINVAL, "null argument");
+    CK(cudaMemcpyAsync(bits, c->d.counts + 4, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemsetAsync(c->d.counts + 4, 0, sizeof(int), c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return FFE_OK;
+}
+
+ffe_status ffe_tci_ratio(ffe_ctx* c, const double* U_dev, double* ratio_dev) {
+    if (!c || !U_dev || !ratio_dev) return fail(FFE_EINVAL, "null argument");
+    launch_tci_ratio(c->d, U_dev, ratio_dev, c->st);
+    CK(cudaGetLastError());
+    return FFE_OK;
+}
+
+ffe_status ffe_near_threshold(ffe_ctx* c, int* idx, int cap, int* n) {
+    if (!c || !n || (cap > 0 && !idx)) return fail(FFE_EINVAL, "bad argument");
+    int cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, c->d.counts + 3, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    cnt = cnt > 4096 ? 4096 : cnt;
+    *n = cnt;
+    if (cap > 0 && cnt > 0)
+        CK(cudaMemcpy(idx, c->d.near_list, (size_t)(cnt < cap ? cnt : cap) * sizeof(int), cudaMemcpyDeviceToHost));
+    return FFE_OK;
+}
+
+ffe_status ffe_launch_count(ffe_ctx* c, int64_t* n) {
+    if (!c || !n) return fail(FFE_EINVAL, "null argument");
+    *n = g_launch_counter;
+    return FFE_OK;
+}
+
+ffe_status ffe_set_profiling(ffe_ctx* c, int on) {
+    if (!c) return fail(FFE_EINVAL, "null context");
+    CK(cudaStreamSynchronize(c->st));
+    g_prof.on = on != 0;
+    g_prof.pending.clear();
+    g_prof.used = 0;
+    return FFE_OK;
+}
+
+ffe_status ffe_profile_read(ffe_ctx* c, char* buf, size_t cap) {
+    if (!c || !buf || cap == 0) return fail(FFE_EINVAL, "bad argument");
+    std::string js = "{";
+    for (size_t i = 0; i < g_prof.totals.size(); ++i) {
+        char tmp[160];
+        snprintf(tmp, sizeof tmp, "%s\"%s\": [%ld, %.6f]", i ? ", " : "", g_prof.totals[i].first.c_str(),
+                 g_prof.totals[i].second.first, g_prof.totals[i].second.second);
+        js += tmp;
+    }
+    js += "}";
+    g_prof.totals.clear();
+    snprintf(buf, cap, "%s", js.c_str());
+    return FFE_OK;
+}
+
+void ffe_destroy(ffe_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,505 @@
+// FD-subcell kernels of libffe (flat metric, affine box elements), Sec. III.C.2:
+//   k_fd_fill_interior / k_fd_fill_ghosts  build, per FD element, an extended
+//       block of 12 quantities (U and J~) with 3 ghost layers per face;
+//   k_fd_flux    one thread per face: WENO5-Z (point-value interpolation form,
+//       Z weights with q = 2) left/right states of the 12 quantities, Rusanov
+//       flux, optional 4th-order corrector with cell-centred fluxes;
+//   k_fd_update  one thread per cell: flux difference, sources and the IMEX stage;
+//   k_rollback_project  DG -> FD projection of a flagged element's substep inputs;
+//   k_fd2dg      end-of-step FD -> DG check with alpha' = alpha + 1 (Sec. III.C.3).
+#include "ffe_internal.h"
+#include "physics.cuh"
+#include "stage.cuh"
+
+namespace ffe {
+
+constexpr int NQ = 12;  // reconstructed quantities: 9 evolved + J~ (3)
+
+__device__ __forceinline__ int ext_n(const Dev& d) { return d.nc + 2 * GH; }
+__device__ __forceinline__ int64_t ext_size(const Dev& d) {
+    const int64_t ne = d.nc + 2 * GH;
+    return ne * ne * ne;
+}
+// ext layout: [NQ][E][ne^3] indexed by list position w
+__device__ __forceinline__ double* ext_at(const Dev& d, int q, int w) {
+    return d.ext + ((int64_t)q * d.E + w) * ext_size(d);
+}
+__device__ __forceinline__ int64_t nface(const Dev& d) { return (int64_t)(d.nc + 1) * d.nc * d.nc; }
+// flux layout: [3][NV][E][nface] indexed by list position w
+__device__ __forceinline__ double* flux_at(const Dev& d, int k, int v, int w) {
+    return d.flux + (((int64_t)k * NV + v) * d.E + w) * nface(d);
+}
+
+__device__ __forceinline__ void axes_of(int dd, int& t1, int& t2) {
+    t1 = dd == 0 ? 1 : 0;
+    t2 = dd == 2 ? 1 : 2;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_fd_fill_interior(Dev d, const int* list, int ci, Field U, Field J) {
+    const int n = d.counts[ci];
+    const int nc = d.nc, ne = nc + 2 * GH;
+    const int64_t total = (int64_t)n * d.ncell;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(q / d.ncell), c = (int)(q % d.ncell);
+        const int e = list[w];
+        const int x = c % nc, y = (c / nc) % nc, z = c / (nc * nc);
+        const int64_t p = (int64_t)e * d.ncell + c;
+        const int64_t o = (x + GH) + ne * ((y + GH) + ne * (z + GH));
+        for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = U.fd(v)[p];
+        for (int k = 0; k < 3; ++k) ext_at(d, NV + k, w)[o] = J.fd(3 + k)[p];
+    }
+}
+
+// One CTA per (list position, face): fill the 3 ghost layers of that face.
+__global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field J) {
+    const Tables& T = *d.tab;
+    const int n = d.counts[ci];
+    const int nc = d.nc, ne = nc + 2 * GH, np1 = d.np1, nn = d.nn;
+    extern __shared__ double sm[];
+    double* su = sm;                          // neighbour DG block [9][nn]
+    double* t1b = su + NV * nn;               // [9][GH][np1][np1]
+    double* t2b = t1b + NV * GH * np1 * np1;  // [9][GH][nc][np1]
+    for (int item = blockIdx.x; item < n * 6; item += gridDim.x) {
+        const int w = item / 6, f = item % 6;
+        const int e = list[w];
+        const int dd = f >> 1, s = f & 1;
+        int t1, t2;
+        axes_of(dd, t1, t2);
+        const int nb = d.nbr[e * 6 + f];
+        const int nper = GH * nc * nc;  // ghost cells of this face
+        auto ghost_offset = [&](int g, int ta, int tb) -> int64_t {
+            int c[3];
+            c[dd] = s ? nc + GH + g : GH - 1 - g;
+            c[t1] = ta + GH;
+            c[t2] = tb + GH;
+            return c[0] + (int64_t)ne * (c[1] + (int64_t)ne * c[2]);
+        };
+        if (nb >= 0 && d.mask[nb] == 1) {
+            const int f2 = d.nbr_face[e * 6 + f];
+            const int d2 = f2 >> 1, s2 = f2 & 1;
+            for (int t = threadIdx.x; t < nper; t += blockDim.x) {
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                int c[3];
+                c[d2] = s2 ? nc - 1 - g : g;
+                c[t1] = ta;
+                c[t2] = tb;
+                const int64_t p = (int64_t)nb * d.ncell + c[0] + nc * (c[1] + nc * c[2]);
+                const int64_t o = ghost_offset(g, ta, tb);
+                for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = U.fd(v)[p];
+                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, w)[o] = J.fd(3 + k)[p];
+            }
+        } else if (nb >= 0) {
+            // DG neighbour: its polynomial at its own subcell centres (DG -> FD), 3 layers
+            const int f2 = d.nbr_face[e * 6 + f];
+            const int d2 = f2 >> 1, s2 = f2 & 1;
+            int u1, u2;
+            axes_of(d2, u1, u2);   // on a box the neighbour's tangential axes equal mine
+            for (int t = threadIdx.x; t < NV * nn; t += blockDim.x)
+                su[t] = U.dg(t / nn)[(int64_t)nb * nn + t % nn];
+            __syncthreads();
+            // contract the normal direction for the 3 layers
+            for (int t = threadIdx.x; t < NV * GH * np1 * np1; t += blockDim.x) {
+                const int v = t / (GH * np1 * np1), r = t % (GH * np1 * np1);
+                const int g = r / (np1 * np1), a1 = r % np1, a2 = (r / np1) % np1;
+                const int cn = s2 ? nc - 1 - g : g;
+                double acc = 0.0;
+                for (int m = 0; m < np1; ++m) {
+                    int c[3];
+                    c[d2] = m; c[u1] = a1; c[u2] = a2;
+                    acc = fma(T.P2F[cn][m], su[v * nn + c[0] + np1 * (c[1] + np1 * c[2])], acc);
+                }
+                t1b[t] = acc;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < NV * GH * nc * np1; t += blockDim.x) {
+                const int v = t / (GH * nc * np1), r = t % (GH * nc * np1);
+                const int g = r / (nc * np1), ta = r % nc, a2 = (r / nc) % np1;
+                double acc = 0.0;
+                for (int m = 0; m < np1; ++m)
+                    acc = fma(T.P2F[ta][m], t1b[((v * GH + g) * np1 + a2) * np1 + m], acc);
+                t2b[t] = acc;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < nper; t += blockDim.x) {
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                double u[NV], jd[3], jf[3];
+                for (int v = 0; v < NV; ++v) {
+                    double acc = 0.0;
+                    for (int m = 0; m < np1; ++m)
+                        acc = fma(T.P2F[tb][m], t2b[((v * GH + g) * np1 + m) * nc + ta], acc);
+                    u[v] = acc;
+                }
+                current_flat(u, d.eta, jd, jf);
+                const int64_t o = ghost_offset(g, ta, tb);
+                for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = u[v];
+                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, w)[o] = jf[k];
+            }
+            __syncthreads();
+        } else {
+            const int kind = d.bc[e * 6 + f];
+            for (int t = threadIdx.x; t < nper; t += blockDim.x) {
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                double u[NV], jd[3], jf[3];
+                if (kind == FFE_BC_DIRICHLET) {
+                    const double* src = d.bfd + (int64_t)d.bface[e * 6 + f] * NV * GH * nc * nc;
+                    for (int v = 0; v < NV; ++v) u[v] = src[(v * GH + g) * nc * nc + ta + nc * tb];
+                } else {
+                    // state from the outermost interior cell of this column
+                    int c[3];
+                    c[dd] = s ? nc - 1 : 0;
+                    c[t1] = ta;
+                    c[t2] = tb;
+                    const int64_t p = (int64_t)e * d.ncell + c[0] + nc * (c[1] + nc * c[2]);
+                    double ui[NV];
+                    for (int v = 0; v < NV; ++v) ui[v] = U.fd(v)[p];
+                    if (kind == FFE_BC_NO_INCOMING) {
+                        double nrm[3] = {0.0, 0.0, 0.0};
+                        nrm[dd] = s ? 1.0 : -1.0;
+                        bc_no_incoming_flat(ui, nrm, u);
+                    } else {
+                        double x[3];
+                        for (int k = 0; k < 3; ++k) x[k] = d.xyz_fd[(int64_t)k * d.nfd + p];
+                        bc_star_flat(ui, x, d.omega, u);
+                    }
+                }
+                current_flat(u, d.eta, jd, jf);
+                const int64_t o = ghost_offset(g, ta, tb);
+                for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = u[v];
+                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, w)[o] = jf[k];
+            }
+        }
+    }
+}
+
+// WENO5-Z at the face right of v2 from v0..v4 (point-value interpolation
+// candidates, ideal weights (1, 10, 5)/16, Jiang-Shu indicators, Z weights q = 2).
+__device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
+    const double p0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
+    const double p1 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
+    const double p2 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
+    const double c13 = 13.0 / 12.0;
+    const double s0a = v0 - 2.0 * v1 + v2, s0b = v0 - 4.0 * v1 + 3.0 * v2;
+    const double s1a = v1 - 2.0 * v2 + v3, s1b = v1 - v3;
+    const double s2a = v2 - 2.0 * v3 + v4, s2b = 3.0 * v2 - 4.0 * v3 + v4;
+    const double b0 = fma(c13 * s0a, s0a, 0.25 * s0b * s0b);
+    const double b1 = fma(c13 * s1a, s1a, 0.25 * s1b * s1b);
+    const double b2 = fma(c13 * s2a, s2a, 0.25 * s2b * s2b);
+    const double tau = fabs(b0 - b2);
+    const double r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
+    const double a0 = 0.0625 * fma(r0, r0, 1.0);
+    const double a1 = 0.625 * fma(r1, r1, 1.0);
+    const double a2 = 0.3125 * fma(r2, r2, 1.0);
+    return fma(a0, p0, fma(a1, p1, a2 * p2)) / (a0 + a1 + a2);
+}
+
+// One thread per (list position, direction, face).
+__global__ void k_fd_flux(Dev d, const int* list, int ci) {
+    const int n = d.counts[ci];
+    const int nc = d.nc, ne = nc + 2 * GH;
+    const int64_t nfc = (int64_t)(nc + 1) * nc * nc;
+    const int64_t total = (int64_t)n * 3 * nfc;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(q / (3 * nfc));
+        const int k = (int)((q / nfc) % 3);
+        const int64_t fi = q % nfc;
+        const int m = (int)(fi % (nc + 1));
+        const int ta = (int)((fi / (nc + 1)) % nc), tb = (int)(fi / ((nc + 1) * nc));
+        int t1, t2;
+        axes_of(k, t1, t2);
+        // extended index of cell (m - 3 + o) along k, o = 0..5
+        int c[3];
+        c[k] = m;
+        c[t1] = ta + GH;
+        c[t2] = tb + GH;
+        const int64_t base = c[0] + (int64_t)ne * (c[1] + (int64_t)ne * c[2]);
+        const int64_t stride = k == 0 ? 1 : (k == 1 ? ne : (int64_t)ne * ne);
+        double UL[NQ], UR[NQ];
+        for (int qq = 0; qq < NQ; ++qq) {
+            const double* src = ext_at(d, qq, w) + base;
+            const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
+            const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
+            UL[qq] = weno5z(v0, v1, v2, v3, v4, d.weno_eps);
+            UR[qq] = weno5z(v5, v4, v3, v2, v1, d.weno_eps);
+        }
+        double FL[NV], FR[NV], Fs[NV];
+        flux_dir_flat(UL, UL + NV, k, FL);
+        flux_dir_flat(UR, UR + NV, k, FR);
+        for (int v = 0; v < NV; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * (UR[v] - UL[v]);
+        if (d.fd_corr) {
+            // cell-centred fluxes of the two cells sharing the face (ext cells m+2, m+3)
+            double Um[NQ], Up[NQ], Fm[NV], Fp[NV];
+            for (int qq = 0; qq < NQ; ++qq) {
+                const double* src = ext_at(d, qq, w) + base;
+                Um[qq] = src[2 * stride];
+                Up[qq] = src[3 * stride];
+            }
+            flux_dir_flat(Um, Um + NV, k, Fm);
+            flux_dir_flat(Up, Up + NV, k, Fp);
+            for (int v = 0; v < NV; ++v) Fs[v] = Fs[v] - (1.0 / 6.0) * (Fm[v] - 2.0 * Fs[v] + Fp[v]);
+        }
+        for (int v = 0; v < NV; ++v) flux_at(d, k, v, w)[fi] = Fs[v];
+    }
+}
+
+// One thread per (list position, cell): flux difference + sources + stage.
+template <int SUB>
+__global__ void k_fd_update(Dev d, const int* list, int ci, SubArgs a, const double* ijac) {
+    const int n = d.counts[ci];
+    const int nc = d.nc;
+    const int64_t total = (int64_t)n * d.ncell;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(q / d.ncell), c = (int)(q % d.ncell);
+        const int e = list[w];
+        const int cc[3] = {c % nc, (c / nc) % nc, c / (nc * nc)};
+        const int64_t p = (int64_t)e * d.ncell + c;
+        double du[NV];
+        double u0[NV];
+        for (int v = 0; v < NV; ++v) u0[v] = a.Uin.fd(v)[p];
+        du[0] = -a.J.fd(0)[p]; du[1] = -a.J.fd(1)[p]; du[2] = -a.J.fd(2)[p];
+        du[3] = du[4] = du[5] = 0.0;
+        du[6] = u0[8];
+        du[7] = du[8] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            int t1, t2;
+            axes_of(k, t1, t2);
+            const int64_t f0 = cc[k] + (int64_t)(nc + 1) * (cc[t1] + nc * cc[t2]);
+            const double sc = ijac[3 * e + k] * (0.5 * nc);
+            for (int v = 0; v < NV; ++v) {
+                const double* fl = flux_at(d, k, v, w);
+                du[v] = fma(-sc, fl[f0 + 1] - fl[f0], du[v]);
+            }
+        }
+        if (SUB == SUB_RHS) {
+            for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
+            continue;
+        }
+        if (c == 0) atomicAdd(d.units, (unsigned long long)d.ncell);
+        if (SUB != SUB_C)
+            for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
+        double u[NV];
+        substep_combine(d, SUB, du, p, true, a, u);
+        bool bad = false;
+        for (int v = 0; v < NV; ++v) {
+            a.Uout.fd(v)[p] = u[v];
+            bad |= !isfinite(u[v]);
+        }
+        if (bad) atomic_status(d, 1);
+        if (SUB != SUB_C) {
+            double g[NG];
+            implicit_G_flat(u, d, g);
+            for (int cg = 0; cg < NG; ++cg) a.Gout.fd(cg)[p] = g[cg];
+        }
+    }
+}
+
+void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin, Field J, Field un,
+                       Field F2, Field F3, Field G1, Field G2, Field G3, Field G4, Field Fout, Field Uout,
+                       Field Gout, cudaStream_t st) {
+    SubArgs a{Uin, J, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
+    const int grid = 152 * 8;
+    prof_begin("fd_fill_interior", st);
+    k_fd_fill_interior<<<grid, 256, 0, st>>>(d, list, ci, Uin, J);
+    prof_end(st);
+    const int np1 = d.np1, nn = d.nn, nc = d.nc;
+    const size_t smem = (size_t)(NV * nn + NV * GH * np1 * np1 + NV * GH * nc * np1) * sizeof(double);
+    cudaFuncSetAttribute(k_fd_fill_ghosts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prof_begin("fd_fill_ghosts", st);
+    k_fd_fill_ghosts<<<152 * 2, 256, smem, st>>>(d, list, ci, Uin, J);
+    prof_end(st);
+    prof_begin("fd_flux", st);
+    k_fd_flux<<<grid, 128, 0, st>>>(d, list, ci);
+    prof_end(st);
+    prof_begin("fd_update", st);
+    switch (sub) {
+        case SUB_A: k_fd_update<SUB_A><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+        case SUB_B: k_fd_update<SUB_B><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+        case SUB_C: k_fd_update<SUB_C><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+        default: k_fd_update<SUB_RHS><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+    }
+    prof_end(st);
+    g_launch_counter += 4;
+}
+
+// ---------------------------------------------------------------------------
+// DG -> FD projection (tensor Lagrange evaluation at subcell centres) of `nv`
+// variables of the flagged elements, in place from the DG block to the FD block.
+__device__ void project_dg2fd_element(const Dev& d, const Field& F, int nv, int e, double* sm) {
+    const Tables& T = *d.tab;
+    const int np1 = d.np1, nn = d.nn, nc = d.nc;
+    double* a = sm;                     // [np1^3]
+    double* b = a + nn;                 // [nc][np1][np1]
+    double* c = b + nc * np1 * np1;     // [nc][nc][np1]
+    for (int v = 0; v < nv; ++v) {
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) a[t] = F.dg(v)[(int64_t)e * nn + t];
+        __syncthreads();
+        for (int t = threadIdx.x; t < nc * np1 * np1; t += blockDim.x) {
+            const int x = t % nc, jk = t / nc;
+            double acc = 0.0;
+            for (int m = 0; m < np1; ++m) acc = fma(T.P2F[x][m], a[m + np1 * jk], acc);
+            b[t] = acc;   // [k][j][x]
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nc * nc * np1; t += blockDim.x) {
+            const int x = t % nc, y = (t / nc) % nc, k = t / (nc * nc);
+            double acc = 0.0;
+            for (int m = 0; m < np1; ++m) acc = fma(T.P2F[y][m], b[x + nc * (m + np1 * k)], acc);
+            c[t] = acc;   // [k][y][x]
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nc * nc * nc; t += blockDim.x) {
+            const int xy = t % (nc * nc), z = t / (nc * nc);
+            double acc = 0.0;
+            for (int m = 0; m < np1; ++m) acc = fma(T.P2F[z][m], c[xy + nc * nc * m], acc);
+            F.fd(v)[(int64_t)e * d.ncell + t] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+struct RollArgs {
+    Field f[8];
+    int nv[8];
+    int nf;
+};
+
+__global__ void k_rollback_project(Dev d, RollArgs r) {
+    extern __shared__ double sm[];
+    const int n = d.counts[2];
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int e = d.flag_list[w];
+        for (int i = 0; i < r.nf; ++i) project_dg2fd_element(d, r.f[i], r.nv[i], e, sm);
+        if (threadIdx.x == 0) d.mask[e] = 1;
+        __syncthreads();
+    }
+}
+
+void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F2, Field F3, Field G1,
+                             Field G2, Field G3, Field G4, cudaStream_t st) {
+    RollArgs r{};
+    int k = 0;
+    auto add = [&](Field f, int nv) { r.f[k] = f; r.nv[k] = nv; ++k; };
+    add(un, NV);
+    add(Uin, NV);
+    if (sub == SUB_A) { add(G1, NG); add(G2, NG); }
+    if (sub == SUB_B) { add(F2, NV); add(G1, NG); add(G2, NG); add(G3, NG); }
+    if (sub == SUB_C) { add(F2, NV); add(F3, NV); add(G2, NG); add(G3, NG); add(G4, NG); }
+    r.nf = k;
+    const int np1 = d.np1, nn = d.nn, nc = d.nc;
+    const size_t smem = (size_t)(nn + nc * np1 * np1 + nc * nc * np1) * sizeof(double);
+    prof_begin("rollback_project", st);
+    k_rollback_project<<<152, 256, smem, st>>>(d, r);
+    prof_end(st);
+    g_launch_counter += 1;
+}
+
+// ---------------------------------------------------------------------------
+// FD -> DG (6-point Lagrange per direction) of variable block `src` (one
+// element, [nc^3]) into dst [np1^3], sum-factorised through shared memory.
+__device__ void project_fd2dg_var(const Dev& d, const double* src, double* dst, double* sm) {
+    const Tables& T = *d.tab;
+    const int np1 = d.np1, nc = d.nc, ncell = d.ncell;
+    double* a = sm;                    // [nc^3]
+    double* b = a + ncell;             // [nc][nc][np1]
+    double* c = b + nc * nc * np1;     // [nc][np1][np1]
+    for (int t = threadIdx.x; t < ncell; t += blockDim.x) a[t] = src[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < nc * nc * np1; t += blockDim.x) {
+        const int i = t % np1, yz = t / np1;
+        const int lo = T.f2d_lo[i];
+        double acc = 0.0;
+        for (int m = 0; m < 6; ++m) acc = fma(T.F2D[i][lo + m], a[lo + m + nc * yz], acc);
+        b[t] = acc;   // [z][y][i]
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nc * np1 * np1; t += blockDim.x) {
+        const int i = t % np1, j = (t / np1) % np1, z = t / (np1 * np1);
+        const int lo = T.f2d_lo[j];
+        double acc = 0.0;
+        for (int m = 0; m < 6; ++m) acc = fma(T.F2D[j][lo + m], b[i + np1 * ((lo + m) + nc * z)], acc);
+        c[t] = acc;   // [z][j][i]
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < np1 * np1 * np1; t += blockDim.x) {
+        const int ij = t % (np1 * np1), k = t / (np1 * np1);
+        const int lo = T.f2d_lo[k];
+        double acc = 0.0;
+        for (int m = 0; m < 6; ++m) acc = fma(T.F2D[k][lo + m], c[ij + np1 * np1 * (lo + m)], acc);
+        dst[t] = acc;
+    }
+    __syncthreads();
+}
+
+// End of step: FD elements that did not switch during the step return to DG
+// when the indicator with alpha' = alpha + 1 finds their FD->DG projection admissible.
+__global__ void k_fd2dg(Dev d, Field un) {
+    extern __shared__ double sm[];
+    const Tables& T = *d.tab;
+    const int np1 = d.np1, nn = d.nn, nc = d.nc, ncell = d.ncell;
+    double* work = sm;                                      // projection scratch
+    double* proj = work + ncell + nc * nc * np1 + nc * np1 * np1;  // [9][nn]
+    double* tmp = proj + NV * nn;                           // [3][nn]
+    __shared__ double red[2];
+    const int n = d.counts[1];
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int e = d.fd_list[w];
+        if (d.switched[e]) continue;
+        for (int v = 3; v < 6; ++v) project_fd2dg_var(d, un.fd(v) + (int64_t)e * ncell, proj + v * nn, work);
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+            const double bx = proj[3 * nn + t], by = proj[4 * nn + t], bz = proj[5 * nn + t];
+            tmp[t] = sqrt(fma(bz, bz, fma(by, by, bx * bx)));
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+            const int i = t % np1, j = (t / np1) % np1, k = t / (np1 * np1);
+            double acc = 0.0;
+            for (int m = 0; m < np1; ++m) acc = fma(T.Pi[i][m], tmp[m + np1 * (j + np1 * k)], acc);
+            tmp[nn + t] = acc;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+            const int i = t % np1, j = (t / np1) % np1, k = t / (np1 * np1);
+            double acc = 0.0;
+            for (int m = 0; m < np1; ++m) acc = fma(T.Pi[j][m], tmp[nn + i + np1 * (m + np1 * k)], acc);
+            tmp[2 * nn + t] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double num = 0.0, den = 0.0;
+            for (int t = 0; t < nn; ++t) {
+                const int i = t % np1, j = (t / np1) % np1;
+                double acc = 0.0;
+                for (int m = 0; m < np1; ++m) acc = fma(T.Pi[t / (np1 * np1)][m], tmp[2 * nn + i + np1 * (j + np1 * m)], acc);
+                const double uh = tmp[t] - acc;
+                num += uh * uh;
+                den += tmp[t] * tmp[t];
+            }
+            const double ratio = den > 0.0 ? sqrt(num / den) : 0.0;
+            if (fabs(ratio - d.thr_fd) <= 1e-12 * d.thr_fd) d.near_list[atomicAdd(&d.counts[3], 1) & 4095] = e;
+            red[0] = ratio > d.thr_fd ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        const bool stay = red[0] != 0.0;
+        __syncthreads();
+        if (stay) continue;
+        for (int v = 0; v < NV; ++v) {
+            if (v < 3 || v > 5) project_fd2dg_var(d, un.fd(v) + (int64_t)e * ncell, proj + v * nn, work);
+        }
+        for (int t = threadIdx.x; t < NV * nn; t += blockDim.x)
+            un.dg(t / nn)[(int64_t)e * nn + t % nn] = proj[t];
+        if (threadIdx.x == 0) d.mask[e] = 0;
+        __syncthreads();
+    }
+}
+
+void launch_fd2dg(const Dev& d, Field un, cudaStream_t st) {
+    const int np1 = d.np1, nn = d.nn, nc = d.nc;
+    const size_t smem = (size_t)(d.ncell + nc * nc * np1 + nc * np1 * np1 + NV * nn + 3 * nn) * sizeof(double);
+    cudaFuncSetAttribute(k_fd2dg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prof_begin("fd2dg", st);
+    k_fd2dg<<<152, 256, smem, st>>>(d, un);
+    prof_end(st);
+    g_launch_counter += 1;
+}
+
+}  // namespace ffe

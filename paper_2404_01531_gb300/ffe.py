@@ -1,0 +1,250 @@
+"""ctypes binding of libffe (include/ffe.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module converts
+Python arguments to the C structs and device pointers.  PyTorch is used for
+device memory (tensors passed by data_ptr) and streams.  Loading fails loudly
+when the compiled library is missing: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libffe.so")
+
+NV = 9
+BC = {"periodic": 1, "dirichlet": 2, "no_incoming": 3, "star": 4}
+ID = {"fast_wave": 0, "breakdown": 1, "cleaning_mode": 2, "wald": 3, "dipole": 4}
+METRIC = {"minkowski": 0, "kerr_schild": 1}
+STATUS = {0: "FFE_OK", 1: "FFE_EINVAL", 2: "FFE_ENOMEM", 3: "FFE_ECUDA", 4: "FFE_ETIMEOUT",
+          5: "FFE_ENUMERIC", 6: "FFE_ESTATE", 7: "FFE_ENOTIMPL"}
+
+# every entry point declared in include/ffe.h
+EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_state", "ffe_set_state",
+           "ffe_download", "ffe_upload", "ffe_get_info", "ffe_get_status", "ffe_tci_ratio",
+           "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
+           "ffe_last_error", "ffe_destroy"]
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
+                ("r_in", ctypes.c_double), ("r_out", ctypes.c_double)]
+
+
+class Elements(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3)]
+
+
+class Metric(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("M", ctypes.c_double), ("a", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("kappa_psi", ctypes.c_double), ("kappa_phi", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("c_over_D", ctypes.c_double), ("dt", ctypes.c_double),
+                ("filter_on", ctypes.c_int), ("filter_a", ctypes.c_double), ("filter_b", ctypes.c_double),
+                ("tci_on", ctypes.c_int), ("tci_M", ctypes.c_int), ("tci_alpha", ctypes.c_double),
+                ("weno_eps", ctypes.c_double), ("fd_corrector", ctypes.c_int),
+                ("constraint_mode", ctypes.c_int), ("omega_star", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int), ("P", ctypes.c_int), ("np1", ctypes.c_int), ("nc", ctypes.c_int),
+                ("n_dg", ctypes.c_int64), ("n_fd", ctypes.c_int64), ("n_state", ctypes.c_int64),
+                ("dt", ctypes.c_double), ("dxmin", ctypes.c_double), ("t", ctypes.c_double),
+                ("steps", ctypes.c_int64), ("n_fd_elem", ctypes.c_int), ("node_updates", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libffe.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libffe.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i, d = ctypes.c_int, ctypes.c_double
+    sig = {
+        "ffe_create": [ctypes.POINTER(Domain), ctypes.POINTER(Elements), i, ctypes.POINTER(Metric),
+                       ctypes.POINTER(Params), P, ctypes.POINTER(P)],
+        "ffe_set_initial": [P, i, ctypes.POINTER(d), i, i],
+        "ffe_rhs": [P, P, P],
+        "ffe_step": [P, i],
+        "ffe_get_state": [P, ctypes.POINTER(P), ctypes.POINTER(P)],
+        "ffe_set_state": [P, P, P],
+        "ffe_download": [P, P, P],
+        "ffe_upload": [P, P, P],
+        "ffe_get_info": [P, ctypes.POINTER(Info)],
+        "ffe_get_status": [P, ctypes.POINTER(i)],
+        "ffe_tci_ratio": [P, P, P],
+        "ffe_near_threshold": [P, ctypes.POINTER(i), i, ctypes.POINTER(i)],
+        "ffe_launch_count": [P, ctypes.POINTER(ctypes.c_int64)],
+        "ffe_set_profiling": [P, i],
+        "ffe_profile_read": [P, ctypes.c_char_p, ctypes.c_size_t],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.ffe_last_error.restype = ctypes.c_char_p
+    lib.ffe_last_error.argtypes = []
+    lib.ffe_destroy.argtypes = [P]
+    lib.ffe_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+class FFEError(RuntimeError):
+    pass
+
+
+def check(status):
+    if status != 0:
+        msg = load().ffe_last_error().decode()
+        raise FFEError(f"{STATUS.get(status, status)}: {msg}")
+
+
+def params_from(p):
+    return Params(p["eta"], p["kappa_psi"], p["kappa_phi"], p["cfl"], p["c_over_D"], p.get("dt", 0.0),
+                  p["filter_on"], p["filter_a"], p["filter_b"], p["tci_on"], p["tci_M"], p["tci_alpha"],
+                  p["weno_eps"], p["fd_corrector"], p["constraint_mode"], p["omega_star"])
+
+
+class _DevArray:
+    """Zero-copy CUDA-array-interface view of library-owned device memory."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+class Context:
+    """One GRFFE problem on the current CUDA device."""
+
+    def __init__(self, cfg, stream=None):
+        import torch
+        lib = load()
+        self.cfg = cfg
+        if cfg["kind"] != "box":
+            raise FFEError("only box domains are built in this version")
+        dom = Domain()
+        dom.kind = 0
+        for a in range(3):
+            dom.lo[a], dom.hi[a] = cfg["lo"][a], cfg["hi"][a]
+            dom.bc_lo[a] = dom.bc_hi[a] = BC[cfg["bc"][a]]
+        el = Elements()
+        for a in range(3):
+            el.n[a] = cfg["n"][a]
+        mk, M, spin = cfg["metric"]
+        met = Metric(METRIC[mk], M, spin)
+        prm = params_from(cfg["params"])
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib.ffe_create(ctypes.byref(dom), ctypes.byref(el), cfg["P"], ctypes.byref(met),
+                             ctypes.byref(prm), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        self.info()
+
+    def close(self):
+        if self.h:
+            load().ffe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        inf = Info()
+        check(load().ffe_get_info(self.h, ctypes.byref(inf)))
+        self.n_elem, self.P, self.np1, self.nc = inf.n_elem, inf.P, inf.np1, inf.nc
+        self.n_dg, self.n_fd, self.n_state = inf.n_dg, inf.n_fd, inf.n_state
+        self.dt, self.dxmin = inf.dt, inf.dxmin
+        return inf
+
+    def set_initial(self, kind=None, params=()):
+        if kind is None:
+            kind, kw = self.cfg["initial"]
+            params = tuple(kw.values())
+        arr = (ctypes.c_double * max(len(params), 1))(*params)
+        check(load().ffe_set_initial(self.h, ID[kind], arr, len(params), 0))
+
+    def step(self, n=1):
+        check(load().ffe_step(self.h, int(n)))
+
+    def rhs(self, U, out):
+        """U, out: float64 CUDA tensors with n_state elements."""
+        check(load().ffe_rhs(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(out.data_ptr())))
+
+    def state(self):
+        """(U, mask) as zero-copy torch views of the library's current state."""
+        import torch
+        pu, pm = ctypes.c_void_p(), ctypes.c_void_p()
+        check(load().ffe_get_state(self.h, ctypes.byref(pu), ctypes.byref(pm)))
+        U = torch.as_tensor(_DevArray(pu.value, (self.n_state,), "<f8"), device="cuda")
+        m = torch.as_tensor(_DevArray(pm.value, (self.n_elem,), "|u1"), device="cuda")
+        return U, m
+
+    def set_state(self, U, mask):
+        check(load().ffe_set_state(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(mask.data_ptr())))
+
+    def download(self):
+        """Host copies (numpy): U (n_state,), mask (n_elem,)."""
+        U = np.empty(self.n_state)
+        m = np.empty(self.n_elem, dtype=np.uint8)
+        check(load().ffe_download(self.h, U.ctypes.data_as(ctypes.c_void_p), m.ctypes.data_as(ctypes.c_void_p)))
+        return U, m
+
+    def download_into(self, U_host_ptr, mask_host_ptr=None):
+        check(load().ffe_download(self.h, ctypes.c_void_p(U_host_ptr),
+                                  ctypes.c_void_p(mask_host_ptr) if mask_host_ptr else None))
+
+    def upload_from(self, U_host_ptr, mask_host_ptr=None):
+        check(load().ffe_upload(self.h, ctypes.c_void_p(U_host_ptr),
+                                ctypes.c_void_p(mask_host_ptr) if mask_host_ptr else None))
+
+    def status(self):
+        b = ctypes.c_int()
+        check(load().ffe_get_status(self.h, ctypes.byref(b)))
+        return b.value
+
+    def tci_ratio(self, U, out):
+        check(load().ffe_tci_ratio(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(out.data_ptr())))
+
+    def near_threshold(self):
+        buf = (ctypes.c_int * 4096)()
+        n = ctypes.c_int()
+        check(load().ffe_near_threshold(self.h, buf, 4096, ctypes.byref(n)))
+        return list(buf[:min(n.value, 4096)])
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        check(load().ffe_launch_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def set_profiling(self, on):
+        check(load().ffe_set_profiling(self.h, int(bool(on))))
+
+    def profile_read(self):
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        check(load().ffe_profile_read(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    # layout helpers: state vector <-> (9, E, ...) blocks
+    def split(self, U):
+        U = np.asarray(U)
+        E, np1, nc = self.n_elem, self.np1, self.nc
+        dg = U[:NV * self.n_dg].reshape(NV, E, np1, np1, np1)
+        fd = U[NV * self.n_dg:].reshape(NV, E, nc, nc, nc)
+        return dg, fd
+
+    def join(self, udg, ufd):
+        return np.concatenate([np.ascontiguousarray(udg).reshape(-1), np.ascontiguousarray(ufd).reshape(-1)])

@@ -1,0 +1,38 @@
+"""Algorithmic FP64 operation counts of the hot kernels (FMA = 2 flops,
+add/mul/div/sqrt = 1), counted from the operations the method defines, not
+from the instructions the kernels happen to issue.  Used for the roofline
+fraction: achieved = count x units per launch / launch time."""
+
+# FP64 peak: 2 FMA lanes per clock per SM x 2 flops x 152 SMs x 2.07 GHz
+# (the GB300's nominal 1.25 TFLOP/s FP64 at its 2070 MHz maximum SM clock).
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+
+def dg_flops_per_node(P, sub, filter_on=True, tci_on=True, solve=True):
+    """One DG node through k_dg_substep: volume term (27 directional (P+1)-point
+    contractions), derivative combination and explicit sources, the lifted
+    Rusanov correction (6 (P+1)^2 face nodes per (P+1)^3 nodes), the IMEX stage
+    combination, the pointwise stiff solve and implicit operator (substeps A, B),
+    the dense F x F x F filter of 9 variables and the indicator (|B|, 3 low-pass
+    contractions, two sums).  sub: 0 (A), 1 (B), 2 (C)."""
+    n = P + 1
+    f = 27 * n * 2              # volume contractions
+    f += 22                     # combination + sources
+    f += 39 * 6 / n             # lift per face node, averaged per node
+    f += (28, 57, 84)[sub]      # stage combination
+    if sub != 2 and solve:
+        f += 38 + 30            # stiff solve + implicit operator
+    if filter_on:
+        f += 3 * n * 2 * 9
+    if tci_on:
+        f += 6 + 3 * n * 2 + 5
+    return f
+
+
+WENO_FLOPS = 73                  # one WENO5-Z face value (3 candidates, 3 indicators, Z weights, 1 div)
+FD_FLUX_FLOPS = 24 * WENO_FLOPS + 45 + 36   # 12 quantities x (L, R) + Rusanov + corrector
+
+
+def fd_faces_per_element(P):
+    nc = 2 * P + 1
+    return 3 * (nc + 1) * nc * nc
