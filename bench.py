@@ -151,6 +151,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=64,
+                    help="elements along x (same width 4/64; smaller values for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -167,7 +169,7 @@ def main():
     from paper_2404_01531_gb300.roofline import (FP64_PEAK_TFLOPS, FD_FLUX_FLOPS, dg_flops_per_node,
                                                  fd_faces_per_element)
 
-    cfg = W.breakdown()
+    cfg = W.breakdown(nx=args.nx, x_half=2.0 * args.nx / 64)
     stream = torch.cuda.current_stream()
     ctx = ffe.Context(cfg, stream=stream)
     ctx.set_initial()
@@ -270,7 +272,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "breakdown 64x8x8 P=5 (FFE breakdown / current sheet, eta=1e3)",
+            "config": {"workload": f"breakdown {args.nx}x8x8 P=5 (FFE breakdown / current sheet, eta=1e3)",
                        "elements": E, "P": P, "dg_nodes": E * nn, "fd_elements_end": n_fd_end,
                        "parallelism": f"replicas x{ws}", "l2": "working set > L2 (no flush needed)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
