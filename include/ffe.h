@@ -170,6 +170,30 @@ ffe_status ffe_launch_count(ffe_ctx* ctx, int64_t* n);
 ffe_status ffe_set_profiling(ffe_ctx* ctx, int on);
 ffe_status ffe_profile_read(ffe_ctx* ctx, char* buf, size_t cap);
 
+/* FD-subcell right-hand side that allocates no memory.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc --
+ * code running inside a CUDA-graph capture, hosts that own all device memory
+ * and forbid allocations behind their back, latency-critical paths where an
+ * allocation would stall.  ffe_create allocates a whole context, so those
+ * callers cannot reach ffe_rhs; this entry point computes the same explicit
+ * FD right-hand side (flat metric, affine element of widths h_host[0..2])
+ * from caller-owned buffers:
+ *   Uext_dev  [9][n_elem][(2P+7)^3]  the 9 evolved variables on each element's
+ *             (2P+1)^3 subcells plus 3 ghost layers on every face (edge and
+ *             corner ghost regions are never read), x fastest;
+ *   dUdt_dev  [9][n_elem][(2P+1)^3]  output, same cell order as the FD block.
+ * Its intermediate data (J~ at every extended cell and the face fluxes) live
+ * in one fixed device array of 2^20 doubles (8 MiB) that every GPU loading the
+ * library holds until exit; calls needing more (per element 3 (2P+7)^3 +
+ * 27 (2P+2)(2P+1)^2 doubles, e.g. at most 19 elements at P = 5) are rejected
+ * with FFE_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, so make it before
+ * any stream capture.  All calls share the array and each overwrites every
+ * entry it reads (nothing needs clearing), so calls that overlap on the GPU
+ * (different streams, no ordering between them) race.  Enqueued on cuda_stream. */
+ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host, double eta, double weno_eps,
+                              int fd_corrector, const double* Uext_dev, double* dUdt_dev, void* cuda_stream);
+
 /* Thread-local message of the last failed call ("" if none). */
 const char* ffe_last_error(void);
 

@@ -492,6 +492,11 @@ ffe_status run_steps(ffe_ctx* c, int nsteps) {
 }  // namespace
 
 
+namespace ffe {
+// error message for entry points defined in other translation units
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace ffe
+
 // ------------------------------------------------------------------ C ABI ---
 extern "C" {
 

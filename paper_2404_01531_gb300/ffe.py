@@ -24,7 +24,7 @@ STATUS = {0: "FFE_OK", 1: "FFE_EINVAL", 2: "FFE_ENOMEM", 3: "FFE_ECUDA", 4: "FFE
 EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_state", "ffe_set_state",
            "ffe_download", "ffe_upload", "ffe_get_info", "ffe_get_status", "ffe_tci_ratio",
            "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
-           "ffe_last_error", "ffe_destroy"]
+           "ffe_fd_rhs_noalloc", "ffe_last_error", "ffe_destroy"]
 
 
 class Domain(ctypes.Structure):
@@ -87,6 +87,7 @@ def load():
         "ffe_launch_count": [P, ctypes.POINTER(ctypes.c_int64)],
         "ffe_set_profiling": [P, i],
         "ffe_profile_read": [P, ctypes.c_char_p, ctypes.c_size_t],
+        "ffe_fd_rhs_noalloc": [i, i, ctypes.POINTER(d), d, d, i, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -102,6 +103,19 @@ def load():
 
 class FFEError(RuntimeError):
     pass
+
+
+def fd_rhs_noalloc(P, Uext, h, eta, weno_eps, fd_corrector, out, stream=None):
+    """FD right-hand side of caller-built extended blocks without any device
+    allocation (see ffe_fd_rhs_noalloc in include/ffe.h).  Uext: float64 CUDA
+    tensor [9][n][(2P+7)^3]; out: float64 CUDA tensor [9][n][(2P+1)^3]."""
+    import torch
+    ne = 2 * P + 7
+    n = Uext.numel() // (9 * ne ** 3)
+    hh = (ctypes.c_double * 3)(*h)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    check(load().ffe_fd_rhs_noalloc(P, n, hh, eta, weno_eps, int(fd_corrector), ctypes.c_void_p(Uext.data_ptr()),
+                                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
 
 
 def check(status):
