@@ -80,3 +80,39 @@ def pulsar_draws(n_inst=32, seed=1531):
         P = 4 + int(2 * next(g))
         out.append(dict(r_lc=r_lc, chi=chi, n_ang=n_ang, n_rad=n_rad, P=P))
     return out
+
+
+def wald(n_ang=8, n_rad=16, P=5, r_in=1.5, r_out=50.0, spin=0.9, steps=1000):
+    """Exact Wald field around a Kerr black hole (M = 1) in Kerr-Schild
+    coordinates on a 6-wedge shell; Dirichlet to the exact solution at both
+    radial ends; eta = 0; CFL factor 0.25."""
+    return dict(name="wald", kind="shell", r_in=r_in, r_out=r_out, n_ang=n_ang, n_rad=n_rad,
+                bc_inner=DIRICHLET, bc_outer=DIRICHLET, P=P, metric=("kerr_schild", 1.0, spin),
+                params=base_params(eta=0.0, cfl=0.25),
+                initial=("wald", dict(M=1.0, a=spin, B0=1.0)), steps=steps)
+
+
+def pulsar(r_lc=6.0, chi=math.pi / 4, n_ang=6, n_rad=12, P=5, mu=1.0, r_out=None, steps=500):
+    """Rotating conducting star of radius 1 with a regularised dipole (delta = 0.1)
+    in flat space: star state at r = 1, no-incoming-Poynting outer boundary at
+    4 R_LC (or r_out), Omega = 1/R_LC, eta = 1e5, CFL 0.25."""
+    return dict(name="pulsar", kind="shell", r_in=1.0, r_out=4.0 * r_lc if r_out is None else r_out,
+                n_ang=n_ang, n_rad=n_rad, bc_inner=STAR, bc_outer=NO_INCOMING, P=P,
+                metric=("minkowski", 0.0, 0.0),
+                params=base_params(eta=1e5, cfl=0.25, omega_star=1.0 / r_lc),
+                initial=("dipole", dict(mu=mu, delta=0.1, chi=chi)), steps=steps)
+
+
+def pulsars(n_inst=32, seed=1531, steps=2000):
+    """The batched workload: one pulsar per seeded draw (R_LC, chi, N_Omega, N_r, P)."""
+    return [pulsar(r_lc=d["r_lc"], chi=d["chi"], n_ang=d["n_ang"], n_rad=d["n_rad"], P=d["P"], steps=steps)
+            for d in pulsar_draws(n_inst, seed)]
+
+
+def adjoint_pulsar(tiny=False, steps=500):
+    """Luminosity-gradient workload: base (mu, chi, Omega) = (1, 45 deg, 1/6),
+    shell r in [1, 24] so that r = 20 is interior; 6 x 6 x 12 per wedge
+    (tiny: 2 x 2 x 4)."""
+    if tiny:
+        return pulsar(r_lc=6.0, chi=math.pi / 4, n_ang=2, n_rad=4, r_out=24.0, steps=steps)
+    return pulsar(r_lc=6.0, chi=math.pi / 4, n_ang=6, n_rad=12, r_out=24.0, steps=steps)

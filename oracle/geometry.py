@@ -172,3 +172,102 @@ class Discretisation:
             dx = np.diff(x, axis=ax)
             best = min(best, np.sqrt(np.sum(dx ** 2, axis=0)).min())
         return best
+
+
+# wedges of the cubed-sphere shell: (normal axis, sign); tangential axes follow cyclically
+WEDGES = ((2, 1), (2, -1), (1, 1), (1, -1), (0, 1), (0, -1))
+
+
+def complex_step_jacobian(fn, xi, h=1e-30):
+    """d fn^i / d xi^k by complex-step differentiation (exact to rounding for
+    analytic maps); fn maps (3, ...) -> (3, ...)."""
+    xi = np.asarray(xi, dtype=np.complex128)
+    cols = []
+    for k in range(3):
+        p = xi.copy()
+        p[k] = p[k] + 1j * h
+        cols.append(np.imag(fn(p)) / h)
+    return np.stack(cols, axis=1)   # [i][k]
+
+
+class ShellMesh:
+    """Spherical shell r_in <= r <= r_out of six cubed-sphere wedges, each split
+    into n_ang x n_ang x n_rad elements (Sec. IV.B).  [reading] Within a wedge the
+    logical coordinates (eta_a, eta_b, eta_r) in [-1,1]^3 map to
+    X = tan(pi eta_a/4), Y = tan(pi eta_b/4) (equiangular) and
+    r = r_in (r_out/r_in)^((eta_r+1)/2) (logarithmic), the point being
+    r (sigma e_n + X e_t1 + Y e_t2) / sqrt(1 + X^2 + Y^2); elements split the
+    logical cube uniformly.  Element e = ia + na (ib + na (ir + nr w)); the
+    reference direction xi^3 is radial; face 4 of ir = 0 lies on r_in, face 5
+    of ir = nr-1 on r_out."""
+
+    def __init__(self, r_in, r_out, n_ang, n_rad, bc_inner, bc_outer):
+        self.r_in, self.r_out = float(r_in), float(r_out)
+        self.na, self.nr = int(n_ang), int(n_rad)
+        self.bc_inner, self.bc_outer = bc_inner, bc_outer
+        self.E = 6 * self.na * self.na * self.nr
+        self.curved = True
+        self._nbr = None
+
+    def eidx(self, e):
+        na, nr = self.na, self.nr
+        return e % na, (e // na) % na, (e // (na * na)) % nr, e // (na * na * nr)
+
+    def map(self, e, xi):
+        ia, ib, ir, w = self.eidx(e)
+        n_ax, sg = WEDGES[w]
+        t1, t2 = (n_ax + 1) % 3, (n_ax + 2) % 3
+        ea = -1.0 + (ia + 0.5 * (xi[0] + 1.0)) * 2.0 / self.na
+        eb = -1.0 + (ib + 0.5 * (xi[1] + 1.0)) * 2.0 / self.na
+        er = -1.0 + (ir + 0.5 * (xi[2] + 1.0)) * 2.0 / self.nr
+        X, Y = np.tan(np.pi * ea / 4.0), np.tan(np.pi * eb / 4.0)
+        r = self.r_in * (self.r_out / self.r_in) ** ((er + 1.0) / 2.0)
+        rho = np.sqrt(1.0 + X * X + Y * Y)
+        out = [None, None, None]
+        out[n_ax] = sg * r / rho
+        out[t1] = r * X / rho
+        out[t2] = r * Y / rho
+        return np.stack(out)
+
+    def inv_jac(self, e, xi):
+        J = complex_step_jacobian(lambda p: self.map(e, p), xi)
+        Jm = np.moveaxis(J, (0, 1), (-2, -1))
+        return np.moveaxis(np.linalg.inv(Jm), (-2, -1), (0, 1))   # [k][j] = d xi^k / d x^j
+
+    def _face_centre(self, e, f):
+        xi = np.zeros((3, 1))
+        xi[f // 2, 0] = -1.0 if f % 2 == 0 else 1.0
+        return self.map(e, xi)[:, 0]
+
+    def _build(self):
+        keys = {}
+        nb = np.full((self.E, 6), -1, dtype=np.int64)
+        scale = self.r_out
+        for e in range(self.E):
+            for f in range(6):
+                c = self._face_centre(e, f)
+                k = tuple(np.round(c / scale * 1e9).astype(np.int64))
+                keys.setdefault(k, []).append((e, f))
+        for k, lst in keys.items():
+            if len(lst) == 2:
+                (e1, f1), (e2, f2) = lst
+                nb[e1, f1], nb[e2, f2] = e2, e1
+            elif len(lst) != 1:
+                raise RuntimeError("face matching failed")
+        self._nbr = nb
+
+    def neighbour(self, e, f):
+        if self._nbr is None:
+            self._build()
+        nb = self._nbr[e, f]
+        if nb >= 0:
+            return nb, BC_NONE
+        _, _, ir, _ = self.eidx(e)
+        if f == 4 and ir == 0:
+            return -1, self.bc_inner
+        if f == 5 and ir == self.nr - 1:
+            return -1, self.bc_outer
+        raise RuntimeError("unmatched interior face")
+
+    def period_shift(self, e, f):
+        return np.zeros(3)

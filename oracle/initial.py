@@ -38,3 +38,77 @@ def cleaning_mode(xyz, eps=1e-3):
 
 def evaluate(kind, xyz, **kw):
     return {"fast_wave": fast_wave, "breakdown": breakdown, "cleaning_mode": cleaning_mode}[kind](xyz, **kw)
+
+
+CS_H = 1e-30
+
+
+def _cs_grad(fn, xyz):
+    """d fn / d x^j by complex step; fn maps (3, ...) -> (n, ...); returns (3, n, ...)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    out = []
+    for j in range(3):
+        p = xyz.astype(np.complex128)
+        p[j] = p[j] + 1j * CS_H
+        out.append(np.imag(fn(p)) / CS_H)
+    return np.stack(out)
+
+
+def wald(xyz, M=1.0, a=0.9, B0=1.0):
+    """Wald's stationary vacuum field (Sec. IV.B.1): A_b = (B0/2)[(d_phi)_b + 2a (d_t)_b]
+    with the Killing vectors d_t = (1,0,0,0) and d_phi = (0,-y,x,0) of the
+    Kerr-Schild chart, F_ab = d_a A_b - d_b A_a (stationary: d_t A = 0),
+    E^i = F^{ib} n_b = -alpha F^{i0}, B~^i = sqrt(gamma) B^i = [ijk] d_j A_k,
+    E~ = sqrt(gamma) E; q~ = 0 (vacuum)."""
+    from .metric import ks_four_metric, adm_from_four
+
+    def A(p):
+        g = ks_four_metric(p, M, a)
+        x, y = p[0], p[1]
+        return 0.5 * B0 * np.stack([g[m, 1] * (-y) + g[m, 2] * x + 2.0 * a * g[m, 0] for m in range(4)])
+    xyz = np.asarray(xyz, dtype=np.float64)
+    dA = _cs_grad(A, xyz)                         # [j][mu] = d_j A_mu
+    shape = xyz.shape[1:]
+    F = np.zeros((4, 4) + shape)
+    for j in range(3):
+        F[0, j + 1] = -dA[j, 0]
+        F[j + 1, 0] = dA[j, 0]
+        for k in range(3):
+            F[j + 1, k + 1] = dA[j, k + 1] - dA[k, j + 1]
+    g = np.real(ks_four_metric(xyz, M, a))
+    gi = np.moveaxis(np.linalg.inv(np.moveaxis(g, (0, 1), (-2, -1))), (-2, -1), (0, 1))
+    alpha, _, gl, _ = adm_from_four(g)
+    sqrtg = np.sqrt(np.linalg.det(np.moveaxis(gl, (0, 1), (-2, -1))))
+    Fup0 = np.einsum('im...,n...,mn...->i...', gi[1:, :], gi[0, :], F)   # F^{i0}
+    U = np.zeros((9,) + shape)
+    U[0:3] = -alpha * sqrtg * Fup0
+    U[3] = dA[1, 3] - dA[2, 2]
+    U[4] = dA[2, 1] - dA[0, 3]
+    U[5] = dA[0, 2] - dA[1, 1]
+    return U
+
+
+def dipole(xyz, mu=1.0, delta=0.1, chi=0.0):
+    """Regularised dipole (Sec. IV.C): A = mu m x x / (r^2 + delta^2)^(3/2) with
+    m = (sin chi, 0, cos chi) (the paper's A_phi for chi = 0), B~ = curl A in
+    flat space; E = psi = phi = q = 0."""
+    m = np.array([np.sin(chi), 0.0, np.cos(chi)])
+
+    def A(p):
+        f = mu / (p[0] ** 2 + p[1] ** 2 + p[2] ** 2 + delta * delta) ** 1.5
+        return np.stack([(m[1] * p[2] - m[2] * p[1]) * f, (m[2] * p[0] - m[0] * p[2]) * f,
+                         (m[0] * p[1] - m[1] * p[0]) * f])
+    dA = _cs_grad(A, xyz)
+    U = np.zeros((9,) + np.shape(xyz)[1:])
+    U[3] = dA[1, 2] - dA[2, 1]
+    U[4] = dA[2, 0] - dA[0, 2]
+    U[5] = dA[0, 1] - dA[1, 0]
+    return U
+
+
+_KINDS = {"fast_wave": fast_wave, "breakdown": breakdown, "cleaning_mode": cleaning_mode,
+          "wald": wald, "dipole": dipole}
+
+
+def evaluate(kind, xyz, **kw):  # noqa: F811  (extends the flat-space table above)
+    return _KINDS[kind](xyz, **kw)

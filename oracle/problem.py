@@ -2,8 +2,9 @@
 import numpy as np
 
 from . import initial, physics as ph
+from .metric import ks_metric
 from .basis import Tables
-from .geometry import BoxMesh, Discretisation, BC_PERIODIC, BC_DIRICHLET, BC_NO_INCOMING, BC_STAR
+from .geometry import BoxMesh, ShellMesh, Discretisation, BC_PERIODIC, BC_DIRICHLET, BC_NO_INCOMING, BC_STAR
 
 _BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "no_incoming": BC_NO_INCOMING, "star": BC_STAR}
 
@@ -16,16 +17,23 @@ class Problem:
         if cfg["kind"] == "box":
             self.mesh = BoxMesh(cfg["lo"], cfg["hi"], cfg["n"], [_BC[b] for b in cfg["bc"]])
         else:
-            raise NotImplementedError(cfg["kind"])
+            self.mesh = ShellMesh(cfg["r_in"], cfg["r_out"], cfg["n_ang"], cfg["n_rad"],
+                                  _BC[cfg["bc_inner"]], _BC[cfg["bc_outer"]])
         self.disc = Discretisation(self.mesh, self.T)
-        mkind = cfg["metric"][0]
+        mkind, M, spin = cfg["metric"]
+        d = self.disc
         if mkind == "minkowski":
             at = lambda xyz: ph.flat_metric()
+        else:
+            at = lambda xyz: ks_metric(xyz, M, spin)
+        self.met = {"dg": at(d.xyz), "fd": at(d.xyz_fd), "fdface": [at(x) for x in d.xyz_ff], "at": at}
+        # lambda_max = max(alpha + |beta|_gamma) over the nodes (Sec. III.B)
+        m = self.met["dg"]
+        if mkind == "minkowski":
             self.lam_max = 1.0
         else:
-            raise NotImplementedError(mkind)
-        d = self.disc
-        self.met = {"dg": at(d.xyz), "fd": at(d.xyz_fd), "fdface": [at(x) for x in d.xyz_ff], "at": at}
+            bl = np.einsum('ij...,j...->i...', m.gl, m.beta)
+            self.lam_max = float(np.max(m.alpha + np.sqrt(np.einsum('i...,i...->...', bl, m.beta))))
         ikind, ikw = cfg["initial"]
         self.initial = lambda xyz: initial.evaluate(ikind, xyz, **ikw)
         # the algebraic-only mode has no driver current

@@ -174,6 +174,10 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
 
 // WENO5-Z at the face right of v2 from v0..v4 (point-value interpolation
 // candidates, ideal weights (1, 10, 5)/16, Jiang-Shu indicators, Z weights q = 2).
+// The Z weights alpha_k = d_k (1 + tau^2/b_k^2), b_k = beta_k + eps, are scaled
+// by b_0^2 b_1^2 b_2^2 so that the normalised combination needs one division:
+//   A_k = d_k (b_k^2 + tau^2) prod_{j != k} b_j^2,  value = sum A_k p_k / sum A_k.
+// With eps >= 1e-40 every A_k stays above 1e-240, inside the normal range.
 __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
     const double p0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
     const double p1 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
@@ -182,15 +186,16 @@ __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double
     const double s0a = v0 - 2.0 * v1 + v2, s0b = v0 - 4.0 * v1 + 3.0 * v2;
     const double s1a = v1 - 2.0 * v2 + v3, s1b = v1 - v3;
     const double s2a = v2 - 2.0 * v3 + v4, s2b = 3.0 * v2 - 4.0 * v3 + v4;
-    const double b0 = fma(c13 * s0a, s0a, 0.25 * s0b * s0b);
-    const double b1 = fma(c13 * s1a, s1a, 0.25 * s1b * s1b);
-    const double b2 = fma(c13 * s2a, s2a, 0.25 * s2b * s2b);
-    const double tau = fabs(b0 - b2);
-    const double r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
-    const double a0 = 0.0625 * fma(r0, r0, 1.0);
-    const double a1 = 0.625 * fma(r1, r1, 1.0);
-    const double a2 = 0.3125 * fma(r2, r2, 1.0);
-    return fma(a0, p0, fma(a1, p1, a2 * p2)) / (a0 + a1 + a2);
+    const double b0 = fma(c13 * s0a, s0a, 0.25 * s0b * s0b) + eps;
+    const double b1 = fma(c13 * s1a, s1a, 0.25 * s1b * s1b) + eps;
+    const double b2 = fma(c13 * s2a, s2a, 0.25 * s2b * s2b) + eps;
+    const double t = b0 - b2;
+    const double t2 = t * t;
+    const double q0 = b0 * b0, q1 = b1 * b1, q2 = b2 * b2;
+    const double A0 = (0.0625 * (q0 + t2)) * (q1 * q2);
+    const double A1 = (0.625 * (q1 + t2)) * (q0 * q2);
+    const double A2 = (0.3125 * (q2 + t2)) * (q0 * q1);
+    return fma(A0, p0, fma(A1, p1, A2 * p2)) / (A0 + A1 + A2);
 }
 
 // One thread per (list position, direction, face).
