@@ -99,7 +99,7 @@ def tensor_points(x1):
 class Discretisation:
     """Tabulated geometry of a mesh for one polynomial degree N."""
 
-    def __init__(self, mesh, T):
+    def __init__(self, mesh, T, fd=True):
         self.mesh, self.T = mesh, T
         E, Np, Nc = mesh.E, T.np1, T.nc
         self.E = E
@@ -107,6 +107,16 @@ class Discretisation:
         xic = tensor_points(T.xc)
         self.xyz = np.stack([mesh.map(e, xin) for e in range(E)], axis=1)      # (3,E,Np,Np,Np)
         self.ijac = np.stack([mesh.inv_jac(e, xin) for e in range(E)], axis=2)  # (3,3,E,...)
+        self.has_fd = fd
+        if not fd:   # DG-only problem: no subcell geometry
+            self.xyz_fd = self.ijac_fd = None
+            self.xyz_ff = self.ijac_ff = None
+            self.nbr = np.full((E, 6), -1, dtype=np.int64)
+            self.bc = np.zeros((E, 6), dtype=np.int64)
+            self.dg_map = np.full((E, 6, Np, Np), -1, dtype=np.int64)
+            self.fd_map = None
+            self._build_connectivity()
+            return
         self.xyz_fd = np.stack([mesh.map(e, xic) for e in range(E)], axis=1)
         self.ijac_fd = np.stack([mesh.inv_jac(e, xic) for e in range(E)], axis=2)
         # FD face points: for direction d, faces at xi^d = -1 + m dxi, m = 0..Nc
@@ -142,6 +152,8 @@ class Discretisation:
                 j = np.argmin(dist, axis=1)
                 assert np.all(dist[np.arange(len(j)), j] < 1e-9 * (1 + np.abs(mine).max()))
                 self.dg_map[e, f] = j.reshape(Np, Np)
+                if not self.has_fd:
+                    continue
                 # FD ghosts: my face points (tangential cell centres on the face)
                 # matched to the neighbour's; layer g of the neighbour counted from its face
                 fpts = self.xyz_ff[d][:, e][(slice(None),) + layer_slice(d, s, Nc + 1, 0)].reshape(3, -1)

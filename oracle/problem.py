@@ -19,14 +19,17 @@ class Problem:
         else:
             self.mesh = ShellMesh(cfg["r_in"], cfg["r_out"], cfg["n_ang"], cfg["n_rad"],
                                   _BC[cfg["bc_inner"]], _BC[cfg["bc_outer"]])
-        self.disc = Discretisation(self.mesh, self.T)
+        self.disc = Discretisation(self.mesh, self.T, fd=bool(p["tci_on"]))
         mkind, M, spin = cfg["metric"]
         d = self.disc
         if mkind == "minkowski":
             at = lambda xyz: ph.flat_metric()
         else:
             at = lambda xyz: ks_metric(xyz, M, spin)
-        self.met = {"dg": at(d.xyz), "fd": at(d.xyz_fd), "fdface": [at(x) for x in d.xyz_ff], "at": at}
+        if d.has_fd:
+            self.met = {"dg": at(d.xyz), "fd": at(d.xyz_fd), "fdface": [at(x) for x in d.xyz_ff], "at": at}
+        else:
+            self.met = {"dg": at(d.xyz), "fd": None, "fdface": None, "at": at}
         # lambda_max = max(alpha + |beta|_gamma) over the nodes (Sec. III.B)
         m = self.met["dg"]
         if mkind == "minkowski":
@@ -53,7 +56,7 @@ class Problem:
         from .stepper import tci_ratio, tci_threshold
         d, T = self.disc, self.T
         udg = self.initial(d.xyz.reshape(3, -1)).reshape((9,) + d.xyz.shape[1:])
-        ufd = np.zeros((9, d.E, T.nc, T.nc, T.nc))
+        ufd = np.zeros((9, d.E, T.nc, T.nc, T.nc)) if d.has_fd else np.zeros((9, d.E, 1, 1, 1))
         mask = np.zeros(d.E, dtype=np.uint8)
         if self.prm["tci_on"]:
             r = tci_ratio(udg[3:6], self.met["dg"], T, np.arange(d.E))

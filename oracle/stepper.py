@@ -42,6 +42,8 @@ def tci_ratio(B, met_dg, T, sel):
     """sqrt(sum u^2 / sum u^) per element, u = |B~|_gamma at the LGL nodes and
     u^ = u - (Pi x Pi x Pi) u the part carried by modes with any index >= N+1-M
     (Sec. III.C.3).  0 when sum u^2 = 0."""
+    if len(sel) == 0:
+        return np.zeros(0)
     m = _met_at(met_dg, sel, ())
     Bl = ph.lower(B, m, B.ndim - 1)
     u = np.sqrt(np.real(np.sum(Bl * B, axis=0)))

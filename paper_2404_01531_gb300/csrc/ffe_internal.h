@@ -15,6 +15,12 @@ constexpr int MAXNP = 8;       // P <= 7
 constexpr int MAXNC = 15;      // 2P+1
 constexpr int GH = 3;          // FD ghost layers
 
+// Stored 3+1 metric quantities per DG node (Kerr-Schild), SoA [NMET][n_dg]:
+// alpha, beta^i, gamma_ij (xx xy xz yy yz zz), gamma^ij (same), sqrt(gamma),
+// d_j alpha, d_j beta^i (index 3 j + i), gamma^jk Gamma^i_jk, K.
+enum MetIdx : int { M_ALPHA = 0, M_BETA = 1, M_GL = 4, M_GU = 10, M_SQRTG = 16, M_DALPHA = 17,
+                    M_DBETA = 20, M_GTRACE = 29, M_K = 32, NMET = 33 };
+
 // IMEX-SSP3(4,3,3) coefficients (Pareschi & Russo 2005).
 constexpr double IM_A = 0.24169426078821;
 constexpr double IM_B = 0.06042356519705;
@@ -54,11 +60,20 @@ struct Dev {
     double thr_dg, thr_fd;          // (P+1-M)^-alpha and (P+1-M)^-(alpha+1)
     // geometry of the affine box: d xi / d x per element and axis
     const double* ijac;             // [E][3]
+    // curved meshes: d xi^k / d x^i per DG node [9][ndg] (index 3 k + i), the
+    // Kerr-Schild metric per DG node [NMET][ndg] (null in flat space), and the
+    // shell map for FD cells and faces (evaluated on the fly)
+    int curved, ks;
+    const double* geo;
+    const double* met;
+    double shell_rin, shell_c;
+    int shell_na, shell_nr;
     const double* xyz_dg;           // [3][ndg] node coordinates
     const double* xyz_fd;           // [3][nfd] subcell-centre coordinates
     // connectivity
     const int* nbr;                 // [E][6] neighbour element or -1
     const int* nbr_face;            // [E][6] the neighbour's face touching mine
+    const int* orient;              // [E][6] orientation code of the shared face (shellmap.cuh)
     const int* bc;                  // [E][6] boundary kind when nbr < 0
     const int* bface;               // [E][6] boundary-face slot (Dirichlet data) or -1
     const double* bdg;              // [nbf][9][np1*np1] Dirichlet states at face nodes
@@ -89,7 +104,9 @@ void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F
                              Field G1, Field G2, Field G3, Field G4, cudaStream_t st);
 void launch_fd2dg(const Dev& d, Field un, cudaStream_t st);
 void launch_tci_ratio(const Dev& d, const double* Udg, double* ratio, cudaStream_t st);
-void launch_project_init(const Dev& d, Field U, cudaStream_t st);
+void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field un, Field F2, Field F3, Field G1,
+                              Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout, cudaStream_t st);
+void launch_stage12_ks(const Dev& d, Field un, Field Ua, Field G1, Field G2, cudaStream_t st);
 
 extern thread_local int64_t g_launch_counter;
 

@@ -7,9 +7,12 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ffe_internal.h"
+#include "geom_host.h"
+#include "shellmap.cuh"
 
 using namespace ffe;
 
@@ -176,7 +179,24 @@ void initial_point(int kind, const double* prm, int nprm, const double* X, doubl
     } else if (kind == FFE_ID_CLEANING_MODE) {
         double eps = nprm > 0 ? prm[0] : 1e-3;
         U[3] = 1.0 + eps * sin(M_PI * x);
+    } else if (kind == FFE_ID_WALD) {
+        wald_point(X, nprm > 0 ? prm[0] : 1.0, nprm > 1 ? prm[1] : 0.0, nprm > 2 ? prm[2] : 1.0, U);
+    } else if (kind == FFE_ID_DIPOLE) {
+        dipole_point(X, nprm > 0 ? prm[0] : 1.0, nprm > 1 ? prm[1] : 0.1, nprm > 2 ? prm[2] : 0.0, U);
     }
+}
+
+// run fn(i) for i in [0, n) on all host cores
+template <typename F>
+void parallel_for(int64_t n, F fn) {
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt == 0 ? 1 : (nt > 64 ? 64 : nt);
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t]() {
+            for (int64_t i = t; i < n; i += nt) fn(i);
+        });
+    for (auto& x : th) x.join();
 }
 
 // ---------------------------------------------------------------- profiler --
@@ -253,6 +273,8 @@ struct ffe_ctx {
     int graph_kernels = 0;
     int nbf = 0;                     // boundary faces with Dirichlet data
     std::vector<int> h_bface;
+    ShellGeo shell{};
+    double lam_max = 1.0;
 };
 
 namespace {
@@ -346,6 +368,9 @@ ffe_status build_box(ffe_ctx* c) {
     CK(cudaMemcpy(d_nbf, nbf.data(), nbf.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_bc, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_bface, bface.data(), bface.size() * 4, cudaMemcpyHostToDevice));
+    int* d_or;
+    if ((s = dalloc(c, &d_or, 6 * (size_t)E))) return s;
+    c->d.orient = d_or;
     c->d.ijac = d_ijac;
     c->d.xyz_dg = d_xdg;
     c->d.xyz_fd = d_xfd;
@@ -363,13 +388,158 @@ ffe_status build_box(ffe_ctx* c) {
     return FFE_OK;
 }
 
+// x(xi) and d xi / d x of element e for either mesh kind.
+MapFn ctx_map(ffe_ctx* c) {
+    if (c->dom.kind == FFE_DOMAIN_SHELL6) {
+        ShellGeo g = c->shell;
+        return [g](int e, const double xi[3], double x[3], double ij[3][3]) { shell_map(g, e, xi, x, ij); };
+    }
+    const int nx = c->nx, ny = c->ny;
+    const double lo[3] = {c->dom.lo[0], c->dom.lo[1], c->dom.lo[2]}, h[3] = {c->h[0], c->h[1], c->h[2]};
+    return [=](int e, const double xi[3], double x[3], double ij[3][3]) {
+        const int ix[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
+        for (int q = 0; q < 3; ++q) {
+            x[q] = lo[q] + (ix[q] + 0.5 * (xi[q] + 1.0)) * h[q];
+            for (int r = 0; r < 3; ++r) ij[q][r] = q == r ? 2.0 / h[q] : 0.0;
+        }
+    };
+}
+
+// Six-wedge shell: coordinates, per-node inverse Jacobians, connectivity with
+// orientation, boundary kinds, Kerr-Schild metric arrays and (dx)_min.
+ffe_status build_shell(ffe_ctx* c) {
+    const int E = c->d.E, np1 = c->d.np1, nc = c->d.nc, nn = c->d.nn, ncell = c->d.ncell;
+    const int64_t ndg = c->d.ndg, nfd = c->d.nfd;
+    MapFn map = ctx_map(c);
+    std::vector<double> xdg(3 * (size_t)ndg), xfd(3 * (size_t)nfd), geo(9 * (size_t)ndg);
+    parallel_for(E, [&](int64_t e) {
+        for (int q = 0; q < nn; ++q) {
+            const int i = q % np1, j = (q / np1) % np1, k = q / (np1 * np1);
+            const double xi[3] = {c->tab.x[i], c->tab.x[j], c->tab.x[k]};
+            double x[3], ij[3][3];
+            map((int)e, xi, x, ij);
+            const int64_t p = e * nn + q;
+            for (int a = 0; a < 3; ++a) xdg[a * ndg + p] = x[a];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) geo[(3 * a + b) * ndg + p] = ij[a][b];
+        }
+        for (int q = 0; q < ncell; ++q) {
+            const int cc[3] = {q % nc, (q / nc) % nc, q / (nc * nc)};
+            double xi[3], x[3], ij[3][3];
+            for (int a = 0; a < 3; ++a) xi[a] = -1.0 + (cc[a] + 0.5) * 2.0 / nc;
+            map((int)e, xi, x, ij);
+            for (int a = 0; a < 3; ++a) xfd[a * nfd + e * ncell + q] = x[a];
+        }
+    });
+    std::vector<double> xn(c->tab.x, c->tab.x + np1);
+    std::vector<int> nbr, nbf, orient, bc(6 * E, 0), bface(6 * E, -1);
+    match_faces(E, map, xn, np1, c->dom.r_out, nbr, nbf, orient);
+    int nbfd = 0;
+    for (int e = 0; e < E; ++e)
+        for (int f = 0; f < 6; ++f) {
+            if (nbr[6 * e + f] == -2) return fail(FFE_EINVAL, "no orientation matches face %d of element %d", f, e);
+            if (nbr[6 * e + f] >= 0) continue;
+            int ia, ib, ir, w;
+            shell_elem(c->shell, e, ia, ib, ir, w);
+            int kind;
+            if (f == 4 && ir == 0) kind = c->dom.bc_lo[0];
+            else if (f == 5 && ir == c->shell.nr - 1) kind = c->dom.bc_hi[0];
+            else return fail(FFE_EINVAL, "unmatched interior face %d of element %d", f, e);
+            if (kind == FFE_BC_PERIODIC) return fail(FFE_EINVAL, "a shell has no periodic boundary");
+            bc[6 * e + f] = kind;
+            if (kind == FFE_BC_DIRICHLET) bface[6 * e + f] = nbfd++;
+        }
+    c->nbf = nbfd;
+    c->h_bface = bface;
+    // (dx)_min along element grid lines
+    double dmin = 1e300;
+    for (int64_t e = 0; e < E; ++e)
+        for (int q = 0; q < nn; ++q) {
+            const int ci[3] = {q % np1, (q / np1) % np1, q / (np1 * np1)};
+            for (int a = 0; a < 3; ++a) {
+                if (ci[a] == np1 - 1) continue;
+                const int q2 = q + (a == 0 ? 1 : (a == 1 ? np1 : np1 * np1));
+                double s2 = 0.0;
+                for (int b = 0; b < 3; ++b) {
+                    const double dx = xdg[b * ndg + e * nn + q2] - xdg[b * ndg + e * nn + q];
+                    s2 += dx * dx;
+                }
+                dmin = fmin(dmin, sqrt(s2));
+            }
+        }
+    c->dxmin = dmin;
+    ffe_status s;
+    double *d_xdg, *d_xfd, *d_geo, *d_bdg, *d_bfd, *d_ijac;
+    int *d_nbr, *d_nbf, *d_bc, *d_bface, *d_or;
+    if ((s = dalloc(c, &d_xdg, xdg.size()))) return s;
+    if ((s = dalloc(c, &d_xfd, xfd.size()))) return s;
+    if ((s = dalloc(c, &d_geo, geo.size()))) return s;
+    if ((s = dalloc(c, &d_ijac, 3 * (size_t)E))) return s;
+    if ((s = dalloc(c, &d_nbr, nbr.size()))) return s;
+    if ((s = dalloc(c, &d_nbf, nbf.size()))) return s;
+    if ((s = dalloc(c, &d_or, orient.size()))) return s;
+    if ((s = dalloc(c, &d_bc, bc.size()))) return s;
+    if ((s = dalloc(c, &d_bface, bface.size()))) return s;
+    if ((s = dalloc(c, &d_bdg, (size_t)(nbfd > 0 ? nbfd : 1) * NV * np1 * np1))) return s;
+    if ((s = dalloc(c, &d_bfd, (size_t)(nbfd > 0 ? nbfd : 1) * NV * GH * nc * nc))) return s;
+    CK(cudaMemcpy(d_xdg, xdg.data(), xdg.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_xfd, xfd.data(), xfd.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_nbf, nbf.data(), nbf.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_or, orient.data(), orient.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_bc, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_bface, bface.data(), bface.size() * 4, cudaMemcpyHostToDevice));
+    Dev& d = c->d;
+    d.xyz_dg = d_xdg;
+    d.xyz_fd = d_xfd;
+    d.geo = d_geo;
+    d.ijac = d_ijac;
+    d.nbr = d_nbr;
+    d.nbr_face = d_nbf;
+    d.orient = d_or;
+    d.bc = d_bc;
+    d.bface = d_bface;
+    d.bdg = d_bdg;
+    d.bfd = d_bfd;
+    d.curved = 1;
+    d.shell_rin = c->shell.r_in;
+    d.shell_c = c->shell.c;
+    d.shell_na = c->shell.na;
+    d.shell_nr = c->shell.nr;
+    if (c->met.kind == FFE_METRIC_KERR_SCHILD) {
+        std::vector<double> met((size_t)NMET * ndg);
+        std::vector<double> lam(ndg);
+        const double M = c->met.M, a = c->met.a;
+        parallel_for(ndg, [&](int64_t p) {
+            double x[3] = {xdg[p], xdg[ndg + p], xdg[2 * ndg + p]}, out[NMET];
+            ks_point(x, M, a, out);
+            for (int q = 0; q < NMET; ++q) met[q * ndg + p] = out[q];
+            // alpha + |beta|_gamma
+            const double* gl = out + M_GL;
+            const double* b = out + M_BETA;
+            const double bb = gl[0] * b[0] * b[0] + gl[3] * b[1] * b[1] + gl[5] * b[2] * b[2] +
+                              2.0 * (gl[1] * b[0] * b[1] + gl[2] * b[0] * b[2] + gl[4] * b[1] * b[2]);
+            lam[p] = out[M_ALPHA] + sqrt(bb);
+        });
+        double* d_met;
+        if ((s = dalloc(c, &d_met, met.size()))) return s;
+        CK(cudaMemcpy(d_met, met.data(), met.size() * 8, cudaMemcpyHostToDevice));
+        d.met = d_met;
+        d.ks = 1;
+        c->lam_max = 0.0;
+        for (double v : lam) c->lam_max = fmax(c->lam_max, v);
+    }
+    return FFE_OK;
+}
+
 // Dirichlet boundary data = the initial data at face nodes and ghost-cell centres.
 ffe_status fill_dirichlet(ffe_ctx* c) {
     if (c->nbf == 0) return FFE_OK;
     const int np1 = c->d.np1, nc = c->d.nc, E = c->d.E;
     std::vector<double> bdg((size_t)c->nbf * NV * np1 * np1), bfd((size_t)c->nbf * NV * GH * nc * nc);
+    MapFn map = ctx_map(c);
     for (int e = 0; e < E; ++e) {
-        const int ix[3] = {e % c->nx, (e / c->nx) % c->ny, e / (c->nx * c->ny)};
         for (int f = 0; f < 6; ++f) {
             const int slot = c->h_bface[6 * e + f];
             if (slot < 0) continue;
@@ -381,8 +551,8 @@ ffe_status fill_dirichlet(ffe_ctx* c) {
                     xi[dd] = s ? 1.0 : -1.0;
                     xi[t1] = c->tab.x[a];
                     xi[t2] = c->tab.x[b];
-                    double X[3], U[NV];
-                    for (int q = 0; q < 3; ++q) X[q] = c->dom.lo[q] + (ix[q] + 0.5 * (xi[q] + 1.0)) * c->h[q];
+                    double X[3], U[NV], ij[3][3];
+                    map(e, xi, X, ij);
                     initial_point(c->id_kind, c->id_prm.data(), (int)c->id_prm.size(), X, U);
                     for (int v = 0; v < NV; ++v) bdg[((size_t)slot * NV + v) * np1 * np1 + a + np1 * b] = U[v];
                 }
@@ -394,8 +564,8 @@ ffe_status fill_dirichlet(ffe_ctx* c) {
                         xi[dd] = s ? 1.0 + (g + 0.5) * dxi : -(1.0 + (g + 0.5) * dxi);
                         xi[t1] = -1.0 + (a + 0.5) * dxi;
                         xi[t2] = -1.0 + (b + 0.5) * dxi;
-                        double X[3], U[NV];
-                        for (int q = 0; q < 3; ++q) X[q] = c->dom.lo[q] + (ix[q] + 0.5 * (xi[q] + 1.0)) * c->h[q];
+                        double X[3], U[NV], ij[3][3];
+                        map(e, xi, X, ij);
                         initial_point(c->id_kind, c->id_prm.data(), (int)c->id_prm.size(), X, U);
                         for (int v = 0; v < NV; ++v)
                             bfd[(((size_t)slot * NV + v) * GH + g) * nc * nc + a + nc * b] = U[v];
@@ -414,15 +584,20 @@ void enqueue_step(ffe_ctx* c) {
     cudaMemsetAsync(d.counts + 2, 0, 2 * sizeof(int), st);
     cudaMemsetAsync(d.switched, 0, d.E, st);
     launch_build_lists(d, st);
-    launch_stage12(d, c->un, c->Ua, c->G1, c->G2, st);
+    if (d.ks) launch_stage12_ks(d, c->un, c->Ua, c->G1, c->G2, st);
+    else launch_stage12(d, c->un, c->Ua, c->G1, c->G2, st);
     struct S { int sub; Field Uin, Fout, Uout, Gout; };
     const S subs[3] = {{SUB_A, c->Ua, c->F2, c->Ub, c->G3},
                        {SUB_B, c->Ub, c->F3, c->Ua, c->G4},
                        {SUB_C, c->Ua, c->Fs, c->un, c->G4}};
     for (const S& s : subs) {
-        launch_current(d, s.Uin, c->J, nullptr, 0, st);
-        launch_dg_substep(d, s.sub, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, s.Fout, s.Uout,
-                          s.Gout, st);
+        if (!d.ks) launch_current(d, s.Uin, c->J, nullptr, 0, st);
+        if (d.curved)
+            launch_dg_substep_curved(d, s.sub, s.Uin, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, s.Fout,
+                                     s.Uout, s.Gout, st);
+        else
+            launch_dg_substep(d, s.sub, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, s.Fout,
+                              s.Uout, s.Gout, st);
         launch_fd_substep(d, s.sub, d.fd_list, 1, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4,
                           s.Fout, s.Uout, s.Gout, st);
         if (d.tci_on) {
@@ -509,9 +684,24 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     *out = nullptr;
     if (P < 2 || P > 6) return fail(FFE_EINVAL, "order P=%d outside [2, 6]", P);
     if (params->tci_on && P < 3) return fail(FFE_EINVAL, "FD subcells need P >= 3 (6-point projection stencil)");
-    if (domain->kind != FFE_DOMAIN_BOX) return fail(FFE_ENOTIMPL, "domain kind %d not implemented", domain->kind);
-    if (metric->kind != FFE_METRIC_MINKOWSKI) return fail(FFE_ENOTIMPL, "metric kind %d not implemented", metric->kind);
-    for (int dd = 0; dd < 3; ++dd) {
+    if (domain->kind != FFE_DOMAIN_BOX && domain->kind != FFE_DOMAIN_SHELL6)
+        return fail(FFE_EINVAL, "domain kind %d", domain->kind);
+    if (metric->kind != FFE_METRIC_MINKOWSKI && metric->kind != FFE_METRIC_KERR_SCHILD)
+        return fail(FFE_EINVAL, "metric kind %d", metric->kind);
+    if (metric->kind == FFE_METRIC_KERR_SCHILD) {
+        if (domain->kind != FFE_DOMAIN_SHELL6) return fail(FFE_EINVAL, "Kerr-Schild needs a shell domain");
+        if (params->tci_on) return fail(FFE_ENOTIMPL, "FD subcells on the Kerr-Schild background are not built");
+        if (!(metric->M > 0) || !(fabs(metric->a) < 1)) return fail(FFE_EINVAL, "need M > 0 and |a| < 1");
+        if (P < 3 || P > 5) return fail(FFE_EINVAL, "curved elements support 3 <= P <= 5");
+    }
+    if (domain->kind == FFE_DOMAIN_SHELL6) {
+        if (!(domain->r_in > 0) || !(domain->r_out > domain->r_in)) return fail(FFE_EINVAL, "need 0 < r_in < r_out");
+        if (elements->n[0] < 1 || elements->n[2] < 1) return fail(FFE_EINVAL, "shell needs n[0], n[2] >= 1");
+        if (P < 3 || P > 5) return fail(FFE_EINVAL, "curved elements support 3 <= P <= 5");
+        for (int k : {domain->bc_lo[0], domain->bc_hi[0]})
+            if (k < FFE_BC_DIRICHLET || k > FFE_BC_STAR) return fail(FFE_EINVAL, "shell boundary kind %d", k);
+    }
+    for (int dd = 0; dd < 3 && domain->kind == FFE_DOMAIN_BOX; ++dd) {
         if (elements->n[dd] < 1) return fail(FFE_EINVAL, "elements n[%d] = %d", dd, elements->n[dd]);
         if (!(domain->hi[dd] > domain->lo[dd])) return fail(FFE_EINVAL, "empty box along axis %d", dd);
         for (int k : {domain->bc_lo[dd], domain->bc_hi[dd]})
@@ -532,12 +722,20 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     c->met = *metric;
     c->prm = *params;
     c->st = (cudaStream_t)cuda_stream;
-    c->nx = elements->n[0];
-    c->ny = elements->n[1];
-    c->nz = elements->n[2];
-    for (int dd = 0; dd < 3; ++dd) c->h[dd] = (domain->hi[dd] - domain->lo[dd]) / elements->n[dd];
     Dev& d = c->d;
-    d.E = c->nx * c->ny * c->nz;
+    if (domain->kind == FFE_DOMAIN_SHELL6) {
+        c->shell.r_in = domain->r_in;
+        c->shell.c = 0.5 * log(domain->r_out / domain->r_in);
+        c->shell.na = elements->n[0];
+        c->shell.nr = elements->n[2];
+        d.E = 6 * elements->n[0] * elements->n[0] * elements->n[2];
+    } else {
+        c->nx = elements->n[0];
+        c->ny = elements->n[1];
+        c->nz = elements->n[2];
+        for (int dd = 0; dd < 3; ++dd) c->h[dd] = (domain->hi[dd] - domain->lo[dd]) / elements->n[dd];
+        d.E = c->nx * c->ny * c->nz;
+    }
     d.P = P;
     d.np1 = P + 1;
     d.nn = d.np1 * d.np1 * d.np1;
@@ -564,8 +762,8 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     if (cudaMemcpy(dtab, &c->tab, sizeof(Tables), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(fail(FFE_ECUDA, "table upload"));
     d.tab = dtab;
-    if ((s = build_box(c))) return bail(s);
-    d.dt = params->dt > 0 ? params->dt : params->cfl * c->dxmin / 1.0 * params->c_over_D;
+    if ((s = (domain->kind == FFE_DOMAIN_SHELL6 ? build_shell(c) : build_box(c)))) return bail(s);
+    d.dt = params->dt > 0 ? params->dt : params->cfl * c->dxmin / c->lam_max * params->c_over_D;
     if ((s = dalloc(c, &d.mask, d.E))) return bail(s);
     if ((s = dalloc(c, &d.switched, d.E))) return bail(s);
     if ((s = dalloc(c, &d.dg_list, d.E))) return bail(s);
@@ -581,7 +779,7 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     if ((s = alloc_field(c, c->J, NJ))) return bail(s);
     const int64_t ne = d.nc + 2 * GH;
     if ((s = dalloc(c, &d.ext, (size_t)12 * d.E * ne * ne * ne))) return bail(s);
-    if ((s = dalloc(c, &d.flux, (size_t)3 * NV * d.E * (d.nc + 1) * d.nc * d.nc))) return bail(s);
+    if ((s = dalloc(c, &d.flux, (size_t)(d.curved ? 9 : 3) * NV * d.E * (d.nc + 1) * d.nc * d.nc))) return bail(s);
     *out = c;
     return FFE_OK;
 }
@@ -589,8 +787,7 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
 ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) {
     g_err.clear();
     if (!c) return fail(FFE_EINVAL, "null context");
-    if (id_kind != FFE_ID_FAST_WAVE && id_kind != FFE_ID_BREAKDOWN && id_kind != FFE_ID_CLEANING_MODE)
-        return fail(FFE_ENOTIMPL, "initial data kind %d not implemented", id_kind);
+    if (id_kind < FFE_ID_FAST_WAVE || id_kind > FFE_ID_DIPOLE) return fail(FFE_EINVAL, "initial data kind %d", id_kind);
     if (n_params < 0 || (n_params > 0 && !id_params)) return fail(FFE_EINVAL, "bad initial-data parameters");
     (void)flags;
     c->id_kind = id_kind;
@@ -598,11 +795,11 @@ ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int
     const Dev& d = c->d;
     std::vector<double> xdg(3 * (size_t)d.ndg), U(NV * (size_t)(d.ndg + d.nfd), 0.0);
     CK(cudaMemcpy(xdg.data(), d.xyz_dg, xdg.size() * 8, cudaMemcpyDeviceToHost));
-    for (int64_t p = 0; p < d.ndg; ++p) {
+    parallel_for(d.ndg, [&](int64_t p) {
         double X[3] = {xdg[p], xdg[d.ndg + p], xdg[2 * d.ndg + p]}, u[NV];
         initial_point(id_kind, id_params, n_params, X, u);
         for (int v = 0; v < NV; ++v) U[v * d.ndg + p] = u[v];
-    }
+    });
     std::vector<unsigned char> mask(d.E, 0);
     if (d.tci_on) {
         double* ratio;
@@ -644,7 +841,10 @@ ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) {
     Field U{(double*)U_dev, NV, d.ndg, d.nfd}, R{dUdt_dev, NV, d.ndg, d.nfd};
     launch_build_lists(d, c->st);
     launch_current(d, U, c->J, nullptr, 0, c->st);
-    launch_dg_substep(d, SUB_RHS, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R, c->G1, c->st);
+    if (d.curved)
+        launch_dg_substep_curved(d, SUB_RHS, U, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R, c->G1, c->st);
+    else
+        launch_dg_substep(d, SUB_RHS, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R, c->G1, c->st);
     launch_fd_substep(d, SUB_RHS, d.fd_list, 1, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R,
                       c->G1, c->st);
     CK(cudaGetLastError());

@@ -1,0 +1,410 @@
+// DG substep on curved elements (cubed-sphere shells), flat or Kerr-Schild metric.
+//
+// Per element (one CTA, one thread per LGL node) the chain-rule strong form
+//   dU/dt = - sum_k sum_j (d xi^k/d x^j)_n (D_k F^j)_n + S
+//           - sum_faces (|grad xi^d|_gamma / w0) (F*.n^ - F_int.n^)
+// with F^j the physical fluxes at the nodes (Sec. II.A), the inverse Jacobian
+// of the element map at each node, the Rusanov flux with lambda = alpha +
+// |beta.n^|, then the same IMEX stage, clamp, filter and indicator as the box
+// kernel.  The stiff solve, clamp and indicator use the gamma inner product.
+#include "ffe_internal.h"
+#include "physics.cuh"
+#include "physics_gen.cuh"
+#include "shellmap.cuh"
+#include "stage.cuh"
+
+namespace ffe {
+
+template <int P>
+struct DGC {
+    static constexpr int np1 = P + 1;
+    static constexpr int nn = np1 * np1 * np1;
+    static constexpr int nf = np1 * np1;
+    static constexpr int NT = ((nn + 31) / 32) * 32;
+    static constexpr int NW = NT / 32;
+    // shared doubles: U[9][nn] | F[27][nn] (the filter buffer [9][nn] aliases it) | C[6][9][nf] | red[2][NW]
+    static constexpr int SMEM = (9 * nn + 27 * nn + 54 * nf + 2 * NW) * 8;
+};
+
+template <bool KS>
+__device__ __forceinline__ void node_metric(const Dev& d, int64_t p, PM& m) {
+    if (KS) {
+        load_pm(d.met, d.ndg, p, m);
+    } else {
+        m.a = 1.0;
+        m.b[0] = m.b[1] = m.b[2] = 0.0;
+        for (int i = 0; i < 6; ++i) m.gl[i] = m.gu[i] = (i == 0 || i == 3 || i == 5) ? 1.0 : 0.0;
+        m.sg = 1.0;
+    }
+}
+
+template <bool KS>
+__device__ __forceinline__ void fluxes_at(const double* U, const PM& m, double eta, double F[3][NV], double* jd) {
+    double jf[3];
+    if (KS) current_gen(U, m, eta, jd, jf);
+    else current_flat(U, eta, jd, jf);
+    flux_gen(U, jf, m, F);
+}
+
+template <int NW>
+__device__ __forceinline__ void block_sum2c(double& x, double& y, double* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { red[w] = x; red[NW + w] = y; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sx = 0.0, sy = 0.0;
+        for (int i = 0; i < NW; ++i) { sx += red[i]; sy += red[NW + i]; }
+        red[0] = sx;
+        red[NW] = sy;
+    }
+    __syncthreads();
+    x = red[0];
+    y = red[NW];
+}
+
+// neighbour's node for my face node (ta, tb) of face f
+template <int P>
+__device__ __forceinline__ void nbr_node(const Dev& d, int e, int f, int ta, int tb, int c[3]) {
+    const int f2 = d.nbr_face[e * 6 + f], d2 = f2 >> 1;
+    const int u1 = d2 == 0 ? 1 : 0, u2 = d2 == 2 ? 1 : 2;
+    int a2, b2;
+    orient_map(d.orient[e * 6 + f], P + 1, ta, tb, a2, b2);
+    c[d2] = (f2 & 1) ? P : 0;
+    c[u1] = a2;
+    c[u2] = b2;
+}
+
+template <int P, int SUB, bool KS>
+__global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
+    using K = DGC<P>;
+    constexpr int np1 = K::np1, nn = K::nn, nf = K::nf, NT = K::NT, NW = K::NW;
+    extern __shared__ double sm[];
+    double* sU = sm;                 // [9][nn]
+    double* sF = sU + 9 * nn;        // [3][9][nn]
+    double* sT = sF;                 // filter buffer [9][nn]
+    double* sC = sF + 27 * nn;       // [6][9][nf]
+    double* red = sC + 54 * nf;
+    const Tables& T = *d.tab;
+    const int tid = threadIdx.x;
+    const bool act = tid < nn;
+    const int ci[3] = {tid % np1, (tid / np1) % np1, tid / (np1 * np1)};
+    const double w0inv = 1.0 / T.w0;
+    const int nwork = d.counts[0];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int e = d.dg_list[w];
+        const int64_t eb = (int64_t)e * nn;
+        for (int t = tid; t < NV * nn; t += NT) sU[t] = a.Uin.dg(t / nn)[eb + t % nn];
+        __syncthreads();
+        PM m;
+        double jd[3] = {0.0, 0.0, 0.0}, ij[3][3];
+        if (act) {
+            node_metric<KS>(d, eb + tid, m);
+            for (int k = 0; k < 3; ++k)
+                for (int i = 0; i < 3; ++i) ij[k][i] = d.geo[(int64_t)(3 * k + i) * d.ndg + eb + tid];
+            double u[NV], F[3][NV];
+            for (int v = 0; v < NV; ++v) u[v] = sU[v * nn + tid];
+            fluxes_at<KS>(u, m, d.eta, F, jd);
+            for (int j = 0; j < 3; ++j)
+                for (int v = 0; v < NV; ++v) sF[(j * NV + v) * nn + tid] = F[j][v];
+        }
+        __syncthreads();
+        double du[NV];
+        if (act) {
+            for (int v = 0; v < NV; ++v) du[v] = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
+                const int base = tid - ci[k] * stride;
+                double Dk[np1];
+                for (int mm = 0; mm < np1; ++mm) Dk[mm] = T.D[ci[k]][mm];
+                for (int j = 0; j < 3; ++j) {
+                    const double s = -ij[k][j];
+                    for (int v = 0; v < NV; ++v) {
+                        const double* src = sF + (j * NV + v) * nn + base;
+                        double acc = 0.0;
+#pragma unroll
+                        for (int mm = 0; mm < np1; ++mm) acc = fma(Dk[mm], src[mm * stride], acc);
+                        du[v] = fma(s, acc, du[v]);
+                    }
+                }
+            }
+            double u[NV], S[NV];
+            for (int v = 0; v < NV; ++v) u[v] = sU[v * nn + tid];
+            if (KS) {
+                sources_gen(u, jd, m, d.met, d.ndg, eb + tid, S);
+                for (int v = 0; v < NV; ++v) du[v] += S[v];
+            } else {
+                du[0] -= jd[0]; du[1] -= jd[1]; du[2] -= jd[2];
+                du[6] += u[8];
+            }
+        }
+        // lift: one thread per face node
+        for (int t = tid; t < 6 * nf; t += NT) {
+            const int f = t / nf, ab = t % nf, ta = ab % np1, tb = ab / np1;
+            const int dd = f >> 1, s = f & 1;
+            const int t1 = dd == 0 ? 1 : 0, t2 = dd == 2 ? 1 : 2;
+            int c[3];
+            c[dd] = s ? P : 0;
+            c[t1] = ta;
+            c[t2] = tb;
+            const int me = c[0] + np1 * (c[1] + np1 * c[2]);
+            const int64_t p = eb + me;
+            PM mf;
+            node_metric<KS>(d, p, mf);
+            double nl[3];
+            for (int i = 0; i < 3; ++i) nl[i] = (s ? 1.0 : -1.0) * d.geo[(int64_t)(3 * dd + i) * d.ndg + p];
+            double nu[3];
+            for (int i = 0; i < 3; ++i) nu[i] = fma(mf.gu[sym3(i, 0)], nl[0], fma(mf.gu[sym3(i, 1)], nl[1], mf.gu[sym3(i, 2)] * nl[2]));
+            const double norm = sqrt(d3(nu, nl));
+            const double inrm = 1.0 / norm;
+            for (int i = 0; i < 3; ++i) nl[i] *= inrm;
+            double Ui[NV], Ue[NV];
+            for (int v = 0; v < NV; ++v) Ui[v] = sU[v * nn + me];
+            const int nb = d.nbr[e * 6 + f];
+            if (nb >= 0) {
+                int cn[3];
+                nbr_node<P>(d, e, f, ta, tb, cn);
+                if (d.mask[nb] == 0) {
+                    const int64_t q = (int64_t)nb * nn + cn[0] + np1 * (cn[1] + np1 * cn[2]);
+                    for (int v = 0; v < NV; ++v) Ue[v] = a.Uin.dg(v)[q];
+                } else {
+                    const int nc = T.nc;
+                    const int lo0 = T.f2d_lo[cn[0]], lo1 = T.f2d_lo[cn[1]], lo2 = T.f2d_lo[cn[2]];
+                    const int64_t base = (int64_t)nb * nc * nc * nc;
+                    for (int v = 0; v < NV; ++v) {
+                        const double* src = a.Uin.fd(v) + base;
+                        double acc = 0.0;
+                        for (int n2 = 0; n2 < 6; ++n2) {
+                            double a2 = 0.0;
+                            for (int n1 = 0; n1 < 6; ++n1) {
+                                double a1 = 0.0;
+                                const double* row = src + (int64_t)(lo0 + nc * ((lo1 + n1) + nc * (lo2 + n2)));
+                                for (int n0 = 0; n0 < 6; ++n0) a1 = fma(T.F2D[cn[0]][lo0 + n0], row[n0], a1);
+                                a2 = fma(T.F2D[cn[1]][lo1 + n1], a1, a2);
+                            }
+                            acc = fma(T.F2D[cn[2]][lo2 + n2], a2, acc);
+                        }
+                        Ue[v] = acc;
+                    }
+                }
+            } else {
+                const int kind = d.bc[e * 6 + f];
+                if (kind == FFE_BC_DIRICHLET) {
+                    const double* src = d.bdg + (int64_t)d.bface[e * 6 + f] * NV * nf;
+                    for (int v = 0; v < NV; ++v) Ue[v] = src[v * nf + ta + np1 * tb];
+                } else if (kind == FFE_BC_NO_INCOMING) {
+                    bc_no_incoming_flat(Ui, nl, Ue);
+                } else {
+                    double xn[3];
+                    for (int q = 0; q < 3; ++q) xn[q] = d.xyz_dg[(int64_t)q * d.ndg + p];
+                    bc_star_flat(Ui, xn, d.omega, Ue);
+                }
+            }
+            double Fe[3][NV], jde[3];
+            fluxes_at<KS>(Ue, mf, d.eta, Fe, jde);
+            const double lam = mf.a + fabs(d3(mf.b, nl));
+            const double sc = 0.5 * norm * w0inv;
+            for (int v = 0; v < NV; ++v) {
+                double dfn = 0.0;
+                for (int j = 0; j < 3; ++j) dfn = fma(nl[j], Fe[j][v] - sF[(j * NV + v) * nn + me], dfn);
+                sC[(f * NV + v) * nf + ab] = sc * fma(-lam, Ue[v] - Ui[v], dfn);
+            }
+        }
+        __syncthreads();
+        if (act) {
+            for (int dd = 0; dd < 3; ++dd) {
+                const int t1 = dd == 0 ? 1 : 0, t2 = dd == 2 ? 1 : 2;
+                const int ab = ci[t1] + np1 * ci[t2];
+                if (ci[dd] == 0)
+                    for (int v = 0; v < NV; ++v) du[v] -= sC[((2 * dd) * NV + v) * nf + ab];
+                if (ci[dd] == P)
+                    for (int v = 0; v < NV; ++v) du[v] -= sC[((2 * dd + 1) * NV + v) * nf + ab];
+            }
+        }
+        if (SUB == SUB_RHS) {
+            if (act)
+                for (int v = 0; v < NV; ++v) a.Fout.dg(v)[eb + tid] = du[v];
+            __syncthreads();
+            continue;
+        }
+        double u[NV];
+        if (act) {
+            if (SUB != SUB_C)
+                for (int v = 0; v < NV; ++v) a.Fout.dg(v)[eb + tid] = du[v];
+            if (KS) {
+                // stage combination with the metric-aware solve and clamp
+                const int gv[NG] = {0, 1, 2, 6, 7};
+                const double dt = d.dt;
+                for (int v = 0; v < NV; ++v) u[v] = a.un.dg(v)[eb + tid];
+                if (SUB == SUB_A) {
+                    for (int v = 0; v < NV; ++v) u[v] = fma(dt, du[v], u[v]);
+                    for (int c = 0; c < NG; ++c) u[gv[c]] = fma(dt * (1.0 - IM_A), a.G2.dg(c)[eb + tid], u[gv[c]]);
+                } else if (SUB == SUB_B) {
+                    for (int v = 0; v < NV; ++v) u[v] = fma(0.25 * dt, a.F2.dg(v)[eb + tid] + du[v], u[v]);
+                    const double z = 0.5 - IM_B - IM_H - IM_A;
+                    for (int c = 0; c < NG; ++c)
+                        u[gv[c]] = fma(dt, IM_B * a.G1.dg(c)[eb + tid] + IM_H * a.G2.dg(c)[eb + tid] + z * a.G3.dg(c)[eb + tid], u[gv[c]]);
+                } else {
+                    for (int v = 0; v < NV; ++v)
+                        u[v] = fma(dt, (a.F2.dg(v)[eb + tid] + a.F3.dg(v)[eb + tid]) * (1.0 / 6.0) + du[v] * (2.0 / 3.0), u[v]);
+                    for (int c = 0; c < NG; ++c)
+                        u[gv[c]] = fma(dt, (a.G2.dg(c)[eb + tid] + a.G3.dg(c)[eb + tid]) * (1.0 / 6.0) + a.G4.dg(c)[eb + tid] * (2.0 / 3.0), u[gv[c]]);
+                }
+                if (SUB != SUB_C && !stiff_solve_gen(u, m, d, dt * IM_A)) atomic_status(d, 2);
+                if (d.mode != FFE_RELAX) hard_clamp_gen(u, m);
+            } else {
+                substep_combine(d, SUB, du, eb + tid, false, a, u);
+            }
+        }
+        __syncthreads();
+        if (d.filter_on) {
+            if (act)
+                for (int v = 0; v < NV; ++v) sU[v * nn + tid] = u[v];
+            __syncthreads();
+            for (int k = 0; k < 3; ++k) {
+                const double* src = (k == 1) ? sT : sU;
+                double* dst = (k == 1) ? sU : sT;
+                const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
+                if (act) {
+                    const int base = tid - ci[k] * stride;
+                    for (int v = 0; v < NV; ++v) {
+                        double acc = 0.0;
+                        for (int mm = 0; mm < np1; ++mm) acc = fma(T.Filt[ci[k]][mm], src[v * nn + base + mm * stride], acc);
+                        if (k < 2) dst[v * nn + tid] = acc;
+                        else u[v] = acc;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        bool flagged = false;
+        if (d.tci_on) {
+            double mag = 0.0;
+            if (act) mag = KS ? bnorm_gen(u, m) : sqrt(fma(u[5], u[5], fma(u[4], u[4], u[3] * u[3])));
+            if (act) sU[tid] = mag;
+            __syncthreads();
+            double low = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
+                if (act) {
+                    const int base = tid - ci[k] * stride;
+                    double acc = 0.0;
+                    for (int mm = 0; mm < np1; ++mm) acc = fma(T.Pi[ci[k]][mm], sU[k * nn + base + mm * stride], acc);
+                    if (k < 2) sU[(k + 1) * nn + tid] = acc;
+                    else low = acc;
+                }
+                __syncthreads();
+            }
+            double num = 0.0, den = 0.0;
+            if (act) {
+                const double uh = mag - low;
+                num = uh * uh;
+                den = mag * mag;
+            }
+            block_sum2c<NW>(num, den, red);
+            const double ratio = den > 0.0 ? sqrt(num / den) : 0.0;
+            flagged = ratio > d.thr_dg;
+            if (tid == 0) {
+                if (fabs(ratio - d.thr_dg) <= 1e-12 * d.thr_dg) d.near_list[atomicAdd(&d.counts[3], 1) & 4095] = e;
+                if (flagged) {
+                    d.flag_list[atomicAdd(&d.counts[2], 1)] = e;
+                    d.switched[e] = 1;
+                }
+            }
+        }
+        if (!flagged && tid == 0) atomicAdd(d.units, (unsigned long long)nn);
+        if (!flagged && act) {
+            bool bad = false;
+            for (int v = 0; v < NV; ++v) {
+                a.Uout.dg(v)[eb + tid] = u[v];
+                bad |= !isfinite(u[v]);
+            }
+            if (bad) atomic_status(d, 1);
+            if (SUB != SUB_C) {
+                double g[NG];
+                if (KS) implicit_G_gen(u, m, d, g);
+                else implicit_G_flat(u, d, g);
+                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int P, bool KS>
+static void curved_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_t st) {
+    using K = DGC<P>;
+    const int grid = 152 * 2;
+#define FFE_LAUNCH_C(S)                                                                                   \
+    cudaFuncSetAttribute(k_dg_curved<P, S, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);   \
+    k_dg_curved<P, S, KS><<<grid, K::NT, K::SMEM, st>>>(d, a);
+    switch (sub) {
+        case SUB_A: FFE_LAUNCH_C(SUB_A) break;
+        case SUB_B: FFE_LAUNCH_C(SUB_B) break;
+        case SUB_C: FFE_LAUNCH_C(SUB_C) break;
+        default: FFE_LAUNCH_C(SUB_RHS) break;
+    }
+#undef FFE_LAUNCH_C
+}
+
+void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field un, Field F2, Field F3, Field G1, Field G2,
+                              Field G3, Field G4, Field Fout, Field Uout, Field Gout, cudaStream_t st) {
+    SubArgs a{Uin, Uin, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
+    prof_begin(sub == SUB_RHS ? "dg_rhs_curved" : "dg_substep_curved", st);
+    if (d.ks) {
+        switch (d.P) {
+            case 3: curved_dispatch<3, true>(d, sub, a, st); break;
+            case 4: curved_dispatch<4, true>(d, sub, a, st); break;
+            case 5: curved_dispatch<5, true>(d, sub, a, st); break;
+            default: break;
+        }
+    } else {
+        switch (d.P) {
+            case 3: curved_dispatch<3, false>(d, sub, a, st); break;
+            case 4: curved_dispatch<4, false>(d, sub, a, st); break;
+            case 5: curved_dispatch<5, false>(d, sub, a, st); break;
+            default: break;
+        }
+    }
+    prof_end(st);
+    g_launch_counter += 1;
+}
+
+// Stages 1 and 2 at DG nodes with the Kerr-Schild metric (FD is flat-only).
+__global__ void k_stage12_ks(Dev d, Field un, Field Ua, Field G1, Field G2) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double dta = d.dt * IM_A;
+    for (int64_t p = tid; p < d.ndg; p += stride) {
+        if (d.mask[p / d.nn] != 0) continue;
+        PM m;
+        load_pm(d.met, d.ndg, p, m);
+        double u[NV], U1[NV], g1[NG], g2[NG];
+        for (int v = 0; v < NV; ++v) { u[v] = un.dg(v)[p]; U1[v] = u[v]; }
+        if (!stiff_solve_gen(U1, m, d, dta)) atomic_status(d, 2);
+        if (d.mode != FFE_RELAX) hard_clamp_gen(U1, m);
+        implicit_G_gen(U1, m, d, g1);
+        u[0] = fma(-dta, g1[0], u[0]);
+        u[1] = fma(-dta, g1[1], u[1]);
+        u[2] = fma(-dta, g1[2], u[2]);
+        u[6] = fma(-dta, g1[3], u[6]);
+        u[7] = fma(-dta, g1[4], u[7]);
+        if (!stiff_solve_gen(u, m, d, dta)) atomic_status(d, 2);
+        if (d.mode != FFE_RELAX) hard_clamp_gen(u, m);
+        implicit_G_gen(u, m, d, g2);
+        for (int v = 0; v < NV; ++v) Ua.dg(v)[p] = u[v];
+        for (int c = 0; c < NG; ++c) { G1.dg(c)[p] = g1[c]; G2.dg(c)[p] = g2[c]; }
+    }
+}
+
+void launch_stage12_ks(const Dev& d, Field un, Field Ua, Field G1, Field G2, cudaStream_t st) {
+    prof_begin("stage12", st);
+    k_stage12_ks<<<152 * 8, 256, 0, st>>>(d, un, Ua, G1, G2);
+    prof_end(st);
+    g_launch_counter += 1;
+}
+
+}  // namespace ffe

@@ -9,6 +9,7 @@
 //   k_fd2dg      end-of-step FD -> DG check with alpha' = alpha + 1 (Sec. III.C.3).
 #include "ffe_internal.h"
 #include "physics.cuh"
+#include "shellmap.cuh"
 #include "stage.cuh"
 
 namespace ffe {
@@ -25,9 +26,21 @@ __device__ __forceinline__ double* ext_at(const Dev& d, int q, int w) {
     return d.ext + ((int64_t)q * d.E + w) * ext_size(d);
 }
 __device__ __forceinline__ int64_t nface(const Dev& d) { return (int64_t)(d.nc + 1) * d.nc * d.nc; }
-// flux layout: [3][NV][E][nface] indexed by list position w
+// flux layout: [3][NV][E][nface] indexed by list position w; curved meshes
+// keep every physical component j: [3 (k)][3 (j)][NV][E][nface]
 __device__ __forceinline__ double* flux_at(const Dev& d, int k, int v, int w) {
     return d.flux + (((int64_t)k * NV + v) * d.E + w) * nface(d);
+}
+__device__ __forceinline__ double* flux_at_c(const Dev& d, int k, int j, int v, int w) {
+    return d.flux + ((((int64_t)k * 3 + j) * NV + v) * d.E + w) * nface(d);
+}
+__device__ __forceinline__ ShellGeo shell_of(const Dev& d) {
+    ShellGeo g;
+    g.r_in = d.shell_rin;
+    g.c = d.shell_c;
+    g.na = d.shell_na;
+    g.nr = d.shell_nr;
+    return g;
 }
 
 __device__ __forceinline__ void axes_of(int dd, int& t1, int& t2) {
@@ -78,12 +91,17 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
         if (nb >= 0 && d.mask[nb] == 1) {
             const int f2 = d.nbr_face[e * 6 + f];
             const int d2 = f2 >> 1, s2 = f2 & 1;
+            int u1, u2;
+            axes_of(d2, u1, u2);
+            const int o = d.orient[e * 6 + f];
             for (int t = threadIdx.x; t < nper; t += blockDim.x) {
                 const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                int a2, b2;
+                orient_map(o, nc, ta, tb, a2, b2);
                 int c[3];
                 c[d2] = s2 ? nc - 1 - g : g;
-                c[t1] = ta;
-                c[t2] = tb;
+                c[u1] = a2;
+                c[u2] = b2;
                 const int64_t p = (int64_t)nb * d.ncell + c[0] + nc * (c[1] + nc * c[2]);
                 const int64_t o = ghost_offset(g, ta, tb);
                 for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = U.fd(v)[p];
@@ -94,7 +112,8 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
             const int f2 = d.nbr_face[e * 6 + f];
             const int d2 = f2 >> 1, s2 = f2 & 1;
             int u1, u2;
-            axes_of(d2, u1, u2);   // on a box the neighbour's tangential axes equal mine
+            axes_of(d2, u1, u2);
+            const int o = d.orient[e * 6 + f];
             for (int t = threadIdx.x; t < NV * nn; t += blockDim.x)
                 su[t] = U.dg(t / nn)[(int64_t)nb * nn + t % nn];
             __syncthreads();
@@ -123,11 +142,13 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
             __syncthreads();
             for (int t = threadIdx.x; t < nper; t += blockDim.x) {
                 const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                int a2, b2;   // the neighbour's subcell (along u1, u2) under this ghost cell
+                orient_map(o, nc, ta, tb, a2, b2);
                 double u[NV], jd[3], jf[3];
                 for (int v = 0; v < NV; ++v) {
                     double acc = 0.0;
                     for (int m = 0; m < np1; ++m)
-                        acc = fma(T.P2F[tb][m], t2b[((v * GH + g) * np1 + m) * nc + ta], acc);
+                        acc = fma(T.P2F[b2][m], t2b[((v * GH + g) * np1 + m) * nc + a2], acc);
                     u[v] = acc;
                 }
                 current_flat(u, d.eta, jd, jf);
@@ -156,6 +177,17 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
                     if (kind == FFE_BC_NO_INCOMING) {
                         double nrm[3] = {0.0, 0.0, 0.0};
                         nrm[dd] = s ? 1.0 : -1.0;
+                        if (d.curved) {
+                            // outward unit normal at the face point of this column
+                            double xi[3], x[3], ij[3][3];
+                            xi[dd] = s ? 1.0 : -1.0;
+                            xi[t1] = -1.0 + (ta + 0.5) * 2.0 / nc;
+                            xi[t2] = -1.0 + (tb + 0.5) * 2.0 / nc;
+                            shell_map(shell_of(d), e, xi, x, ij);
+                            const double sg = s ? 1.0 : -1.0;
+                            const double nn2 = sqrt(ij[dd][0] * ij[dd][0] + ij[dd][1] * ij[dd][1] + ij[dd][2] * ij[dd][2]);
+                            for (int q = 0; q < 3; ++q) nrm[q] = sg * ij[dd][q] / nn2;
+                        }
                         bc_no_incoming_flat(ui, nrm, u);
                     } else {
                         double x[3];
@@ -247,6 +279,119 @@ __global__ void k_fd_flux(Dev d, const int* list, int ci) {
     }
 }
 
+// Curved (flat-metric) variant: all three physical flux components at each
+// face, Rusanov dissipation along the unit face normal n^ (lambda = 1):
+//   F^j = (F^j(L) + F^j(R))/2 - n^_j (U_R - U_L)/2,
+// optional corrector per component.
+__global__ void k_fd_flux_curved(Dev d, const int* list, int ci) {
+    const int n = d.counts[ci];
+    const int nc = d.nc, ne = nc + 2 * GH;
+    const int64_t nfc = (int64_t)(nc + 1) * nc * nc;
+    const int64_t total = (int64_t)n * 3 * nfc;
+    const ShellGeo sg = shell_of(d);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(q / (3 * nfc));
+        const int k = (int)((q / nfc) % 3);
+        const int64_t fi = q % nfc;
+        const int m = (int)(fi % (nc + 1));
+        const int ta = (int)((fi / (nc + 1)) % nc), tb = (int)(fi / ((nc + 1) * nc));
+        const int e = list[w];
+        int t1, t2;
+        axes_of(k, t1, t2);
+        int c[3];
+        c[k] = m;
+        c[t1] = ta + GH;
+        c[t2] = tb + GH;
+        const int64_t base = c[0] + (int64_t)ne * (c[1] + (int64_t)ne * c[2]);
+        const int64_t stride = k == 0 ? 1 : (k == 1 ? ne : (int64_t)ne * ne);
+        double UL[NQ], UR[NQ], Um[NQ], Up[NQ];
+        for (int qq = 0; qq < NQ; ++qq) {
+            const double* src = ext_at(d, qq, w) + base;
+            const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
+            const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
+            UL[qq] = weno5z(v0, v1, v2, v3, v4, d.weno_eps);
+            UR[qq] = weno5z(v5, v4, v3, v2, v1, d.weno_eps);
+            Um[qq] = v2;
+            Up[qq] = v3;
+        }
+        double xi[3], x[3], ij[3][3];
+        xi[k] = -1.0 + m * 2.0 / nc;
+        xi[t1] = -1.0 + (ta + 0.5) * 2.0 / nc;
+        xi[t2] = -1.0 + (tb + 0.5) * 2.0 / nc;
+        shell_map(sg, e, xi, x, ij);
+        const double inrm = 1.0 / sqrt(ij[k][0] * ij[k][0] + ij[k][1] * ij[k][1] + ij[k][2] * ij[k][2]);
+        for (int j = 0; j < 3; ++j) {
+            double FL[NV], FR[NV], Fs[NV];
+            flux_dir_flat(UL, UL + NV, j, FL);
+            flux_dir_flat(UR, UR + NV, j, FR);
+            const double nj = ij[k][j] * inrm;
+            for (int v = 0; v < NV; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * nj * (UR[v] - UL[v]);
+            if (d.fd_corr) {
+                double Fm[NV], Fp[NV];
+                flux_dir_flat(Um, Um + NV, j, Fm);
+                flux_dir_flat(Up, Up + NV, j, Fp);
+                for (int v = 0; v < NV; ++v) Fs[v] = Fs[v] - (1.0 / 6.0) * (Fm[v] - 2.0 * Fs[v] + Fp[v]);
+            }
+            for (int v = 0; v < NV; ++v) flux_at_c(d, k, j, v, w)[fi] = Fs[v];
+        }
+    }
+}
+
+template <int SUB>
+__global__ void k_fd_update_curved(Dev d, const int* list, int ci, SubArgs a) {
+    const int n = d.counts[ci];
+    const int nc = d.nc;
+    const int64_t total = (int64_t)n * d.ncell;
+    const ShellGeo sg = shell_of(d);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(q / d.ncell), c = (int)(q % d.ncell);
+        const int e = list[w];
+        const int cc[3] = {c % nc, (c / nc) % nc, c / (nc * nc)};
+        const int64_t p = (int64_t)e * d.ncell + c;
+        double xi[3], x[3], ij[3][3];
+        for (int k = 0; k < 3; ++k) xi[k] = -1.0 + (cc[k] + 0.5) * 2.0 / nc;
+        shell_map(sg, e, xi, x, ij);
+        double du[NV], u0[NV];
+        for (int v = 0; v < NV; ++v) u0[v] = a.Uin.fd(v)[p];
+        du[0] = -a.J.fd(0)[p]; du[1] = -a.J.fd(1)[p]; du[2] = -a.J.fd(2)[p];
+        du[3] = du[4] = du[5] = 0.0;
+        du[6] = u0[8];
+        du[7] = du[8] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            int t1, t2;
+            axes_of(k, t1, t2);
+            const int64_t f0 = cc[k] + (int64_t)(nc + 1) * (cc[t1] + nc * cc[t2]);
+            for (int j = 0; j < 3; ++j) {
+                const double sc = ij[k][j] * (0.5 * nc);
+                for (int v = 0; v < NV; ++v) {
+                    const double* fl = flux_at_c(d, k, j, v, w);
+                    du[v] = fma(-sc, fl[f0 + 1] - fl[f0], du[v]);
+                }
+            }
+        }
+        if (SUB == SUB_RHS) {
+            for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
+            continue;
+        }
+        if (c == 0) atomicAdd(d.units, (unsigned long long)d.ncell);
+        if (SUB != SUB_C)
+            for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
+        double u[NV];
+        substep_combine(d, SUB, du, p, true, a, u);
+        bool bad = false;
+        for (int v = 0; v < NV; ++v) {
+            a.Uout.fd(v)[p] = u[v];
+            bad |= !isfinite(u[v]);
+        }
+        if (bad) atomic_status(d, 1);
+        if (SUB != SUB_C) {
+            double g[NG];
+            implicit_G_flat(u, d, g);
+            for (int cg = 0; cg < NG; ++cg) a.Gout.fd(cg)[p] = g[cg];
+        }
+    }
+}
+
 // One thread per (list position, cell): flux difference + sources + stage.
 template <int SUB>
 __global__ void k_fd_update(Dev d, const int* list, int ci, SubArgs a, const double* ijac) {
@@ -313,14 +458,24 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin
     k_fd_fill_ghosts<<<152 * 2, 256, smem, st>>>(d, list, ci, Uin, J);
     prof_end(st);
     prof_begin("fd_flux", st);
-    k_fd_flux<<<grid, 128, 0, st>>>(d, list, ci);
+    if (d.curved) k_fd_flux_curved<<<grid, 128, 0, st>>>(d, list, ci);
+    else k_fd_flux<<<grid, 128, 0, st>>>(d, list, ci);
     prof_end(st);
     prof_begin("fd_update", st);
-    switch (sub) {
-        case SUB_A: k_fd_update<SUB_A><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
-        case SUB_B: k_fd_update<SUB_B><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
-        case SUB_C: k_fd_update<SUB_C><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
-        default: k_fd_update<SUB_RHS><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+    if (d.curved) {
+        switch (sub) {
+            case SUB_A: k_fd_update_curved<SUB_A><<<grid, 256, 0, st>>>(d, list, ci, a); break;
+            case SUB_B: k_fd_update_curved<SUB_B><<<grid, 256, 0, st>>>(d, list, ci, a); break;
+            case SUB_C: k_fd_update_curved<SUB_C><<<grid, 256, 0, st>>>(d, list, ci, a); break;
+            default: k_fd_update_curved<SUB_RHS><<<grid, 256, 0, st>>>(d, list, ci, a); break;
+        }
+    } else {
+        switch (sub) {
+            case SUB_A: k_fd_update<SUB_A><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+            case SUB_B: k_fd_update<SUB_B><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+            case SUB_C: k_fd_update<SUB_C><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+            default: k_fd_update<SUB_RHS><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
+        }
     }
     prof_end(st);
     g_launch_counter += 4;

@@ -1,0 +1,84 @@
+// Cubed-sphere wedge map and its Jacobian (host and device).
+//
+// Wedge w has normal axis n and sign s (w = 0..5: +z, -z, +y, -y, +x, -x) and
+// tangential axes t1 = (n+1)%3, t2 = (n+2)%3.  Logical coordinates
+// (ea, eb, er) in [-1,1]^3 map to
+//   X = tan(pi ea / 4), Y = tan(pi eb / 4), rho = sqrt(1 + X^2 + Y^2),
+//   v = (s e_n + X e_t1 + Y e_t2) / rho,  r = r_in exp(c (er + 1)), c = ln(r_out/r_in)/2,
+//   x = r v                                           (Sec. IV.B: equiangular + logarithmic).
+// Element (ia, ib, ir) of an na x na x nr split covers ea in [-1 + 2 ia/na, -1 + 2 (ia+1)/na]
+// etc., so d ea / d xi^1 = 1/na, d eb / d xi^2 = 1/na, d er / d xi^3 = 1/nr.
+// Jacobian columns (derived from the closed form):
+//   dx/dea = r (pi/4)(1 + X^2) [e_t1/rho - X v/rho^2],
+//   dx/deb = r (pi/4)(1 + Y^2) [e_t2/rho - Y v/rho^2],   (d rho/dX = X/rho)
+//   dx/der = c r v.
+#pragma once
+#include <cmath>
+
+namespace ffe {
+
+struct ShellGeo {
+    double r_in, c;     // r = r_in exp(c (er + 1))
+    int na, nr;         // elements per wedge: angular, radial
+};
+
+__host__ __device__ inline void shell_elem(const ShellGeo& g, int e, int& ia, int& ib, int& ir, int& w) {
+    ia = e % g.na;
+    ib = (e / g.na) % g.na;
+    ir = (e / (g.na * g.na)) % g.nr;
+    w = e / (g.na * g.na * g.nr);
+}
+
+// Point x and inverse Jacobian ijac[k][i] = d xi^k / d x^i at reference point xi of element e.
+__host__ __device__ inline void shell_map(const ShellGeo& g, int e, const double xi[3], double x[3],
+                                          double ijac[3][3]) {
+    int ia, ib, ir, w;
+    shell_elem(g, e, ia, ib, ir, w);
+    const int n = (w >> 1) == 0 ? 2 : ((w >> 1) == 1 ? 1 : 0);
+    const double s = (w & 1) ? -1.0 : 1.0;
+    const int t1 = (n + 1) % 3, t2 = (n + 2) % 3;
+    const double ea = -1.0 + (ia + 0.5 * (xi[0] + 1.0)) * 2.0 / g.na;
+    const double eb = -1.0 + (ib + 0.5 * (xi[1] + 1.0)) * 2.0 / g.na;
+    const double er = -1.0 + (ir + 0.5 * (xi[2] + 1.0)) * 2.0 / g.nr;
+    const double q = 0.78539816339744830962;   // pi/4
+    const double X = tan(q * ea), Y = tan(q * eb);
+    const double rho = sqrt(1.0 + X * X + Y * Y);
+    const double r = g.r_in * exp(g.c * (er + 1.0));
+    double v[3];
+    v[n] = s / rho;
+    v[t1] = X / rho;
+    v[t2] = Y / rho;
+    for (int i = 0; i < 3; ++i) x[i] = r * v[i];
+    double J[3][3];   // J[i][k] = d x^i / d xi^k
+    const double fa = r * q * (1.0 + X * X) / g.na, fb = r * q * (1.0 + Y * Y) / g.na, fr = g.c * r / g.nr;
+    for (int i = 0; i < 3; ++i) {
+        const double et1 = i == t1 ? 1.0 : 0.0, et2 = i == t2 ? 1.0 : 0.0;
+        J[i][0] = fa * (et1 / rho - X * v[i] / (rho * rho));
+        J[i][1] = fb * (et2 / rho - Y * v[i] / (rho * rho));
+        J[i][2] = fr * v[i];
+    }
+    // inverse by cofactors
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    const double id = 1.0 / det;
+    ijac[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) * id;
+    ijac[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    ijac[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    ijac[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) * id;
+    ijac[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    ijac[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    ijac[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) * id;
+    ijac[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    ijac[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+}
+
+// Neighbour face index (a2, b2) for my face index (a, b) under orientation code
+// o: bit 0 swaps a and b, bit 1 reverses the first, bit 2 the second.
+__host__ __device__ inline void orient_map(int o, int n, int a, int b, int& a2, int& b2) {
+    int x = (o & 1) ? b : a, y = (o & 1) ? a : b;
+    a2 = (o & 2) ? n - 1 - x : x;
+    b2 = (o & 4) ? n - 1 - y : y;
+}
+
+}  // namespace ffe

@@ -144,16 +144,20 @@ class Context:
         import torch
         lib = load()
         self.cfg = cfg
-        if cfg["kind"] != "box":
-            raise FFEError("only box domains are built in this version")
         dom = Domain()
-        dom.kind = 0
-        for a in range(3):
-            dom.lo[a], dom.hi[a] = cfg["lo"][a], cfg["hi"][a]
-            dom.bc_lo[a] = dom.bc_hi[a] = BC[cfg["bc"][a]]
         el = Elements()
-        for a in range(3):
-            el.n[a] = cfg["n"][a]
+        if cfg["kind"] == "box":
+            dom.kind = 0
+            for a in range(3):
+                dom.lo[a], dom.hi[a] = cfg["lo"][a], cfg["hi"][a]
+                dom.bc_lo[a] = dom.bc_hi[a] = BC[cfg["bc"][a]]
+                el.n[a] = cfg["n"][a]
+        else:
+            dom.kind = 1
+            dom.r_in, dom.r_out = cfg["r_in"], cfg["r_out"]
+            dom.bc_lo[0], dom.bc_hi[0] = BC[cfg["bc_inner"]], BC[cfg["bc_outer"]]
+            el.n[0] = el.n[1] = cfg["n_ang"]
+            el.n[2] = cfg["n_rad"]
         mk, M, spin = cfg["metric"]
         met = Metric(METRIC[mk], M, spin)
         prm = params_from(cfg["params"])
