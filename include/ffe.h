@@ -113,10 +113,38 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
                       const ffe_metric* metric, const ffe_params* params,
                       void* cuda_stream, ffe_ctx** out);
 
+/* Batched context (Sec. IV.C workloads, many independent magnetospheres): n_inst
+ * six-wedge shells in flat space, each with its own domain (r_in, r_out,
+ * boundary kinds), elements (n[0] angular, n[2] radial per wedge), order
+ * P[i] in {3, 4, 5} and parameters params[i] (time step from its own CFL
+ * condition, star rotation omega_star); every other scheme parameter must
+ * equal params[0].  All instances advance together: one launch per kernel and
+ * substep covers every element of every instance, whatever its order.
+ * fd_capacity bounds the number of elements on FD subcells at any time
+ * (0 = every element); an element the indicator flags when no FD slot is left
+ * stays on DG and status bit 2 is raised.  State layout: every element owns a
+ * DG slot of (Pmax+1)^3 nodes (its own (P+1)^3 at the front) and an FD element
+ * owns one of fd_capacity FD slots of (2 Pmax+1)^3 cells (see ffe_get_layout). */
+ffe_status ffe_create_batch(int n_inst, const ffe_domain* domains, const ffe_elements* elements, const int* P,
+                            const ffe_metric* metric, const ffe_params* params, int fd_capacity,
+                            void* cuda_stream, ffe_ctx** out);
+
+/* Per-element layout (host copies, synchronising; any pointer may be NULL):
+ * order of each element [n_elem], FD slot of each element [n_elem] (-1 when it
+ * has none), instance of each element [n_elem], first element of each
+ * instance [n_inst + 1], and the number of instances. */
+ffe_status ffe_get_layout(ffe_ctx* ctx, int* elem_P, int* fd_slot, int* elem_inst, int* inst_first, int* n_inst);
+
+/* Initial data for every instance of a context: id_params holds n_inst blocks
+ * of n_params values, one block per instance (same meaning as ffe_set_initial). */
+ffe_status ffe_set_initial_batch(ffe_ctx* ctx, int id_kind, const double* id_params, int n_params, int flags);
+
 /* Set analytic initial data.  id_params (may be NULL when n_params = 0):
  *   FAST_WAVE      {amp}                 B=(1,b,0), E=(0,0,-b), b = 1 + amp sin(pi x)
  *   BREAKDOWN      {}                    current sheet of the breakdown workload
  *   CLEANING_MODE  {eps}                 B=(1+eps sin(pi x),0,0)
+ *   WALD           {M, a, B0}            Wald's field (Kerr-Schild metric)
+ *   DIPOLE         {mu, delta, chi}      B~ = curl[mu m x x/(r^2+delta^2)^(3/2)], m = (sin chi, 0, cos chi)
  * The data are set on the LGL nodes, then the troubled-cell indicator runs and
  * flagged elements take the data at their subcell centres (Sec. III.C.1/III.C.3).
  * Resets time and step counters. */

@@ -41,6 +41,12 @@ struct Tables {
     int f2d_lo[MAXNP];             // first subcell of the 6-point stencil of node i
 };
 
+// Per-instance data of a batched context (one magnetosphere per instance).
+struct InstInfo {
+    double r_in, c, dt, omega;   // shell map r = r_in exp(c (er + 1)), time step, star rotation
+    int na, nr, e0, P;           // elements per wedge side / radially, first element, order
+};
+
 // A field buffer in state-vector layout: [nv][n_dg] then [nv][n_fd].
 struct Field {
     double* p;
@@ -52,8 +58,24 @@ struct Field {
 
 // Everything a kernel needs to know about the context (passed by value).
 struct Dev {
-    int E, P, np1, nn, nc, ncell;   // elements, order, 1-D sizes, nodes/cells per element
+    // E elements; P, np1, nc are the largest order's sizes and nn, ncell the
+    // node / cell slot of every element (elements of lower order use the front
+    // of their slot); uniform contexts have one order.
+    int E, P, np1, nn, nc, ncell;
     int64_t ndg, nfd;
+    const unsigned char* eP;        // [E] order of each element (null: all P)
+    const int* einst;               // [E] instance of each element (null: one instance)
+    const InstInfo* inst;           // [n_inst]
+    const Tables* tabs;             // [MAXNP] tables indexed by order
+    double thr_dgP[MAXNP], thr_fdP[MAXNP];   // indicator thresholds per order
+    // FD storage: slot of each element ([E], -1 if none) and element of each
+    // slot; null = slot e for element e.  Free slots form a stack.
+    int* fd_slot;
+    int* slot_elem;
+    int* free_slots;
+    int fd_cap;                     // FD slots
+    int chunk;                      // FD elements per scratch chunk
+    int dg_grid;                    // CTAs of the curved DG kernel (chosen by the autotuner; 0 = default)
     // physics and scheme parameters
     double eta, kpsi, kphi, dt, weno_eps, omega;
     int mode, filter_on, tci_on, fd_corr;
@@ -83,12 +105,34 @@ struct Dev {
     unsigned char* mask;            // [E] 0 = DG, 1 = FD
     unsigned char* switched;        // [E] switched to FD during the current step
     int* dg_list; int* fd_list; int* flag_list; int* near_list;
-    int* counts;                    // [0] n_dg, [1] n_fd, [2] n_flag, [3] n_near, [4] status bits
+    int* counts;                    // [0] n_dg, [1] n_fd, [2] n_flag, [3] n_near, [4] status bits, [5] free slots
     unsigned long long* units;      // element-node updates (DG nodes + FD cells per substep)
-    // FD scratch: extended cells [12][E][(nc+6)^3], face fluxes [3][9][E][(nc+1) nc^2]
+    // FD scratch per chunk of listed FD elements: extended cells [12][chunk][(nc+6)^3],
+    // face fluxes [3 (x3 curved)][9][chunk][(nc+1) nc^2]
     double* ext;
     double* flux;
 };
+
+// sizes of one element
+struct ES {
+    int P, np1, nn, nc, ncell;
+};
+__host__ __device__ inline ES es_of(int P) {
+    ES s;
+    s.P = P;
+    s.np1 = P + 1;
+    s.nn = s.np1 * s.np1 * s.np1;
+    s.nc = 2 * P + 1;
+    s.ncell = s.nc * s.nc * s.nc;
+    return s;
+}
+__device__ __forceinline__ int elem_P(const Dev& d, int e) { return d.eP ? (int)d.eP[e] : d.P; }
+__device__ __forceinline__ ES esz(const Dev& d, int e) { return es_of(elem_P(d, e)); }
+__device__ __forceinline__ int64_t fdb(const Dev& d, int e) {
+    return (int64_t)(d.fd_slot ? d.fd_slot[e] : e) * d.ncell;
+}
+__device__ __forceinline__ double dt_of(const Dev& d, int e) { return d.einst ? d.inst[d.einst[e]].dt : d.dt; }
+__device__ __forceinline__ double omega_of(const Dev& d, int e) { return d.einst ? d.inst[d.einst[e]].omega : d.omega; }
 
 // kernel launchers (kernels_*.cu); all enqueue on `st`
 void launch_build_lists(const Dev& d, cudaStream_t st);
@@ -100,6 +144,7 @@ void launch_dg_substep(const Dev& d, int sub, Field Uin, Field J, Field un, Fiel
 void launch_fd_substep(const Dev& d, int sub, const int* list, int count_index, Field Uin, Field J,
                        Field un, Field F2, Field F3, Field G1, Field G2, Field G3, Field G4,
                        Field Fout, Field Uout, Field Gout, cudaStream_t st);
+int fd_chunks(const Dev& d);
 void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F2, Field F3,
                              Field G1, Field G2, Field G3, Field G4, cudaStream_t st);
 void launch_fd2dg(const Dev& d, Field un, cudaStream_t st);

@@ -275,6 +275,17 @@ struct ffe_ctx {
     std::vector<int> h_bface;
     ShellGeo shell{};
     double lam_max = 1.0;
+    // batched contexts
+    bool batch = false;
+    int n_inst = 1;
+    std::vector<InstInfo> insts;          // per instance
+    std::vector<ffe_domain> doms;
+    std::vector<int> h_eP, h_einst;       // per element
+    std::vector<int> h_fd_slot;           // per element (pool only)
+    std::vector<double> id_prm_inst;      // initial-data parameters per instance
+    int id_nprm = 0;
+    Tables tabs_h[MAXNP];
+    bool tuned = false;
 };
 
 namespace {
@@ -390,6 +401,15 @@ ffe_status build_box(ffe_ctx* c) {
 
 // x(xi) and d xi / d x of element e for either mesh kind.
 MapFn ctx_map(ffe_ctx* c) {
+    if (c->batch) {
+        std::vector<InstInfo> in = c->insts;
+        std::vector<int> ei = c->h_einst;
+        return [in, ei](int e, const double xi[3], double x[3], double ij[3][3]) {
+            const InstInfo& q = in[ei[e]];
+            ShellGeo g{q.r_in, q.c, q.na, q.nr};
+            shell_map(g, e - q.e0, xi, x, ij);
+        };
+    }
     if (c->dom.kind == FFE_DOMAIN_SHELL6) {
         ShellGeo g = c->shell;
         return [g](int e, const double xi[3], double x[3], double ij[3][3]) { shell_map(g, e, xi, x, ij); };
@@ -404,6 +424,8 @@ MapFn ctx_map(ffe_ctx* c) {
         }
     };
 }
+
+int host_P(const ffe_ctx* c, int e) { return c->batch ? c->h_eP[e] : c->d.P; }
 
 // Six-wedge shell: coordinates, per-node inverse Jacobians, connectivity with
 // orientation, boundary kinds, Kerr-Schild metric arrays and (dx)_min.
@@ -536,10 +558,14 @@ ffe_status build_shell(ffe_ctx* c) {
 // Dirichlet boundary data = the initial data at face nodes and ghost-cell centres.
 ffe_status fill_dirichlet(ffe_ctx* c) {
     if (c->nbf == 0) return FFE_OK;
-    const int np1 = c->d.np1, nc = c->d.nc, E = c->d.E;
-    std::vector<double> bdg((size_t)c->nbf * NV * np1 * np1), bfd((size_t)c->nbf * NV * GH * nc * nc);
+    const int np1m = c->d.np1, ncm = c->d.nc, E = c->d.E;
+    std::vector<double> bdg((size_t)c->nbf * NV * np1m * np1m), bfd((size_t)c->nbf * NV * GH * ncm * ncm);
     MapFn map = ctx_map(c);
     for (int e = 0; e < E; ++e) {
+        const int P = host_P(c, e), np1 = P + 1, nc = 2 * P + 1;
+        const Tables& T = c->tabs_h[P];
+        const double* prm = c->batch ? c->id_prm_inst.data() + (size_t)c->h_einst[e] * c->id_nprm : c->id_prm.data();
+        const int nprm = c->batch ? c->id_nprm : (int)c->id_prm.size();
         for (int f = 0; f < 6; ++f) {
             const int slot = c->h_bface[6 * e + f];
             if (slot < 0) continue;
@@ -549,12 +575,12 @@ ffe_status fill_dirichlet(ffe_ctx* c) {
                 for (int a = 0; a < np1; ++a) {
                     double xi[3];
                     xi[dd] = s ? 1.0 : -1.0;
-                    xi[t1] = c->tab.x[a];
-                    xi[t2] = c->tab.x[b];
+                    xi[t1] = T.x[a];
+                    xi[t2] = T.x[b];
                     double X[3], U[NV], ij[3][3];
                     map(e, xi, X, ij);
-                    initial_point(c->id_kind, c->id_prm.data(), (int)c->id_prm.size(), X, U);
-                    for (int v = 0; v < NV; ++v) bdg[((size_t)slot * NV + v) * np1 * np1 + a + np1 * b] = U[v];
+                    initial_point(c->id_kind, prm, nprm, X, U);
+                    for (int v = 0; v < NV; ++v) bdg[((size_t)slot * NV + v) * np1m * np1m + a + np1 * b] = U[v];
                 }
             for (int g = 0; g < GH; ++g)
                 for (int b = 0; b < nc; ++b)
@@ -566,9 +592,9 @@ ffe_status fill_dirichlet(ffe_ctx* c) {
                         xi[t2] = -1.0 + (b + 0.5) * dxi;
                         double X[3], U[NV], ij[3][3];
                         map(e, xi, X, ij);
-                        initial_point(c->id_kind, c->id_prm.data(), (int)c->id_prm.size(), X, U);
+                        initial_point(c->id_kind, prm, nprm, X, U);
                         for (int v = 0; v < NV; ++v)
-                            bfd[(((size_t)slot * NV + v) * GH + g) * nc * nc + a + nc * b] = U[v];
+                            bfd[(((size_t)slot * NV + v) * GH + g) * ncm * ncm + a + nc * b] = U[v];
                     }
         }
     }
@@ -612,8 +638,49 @@ void enqueue_step(ffe_ctx* c) {
     if (d.tci_on) launch_fd2dg(d, c->un, st);
 }
 
+// Launch-shape autotuner: times the DG right-hand side (no state change)
+// with persistent grids of 1, 2, 3 and 4 CTAs per SM and keeps the fastest.
+ffe_status autotune(ffe_ctx* c) {
+    Dev& d = c->d;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    launch_build_lists(d, c->st);
+    if (!d.ks) launch_current(d, c->un, c->J, nullptr, 0, c->st);
+    float best = 1e30f;
+    int best_g = 0;
+    for (int g : {152, 304, 456, 608}) {
+        d.dg_grid = g;
+        float tot = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaEventRecord(a, c->st));
+            if (d.curved)
+                launch_dg_substep_curved(d, SUB_RHS, c->un, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, c->Fs,
+                                         c->Fs, c->G1, c->st);
+            else
+                launch_dg_substep(d, SUB_RHS, c->un, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, c->Fs,
+                                  c->Fs, c->G1, c->st);
+            CK(cudaEventRecord(b, c->st));
+            CK(cudaEventSynchronize(b));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (rep > 0) tot += ms;
+        }
+        if (tot < best) { best = tot; best_g = g; }
+    }
+    d.dg_grid = best_g;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    c->tuned = true;
+    return FFE_OK;
+}
+
 ffe_status run_steps(ffe_ctx* c, int nsteps) {
     static const bool no_graph = getenv("FFE_NO_GRAPH") != nullptr;
+    if (!c->tuned && nsteps > 0 && getenv("FFE_NO_AUTOTUNE") == nullptr) {
+        ffe_status s = autotune(c);
+        if (s) return s;
+    }
     for (int n = 0; n < nsteps; ++n) {
         if (g_prof.on) {
             enqueue_step(c);
@@ -661,6 +728,147 @@ ffe_status run_steps(ffe_ctx* c, int nsteps) {
         c->t += c->d.dt;
         c->steps += 1;
     }
+    return FFE_OK;
+}
+
+// Tables for every order in use, thresholds, per-element arrays, work buffers
+// and the FD slot pool.  d.P/np1/nn/nc/ncell already hold the largest order's
+// sizes and d.E the element count; fd_cap the number of FD slots.
+ffe_status finish_create(ffe_ctx* c, int fd_cap, const std::vector<int>& orders) {
+    Dev& d = c->d;
+    const ffe_params* params = &c->prm;
+    ffe_status s;
+    for (int P : orders) {
+        build_tables(P, params->filter_a, params->filter_b, params->tci_M, c->tabs_h[P]);
+        d.thr_dgP[P] = pow((double)(P + 1 - params->tci_M), -params->tci_alpha);
+        d.thr_fdP[P] = pow((double)(P + 1 - params->tci_M), -(params->tci_alpha + 1.0));
+    }
+    c->tab = c->tabs_h[d.P];
+    Tables* dtabs;
+    if ((s = dalloc(c, &dtabs, MAXNP))) return s;
+    CK(cudaMemcpy(dtabs, c->tabs_h, sizeof(c->tabs_h), cudaMemcpyHostToDevice));
+    d.tabs = dtabs;
+    d.tab = dtabs + d.P;
+    d.thr_dg = d.thr_dgP[d.P];
+    d.thr_fd = d.thr_fdP[d.P];
+    d.fd_cap = fd_cap;
+    d.nfd = (int64_t)fd_cap * d.ncell;
+    d.chunk = fd_cap < 2048 ? (fd_cap > 0 ? fd_cap : 1) : 2048;
+    if ((s = dalloc(c, &d.mask, d.E))) return s;
+    if ((s = dalloc(c, &d.switched, d.E))) return s;
+    if ((s = dalloc(c, &d.dg_list, d.E))) return s;
+    if ((s = dalloc(c, &d.fd_list, d.E))) return s;
+    if ((s = dalloc(c, &d.flag_list, d.E))) return s;
+    if ((s = dalloc(c, &d.near_list, 4096))) return s;
+    if ((s = dalloc(c, &d.counts, 8))) return s;
+    if ((s = dalloc(c, &d.units, 1))) return s;
+    if (c->batch) {
+        int *eP8, *ein;
+        InstInfo* dinst;
+        std::vector<unsigned char> ep(c->h_eP.begin(), c->h_eP.end());
+        unsigned char* dep;
+        if ((s = dalloc(c, &dep, d.E))) return s;
+        if ((s = dalloc(c, &ein, d.E))) return s;
+        if ((s = dalloc(c, &dinst, c->insts.size()))) return s;
+        CK(cudaMemcpy(dep, ep.data(), d.E, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ein, c->h_einst.data(), d.E * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dinst, c->insts.data(), c->insts.size() * sizeof(InstInfo), cudaMemcpyHostToDevice));
+        d.eP = dep;
+        d.einst = ein;
+        d.inst = dinst;
+        (void)eP8;
+        // FD slot pool: every slot free until ffe_set_initial assigns some
+        if ((s = dalloc(c, &d.fd_slot, d.E))) return s;
+        if ((s = dalloc(c, &d.slot_elem, fd_cap))) return s;
+        if ((s = dalloc(c, &d.free_slots, fd_cap))) return s;
+    }
+    for (Field* f : {&c->un, &c->Ua, &c->Ub, &c->F2, &c->F3, &c->Fs})
+        if ((s = alloc_field(c, *f, NV))) return s;
+    for (Field* f : {&c->G1, &c->G2, &c->G3, &c->G4})
+        if ((s = alloc_field(c, *f, NG))) return s;
+    if ((s = alloc_field(c, c->J, NJ))) return s;
+    const int64_t ne = d.nc + 2 * GH;
+    if ((s = dalloc(c, &d.ext, (size_t)12 * d.chunk * ne * ne * ne))) return s;
+    if ((s = dalloc(c, &d.flux, (size_t)(d.curved ? 9 : 3) * NV * d.chunk * (d.nc + 1) * d.nc * d.nc))) return s;
+    return FFE_OK;
+}
+
+// Assign FD slots to the elements flagged at initialisation (pool contexts).
+ffe_status init_slots(ffe_ctx* c, const std::vector<unsigned char>& mask) {
+    Dev& d = c->d;
+    if (!d.fd_slot) return FFE_OK;
+    std::vector<int> slot(d.E, -1), selem(d.fd_cap, -1), freel;
+    int next = 0;
+    for (int e = 0; e < d.E; ++e)
+        if (mask[e]) {
+            if (next >= d.fd_cap)
+                return fail(FFE_ENOMEM, "the initial data put more than fd_capacity = %d elements on FD", d.fd_cap);
+            slot[e] = next;
+            selem[next] = e;
+            ++next;
+        }
+    for (int sl = d.fd_cap - 1; sl >= next; --sl) freel.push_back(sl);
+    freel.resize(d.fd_cap, -1);
+    const int nfree = d.fd_cap - next;
+    CK(cudaMemcpy(d.fd_slot, slot.data(), d.E * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.slot_elem, selem.data(), d.fd_cap * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.free_slots, freel.data(), d.fd_cap * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.counts + 5, &nfree, sizeof(int), cudaMemcpyHostToDevice));
+    c->h_fd_slot = slot;
+    return FFE_OK;
+}
+
+// Initial data for all elements (per-instance parameters in batched contexts).
+ffe_status set_initial_impl(ffe_ctx* c, int id_kind) {
+    const Dev& d = c->d;
+    auto prm_of = [&](int e) -> const double* {
+        return c->batch ? c->id_prm_inst.data() + (size_t)c->h_einst[e] * c->id_nprm : c->id_prm.data();
+    };
+    const int nprm = c->batch ? c->id_nprm : (int)c->id_prm.size();
+    std::vector<double> xdg(3 * (size_t)d.ndg), U(NV * (size_t)(d.ndg + d.nfd), 0.0);
+    CK(cudaMemcpy(xdg.data(), d.xyz_dg, xdg.size() * 8, cudaMemcpyDeviceToHost));
+    parallel_for(d.ndg, [&](int64_t p) {
+        const int e = (int)(p / d.nn);
+        const int P = host_P(c, e);
+        if ((int)(p % d.nn) >= (P + 1) * (P + 1) * (P + 1)) return;
+        double X[3] = {xdg[p], xdg[d.ndg + p], xdg[2 * d.ndg + p]}, u[NV];
+        initial_point(id_kind, prm_of(e), nprm, X, u);
+        for (int v = 0; v < NV; ++v) U[v * d.ndg + p] = u[v];
+    });
+    std::vector<unsigned char> mask(d.E, 0);
+    if (d.tci_on) {
+        double* ratio;
+        ffe_status s;
+        if ((s = dalloc(c, &ratio, d.E))) return s;
+        CK(cudaMemcpy(c->un.p, U.data(), NV * d.ndg * 8, cudaMemcpyHostToDevice));
+        launch_tci_ratio(d, c->un.p, ratio, c->st);
+        std::vector<double> r(d.E);
+        CK(cudaMemcpyAsync(r.data(), ratio, d.E * 8, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int e = 0; e < d.E; ++e) mask[e] = r[e] > d.thr_dgP[host_P(c, e)];
+        if ((s = init_slots(c, mask))) return s;
+        MapFn map = ctx_map(c);
+        parallel_for(d.E, [&](int64_t e) {
+            if (!mask[e]) return;
+            const int P = host_P(c, (int)e), nc = 2 * P + 1;
+            const int64_t base = (int64_t)(d.fd_slot ? c->h_fd_slot[e] : e) * d.ncell;
+            for (int q = 0; q < nc * nc * nc; ++q) {
+                const int cc[3] = {q % nc, (q / nc) % nc, q / (nc * nc)};
+                double xi[3], X[3], ij[3][3], u[NV];
+                for (int a = 0; a < 3; ++a) xi[a] = -1.0 + (cc[a] + 0.5) * 2.0 / nc;
+                map((int)e, xi, X, ij);
+                initial_point(id_kind, prm_of((int)e), nprm, X, u);
+                for (int v = 0; v < NV; ++v) U[NV * d.ndg + v * d.nfd + base + q] = u[v];
+            }
+        });
+    }
+    CK(cudaMemcpy(c->un.p, U.data(), U.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.mask, mask.data(), d.E, cudaMemcpyHostToDevice));
+    ffe_status s;
+    if ((s = fill_dirichlet(c))) return s;
+    CK(cudaMemset(d.units, 0, sizeof(unsigned long long)));
+    c->t = 0.0;
+    c->steps = 0;
     return FFE_OK;
 }
 
@@ -752,36 +960,233 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     d.filter_on = params->filter_on;
     d.tci_on = params->tci_on;
     d.fd_corr = params->fd_corrector;
-    d.thr_dg = pow((double)(P + 1 - params->tci_M), -params->tci_alpha);
-    d.thr_fd = pow((double)(P + 1 - params->tci_M), -(params->tci_alpha + 1.0));
-    build_tables(P, params->filter_a, params->filter_b, params->tci_M, c->tab);
     ffe_status s;
-    Tables* dtab;
     auto bail = [&](ffe_status s) { ffe_destroy(c); return s; };
-    if ((s = dalloc(c, &dtab, 1))) return bail(s);
-    if (cudaMemcpy(dtab, &c->tab, sizeof(Tables), cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(fail(FFE_ECUDA, "table upload"));
-    d.tab = dtab;
+    build_tables(P, params->filter_a, params->filter_b, params->tci_M, c->tabs_h[P]);
+    c->tab = c->tabs_h[P];
     if ((s = (domain->kind == FFE_DOMAIN_SHELL6 ? build_shell(c) : build_box(c)))) return bail(s);
     d.dt = params->dt > 0 ? params->dt : params->cfl * c->dxmin / c->lam_max * params->c_over_D;
-    if ((s = dalloc(c, &d.mask, d.E))) return bail(s);
-    if ((s = dalloc(c, &d.switched, d.E))) return bail(s);
-    if ((s = dalloc(c, &d.dg_list, d.E))) return bail(s);
-    if ((s = dalloc(c, &d.fd_list, d.E))) return bail(s);
-    if ((s = dalloc(c, &d.flag_list, d.E))) return bail(s);
-    if ((s = dalloc(c, &d.near_list, 4096))) return bail(s);
-    if ((s = dalloc(c, &d.counts, 8))) return bail(s);
-    if ((s = dalloc(c, &d.units, 1))) return bail(s);
-    for (Field* f : {&c->un, &c->Ua, &c->Ub, &c->F2, &c->F3, &c->Fs})
-        if ((s = alloc_field(c, *f, NV))) return bail(s);
-    for (Field* f : {&c->G1, &c->G2, &c->G3, &c->G4})
-        if ((s = alloc_field(c, *f, NG))) return bail(s);
-    if ((s = alloc_field(c, c->J, NJ))) return bail(s);
-    const int64_t ne = d.nc + 2 * GH;
-    if ((s = dalloc(c, &d.ext, (size_t)12 * d.E * ne * ne * ne))) return bail(s);
-    if ((s = dalloc(c, &d.flux, (size_t)(d.curved ? 9 : 3) * NV * d.E * (d.nc + 1) * d.nc * d.nc))) return bail(s);
+    if ((s = finish_create(c, d.E, {P}))) return bail(s);
     *out = c;
     return FFE_OK;
+}
+
+ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elements* els, const int* Ps,
+                            const ffe_metric* metric, const ffe_params* params, int fd_capacity, void* cuda_stream,
+                            ffe_ctx** out) {
+    g_err.clear();
+    if (n_inst < 1 || !doms || !els || !Ps || !metric || !params || !out) return fail(FFE_EINVAL, "bad argument");
+    *out = nullptr;
+    if (metric->kind != FFE_METRIC_MINKOWSKI) return fail(FFE_ENOTIMPL, "batched contexts are flat-space shells");
+    if (fd_capacity < 0) return fail(FFE_EINVAL, "fd_capacity < 0");
+    const ffe_params& p0 = params[0];
+    for (int i = 0; i < n_inst; ++i) {
+        const ffe_domain& dm = doms[i];
+        const ffe_params& pi = params[i];
+        if (dm.kind != FFE_DOMAIN_SHELL6) return fail(FFE_EINVAL, "instance %d: batched instances are shells", i);
+        if (!(dm.r_in > 0) || !(dm.r_out > dm.r_in)) return fail(FFE_EINVAL, "instance %d: need 0 < r_in < r_out", i);
+        if (els[i].n[0] < 1 || els[i].n[2] < 1) return fail(FFE_EINVAL, "instance %d: element counts", i);
+        if (Ps[i] < 3 || Ps[i] > 5) return fail(FFE_EINVAL, "instance %d: order %d outside [3, 5]", i, Ps[i]);
+        for (int k : {dm.bc_lo[0], dm.bc_hi[0]})
+            if (k < FFE_BC_DIRICHLET || k > FFE_BC_STAR) return fail(FFE_EINVAL, "instance %d: boundary kind %d", i, k);
+        if (pi.eta != p0.eta || pi.kappa_psi != p0.kappa_psi || pi.kappa_phi != p0.kappa_phi ||
+            pi.filter_on != p0.filter_on || pi.filter_a != p0.filter_a || pi.filter_b != p0.filter_b ||
+            pi.tci_on != p0.tci_on || pi.tci_M != p0.tci_M || pi.tci_alpha != p0.tci_alpha ||
+            pi.weno_eps != p0.weno_eps || pi.fd_corrector != p0.fd_corrector ||
+            pi.constraint_mode != p0.constraint_mode)
+            return fail(FFE_EINVAL, "instance %d: scheme parameters differ from instance 0", i);
+        if (pi.dt < 0 || (pi.dt == 0 && !(pi.cfl > 0 && pi.c_over_D > 0)))
+            return fail(FFE_EINVAL, "instance %d: need dt > 0 or cfl > 0 and c_over_D > 0", i);
+        if (p0.tci_on && (p0.tci_M < 1 || p0.tci_M > Ps[i])) return fail(FFE_EINVAL, "tci_M=%d", p0.tci_M);
+    }
+    if (p0.constraint_mode < FFE_RELAX || p0.constraint_mode > FFE_RELAX_THEN_HARD)
+        return fail(FFE_EINVAL, "constraint mode %d", p0.constraint_mode);
+    ffe_ctx* c = new ffe_ctx();
+    auto bail = [&](ffe_status s) { ffe_destroy(c); return s; };
+    c->batch = true;
+    c->n_inst = n_inst;
+    c->dom = doms[0];
+    c->el = els[0];
+    c->met = *metric;
+    c->prm = p0;
+    c->st = (cudaStream_t)cuda_stream;
+    c->doms.assign(doms, doms + n_inst);
+    Dev& d = c->d;
+    int Pmax = 0, E = 0;
+    std::vector<int> orders;
+    for (int i = 0; i < n_inst; ++i) {
+        InstInfo in{};
+        in.r_in = doms[i].r_in;
+        in.c = 0.5 * log(doms[i].r_out / doms[i].r_in);
+        in.omega = params[i].omega_star;
+        in.na = els[i].n[0];
+        in.nr = els[i].n[2];
+        in.e0 = E;
+        in.P = Ps[i];
+        c->insts.push_back(in);
+        const int Ei = 6 * in.na * in.na * in.nr;
+        for (int k = 0; k < Ei; ++k) { c->h_eP.push_back(Ps[i]); c->h_einst.push_back(i); }
+        E += Ei;
+        Pmax = Ps[i] > Pmax ? Ps[i] : Pmax;
+        bool seen = false;
+        for (int q : orders) seen |= q == Ps[i];
+        if (!seen) orders.push_back(Ps[i]);
+    }
+    d.E = E;
+    d.P = Pmax;
+    d.np1 = Pmax + 1;
+    d.nn = d.np1 * d.np1 * d.np1;
+    d.nc = 2 * Pmax + 1;
+    d.ncell = d.nc * d.nc * d.nc;
+    d.ndg = (int64_t)E * d.nn;
+    d.eta = p0.constraint_mode == FFE_HARD ? 0.0 : p0.eta;
+    d.kpsi = p0.kappa_psi;
+    d.kphi = p0.kappa_phi;
+    d.weno_eps = p0.weno_eps;
+    d.omega = p0.omega_star;
+    d.mode = p0.constraint_mode;
+    d.filter_on = p0.filter_on;
+    d.tci_on = p0.tci_on;
+    d.fd_corr = p0.fd_corrector;
+    d.curved = 1;
+    for (int P : orders) build_tables(P, p0.filter_a, p0.filter_b, p0.tci_M, c->tabs_h[P]);
+    // geometry of every instance into the element slots
+    const int64_t ndg = d.ndg;
+    std::vector<double> xdg(3 * (size_t)ndg, 0.0), geo(9 * (size_t)ndg, 0.0);
+    std::vector<int> nbr(6 * E, -1), nbf(6 * E, -1), orient(6 * E, 0), bc(6 * E, 0), bface(6 * E, -1);
+    int nbfd = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        InstInfo& in = c->insts[i];
+        const ShellGeo g{in.r_in, in.c, in.na, in.nr};
+        const int P = in.P, np1 = P + 1, nn = np1 * np1 * np1, Ei = 6 * in.na * in.na * in.nr;
+        const Tables& T = c->tabs_h[P];
+        MapFn map = [g](int e, const double xi[3], double x[3], double ij[3][3]) { shell_map(g, e, xi, x, ij); };
+        double dmin = 1e300;
+        for (int el = 0; el < Ei; ++el) {
+            const int e = in.e0 + el;
+            for (int q = 0; q < nn; ++q) {
+                const int ci[3] = {q % np1, (q / np1) % np1, q / (np1 * np1)};
+                const double xi[3] = {T.x[ci[0]], T.x[ci[1]], T.x[ci[2]]};
+                double x[3], ij[3][3];
+                map(el, xi, x, ij);
+                const int64_t p = (int64_t)e * d.nn + q;
+                for (int a = 0; a < 3; ++a) xdg[a * ndg + p] = x[a];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) geo[(3 * a + b) * ndg + p] = ij[a][b];
+            }
+            for (int q = 0; q < nn; ++q) {
+                const int ci[3] = {q % np1, (q / np1) % np1, q / (np1 * np1)};
+                for (int a = 0; a < 3; ++a) {
+                    if (ci[a] == P) continue;
+                    const int q2 = q + (a == 0 ? 1 : (a == 1 ? np1 : np1 * np1));
+                    double s2 = 0.0;
+                    for (int b = 0; b < 3; ++b) {
+                        const double dx = xdg[b * ndg + (int64_t)e * d.nn + q2] - xdg[b * ndg + (int64_t)e * d.nn + q];
+                        s2 += dx * dx;
+                    }
+                    dmin = fmin(dmin, sqrt(s2));
+                }
+            }
+        }
+        in.dt = params[i].dt > 0 ? params[i].dt : params[i].cfl * dmin * params[i].c_over_D;
+        std::vector<double> xn(T.x, T.x + np1);
+        std::vector<int> lnbr, lnbf, lor;
+        match_faces(Ei, map, xn, np1, doms[i].r_out, lnbr, lnbf, lor);
+        for (int el = 0; el < Ei; ++el)
+            for (int f = 0; f < 6; ++f) {
+                const int e = in.e0 + el, k = 6 * el + f;
+                if (lnbr[k] == -2) return bail(fail(FFE_EINVAL, "instance %d: no orientation for a face", i));
+                if (lnbr[k] >= 0) {
+                    nbr[6 * e + f] = lnbr[k] + in.e0;
+                    nbf[6 * e + f] = lnbf[k];
+                    orient[6 * e + f] = lor[k];
+                    continue;
+                }
+                const int ir = (el / (in.na * in.na)) % in.nr;
+                int kind;
+                if (f == 4 && ir == 0) kind = doms[i].bc_lo[0];
+                else if (f == 5 && ir == in.nr - 1) kind = doms[i].bc_hi[0];
+                else return bail(fail(FFE_EINVAL, "instance %d: unmatched interior face", i));
+                bc[6 * e + f] = kind;
+                if (kind == FFE_BC_DIRICHLET) bface[6 * e + f] = nbfd++;
+            }
+    }
+    c->nbf = nbfd;
+    c->h_bface = bface;
+    d.dt = c->insts[0].dt;
+    ffe_status s;
+    double *d_xdg, *d_geo, *d_bdg, *d_bfd, *d_ijac;
+    int *d_nbr, *d_nbf, *d_bc, *d_bface, *d_or;
+    if ((s = dalloc(c, &d_xdg, xdg.size()))) return bail(s);
+    if ((s = dalloc(c, &d_geo, geo.size()))) return bail(s);
+    if ((s = dalloc(c, &d_ijac, 3 * (size_t)E))) return bail(s);
+    if ((s = dalloc(c, &d_nbr, nbr.size()))) return bail(s);
+    if ((s = dalloc(c, &d_nbf, nbf.size()))) return bail(s);
+    if ((s = dalloc(c, &d_or, orient.size()))) return bail(s);
+    if ((s = dalloc(c, &d_bc, bc.size()))) return bail(s);
+    if ((s = dalloc(c, &d_bface, bface.size()))) return bail(s);
+    if ((s = dalloc(c, &d_bdg, (size_t)(nbfd > 0 ? nbfd : 1) * NV * d.np1 * d.np1))) return bail(s);
+    if ((s = dalloc(c, &d_bfd, (size_t)(nbfd > 0 ? nbfd : 1) * NV * GH * d.nc * d.nc))) return bail(s);
+    if (cudaMemcpy(d_xdg, xdg.data(), xdg.size() * 8, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d_geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d_nbf, nbf.data(), nbf.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d_or, orient.data(), orient.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d_bc, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d_bface, bface.data(), bface.size() * 4, cudaMemcpyHostToDevice))
+        return bail(fail(FFE_ECUDA, "geometry upload"));
+    d.xyz_dg = d_xdg;
+    d.xyz_fd = nullptr;
+    d.geo = d_geo;
+    d.ijac = d_ijac;
+    d.nbr = d_nbr;
+    d.nbr_face = d_nbf;
+    d.orient = d_or;
+    d.bc = d_bc;
+    d.bface = d_bface;
+    d.bdg = d_bdg;
+    d.bfd = d_bfd;
+    const int cap = fd_capacity > 0 && fd_capacity < E ? fd_capacity : E;
+    if ((s = finish_create(c, cap, orders))) return bail(s);
+    *out = c;
+    return FFE_OK;
+}
+
+ffe_status ffe_get_layout(ffe_ctx* c, int* elem_P, int* fd_slot, int* elem_inst, int* inst_first, int* n_inst) {
+    if (!c) return fail(FFE_EINVAL, "null context");
+    const Dev& d = c->d;
+    CK(cudaStreamSynchronize(c->st));
+    for (int e = 0; e < d.E; ++e) {
+        if (elem_P) elem_P[e] = host_P(c, e);
+        if (elem_inst) elem_inst[e] = c->batch ? c->h_einst[e] : 0;
+    }
+    if (fd_slot) {
+        if (d.fd_slot) CK(cudaMemcpy(fd_slot, d.fd_slot, d.E * sizeof(int), cudaMemcpyDeviceToHost));
+        else
+            for (int e = 0; e < d.E; ++e) fd_slot[e] = e;
+    }
+    if (inst_first) {
+        for (int i = 0; i < c->n_inst; ++i) inst_first[i] = c->batch ? c->insts[i].e0 : 0;
+        inst_first[c->n_inst] = d.E;
+    }
+    if (n_inst) *n_inst = c->n_inst;
+    return FFE_OK;
+}
+
+ffe_status ffe_set_initial_batch(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) {
+    g_err.clear();
+    if (!c) return fail(FFE_EINVAL, "null context");
+    if (id_kind < FFE_ID_FAST_WAVE || id_kind > FFE_ID_DIPOLE) return fail(FFE_EINVAL, "initial data kind %d", id_kind);
+    if (n_params < 0 || (n_params > 0 && !id_params)) return fail(FFE_EINVAL, "bad initial-data parameters");
+    (void)flags;
+    c->id_kind = id_kind;
+    if (c->batch) {
+        c->id_nprm = n_params;
+        c->id_prm_inst.assign(id_params, id_params + (size_t)n_params * c->n_inst);
+    } else {
+        c->id_prm.assign(id_params, id_params + n_params);
+    }
+    return set_initial_impl(c, id_kind);
 }
 
 ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) {
@@ -792,45 +1197,12 @@ ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int
     (void)flags;
     c->id_kind = id_kind;
     c->id_prm.assign(id_params, id_params + n_params);
-    const Dev& d = c->d;
-    std::vector<double> xdg(3 * (size_t)d.ndg), U(NV * (size_t)(d.ndg + d.nfd), 0.0);
-    CK(cudaMemcpy(xdg.data(), d.xyz_dg, xdg.size() * 8, cudaMemcpyDeviceToHost));
-    parallel_for(d.ndg, [&](int64_t p) {
-        double X[3] = {xdg[p], xdg[d.ndg + p], xdg[2 * d.ndg + p]}, u[NV];
-        initial_point(id_kind, id_params, n_params, X, u);
-        for (int v = 0; v < NV; ++v) U[v * d.ndg + p] = u[v];
-    });
-    std::vector<unsigned char> mask(d.E, 0);
-    if (d.tci_on) {
-        double* ratio;
-        ffe_status s;
-        if ((s = dalloc(c, &ratio, d.E))) return s;
-        CK(cudaMemcpy(c->un.p, U.data(), NV * d.ndg * 8, cudaMemcpyHostToDevice));
-        launch_tci_ratio(d, c->un.p, ratio, c->st);
-        std::vector<double> r(d.E);
-        CK(cudaMemcpyAsync(r.data(), ratio, d.E * 8, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        std::vector<double> xfd(3 * (size_t)d.nfd);
-        CK(cudaMemcpy(xfd.data(), d.xyz_fd, xfd.size() * 8, cudaMemcpyDeviceToHost));
-        for (int e = 0; e < d.E; ++e) {
-            if (!(r[e] > d.thr_dg)) continue;
-            mask[e] = 1;
-            for (int q = 0; q < d.ncell; ++q) {
-                const int64_t p = (int64_t)e * d.ncell + q;
-                double X[3] = {xfd[p], xfd[d.nfd + p], xfd[2 * d.nfd + p]}, u[NV];
-                initial_point(id_kind, id_params, n_params, X, u);
-                for (int v = 0; v < NV; ++v) U[NV * d.ndg + v * d.nfd + p] = u[v];
-            }
-        }
+    if (c->batch) {
+        c->id_nprm = n_params;
+        c->id_prm_inst.clear();
+        for (int i = 0; i < c->n_inst; ++i) c->id_prm_inst.insert(c->id_prm_inst.end(), id_params, id_params + n_params);
     }
-    CK(cudaMemcpy(c->un.p, U.data(), U.size() * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d.mask, mask.data(), d.E, cudaMemcpyHostToDevice));
-    ffe_status s;
-    if ((s = fill_dirichlet(c))) return s;
-    CK(cudaMemset(d.units, 0, sizeof(unsigned long long)));
-    c->t = 0.0;
-    c->steps = 0;
-    return FFE_OK;
+    return set_initial_impl(c, id_kind);
 }
 
 ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) {

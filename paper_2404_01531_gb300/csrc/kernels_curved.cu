@@ -23,7 +23,7 @@ struct DGC {
     static constexpr int NT = ((nn + 31) / 32) * 32;
     static constexpr int NW = NT / 32;
     // shared doubles: U[9][nn] | F[27][nn] (the filter buffer [9][nn] aliases it) | C[6][9][nf] | red[2][NW]
-    static constexpr int SMEM = (9 * nn + 27 * nn + 54 * nf + 2 * NW) * 8;
+    static constexpr int SMEM = (9 * nn + 27 * nn + 54 * nf + 2 * NW + 1) * 8;
 };
 
 template <bool KS>
@@ -78,25 +78,24 @@ __device__ __forceinline__ void nbr_node(const Dev& d, int e, int f, int ta, int
     c[u2] = b2;
 }
 
-template <int P, int SUB, bool KS>
-__global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
+// One element of order P processed by a block of NT threads (NT >= (P+1)^3).
+template <int P, int NT, int SUB, bool KS>
+__device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, int e, double* sm) {
     using K = DGC<P>;
-    constexpr int np1 = K::np1, nn = K::nn, nf = K::nf, NT = K::NT, NW = K::NW;
-    extern __shared__ double sm[];
+    constexpr int np1 = K::np1, nn = K::nn, nf = K::nf, NW = NT / 32;
     double* sU = sm;                 // [9][nn]
     double* sF = sU + 9 * nn;        // [3][9][nn]
     double* sT = sF;                 // filter buffer [9][nn]
     double* sC = sF + 27 * nn;       // [6][9][nf]
     double* red = sC + 54 * nf;
-    const Tables& T = *d.tab;
+    const Tables& T = d.tabs[P];
     const int tid = threadIdx.x;
     const bool act = tid < nn;
     const int ci[3] = {tid % np1, (tid / np1) % np1, tid / (np1 * np1)};
     const double w0inv = 1.0 / T.w0;
-    const int nwork = d.counts[0];
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-        const int e = d.dg_list[w];
-        const int64_t eb = (int64_t)e * nn;
+    {
+        const int64_t eb = (int64_t)e * d.nn;
+        const double dt = dt_of(d, e);
         for (int t = tid; t < NV * nn; t += NT) sU[t] = a.Uin.dg(t / nn)[eb + t % nn];
         __syncthreads();
         PM m;
@@ -168,12 +167,12 @@ __global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
                 int cn[3];
                 nbr_node<P>(d, e, f, ta, tb, cn);
                 if (d.mask[nb] == 0) {
-                    const int64_t q = (int64_t)nb * nn + cn[0] + np1 * (cn[1] + np1 * cn[2]);
+                    const int64_t q = (int64_t)nb * d.nn + cn[0] + np1 * (cn[1] + np1 * cn[2]);
                     for (int v = 0; v < NV; ++v) Ue[v] = a.Uin.dg(v)[q];
                 } else {
                     const int nc = T.nc;
                     const int lo0 = T.f2d_lo[cn[0]], lo1 = T.f2d_lo[cn[1]], lo2 = T.f2d_lo[cn[2]];
-                    const int64_t base = (int64_t)nb * nc * nc * nc;
+                    const int64_t base = fdb(d, nb);
                     for (int v = 0; v < NV; ++v) {
                         const double* src = a.Uin.fd(v) + base;
                         double acc = 0.0;
@@ -200,7 +199,7 @@ __global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
                 } else {
                     double xn[3];
                     for (int q = 0; q < 3; ++q) xn[q] = d.xyz_dg[(int64_t)q * d.ndg + p];
-                    bc_star_flat(Ui, xn, d.omega, Ue);
+                    bc_star_flat(Ui, xn, omega_of(d, e), Ue);
                 }
             }
             double Fe[3][NV], jde[3];
@@ -228,7 +227,7 @@ __global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
             if (act)
                 for (int v = 0; v < NV; ++v) a.Fout.dg(v)[eb + tid] = du[v];
             __syncthreads();
-            continue;
+            return;
         }
         double u[NV];
         if (act) {
@@ -237,7 +236,6 @@ __global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
             if (KS) {
                 // stage combination with the metric-aware solve and clamp
                 const int gv[NG] = {0, 1, 2, 6, 7};
-                const double dt = d.dt;
                 for (int v = 0; v < NV; ++v) u[v] = a.un.dg(v)[eb + tid];
                 if (SUB == SUB_A) {
                     for (int v = 0; v < NV; ++v) u[v] = fma(dt, du[v], u[v]);
@@ -256,7 +254,7 @@ __global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
                 if (SUB != SUB_C && !stiff_solve_gen(u, m, d, dt * IM_A)) atomic_status(d, 2);
                 if (d.mode != FFE_RELAX) hard_clamp_gen(u, m);
             } else {
-                substep_combine(d, SUB, du, eb + tid, false, a, u);
+                substep_combine(d, SUB, du, eb + tid, false, a, dt, u);
             }
         }
         __syncthreads();
@@ -306,14 +304,20 @@ __global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
             }
             block_sum2c<NW>(num, den, red);
             const double ratio = den > 0.0 ? sqrt(num / den) : 0.0;
-            flagged = ratio > d.thr_dg;
+            const double thr = d.thr_dgP[P];
             if (tid == 0) {
-                if (fabs(ratio - d.thr_dg) <= 1e-12 * d.thr_dg) d.near_list[atomicAdd(&d.counts[3], 1) & 4095] = e;
-                if (flagged) {
+                int fl = ratio > thr;
+                if (fabs(ratio - thr) <= 1e-12 * thr) d.near_list[atomicAdd(&d.counts[3], 1) & 4095] = e;
+                if (fl && take_fd_slot(d, e)) {
                     d.flag_list[atomicAdd(&d.counts[2], 1)] = e;
                     d.switched[e] = 1;
+                } else {
+                    fl = 0;
                 }
+                red[2 * NW] = fl;
             }
+            __syncthreads();
+            flagged = red[2 * NW] != 0.0;
         }
         if (!flagged && tid == 0) atomicAdd(d.units, (unsigned long long)nn);
         if (!flagged && act) {
@@ -334,10 +338,32 @@ __global__ void __launch_bounds__(DGC<P>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
     }
 }
 
+
+// Persistent kernel over the DG work list: each item is dispatched on its
+// element's order (batched contexts mix P = 4 and P = 5 in one launch).
+template <int PMAX, int SUB, bool KS>
+__global__ void __launch_bounds__(DGC<PMAX>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
+    constexpr int NT = DGC<PMAX>::NT;
+    extern __shared__ double sm[];
+    const int nwork = d.counts[0];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int e = d.dg_list[w];
+        const int P = elem_P(d, e);
+        if (P == PMAX) {
+            dg_curved_elem<PMAX, NT, SUB, KS>(d, a, e, sm);
+        } else if constexpr (PMAX > 3) {
+            if (P == PMAX - 1) dg_curved_elem<PMAX - 1, NT, SUB, KS>(d, a, e, sm);
+            else if constexpr (PMAX > 4) {
+                if (P == PMAX - 2) dg_curved_elem<PMAX - 2, NT, SUB, KS>(d, a, e, sm);
+            }
+        }
+    }
+}
+
 template <int P, bool KS>
 static void curved_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_t st) {
     using K = DGC<P>;
-    const int grid = 152 * 2;
+    const int grid = d.dg_grid > 0 ? d.dg_grid : 152 * 2;
 #define FFE_LAUNCH_C(S)                                                                                   \
     cudaFuncSetAttribute(k_dg_curved<P, S, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);   \
     k_dg_curved<P, S, KS><<<grid, K::NT, K::SMEM, st>>>(d, a);

@@ -52,16 +52,17 @@ __global__ void k_current(Dev d, Field U, Field J, const int* list, int count_in
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (list == nullptr) {
         for (int64_t p = tid; p < d.ndg; p += stride) {
-            int e = (int)(p / d.nn);
-            if (d.mask[e] != 0) continue;
+            const int e = (int)(p / d.nn);
+            if (d.mask[e] != 0 || (int)(p % d.nn) >= esz(d, e).nn) continue;
             double u[NV], jd[3], jf[3];
             for (int v = 0; v < NV; ++v) u[v] = U.dg(v)[p];
             current_flat(u, d.eta, jd, jf);
             for (int c = 0; c < 3; ++c) { J.dg(c)[p] = jd[c]; J.dg(3 + c)[p] = jf[c]; }
         }
         for (int64_t p = tid; p < d.nfd; p += stride) {
-            int e = (int)(p / d.ncell);
-            if (d.mask[e] != 1) continue;
+            const int sl = (int)(p / d.ncell);
+            const int e = d.slot_elem ? d.slot_elem[sl] : sl;
+            if (e < 0 || d.mask[e] != 1 || (int)(p % d.ncell) >= esz(d, e).ncell) continue;
             double u[NV], jd[3], jf[3];
             for (int v = 0; v < NV; ++v) u[v] = U.fd(v)[p];
             current_flat(u, d.eta, jd, jf);
@@ -70,12 +71,14 @@ __global__ void k_current(Dev d, Field U, Field J, const int* list, int count_in
     } else {
         int n = d.counts[count_index];
         for (int64_t q = tid; q < (int64_t)n * d.ncell; q += stride) {
-            int e = list[q / d.ncell];
-            int64_t p = (int64_t)e * d.ncell + q % d.ncell;
+            const int e = list[q / d.ncell];
+            const int c = (int)(q % d.ncell);
+            if (d.mask[e] != 1 || c >= esz(d, e).ncell) continue;
+            const int64_t p = fdb(d, e) + c;
             double u[NV], jd[3], jf[3];
             for (int v = 0; v < NV; ++v) u[v] = U.fd(v)[p];
             current_flat(u, d.eta, jd, jf);
-            for (int c = 0; c < 3; ++c) { J.fd(c)[p] = jd[c]; J.fd(3 + c)[p] = jf[c]; }
+            for (int c2 = 0; c2 < 3; ++c2) { J.fd(c2)[p] = jd[c2]; J.fd(3 + c2)[p] = jf[c2]; }
         }
     }
 }
@@ -89,8 +92,8 @@ void launch_current(const Dev& d, Field U, Field J, const int* list, int count_i
 
 // ---------------------------------------------------------------------------
 // Stages 1 and 2 are pointwise: U1 = solve(u_n), G1 = G(U1); U2 = solve(u_n - dt a G1), G2 = G(U2).
-__device__ __forceinline__ void stage12_point(const Dev& d, double* u, double* g1, double* g2) {
-    const double dta = d.dt * IM_A;
+__device__ __forceinline__ void stage12_point(const Dev& d, double dt, double* u, double* g1, double* g2) {
+    const double dta = dt * IM_A;
     double U1[NV];
     for (int v = 0; v < NV; ++v) U1[v] = u[v];
     if (!stiff_solve_flat(U1, d, dta)) atomic_status(d, 2);
@@ -110,18 +113,21 @@ __global__ void k_stage12(Dev d, Field un, Field Ua, Field G1, Field G2) {
     int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = tid; p < d.ndg; p += stride) {
-        if (d.mask[p / d.nn] != 0) continue;
+        const int e = (int)(p / d.nn);
+        if (d.mask[e] != 0 || (int)(p % d.nn) >= esz(d, e).nn) continue;
         double u[NV], g1[NG], g2[NG];
         for (int v = 0; v < NV; ++v) u[v] = un.dg(v)[p];
-        stage12_point(d, u, g1, g2);
+        stage12_point(d, dt_of(d, e), u, g1, g2);
         for (int v = 0; v < NV; ++v) Ua.dg(v)[p] = u[v];
         for (int c = 0; c < NG; ++c) { G1.dg(c)[p] = g1[c]; G2.dg(c)[p] = g2[c]; }
     }
     for (int64_t p = tid; p < d.nfd; p += stride) {
-        if (d.mask[p / d.ncell] != 1) continue;
+        const int sl = (int)(p / d.ncell);
+        const int e = d.slot_elem ? d.slot_elem[sl] : sl;
+        if (e < 0 || d.mask[e] != 1 || (int)(p % d.ncell) >= esz(d, e).ncell) continue;
         double u[NV], g1[NG], g2[NG];
         for (int v = 0; v < NV; ++v) u[v] = un.fd(v)[p];
-        stage12_point(d, u, g1, g2);
+        stage12_point(d, dt_of(d, e), u, g1, g2);
         for (int v = 0; v < NV; ++v) Ua.fd(v)[p] = u[v];
         for (int c = 0; c < NG; ++c) { G1.fd(c)[p] = g1[c]; G2.fd(c)[p] = g2[c]; }
     }
@@ -193,7 +199,7 @@ __device__ void dg_external_state(const Dev& d, const SubArgs& a, int e, int f, 
         // FD neighbour: its FD->DG projection evaluated at this node (6-point stencils)
         const int nc = T.nc;
         const int lo0 = T.f2d_lo[c[0]], lo1 = T.f2d_lo[c[1]], lo2 = T.f2d_lo[c[2]];
-        const int64_t base = (int64_t)nb * nc * nc * nc;
+        const int64_t base = fdb(d, nb);
         for (int v = 0; v < NV; ++v) {
             const double* src = a.Uin.fd(v) + base;
             double acc = 0.0;
@@ -336,7 +342,7 @@ __global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) 
         if (act) {
             if (SUB != SUB_C)
                 for (int v = 0; v < NV; ++v) a.Fout.dg(v)[eb + tid] = du[v];
-            substep_combine(d, SUB, du, eb + tid, false, a, u);
+            substep_combine(d, SUB, du, eb + tid, false, a, d.dt, u);
         }
         __syncthreads();   // sU, sJ, sC are free from here on
         if (d.filter_on) {
@@ -403,14 +409,19 @@ __global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) 
             }
             block_sum2<NW>(num, den, red);
             const double ratio = den > 0.0 ? sqrt(num / den) : 0.0;
-            flagged = ratio > d.thr_dg;
             if (tid == 0) {
+                int fl = ratio > d.thr_dg;
                 if (fabs(ratio - d.thr_dg) <= 1e-12 * d.thr_dg) d.near_list[atomicAdd(&d.counts[3], 1) & 4095] = e;
-                if (flagged) {
+                if (fl && take_fd_slot(d, e)) {
                     d.flag_list[atomicAdd(&d.counts[2], 1)] = e;
                     d.switched[e] = 1;
+                } else {
+                    fl = 0;
                 }
+                s_flag = fl;
             }
+            __syncthreads();
+            flagged = s_flag != 0;
         }
         if (!flagged && tid == 0) atomicAdd(d.units, (unsigned long long)nn);
         if (!flagged && act) {
@@ -433,7 +444,7 @@ __global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) 
 template <int P>
 static void dg_sub_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_t st) {
     using K = DGK<P>;
-    const int grid = 152 * 4;
+    const int grid = d.dg_grid > 0 ? d.dg_grid : 152 * 4;
     switch (sub) {
         case SUB_A:
             cudaFuncSetAttribute(k_dg_substep<P, SUB_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
@@ -473,13 +484,14 @@ void launch_dg_substep(const Dev& d, int sub, Field Uin, Field J, Field un, Fiel
 // ---------------------------------------------------------------------------
 // Indicator ratio of the DG data of every element (diagnostic entry point).
 __global__ void k_tci_ratio(Dev d, const double* Udg, double* ratio) {
-    const Tables& T = *d.tab;
-    const int np1 = d.np1, nn = d.nn;
     __shared__ double su[MAXNP * MAXNP * MAXNP * 3];
     __shared__ double red[2];
     for (int e = blockIdx.x; e < d.E; e += gridDim.x) {
+        const ES es = esz(d, e);
+        const Tables& T = d.tabs[es.P];
+        const int np1 = es.np1, nn = es.nn;
         for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-            const int64_t p = (int64_t)e * nn + t;
+            const int64_t p = (int64_t)e * d.nn + t;
             const double bx = Udg[3 * d.ndg + p], by = Udg[4 * d.ndg + p], bz = Udg[5 * d.ndg + p];
             su[t] = sqrt(fma(bz, bz, fma(by, by, bx * bx)));
         }

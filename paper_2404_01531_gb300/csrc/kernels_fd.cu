@@ -1,12 +1,17 @@
-// FD-subcell kernels of libffe (flat metric, affine box elements), Sec. III.C.2:
-//   k_fd_fill_interior / k_fd_fill_ghosts  build, per FD element, an extended
-//       block of 12 quantities (U and J~) with 3 ghost layers per face;
-//   k_fd_flux    one thread per face: WENO5-Z (point-value interpolation form,
-//       Z weights with q = 2) left/right states of the 12 quantities, Rusanov
-//       flux, optional 4th-order corrector with cell-centred fluxes;
-//   k_fd_update  one thread per cell: flux difference, sources and the IMEX stage;
+// FD-subcell kernels of libffe, Sec. III.C.2:
+//   k_fd_fill_interior / k_fd_fill_ghosts  build, per listed FD element, an
+//       extended block of 12 quantities (U and J~) with 3 ghost layers per face;
+//   k_fd_flux[_curved]  one thread per face: WENO5-Z (point-value interpolation
+//       form, Z weights with q = 2) left/right states of the 12 quantities,
+//       Rusanov flux, optional 4th-order corrector with cell-centred fluxes;
+//   k_fd_update  one thread per cell: flux difference, sources, IMEX stage;
 //   k_rollback_project  DG -> FD projection of a flagged element's substep inputs;
 //   k_fd2dg      end-of-step FD -> DG check with alpha' = alpha + 1 (Sec. III.C.3).
+// Listed FD elements are processed in chunks of d.chunk so that the scratch
+// (extended blocks, face fluxes) is bounded whatever the number of FD elements.
+// Elements may have different orders (batched contexts): every size below is
+// the element's own; the slot strides d.ncell / (d.nc+6)^3 / (d.nc+1) d.nc^2
+// are those of the largest order.
 #include "ffe_internal.h"
 #include "physics.cuh"
 #include "shellmap.cuh"
@@ -16,30 +21,40 @@ namespace ffe {
 
 constexpr int NQ = 12;  // reconstructed quantities: 9 evolved + J~ (3)
 
-__device__ __forceinline__ int ext_n(const Dev& d) { return d.nc + 2 * GH; }
 __device__ __forceinline__ int64_t ext_size(const Dev& d) {
     const int64_t ne = d.nc + 2 * GH;
     return ne * ne * ne;
 }
-// ext layout: [NQ][E][ne^3] indexed by list position w
-__device__ __forceinline__ double* ext_at(const Dev& d, int q, int w) {
-    return d.ext + ((int64_t)q * d.E + w) * ext_size(d);
+// ext layout: [NQ][chunk][ext_size] indexed by position in the chunk
+__device__ __forceinline__ double* ext_at(const Dev& d, int q, int wl) {
+    return d.ext + ((int64_t)q * d.chunk + wl) * ext_size(d);
 }
 __device__ __forceinline__ int64_t nface(const Dev& d) { return (int64_t)(d.nc + 1) * d.nc * d.nc; }
-// flux layout: [3][NV][E][nface] indexed by list position w; curved meshes
-// keep every physical component j: [3 (k)][3 (j)][NV][E][nface]
-__device__ __forceinline__ double* flux_at(const Dev& d, int k, int v, int w) {
-    return d.flux + (((int64_t)k * NV + v) * d.E + w) * nface(d);
+// flux layout: [3][NV][chunk][nface]; curved meshes keep every physical
+// component j: [3 (k)][3 (j)][NV][chunk][nface]
+__device__ __forceinline__ double* flux_at(const Dev& d, int k, int v, int wl) {
+    return d.flux + (((int64_t)k * NV + v) * d.chunk + wl) * nface(d);
 }
-__device__ __forceinline__ double* flux_at_c(const Dev& d, int k, int j, int v, int w) {
-    return d.flux + ((((int64_t)k * 3 + j) * NV + v) * d.E + w) * nface(d);
+__device__ __forceinline__ double* flux_at_c(const Dev& d, int k, int j, int v, int wl) {
+    return d.flux + ((((int64_t)k * 3 + j) * NV + v) * d.chunk + wl) * nface(d);
 }
-__device__ __forceinline__ ShellGeo shell_of(const Dev& d) {
+// shell map of element e (its instance's geometry and its index inside the instance)
+__device__ __forceinline__ ShellGeo shell_for(const Dev& d, int e, int& el) {
     ShellGeo g;
-    g.r_in = d.shell_rin;
-    g.c = d.shell_c;
-    g.na = d.shell_na;
-    g.nr = d.shell_nr;
+    if (d.einst) {
+        const InstInfo& in = d.inst[d.einst[e]];
+        g.r_in = in.r_in;
+        g.c = in.c;
+        g.na = in.na;
+        g.nr = in.nr;
+        el = e - in.e0;
+    } else {
+        g.r_in = d.shell_rin;
+        g.c = d.shell_c;
+        g.na = d.shell_na;
+        g.nr = d.shell_nr;
+        el = e;
+    }
     return g;
 }
 
@@ -48,34 +63,43 @@ __device__ __forceinline__ void axes_of(int dd, int& t1, int& t2) {
     t2 = dd == 2 ? 1 : 2;
 }
 
+// number of listed elements in this chunk
+__device__ __forceinline__ int chunk_n(const Dev& d, int ci, int w0) {
+    const int n = d.counts[ci] - w0;
+    return n < 0 ? 0 : (n > d.chunk ? d.chunk : n);
+}
+
 // ---------------------------------------------------------------------------
-__global__ void k_fd_fill_interior(Dev d, const int* list, int ci, Field U, Field J) {
-    const int n = d.counts[ci];
-    const int nc = d.nc, ne = nc + 2 * GH;
+__global__ void k_fd_fill_interior(Dev d, const int* list, int ci, int w0, Field U, Field J) {
+    const int n = chunk_n(d, ci, w0);
     const int64_t total = (int64_t)n * d.ncell;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(q / d.ncell), c = (int)(q % d.ncell);
-        const int e = list[w];
+        const int wl = (int)(q / d.ncell), c = (int)(q % d.ncell);
+        const int e = list[w0 + wl];
+        const ES s = esz(d, e);
+        if (c >= s.ncell) continue;
+        const int nc = s.nc, ne = nc + 2 * GH;
         const int x = c % nc, y = (c / nc) % nc, z = c / (nc * nc);
-        const int64_t p = (int64_t)e * d.ncell + c;
+        const int64_t p = fdb(d, e) + c;
         const int64_t o = (x + GH) + ne * ((y + GH) + ne * (z + GH));
-        for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = U.fd(v)[p];
-        for (int k = 0; k < 3; ++k) ext_at(d, NV + k, w)[o] = J.fd(3 + k)[p];
+        for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[o] = U.fd(v)[p];
+        for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[o] = J.fd(3 + k)[p];
     }
 }
 
-// One CTA per (list position, face): fill the 3 ghost layers of that face.
-__global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field J) {
-    const Tables& T = *d.tab;
-    const int n = d.counts[ci];
-    const int nc = d.nc, ne = nc + 2 * GH, np1 = d.np1, nn = d.nn;
+// One CTA per (chunk position, face): fill the 3 ghost layers of that face.
+__global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U, Field J) {
+    const int n = chunk_n(d, ci, w0);
     extern __shared__ double sm[];
-    double* su = sm;                          // neighbour DG block [9][nn]
-    double* t1b = su + NV * nn;               // [9][GH][np1][np1]
-    double* t2b = t1b + NV * GH * np1 * np1;  // [9][GH][nc][np1]
     for (int item = blockIdx.x; item < n * 6; item += gridDim.x) {
-        const int w = item / 6, f = item % 6;
-        const int e = list[w];
+        const int wl = item / 6, f = item % 6;
+        const int e = list[w0 + wl];
+        const ES es = esz(d, e);
+        const Tables& T = d.tabs[es.P];
+        const int nc = es.nc, ne = nc + 2 * GH, np1 = es.np1, nn = es.nn;
+        double* su = sm;                          // neighbour DG block [9][nn]
+        double* t1b = su + NV * nn;               // [9][GH][np1][np1]
+        double* t2b = t1b + NV * GH * np1 * np1;  // [9][GH][np1][nc]
         const int dd = f >> 1, s = f & 1;
         int t1, t2;
         axes_of(dd, t1, t2);
@@ -94,6 +118,7 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
             int u1, u2;
             axes_of(d2, u1, u2);
             const int o = d.orient[e * 6 + f];
+            const int64_t nbase = fdb(d, nb);
             for (int t = threadIdx.x; t < nper; t += blockDim.x) {
                 const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
                 int a2, b2;
@@ -102,10 +127,10 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
                 c[d2] = s2 ? nc - 1 - g : g;
                 c[u1] = a2;
                 c[u2] = b2;
-                const int64_t p = (int64_t)nb * d.ncell + c[0] + nc * (c[1] + nc * c[2]);
-                const int64_t o = ghost_offset(g, ta, tb);
-                for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = U.fd(v)[p];
-                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, w)[o] = J.fd(3 + k)[p];
+                const int64_t p = nbase + c[0] + nc * (c[1] + nc * c[2]);
+                const int64_t og = ghost_offset(g, ta, tb);
+                for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[og] = U.fd(v)[p];
+                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = J.fd(3 + k)[p];
             }
         } else if (nb >= 0) {
             // DG neighbour: its polynomial at its own subcell centres (DG -> FD), 3 layers
@@ -115,7 +140,7 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
             axes_of(d2, u1, u2);
             const int o = d.orient[e * 6 + f];
             for (int t = threadIdx.x; t < NV * nn; t += blockDim.x)
-                su[t] = U.dg(t / nn)[(int64_t)nb * nn + t % nn];
+                su[t] = U.dg(t / nn)[(int64_t)nb * d.nn + t % nn];
             __syncthreads();
             // contract the normal direction for the 3 layers
             for (int t = threadIdx.x; t < NV * GH * np1 * np1; t += blockDim.x) {
@@ -125,7 +150,9 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
                 double acc = 0.0;
                 for (int m = 0; m < np1; ++m) {
                     int c[3];
-                    c[d2] = m; c[u1] = a1; c[u2] = a2;
+                    c[d2] = m;
+                    c[u1] = a1;
+                    c[u2] = a2;
                     acc = fma(T.P2F[cn][m], su[v * nn + c[0] + np1 * (c[1] + np1 * c[2])], acc);
                 }
                 t1b[t] = acc;
@@ -135,8 +162,7 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
                 const int v = t / (GH * nc * np1), r = t % (GH * nc * np1);
                 const int g = r / (nc * np1), ta = r % nc, a2 = (r / nc) % np1;
                 double acc = 0.0;
-                for (int m = 0; m < np1; ++m)
-                    acc = fma(T.P2F[ta][m], t1b[((v * GH + g) * np1 + a2) * np1 + m], acc);
+                for (int m = 0; m < np1; ++m) acc = fma(T.P2F[ta][m], t1b[((v * GH + g) * np1 + a2) * np1 + m], acc);
                 t2b[t] = acc;
             }
             __syncthreads();
@@ -147,14 +173,13 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
                 double u[NV], jd[3], jf[3];
                 for (int v = 0; v < NV; ++v) {
                     double acc = 0.0;
-                    for (int m = 0; m < np1; ++m)
-                        acc = fma(T.P2F[b2][m], t2b[((v * GH + g) * np1 + m) * nc + a2], acc);
+                    for (int m = 0; m < np1; ++m) acc = fma(T.P2F[b2][m], t2b[((v * GH + g) * np1 + m) * nc + a2], acc);
                     u[v] = acc;
                 }
                 current_flat(u, d.eta, jd, jf);
-                const int64_t o = ghost_offset(g, ta, tb);
-                for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = u[v];
-                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, w)[o] = jf[k];
+                const int64_t og = ghost_offset(g, ta, tb);
+                for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[og] = u[v];
+                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = jf[k];
             }
             __syncthreads();
         } else {
@@ -163,7 +188,7 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
                 const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
                 double u[NV], jd[3], jf[3];
                 if (kind == FFE_BC_DIRICHLET) {
-                    const double* src = d.bfd + (int64_t)d.bface[e * 6 + f] * NV * GH * nc * nc;
+                    const double* src = d.bfd + (int64_t)d.bface[e * 6 + f] * NV * GH * d.nc * d.nc;
                     for (int v = 0; v < NV; ++v) u[v] = src[(v * GH + g) * nc * nc + ta + nc * tb];
                 } else {
                     // state from the outermost interior cell of this column
@@ -171,7 +196,7 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
                     c[dd] = s ? nc - 1 : 0;
                     c[t1] = ta;
                     c[t2] = tb;
-                    const int64_t p = (int64_t)e * d.ncell + c[0] + nc * (c[1] + nc * c[2]);
+                    const int64_t p = fdb(d, e) + c[0] + nc * (c[1] + nc * c[2]);
                     double ui[NV];
                     for (int v = 0; v < NV; ++v) ui[v] = U.fd(v)[p];
                     if (kind == FFE_BC_NO_INCOMING) {
@@ -183,22 +208,33 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, Field U, Field 
                             xi[dd] = s ? 1.0 : -1.0;
                             xi[t1] = -1.0 + (ta + 0.5) * 2.0 / nc;
                             xi[t2] = -1.0 + (tb + 0.5) * 2.0 / nc;
-                            shell_map(shell_of(d), e, xi, x, ij);
-                            const double sg = s ? 1.0 : -1.0;
+                            int el;
+                            const ShellGeo sg = shell_for(d, e, el);
+                            shell_map(sg, el, xi, x, ij);
+                            const double sgn = s ? 1.0 : -1.0;
                             const double nn2 = sqrt(ij[dd][0] * ij[dd][0] + ij[dd][1] * ij[dd][1] + ij[dd][2] * ij[dd][2]);
-                            for (int q = 0; q < 3; ++q) nrm[q] = sg * ij[dd][q] / nn2;
+                            for (int q = 0; q < 3; ++q) nrm[q] = sgn * ij[dd][q] / nn2;
                         }
                         bc_no_incoming_flat(ui, nrm, u);
                     } else {
                         double x[3];
-                        for (int k = 0; k < 3; ++k) x[k] = d.xyz_fd[(int64_t)k * d.nfd + p];
-                        bc_star_flat(ui, x, d.omega, u);
+                        if (d.curved) {
+                            // centre of the outermost cell of this column
+                            double xi[3], ij[3][3];
+                            for (int q = 0; q < 3; ++q) xi[q] = -1.0 + (c[q] + 0.5) * 2.0 / nc;
+                            int el;
+                            const ShellGeo sg = shell_for(d, e, el);
+                            shell_map(sg, el, xi, x, ij);
+                        } else {
+                            for (int k = 0; k < 3; ++k) x[k] = d.xyz_fd[(int64_t)k * d.nfd + p];
+                        }
+                        bc_star_flat(ui, x, omega_of(d, e), u);
                     }
                 }
                 current_flat(u, d.eta, jd, jf);
-                const int64_t o = ghost_offset(g, ta, tb);
-                for (int v = 0; v < NV; ++v) ext_at(d, v, w)[o] = u[v];
-                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, w)[o] = jf[k];
+                const int64_t og = ghost_offset(g, ta, tb);
+                for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[og] = u[v];
+                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = jf[k];
             }
         }
     }
@@ -230,52 +266,65 @@ __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double
     return fma(A0, p0, fma(A1, p1, A2 * p2)) / (A0 + A1 + A2);
 }
 
-// One thread per (list position, direction, face).
-__global__ void k_fd_flux(Dev d, const int* list, int ci) {
-    const int n = d.counts[ci];
-    const int nc = d.nc, ne = nc + 2 * GH;
-    const int64_t nfc = (int64_t)(nc + 1) * nc * nc;
+// face fi of direction k: position m along k, tangential (ta, tb); false past the element's faces
+__device__ __forceinline__ bool face_coords(int64_t fi, int nc, int& m, int& ta, int& tb) {
+    const int64_t nf = (int64_t)(nc + 1) * nc * nc;
+    if (fi >= nf) return false;
+    m = (int)(fi % (nc + 1));
+    ta = (int)((fi / (nc + 1)) % nc);
+    tb = (int)(fi / ((int64_t)(nc + 1) * nc));
+    return true;
+}
+
+// 12 left/right face values and the two cells either side, from the extended block
+__device__ __forceinline__ void reconstruct(const Dev& d, int wl, int k, int m, int ta, int tb, int nc,
+                                            double* UL, double* UR, double* Um, double* Up) {
+    const int ne = nc + 2 * GH;
+    int t1, t2;
+    axes_of(k, t1, t2);
+    int c[3];
+    c[k] = m;
+    c[t1] = ta + GH;
+    c[t2] = tb + GH;
+    const int64_t base = c[0] + (int64_t)ne * (c[1] + (int64_t)ne * c[2]);
+    const int64_t stride = k == 0 ? 1 : (k == 1 ? ne : (int64_t)ne * ne);
+    for (int qq = 0; qq < NQ; ++qq) {
+        const double* src = ext_at(d, qq, wl) + base;
+        const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
+        const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
+        UL[qq] = weno5z(v0, v1, v2, v3, v4, d.weno_eps);
+        UR[qq] = weno5z(v5, v4, v3, v2, v1, d.weno_eps);
+        Um[qq] = v2;
+        Up[qq] = v3;
+    }
+}
+
+// One thread per (chunk position, direction, face): box elements.
+__global__ void k_fd_flux(Dev d, const int* list, int ci, int w0) {
+    const int n = chunk_n(d, ci, w0);
+    const int64_t nfc = nface(d);
     const int64_t total = (int64_t)n * 3 * nfc;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(q / (3 * nfc));
+        const int wl = (int)(q / (3 * nfc));
         const int k = (int)((q / nfc) % 3);
         const int64_t fi = q % nfc;
-        const int m = (int)(fi % (nc + 1));
-        const int ta = (int)((fi / (nc + 1)) % nc), tb = (int)(fi / ((nc + 1) * nc));
-        int t1, t2;
-        axes_of(k, t1, t2);
-        // extended index of cell (m - 3 + o) along k, o = 0..5
-        int c[3];
-        c[k] = m;
-        c[t1] = ta + GH;
-        c[t2] = tb + GH;
-        const int64_t base = c[0] + (int64_t)ne * (c[1] + (int64_t)ne * c[2]);
-        const int64_t stride = k == 0 ? 1 : (k == 1 ? ne : (int64_t)ne * ne);
-        double UL[NQ], UR[NQ];
-        for (int qq = 0; qq < NQ; ++qq) {
-            const double* src = ext_at(d, qq, w) + base;
-            const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
-            const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
-            UL[qq] = weno5z(v0, v1, v2, v3, v4, d.weno_eps);
-            UR[qq] = weno5z(v5, v4, v3, v2, v1, d.weno_eps);
-        }
+        const int e = list[w0 + wl];
+        const int nc = esz(d, e).nc;
+        int m, ta, tb;
+        if (!face_coords(fi, nc, m, ta, tb)) continue;
+        double UL[NQ], UR[NQ], Um[NQ], Up[NQ];
+        reconstruct(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
         double FL[NV], FR[NV], Fs[NV];
         flux_dir_flat(UL, UL + NV, k, FL);
         flux_dir_flat(UR, UR + NV, k, FR);
         for (int v = 0; v < NV; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * (UR[v] - UL[v]);
         if (d.fd_corr) {
-            // cell-centred fluxes of the two cells sharing the face (ext cells m+2, m+3)
-            double Um[NQ], Up[NQ], Fm[NV], Fp[NV];
-            for (int qq = 0; qq < NQ; ++qq) {
-                const double* src = ext_at(d, qq, w) + base;
-                Um[qq] = src[2 * stride];
-                Up[qq] = src[3 * stride];
-            }
+            double Fm[NV], Fp[NV];
             flux_dir_flat(Um, Um + NV, k, Fm);
             flux_dir_flat(Up, Up + NV, k, Fp);
             for (int v = 0; v < NV; ++v) Fs[v] = Fs[v] - (1.0 / 6.0) * (Fm[v] - 2.0 * Fs[v] + Fp[v]);
         }
-        for (int v = 0; v < NV; ++v) flux_at(d, k, v, w)[fi] = Fs[v];
+        for (int v = 0; v < NV; ++v) flux_at(d, k, v, wl)[fi] = Fs[v];
     }
 }
 
@@ -283,42 +332,29 @@ __global__ void k_fd_flux(Dev d, const int* list, int ci) {
 // face, Rusanov dissipation along the unit face normal n^ (lambda = 1):
 //   F^j = (F^j(L) + F^j(R))/2 - n^_j (U_R - U_L)/2,
 // optional corrector per component.
-__global__ void k_fd_flux_curved(Dev d, const int* list, int ci) {
-    const int n = d.counts[ci];
-    const int nc = d.nc, ne = nc + 2 * GH;
-    const int64_t nfc = (int64_t)(nc + 1) * nc * nc;
+__global__ void k_fd_flux_curved(Dev d, const int* list, int ci, int w0) {
+    const int n = chunk_n(d, ci, w0);
+    const int64_t nfc = nface(d);
     const int64_t total = (int64_t)n * 3 * nfc;
-    const ShellGeo sg = shell_of(d);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(q / (3 * nfc));
+        const int wl = (int)(q / (3 * nfc));
         const int k = (int)((q / nfc) % 3);
         const int64_t fi = q % nfc;
-        const int m = (int)(fi % (nc + 1));
-        const int ta = (int)((fi / (nc + 1)) % nc), tb = (int)(fi / ((nc + 1) * nc));
-        const int e = list[w];
+        const int e = list[w0 + wl];
+        const int nc = esz(d, e).nc;
+        int m, ta, tb;
+        if (!face_coords(fi, nc, m, ta, tb)) continue;
         int t1, t2;
         axes_of(k, t1, t2);
-        int c[3];
-        c[k] = m;
-        c[t1] = ta + GH;
-        c[t2] = tb + GH;
-        const int64_t base = c[0] + (int64_t)ne * (c[1] + (int64_t)ne * c[2]);
-        const int64_t stride = k == 0 ? 1 : (k == 1 ? ne : (int64_t)ne * ne);
         double UL[NQ], UR[NQ], Um[NQ], Up[NQ];
-        for (int qq = 0; qq < NQ; ++qq) {
-            const double* src = ext_at(d, qq, w) + base;
-            const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
-            const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
-            UL[qq] = weno5z(v0, v1, v2, v3, v4, d.weno_eps);
-            UR[qq] = weno5z(v5, v4, v3, v2, v1, d.weno_eps);
-            Um[qq] = v2;
-            Up[qq] = v3;
-        }
+        reconstruct(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
         double xi[3], x[3], ij[3][3];
         xi[k] = -1.0 + m * 2.0 / nc;
         xi[t1] = -1.0 + (ta + 0.5) * 2.0 / nc;
         xi[t2] = -1.0 + (tb + 0.5) * 2.0 / nc;
-        shell_map(sg, e, xi, x, ij);
+        int el;
+        const ShellGeo sg = shell_for(d, e, el);
+        shell_map(sg, el, xi, x, ij);
         const double inrm = 1.0 / sqrt(ij[k][0] * ij[k][0] + ij[k][1] * ij[k][1] + ij[k][2] * ij[k][2]);
         for (int j = 0; j < 3; ++j) {
             double FL[NV], FR[NV], Fs[NV];
@@ -332,28 +368,37 @@ __global__ void k_fd_flux_curved(Dev d, const int* list, int ci) {
                 flux_dir_flat(Up, Up + NV, j, Fp);
                 for (int v = 0; v < NV; ++v) Fs[v] = Fs[v] - (1.0 / 6.0) * (Fm[v] - 2.0 * Fs[v] + Fp[v]);
             }
-            for (int v = 0; v < NV; ++v) flux_at_c(d, k, j, v, w)[fi] = Fs[v];
+            for (int v = 0; v < NV; ++v) flux_at_c(d, k, j, v, wl)[fi] = Fs[v];
         }
     }
 }
 
-template <int SUB>
-__global__ void k_fd_update_curved(Dev d, const int* list, int ci, SubArgs a) {
-    const int n = d.counts[ci];
-    const int nc = d.nc;
+// One thread per (chunk position, cell): flux difference + sources + stage.
+template <int SUB, bool CURVED>
+__global__ void k_fd_update(Dev d, const int* list, int ci, int w0, SubArgs a) {
+    const int n = chunk_n(d, ci, w0);
     const int64_t total = (int64_t)n * d.ncell;
-    const ShellGeo sg = shell_of(d);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(q / d.ncell), c = (int)(q % d.ncell);
-        const int e = list[w];
+        const int wl = (int)(q / d.ncell), c = (int)(q % d.ncell);
+        const int e = list[w0 + wl];
+        const ES es = esz(d, e);
+        if (c >= es.ncell) continue;
+        const int nc = es.nc;
         const int cc[3] = {c % nc, (c / nc) % nc, c / (nc * nc)};
-        const int64_t p = (int64_t)e * d.ncell + c;
-        double xi[3], x[3], ij[3][3];
-        for (int k = 0; k < 3; ++k) xi[k] = -1.0 + (cc[k] + 0.5) * 2.0 / nc;
-        shell_map(sg, e, xi, x, ij);
+        const int64_t p = fdb(d, e) + c;
+        double ij[3][3];
+        if (CURVED) {
+            double xi[3], x[3];
+            for (int k = 0; k < 3; ++k) xi[k] = -1.0 + (cc[k] + 0.5) * 2.0 / nc;
+            int el;
+            const ShellGeo sg = shell_for(d, e, el);
+            shell_map(sg, el, xi, x, ij);
+        }
         double du[NV], u0[NV];
         for (int v = 0; v < NV; ++v) u0[v] = a.Uin.fd(v)[p];
-        du[0] = -a.J.fd(0)[p]; du[1] = -a.J.fd(1)[p]; du[2] = -a.J.fd(2)[p];
+        du[0] = -a.J.fd(0)[p];
+        du[1] = -a.J.fd(1)[p];
+        du[2] = -a.J.fd(2)[p];
         du[3] = du[4] = du[5] = 0.0;
         du[6] = u0[8];
         du[7] = du[8] = 0.0;
@@ -361,10 +406,18 @@ __global__ void k_fd_update_curved(Dev d, const int* list, int ci, SubArgs a) {
             int t1, t2;
             axes_of(k, t1, t2);
             const int64_t f0 = cc[k] + (int64_t)(nc + 1) * (cc[t1] + nc * cc[t2]);
-            for (int j = 0; j < 3; ++j) {
-                const double sc = ij[k][j] * (0.5 * nc);
+            if (CURVED) {
+                for (int j = 0; j < 3; ++j) {
+                    const double sc = ij[k][j] * (0.5 * nc);
+                    for (int v = 0; v < NV; ++v) {
+                        const double* fl = flux_at_c(d, k, j, v, wl);
+                        du[v] = fma(-sc, fl[f0 + 1] - fl[f0], du[v]);
+                    }
+                }
+            } else {
+                const double sc = d.ijac[3 * e + k] * (0.5 * nc);
                 for (int v = 0; v < NV; ++v) {
-                    const double* fl = flux_at_c(d, k, j, v, w);
+                    const double* fl = flux_at(d, k, v, wl);
                     du[v] = fma(-sc, fl[f0 + 1] - fl[f0], du[v]);
                 }
             }
@@ -373,11 +426,11 @@ __global__ void k_fd_update_curved(Dev d, const int* list, int ci, SubArgs a) {
             for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
             continue;
         }
-        if (c == 0) atomicAdd(d.units, (unsigned long long)d.ncell);
+        if (c == 0) atomicAdd(d.units, (unsigned long long)es.ncell);
         if (SUB != SUB_C)
             for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
         double u[NV];
-        substep_combine(d, SUB, du, p, true, a, u);
+        substep_combine(d, SUB, du, p, true, a, dt_of(d, e), u);
         bool bad = false;
         for (int v = 0; v < NV; ++v) {
             a.Uout.fd(v)[p] = u[v];
@@ -392,126 +445,79 @@ __global__ void k_fd_update_curved(Dev d, const int* list, int ci, SubArgs a) {
     }
 }
 
-// One thread per (list position, cell): flux difference + sources + stage.
+int fd_chunks(const Dev& d) { return (d.fd_cap + d.chunk - 1) / d.chunk; }
+
 template <int SUB>
-__global__ void k_fd_update(Dev d, const int* list, int ci, SubArgs a, const double* ijac) {
-    const int n = d.counts[ci];
-    const int nc = d.nc;
-    const int64_t total = (int64_t)n * d.ncell;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(q / d.ncell), c = (int)(q % d.ncell);
-        const int e = list[w];
-        const int cc[3] = {c % nc, (c / nc) % nc, c / (nc * nc)};
-        const int64_t p = (int64_t)e * d.ncell + c;
-        double du[NV];
-        double u0[NV];
-        for (int v = 0; v < NV; ++v) u0[v] = a.Uin.fd(v)[p];
-        du[0] = -a.J.fd(0)[p]; du[1] = -a.J.fd(1)[p]; du[2] = -a.J.fd(2)[p];
-        du[3] = du[4] = du[5] = 0.0;
-        du[6] = u0[8];
-        du[7] = du[8] = 0.0;
-        for (int k = 0; k < 3; ++k) {
-            int t1, t2;
-            axes_of(k, t1, t2);
-            const int64_t f0 = cc[k] + (int64_t)(nc + 1) * (cc[t1] + nc * cc[t2]);
-            const double sc = ijac[3 * e + k] * (0.5 * nc);
-            for (int v = 0; v < NV; ++v) {
-                const double* fl = flux_at(d, k, v, w);
-                du[v] = fma(-sc, fl[f0 + 1] - fl[f0], du[v]);
-            }
-        }
-        if (SUB == SUB_RHS) {
-            for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
-            continue;
-        }
-        if (c == 0) atomicAdd(d.units, (unsigned long long)d.ncell);
-        if (SUB != SUB_C)
-            for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
-        double u[NV];
-        substep_combine(d, SUB, du, p, true, a, u);
-        bool bad = false;
-        for (int v = 0; v < NV; ++v) {
-            a.Uout.fd(v)[p] = u[v];
-            bad |= !isfinite(u[v]);
-        }
-        if (bad) atomic_status(d, 1);
-        if (SUB != SUB_C) {
-            double g[NG];
-            implicit_G_flat(u, d, g);
-            for (int cg = 0; cg < NG; ++cg) a.Gout.fd(cg)[p] = g[cg];
-        }
-    }
+static void launch_update(const Dev& d, const int* list, int ci, int w0, const SubArgs& a, cudaStream_t st) {
+    if (d.curved) k_fd_update<SUB, true><<<152 * 8, 256, 0, st>>>(d, list, ci, w0, a);
+    else k_fd_update<SUB, false><<<152 * 8, 256, 0, st>>>(d, list, ci, w0, a);
 }
 
-void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin, Field J, Field un,
-                       Field F2, Field F3, Field G1, Field G2, Field G3, Field G4, Field Fout, Field Uout,
-                       Field Gout, cudaStream_t st) {
+void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin, Field J, Field un, Field F2,
+                       Field F3, Field G1, Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout,
+                       cudaStream_t st) {
     SubArgs a{Uin, J, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
     const int grid = 152 * 8;
-    prof_begin("fd_fill_interior", st);
-    k_fd_fill_interior<<<grid, 256, 0, st>>>(d, list, ci, Uin, J);
-    prof_end(st);
     const int np1 = d.np1, nn = d.nn, nc = d.nc;
     const size_t smem = (size_t)(NV * nn + NV * GH * np1 * np1 + NV * GH * nc * np1) * sizeof(double);
     cudaFuncSetAttribute(k_fd_fill_ghosts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    prof_begin("fd_fill_ghosts", st);
-    k_fd_fill_ghosts<<<152 * 2, 256, smem, st>>>(d, list, ci, Uin, J);
-    prof_end(st);
-    prof_begin("fd_flux", st);
-    if (d.curved) k_fd_flux_curved<<<grid, 128, 0, st>>>(d, list, ci);
-    else k_fd_flux<<<grid, 128, 0, st>>>(d, list, ci);
-    prof_end(st);
-    prof_begin("fd_update", st);
-    if (d.curved) {
+    for (int k = 0, nch = fd_chunks(d); k < nch; ++k) {
+        const int w0 = k * d.chunk;
+        prof_begin("fd_fill_interior", st);
+        k_fd_fill_interior<<<grid, 256, 0, st>>>(d, list, ci, w0, Uin, J);
+        prof_end(st);
+        prof_begin("fd_fill_ghosts", st);
+        k_fd_fill_ghosts<<<152 * 2, 256, smem, st>>>(d, list, ci, w0, Uin, J);
+        prof_end(st);
+        prof_begin("fd_flux", st);
+        if (d.curved) k_fd_flux_curved<<<grid, 128, 0, st>>>(d, list, ci, w0);
+        else k_fd_flux<<<grid, 128, 0, st>>>(d, list, ci, w0);
+        prof_end(st);
+        prof_begin("fd_update", st);
         switch (sub) {
-            case SUB_A: k_fd_update_curved<SUB_A><<<grid, 256, 0, st>>>(d, list, ci, a); break;
-            case SUB_B: k_fd_update_curved<SUB_B><<<grid, 256, 0, st>>>(d, list, ci, a); break;
-            case SUB_C: k_fd_update_curved<SUB_C><<<grid, 256, 0, st>>>(d, list, ci, a); break;
-            default: k_fd_update_curved<SUB_RHS><<<grid, 256, 0, st>>>(d, list, ci, a); break;
+            case SUB_A: launch_update<SUB_A>(d, list, ci, w0, a, st); break;
+            case SUB_B: launch_update<SUB_B>(d, list, ci, w0, a, st); break;
+            case SUB_C: launch_update<SUB_C>(d, list, ci, w0, a, st); break;
+            default: launch_update<SUB_RHS>(d, list, ci, w0, a, st); break;
         }
-    } else {
-        switch (sub) {
-            case SUB_A: k_fd_update<SUB_A><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
-            case SUB_B: k_fd_update<SUB_B><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
-            case SUB_C: k_fd_update<SUB_C><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
-            default: k_fd_update<SUB_RHS><<<grid, 256, 0, st>>>(d, list, ci, a, d.ijac); break;
-        }
+        prof_end(st);
+        g_launch_counter += 4;
     }
-    prof_end(st);
-    g_launch_counter += 4;
 }
 
 // ---------------------------------------------------------------------------
 // DG -> FD projection (tensor Lagrange evaluation at subcell centres) of `nv`
-// variables of the flagged elements, in place from the DG block to the FD block.
+// variables of element e, from its DG slot to its FD slot.
 __device__ void project_dg2fd_element(const Dev& d, const Field& F, int nv, int e, double* sm) {
-    const Tables& T = *d.tab;
-    const int np1 = d.np1, nn = d.nn, nc = d.nc;
+    const ES es = esz(d, e);
+    const Tables& T = d.tabs[es.P];
+    const int np1 = es.np1, nn = es.nn, nc = es.nc;
+    const int64_t fb = fdb(d, e);
     double* a = sm;                     // [np1^3]
-    double* b = a + nn;                 // [nc][np1][np1]
-    double* c = b + nc * np1 * np1;     // [nc][nc][np1]
+    double* b = a + nn;                 // [np1][np1][nc]
+    double* c = b + nc * np1 * np1;     // [np1][nc][nc]
     for (int v = 0; v < nv; ++v) {
-        for (int t = threadIdx.x; t < nn; t += blockDim.x) a[t] = F.dg(v)[(int64_t)e * nn + t];
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) a[t] = F.dg(v)[(int64_t)e * d.nn + t];
         __syncthreads();
         for (int t = threadIdx.x; t < nc * np1 * np1; t += blockDim.x) {
             const int x = t % nc, jk = t / nc;
             double acc = 0.0;
             for (int m = 0; m < np1; ++m) acc = fma(T.P2F[x][m], a[m + np1 * jk], acc);
-            b[t] = acc;   // [k][j][x]
+            b[t] = acc;
         }
         __syncthreads();
         for (int t = threadIdx.x; t < nc * nc * np1; t += blockDim.x) {
             const int x = t % nc, y = (t / nc) % nc, k = t / (nc * nc);
             double acc = 0.0;
             for (int m = 0; m < np1; ++m) acc = fma(T.P2F[y][m], b[x + nc * (m + np1 * k)], acc);
-            c[t] = acc;   // [k][y][x]
+            c[t] = acc;
         }
         __syncthreads();
         for (int t = threadIdx.x; t < nc * nc * nc; t += blockDim.x) {
             const int xy = t % (nc * nc), z = t / (nc * nc);
             double acc = 0.0;
             for (int m = 0; m < np1; ++m) acc = fma(T.P2F[z][m], c[xy + nc * nc * m], acc);
-            F.fd(v)[(int64_t)e * d.ncell + t] = acc;
+            F.fd(v)[fb + t] = acc;
         }
         __syncthreads();
     }
@@ -523,22 +529,45 @@ struct RollArgs {
     int nf;
 };
 
+// Flagged elements: take an FD slot (slot pool), project the substep inputs, mark FD.
 __global__ void k_rollback_project(Dev d, RollArgs r) {
     extern __shared__ double sm[];
+    __shared__ int s_ok;
     const int n = d.counts[2];
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int e = d.flag_list[w];
-        for (int i = 0; i < r.nf; ++i) project_dg2fd_element(d, r.f[i], r.nv[i], e, sm);
-        if (threadIdx.x == 0) d.mask[e] = 1;
+        if (threadIdx.x == 0) {
+            s_ok = 1;
+            if (d.fd_slot && d.fd_slot[e] < 0) {
+                const int top = atomicSub(&d.counts[5], 1) - 1;
+                if (top < 0) {
+                    s_ok = 0;   // pool exhausted: reported through the status word
+                    atomicOr(&d.counts[4], 4);
+                } else {
+                    const int sl = d.free_slots[top];
+                    d.fd_slot[e] = sl;
+                    d.slot_elem[sl] = e;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_ok) {
+            for (int i = 0; i < r.nf; ++i) project_dg2fd_element(d, r.f[i], r.nv[i], e, sm);
+            if (threadIdx.x == 0) d.mask[e] = 1;
+        }
         __syncthreads();
     }
 }
 
-void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F2, Field F3, Field G1,
-                             Field G2, Field G3, Field G4, cudaStream_t st) {
+void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F2, Field F3, Field G1, Field G2,
+                             Field G3, Field G4, cudaStream_t st) {
     RollArgs r{};
     int k = 0;
-    auto add = [&](Field f, int nv) { r.f[k] = f; r.nv[k] = nv; ++k; };
+    auto add = [&](Field f, int nv) {
+        r.f[k] = f;
+        r.nv[k] = nv;
+        ++k;
+    };
     add(un, NV);
     add(Uin, NV);
     if (sub == SUB_A) { add(G1, NG); add(G2, NG); }
@@ -554,11 +583,10 @@ void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F
 }
 
 // ---------------------------------------------------------------------------
-// FD -> DG (6-point Lagrange per direction) of variable block `src` (one
-// element, [nc^3]) into dst [np1^3], sum-factorised through shared memory.
-__device__ void project_fd2dg_var(const Dev& d, const double* src, double* dst, double* sm) {
-    const Tables& T = *d.tab;
-    const int np1 = d.np1, nc = d.nc, ncell = d.ncell;
+// FD -> DG (6-point Lagrange per direction) of one variable block src
+// ([nc^3]) into dst ([np1^3]), sum-factorised through shared memory.
+__device__ void project_fd2dg_var(const ES& es, const Tables& T, const double* src, double* dst, double* sm) {
+    const int np1 = es.np1, nc = es.nc, ncell = es.ncell;
     double* a = sm;                    // [nc^3]
     double* b = a + ncell;             // [nc][nc][np1]
     double* c = b + nc * nc * np1;     // [nc][np1][np1]
@@ -569,7 +597,7 @@ __device__ void project_fd2dg_var(const Dev& d, const double* src, double* dst, 
         const int lo = T.f2d_lo[i];
         double acc = 0.0;
         for (int m = 0; m < 6; ++m) acc = fma(T.F2D[i][lo + m], a[lo + m + nc * yz], acc);
-        b[t] = acc;   // [z][y][i]
+        b[t] = acc;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nc * np1 * np1; t += blockDim.x) {
@@ -577,7 +605,7 @@ __device__ void project_fd2dg_var(const Dev& d, const double* src, double* dst, 
         const int lo = T.f2d_lo[j];
         double acc = 0.0;
         for (int m = 0; m < 6; ++m) acc = fma(T.F2D[j][lo + m], b[i + np1 * ((lo + m) + nc * z)], acc);
-        c[t] = acc;   // [z][j][i]
+        c[t] = acc;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < np1 * np1 * np1; t += blockDim.x) {
@@ -591,20 +619,23 @@ __device__ void project_fd2dg_var(const Dev& d, const double* src, double* dst, 
 }
 
 // End of step: FD elements that did not switch during the step return to DG
-// when the indicator with alpha' = alpha + 1 finds their FD->DG projection admissible.
+// when the indicator with alpha' = alpha + 1 finds their FD->DG projection
+// admissible; their FD slot returns to the pool.
 __global__ void k_fd2dg(Dev d, Field un) {
     extern __shared__ double sm[];
-    const Tables& T = *d.tab;
-    const int np1 = d.np1, nn = d.nn, nc = d.nc, ncell = d.ncell;
-    double* work = sm;                                      // projection scratch
-    double* proj = work + ncell + nc * nc * np1 + nc * np1 * np1;  // [9][nn]
-    double* tmp = proj + NV * nn;                           // [3][nn]
     __shared__ double red[2];
     const int n = d.counts[1];
     for (int w = blockIdx.x; w < n; w += gridDim.x) {
         const int e = d.fd_list[w];
         if (d.switched[e]) continue;
-        for (int v = 3; v < 6; ++v) project_fd2dg_var(d, un.fd(v) + (int64_t)e * ncell, proj + v * nn, work);
+        const ES es = esz(d, e);
+        const Tables& T = d.tabs[es.P];
+        const int np1 = es.np1, nn = es.nn;
+        double* work = sm;                                                            // projection scratch
+        double* proj = work + d.ncell + d.nc * d.nc * d.np1 + d.nc * d.np1 * d.np1;   // [9][nn]
+        double* tmp = proj + NV * d.nn;                                               // [3][nn]
+        const int64_t fb = fdb(d, e);
+        for (int v = 3; v < 6; ++v) project_fd2dg_var(es, T, un.fd(v) + fb, proj + v * nn, work);
         for (int t = threadIdx.x; t < nn; t += blockDim.x) {
             const double bx = proj[3 * nn + t], by = proj[4 * nn + t], bz = proj[5 * nn + t];
             tmp[t] = sqrt(fma(bz, bz, fma(by, by, bx * bx)));
@@ -634,20 +665,27 @@ __global__ void k_fd2dg(Dev d, Field un) {
                 num += uh * uh;
                 den += tmp[t] * tmp[t];
             }
+            const double thr = d.thr_fdP[es.P];
             const double ratio = den > 0.0 ? sqrt(num / den) : 0.0;
-            if (fabs(ratio - d.thr_fd) <= 1e-12 * d.thr_fd) d.near_list[atomicAdd(&d.counts[3], 1) & 4095] = e;
-            red[0] = ratio > d.thr_fd ? 1.0 : 0.0;
+            if (fabs(ratio - thr) <= 1e-12 * thr) d.near_list[atomicAdd(&d.counts[3], 1) & 4095] = e;
+            red[0] = ratio > thr ? 1.0 : 0.0;
         }
         __syncthreads();
         const bool stay = red[0] != 0.0;
         __syncthreads();
         if (stay) continue;
-        for (int v = 0; v < NV; ++v) {
-            if (v < 3 || v > 5) project_fd2dg_var(d, un.fd(v) + (int64_t)e * ncell, proj + v * nn, work);
+        for (int v = 0; v < NV; ++v)
+            if (v < 3 || v > 5) project_fd2dg_var(es, T, un.fd(v) + fb, proj + v * nn, work);
+        for (int t = threadIdx.x; t < NV * nn; t += blockDim.x) un.dg(t / nn)[(int64_t)e * d.nn + t % nn] = proj[t];
+        if (threadIdx.x == 0) {
+            d.mask[e] = 0;
+            if (d.fd_slot) {
+                const int sl = d.fd_slot[e];
+                d.fd_slot[e] = -1;
+                d.slot_elem[sl] = -1;
+                d.free_slots[atomicAdd(&d.counts[5], 1)] = sl;
+            }
         }
-        for (int t = threadIdx.x; t < NV * nn; t += blockDim.x)
-            un.dg(t / nn)[(int64_t)e * nn + t % nn] = proj[t];
-        if (threadIdx.x == 0) d.mask[e] = 0;
         __syncthreads();
     }
 }

@@ -17,8 +17,7 @@ __device__ __forceinline__ void atomic_status(const Dev& d, int bits) { atomicOr
 //   SUB_C: u_{n+1} = u_n + dt ((F2 + F3)/6 + 2 F4/3 + (G2 + G3)/6 + 2 G4/3)
 // followed by the algebraic clamp when the constraint mode asks for it.
 __device__ __forceinline__ void substep_combine(const Dev& d, int sub, const double* f, int64_t p, bool isfd,
-                                                const SubArgs& a, double* u) {
-    const double dt = d.dt;
+                                                const SubArgs& a, double dt, double* u) {
     auto ld = [&](const Field& F, int v) { return isfd ? F.fd(v)[p] : F.dg(v)[p]; };
     const int gv[NG] = {0, 1, 2, 6, 7};
     for (int v = 0; v < NV; ++v) u[v] = ld(a.un, v);
@@ -40,6 +39,27 @@ __device__ __forceinline__ void substep_combine(const Dev& d, int sub, const dou
         if (!stiff_solve_flat(u, d, dt * IM_A)) atomic_status(d, 2);
     }
     if (d.mode != FFE_RELAX) hard_clamp_flat(u);
+}
+
+// A DG element the indicator flags needs an FD slot.  Contexts with a slot
+// pool take one from the free stack; when the pool is empty the element stays
+// on DG and status bit 2 (value 4) is raised.  Called by one thread.
+__device__ __forceinline__ bool take_fd_slot(const Dev& d, int e) {
+    if (!d.fd_slot || d.fd_slot[e] >= 0) return true;
+    int old = d.counts[5];
+    while (old > 0) {
+        const int prev = atomicCAS(&d.counts[5], old, old - 1);
+        if (prev == old) break;
+        old = prev;
+    }
+    if (old <= 0) {
+        atomic_status(d, 4);
+        return false;
+    }
+    const int sl = d.free_slots[old - 1];
+    d.fd_slot[e] = sl;
+    d.slot_elem[sl] = e;
+    return true;
 }
 
 }  // namespace ffe

@@ -24,7 +24,8 @@ STATUS = {0: "FFE_OK", 1: "FFE_EINVAL", 2: "FFE_ENOMEM", 3: "FFE_ECUDA", 4: "FFE
 EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_state", "ffe_set_state",
            "ffe_download", "ffe_upload", "ffe_get_info", "ffe_get_status", "ffe_tci_ratio",
            "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
-           "ffe_fd_rhs_noalloc", "ffe_last_error", "ffe_destroy"]
+           "ffe_fd_rhs_noalloc", "ffe_create_batch", "ffe_get_layout", "ffe_set_initial_batch",
+           "ffe_last_error", "ffe_destroy"]
 
 
 class Domain(ctypes.Structure):
@@ -88,6 +89,11 @@ def load():
         "ffe_set_profiling": [P, i],
         "ffe_profile_read": [P, ctypes.c_char_p, ctypes.c_size_t],
         "ffe_fd_rhs_noalloc": [i, i, ctypes.POINTER(d), d, d, i, P, P, P],
+        "ffe_create_batch": [i, ctypes.POINTER(Domain), ctypes.POINTER(Elements), ctypes.POINTER(i),
+                             ctypes.POINTER(Metric), ctypes.POINTER(Params), i, P, ctypes.POINTER(P)],
+        "ffe_get_layout": [P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                           ctypes.POINTER(i)],
+        "ffe_set_initial_batch": [P, i, ctypes.POINTER(d), i, i],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -137,6 +143,24 @@ class _DevArray:
         self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3}
 
 
+def domain_of(cfg):
+    dom = Domain()
+    el = Elements()
+    if cfg["kind"] == "box":
+        dom.kind = 0
+        for a in range(3):
+            dom.lo[a], dom.hi[a] = cfg["lo"][a], cfg["hi"][a]
+            dom.bc_lo[a] = dom.bc_hi[a] = BC[cfg["bc"][a]]
+            el.n[a] = cfg["n"][a]
+    else:
+        dom.kind = 1
+        dom.r_in, dom.r_out = cfg["r_in"], cfg["r_out"]
+        dom.bc_lo[0], dom.bc_hi[0] = BC[cfg["bc_inner"]], BC[cfg["bc_outer"]]
+        el.n[0] = el.n[1] = cfg["n_ang"]
+        el.n[2] = cfg["n_rad"]
+    return dom, el
+
+
 class Context:
     """One GRFFE problem on the current CUDA device."""
 
@@ -144,20 +168,7 @@ class Context:
         import torch
         lib = load()
         self.cfg = cfg
-        dom = Domain()
-        el = Elements()
-        if cfg["kind"] == "box":
-            dom.kind = 0
-            for a in range(3):
-                dom.lo[a], dom.hi[a] = cfg["lo"][a], cfg["hi"][a]
-                dom.bc_lo[a] = dom.bc_hi[a] = BC[cfg["bc"][a]]
-                el.n[a] = cfg["n"][a]
-        else:
-            dom.kind = 1
-            dom.r_in, dom.r_out = cfg["r_in"], cfg["r_out"]
-            dom.bc_lo[0], dom.bc_hi[0] = BC[cfg["bc_inner"]], BC[cfg["bc_outer"]]
-            el.n[0] = el.n[1] = cfg["n_ang"]
-            el.n[2] = cfg["n_rad"]
+        dom, el = domain_of(cfg)
         mk, M, spin = cfg["metric"]
         met = Metric(METRIC[mk], M, spin)
         prm = params_from(cfg["params"])
@@ -266,3 +277,64 @@ class Context:
 
     def join(self, udg, ufd):
         return np.concatenate([np.ascontiguousarray(udg).reshape(-1), np.ascontiguousarray(ufd).reshape(-1)])
+
+    def layout(self):
+        """(elem_P, fd_slot, elem_inst, inst_first) as numpy arrays."""
+        E = self.n_elem
+        eP, sl, ei = (ctypes.c_int * E)(), (ctypes.c_int * E)(), (ctypes.c_int * E)()
+        n = ctypes.c_int()
+        check(load().ffe_get_layout(self.h, eP, sl, ei, None, ctypes.byref(n)))
+        first = (ctypes.c_int * (n.value + 1))()
+        check(load().ffe_get_layout(self.h, None, None, None, first, None))
+        return np.array(eP), np.array(sl), np.array(ei), np.array(first)
+
+
+class BatchContext(Context):
+    """Many independent flat-space shells advanced together (ffe_create_batch)."""
+
+    def __init__(self, cfgs, fd_capacity=0, stream=None):
+        import torch
+        lib = load()
+        self.cfgs = cfgs
+        self.cfg = cfgs[0]
+        n = len(cfgs)
+        doms, els = (Domain * n)(), (Elements * n)()
+        prms = (Params * n)()
+        Ps = (ctypes.c_int * n)(*[c["P"] for c in cfgs])
+        for i, c in enumerate(cfgs):
+            doms[i], els[i] = domain_of(c)
+            prms[i] = params_from(c["params"])
+        mk, M, spin = cfgs[0]["metric"]
+        met = Metric(METRIC[mk], M, spin)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib.ffe_create_batch(n, doms, els, Ps, ctypes.byref(met), prms, int(fd_capacity),
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        self.info()
+
+    def set_initial(self, kind=None, params=()):
+        kind = self.cfgs[0]["initial"][0]
+        blocks = [tuple(c["initial"][1].values()) for c in self.cfgs]
+        k = len(blocks[0])
+        flat = [v for b in blocks for v in b]
+        arr = (ctypes.c_double * max(len(flat), 1))(*flat)
+        check(load().ffe_set_initial_batch(self.h, ID[kind], arr, k, 0))
+
+    def split_instance(self, U, i):
+        """(udg, ufd, mask) of instance i from a state vector and the current layout;
+        FD blocks of elements without an FD slot are zero."""
+        eP, sl, ei, first = self.layout()
+        E = self.n_elem
+        Pm = self.P
+        nns, ncs = (Pm + 1) ** 3, (2 * Pm + 1) ** 3
+        dg = np.asarray(U)[:NV * self.n_dg].reshape(NV, E, nns)
+        cap = self.n_fd // ncs
+        fd = np.asarray(U)[NV * self.n_dg:].reshape(NV, cap, ncs)
+        P = self.cfgs[i]["P"]
+        np1, nc = P + 1, 2 * P + 1
+        es = range(first[i], first[i + 1])
+        udg = np.stack([dg[:, e, :np1 ** 3].reshape(NV, np1, np1, np1) for e in es], axis=1)
+        ufd = np.stack([fd[:, sl[e], :nc ** 3].reshape(NV, nc, nc, nc) if sl[e] >= 0 else np.zeros((NV, nc, nc, nc))
+                        for e in es], axis=1)
+        return udg, ufd

@@ -1,0 +1,79 @@
+"""Batched contexts (many shells, mixed orders, one launch per kernel and
+substep) against one context per instance and against the oracle."""
+import numpy as np
+import pytest
+
+import ffe_workloads as W
+from gpu_common import rel_err_split
+from oracle.problem import Problem
+from oracle.stepper import Stepper
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CFGS = [W.pulsar(r_lc=3.0, chi=0.4, n_ang=1, n_rad=4, P=5, r_out=4.0),
+        W.pulsar(r_lc=3.0, chi=0.4, n_ang=2, n_rad=8, P=4, r_out=8.0),
+        W.pulsar(r_lc=3.5, chi=0.2, n_ang=1, n_rad=6, P=4, r_out=6.0)]
+
+
+@pytest.fixture(scope="module")
+def ffe():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2404_01531_gb300 import ffe
+    ffe.load()
+    return ffe
+
+
+def _instance_mask(ctx, i, mask):
+    _, _, _, first = ctx.layout()
+    return mask[first[i]:first[i + 1]]
+
+
+def test_batch_matches_single_contexts_and_oracle(ffe):
+    nsteps = 3
+    b = ffe.BatchContext(CFGS)
+    b.set_initial()
+    b.step(nsteps)
+    Ub, mb = b.download()
+    assert b.status() == 0
+    for i, cfg in enumerate(CFGS):
+        udg_b, ufd_b = b.split_instance(Ub, i)
+        m_b = _instance_mask(b, i, mb)
+        s = ffe.Context(cfg)
+        s.set_initial()
+        s.step(nsteps)
+        Us, ms = s.download()
+        dgs, fds = s.split(Us)
+        assert np.array_equal(ms, m_b)
+        # same kernels, same arithmetic: agreement to rounding
+        assert rel_err_split(udg_b, dgs, ufd_b, fds, ms == 0).max() <= 1e-13
+        s.close()
+        pr = Problem(cfg)
+        st = pr.initial_state()
+        S = Stepper(pr)
+        near = set()
+        for _ in range(nsteps):
+            st = S.step(st)
+            near |= set(S.near)
+        assert set(np.nonzero(m_b != st["mask"])[0].tolist()) <= near
+        assert 0 < m_b.sum() < len(m_b) or i == 2
+        assert rel_err_split(udg_b, st["udg"], ufd_b, st["ufd"], st["mask"] == 0).max() <= 1e-8
+    b.close()
+
+
+def test_batch_fd_capacity_too_small_is_reported(ffe):
+    b = ffe.BatchContext(CFGS, fd_capacity=4)
+    with pytest.raises(ffe.FFEError, match="FFE_ENOMEM"):
+        b.set_initial()
+    b.close()
+
+
+def test_batch_layout(ffe):
+    b = ffe.BatchContext(CFGS)
+    eP, sl, ei, first = b.layout()
+    sizes = [6 * c["n_ang"] ** 2 * c["n_rad"] for c in CFGS]
+    assert list(first) == list(np.cumsum([0] + sizes))
+    for i, c in enumerate(CFGS):
+        assert np.all(eP[first[i]:first[i + 1]] == c["P"]) and np.all(ei[first[i]:first[i + 1]] == i)
+    b.close()
