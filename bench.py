@@ -144,6 +144,62 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_pulsars(args):
+    """Batched shells: one launch per kernel and substep for every instance,
+    against the same instances advanced one context at a time."""
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfgs = W.pulsars(n_inst=args.n_inst)
+    E = sum(6 * c["n_ang"] ** 2 * c["n_rad"] for c in cfgs)
+    b = ffe.BatchContext(cfgs, fd_capacity=int(args.fd_capacity * E))
+    b.set_initial()
+    b.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    u0 = b.info().node_updates
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.step(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    inf = b.info()
+    units_b = inf.node_updates - u0
+    fd_end = inf.n_fd_elem
+    status = b.status()
+    b.set_profiling(True)
+    b.step(2)
+    b.set_profiling(False)
+    prof = b.profile_read()
+    b.close()
+    # one context per instance, same steps, timed one after the other
+    ms_s, units_s = 0.0, 0
+    for c in cfgs:
+        s = ffe.Context(c)
+        s.set_initial()
+        s.step(max(args.warmup, 3))
+        torch.cuda.synchronize()
+        u0 = s.info().node_updates
+        e0.record(st)
+        s.step(args.steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_s += e0.elapsed_time(e1)
+        units_s += s.info().node_updates - u0
+        s.close()
+    vb, vs = units_b / (ms_b / 1e3), units_s / (ms_s / 1e3)
+    line = {"metric": METRIC, "value": vb, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"pulsars: {len(cfgs)} rotating-dipole shells (seed 1531), P in {{4,5}}",
+                       "elements": E, "fd_elements_end": fd_end, "fd_capacity": int(args.fd_capacity * E)},
+            "one_instance_per_launch": {"value": vs, "ms_per_step": ms_s / args.steps},
+            "batched_over_single": vb / vs, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
+            "status_bits": status}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -153,9 +209,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64,
                     help="elements along x (same width 4/64; smaller values for profiler captures)")
+    ap.add_argument("--workload", default="breakdown", choices=["breakdown", "pulsars"],
+                    help="pulsars: the 32-shell batch, batched launch vs one context per instance")
+    ap.add_argument("--n-inst", type=int, default=32)
+    ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "pulsars":
+        return run_pulsars(args)
 
     import numpy as np
     import torch

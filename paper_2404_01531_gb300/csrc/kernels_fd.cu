@@ -655,16 +655,24 @@ __global__ void k_fd2dg(Dev d, Field un) {
             tmp[2 * nn + t] = acc;
         }
         __syncthreads();
+        // third low-pass direction and the two sums: per-thread partial sums in a
+        // fixed order, combined by thread 0 in thread order (deterministic)
+        double pn = 0.0, pd = 0.0;
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+            const int i = t % np1, j = (t / np1) % np1;
+            double acc = 0.0;
+            for (int m = 0; m < np1; ++m) acc = fma(T.Pi[t / (np1 * np1)][m], tmp[2 * nn + i + np1 * (j + np1 * m)], acc);
+            const double uh = tmp[t] - acc;
+            pn = fma(uh, uh, pn);
+            pd = fma(tmp[t], tmp[t], pd);
+        }
+        double* part = tmp + 3 * nn;   // [2][blockDim]
+        part[threadIdx.x] = pn;
+        part[blockDim.x + threadIdx.x] = pd;
+        __syncthreads();
         if (threadIdx.x == 0) {
             double num = 0.0, den = 0.0;
-            for (int t = 0; t < nn; ++t) {
-                const int i = t % np1, j = (t / np1) % np1;
-                double acc = 0.0;
-                for (int m = 0; m < np1; ++m) acc = fma(T.Pi[t / (np1 * np1)][m], tmp[2 * nn + i + np1 * (j + np1 * m)], acc);
-                const double uh = tmp[t] - acc;
-                num += uh * uh;
-                den += tmp[t] * tmp[t];
-            }
+            for (int t = 0; t < (int)blockDim.x; ++t) { num += part[t]; den += part[blockDim.x + t]; }
             const double thr = d.thr_fdP[es.P];
             const double ratio = den > 0.0 ? sqrt(num / den) : 0.0;
             if (fabs(ratio - thr) <= 1e-12 * thr) d.near_list[atomicAdd(&d.counts[3], 1) & 4095] = e;
@@ -692,7 +700,7 @@ __global__ void k_fd2dg(Dev d, Field un) {
 
 void launch_fd2dg(const Dev& d, Field un, cudaStream_t st) {
     const int np1 = d.np1, nn = d.nn, nc = d.nc;
-    const size_t smem = (size_t)(d.ncell + nc * nc * np1 + nc * np1 * np1 + NV * nn + 3 * nn) * sizeof(double);
+    const size_t smem = (size_t)(d.ncell + nc * nc * np1 + nc * np1 * np1 + NV * nn + 3 * nn + 2 * 256) * sizeof(double);
     cudaFuncSetAttribute(k_fd2dg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin("fd2dg", st);
     k_fd2dg<<<152, 256, smem, st>>>(d, un);

@@ -127,16 +127,20 @@ __device__ __forceinline__ bool stiff_solve_flat(double* U, const Dev& d, double
         return true;
     }
     double p2 = dot3(pe, pe), a2 = dot3(pa, pa);
-    double s = 0.0;
-    bool ok = false;
-    for (int it = 0; it < 200; ++it) {
+    // Newton from s = 0 increases monotonically to the root (g decreasing and
+    // convex); stop once a step is at the rounding level of s.
+    double s = 0.0, step = 1.0;
+    for (int it = 0; it < 100; ++it) {
         double u = 1.0 / (1.0 + s), v = 1.0 / (1.0 + c + s);
         double g = c * ((p2 * u * u + a2 * v * v) - B2) * ib2 - s;
         double dg = -2.0 * c * (p2 * u * u * u + a2 * v * v * v) * ib2 - 1.0;
         double sn = s - g / dg;
-        if (!(sn > s) || sn - s <= 1e-16 * sn) { s = sn > s ? sn : s; ok = true; break; }
+        step = sn - s;
+        if (!(sn > s)) break;
         s = sn;
+        if (step <= 4e-16 * s) break;
     }
+    const bool ok = step <= 1e-12 * (s > 1.0 ? s : 1.0);
     double u = 1.0 / (1.0 + s), v = 1.0 / (1.0 + c + s);
     E[0] = fma(pe[0], u, pa[0] * v);
     E[1] = fma(pe[1], u, pa[1] * v);
