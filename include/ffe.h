@@ -222,6 +222,37 @@ ffe_status ffe_profile_read(ffe_ctx* ctx, char* buf, size_t cap);
 ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host, double eta, double weno_eps,
                               int fd_corrector, const double* Uext_dev, double* dUdt_dev, void* cuda_stream);
 
+/* ---- adjoint (reverse mode) ------------------------------------------------
+ * Hand-written vector-Jacobian products of the DG path with every branch
+ * frozen as the forward pass took it (piecewise differentiability): the mask
+ * must be all DG (FD subcells are not differentiated in this version;
+ * FFE_ENOTIMPL otherwise), the rectifier max(E^2-B^2,0), the stiff-solve
+ * branch and the sign of S.n at a no-incoming-Poynting face stay as they are at
+ * the linearisation point.  Flat-metric shells (FFE_DOMAIN_SHELL6) only.
+ * All buffers are device state vectors (DG block used). */
+
+/* out_dev = lambda^T dF/dU at U_dev (F the explicit right-hand side of ffe_rhs);
+ * *omega_bar (host, may be NULL) += lambda^T dF/dOmega (star rotation). */
+ffe_status ffe_rhs_vjp(ffe_ctx* ctx, const double* U_dev, const double* lam_dev, double* out_dev, double* omega_bar);
+
+/* One IMEX step backward: given the step's input state U_n (U_dev) and
+ * lambda_{n+1} = dL/du_{n+1}, writes lambda_n = dL/du_n (lam_out_dev, may alias
+ * nothing else) and adds the step's d L/d Omega to *omega_bar (may be NULL).  The
+ * step's internal stages are recomputed from U_n (checkpointed recomputation). */
+ffe_status ffe_adjoint_step(ffe_ctx* ctx, const double* U_dev, const double* lam_in_dev, double* lam_out_dev,
+                            double* omega_bar);
+
+/* Spin-down luminosity through the sphere r = r_L (Sec. IV.C.2): L = closed
+ * integral of (E x B).r^ dA on the radial element layer containing r_L (xi^3
+ * interpolation, LGL quadrature, exact area element).  *L_host receives L;
+ * when grad_dev is not NULL, scale * dL/dU is added to it. */
+ffe_status ffe_luminosity(ffe_ctx* ctx, const double* U_dev, double r_L, double* L_host, double* grad_dev,
+                          double scale);
+
+/* Derivative of the initial DG state set by ffe_set_initial with respect to its
+ * parameter `which` (DIPOLE: 0 = mu, 2 = chi) at the nodes, into dU_dev. */
+ffe_status ffe_initial_tangent(ffe_ctx* ctx, int which, double* dU_dev);
+
 /* Thread-local message of the last failed call ("" if none). */
 const char* ffe_last_error(void);
 

@@ -91,7 +91,10 @@ def wald(xyz, M=1.0, a=0.9, B0=1.0):
 def dipole(xyz, mu=1.0, delta=0.1, chi=0.0):
     """Regularised dipole (Sec. IV.C): A = mu m x x / (r^2 + delta^2)^(3/2) with
     m = (sin chi, 0, cos chi) (the paper's A_phi for chi = 0), B~ = curl A in
-    flat space; E = psi = phi = q = 0."""
+    flat space; E = psi = phi = q = 0.  Complex (mu, chi) use the closed form
+    of the curl (dipole_closed), pinned against this construction."""
+    if np.iscomplexobj(np.asarray(mu)) or np.iscomplexobj(np.asarray(chi)):
+        return dipole_closed(xyz, mu, delta, chi)
     m = np.array([np.sin(chi), 0.0, np.cos(chi)])
 
     def A(p):
@@ -103,6 +106,20 @@ def dipole(xyz, mu=1.0, delta=0.1, chi=0.0):
     U[3] = dA[1, 2] - dA[2, 1]
     U[4] = dA[2, 0] - dA[0, 2]
     U[5] = dA[0, 1] - dA[1, 0]
+    return U
+
+
+def dipole_closed(xyz, mu=1.0, delta=0.1, chi=0.0):
+    """curl of mu m x x / (r^2+delta^2)^(3/2):
+    B~ = mu [3 x (m.x) - m (r^2 - 2 delta^2)] / (r^2 + delta^2)^(5/2)."""
+    xyz = np.asarray(xyz)
+    m = [np.sin(chi), 0.0 * chi, np.cos(chi)]
+    r2 = xyz[0] ** 2 + xyz[1] ** 2 + xyz[2] ** 2
+    mx = m[0] * xyz[0] + m[1] * xyz[1] + m[2] * xyz[2]
+    f = mu / (r2 + delta * delta) ** 2.5
+    U = np.zeros((9,) + np.shape(xyz)[1:], dtype=np.result_type(mu, chi, float))
+    for i in range(3):
+        U[3 + i] = f * (3 * xyz[i] * mx - m[i] * (r2 - 2 * delta * delta))
     return U
 
 

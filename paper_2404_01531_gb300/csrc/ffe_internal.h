@@ -153,6 +153,19 @@ void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field un, Field 
                               Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout, cudaStream_t st);
 void launch_stage12_ks(const Dev& d, Field un, Field Ua, Field G1, Field G2, cudaStream_t st);
 
+// adjoint (kernels_adjoint.cu)
+struct AdjArgs {
+    Field un, U2, R3, R4, T3, T4, U3, U4, F2, F3, F4, G1, G2, G3, G4, W;
+    Field lam, ubar, F2b, F3b, F4b, G1b, G2b, G3b, G4b, tmp, tmp2;
+};
+void launch_rhs_vjp(const Dev& d, Field U, Field L, Field out, double* omega_bar, cudaStream_t st);
+void launch_filter(const Dev& d, Field in, Field out, int nv, int transpose, cudaStream_t st);
+void launch_adj(const Dev& d, int which, AdjArgs a, int sub, cudaStream_t st);
+void launch_adj_G(const Dev& d, Field U, Field G, cudaStream_t st);
+void launch_adj_addG(const Dev& d, Field U, Field Gb, Field io, cudaStream_t st);
+void launch_luminosity(const Dev& d, Field U, const int* elem, const double* lk, const double* wn, int ns,
+                       double* partial, int nblocks, Field grad, double scale, cudaStream_t st);
+
 extern thread_local int64_t g_launch_counter;
 
 // optional per-kernel event timing (host.cu); no-ops unless profiling is on

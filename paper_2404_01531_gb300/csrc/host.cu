@@ -286,6 +286,17 @@ struct ffe_ctx {
     int id_nprm = 0;
     Tables tabs_h[MAXNP];
     bool tuned = false;
+    // adjoint work fields (allocated by the first adjoint call)
+    bool adj_ready = false;
+    AdjArgs adj{};
+    double* d_omega_bar = nullptr;
+    double* d_partial = nullptr;
+    // luminosity surface (cached per radius)
+    double lum_r = -1.0;
+    int lum_ns = 0;
+    int* d_lum_elem = nullptr;
+    double* d_lum_lk = nullptr;
+    double* d_lum_w = nullptr;
 };
 
 namespace {
@@ -1318,6 +1329,222 @@ ffe_status ffe_near_threshold(ffe_ctx* c, int* idx, int cap, int* n) {
 ffe_status ffe_launch_count(ffe_ctx* c, int64_t* n) {
     if (!c || !n) return fail(FFE_EINVAL, "null argument");
     *n = g_launch_counter;
+    return FFE_OK;
+}
+
+static ffe_status adjoint_ready(ffe_ctx* c) {
+    const Dev& d = c->d;
+    if (!d.curved || d.ks || c->batch) return fail(FFE_ENOTIMPL, "the adjoint is built for flat-metric shells");
+    if (d.mode == FFE_HARD || d.mode == FFE_RELAX_THEN_HARD) return fail(FFE_ENOTIMPL, "the adjoint of the clamp is not built");
+    std::vector<unsigned char> m(d.E);
+    CK(cudaMemcpyAsync(m.data(), d.mask, d.E, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (unsigned char x : m)
+        if (x) return fail(FFE_ENOTIMPL, "the adjoint differentiates all-DG masks only (an element is on FD)");
+    if (c->adj_ready) return FFE_OK;
+    AdjArgs& a = c->adj;
+    ffe_status s;
+    for (Field* f : {&a.U2, &a.R3, &a.R4, &a.T3, &a.T4, &a.U3, &a.U4, &a.F2, &a.F3, &a.F4, &a.W, &a.lam, &a.ubar,
+                     &a.F2b, &a.F3b, &a.F4b, &a.tmp, &a.tmp2})
+        if ((s = alloc_field(c, *f, NV))) return s;
+    for (Field* f : {&a.G1, &a.G2, &a.G3, &a.G4, &a.G1b, &a.G2b, &a.G3b, &a.G4b})
+        if ((s = alloc_field(c, *f, NG))) return s;
+    if ((s = dalloc(c, &c->d_omega_bar, 1))) return s;
+    if ((s = dalloc(c, &c->d_partial, 1024))) return s;
+    c->adj_ready = true;
+    return FFE_OK;
+}
+
+static ffe_status filter_or_copy(ffe_ctx* c, Field in, Field out, int transpose) {
+    const Dev& d = c->d;
+    if (d.filter_on) launch_filter(d, in, out, NV, transpose, c->st);
+    else CK(cudaMemcpyAsync(out.p, in.p, (size_t)NV * d.ndg * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return FFE_OK;
+}
+
+static void rhs_at(ffe_ctx* c, Field U, Field out) {
+    launch_dg_substep_curved(c->d, SUB_RHS, U, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, out, out, c->G1, c->st);
+}
+
+ffe_status ffe_rhs_vjp(ffe_ctx* c, const double* U_dev, const double* lam_dev, double* out_dev, double* omega_bar) {
+    g_err.clear();
+    if (!c || !U_dev || !lam_dev || !out_dev) return fail(FFE_EINVAL, "null argument");
+    ffe_status s;
+    if ((s = adjoint_ready(c))) return s;
+    const Dev& d = c->d;
+    Field U{(double*)U_dev, NV, d.ndg, d.nfd}, L{(double*)lam_dev, NV, d.ndg, d.nfd}, O{out_dev, NV, d.ndg, d.nfd};
+    CK(cudaMemsetAsync(c->d_omega_bar, 0, sizeof(double), c->st));
+    launch_rhs_vjp(d, U, L, O, c->d_omega_bar, c->st);
+    if (omega_bar) {
+        double ob = 0.0;
+        CK(cudaMemcpyAsync(&ob, c->d_omega_bar, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        *omega_bar += ob;
+    }
+    CK(cudaGetLastError());
+    return FFE_OK;
+}
+
+ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_in_dev, double* lam_out_dev,
+                            double* omega_bar) {
+    g_err.clear();
+    if (!c || !U_dev || !lam_in_dev || !lam_out_dev) return fail(FFE_EINVAL, "null argument");
+    ffe_status s;
+    if ((s = adjoint_ready(c))) return s;
+    const Dev& d = c->d;
+    cudaStream_t st = c->st;
+    AdjArgs a = c->adj;
+    a.un = Field{(double*)U_dev, NV, d.ndg, d.nfd};
+    Field lin{(double*)lam_in_dev, NV, d.ndg, d.nfd};
+    a.lam = Field{lam_out_dev, NV, d.ndg, d.nfd};
+    launch_build_lists(d, st);
+    // forward recomputation of the step's stages from U_n
+    launch_adj(d, 0, a, 0, st);
+    rhs_at(c, a.U2, a.F2);
+    launch_adj(d, 1, a, SUB_A, st);
+    if ((s = filter_or_copy(c, a.T3, a.U3, 0))) return s;
+    launch_adj_G(d, a.U3, a.G3, st);
+    rhs_at(c, a.U3, a.F3);
+    launch_adj(d, 1, a, SUB_B, st);
+    if ((s = filter_or_copy(c, a.T4, a.U4, 0))) return s;
+    launch_adj_G(d, a.U4, a.G4, st);
+    rhs_at(c, a.U4, a.F4);
+    // reverse
+    CK(cudaMemsetAsync(c->d_omega_bar, 0, sizeof(double), st));
+    if ((s = filter_or_copy(c, lin, a.tmp, 1))) return s;               // W-bar
+    launch_adj(d, 2, a, 0, st);                                         // seeds
+    launch_rhs_vjp(d, a.U4, a.F4b, a.tmp, c->d_omega_bar, st);          // U4-bar from F4
+    launch_adj_addG(d, a.U4, a.G4b, a.tmp, st);
+    if ((s = filter_or_copy(c, a.tmp, a.tmp2, 1))) return s;            // T4-bar
+    launch_adj(d, 3, a, SUB_B, st);
+    launch_rhs_vjp(d, a.U3, a.F3b, a.tmp, c->d_omega_bar, st);
+    launch_adj_addG(d, a.U3, a.G3b, a.tmp, st);
+    if ((s = filter_or_copy(c, a.tmp, a.tmp2, 1))) return s;            // T3-bar
+    launch_adj(d, 3, a, SUB_A, st);
+    launch_rhs_vjp(d, a.U2, a.F2b, a.tmp, c->d_omega_bar, st);
+    launch_adj_addG(d, a.U2, a.G2b, a.tmp, st);                         // U2-bar
+    launch_adj(d, 4, a, 0, st);                                         // stages 2, 1 -> lambda_n
+    if (omega_bar) {
+        double ob = 0.0;
+        CK(cudaMemcpyAsync(&ob, c->d_omega_bar, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *omega_bar += ob;
+    }
+    CK(cudaGetLastError());
+    return FFE_OK;
+}
+
+ffe_status ffe_luminosity(ffe_ctx* c, const double* U_dev, double r_L, double* L_host, double* grad_dev,
+                          double scale) {
+    g_err.clear();
+    if (!c || !U_dev) return fail(FFE_EINVAL, "null argument");
+    const Dev& d = c->d;
+    if (!d.curved || c->batch || c->dom.kind != FFE_DOMAIN_SHELL6) return fail(FFE_ENOTIMPL, "luminosity needs a shell");
+    if (!(r_L > c->dom.r_in && r_L < c->dom.r_out)) return fail(FFE_EINVAL, "r_L outside the shell");
+    ffe_status s;
+    if (c->lum_r != r_L) {
+        // surface layer, interpolation weights and quadrature weights (host)
+        const ShellGeo g = c->shell;
+        const double er = std::log(r_L / g.r_in) / g.c - 1.0;
+        const double pos = (er + 1.0) / 2.0 * g.nr;
+        int ir = (int)std::floor(pos);
+        ir = ir > g.nr - 1 ? g.nr - 1 : ir;
+        const double xr = 2.0 * (pos - ir) - 1.0;
+        const int np1 = d.np1, nf = np1 * np1;
+        std::vector<double> lk(np1);
+        for (int k = 0; k < np1; ++k) {
+            double v = 1.0;
+            for (int m = 0; m < np1; ++m)
+                if (m != k) v *= (xr - c->tab.x[m]) / (c->tab.x[k] - c->tab.x[m]);
+            lk[k] = v;
+        }
+        std::vector<int> elem;
+        std::vector<double> wn;
+        for (int e = 0; e < d.E; ++e) {
+            int ia, ib, irr, w;
+            shell_elem(g, e, ia, ib, irr, w);
+            if (irr != ir) continue;
+            elem.push_back(e);
+            for (int j = 0; j < np1; ++j)
+                for (int i = 0; i < np1; ++i) {
+                    const double xi[3] = {c->tab.x[i], c->tab.x[j], xr};
+                    double x[3], ij[3][3];
+                    shell_map(g, e, xi, x, ij);
+                    // area element |dx/dxi1 x dx/dxi2| from the Jacobian (inverse of ij)
+                    double J[3][3];
+                    const double det = ij[0][0] * (ij[1][1] * ij[2][2] - ij[1][2] * ij[2][1]) -
+                                       ij[0][1] * (ij[1][0] * ij[2][2] - ij[1][2] * ij[2][0]) +
+                                       ij[0][2] * (ij[1][0] * ij[2][1] - ij[1][1] * ij[2][0]);
+                    J[0][0] = (ij[1][1] * ij[2][2] - ij[1][2] * ij[2][1]) / det;
+                    J[0][1] = (ij[0][2] * ij[2][1] - ij[0][1] * ij[2][2]) / det;
+                    J[0][2] = (ij[0][1] * ij[1][2] - ij[0][2] * ij[1][1]) / det;
+                    J[1][0] = (ij[1][2] * ij[2][0] - ij[1][0] * ij[2][2]) / det;
+                    J[1][1] = (ij[0][0] * ij[2][2] - ij[0][2] * ij[2][0]) / det;
+                    J[1][2] = (ij[0][2] * ij[1][0] - ij[0][0] * ij[1][2]) / det;
+                    J[2][0] = (ij[1][0] * ij[2][1] - ij[1][1] * ij[2][0]) / det;
+                    J[2][1] = (ij[0][1] * ij[2][0] - ij[0][0] * ij[2][1]) / det;
+                    J[2][2] = (ij[0][0] * ij[1][1] - ij[0][1] * ij[1][0]) / det;
+                    const double a1[3] = {J[0][0], J[1][0], J[2][0]}, a2[3] = {J[0][1], J[1][1], J[2][1]};
+                    const double cr[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
+                    const double rr = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                    const double rh[3] = {x[0] / rr, x[1] / rr, x[2] / rr};
+                    const double area = std::fabs(cr[0] * rh[0] + cr[1] * rh[1] + cr[2] * rh[2]);
+                    wn.push_back(c->tab.w[i] * c->tab.w[j] * area);
+                    wn.push_back(rh[0]);
+                    wn.push_back(rh[1]);
+                    wn.push_back(rh[2]);
+                }
+        }
+        (void)nf;
+        if ((s = dalloc(c, &c->d_lum_elem, elem.size()))) return s;
+        if ((s = dalloc(c, &c->d_lum_lk, lk.size()))) return s;
+        if ((s = dalloc(c, &c->d_lum_w, wn.size()))) return s;
+        CK(cudaMemcpy(c->d_lum_elem, elem.data(), elem.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_lum_lk, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_lum_w, wn.data(), wn.size() * 8, cudaMemcpyHostToDevice));
+        c->lum_ns = (int)elem.size();
+        c->lum_r = r_L;
+    }
+    if (!c->d_partial && (s = dalloc(c, &c->d_partial, 1024))) return s;
+    Field U{(double*)U_dev, NV, d.ndg, d.nfd}, G{grad_dev, NV, d.ndg, d.nfd};
+    const int nb = 152;
+    launch_luminosity(d, U, c->d_lum_elem, c->d_lum_lk, c->d_lum_w, c->lum_ns, c->d_partial, nb, G, scale, c->st);
+    if (L_host) {
+        std::vector<double> part(nb);
+        CK(cudaMemcpyAsync(part.data(), c->d_partial, nb * 8, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        double sum = 0.0;
+        for (double v : part) sum += v;
+        *L_host = sum;
+    }
+    CK(cudaGetLastError());
+    return FFE_OK;
+}
+
+ffe_status ffe_initial_tangent(ffe_ctx* c, int which, double* dU_dev) {
+    g_err.clear();
+    if (!c || !dU_dev) return fail(FFE_EINVAL, "null argument");
+    if (c->id_kind != FFE_ID_DIPOLE || c->batch) return fail(FFE_ENOTIMPL, "tangents are built for the dipole data");
+    if (which != 0 && which != 2) return fail(FFE_EINVAL, "dipole parameter %d has no tangent (0 = mu, 2 = chi)", which);
+    const Dev& d = c->d;
+    const double mu = c->id_prm.size() > 0 ? c->id_prm[0] : 1.0;
+    const double dl = c->id_prm.size() > 1 ? c->id_prm[1] : 0.1;
+    const double chi = c->id_prm.size() > 2 ? c->id_prm[2] : 0.0;
+    std::vector<double> xdg(3 * (size_t)d.ndg), T(NV * (size_t)d.ndg, 0.0);
+    CK(cudaMemcpy(xdg.data(), d.xyz_dg, xdg.size() * 8, cudaMemcpyDeviceToHost));
+    // B = mu [3 x (m.x) - m (r^2 - 2 delta^2)] / (r^2 + delta^2)^(5/2), m = (sin chi, 0, cos chi)
+    const double m[3] = {std::sin(chi), 0.0, std::cos(chi)}, dm[3] = {std::cos(chi), 0.0, -std::sin(chi)};
+    parallel_for(d.ndg, [&](int64_t p) {
+        const double x[3] = {xdg[p], xdg[d.ndg + p], xdg[2 * d.ndg + p]};
+        const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        const double f = 1.0 / std::pow(r2 + dl * dl, 2.5);
+        const double* mm = which == 0 ? m : dm;
+        const double scale = which == 0 ? 1.0 : mu;
+        const double mx = mm[0] * x[0] + mm[1] * x[1] + mm[2] * x[2];
+        for (int i = 0; i < 3; ++i) T[(3 + i) * d.ndg + p] = scale * f * (3.0 * x[i] * mx - mm[i] * (r2 - 2.0 * dl * dl));
+    });
+    CK(cudaMemset(dU_dev, 0, NV * (size_t)(d.ndg + d.nfd) * sizeof(double)));
+    CK(cudaMemcpy(dU_dev, T.data(), T.size() * 8, cudaMemcpyHostToDevice));
     return FFE_OK;
 }
 

@@ -1,0 +1,623 @@
+// Hand-written vector-Jacobian products (reverse mode) of the DG path on
+// flat-metric shells, with every branch frozen as the forward pass took it:
+// the mask (all elements DG), the rectifier max(E^2 - B^2, 0), the branch of
+// the stiff solve, the sign of S.n in the no-incoming-Poynting state.  The
+// discrete map is smooth between branch changes (piecewise differentiable).
+//
+//   current_vjp     J~ = J~_drift + J~_eta (Sec. II.B)
+//   solve_vjp       U = R + dt a G(U) (Sec. III.B): analytic branch and the
+//                   scalar root s of the nonlinear branch by implicit differentiation
+//   k_rhs_vjp       lambda^T dF/dU of the DG right-hand side: transposed
+//                   derivative contractions, flux Jacobians, sources, the lifted
+//                   Rusanov terms of my faces and of my neighbours' faces, the
+//                   star / no-incoming boundary states, and d/d Omega at the star
+//   k_filter_t      transpose of the exponential filter
+#include "ffe_internal.h"
+#include "physics.cuh"
+#include "shellmap.cuh"
+#include "stage.cuh"
+
+namespace ffe {
+
+// Ub += (dJ_drift/dU)^T wd + (dJ_eta/dU)^T wp  (flat metric)
+__device__ __forceinline__ void current_vjp(const double* U, double eta, const double* wd, const double* wp, double* Ub) {
+    const double* E = U;
+    const double* B = U + 3;
+    const double B2 = dot3(B, B);
+    if (B2 == 0.0) return;
+    const double ib2 = 1.0 / B2, q = U[8];
+    const double c[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
+    // drift: J_d = q c / B^2
+    const double s = dot3(wd, c);
+    const double fq = q * ib2;
+    Ub[8] += s * ib2;
+    Ub[0] += fq * (B[1] * wd[2] - B[2] * wd[1]);
+    Ub[1] += fq * (B[2] * wd[0] - B[0] * wd[2]);
+    Ub[2] += fq * (B[0] * wd[1] - B[1] * wd[0]);
+    Ub[3] += fq * (wd[1] * E[2] - wd[2] * E[1]) - 2.0 * fq * s * ib2 * B[0];
+    Ub[4] += fq * (wd[2] * E[0] - wd[0] * E[2]) - 2.0 * fq * s * ib2 * B[1];
+    Ub[5] += fq * (wd[0] * E[1] - wd[1] * E[0]) - 2.0 * fq * s * ib2 * B[2];
+    if (eta == 0.0) return;
+    // eta part: J_p = eta (f B + g E), f = E.B/B^2, g = max(E^2 - B^2, 0)/B^2
+    const double EB = dot3(E, B), E2 = dot3(E, E);
+    const bool act = E2 - B2 > 0.0;
+    const double f = EB * ib2, g = act ? (E2 - B2) * ib2 : 0.0;
+    const double wB = dot3(wp, B), wE = dot3(wp, E);
+    for (int a = 0; a < 3; ++a) {
+        Ub[a] += eta * (wB * B[a] * ib2 + (act ? 2.0 * wE * E[a] * ib2 : 0.0) + g * wp[a]);
+        Ub[3 + a] += eta * (wB * (E[a] * ib2 - 2.0 * EB * B[a] * ib2 * ib2) + f * wp[a] +
+                            (act ? -2.0 * wE * E2 * B[a] * ib2 * ib2 : 0.0));
+    }
+}
+
+// Ub += sum_j (dF^j/dU)^T w[j]  with F^j the flat flux of direction j (J~ in the q~ row)
+__device__ __forceinline__ void flux_t(const double* U, double eta, const double w[3][NV], double* Ub) {
+    double wj[3];
+    for (int j = 0; j < 3; ++j) {
+        const double* x = w[j];
+        // F^j(E^i) = d^ij psi - [ijk] B_k ; F^j(B^i) = d^ij phi + [ijk] E_k
+        Ub[6] += x[j];
+        Ub[7] += x[3 + j];
+        for (int i = 0; i < 3; ++i) {
+            if (i == j) continue;
+            const int k = 3 - i - j;
+            const double sg = ((j - i + 3) % 3 == 1) ? 1.0 : -1.0;
+            Ub[3 + k] -= sg * x[i];
+            Ub[k] += sg * x[3 + i];
+        }
+        Ub[j] += x[6];       // F^j(psi) = E^j
+        Ub[3 + j] += x[7];   // F^j(phi) = B^j
+        wj[j] = x[8];        // F^j(q) = J^j
+    }
+    current_vjp(U, eta, wj, wj, Ub);
+}
+
+// R-bar of the pointwise stiff solve U = S(R) given U-bar (the branch taken by the forward solve).
+__device__ __forceinline__ void solve_vjp(const double* R, const Dev& d, double dta, const double* Ub, double* Rb) {
+    for (int v = 0; v < NV; ++v) Rb[v] = Ub[v];
+    Rb[6] = Ub[6] / fma(d.kpsi, dta, 1.0);
+    Rb[7] = Ub[7] / fma(d.kphi, dta, 1.0);
+    if (d.eta == 0.0) return;
+    const double* E = R;
+    const double* B = R + 3;
+    const double B2 = dot3(B, B);
+    if (B2 == 0.0) return;
+    const double c = d.eta * dta, ib2 = 1.0 / B2;
+    const double EB = dot3(E, B), f = EB * ib2, RR = dot3(E, E);
+    const double* Eb = Ub;
+    const double ebB = dot3(Eb, B);
+    double pa[3], pe[3], e0[3];
+    for (int i = 0; i < 3; ++i) {
+        pa[i] = f * B[i];
+        pe[i] = E[i] - pa[i];
+        e0[i] = fma(pa[i], 1.0 / (1.0 + c), pe[i]);
+    }
+    double u, v;
+    bool nonlin = dot3(e0, e0) > B2;
+    double s = 0.0;
+    if (nonlin) {
+        const double p2 = dot3(pe, pe), a2 = dot3(pa, pa);
+        double step = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            const double uu = 1.0 / (1.0 + s), vv = 1.0 / (1.0 + c + s);
+            const double g = c * ((p2 * uu * uu + a2 * vv * vv) - B2) * ib2 - s;
+            const double dg = -2.0 * c * (p2 * uu * uu * uu + a2 * vv * vv * vv) * ib2 - 1.0;
+            const double sn = s - g / dg;
+            step = sn - s;
+            if (!(sn > s)) break;
+            s = sn;
+            if (step <= 4e-16 * s) break;
+        }
+    }
+    u = 1.0 / (1.0 + s);
+    v = 1.0 / (1.0 + c + s);
+    // E_out = u E + (v - u) f B
+    const double k1 = v - u;
+    for (int a = 0; a < 3; ++a) {
+        Rb[a] = u * Eb[a] + k1 * ebB * B[a] * ib2;
+        Rb[3 + a] += k1 * (f * Eb[a] + ebB * (E[a] * ib2 - 2.0 * EB * B[a] * ib2 * ib2));
+    }
+    if (!nonlin) return;
+    // s(R): g(s; E, B) = c (u^2 |E|^2 + (v^2 - u^2) (E.B)^2/B^2 - B^2)/B^2 - s = 0
+    const double u2 = u * u, v2 = v * v;
+    const double par2 = EB * EB * ib2, perp2 = RR - par2;
+    const double gs = -2.0 * c * ib2 * (u2 * u * perp2 + v2 * v * par2) - 1.0;
+    double dEds[3];
+    for (int a = 0; a < 3; ++a) dEds[a] = -u2 * pe[a] - v2 * pa[a];
+    const double es = dot3(Eb, dEds);
+    const double coef = -es / gs;
+    const double inner = u2 * RR + (v2 - u2) * EB * EB * ib2 - B2;
+    for (int a = 0; a < 3; ++a) {
+        const double dgE = c * ib2 * (2.0 * u2 * E[a] + 2.0 * (v2 - u2) * EB * ib2 * B[a]);
+        const double dgB = c * ((2.0 * (v2 - u2) * EB * ib2 * E[a] - 2.0 * (v2 - u2) * EB * EB * ib2 * ib2 * B[a] -
+                                 2.0 * B[a]) * ib2 - 2.0 * ib2 * ib2 * B[a] * inner);
+        Rb[a] += coef * dgE;
+        Rb[3 + a] += coef * dgB;
+    }
+}
+
+// Ub += (dG/dU)^T Gb, G = (-J~_eta, -kpsi psi, -kphi phi)
+__device__ __forceinline__ void G_vjp(const double* U, const Dev& d, const double* Gb, double* Ub) {
+    const double zero[3] = {0.0, 0.0, 0.0};
+    const double wp[3] = {-Gb[0], -Gb[1], -Gb[2]};
+    current_vjp(U, d.eta, zero, wp, Ub);
+    Ub[6] -= d.kpsi * Gb[3];
+    Ub[7] -= d.kphi * Gb[4];
+}
+
+// ---------------------------------------------------------------------------
+template <int P>
+struct AVJ {
+    static constexpr int np1 = P + 1, nn = np1 * np1 * np1, nf = np1 * np1, NT = ((nn + 31) / 32) * 32;
+    // shared doubles: lambda [9][nn] | Y [27][nn] | C [6][9][nf]
+    static constexpr int SMEM = (9 * nn + 27 * nn + 54 * nf) * 8;
+};
+
+__device__ __forceinline__ void unit_normal(const Dev& d, int64_t p, int dd, int s, double* n, double& norm) {
+    double nn2 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        n[i] = (s ? 1.0 : -1.0) * d.geo[(int64_t)(3 * dd + i) * d.ndg + p];
+        nn2 = fma(n[i], n[i], nn2);
+    }
+    norm = sqrt(nn2);
+    for (int i = 0; i < 3; ++i) n[i] /= norm;
+}
+
+// z = (dC/dU_ext)^T lam = sc (sum_j n_j (dF^j/dU|_Ue)^T lam - lam), C the lifted Rusanov term
+__device__ __forceinline__ void lift_ext_t(const double* Ue, double eta, const double* n, double sc, const double* lam,
+                                           double* z) {
+    double w[3][NV];
+    for (int j = 0; j < 3; ++j)
+        for (int v = 0; v < NV; ++v) w[j][v] = n[j] * lam[v];
+    for (int v = 0; v < NV; ++v) z[v] = 0.0;
+    flux_t(Ue, eta, w, z);
+    for (int v = 0; v < NV; ++v) z[v] = sc * (z[v] - lam[v]);
+}
+
+template <int P>
+__global__ void __launch_bounds__(AVJ<P>::NT) k_rhs_vjp(Dev d, Field U, Field L, Field out, double* omega_bar) {
+    using K = AVJ<P>;
+    constexpr int np1 = K::np1, nn = K::nn, nf = K::nf, NT = K::NT;
+    extern __shared__ double sm[];
+    double* sL = sm;              // [9][nn]
+    double* sY = sL + 9 * nn;     // [27][nn]
+    double* sC = sY + 27 * nn;    // [6][9][nf]
+    __shared__ double s_om[NT];
+    const Tables& T = d.tabs[P];
+    const int tid = threadIdx.x;
+    const bool act = tid < nn;
+    const int ci[3] = {tid % np1, (tid / np1) % np1, tid / (np1 * np1)};
+    const double w0inv = 1.0 / T.w0;
+    for (int w = blockIdx.x; w < d.E; w += gridDim.x) {
+        const int e = w;
+        const int64_t eb = (int64_t)e * d.nn;
+        const double om = omega_of(d, e);
+        double om_acc = 0.0;
+        for (int t = tid; t < NV * nn; t += NT) sL[t] = L.dg(t / nn)[eb + t % nn];
+        double lam[NV], u[NV], ij[3][3], mu[3][NV];
+        if (act) {
+            for (int v = 0; v < NV; ++v) { lam[v] = L.dg(v)[eb + tid]; u[v] = U.dg(v)[eb + tid]; }
+            for (int k = 0; k < 3; ++k)
+                for (int i = 0; i < 3; ++i) ij[k][i] = d.geo[(int64_t)(3 * k + i) * d.ndg + eb + tid];
+        }
+        for (int j = 0; j < 3; ++j)
+            for (int v = 0; v < NV; ++v) mu[j][v] = 0.0;
+        // volume: mu^j_m = sum_k sum_n D_k[n][m] ij_n[k][j] lambda_n  (transposed contraction)
+        for (int k = 0; k < 3; ++k) {
+            __syncthreads();
+            if (act)
+                for (int j = 0; j < 3; ++j)
+                    for (int v = 0; v < NV; ++v) sY[(j * NV + v) * nn + tid] = ij[k][j] * lam[v];
+            __syncthreads();
+            if (act) {
+                const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
+                const int base = tid - ci[k] * stride;
+                double Dt[np1];
+                for (int m = 0; m < np1; ++m) Dt[m] = T.D[m][ci[k]];
+                for (int j = 0; j < 3; ++j)
+                    for (int v = 0; v < NV; ++v) {
+                        const double* src = sY + (j * NV + v) * nn + base;
+                        double acc = mu[j][v];
+#pragma unroll
+                        for (int m = 0; m < np1; ++m) acc = fma(Dt[m], src[m * stride], acc);
+                        mu[j][v] = acc;
+                    }
+            }
+        }
+        double ub[NV];
+        for (int v = 0; v < NV; ++v) ub[v] = 0.0;
+        if (act) {
+            // dU_n = - sum (...) F^j(U_m) + S(U_n): volume and explicit sources
+            double neg[3][NV];
+            for (int j = 0; j < 3; ++j)
+                for (int v = 0; v < NV; ++v) neg[j][v] = -mu[j][v];
+            flux_t(u, d.eta, neg, ub);
+            const double wd[3] = {-lam[0], -lam[1], -lam[2]}, zero[3] = {0.0, 0.0, 0.0};
+            current_vjp(u, d.eta, wd, zero, ub);
+            ub[8] += lam[6];
+        }
+        // lift terms at face nodes: mine (dU_int) and my neighbours' (their dU_ext)
+        for (int t = tid; t < 6 * nf; t += NT) {
+            const int f = t / nf, ab = t % nf, ta = ab % np1, tb = ab / np1;
+            const int dd = f >> 1, s = f & 1;
+            const int t1 = dd == 0 ? 1 : 0, t2 = dd == 2 ? 1 : 2;
+            int c[3];
+            c[dd] = s ? P : 0;
+            c[t1] = ta;
+            c[t2] = tb;
+            const int me = c[0] + np1 * (c[1] + np1 * c[2]);
+            const int64_t p = eb + me;
+            double n[3], norm;
+            unit_normal(d, p, dd, s, n, norm);
+            const double sc = 0.5 * norm * w0inv;
+            double lm[NV], Ui[NV], acc[NV];
+            for (int v = 0; v < NV; ++v) { lm[v] = sL[v * nn + me]; Ui[v] = U.dg(v)[p]; acc[v] = 0.0; }
+            // (a) my term, through U_int: dU -= sc (n.(F(Ue) - F(Ui)) - (Ue - Ui))
+            {
+                double z[NV];
+                lift_ext_t(Ui, d.eta, n, sc, lm, z);
+                for (int v = 0; v < NV; ++v) acc[v] += z[v];
+            }
+            const int nb = d.nbr[e * 6 + f];
+            if (nb < 0) {
+                const int kind = d.bc[e * 6 + f];
+                if (kind == FFE_BC_STAR || kind == FFE_BC_NO_INCOMING) {
+                    double Ue[NV], z[NV];
+                    double xn[3];
+                    for (int q = 0; q < 3; ++q) xn[q] = d.xyz_dg[(int64_t)q * d.ndg + p];
+                    if (kind == FFE_BC_STAR) bc_star_flat(Ui, xn, om, Ue);
+                    else bc_no_incoming_flat(Ui, n, Ue);
+                    lift_ext_t(Ue, d.eta, n, sc, lm, z);   // (dC/dUe)^T lambda
+                    if (kind == FFE_BC_STAR) {
+                        // Ue: E = B x v, v = Omega (-y, x, 0); B = B_i; phi = phi_i; psi = q = 0
+                        const double vv[3] = {-om * xn[1], om * xn[0], 0.0};
+                        acc[3] -= vv[1] * z[2] - vv[2] * z[1];
+                        acc[4] -= vv[2] * z[0] - vv[0] * z[2];
+                        acc[5] -= vv[0] * z[1] - vv[1] * z[0];
+                        acc[3] -= z[3]; acc[4] -= z[4]; acc[5] -= z[5];
+                        acc[7] -= z[7];
+                        // d Ue_E / d Omega = B x (z^ x x) = B x (-y, x, 0)
+                        const double dv[3] = {-xn[1], xn[0], 0.0};
+                        const double* B = Ui + 3;
+                        const double dE[3] = {B[1] * dv[2] - B[2] * dv[1], B[2] * dv[0] - B[0] * dv[2], B[0] * dv[1] - B[1] * dv[0]};
+                        om_acc -= dot3(z, dE);
+                    } else {
+                        const double S[3] = {Ui[1] * Ui[5] - Ui[2] * Ui[4], Ui[2] * Ui[3] - Ui[0] * Ui[5], Ui[0] * Ui[4] - Ui[1] * Ui[3]};
+                        const bool inward = dot3(S, n) < 0.0;
+                        if (!inward) { acc[0] -= z[0]; acc[1] -= z[1]; acc[2] -= z[2]; }
+                        acc[3] -= z[3]; acc[4] -= z[4]; acc[5] -= z[5];
+                        acc[8] -= z[8];
+                    }
+                }
+            } else {
+                // (c) the neighbour's lift term at its node used my U as its exterior state
+                const int f2 = d.nbr_face[e * 6 + f], d2 = f2 >> 1, s2 = f2 & 1;
+                const int u1 = d2 == 0 ? 1 : 0, u2 = d2 == 2 ? 1 : 2;
+                int a2, b2, cn[3];
+                orient_map(d.orient[e * 6 + f], np1, ta, tb, a2, b2);
+                cn[d2] = s2 ? P : 0;
+                cn[u1] = a2;
+                cn[u2] = b2;
+                const int64_t q = (int64_t)nb * d.nn + cn[0] + np1 * (cn[1] + np1 * cn[2]);
+                double n2[3], norm2, lnb[NV], z[NV];
+                unit_normal(d, q, d2, s2, n2, norm2);
+                for (int v = 0; v < NV; ++v) lnb[v] = L.dg(v)[q];
+                lift_ext_t(Ui, d.eta, n2, 0.5 * norm2 * w0inv, lnb, z);
+                for (int v = 0; v < NV; ++v) acc[v] -= z[v];
+            }
+            for (int v = 0; v < NV; ++v) sC[(f * NV + v) * nf + ab] = acc[v];
+        }
+        __syncthreads();
+        if (act) {
+            for (int dd = 0; dd < 3; ++dd) {
+                const int t1 = dd == 0 ? 1 : 0, t2 = dd == 2 ? 1 : 2;
+                const int ab = ci[t1] + np1 * ci[t2];
+                if (ci[dd] == 0)
+                    for (int v = 0; v < NV; ++v) ub[v] += sC[((2 * dd) * NV + v) * nf + ab];
+                if (ci[dd] == P)
+                    for (int v = 0; v < NV; ++v) ub[v] += sC[((2 * dd + 1) * NV + v) * nf + ab];
+            }
+            for (int v = 0; v < NV; ++v) out.dg(v)[eb + tid] = ub[v];
+        }
+        // Omega-bar: block sum in a fixed order, one atomic per element
+        s_om[tid] = om_acc;
+        __syncthreads();
+        if (tid == 0 && omega_bar) {
+            double sacc = 0.0;
+            for (int i = 0; i < NT; ++i) sacc += s_om[i];
+            if (sacc != 0.0) atomicAdd(omega_bar, sacc);
+        }
+        __syncthreads();
+    }
+}
+
+void launch_rhs_vjp(const Dev& d, Field U, Field L, Field out, double* omega_bar, cudaStream_t st) {
+    prof_begin("rhs_vjp", st);
+    switch (d.P) {
+#define FFE_VJP(PP)                                                                                        \
+    case PP:                                                                                               \
+        cudaFuncSetAttribute(k_rhs_vjp<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, AVJ<PP>::SMEM);  \
+        k_rhs_vjp<PP><<<152 * 2, AVJ<PP>::NT, AVJ<PP>::SMEM, st>>>(d, U, L, out, omega_bar);            \
+        break;
+        FFE_VJP(3)
+        FFE_VJP(4)
+        FFE_VJP(5)
+#undef FFE_VJP
+        default: break;
+    }
+    prof_end(st);
+    g_launch_counter += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Filter (or its transpose) of nv variables of every element, one CTA per element.
+__global__ void k_filter(Dev d, Field in, Field outf, int nv, int transpose) {
+    extern __shared__ double sm[];
+    const int np1 = d.np1, nn = d.nn;
+    const Tables& T = d.tabs[d.P];
+    double* a = sm;
+    double* b = sm + nn;
+    for (int e = blockIdx.x; e < d.E; e += gridDim.x) {
+        const int64_t eb = (int64_t)e * d.nn;
+        for (int v = 0; v < nv; ++v) {
+            for (int t = threadIdx.x; t < nn; t += blockDim.x) a[t] = in.dg(v)[eb + t];
+            __syncthreads();
+            for (int k = 0; k < 3; ++k) {
+                const double* src = (k == 1) ? b : a;
+                double* dst = (k == 1) ? a : b;
+                const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
+                for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+                    const int ck = (t / stride) % np1, base = t - ck * stride;
+                    double acc = 0.0;
+                    for (int m = 0; m < np1; ++m)
+                        acc = fma(transpose ? T.Filt[m][ck] : T.Filt[ck][m], src[base + m * stride], acc);
+                    if (k < 2) dst[t] = acc;
+                    else outf.dg(v)[eb + t] = acc;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+void launch_filter(const Dev& d, Field in, Field out, int nv, int transpose, cudaStream_t st) {
+    prof_begin("filter", st);
+    k_filter<<<152 * 4, 128, 2 * d.nn * sizeof(double), st>>>(d, in, out, nv, transpose);
+    prof_end(st);
+    g_launch_counter += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise kernels of the adjoint step (DG nodes; the mask is all DG).
+
+// forward recomputation: stage 1-2 (U2, G1, G2)
+__global__ void k_adj_s12(Dev d, AdjArgs a) {
+    const double dt = d.dt, dta = dt * IM_A;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+        double u[NV], U1[NV], g1[NG], g2[NG];
+        for (int v = 0; v < NV; ++v) { u[v] = a.un.dg(v)[p]; U1[v] = u[v]; }
+        stiff_solve_flat(U1, d, dta);
+        implicit_G_flat(U1, d, g1);
+        u[0] = fma(-dta, g1[0], u[0]);
+        u[1] = fma(-dta, g1[1], u[1]);
+        u[2] = fma(-dta, g1[2], u[2]);
+        u[6] = fma(-dta, g1[3], u[6]);
+        u[7] = fma(-dta, g1[4], u[7]);
+        stiff_solve_flat(u, d, dta);
+        implicit_G_flat(u, d, g2);
+        for (int v = 0; v < NV; ++v) a.U2.dg(v)[p] = u[v];
+        for (int c = 0; c < NG; ++c) { a.G1.dg(c)[p] = g1[c]; a.G2.dg(c)[p] = g2[c]; }
+    }
+}
+
+// forward recomputation: R = un + dt (...) of substep sub; T = S(R) (A, B) or W = R (C)
+__global__ void k_adj_comb(Dev d, AdjArgs a, int sub) {
+    const double dt = d.dt;
+    const int gv[NG] = {0, 1, 2, 6, 7};
+    const double z = 0.5 - IM_B - IM_H - IM_A;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+        double u[NV];
+        for (int v = 0; v < NV; ++v) u[v] = a.un.dg(v)[p];
+        if (sub == SUB_A) {
+            for (int v = 0; v < NV; ++v) u[v] = fma(dt, a.F2.dg(v)[p], u[v]);
+            for (int c = 0; c < NG; ++c) u[gv[c]] = fma(dt * (1.0 - IM_A), a.G2.dg(c)[p], u[gv[c]]);
+        } else if (sub == SUB_B) {
+            for (int v = 0; v < NV; ++v) u[v] = fma(0.25 * dt, a.F2.dg(v)[p] + a.F3.dg(v)[p], u[v]);
+            for (int c = 0; c < NG; ++c)
+                u[gv[c]] = fma(dt, IM_B * a.G1.dg(c)[p] + IM_H * a.G2.dg(c)[p] + z * a.G3.dg(c)[p], u[gv[c]]);
+        } else {
+            for (int v = 0; v < NV; ++v)
+                u[v] = fma(dt, (a.F2.dg(v)[p] + a.F3.dg(v)[p]) * (1.0 / 6.0) + a.F4.dg(v)[p] * (2.0 / 3.0), u[v]);
+            for (int c = 0; c < NG; ++c)
+                u[gv[c]] = fma(dt, (a.G2.dg(c)[p] + a.G3.dg(c)[p]) * (1.0 / 6.0) + a.G4.dg(c)[p] * (2.0 / 3.0), u[gv[c]]);
+        }
+        const Field& R = sub == SUB_A ? a.R3 : (sub == SUB_B ? a.R4 : a.W);
+        for (int v = 0; v < NV; ++v) R.dg(v)[p] = u[v];
+        if (sub != SUB_C) {
+            stiff_solve_flat(u, d, dt * IM_A);
+            const Field& Tt = sub == SUB_A ? a.T3 : a.T4;
+            for (int v = 0; v < NV; ++v) Tt.dg(v)[p] = u[v];
+        }
+    }
+}
+
+__global__ void k_adj_G(Dev d, Field U, Field G) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+        double u[NV], g[NG];
+        for (int v = 0; v < NV; ++v) u[v] = U.dg(v)[p];
+        implicit_G_flat(u, d, g);
+        for (int c = 0; c < NG; ++c) G.dg(c)[p] = g[c];
+    }
+}
+
+// reverse step pieces (see adjoint_step in host.cu for the order)
+// (1) from W-bar (in tmp): u-bar = Wb; Fk-bar, Gk-bar seeds
+__global__ void k_adj_seed(Dev d, AdjArgs a) {
+    const double dt = d.dt;
+    const int gv[NG] = {0, 1, 2, 6, 7};
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+        for (int v = 0; v < NV; ++v) {
+            const double w = a.tmp.dg(v)[p];
+            a.ubar.dg(v)[p] = w;
+            a.F2b.dg(v)[p] = dt / 6.0 * w;
+            a.F3b.dg(v)[p] = dt / 6.0 * w;
+            a.F4b.dg(v)[p] = 2.0 * dt / 3.0 * w;
+        }
+        for (int c = 0; c < NG; ++c) {
+            const double w = a.tmp.dg(gv[c])[p];
+            a.G1b.dg(c)[p] = 0.0;
+            a.G2b.dg(c)[p] = dt / 6.0 * w;
+            a.G3b.dg(c)[p] = dt / 6.0 * w;
+            a.G4b.dg(c)[p] = 2.0 * dt / 3.0 * w;
+        }
+    }
+}
+
+// (2) tmp = U-bar of stage U_s: RHS-vjp result (in tmp) + G-vjp of Gs-bar at U_s
+__global__ void k_adj_addG(Dev d, Field U, Field Gb, Field io) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+        double u[NV], gb[NG], ub[NV];
+        for (int v = 0; v < NV; ++v) { u[v] = U.dg(v)[p]; ub[v] = io.dg(v)[p]; }
+        for (int c = 0; c < NG; ++c) gb[c] = Gb.dg(c)[p];
+        G_vjp(u, d, gb, ub);
+        for (int v = 0; v < NV; ++v) io.dg(v)[p] = ub[v];
+    }
+}
+
+// (3) given T-bar (in tmp2, the filter transpose of U_s-bar): R-bar = solve_vjp(R, T-bar)
+//     and the contributions of R = un + dt(...) to u-bar, F-bar, G-bar
+__global__ void k_adj_back_comb(Dev d, AdjArgs a, int sub) {
+    const double dt = d.dt;
+    const int gv[NG] = {0, 1, 2, 6, 7};
+    const double z = 0.5 - IM_B - IM_H - IM_A;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+        double r[NV], tb[NV], rb[NV];
+        const Field& R = sub == SUB_A ? a.R3 : a.R4;
+        for (int v = 0; v < NV; ++v) { r[v] = R.dg(v)[p]; tb[v] = a.tmp2.dg(v)[p]; }
+        solve_vjp(r, d, dt * IM_A, tb, rb);
+        for (int v = 0; v < NV; ++v) a.ubar.dg(v)[p] += rb[v];
+        if (sub == SUB_B) {
+            for (int v = 0; v < NV; ++v) {
+                a.F2b.dg(v)[p] += 0.25 * dt * rb[v];
+                a.F3b.dg(v)[p] += 0.25 * dt * rb[v];
+            }
+            for (int c = 0; c < NG; ++c) {
+                a.G1b.dg(c)[p] += dt * IM_B * rb[gv[c]];
+                a.G2b.dg(c)[p] += dt * IM_H * rb[gv[c]];
+                a.G3b.dg(c)[p] += dt * z * rb[gv[c]];
+            }
+        } else {
+            for (int v = 0; v < NV; ++v) a.F2b.dg(v)[p] += dt * rb[v];
+            for (int c = 0; c < NG; ++c) a.G2b.dg(c)[p] += dt * (1.0 - IM_A) * rb[gv[c]];
+        }
+    }
+}
+
+// (4) stages 2 and 1: U2-bar in tmp; recompute U1, R2 from un
+__global__ void k_adj_back_s12(Dev d, AdjArgs a) {
+    const double dta = d.dt * IM_A;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+        double un[NV], U1[NV], R2[NV], g1[NG], u2b[NV], r2b[NV], g1b[NG], u1b[NV], r1b[NV];
+        for (int v = 0; v < NV; ++v) { un[v] = a.un.dg(v)[p]; U1[v] = un[v]; u2b[v] = a.tmp.dg(v)[p]; }
+        stiff_solve_flat(U1, d, dta);
+        implicit_G_flat(U1, d, g1);
+        for (int v = 0; v < NV; ++v) R2[v] = un[v];
+        R2[0] = fma(-dta, g1[0], R2[0]);
+        R2[1] = fma(-dta, g1[1], R2[1]);
+        R2[2] = fma(-dta, g1[2], R2[2]);
+        R2[6] = fma(-dta, g1[3], R2[6]);
+        R2[7] = fma(-dta, g1[4], R2[7]);
+        solve_vjp(R2, d, dta, u2b, r2b);
+        const int gv[NG] = {0, 1, 2, 6, 7};
+        for (int c = 0; c < NG; ++c) g1b[c] = a.G1b.dg(c)[p] - dta * r2b[gv[c]];
+        for (int v = 0; v < NV; ++v) u1b[v] = 0.0;
+        G_vjp(U1, d, g1b, u1b);
+        solve_vjp(un, d, dta, u1b, r1b);
+        for (int v = 0; v < NV; ++v) a.lam.dg(v)[p] = a.ubar.dg(v)[p] + r2b[v] + r1b[v];
+    }
+}
+
+void launch_adj(const Dev& d, int which, AdjArgs a, int sub, cudaStream_t st) {
+    const int grid = 152 * 8;
+    switch (which) {
+        case 0: k_adj_s12<<<grid, 256, 0, st>>>(d, a); break;
+        case 1: k_adj_comb<<<grid, 256, 0, st>>>(d, a, sub); break;
+        case 2: k_adj_seed<<<grid, 256, 0, st>>>(d, a); break;
+        case 3: k_adj_back_comb<<<grid, 256, 0, st>>>(d, a, sub); break;
+        case 4: k_adj_back_s12<<<grid, 256, 0, st>>>(d, a); break;
+        default: break;
+    }
+    g_launch_counter += 1;
+}
+
+void launch_adj_G(const Dev& d, Field U, Field G, cudaStream_t st) {
+    k_adj_G<<<152 * 8, 256, 0, st>>>(d, U, G);
+    g_launch_counter += 1;
+}
+
+void launch_adj_addG(const Dev& d, Field U, Field Gb, Field io, cudaStream_t st) {
+    k_adj_addG<<<152 * 8, 256, 0, st>>>(d, U, Gb, io);
+    g_launch_counter += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Luminosity through r = r_L: L = sum over surface nodes W_n (E x B).rhat at the
+// interpolated point; gradient dL/dU at the nodes of the radial element layer.
+struct LumArgs {
+    const int* elem;        // [ns] element of surface column s
+    const double* lk;       // [np1] interpolation weights along xi^3
+    const double* wn;       // [ns][np1^2][4]: weight, rhat (3) at (i, j)
+    int ns;
+};
+
+__global__ void k_luminosity(Dev d, Field U, LumArgs la, double* out, Field grad, double scale) {
+    const int np1 = d.np1, nf = np1 * np1;
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < la.ns * nf; t += gridDim.x * blockDim.x) {
+        const int s = t / nf, ij = t % nf;
+        const int e = la.elem[s];
+        const int64_t eb = (int64_t)e * d.nn;
+        double E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+        for (int k = 0; k < np1; ++k) {
+            const int64_t p = eb + ij + nf * k;
+            for (int a = 0; a < 3; ++a) {
+                E[a] = fma(la.lk[k], U.dg(a)[p], E[a]);
+                B[a] = fma(la.lk[k], U.dg(3 + a)[p], B[a]);
+            }
+        }
+        const double* w = la.wn + ((int64_t)s * nf + ij) * 4;
+        const double r[3] = {w[1], w[2], w[3]};
+        const double S[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
+        acc = fma(w[0], dot3(S, r), acc);
+        if (grad.p) {
+            // d/dE = W (B x r), d/dB = W (r x E), spread with l_k
+            const double gE[3] = {B[1] * r[2] - B[2] * r[1], B[2] * r[0] - B[0] * r[2], B[0] * r[1] - B[1] * r[0]};
+            const double gB[3] = {r[1] * E[2] - r[2] * E[1], r[2] * E[0] - r[0] * E[2], r[0] * E[1] - r[1] * E[0]};
+            for (int k = 0; k < np1; ++k) {
+                const int64_t p = eb + ij + nf * k;
+                const double f = scale * w[0] * la.lk[k];
+                for (int a = 0; a < 3; ++a) {
+                    grad.dg(a)[p] += f * gE[a];
+                    grad.dg(3 + a)[p] += f * gB[a];
+                }
+            }
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sacc = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) sacc += red[i];
+        out[blockIdx.x] = sacc;
+    }
+}
+
+void launch_luminosity(const Dev& d, Field U, const int* elem, const double* lk, const double* wn, int ns,
+                       double* partial, int nblocks, Field grad, double scale, cudaStream_t st) {
+    LumArgs la{elem, lk, wn, ns};
+    k_luminosity<<<nblocks, 256, 0, st>>>(d, U, la, partial, grad, scale);
+    g_launch_counter += 1;
+}
+
+}  // namespace ffe

@@ -25,6 +25,7 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
            "ffe_download", "ffe_upload", "ffe_get_info", "ffe_get_status", "ffe_tci_ratio",
            "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
            "ffe_fd_rhs_noalloc", "ffe_create_batch", "ffe_get_layout", "ffe_set_initial_batch",
+           "ffe_rhs_vjp", "ffe_adjoint_step", "ffe_luminosity", "ffe_initial_tangent",
            "ffe_last_error", "ffe_destroy"]
 
 
@@ -94,6 +95,10 @@ def load():
         "ffe_get_layout": [P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                            ctypes.POINTER(i)],
         "ffe_set_initial_batch": [P, i, ctypes.POINTER(d), i, i],
+        "ffe_rhs_vjp": [P, P, P, P, ctypes.POINTER(d)],
+        "ffe_adjoint_step": [P, P, P, P, ctypes.POINTER(d)],
+        "ffe_luminosity": [P, P, d, ctypes.POINTER(d), P, d],
+        "ffe_initial_tangent": [P, i, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -277,6 +282,30 @@ class Context:
 
     def join(self, udg, ufd):
         return np.concatenate([np.ascontiguousarray(udg).reshape(-1), np.ascontiguousarray(ufd).reshape(-1)])
+
+    # ---- adjoint -----------------------------------------------------------
+    def rhs_vjp(self, U, lam, out):
+        """out = lam^T dF/dU at U; returns lam^T dF/dOmega."""
+        ob = ctypes.c_double(0.0)
+        check(load().ffe_rhs_vjp(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.byref(ob)))
+        return ob.value
+
+    def adjoint_step(self, U, lam_in, lam_out):
+        """lam_out = lambda_n from lambda_{n+1} for the step starting at U; returns dL/dOmega of the step."""
+        ob = ctypes.c_double(0.0)
+        check(load().ffe_adjoint_step(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
+                                      ctypes.c_void_p(lam_out.data_ptr()), ctypes.byref(ob)))
+        return ob.value
+
+    def luminosity(self, U, r_L, grad=None, scale=1.0):
+        L = ctypes.c_double(0.0)
+        check(load().ffe_luminosity(self.h, ctypes.c_void_p(U.data_ptr()), float(r_L), ctypes.byref(L),
+                                    ctypes.c_void_p(grad.data_ptr()) if grad is not None else None, float(scale)))
+        return L.value
+
+    def initial_tangent(self, which, out):
+        check(load().ffe_initial_tangent(self.h, int(which), ctypes.c_void_p(out.data_ptr())))
 
     def layout(self):
         """(elem_P, fd_slot, elem_inst, inst_first) as numpy arrays."""
