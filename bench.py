@@ -200,6 +200,89 @@ def run_pulsars(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_measure(steps=500, every=25, r_L=20.0, fd_check=False):
+    """Neutron-star shell 6 wedges x 6x6x12 at P=5: time of `steps` forward steps
+    (graph replays) against the checkpointed gradient of the time-averaged
+    luminosity through r = r_L w.r.t. (mu, chi, Omega); optionally the gradient
+    against central differences of the forward run (relative step 1e-6)."""
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    from paper_2404_01531_gb300.adjoint import lbar_forward, luminosity_gradient
+    cfg = W.adjoint_pulsar(steps=steps)
+    cfg["params"].update(tci_on=0)
+    ctx = ffe.Context(cfg)
+    ctx.set_initial()
+    U0, m0 = (t.clone() for t in ctx.state())
+    st = torch.cuda.current_stream()
+    ctx.step(3)
+    ctx.set_state(U0, m0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    ctx.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    # one adjoint step alone (stage recomputation + reverse), same state
+    lam = torch.randn(U0.shape, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(lam)
+    for _ in range(3):
+        ctx.adjoint_step(U0, lam, out)
+    k = 20
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(k):
+        ctx.adjoint_step(U0, lam, out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    adj_ms = e0.elapsed_time(e1) / k
+    ctx.set_state(U0, m0)
+    L, g, tm = luminosity_gradient(ctx, steps, r_L=r_L, every=every)
+    ctx.close()
+    res = {"workload": f"rotating dipole (mu, chi, Omega) = (1, 45 deg, 1/6), shell r in [1, 24], "
+                       f"6 wedges x 6x6x12 elements P=5, eta=1e5, {steps} steps, checkpoint every {every}",
+           "forward_ms_per_step": fwd_ms / steps, "adjoint_step_ms": adj_ms,
+           "adjoint_step_over_forward_step": adj_ms / (fwd_ms / steps),
+           "gradient_s": tm["forward_s"] + tm["adjoint_s"], "forward_s": fwd_ms / 1e3,
+           "gradient_over_forward": (tm["forward_s"] + tm["adjoint_s"]) / (fwd_ms / 1e3),
+           "Lbar": L, "grad": g}
+    if fd_check:
+        kind, kw = cfg["initial"]
+        base = {"mu": kw["mu"], "chi": kw["chi"], "omega": cfg["params"]["omega_star"]}
+        fd = []
+        for name in ("mu", "chi", "omega"):
+            h = 1e-6 * base[name]
+            vals = []
+            for sgn in (1, -1):
+                c = dict(cfg)
+                c["params"] = dict(cfg["params"])
+                kw2 = dict(kw)
+                if name == "omega":
+                    c["params"]["omega_star"] = base[name] + sgn * h
+                else:
+                    kw2[name] = base[name] + sgn * h
+                c["initial"] = (kind, kw2)
+                cx = ffe.Context(c)
+                cx.set_initial()
+                vals.append(lbar_forward(cx, steps, r_L))
+                cx.close()
+            fd.append((vals[0] - vals[1]) / (2 * h))
+        res["grad_central_differences"] = fd
+        res["max_rel_err_vs_fd"] = max(abs(a - b) / abs(b) for a, b in zip(g, fd))
+    return res
+
+
+def run_adjoint(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    r = adjoint_measure(steps=args.steps, every=25, fd_check=True)
+    line = {"metric": METRIC, "value": r["adjoint_step_over_forward_step"], "unit": "adjoint step / forward step",
+            "n_gpus": 1, "steps": args.steps, "warmup": 3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": r.pop("workload")},
+            "adjoint": r}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,8 +292,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64,
                     help="elements along x (same width 4/64; smaller values for profiler captures)")
-    ap.add_argument("--workload", default="breakdown", choices=["breakdown", "pulsars"],
-                    help="pulsars: the 32-shell batch, batched launch vs one context per instance")
+    ap.add_argument("--workload", default="breakdown", choices=["breakdown", "pulsars", "adjoint"],
+                    help="pulsars: the 32-shell batch, batched launch vs one context per instance; "
+                         "adjoint: luminosity gradient of one neutron-star shell (--steps steps)")
+    ap.add_argument("--no-adjoint", action="store_true", help="breakdown: skip the adjoint/forward timing")
     ap.add_argument("--n-inst", type=int, default=32)
     ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
     args = ap.parse_args()
@@ -218,6 +303,8 @@ def main():
         return run_reference(args)
     if args.workload == "pulsars":
         return run_pulsars(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
 
     import numpy as np
     import torch
@@ -273,32 +360,36 @@ def main():
     launches = per_step_launches * args.steps
 
     # ---- per-kernel event timing of the same steps (eager launches)
+    # algorithmic work of the window from the library's element-update counters
+    # (every FD element update is one pass of fd_flux over it, every DG element
+    # update one pass of dg_substep); per-launch work = total / launches
+    i0 = ctx.info()
     ctx.set_profiling(True)
-    fd_before = ctx.info().n_fd_elem
     ctx.step(args.steps)
-    fd_after = ctx.info().n_fd_elem
     ctx.set_profiling(False)
+    i1 = ctx.info()
     prof = ctx.profile_read()
     total_ms = sum(v[1] for v in prof.values())
     dom = max(prof, key=lambda k: prof[k][1])
     dom_launches, dom_ms = prof[dom]
-    fd_mean = 0.5 * (fd_before + fd_after)
     E, P = ctx.n_elem, ctx.P
     nn = (P + 1) ** 3
+    n_fd_upd = i1.fd_elem_updates - i0.fd_elem_updates
+    n_dg_upd = i1.dg_elem_updates - i0.dg_elem_updates
     if dom == "dg_substep":
-        flops = (E - fd_mean) * nn * sum(dg_flops_per_node(P, s) for s in range(3)) / 3.0
+        flops = n_dg_upd * nn * sum(dg_flops_per_node(P, s) for s in range(3)) / 3.0
     elif dom == "fd_flux":
-        flops = fd_mean * fd_faces_per_element(P) * FD_FLUX_FLOPS
+        flops = n_fd_upd * fd_faces_per_element(P) * FD_FLUX_FLOPS
     else:
         flops = None
-    avg_ms = dom_ms / dom_launches
     roof = None
     if flops is not None:
-        ach = flops / (avg_ms / 1e3) / 1e12
+        ach = flops / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
                 "kernel": dom, "peak_source": "derived: 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz",
-                "share": dom_ms / total_ms}
+                "share": dom_ms / total_ms, "launches": dom_launches,
+                "units": {"fd_elem_updates": n_fd_upd, "dg_elem_updates": n_dg_upd}}
 
     # ---- end to end through the C ABI with host buffers
     pin = torch.empty(ctx.n_state, dtype=torch.float64, pin_memory=True)
@@ -323,6 +414,12 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
+    adj = None
+    if not args.no_adjoint:
+        try:
+            adj = adjoint_measure()
+        except Exception as ex:  # reported, not fatal
+            adj = {"failed": str(ex)}
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -339,7 +436,7 @@ def main():
                        "parallelism": f"replicas x{ws}", "l2": "working set > L2 (no flush needed)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
-            "status_bits": status}
+            "adjoint": adj, "status_bits": status}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

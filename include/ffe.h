@@ -104,6 +104,9 @@ typedef struct {
     int n_fd_elem;                /* elements currently on FD                             */
     int64_t node_updates;         /* DG nodes + FD cells advanced through an explicit RHS
                                      and its stage update, summed since ffe_set_initial     */
+    int64_t fd_elem_updates;      /* FD elements advanced through an RHS and stage update
+                                     (rollback redos included), since ffe_set_initial      */
+    int64_t dg_elem_updates;      /* DG elements advanced likewise                         */
 } ffe_info;
 
 /* Create a context: builds the mesh, operator tables and geometry, allocates

@@ -13,6 +13,12 @@ sides ("substeps") per step; u_{n+1} = u_n + dt sum_j w_j (F_j + G_j).
 
 [reading] order inside a substep result (U_3, U_4, u_{n+1}):
   stiff solve -> algebraic clamp (if on) -> filter (DG elements) -> TCI (DG elements).
+[reading] G(U_3), G(U_4) are taken at the solved stage values before the
+filter, so that G_s = (U_s - R_s)/(dt a) holds exactly; the filtered values go
+to the next explicit RHS, the TCI and the step result.  With eta dt >> 1 (the
+regime Sec. III.B aims for), G at the filtered value differs from the implicit
+increment by eta times the removed top mode, and that difference enters
+u_{n+1} (which has no solve) amplified by ~eta dt every step.
 A DG element the TCI flags after a substep is rolled back: the substep's
 inputs (u_n, the earlier F and G, and the stage state the RHS was taken at) are
 projected to its subcells, the RHS is recomputed with the FD operator using the
@@ -136,18 +142,20 @@ class Stepper:
         hist = dict(un=un, G1=G1, G2=G2)
 
         def substep(Uprev, Fprev, build, proj_keys):
-            """Compute F at Uprev, build the substep result, filter, TCI and roll back."""
+            """Compute F at Uprev, build the substep result, filter, TCI and roll back.
+            Returns (F, filtered result, result before the filter)."""
             nonlocal mask
             Fs = self.rhs(Uprev, mask)
-            Un = self.filt(build(Fs, mask), mask)
+            Ub = build(Fs, mask)
+            Un = self.filt(Ub, mask)
             if not P.prm["tci_on"]:
-                return Fs, Un
+                return Fs, Un, Ub
             sel = self._sel(mask, DG)
             r = tci_ratio(Un[0][3:6, sel], P.met["dg"], T, sel)
             self.near += [int(e) for e, x in zip(sel, r) if abs(x - thr) <= 1e-12 * thr]
             flagged = sel[r > thr]
             if len(flagged) == 0:
-                return Fs, Un
+                return Fs, Un, Ub
             for e in flagged:
                 mask[e] = FD
                 switched.add(int(e))
@@ -161,17 +169,20 @@ class Stepper:
                 Fs[1][:, e] = Ffd[:, e]
             Un2 = build(Fs, mask)
             Un = (Un[0], Un[1].copy())
+            Ub = (Ub[0], Ub[1].copy())
             for e in flagged:
                 Un[1][:, e] = Un2[1][:, e]
-            return Fs, Un
+                Ub[1][:, e] = Un2[1][:, e]
+            return Fs, Un, Ub
 
         # substep A: F2 = F(U2), U3
         def build3(F2, mk):
             R = self.lin([(1.0, hist["un"]), (dt, F2), (dt * (1 - a), hist["G2"])])
             return self.solve(R, mk)
-        F2, U3 = substep(U2, None, build3, ["un", "G1", "G2"])
+        # G_s at the solved stage value before the filter (module docstring)
+        F2, U3, U3b = substep(U2, None, build3, ["un", "G1", "G2"])
         hist["F2"] = F2
-        G3 = self.G(U3, mask)
+        G3 = self.G(U3b, mask)
         hist["G3"] = G3
 
         # substep B: F3 = F(U3), U4
@@ -179,9 +190,9 @@ class Stepper:
             R = self.lin([(1.0, hist["un"]), (0.25 * dt, hist["F2"]), (0.25 * dt, F3),
                           (dt * b, hist["G1"]), (dt * h, hist["G2"]), (dt * z, hist["G3"])])
             return self.solve(R, mk)
-        F3, U4 = substep(U3, None, build4, ["un", "F2", "G1", "G2", "G3"])
+        F3, U4, U4b = substep(U3, None, build4, ["un", "F2", "G1", "G2", "G3"])
         hist["F3"] = F3
-        G4 = self.G(U4, mask)
+        G4 = self.G(U4b, mask)
         hist["G4"] = G4
 
         # substep C: F4 = F(U4), u_{n+1}
@@ -191,7 +202,7 @@ class Stepper:
             if P.prm["mode"] in (1, 2):
                 R = self.pair_map(lambda r, m: ph.hard_clamp(r, m), mk, R)
             return R
-        _, un1 = substep(U4, None, buildn, ["un", "F2", "F3", "G2", "G3", "G4"])
+        _, un1, _ = substep(U4, None, buildn, ["un", "F2", "F3", "G2", "G3", "G4"])
 
         udg, ufd = un1[0].copy(), un1[1].copy()
         # end of step: FD -> DG where admissible with alpha' = alpha + 1

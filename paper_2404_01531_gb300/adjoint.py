@@ -28,6 +28,16 @@ class Step(torch.autograd.Function):
         return lam_out, None
 
 
+def lbar_forward(ctx, nsteps, r_L=20.0):
+    """Lbar = mean of L(u_n), n = 1..nsteps, forward only (no checkpoints);
+    the state of ctx is advanced by nsteps."""
+    acc = 0.0
+    for _ in range(nsteps):
+        ctx.step(1)
+        acc += ctx.luminosity(ctx.state()[0], r_L)
+    return acc / nsteps
+
+
 def luminosity_gradient(ctx, nsteps, r_L=20.0, every=25):
     """Lbar = mean of L(u_n), n = 1..nsteps, and d Lbar/d (mu, chi, Omega).
 

@@ -106,7 +106,7 @@ struct Dev {
     unsigned char* switched;        // [E] switched to FD during the current step
     int* dg_list; int* fd_list; int* flag_list; int* near_list;
     int* counts;                    // [0] n_dg, [1] n_fd, [2] n_flag, [3] n_near, [4] status bits, [5] free slots
-    unsigned long long* units;      // element-node updates (DG nodes + FD cells per substep)
+    unsigned long long* units;      // [0] node updates (DG nodes + FD cells per substep), [1] FD and [2] DG element updates
     // FD scratch per chunk of listed FD elements: extended cells [12][chunk][(nc+6)^3],
     // face fluxes [3 (x3 curved)][9][chunk][(nc+1) nc^2]
     double* ext;

@@ -772,7 +772,7 @@ ffe_status finish_create(ffe_ctx* c, int fd_cap, const std::vector<int>& orders)
     if ((s = dalloc(c, &d.flag_list, d.E))) return s;
     if ((s = dalloc(c, &d.near_list, 4096))) return s;
     if ((s = dalloc(c, &d.counts, 8))) return s;
-    if ((s = dalloc(c, &d.units, 1))) return s;
+    if ((s = dalloc(c, &d.units, 3))) return s;   // node updates, FD and DG element updates
     if (c->batch) {
         int *eP8, *ein;
         InstInfo* dinst;
@@ -877,7 +877,7 @@ ffe_status set_initial_impl(ffe_ctx* c, int id_kind) {
     CK(cudaMemcpy(d.mask, mask.data(), d.E, cudaMemcpyHostToDevice));
     ffe_status s;
     if ((s = fill_dirichlet(c))) return s;
-    CK(cudaMemset(d.units, 0, sizeof(unsigned long long)));
+    CK(cudaMemset(d.units, 0, 3 * sizeof(unsigned long long)));
     c->t = 0.0;
     c->steps = 0;
     return FFE_OK;
@@ -1293,9 +1293,11 @@ ffe_status ffe_get_info(ffe_ctx* c, ffe_info* info) {
     int n = 0;
     for (unsigned char x : m) n += x;
     info->n_fd_elem = n;
-    unsigned long long u = 0;
-    CK(cudaMemcpy(&u, d.units, sizeof u, cudaMemcpyDeviceToHost));
-    info->node_updates = (int64_t)u;
+    unsigned long long u[3] = {0, 0, 0};
+    CK(cudaMemcpy(u, d.units, sizeof u, cudaMemcpyDeviceToHost));
+    info->node_updates = (int64_t)u[0];
+    info->fd_elem_updates = (int64_t)u[1];
+    info->dg_elem_updates = (int64_t)u[2];
     return FFE_OK;
 }
 
@@ -1403,23 +1405,23 @@ ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_i
     rhs_at(c, a.U2, a.F2);
     launch_adj(d, 1, a, SUB_A, st);
     if ((s = filter_or_copy(c, a.T3, a.U3, 0))) return s;
-    launch_adj_G(d, a.U3, a.G3, st);
+    launch_adj_G(d, a.T3, a.G3, st);                                    // G at the pre-filter value
     rhs_at(c, a.U3, a.F3);
     launch_adj(d, 1, a, SUB_B, st);
     if ((s = filter_or_copy(c, a.T4, a.U4, 0))) return s;
-    launch_adj_G(d, a.U4, a.G4, st);
+    launch_adj_G(d, a.T4, a.G4, st);
     rhs_at(c, a.U4, a.F4);
     // reverse
     CK(cudaMemsetAsync(c->d_omega_bar, 0, sizeof(double), st));
     if ((s = filter_or_copy(c, lin, a.tmp, 1))) return s;               // W-bar
     launch_adj(d, 2, a, 0, st);                                         // seeds
     launch_rhs_vjp(d, a.U4, a.F4b, a.tmp, c->d_omega_bar, st);          // U4-bar from F4
-    launch_adj_addG(d, a.U4, a.G4b, a.tmp, st);
-    if ((s = filter_or_copy(c, a.tmp, a.tmp2, 1))) return s;            // T4-bar
+    if ((s = filter_or_copy(c, a.tmp, a.tmp2, 1))) return s;            // T4-bar from U4-bar
+    launch_adj_addG(d, a.T4, a.G4b, a.tmp2, st);                        // + G4 taken at T4
     launch_adj(d, 3, a, SUB_B, st);
     launch_rhs_vjp(d, a.U3, a.F3b, a.tmp, c->d_omega_bar, st);
-    launch_adj_addG(d, a.U3, a.G3b, a.tmp, st);
-    if ((s = filter_or_copy(c, a.tmp, a.tmp2, 1))) return s;            // T3-bar
+    if ((s = filter_or_copy(c, a.tmp, a.tmp2, 1))) return s;            // T3-bar from U3-bar
+    launch_adj_addG(d, a.T3, a.G3b, a.tmp2, st);
     launch_adj(d, 3, a, SUB_A, st);
     launch_rhs_vjp(d, a.U2, a.F2b, a.tmp, c->d_omega_bar, st);
     launch_adj_addG(d, a.U2, a.G2b, a.tmp, st);                         // U2-bar

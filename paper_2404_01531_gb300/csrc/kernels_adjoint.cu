@@ -96,18 +96,8 @@ __device__ __forceinline__ void solve_vjp(const double* R, const Dev& d, double 
     bool nonlin = dot3(e0, e0) > B2;
     double s = 0.0;
     if (nonlin) {
-        const double p2 = dot3(pe, pe), a2 = dot3(pa, pa);
-        double step = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            const double uu = 1.0 / (1.0 + s), vv = 1.0 / (1.0 + c + s);
-            const double g = c * ((p2 * uu * uu + a2 * vv * vv) - B2) * ib2 - s;
-            const double dg = -2.0 * c * (p2 * uu * uu * uu + a2 * vv * vv * vv) * ib2 - 1.0;
-            const double sn = s - g / dg;
-            step = sn - s;
-            if (!(sn > s)) break;
-            s = sn;
-            if (step <= 4e-16 * s) break;
-        }
+        bool ok;
+        s = stiff_root(c, dot3(pe, pe), dot3(pa, pa), B2, ib2, ok);
     }
     u = 1.0 / (1.0 + s);
     v = 1.0 / (1.0 + c + s);

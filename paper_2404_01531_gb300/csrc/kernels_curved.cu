@@ -256,6 +256,13 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
             } else {
                 substep_combine(d, SUB, du, eb + tid, false, a, dt, u);
             }
+            if (SUB != SUB_C) {
+                // G at the solved stage value, before the filter: G_s = (U_s - R_s)/(dt a)
+                double g[NG];
+                if (KS) implicit_G_gen(u, m, d, g);
+                else implicit_G_flat(u, d, g);
+                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
+            }
         }
         __syncthreads();
         if (d.filter_on) {
@@ -319,7 +326,10 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
             __syncthreads();
             flagged = red[2 * NW] != 0.0;
         }
-        if (!flagged && tid == 0) atomicAdd(d.units, (unsigned long long)nn);
+        if (!flagged && tid == 0) {
+            atomicAdd(d.units, (unsigned long long)nn);
+            atomicAdd(d.units + 2, 1ull);
+        }
         if (!flagged && act) {
             bool bad = false;
             for (int v = 0; v < NV; ++v) {
@@ -327,12 +337,6 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                 bad |= !isfinite(u[v]);
             }
             if (bad) atomic_status(d, 1);
-            if (SUB != SUB_C) {
-                double g[NG];
-                if (KS) implicit_G_gen(u, m, d, g);
-                else implicit_G_flat(u, d, g);
-                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
-            }
         }
         __syncthreads();
     }

@@ -343,6 +343,12 @@ __global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) 
             if (SUB != SUB_C)
                 for (int v = 0; v < NV; ++v) a.Fout.dg(v)[eb + tid] = du[v];
             substep_combine(d, SUB, du, eb + tid, false, a, d.dt, u);
+            if (SUB != SUB_C) {
+                // G at the solved stage value, before the filter: G_s = (U_s - R_s)/(dt a)
+                double g[NG];
+                implicit_G_flat(u, d, g);
+                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
+            }
         }
         __syncthreads();   // sU, sJ, sC are free from here on
         if (d.filter_on) {
@@ -423,7 +429,10 @@ __global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) 
             __syncthreads();
             flagged = s_flag != 0;
         }
-        if (!flagged && tid == 0) atomicAdd(d.units, (unsigned long long)nn);
+        if (!flagged && tid == 0) {
+            atomicAdd(d.units, (unsigned long long)nn);
+            atomicAdd(d.units + 2, 1ull);
+        }
         if (!flagged && act) {
             bool bad = false;
             for (int v = 0; v < NV; ++v) {
@@ -431,11 +440,6 @@ __global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) 
                 bad |= !isfinite(u[v]);
             }
             if (bad) atomic_status(d, 1);
-            if (SUB != SUB_C) {
-                double g[NG];
-                implicit_G_flat(u, d, g);
-                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
-            }
         }
         __syncthreads();
     }

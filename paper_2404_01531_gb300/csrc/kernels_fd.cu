@@ -426,7 +426,10 @@ __global__ void k_fd_update(Dev d, const int* list, int ci, int w0, SubArgs a) {
             for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
             continue;
         }
-        if (c == 0) atomicAdd(d.units, (unsigned long long)es.ncell);
+        if (c == 0) {
+            atomicAdd(d.units, (unsigned long long)es.ncell);
+            atomicAdd(d.units + 1, 1ull);
+        }
         if (SUB != SUB_C)
             for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
         double u[NV];

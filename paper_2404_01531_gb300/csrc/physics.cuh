@@ -102,11 +102,44 @@ __device__ __forceinline__ void hard_clamp_flat(double* U) {
     }
 }
 
+// Root s >= 0 of g(s) = c (p2/(1+s)^2 + a2/(1+c+s)^2 - B2)/B2 - s when g(0) > 0
+// (p2, a2: squared norms of the parts of E* across and along B; ib2 = 1/B2).
+// g is decreasing and convex, so Newton from any s0 with g(s0) >= 0 climbs
+// monotonically to the root.  Start: with t = 1 + s and K = c p2/B2, every
+// t with t^2 (t - 1 + c) <= K has g(t - 1) >= 0, and
+// t_a = sqrt(K / (max(c - 1, 0) + K^(1/3))) is such a t (t_a <= K^(1/3)); it is
+// within a few per cent of the root unless the along-B part dominates, so a
+// handful of steps reach the rounding level of s.  ok = false if the last step
+// was not at that level (iteration cap).
+__device__ __forceinline__ double stiff_root(double c, double p2, double a2, double B2, double ib2, bool& ok) {
+    const double K = c * p2 * ib2;
+    double s = 0.0;
+    if (K > 0.0) {
+        const double ta = sqrt(K / ((c > 1.0 ? c - 1.0 : 0.0) + cbrt(K)));
+        s = ta > 1.0 ? ta - 1.0 : 0.0;
+    }
+    double step = 1.0;
+    for (int it = 0; it < 100; ++it) {
+        const double a1 = 1.0 + s, b1 = 1.0 + c + s, w = 1.0 / (a1 * b1);
+        const double u = b1 * w, v = a1 * w;
+        const double pu = p2 * u * u, av = a2 * v * v;
+        const double g = c * ((pu + av) - B2) * ib2 - s;
+        const double dg = -2.0 * c * (pu * u + av * v) * ib2 - 1.0;
+        const double sn = s - g / dg;
+        step = sn - s;
+        if (!(sn > s)) break;
+        s = sn;
+        if (step <= 4e-16 * s) break;
+    }
+    ok = step <= 1e-12 * (s > 1.0 ? s : 1.0);
+    return s;
+}
+
 // Solve U = R + dta G(U) in place (Sec. III.B).  With c = eta dta and E* split
 // along B into E*_par + E*_perp, E(s) = E*_perp/(1+s) + E*_par/(1+c+s); s = 0 when
 // |E(0)|^2 <= B^2, otherwise the root of the decreasing convex function
-// g(s) = c (|E(s)|^2 - B^2)/B^2 - s, reached monotonically by Newton from s = 0.
-// Returns false if Newton hit its iteration cap.
+// g(s) = c (|E(s)|^2 - B^2)/B^2 - s (stiff_root).  Returns false if Newton hit
+// its iteration cap.
 __device__ __forceinline__ bool stiff_solve_flat(double* U, const Dev& d, double dta) {
     U[6] = U[6] / fma(d.kpsi, dta, 1.0);
     U[7] = U[7] / fma(d.kphi, dta, 1.0);
@@ -126,21 +159,8 @@ __device__ __forceinline__ bool stiff_solve_flat(double* U, const Dev& d, double
         E[0] = e0[0]; E[1] = e0[1]; E[2] = e0[2];
         return true;
     }
-    double p2 = dot3(pe, pe), a2 = dot3(pa, pa);
-    // Newton from s = 0 increases monotonically to the root (g decreasing and
-    // convex); stop once a step is at the rounding level of s.
-    double s = 0.0, step = 1.0;
-    for (int it = 0; it < 100; ++it) {
-        double u = 1.0 / (1.0 + s), v = 1.0 / (1.0 + c + s);
-        double g = c * ((p2 * u * u + a2 * v * v) - B2) * ib2 - s;
-        double dg = -2.0 * c * (p2 * u * u * u + a2 * v * v * v) * ib2 - 1.0;
-        double sn = s - g / dg;
-        step = sn - s;
-        if (!(sn > s)) break;
-        s = sn;
-        if (step <= 4e-16 * s) break;
-    }
-    const bool ok = step <= 1e-12 * (s > 1.0 ? s : 1.0);
+    bool ok;
+    const double s = stiff_root(c, dot3(pe, pe), dot3(pa, pa), B2, ib2, ok);
     double u = 1.0 / (1.0 + s), v = 1.0 / (1.0 + c + s);
     E[0] = fma(pe[0], u, pa[0] * v);
     E[1] = fma(pe[1], u, pa[1] * v);

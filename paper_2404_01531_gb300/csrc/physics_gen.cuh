@@ -9,6 +9,7 @@
 //   J~_eta    = alpha eta [(E~.B~)/B~^2 B~ + max(E~^2 - B~^2, 0)/B~^2 E~].
 #pragma once
 #include "ffe_internal.h"
+#include "physics.cuh"
 
 namespace ffe {
 
@@ -161,20 +162,8 @@ __device__ __forceinline__ bool stiff_solve_gen(double* U, const PM& m, const De
     double lp[3], la[3];
     lowr(m, pe, lp);
     lowr(m, pa, la);
-    const double p2 = d3(lp, pe), a2 = d3(la, pa);
-    // Newton from s = 0 increases monotonically to the root; stop at the rounding level of s.
-    double s = 0.0, step = 1.0;
-    for (int it = 0; it < 100; ++it) {
-        const double u = 1.0 / (1.0 + s), v = 1.0 / (1.0 + c + s);
-        const double g = c * ((p2 * u * u + a2 * v * v) - B2) * ib2 - s;
-        const double dg = -2.0 * c * (p2 * u * u * u + a2 * v * v * v) * ib2 - 1.0;
-        const double sn = s - g / dg;
-        step = sn - s;
-        if (!(sn > s)) break;
-        s = sn;
-        if (step <= 4e-16 * s) break;
-    }
-    const bool ok = step <= 1e-12 * (s > 1.0 ? s : 1.0);
+    bool ok;
+    const double s = stiff_root(c, d3(lp, pe), d3(la, pa), B2, ib2, ok);
     const double u = 1.0 / (1.0 + s), v = 1.0 / (1.0 + c + s);
     for (int i = 0; i < 3; ++i) E[i] = fma(pe[i], u, pa[i] * v);
     return ok;

@@ -56,7 +56,8 @@ class Info(ctypes.Structure):
     _fields_ = [("n_elem", ctypes.c_int), ("P", ctypes.c_int), ("np1", ctypes.c_int), ("nc", ctypes.c_int),
                 ("n_dg", ctypes.c_int64), ("n_fd", ctypes.c_int64), ("n_state", ctypes.c_int64),
                 ("dt", ctypes.c_double), ("dxmin", ctypes.c_double), ("t", ctypes.c_double),
-                ("steps", ctypes.c_int64), ("n_fd_elem", ctypes.c_int), ("node_updates", ctypes.c_int64)]
+                ("steps", ctypes.c_int64), ("n_fd_elem", ctypes.c_int), ("node_updates", ctypes.c_int64),
+                ("fd_elem_updates", ctypes.c_int64), ("dg_elem_updates", ctypes.c_int64)]
 
 
 _lib = None

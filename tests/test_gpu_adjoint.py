@@ -108,6 +108,44 @@ def test_luminosity_gradient_matches_oracle_complex_step(ffe):
     ctx.close()
 
 
+def _with(cfg, mu=None, chi=None, omega=None):
+    cfg = dict(cfg)
+    kind, kw = cfg["initial"]
+    kw = dict(kw)
+    if mu is not None:
+        kw["mu"] = mu
+    if chi is not None:
+        kw["chi"] = chi
+    cfg["initial"] = (kind, kw)
+    cfg["params"] = dict(cfg["params"])
+    if omega is not None:
+        cfg["params"]["omega_star"] = omega
+    return cfg
+
+
+def test_luminosity_gradient_matches_central_differences(ffe):
+    """d Lbar/d (mu, chi, Omega) through r = 1.5 over 10 steps against central
+    differences of the GPU forward run with a relative step of 1e-6."""
+    from paper_2404_01531_gb300.adjoint import lbar_forward, luminosity_gradient
+    cfg = _tiny()
+    nsteps, rL = 10, 1.5
+    ctx = ffe.Context(cfg)
+    ctx.set_initial()
+    L, g, _ = luminosity_gradient(ctx, nsteps, r_L=rL, every=4)
+    ctx.close()
+    base = dict(mu=cfg["initial"][1]["mu"], chi=cfg["initial"][1]["chi"], omega=cfg["params"]["omega_star"])
+    for k, name in enumerate(("mu", "chi", "omega")):
+        h = 1e-6 * base[name]
+        vals = []
+        for sgn in (1, -1):
+            c = ffe.Context(_with(cfg, **{name: base[name] + sgn * h}))
+            c.set_initial()
+            vals.append(lbar_forward(c, nsteps, rL))
+            c.close()
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * abs(fd), (name, g[k], fd)
+
+
 def test_autograd_function_step(ffe):
     from paper_2404_01531_gb300.adjoint import Step
     ctx = ffe.Context(_tiny())
