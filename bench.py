@@ -208,10 +208,15 @@ def adjoint_measure(steps=500, every=25, r_L=20.0, fd_check=False):
     import torch
     from paper_2404_01531_gb300 import ffe
     from paper_2404_01531_gb300.adjoint import lbar_forward, luminosity_gradient
+    from paper_2404_01531_gb300.adjoint import freeze_union_mask
     cfg = W.adjoint_pulsar(steps=steps)
-    cfg["params"].update(tci_on=0)
+    cfg["params"].update(tci_on=1)
     ctx = ffe.Context(cfg)
     ctx.set_initial()
+    t_m = time.perf_counter()
+    union = freeze_union_mask(ctx, steps)      # mask frozen from the indicator-on forward pass
+    torch.cuda.synchronize()
+    t_m = time.perf_counter() - t_m
     U0, m0 = (t.clone() for t in ctx.state())
     st = torch.cuda.current_stream()
     ctx.step(3)
@@ -240,7 +245,9 @@ def adjoint_measure(steps=500, every=25, r_L=20.0, fd_check=False):
     L, g, tm = luminosity_gradient(ctx, steps, r_L=r_L, every=every)
     ctx.close()
     res = {"workload": f"rotating dipole (mu, chi, Omega) = (1, 45 deg, 1/6), shell r in [1, 24], "
-                       f"6 wedges x 6x6x12 elements P=5, eta=1e5, {steps} steps, checkpoint every {every}",
+                       f"6 wedges x 6x6x12 elements P=5, eta=1e5, {steps} steps, checkpoint every {every}, "
+                       f"mask frozen as the union of the indicator's masks over a forward pass",
+           "fd_elements": int(union.sum()), "mask_pass_s": t_m,
            "forward_ms_per_step": fwd_ms / steps, "adjoint_step_ms": adj_ms,
            "adjoint_step_over_forward_step": adj_ms / (fwd_ms / steps),
            "gradient_s": tm["forward_s"] + tm["adjoint_s"], "forward_s": fwd_ms / 1e3,
@@ -263,7 +270,9 @@ def adjoint_measure(steps=500, every=25, r_L=20.0, fd_check=False):
                     kw2[name] = base[name] + sgn * h
                 c["initial"] = (kind, kw2)
                 cx = ffe.Context(c)
-                cx.set_initial()
+                cx.set_state(cx.state()[0].clone(), union)
+                cx.set_initial(keep_mask=True)
+                cx.freeze_mask(True)
                 vals.append(lbar_forward(cx, steps, r_L))
                 cx.close()
             fd.append((vals[0] - vals[1]) / (2 * h))

@@ -64,6 +64,7 @@ enum { FFE_METRIC_MINKOWSKI = 0, FFE_METRIC_KERR_SCHILD = 1 };
 enum { FFE_ID_FAST_WAVE = 0, FFE_ID_BREAKDOWN = 1, FFE_ID_CLEANING_MODE = 2,
        FFE_ID_WALD = 3, FFE_ID_DIPOLE = 4 };
 enum { FFE_RELAX = 0, FFE_HARD = 1, FFE_RELAX_THEN_HARD = 2 };
+enum { FFE_INIT_KEEP_MASK = 1 };   /* ffe_set_initial flag */
 
 /* Domain (Sec. III.A; shell: Sec. IV.B).  BOX: [lo, hi], boundary kind per axis
  * (periodic or a physical kind applied at both ends).  SHELL6: six cubed-sphere
@@ -150,6 +151,8 @@ ffe_status ffe_set_initial_batch(ffe_ctx* ctx, int id_kind, const double* id_par
  *   DIPOLE         {mu, delta, chi}      B~ = curl[mu m x x/(r^2+delta^2)^(3/2)], m = (sin chi, 0, cos chi)
  * The data are set on the LGL nodes, then the troubled-cell indicator runs and
  * flagged elements take the data at their subcell centres (Sec. III.C.1/III.C.3).
+ * flags & FFE_INIT_KEEP_MASK: no indicator; the context's current mask is kept
+ * and its FD elements take the data at their subcell centres (fixed-mask runs).
  * Resets time and step counters. */
 ffe_status ffe_set_initial(ffe_ctx* ctx, int id_kind, const double* id_params, int n_params, int flags);
 
@@ -226,13 +229,21 @@ ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host, double et
                               int fd_corrector, const double* Uext_dev, double* dUdt_dev, void* cuda_stream);
 
 /* ---- adjoint (reverse mode) ------------------------------------------------
- * Hand-written vector-Jacobian products of the DG path with every branch
- * frozen as the forward pass took it (piecewise differentiability): the mask
- * must be all DG (FD subcells are not differentiated in this version;
- * FFE_ENOTIMPL otherwise), the rectifier max(E^2-B^2,0), the stiff-solve
- * branch and the sign of S.n at a no-incoming-Poynting face stay as they are at
- * the linearisation point.  Flat-metric shells (FFE_DOMAIN_SHELL6) only.
- * All buffers are device state vectors (DG block used). */
+ * Hand-written vector-Jacobian products of the hybrid DG-FD step with every
+ * discrete decision frozen as the forward pass took it (piecewise
+ * differentiability): the DG/FD mask (which must be frozen, ffe_freeze_mask:
+ * FFE_ESTATE otherwise), the rectifier max(E^2-B^2,0), the stiff-solve branch
+ * and the sign of S.n at a no-incoming-Poynting face.  WENO5-Z weights are
+ * differentiated (they are smooth).  Flat-metric shells (FFE_DOMAIN_SHELL6),
+ * RELAX constraint mode.  All buffers are device state vectors; lambda and the
+ * outputs live on the representation each element uses (DG nodes of DG
+ * elements, cells of FD elements) and are zero on the other one. */
+
+/* Freeze (on != 0) or release the DG/FD mask: while frozen the troubled-cell
+ * indicator is not evaluated, no element switches, and ffe_step advances the
+ * hybrid operator with the current mask.  Released, the indicator setting of
+ * ffe_create applies again.  Invalidates the captured step graph. */
+ffe_status ffe_freeze_mask(ffe_ctx* ctx, int on);
 
 /* out_dev = lambda^T dF/dU at U_dev (F the explicit right-hand side of ffe_rhs);
  * *omega_bar (host, may be NULL) += lambda^T dF/dOmega (star rotation). */

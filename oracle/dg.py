@@ -48,6 +48,21 @@ def external_dg_state(st, disc, e, f, Tbl):
     return src.reshape(src.shape[0], -1)[:, disc.dg_map[e, f]]
 
 
+def external_fd_current(st, disc, met, prm, e, f, Tbl):
+    """J~ at my face nodes of face f from an FD neighbour: the FD->DG projection
+    of the current of its cells, traced like the state.
+    [reading] The current of an exterior state that is a projection is the
+    projection of the current, not the current of the projected state: the
+    projected E~ is not a stiff-solve output, its E~.B~ is of the size of the
+    projection error, and J~_eta = alpha eta (E~.B~) B~/B~^2 would carry it into
+    the q~ flux amplified by eta (unstable for eta dt >> 1 at DG-FD interfaces)."""
+    nb = disc.nbr[e, f]
+    m = _met_at(met["fd"], np.array([nb]), ())
+    jd, jp = ph.current(st["ufd"][:, nb:nb + 1], m, prm["eta"])
+    src = apply_3d(Tbl.R, (jd + jp)[:, 0])
+    return src.reshape(3, -1)[:, disc.dg_map[e, f]]
+
+
 def rhs_dg(st, disc, met, prm):
     """Explicit DG right-hand side for all elements with mask == DG.
 
@@ -76,10 +91,13 @@ def rhs_dg(st, disc, met, prm):
         mf = _met_at(met["dg"], sel, fs)
         nhat, norm = face_normal(ijac[(slice(None), slice(None), slice(None)) + fs], mf, d, s)
         Ue = np.zeros_like(Ui)
+        Jx = {}   # exterior current of faces with an FD neighbour
         for a, e in enumerate(sel):
             nb, kind = disc.nbr[e, f], disc.bc[e, f]
             if nb >= 0:
                 Ue[:, a] = external_dg_state(st, disc, e, f, T)
+                if mask[nb] == FD:
+                    Jx[a] = external_fd_current(st, disc, met, prm, e, f, T)
             elif kind == BC_DIRICHLET:
                 Ue[:, a] = prm["dirichlet"](disc.xyz[:, e][(slice(None),) + fs])
             elif kind == BC_NO_INCOMING:
@@ -91,6 +109,9 @@ def rhs_dg(st, disc, met, prm):
                 raise ValueError("face without neighbour or boundary condition")
         jdi, jpi = ph.current(Ui, mf, prm["eta"])
         jde, jpe = ph.current(Ue, mf, prm["eta"])
+        for a, jx in Jx.items():
+            jde[:, a] = 0.0
+            jpe[:, a] = jx
         Fi = ph.fluxes(Ui, jdi + jpi, mf)
         Fe = ph.fluxes(Ue, jde + jpe, mf)
         Fin = np.einsum('j...,jv...->v...', nhat, Fi)

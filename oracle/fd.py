@@ -51,13 +51,18 @@ def weno5z(v0, v1, v2, v3, v4, eps, q=2):
 
 
 def fill_ghosts(st, disc, sel, met_fn, prm):
-    """Extended cell arrays (9, n, Nc+6, Nc+6, Nc+6) for FD elements `sel`, and
-    the coordinates of every filled cell (for the metric).  Corner/edge ghost
-    regions are never read by the dimension-split scheme and stay NaN."""
+    """Extended cell arrays (9, n, Nc+6, Nc+6, Nc+6) for FD elements `sel`, the
+    coordinates of every filled cell (for the metric), and the current J~ of the
+    ghost cells that come from a DG neighbour (NaN elsewhere).  Corner/edge ghost
+    regions are never read by the dimension-split scheme and stay NaN.
+    [reading] A DG neighbour's ghost cells take its polynomial at its subcell
+    centres for U and, for J~, the same evaluation of its nodal current (not the
+    current of the evaluated state; see dg.external_fd_current)."""
     T = disc.T
     Nc = T.nc
     n = len(sel)
     ext = np.full((9, n, Nc + 2 * NG, Nc + 2 * NG, Nc + 2 * NG), np.nan, dtype=st["ufd"].dtype)
+    jgh = np.full((3,) + ext.shape[1:], np.nan, dtype=st["ufd"].dtype)
     xyz = np.full((3, n) + ext.shape[2:], np.nan)
     inner = (slice(NG, NG + Nc),) * 3
     ext[(slice(None), slice(None)) + inner] = st["ufd"][:, sel]
@@ -76,6 +81,11 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
                 if nb >= 0:
                     src = st["ufd"][:, nb] if st["mask"][nb] == FD else apply_3d(T.P, st["udg"][:, nb])
                     ext[tgt] = src.reshape(9, -1)[:, disc.fd_map[e, f, g]]
+                    if st["mask"][nb] == DG:
+                        m = _met_at(met_fn["dg"], np.array([nb]), ())
+                        jd, jp = ph.current(st["udg"][:, nb:nb + 1], m, prm["eta"])
+                        jsrc = apply_3d(T.P, (jd + jp)[:, 0])
+                        jgh[(slice(None),) + tgt[1:]] = jsrc.reshape(3, -1)[:, disc.fd_map[e, f, g]]
                     xyz[tgt] = disc.xyz_fd[:, nb].reshape(3, -1)[:, disc.fd_map[e, f, g]]
                 else:
                     # ghost centre from the element map continued past the face
@@ -102,7 +112,7 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
                         ext[tgt] = ph.bc_star(outer, disc.xyz_fd[:, e][(slice(None),) + lay], prm["omega"])
                     else:
                         raise ValueError("face without neighbour or boundary condition")
-    return ext, xyz
+    return ext, xyz, jgh
 
 
 def rhs_fd(st, disc, met, prm):
@@ -118,10 +128,11 @@ def rhs_fd(st, disc, met, prm):
     out = np.zeros_like(st["ufd"])
     if len(sel) == 0:
         return out
-    ext, xyz = fill_ghosts(st, disc, sel, met, prm)
+    ext, xyz, jgh = fill_ghosts(st, disc, sel, met, prm)
     mext = met["at"](np.nan_to_num(xyz))
     jd, jp = ph.current(np.nan_to_num(ext), mext, prm["eta"])
-    W = np.concatenate([ext, jd + jp], axis=0)  # 12 reconstructed quantities
+    Jx = np.where(np.isnan(np.real(jgh)), jd + jp, jgh)   # DG-neighbour ghosts: their current
+    W = np.concatenate([ext, Jx], axis=0)  # 12 reconstructed quantities
     mc = _met_at(met["fd"], sel, ())
     ijac = disc.ijac_fd[:, :, sel]
     U = st["ufd"][:, sel]
@@ -157,7 +168,7 @@ def rhs_fd(st, disc, met, prm):
             # cell-centred fluxes either side of each interior face; the
             # element-boundary faces use the ghost cells' fluxes
             mg = met["at"](np.nan_to_num(xyz))
-            Fg = ph.fluxes(np.nan_to_num(ext), jd + jp, mg)
+            Fg = ph.fluxes(np.nan_to_num(ext), Jx, mg)
             def slc(lo, hi):
                 idx = [slice(None), slice(None), slice(None), slice(NG, NG + Nc), slice(NG, NG + Nc), slice(NG, NG + Nc)]
                 idx[ax + 1] = slice(lo, hi)

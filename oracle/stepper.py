@@ -11,14 +11,17 @@ R_s = u_n + dt sum_{j<s} (A_sj F(U_j) + A~_sj G(U_j)).  The explicit column of
 stage 1 is zero, so F is evaluated at U_2, U_3, U_4 only: three right-hand
 sides ("substeps") per step; u_{n+1} = u_n + dt sum_j w_j (F_j + G_j).
 
-[reading] order inside a substep result (U_3, U_4, u_{n+1}):
-  stiff solve -> algebraic clamp (if on) -> filter (DG elements) -> TCI (DG elements).
-[reading] G(U_3), G(U_4) are taken at the solved stage values before the
-filter, so that G_s = (U_s - R_s)/(dt a) holds exactly; the filtered values go
-to the next explicit RHS, the TCI and the step result.  With eta dt >> 1 (the
-regime Sec. III.B aims for), G at the filtered value differs from the implicit
-increment by eta times the removed top mode, and that difference enters
-u_{n+1} (which has no solve) amplified by ~eta dt every step.
+[reading] order inside a substep (U_3, U_4): explicit part R_s -> filter (DG
+elements) -> stiff solve -> algebraic clamp (if on) -> TCI (DG elements); for
+u_{n+1}, which has no solve: R -> filter -> clamp (if on) -> TCI.  The filter
+("after every substep", Sec. III.A) thus acts on each substep's explicit
+update, and every state the explicit right-hand side is evaluated at (U_2, U_3,
+U_4) is a solve output.  Filtering after the solve re-creates a parallel E~ of
+the size of the removed top mode at stage states; with eta dt >> 1 (the regime
+Sec. III.B aims for) the q~ flux J~_eta = alpha eta (E~.B~) B~/B~^2 + ... then
+carries that field amplified by eta, and the all-DG rotating dipole at
+eta = 1e5 diverges.  G_s = G(U_s) = (U_s - R~_s)/(dt a) with R~_s the filtered
+explicit part.
 A DG element the TCI flags after a substep is rolled back: the substep's
 inputs (u_n, the earlier F and G, and the stage state the RHS was taken at) are
 projected to its subcells, the RHS is recomputed with the FD operator using the
@@ -142,20 +145,19 @@ class Stepper:
         hist = dict(un=un, G1=G1, G2=G2)
 
         def substep(Uprev, Fprev, build, proj_keys):
-            """Compute F at Uprev, build the substep result, filter, TCI and roll back.
-            Returns (F, filtered result, result before the filter)."""
+            """Compute F at Uprev, build the substep result (filter and solve
+            inside build), TCI and roll back."""
             nonlocal mask
             Fs = self.rhs(Uprev, mask)
-            Ub = build(Fs, mask)
-            Un = self.filt(Ub, mask)
+            Un = build(Fs, mask)
             if not P.prm["tci_on"]:
-                return Fs, Un, Ub
+                return Fs, Un
             sel = self._sel(mask, DG)
             r = tci_ratio(Un[0][3:6, sel], P.met["dg"], T, sel)
             self.near += [int(e) for e, x in zip(sel, r) if abs(x - thr) <= 1e-12 * thr]
             flagged = sel[r > thr]
             if len(flagged) == 0:
-                return Fs, Un, Ub
+                return Fs, Un
             for e in flagged:
                 mask[e] = FD
                 switched.add(int(e))
@@ -169,40 +171,38 @@ class Stepper:
                 Fs[1][:, e] = Ffd[:, e]
             Un2 = build(Fs, mask)
             Un = (Un[0], Un[1].copy())
-            Ub = (Ub[0], Ub[1].copy())
             for e in flagged:
                 Un[1][:, e] = Un2[1][:, e]
-                Ub[1][:, e] = Un2[1][:, e]
-            return Fs, Un, Ub
+            return Fs, Un
 
         # substep A: F2 = F(U2), U3
         def build3(F2, mk):
             R = self.lin([(1.0, hist["un"]), (dt, F2), (dt * (1 - a), hist["G2"])])
-            return self.solve(R, mk)
-        # G_s at the solved stage value before the filter (module docstring)
-        F2, U3, U3b = substep(U2, None, build3, ["un", "G1", "G2"])
+            return self.solve(self.filt(R, mk), mk)
+        F2, U3 = substep(U2, None, build3, ["un", "G1", "G2"])
         hist["F2"] = F2
-        G3 = self.G(U3b, mask)
+        G3 = self.G(U3, mask)
         hist["G3"] = G3
 
         # substep B: F3 = F(U3), U4
         def build4(F3, mk):
             R = self.lin([(1.0, hist["un"]), (0.25 * dt, hist["F2"]), (0.25 * dt, F3),
                           (dt * b, hist["G1"]), (dt * h, hist["G2"]), (dt * z, hist["G3"])])
-            return self.solve(R, mk)
-        F3, U4, U4b = substep(U3, None, build4, ["un", "F2", "G1", "G2", "G3"])
+            return self.solve(self.filt(R, mk), mk)
+        F3, U4 = substep(U3, None, build4, ["un", "F2", "G1", "G2", "G3"])
         hist["F3"] = F3
-        G4 = self.G(U4b, mask)
+        G4 = self.G(U4, mask)
         hist["G4"] = G4
 
         # substep C: F4 = F(U4), u_{n+1}
         def buildn(F4, mk):
             R = self.lin([(1.0, hist["un"]), (dt / 6, hist["F2"]), (dt / 6, hist["F3"]), (2 * dt / 3, F4),
                           (dt / 6, hist["G2"]), (dt / 6, hist["G3"]), (2 * dt / 3, hist["G4"])])
+            R = self.filt(R, mk)
             if P.prm["mode"] in (1, 2):
                 R = self.pair_map(lambda r, m: ph.hard_clamp(r, m), mk, R)
             return R
-        _, un1, _ = substep(U4, None, buildn, ["un", "F2", "F3", "G2", "G3", "G4"])
+        _, un1 = substep(U4, None, buildn, ["un", "F2", "F3", "G2", "G3", "G4"])
 
         udg, ufd = un1[0].copy(), un1[1].copy()
         # end of step: FD -> DG where admissible with alpha' = alpha + 1

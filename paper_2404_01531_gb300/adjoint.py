@@ -28,6 +28,24 @@ class Step(torch.autograd.Function):
         return lam_out, None
 
 
+def freeze_union_mask(ctx, nsteps):
+    """The troubled-cell mask frozen from a forward pass: advance the hybrid
+    step with the indicator for nsteps from the initial data of ctx, then
+    restart from that initial data with every element the indicator flagged at
+    any step on FD subcells (initial data at their cell centres) and the mask
+    frozen.  Returns the mask."""
+    import torch
+    U0, m0 = (t.clone() for t in ctx.state())
+    union = m0.clone()
+    for _ in range(nsteps):
+        ctx.step(1)
+        torch.bitwise_or(union, ctx.state()[1], out=union)
+    ctx.set_state(U0, union)
+    ctx.set_initial(keep_mask=True)
+    ctx.freeze_mask(True)
+    return union
+
+
 def lbar_forward(ctx, nsteps, r_L=20.0):
     """Lbar = mean of L(u_n), n = 1..nsteps, forward only (no checkpoints);
     the state of ctx is advanced by nsteps."""

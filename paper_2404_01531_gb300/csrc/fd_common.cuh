@@ -1,0 +1,144 @@
+// Helpers shared by the FD-subcell kernels and their reverse mode: scratch
+// layouts (extended blocks, face fluxes), shell geometry of an element, face
+// indexing, and the WENO5-Z interpolation (Sec. III.C.2).
+#pragma once
+#include "ffe_internal.h"
+#include "shellmap.cuh"
+
+namespace ffe {
+
+constexpr int NQ = 12;  // reconstructed quantities: 9 evolved + J~ (3)
+
+__device__ __forceinline__ int64_t ext_size(const Dev& d) {
+    const int64_t ne = d.nc + 2 * GH;
+    return ne * ne * ne;
+}
+// ext layout: [NQ][chunk][ext_size] indexed by position in the chunk
+__device__ __forceinline__ double* ext_at(const Dev& d, int q, int wl) {
+    return d.ext + ((int64_t)q * d.chunk + wl) * ext_size(d);
+}
+__device__ __forceinline__ int64_t nface(const Dev& d) { return (int64_t)(d.nc + 1) * d.nc * d.nc; }
+// flux layout: [3][NV][chunk][nface]; curved meshes keep every physical
+// component j: [3 (k)][3 (j)][NV][chunk][nface]
+__device__ __forceinline__ double* flux_at(const Dev& d, int k, int v, int wl) {
+    return d.flux + (((int64_t)k * NV + v) * d.chunk + wl) * nface(d);
+}
+__device__ __forceinline__ double* flux_at_c(const Dev& d, int k, int j, int v, int wl) {
+    return d.flux + ((((int64_t)k * 3 + j) * NV + v) * d.chunk + wl) * nface(d);
+}
+// shell map of element e (its instance's geometry and its index inside the instance)
+__device__ __forceinline__ ShellGeo shell_for(const Dev& d, int e, int& el) {
+    ShellGeo g;
+    if (d.einst) {
+        const InstInfo& in = d.inst[d.einst[e]];
+        g.r_in = in.r_in;
+        g.c = in.c;
+        g.na = in.na;
+        g.nr = in.nr;
+        el = e - in.e0;
+    } else {
+        g.r_in = d.shell_rin;
+        g.c = d.shell_c;
+        g.na = d.shell_na;
+        g.nr = d.shell_nr;
+        el = e;
+    }
+    return g;
+}
+
+__device__ __forceinline__ void axes_of(int dd, int& t1, int& t2) {
+    t1 = dd == 0 ? 1 : 0;
+    t2 = dd == 2 ? 1 : 2;
+}
+
+// number of listed elements in this chunk
+__device__ __forceinline__ int chunk_n(const Dev& d, int ci, int w0) {
+    const int n = d.counts[ci] - w0;
+    return n < 0 ? 0 : (n > d.chunk ? d.chunk : n);
+}
+
+// WENO5-Z at the face right of v2 from v0..v4 (point-value interpolation
+// candidates, ideal weights (1, 10, 5)/16, Jiang-Shu indicators, Z weights q = 2).
+// The Z weights alpha_k = d_k (1 + tau^2/b_k^2), b_k = beta_k + eps, are scaled
+// by b_0^2 b_1^2 b_2^2 so that the normalised combination needs one division:
+//   A_k = d_k (b_k^2 + tau^2) prod_{j != k} b_j^2,  value = sum A_k p_k / sum A_k.
+// With eps >= 1e-40 every A_k stays above 1e-240, inside the normal range.
+__device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
+    const double p0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
+    const double p1 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
+    const double p2 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
+    const double c13 = 13.0 / 12.0;
+    const double s0a = v0 - 2.0 * v1 + v2, s0b = v0 - 4.0 * v1 + 3.0 * v2;
+    const double s1a = v1 - 2.0 * v2 + v3, s1b = v1 - v3;
+    const double s2a = v2 - 2.0 * v3 + v4, s2b = 3.0 * v2 - 4.0 * v3 + v4;
+    const double b0 = fma(c13 * s0a, s0a, 0.25 * s0b * s0b) + eps;
+    const double b1 = fma(c13 * s1a, s1a, 0.25 * s1b * s1b) + eps;
+    const double b2 = fma(c13 * s2a, s2a, 0.25 * s2b * s2b) + eps;
+    const double t = b0 - b2;
+    const double t2 = t * t;
+    const double q0 = b0 * b0, q1 = b1 * b1, q2 = b2 * b2;
+    const double A0 = (0.0625 * (q0 + t2)) * (q1 * q2);
+    const double A1 = (0.625 * (q1 + t2)) * (q0 * q2);
+    const double A2 = (0.3125 * (q2 + t2)) * (q0 * q1);
+    return fma(A0, p0, fma(A1, p1, A2 * p2)) / (A0 + A1 + A2);
+}
+
+// Reverse mode of weno5z: g[i] += yb d weno5z(v0..v4)/d v_i.  The weights are
+// homogeneous of degree 0 in (b_0, b_1, b_2), so the b_k are first scaled by
+// their maximum; the A_k are then O(1) and their derivatives stay in range.
+__device__ __forceinline__ void weno5z_vjp(double v0, double v1, double v2, double v3, double v4, double eps,
+                                           double yb, double* g) {
+    const double p0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
+    const double p1 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
+    const double p2 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
+    const double c13 = 13.0 / 12.0;
+    const double s0a = v0 - 2.0 * v1 + v2, s0b = v0 - 4.0 * v1 + 3.0 * v2;
+    const double s1a = v1 - 2.0 * v2 + v3, s1b = v1 - v3;
+    const double s2a = v2 - 2.0 * v3 + v4, s2b = 3.0 * v2 - 4.0 * v3 + v4;
+    const double B0 = fma(c13 * s0a, s0a, 0.25 * s0b * s0b) + eps;
+    const double B1 = fma(c13 * s1a, s1a, 0.25 * s1b * s1b) + eps;
+    const double B2 = fma(c13 * s2a, s2a, 0.25 * s2b * s2b) + eps;
+    const double bm = fmax(B0, fmax(B1, B2)), ibm = 1.0 / bm;
+    const double b0 = B0 * ibm, b1 = B1 * ibm, b2 = B2 * ibm;
+    const double t = b0 - b2, t2 = t * t;
+    const double q0 = b0 * b0, q1 = b1 * b1, q2 = b2 * b2;
+    const double A0 = (0.0625 * (q0 + t2)) * (q1 * q2);
+    const double A1 = (0.625 * (q1 + t2)) * (q0 * q2);
+    const double A2 = (0.3125 * (q2 + t2)) * (q0 * q1);
+    const double iS = 1.0 / (A0 + A1 + A2);
+    const double val = fma(A0, p0, fma(A1, p1, A2 * p2)) * iS;
+    const double pb0 = yb * A0 * iS, pb1 = yb * A1 * iS, pb2 = yb * A2 * iS;
+    const double ab0 = yb * (p0 - val) * iS, ab1 = yb * (p1 - val) * iS, ab2 = yb * (p2 - val) * iS;
+    // A0 = d0 (q0 + t^2) q1 q2, A1 = d1 (q1 + t^2) q0 q2, A2 = d2 (q2 + t^2) q0 q1, t = b0 - b2
+    const double bb0 = ab0 * 0.0625 * (2.0 * b0 + 2.0 * t) * q1 * q2 +
+                       ab1 * 0.625 * (2.0 * t * q0 * q2 + (q1 + t2) * 2.0 * b0 * q2) +
+                       ab2 * 0.3125 * (2.0 * t * q0 * q1 + (q2 + t2) * 2.0 * b0 * q1);
+    const double bb1 = ab0 * 0.0625 * (q0 + t2) * 2.0 * b1 * q2 + ab1 * 0.625 * 2.0 * b1 * q0 * q2 +
+                       ab2 * 0.3125 * (q2 + t2) * q0 * 2.0 * b1;
+    const double bb2 = ab0 * 0.0625 * (-2.0 * t * q1 * q2 + (q0 + t2) * q1 * 2.0 * b2) +
+                       ab1 * 0.625 * (-2.0 * t * q0 * q2 + (q1 + t2) * q0 * 2.0 * b2) +
+                       ab2 * 0.3125 * (2.0 * b2 - 2.0 * t) * q0 * q1;
+    // back to the unscaled beta_k (b_k = beta_k / bm; bm is a maximum, whose own
+    // derivative cancels because the weights are scale invariant)
+    const double be0 = bb0 * ibm, be1 = bb1 * ibm, be2 = bb2 * ibm;
+    const double s0ab = be0 * 2.0 * c13 * s0a, s0bb = be0 * 0.5 * s0b;
+    const double s1ab = be1 * 2.0 * c13 * s1a, s1bb = be1 * 0.5 * s1b;
+    const double s2ab = be2 * 2.0 * c13 * s2a, s2bb = be2 * 0.5 * s2b;
+    g[0] += 0.375 * pb0 + s0ab + s0bb;
+    g[1] += -1.25 * pb0 - 0.125 * pb1 - 2.0 * s0ab - 4.0 * s0bb + s1ab + s1bb;
+    g[2] += 1.875 * pb0 + 0.75 * pb1 + 0.375 * pb2 + s0ab + 3.0 * s0bb - 2.0 * s1ab + s2ab + 3.0 * s2bb;
+    g[3] += 0.375 * pb1 + 0.75 * pb2 + s1ab - s1bb - 2.0 * s2ab - 4.0 * s2bb;
+    g[4] += -0.125 * pb2 + s2ab + s2bb;
+}
+
+// face fi of direction k: position m along k, tangential (ta, tb); false past the element's faces
+__device__ __forceinline__ bool face_coords(int64_t fi, int nc, int& m, int& ta, int& tb) {
+    const int64_t nf = (int64_t)(nc + 1) * nc * nc;
+    if (fi >= nf) return false;
+    m = (int)(fi % (nc + 1));
+    ta = (int)((fi / (nc + 1)) % nc);
+    tb = (int)(fi / ((int64_t)(nc + 1) * nc));
+    return true;
+}
+
+}  // namespace ffe

@@ -145,11 +145,16 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int count_index, 
                        Field un, Field F2, Field F3, Field G1, Field G2, Field G3, Field G4,
                        Field Fout, Field Uout, Field Gout, cudaStream_t st);
 int fd_chunks(const Dev& d);
+// extended blocks (U, J~ with ghosts) of the listed FD elements of one chunk
+void launch_fd_fill(const Dev& d, const int* list, int count_index, int w0, Field U, Field J, cudaStream_t st);
+// out += (d RHS_FD/dU)^T L (kernels_adjoint_fd.cu); extb: scratch of the size of d.ext
+void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, double* extb, double* omega_bar,
+                       cudaStream_t st);
 void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F2, Field F3,
                              Field G1, Field G2, Field G3, Field G4, cudaStream_t st);
 void launch_fd2dg(const Dev& d, Field un, cudaStream_t st);
 void launch_tci_ratio(const Dev& d, const double* Udg, double* ratio, cudaStream_t st);
-void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field un, Field F2, Field F3, Field G1,
+void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field J, Field un, Field F2, Field F3, Field G1,
                               Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout, cudaStream_t st);
 void launch_stage12_ks(const Dev& d, Field un, Field Ua, Field G1, Field G2, cudaStream_t st);
 
@@ -161,7 +166,6 @@ struct AdjArgs {
 void launch_rhs_vjp(const Dev& d, Field U, Field L, Field out, double* omega_bar, cudaStream_t st);
 void launch_filter(const Dev& d, Field in, Field out, int nv, int transpose, cudaStream_t st);
 void launch_adj(const Dev& d, int which, AdjArgs a, int sub, cudaStream_t st);
-void launch_adj_G(const Dev& d, Field U, Field G, cudaStream_t st);
 void launch_adj_addG(const Dev& d, Field U, Field Gb, Field io, cudaStream_t st);
 void launch_luminosity(const Dev& d, Field U, const int* elem, const double* lk, const double* wn, int ns,
                        double* partial, int nblocks, Field grad, double scale, cudaStream_t st);

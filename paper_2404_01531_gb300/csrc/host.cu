@@ -288,7 +288,10 @@ struct ffe_ctx {
     bool tuned = false;
     // adjoint work fields (allocated by the first adjoint call)
     bool adj_ready = false;
+    int tci_param = 0;               // the indicator setting of ffe_create
     AdjArgs adj{};
+    bool adj_fd = false;             // the current mask has FD elements
+    double* d_extb = nullptr;        // extended-block adjoint of one FD chunk
     double* d_omega_bar = nullptr;
     double* d_partial = nullptr;
     // luminosity surface (cached per radius)
@@ -630,7 +633,7 @@ void enqueue_step(ffe_ctx* c) {
     for (const S& s : subs) {
         if (!d.ks) launch_current(d, s.Uin, c->J, nullptr, 0, st);
         if (d.curved)
-            launch_dg_substep_curved(d, s.sub, s.Uin, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, s.Fout,
+            launch_dg_substep_curved(d, s.sub, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, s.Fout,
                                      s.Uout, s.Gout, st);
         else
             launch_dg_substep(d, s.sub, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, s.Fout,
@@ -666,7 +669,7 @@ ffe_status autotune(ffe_ctx* c) {
         for (int rep = 0; rep < 3; ++rep) {
             CK(cudaEventRecord(a, c->st));
             if (d.curved)
-                launch_dg_substep_curved(d, SUB_RHS, c->un, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, c->Fs,
+                launch_dg_substep_curved(d, SUB_RHS, c->un, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, c->Fs,
                                          c->Fs, c->G1, c->st);
             else
                 launch_dg_substep(d, SUB_RHS, c->un, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, c->Fs,
@@ -830,7 +833,7 @@ ffe_status init_slots(ffe_ctx* c, const std::vector<unsigned char>& mask) {
 }
 
 // Initial data for all elements (per-instance parameters in batched contexts).
-ffe_status set_initial_impl(ffe_ctx* c, int id_kind) {
+ffe_status set_initial_impl(ffe_ctx* c, int id_kind, bool keep_mask) {
     const Dev& d = c->d;
     auto prm_of = [&](int e) -> const double* {
         return c->batch ? c->id_prm_inst.data() + (size_t)c->h_einst[e] * c->id_nprm : c->id_prm.data();
@@ -847,16 +850,19 @@ ffe_status set_initial_impl(ffe_ctx* c, int id_kind) {
         for (int v = 0; v < NV; ++v) U[v * d.ndg + p] = u[v];
     });
     std::vector<unsigned char> mask(d.E, 0);
-    if (d.tci_on) {
-        double* ratio;
+    if (keep_mask) CK(cudaMemcpy(mask.data(), d.mask, d.E, cudaMemcpyDeviceToHost));
+    if (d.tci_on || keep_mask) {
         ffe_status s;
-        if ((s = dalloc(c, &ratio, d.E))) return s;
-        CK(cudaMemcpy(c->un.p, U.data(), NV * d.ndg * 8, cudaMemcpyHostToDevice));
-        launch_tci_ratio(d, c->un.p, ratio, c->st);
-        std::vector<double> r(d.E);
-        CK(cudaMemcpyAsync(r.data(), ratio, d.E * 8, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        for (int e = 0; e < d.E; ++e) mask[e] = r[e] > d.thr_dgP[host_P(c, e)];
+        if (!keep_mask) {
+            double* ratio;
+            if ((s = dalloc(c, &ratio, d.E))) return s;
+            CK(cudaMemcpy(c->un.p, U.data(), NV * d.ndg * 8, cudaMemcpyHostToDevice));
+            launch_tci_ratio(d, c->un.p, ratio, c->st);
+            std::vector<double> r(d.E);
+            CK(cudaMemcpyAsync(r.data(), ratio, d.E * 8, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            for (int e = 0; e < d.E; ++e) mask[e] = r[e] > d.thr_dgP[host_P(c, e)];
+        }
         if ((s = init_slots(c, mask))) return s;
         MapFn map = ctx_map(c);
         parallel_for(d.E, [&](int64_t e) {
@@ -970,6 +976,7 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     d.mode = params->constraint_mode;
     d.filter_on = params->filter_on;
     d.tci_on = params->tci_on;
+    c->tci_param = params->tci_on;
     d.fd_corr = params->fd_corrector;
     ffe_status s;
     auto bail = [&](ffe_status s) { ffe_destroy(c); return s; };
@@ -1058,6 +1065,7 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
     d.mode = p0.constraint_mode;
     d.filter_on = p0.filter_on;
     d.tci_on = p0.tci_on;
+    c->tci_param = p0.tci_on;
     d.fd_corr = p0.fd_corrector;
     d.curved = 1;
     for (int P : orders) build_tables(P, p0.filter_a, p0.filter_b, p0.tci_M, c->tabs_h[P]);
@@ -1197,7 +1205,7 @@ ffe_status ffe_set_initial_batch(ffe_ctx* c, int id_kind, const double* id_param
     } else {
         c->id_prm.assign(id_params, id_params + n_params);
     }
-    return set_initial_impl(c, id_kind);
+    return set_initial_impl(c, id_kind, (flags & FFE_INIT_KEEP_MASK) != 0);
 }
 
 ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) {
@@ -1205,7 +1213,6 @@ ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int
     if (!c) return fail(FFE_EINVAL, "null context");
     if (id_kind < FFE_ID_FAST_WAVE || id_kind > FFE_ID_DIPOLE) return fail(FFE_EINVAL, "initial data kind %d", id_kind);
     if (n_params < 0 || (n_params > 0 && !id_params)) return fail(FFE_EINVAL, "bad initial-data parameters");
-    (void)flags;
     c->id_kind = id_kind;
     c->id_prm.assign(id_params, id_params + n_params);
     if (c->batch) {
@@ -1213,7 +1220,7 @@ ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int
         c->id_prm_inst.clear();
         for (int i = 0; i < c->n_inst; ++i) c->id_prm_inst.insert(c->id_prm_inst.end(), id_params, id_params + n_params);
     }
-    return set_initial_impl(c, id_kind);
+    return set_initial_impl(c, id_kind, (flags & FFE_INIT_KEEP_MASK) != 0);
 }
 
 ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) {
@@ -1225,7 +1232,8 @@ ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) {
     launch_build_lists(d, c->st);
     launch_current(d, U, c->J, nullptr, 0, c->st);
     if (d.curved)
-        launch_dg_substep_curved(d, SUB_RHS, U, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R, c->G1, c->st);
+        launch_dg_substep_curved(d, SUB_RHS, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R, c->G1,
+                                 c->st);
     else
         launch_dg_substep(d, SUB_RHS, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R, c->G1, c->st);
     launch_fd_substep(d, SUB_RHS, d.fd_list, 1, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, R, R,
@@ -1334,15 +1342,31 @@ ffe_status ffe_launch_count(ffe_ctx* c, int64_t* n) {
     return FFE_OK;
 }
 
+ffe_status ffe_freeze_mask(ffe_ctx* c, int on) {
+    g_err.clear();
+    if (!c) return fail(FFE_EINVAL, "null context");
+    CK(cudaStreamSynchronize(c->st));
+    const int want = on ? 0 : c->tci_param;
+    if (c->d.tci_on != want) {
+        c->d.tci_on = want;
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->gexec = nullptr;
+        c->graph = nullptr;
+    }
+    return FFE_OK;
+}
+
 static ffe_status adjoint_ready(ffe_ctx* c) {
     const Dev& d = c->d;
     if (!d.curved || d.ks || c->batch) return fail(FFE_ENOTIMPL, "the adjoint is built for flat-metric shells");
     if (d.mode == FFE_HARD || d.mode == FFE_RELAX_THEN_HARD) return fail(FFE_ENOTIMPL, "the adjoint of the clamp is not built");
+    if (d.tci_on) return fail(FFE_ESTATE, "the adjoint differentiates a fixed mask: freeze it first (ffe_freeze_mask)");
     std::vector<unsigned char> m(d.E);
     CK(cudaMemcpyAsync(m.data(), d.mask, d.E, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    for (unsigned char x : m)
-        if (x) return fail(FFE_ENOTIMPL, "the adjoint differentiates all-DG masks only (an element is on FD)");
+    c->adj_fd = false;
+    for (unsigned char x : m) c->adj_fd |= x != 0;
     if (c->adj_ready) return FFE_OK;
     AdjArgs& a = c->adj;
     ffe_status s;
@@ -1353,19 +1377,46 @@ static ffe_status adjoint_ready(ffe_ctx* c) {
         if ((s = alloc_field(c, *f, NG))) return s;
     if ((s = dalloc(c, &c->d_omega_bar, 1))) return s;
     if ((s = dalloc(c, &c->d_partial, 1024))) return s;
+    const size_t ne = (size_t)d.nc + 2 * GH;
+    if ((s = dalloc(c, &c->d_extb, (size_t)12 * d.chunk * ne * ne * ne))) return s;
     c->adj_ready = true;
     return FFE_OK;
 }
 
+// out = filter (or its transpose) of in on DG elements; FD blocks are copied
 static ffe_status filter_or_copy(ffe_ctx* c, Field in, Field out, int transpose) {
     const Dev& d = c->d;
-    if (d.filter_on) launch_filter(d, in, out, NV, transpose, c->st);
-    else CK(cudaMemcpyAsync(out.p, in.p, (size_t)NV * d.ndg * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    if (d.filter_on) {
+        launch_filter(d, in, out, NV, transpose, c->st);
+        if (c->adj_fd)
+            CK(cudaMemcpyAsync(out.fd(0), in.fd(0), (size_t)NV * d.nfd * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    } else {
+        CK(cudaMemcpyAsync(out.p, in.p, (size_t)NV * (d.ndg + (c->adj_fd ? d.nfd : 0)) * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->st));
+    }
     return FFE_OK;
 }
 
+// right-hand side of the hybrid operator at U (fixed mask)
 static void rhs_at(ffe_ctx* c, Field U, Field out) {
-    launch_dg_substep_curved(c->d, SUB_RHS, U, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, out, out, c->G1, c->st);
+    const Dev& d = c->d;
+    if (c->adj_fd) launch_current(d, U, c->J, nullptr, 0, c->st);
+    launch_dg_substep_curved(d, SUB_RHS, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, out, out, c->G1,
+                             c->st);
+    if (c->adj_fd)
+        launch_fd_substep(d, SUB_RHS, d.fd_list, 1, U, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, out, out,
+                          c->G1, c->st);
+}
+
+// out = (d RHS/dU)^T L at U for the hybrid operator (fixed mask)
+static void rhs_vjp_at(ffe_ctx* c, Field U, Field L, Field out) {
+    const Dev& d = c->d;
+    cudaMemsetAsync(out.fd(0), 0, (size_t)NV * d.nfd * sizeof(double), c->st);
+    launch_rhs_vjp(d, U, L, out, c->d_omega_bar, c->st);
+    if (c->adj_fd) {
+        launch_current(d, U, c->J, nullptr, 0, c->st);
+        launch_fd_rhs_vjp(d, U, c->J, L, out, c->d_extb, c->d_omega_bar, c->st);
+    }
 }
 
 ffe_status ffe_rhs_vjp(ffe_ctx* c, const double* U_dev, const double* lam_dev, double* out_dev, double* omega_bar) {
@@ -1376,7 +1427,9 @@ ffe_status ffe_rhs_vjp(ffe_ctx* c, const double* U_dev, const double* lam_dev, d
     const Dev& d = c->d;
     Field U{(double*)U_dev, NV, d.ndg, d.nfd}, L{(double*)lam_dev, NV, d.ndg, d.nfd}, O{out_dev, NV, d.ndg, d.nfd};
     CK(cudaMemsetAsync(c->d_omega_bar, 0, sizeof(double), c->st));
-    launch_rhs_vjp(d, U, L, O, c->d_omega_bar, c->st);
+    launch_build_lists(d, c->st);
+    rhs_vjp_at(c, U, L, O);
+    prof_collect(c->st);
     if (omega_bar) {
         double ob = 0.0;
         CK(cudaMemcpyAsync(&ob, c->d_omega_bar, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -1400,32 +1453,36 @@ ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_i
     Field lin{(double*)lam_in_dev, NV, d.ndg, d.nfd};
     a.lam = Field{lam_out_dev, NV, d.ndg, d.nfd};
     launch_build_lists(d, st);
-    // forward recomputation of the step's stages from U_n
+    // forward recomputation of the step's stages from U_n: stage s = 3, 4 is
+    // R_s (explicit part) -> T_s = filter(R_s) -> U_s = S(T_s), G_s = G(U_s)
     launch_adj(d, 0, a, 0, st);
     rhs_at(c, a.U2, a.F2);
     launch_adj(d, 1, a, SUB_A, st);
-    if ((s = filter_or_copy(c, a.T3, a.U3, 0))) return s;
-    launch_adj_G(d, a.T3, a.G3, st);                                    // G at the pre-filter value
+    if ((s = filter_or_copy(c, a.R3, a.T3, 0))) return s;
+    launch_adj(d, 6, a, SUB_A, st);
     rhs_at(c, a.U3, a.F3);
     launch_adj(d, 1, a, SUB_B, st);
-    if ((s = filter_or_copy(c, a.T4, a.U4, 0))) return s;
-    launch_adj_G(d, a.T4, a.G4, st);
+    if ((s = filter_or_copy(c, a.R4, a.T4, 0))) return s;
+    launch_adj(d, 6, a, SUB_B, st);
     rhs_at(c, a.U4, a.F4);
     // reverse
     CK(cudaMemsetAsync(c->d_omega_bar, 0, sizeof(double), st));
-    if ((s = filter_or_copy(c, lin, a.tmp, 1))) return s;               // W-bar
+    if ((s = filter_or_copy(c, lin, a.tmp, 1))) return s;               // W-bar (u_{n+1} = filter(W))
     launch_adj(d, 2, a, 0, st);                                         // seeds
-    launch_rhs_vjp(d, a.U4, a.F4b, a.tmp, c->d_omega_bar, st);          // U4-bar from F4
-    if ((s = filter_or_copy(c, a.tmp, a.tmp2, 1))) return s;            // T4-bar from U4-bar
-    launch_adj_addG(d, a.T4, a.G4b, a.tmp2, st);                        // + G4 taken at T4
+    rhs_vjp_at(c, a.U4, a.F4b, a.tmp);                                  // U4-bar from F4
+    launch_adj_addG(d, a.U4, a.G4b, a.tmp, st);                         // + G4 = G(U4)
+    launch_adj(d, 5, a, SUB_B, st);                                     // T4-bar (tmp2)
+    if ((s = filter_or_copy(c, a.tmp2, a.tmp, 1))) return s;            // R4-bar (tmp)
     launch_adj(d, 3, a, SUB_B, st);
-    launch_rhs_vjp(d, a.U3, a.F3b, a.tmp, c->d_omega_bar, st);
-    if ((s = filter_or_copy(c, a.tmp, a.tmp2, 1))) return s;            // T3-bar from U3-bar
-    launch_adj_addG(d, a.T3, a.G3b, a.tmp2, st);
+    rhs_vjp_at(c, a.U3, a.F3b, a.tmp);
+    launch_adj_addG(d, a.U3, a.G3b, a.tmp, st);
+    launch_adj(d, 5, a, SUB_A, st);                                     // T3-bar
+    if ((s = filter_or_copy(c, a.tmp2, a.tmp, 1))) return s;            // R3-bar
     launch_adj(d, 3, a, SUB_A, st);
-    launch_rhs_vjp(d, a.U2, a.F2b, a.tmp, c->d_omega_bar, st);
+    rhs_vjp_at(c, a.U2, a.F2b, a.tmp);
     launch_adj_addG(d, a.U2, a.G2b, a.tmp, st);                         // U2-bar
     launch_adj(d, 4, a, 0, st);                                         // stages 2, 1 -> lambda_n
+    prof_collect(st);
     if (omega_bar) {
         double ob = 0.0;
         CK(cudaMemcpyAsync(&ob, c->d_omega_bar, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1532,20 +1589,43 @@ ffe_status ffe_initial_tangent(ffe_ctx* c, int which, double* dU_dev) {
     const double mu = c->id_prm.size() > 0 ? c->id_prm[0] : 1.0;
     const double dl = c->id_prm.size() > 1 ? c->id_prm[1] : 0.1;
     const double chi = c->id_prm.size() > 2 ? c->id_prm[2] : 0.0;
-    std::vector<double> xdg(3 * (size_t)d.ndg), T(NV * (size_t)d.ndg, 0.0);
+    std::vector<double> xdg(3 * (size_t)d.ndg), T(NV * (size_t)(d.ndg + d.nfd), 0.0);
+    std::vector<unsigned char> mask(d.E);
     CK(cudaMemcpy(xdg.data(), d.xyz_dg, xdg.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(mask.data(), d.mask, d.E, cudaMemcpyDeviceToHost));
     // B = mu [3 x (m.x) - m (r^2 - 2 delta^2)] / (r^2 + delta^2)^(5/2), m = (sin chi, 0, cos chi)
     const double m[3] = {std::sin(chi), 0.0, std::cos(chi)}, dm[3] = {std::cos(chi), 0.0, -std::sin(chi)};
-    parallel_for(d.ndg, [&](int64_t p) {
-        const double x[3] = {xdg[p], xdg[d.ndg + p], xdg[2 * d.ndg + p]};
+    auto tangent_B = [&](const double* x, double* tb) {
         const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
         const double f = 1.0 / std::pow(r2 + dl * dl, 2.5);
         const double* mm = which == 0 ? m : dm;
         const double scale = which == 0 ? 1.0 : mu;
         const double mx = mm[0] * x[0] + mm[1] * x[1] + mm[2] * x[2];
-        for (int i = 0; i < 3; ++i) T[(3 + i) * d.ndg + p] = scale * f * (3.0 * x[i] * mx - mm[i] * (r2 - 2.0 * dl * dl));
+        for (int i = 0; i < 3; ++i) tb[i] = scale * f * (3.0 * x[i] * mx - mm[i] * (r2 - 2.0 * dl * dl));
+    };
+    // DG nodes of DG elements
+    parallel_for(d.ndg, [&](int64_t p) {
+        if (mask[p / d.nn]) return;
+        const double x[3] = {xdg[p], xdg[d.ndg + p], xdg[2 * d.ndg + p]};
+        double tb[3];
+        tangent_B(x, tb);
+        for (int i = 0; i < 3; ++i) T[(3 + i) * d.ndg + p] = tb[i];
     });
-    CK(cudaMemset(dU_dev, 0, NV * (size_t)(d.ndg + d.nfd) * sizeof(double)));
+    // cells of FD elements (their data is the initial data at the cell centres)
+    MapFn map = ctx_map(c);
+    parallel_for(d.E, [&](int64_t e) {
+        if (!mask[e]) return;
+        const int nc = d.nc;
+        const int64_t base = (int64_t)(d.fd_slot ? c->h_fd_slot[e] : e) * d.ncell;
+        for (int q = 0; q < nc * nc * nc; ++q) {
+            const int cc[3] = {q % nc, (q / nc) % nc, q / (nc * nc)};
+            double xi[3], X[3], ij[3][3], tb[3];
+            for (int a = 0; a < 3; ++a) xi[a] = -1.0 + (cc[a] + 0.5) * 2.0 / nc;
+            map((int)e, xi, X, ij);
+            tangent_B(X, tb);
+            for (int i = 0; i < 3; ++i) T[NV * d.ndg + (3 + i) * d.nfd + base + q] = tb[i];
+        }
+    });
     CK(cudaMemcpy(dU_dev, T.data(), T.size() * 8, cudaMemcpyHostToDevice));
     return FFE_OK;
 }

@@ -16,124 +16,9 @@
 #include "physics.cuh"
 #include "shellmap.cuh"
 #include "stage.cuh"
+#include "adjoint_common.cuh"
 
 namespace ffe {
-
-// Ub += (dJ_drift/dU)^T wd + (dJ_eta/dU)^T wp  (flat metric)
-__device__ __forceinline__ void current_vjp(const double* U, double eta, const double* wd, const double* wp, double* Ub) {
-    const double* E = U;
-    const double* B = U + 3;
-    const double B2 = dot3(B, B);
-    if (B2 == 0.0) return;
-    const double ib2 = 1.0 / B2, q = U[8];
-    const double c[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
-    // drift: J_d = q c / B^2
-    const double s = dot3(wd, c);
-    const double fq = q * ib2;
-    Ub[8] += s * ib2;
-    Ub[0] += fq * (B[1] * wd[2] - B[2] * wd[1]);
-    Ub[1] += fq * (B[2] * wd[0] - B[0] * wd[2]);
-    Ub[2] += fq * (B[0] * wd[1] - B[1] * wd[0]);
-    Ub[3] += fq * (wd[1] * E[2] - wd[2] * E[1]) - 2.0 * fq * s * ib2 * B[0];
-    Ub[4] += fq * (wd[2] * E[0] - wd[0] * E[2]) - 2.0 * fq * s * ib2 * B[1];
-    Ub[5] += fq * (wd[0] * E[1] - wd[1] * E[0]) - 2.0 * fq * s * ib2 * B[2];
-    if (eta == 0.0) return;
-    // eta part: J_p = eta (f B + g E), f = E.B/B^2, g = max(E^2 - B^2, 0)/B^2
-    const double EB = dot3(E, B), E2 = dot3(E, E);
-    const bool act = E2 - B2 > 0.0;
-    const double f = EB * ib2, g = act ? (E2 - B2) * ib2 : 0.0;
-    const double wB = dot3(wp, B), wE = dot3(wp, E);
-    for (int a = 0; a < 3; ++a) {
-        Ub[a] += eta * (wB * B[a] * ib2 + (act ? 2.0 * wE * E[a] * ib2 : 0.0) + g * wp[a]);
-        Ub[3 + a] += eta * (wB * (E[a] * ib2 - 2.0 * EB * B[a] * ib2 * ib2) + f * wp[a] +
-                            (act ? -2.0 * wE * E2 * B[a] * ib2 * ib2 : 0.0));
-    }
-}
-
-// Ub += sum_j (dF^j/dU)^T w[j]  with F^j the flat flux of direction j (J~ in the q~ row)
-__device__ __forceinline__ void flux_t(const double* U, double eta, const double w[3][NV], double* Ub) {
-    double wj[3];
-    for (int j = 0; j < 3; ++j) {
-        const double* x = w[j];
-        // F^j(E^i) = d^ij psi - [ijk] B_k ; F^j(B^i) = d^ij phi + [ijk] E_k
-        Ub[6] += x[j];
-        Ub[7] += x[3 + j];
-        for (int i = 0; i < 3; ++i) {
-            if (i == j) continue;
-            const int k = 3 - i - j;
-            const double sg = ((j - i + 3) % 3 == 1) ? 1.0 : -1.0;
-            Ub[3 + k] -= sg * x[i];
-            Ub[k] += sg * x[3 + i];
-        }
-        Ub[j] += x[6];       // F^j(psi) = E^j
-        Ub[3 + j] += x[7];   // F^j(phi) = B^j
-        wj[j] = x[8];        // F^j(q) = J^j
-    }
-    current_vjp(U, eta, wj, wj, Ub);
-}
-
-// R-bar of the pointwise stiff solve U = S(R) given U-bar (the branch taken by the forward solve).
-__device__ __forceinline__ void solve_vjp(const double* R, const Dev& d, double dta, const double* Ub, double* Rb) {
-    for (int v = 0; v < NV; ++v) Rb[v] = Ub[v];
-    Rb[6] = Ub[6] / fma(d.kpsi, dta, 1.0);
-    Rb[7] = Ub[7] / fma(d.kphi, dta, 1.0);
-    if (d.eta == 0.0) return;
-    const double* E = R;
-    const double* B = R + 3;
-    const double B2 = dot3(B, B);
-    if (B2 == 0.0) return;
-    const double c = d.eta * dta, ib2 = 1.0 / B2;
-    const double EB = dot3(E, B), f = EB * ib2, RR = dot3(E, E);
-    const double* Eb = Ub;
-    const double ebB = dot3(Eb, B);
-    double pa[3], pe[3], e0[3];
-    for (int i = 0; i < 3; ++i) {
-        pa[i] = f * B[i];
-        pe[i] = E[i] - pa[i];
-        e0[i] = fma(pa[i], 1.0 / (1.0 + c), pe[i]);
-    }
-    double u, v;
-    bool nonlin = dot3(e0, e0) > B2;
-    double s = 0.0;
-    if (nonlin) {
-        bool ok;
-        s = stiff_root(c, dot3(pe, pe), dot3(pa, pa), B2, ib2, ok);
-    }
-    u = 1.0 / (1.0 + s);
-    v = 1.0 / (1.0 + c + s);
-    // E_out = u E + (v - u) f B
-    const double k1 = v - u;
-    for (int a = 0; a < 3; ++a) {
-        Rb[a] = u * Eb[a] + k1 * ebB * B[a] * ib2;
-        Rb[3 + a] += k1 * (f * Eb[a] + ebB * (E[a] * ib2 - 2.0 * EB * B[a] * ib2 * ib2));
-    }
-    if (!nonlin) return;
-    // s(R): g(s; E, B) = c (u^2 |E|^2 + (v^2 - u^2) (E.B)^2/B^2 - B^2)/B^2 - s = 0
-    const double u2 = u * u, v2 = v * v;
-    const double par2 = EB * EB * ib2, perp2 = RR - par2;
-    const double gs = -2.0 * c * ib2 * (u2 * u * perp2 + v2 * v * par2) - 1.0;
-    double dEds[3];
-    for (int a = 0; a < 3; ++a) dEds[a] = -u2 * pe[a] - v2 * pa[a];
-    const double es = dot3(Eb, dEds);
-    const double coef = -es / gs;
-    const double inner = u2 * RR + (v2 - u2) * EB * EB * ib2 - B2;
-    for (int a = 0; a < 3; ++a) {
-        const double dgE = c * ib2 * (2.0 * u2 * E[a] + 2.0 * (v2 - u2) * EB * ib2 * B[a]);
-        const double dgB = c * ((2.0 * (v2 - u2) * EB * ib2 * E[a] - 2.0 * (v2 - u2) * EB * EB * ib2 * ib2 * B[a] -
-                                 2.0 * B[a]) * ib2 - 2.0 * ib2 * ib2 * B[a] * inner);
-        Rb[a] += coef * dgE;
-        Rb[3 + a] += coef * dgB;
-    }
-}
-
-// Ub += (dG/dU)^T Gb, G = (-J~_eta, -kpsi psi, -kphi phi)
-__device__ __forceinline__ void G_vjp(const double* U, const Dev& d, const double* Gb, double* Ub) {
-    const double zero[3] = {0.0, 0.0, 0.0};
-    const double wp[3] = {-Gb[0], -Gb[1], -Gb[2]};
-    current_vjp(U, d.eta, zero, wp, Ub);
-    Ub[6] -= d.kpsi * Gb[3];
-    Ub[7] -= d.kphi * Gb[4];
-}
 
 // ---------------------------------------------------------------------------
 template <int P>
@@ -181,6 +66,11 @@ __global__ void __launch_bounds__(AVJ<P>::NT) k_rhs_vjp(Dev d, Field U, Field L,
     for (int w = blockIdx.x; w < d.E; w += gridDim.x) {
         const int e = w;
         const int64_t eb = (int64_t)e * d.nn;
+        if (d.mask[e] != 0) {
+            // FD element: no DG right-hand side; its DG block of the adjoint is zero
+            for (int t = tid; t < NV * nn; t += NT) out.dg(t / nn)[eb + t % nn] = 0.0;
+            continue;
+        }
         const double om = omega_of(d, e);
         double om_acc = 0.0;
         for (int t = tid; t < NV * nn; t += NT) sL[t] = L.dg(t / nn)[eb + t % nn];
@@ -279,6 +169,35 @@ __global__ void __launch_bounds__(AVJ<P>::NT) k_rhs_vjp(Dev d, Field U, Field L,
                         acc[8] -= z[8];
                     }
                 }
+            } else if (d.mask[nb] == 1) {
+                // (b) my lift used the trace of the FD neighbour's FD -> DG projection
+                // (6-point Lagrange per direction) of its cells and of their current as
+                // exterior state and current (the flux is linear in both): scatter into its cells
+                const int f2 = d.nbr_face[e * 6 + f], d2 = f2 >> 1, s2 = f2 & 1;
+                const int u1 = d2 == 0 ? 1 : 0, u2 = d2 == 2 ? 1 : 2;
+                int a2, b2, cn[3];
+                orient_map(d.orient[e * 6 + f], np1, ta, tb, a2, b2);
+                cn[d2] = s2 ? P : 0;
+                cn[u1] = a2;
+                cn[u2] = b2;
+                const int nc = T.nc;
+                const int lo0 = T.f2d_lo[cn[0]], lo1 = T.f2d_lo[cn[1]], lo2 = T.f2d_lo[cn[2]];
+                const int64_t base = fdb(d, nb);
+                double z[NV], zJ[3];
+                // the exterior current is the projection of the cells' J~(U): (dC/d(Ue, Je))^T lambda
+                lift_ext_tJ(n, sc, lm, z, zJ);   // dU -= C
+                for (int n2 = 0; n2 < 6; ++n2)
+                    for (int n1 = 0; n1 < 6; ++n1)
+                        for (int n0 = 0; n0 < 6; ++n0) {
+                            const double wgt = T.F2D[cn[0]][lo0 + n0] * T.F2D[cn[1]][lo1 + n1] * T.F2D[cn[2]][lo2 + n2];
+                            const int64_t cell = base + (lo0 + n0) + nc * ((lo1 + n1) + nc * (lo2 + n2));
+                            double uc[NV], ub[NV], jb[3];
+                            for (int v = 0; v < NV; ++v) { uc[v] = U.fd(v)[cell]; ub[v] = -wgt * z[v]; }
+                            for (int k = 0; k < 3; ++k) jb[k] = -wgt * zJ[k];
+                            current_vjp(uc, d.eta, jb, jb, ub);
+                            for (int v = 0; v < NV; ++v)
+                                if (ub[v] != 0.0) atomicAdd(out.fd(v) + cell, ub[v]);
+                        }
             } else {
                 // (c) the neighbour's lift term at its node used my U as its exterior state
                 const int f2 = d.nbr_face[e * 6 + f], d2 = f2 >> 1, s2 = f2 & 1;
@@ -348,6 +267,7 @@ __global__ void k_filter(Dev d, Field in, Field outf, int nv, int transpose) {
     double* a = sm;
     double* b = sm + nn;
     for (int e = blockIdx.x; e < d.E; e += gridDim.x) {
+        if (d.mask[e] != 0) continue;   // FD elements are not filtered
         const int64_t eb = (int64_t)e * d.nn;
         for (int v = 0; v < nv; ++v) {
             for (int t = threadIdx.x; t < nn; t += blockDim.x) a[t] = in.dg(v)[eb + t];
@@ -378,14 +298,34 @@ void launch_filter(const Dev& d, Field in, Field out, int nv, int transpose, cud
 }
 
 // ---------------------------------------------------------------------------
-// Pointwise kernels of the adjoint step (DG nodes; the mask is all DG).
+// Pointwise kernels of the adjoint step over the active points: DG nodes of
+// DG elements and cells of FD elements (fixed mask).
+
+// Point p of [0, ndg + nfd): DG node p, else FD cell p - ndg; q is its index in
+// its block.  False unless the point belongs to its element's representation.
+__device__ __forceinline__ bool act_point(const Dev& d, int64_t p, bool& isfd, int64_t& q) {
+    if (p < d.ndg) {
+        isfd = false;
+        q = p;
+        return d.mask[p / d.nn] == 0;
+    }
+    isfd = true;
+    q = p - d.ndg;
+    const int sl = (int)(q / d.ncell);
+    const int e = d.slot_elem ? d.slot_elem[sl] : sl;
+    return e >= 0 && d.mask[e] == 1;
+}
+__device__ __forceinline__ double* fp(const Field& f, int v, bool isfd) { return isfd ? f.fd(v) : f.dg(v); }
 
 // forward recomputation: stage 1-2 (U2, G1, G2)
 __global__ void k_adj_s12(Dev d, AdjArgs a) {
     const double dt = d.dt, dta = dt * IM_A;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_point(d, p, isfd, q)) continue;
         double u[NV], U1[NV], g1[NG], g2[NG];
-        for (int v = 0; v < NV; ++v) { u[v] = a.un.dg(v)[p]; U1[v] = u[v]; }
+        for (int v = 0; v < NV; ++v) { u[v] = fp(a.un, v, isfd)[q]; U1[v] = u[v]; }
         stiff_solve_flat(U1, d, dta);
         implicit_G_flat(U1, d, g1);
         u[0] = fma(-dta, g1[0], u[0]);
@@ -395,8 +335,8 @@ __global__ void k_adj_s12(Dev d, AdjArgs a) {
         u[7] = fma(-dta, g1[4], u[7]);
         stiff_solve_flat(u, d, dta);
         implicit_G_flat(u, d, g2);
-        for (int v = 0; v < NV; ++v) a.U2.dg(v)[p] = u[v];
-        for (int c = 0; c < NG; ++c) { a.G1.dg(c)[p] = g1[c]; a.G2.dg(c)[p] = g2[c]; }
+        for (int v = 0; v < NV; ++v) fp(a.U2, v, isfd)[q] = u[v];
+        for (int c = 0; c < NG; ++c) { fp(a.G1, c, isfd)[q] = g1[c]; fp(a.G2, c, isfd)[q] = g2[c]; }
     }
 }
 
@@ -405,38 +345,46 @@ __global__ void k_adj_comb(Dev d, AdjArgs a, int sub) {
     const double dt = d.dt;
     const int gv[NG] = {0, 1, 2, 6, 7};
     const double z = 0.5 - IM_B - IM_H - IM_A;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_point(d, p, isfd, q)) continue;
         double u[NV];
-        for (int v = 0; v < NV; ++v) u[v] = a.un.dg(v)[p];
+        for (int v = 0; v < NV; ++v) u[v] = fp(a.un, v, isfd)[q];
         if (sub == SUB_A) {
-            for (int v = 0; v < NV; ++v) u[v] = fma(dt, a.F2.dg(v)[p], u[v]);
-            for (int c = 0; c < NG; ++c) u[gv[c]] = fma(dt * (1.0 - IM_A), a.G2.dg(c)[p], u[gv[c]]);
+            for (int v = 0; v < NV; ++v) u[v] = fma(dt, fp(a.F2, v, isfd)[q], u[v]);
+            for (int c = 0; c < NG; ++c) u[gv[c]] = fma(dt * (1.0 - IM_A), fp(a.G2, c, isfd)[q], u[gv[c]]);
         } else if (sub == SUB_B) {
-            for (int v = 0; v < NV; ++v) u[v] = fma(0.25 * dt, a.F2.dg(v)[p] + a.F3.dg(v)[p], u[v]);
+            for (int v = 0; v < NV; ++v) u[v] = fma(0.25 * dt, fp(a.F2, v, isfd)[q] + fp(a.F3, v, isfd)[q], u[v]);
             for (int c = 0; c < NG; ++c)
-                u[gv[c]] = fma(dt, IM_B * a.G1.dg(c)[p] + IM_H * a.G2.dg(c)[p] + z * a.G3.dg(c)[p], u[gv[c]]);
+                u[gv[c]] = fma(dt, IM_B * fp(a.G1, c, isfd)[q] + IM_H * fp(a.G2, c, isfd)[q] + z * fp(a.G3, c, isfd)[q], u[gv[c]]);
         } else {
             for (int v = 0; v < NV; ++v)
-                u[v] = fma(dt, (a.F2.dg(v)[p] + a.F3.dg(v)[p]) * (1.0 / 6.0) + a.F4.dg(v)[p] * (2.0 / 3.0), u[v]);
+                u[v] = fma(dt, (fp(a.F2, v, isfd)[q] + fp(a.F3, v, isfd)[q]) * (1.0 / 6.0) + fp(a.F4, v, isfd)[q] * (2.0 / 3.0), u[v]);
             for (int c = 0; c < NG; ++c)
-                u[gv[c]] = fma(dt, (a.G2.dg(c)[p] + a.G3.dg(c)[p]) * (1.0 / 6.0) + a.G4.dg(c)[p] * (2.0 / 3.0), u[gv[c]]);
+                u[gv[c]] = fma(dt, (fp(a.G2, c, isfd)[q] + fp(a.G3, c, isfd)[q]) * (1.0 / 6.0) + fp(a.G4, c, isfd)[q] * (2.0 / 3.0), u[gv[c]]);
         }
         const Field& R = sub == SUB_A ? a.R3 : (sub == SUB_B ? a.R4 : a.W);
-        for (int v = 0; v < NV; ++v) R.dg(v)[p] = u[v];
-        if (sub != SUB_C) {
-            stiff_solve_flat(u, d, dt * IM_A);
-            const Field& Tt = sub == SUB_A ? a.T3 : a.T4;
-            for (int v = 0; v < NV; ++v) Tt.dg(v)[p] = u[v];
-        }
+        for (int v = 0; v < NV; ++v) fp(R, v, isfd)[q] = u[v];
     }
 }
 
-__global__ void k_adj_G(Dev d, Field U, Field G) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+// forward recomputation: U_s = S(T_s) with T_s the filtered explicit part, G_s = G(U_s)
+__global__ void k_adj_solve(Dev d, AdjArgs a, int sub) {
+    const double dta = d.dt * IM_A;
+    const Field& Tt = sub == SUB_A ? a.T3 : a.T4;
+    const Field& Us = sub == SUB_A ? a.U3 : a.U4;
+    const Field& Gs = sub == SUB_A ? a.G3 : a.G4;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_point(d, p, isfd, q)) continue;
         double u[NV], g[NG];
-        for (int v = 0; v < NV; ++v) u[v] = U.dg(v)[p];
+        for (int v = 0; v < NV; ++v) u[v] = fp(Tt, v, isfd)[q];
+        stiff_solve_flat(u, d, dta);
         implicit_G_flat(u, d, g);
-        for (int c = 0; c < NG; ++c) G.dg(c)[p] = g[c];
+        for (int v = 0; v < NV; ++v) fp(Us, v, isfd)[q] = u[v];
+        for (int c = 0; c < NG; ++c) fp(Gs, c, isfd)[q] = g[c];
     }
 }
 
@@ -445,60 +393,82 @@ __global__ void k_adj_G(Dev d, Field U, Field G) {
 __global__ void k_adj_seed(Dev d, AdjArgs a) {
     const double dt = d.dt;
     const int gv[NG] = {0, 1, 2, 6, 7};
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_point(d, p, isfd, q)) continue;
         for (int v = 0; v < NV; ++v) {
-            const double w = a.tmp.dg(v)[p];
-            a.ubar.dg(v)[p] = w;
-            a.F2b.dg(v)[p] = dt / 6.0 * w;
-            a.F3b.dg(v)[p] = dt / 6.0 * w;
-            a.F4b.dg(v)[p] = 2.0 * dt / 3.0 * w;
+            const double w = fp(a.tmp, v, isfd)[q];
+            fp(a.ubar, v, isfd)[q] = w;
+            fp(a.F2b, v, isfd)[q] = dt / 6.0 * w;
+            fp(a.F3b, v, isfd)[q] = dt / 6.0 * w;
+            fp(a.F4b, v, isfd)[q] = 2.0 * dt / 3.0 * w;
         }
         for (int c = 0; c < NG; ++c) {
-            const double w = a.tmp.dg(gv[c])[p];
-            a.G1b.dg(c)[p] = 0.0;
-            a.G2b.dg(c)[p] = dt / 6.0 * w;
-            a.G3b.dg(c)[p] = dt / 6.0 * w;
-            a.G4b.dg(c)[p] = 2.0 * dt / 3.0 * w;
+            const double w = fp(a.tmp, gv[c], isfd)[q];
+            fp(a.G1b, c, isfd)[q] = 0.0;
+            fp(a.G2b, c, isfd)[q] = dt / 6.0 * w;
+            fp(a.G3b, c, isfd)[q] = dt / 6.0 * w;
+            fp(a.G4b, c, isfd)[q] = 2.0 * dt / 3.0 * w;
         }
     }
 }
 
 // (2) tmp = U-bar of stage U_s: RHS-vjp result (in tmp) + G-vjp of Gs-bar at U_s
 __global__ void k_adj_addG(Dev d, Field U, Field Gb, Field io) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_point(d, p, isfd, q)) continue;
         double u[NV], gb[NG], ub[NV];
-        for (int v = 0; v < NV; ++v) { u[v] = U.dg(v)[p]; ub[v] = io.dg(v)[p]; }
-        for (int c = 0; c < NG; ++c) gb[c] = Gb.dg(c)[p];
+        for (int v = 0; v < NV; ++v) { u[v] = fp(U, v, isfd)[q]; ub[v] = fp(io, v, isfd)[q]; }
+        for (int c = 0; c < NG; ++c) gb[c] = fp(Gb, c, isfd)[q];
         G_vjp(u, d, gb, ub);
-        for (int v = 0; v < NV; ++v) io.dg(v)[p] = ub[v];
+        for (int v = 0; v < NV; ++v) fp(io, v, isfd)[q] = ub[v];
     }
 }
 
-// (3) given T-bar (in tmp2, the filter transpose of U_s-bar): R-bar = solve_vjp(R, T-bar)
-//     and the contributions of R = un + dt(...) to u-bar, F-bar, G-bar
+// (2b) T-bar (in tmp2) = solve_vjp(T_s, U_s-bar in tmp)
+__global__ void k_adj_solve_back(Dev d, AdjArgs a, int sub) {
+    const double dta = d.dt * IM_A;
+    const Field& Tt = sub == SUB_A ? a.T3 : a.T4;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_point(d, p, isfd, q)) continue;
+        double t[NV], ub[NV], tb[NV];
+        for (int v = 0; v < NV; ++v) { t[v] = fp(Tt, v, isfd)[q]; ub[v] = fp(a.tmp, v, isfd)[q]; }
+        solve_vjp(t, d, dta, ub, tb);
+        for (int v = 0; v < NV; ++v) fp(a.tmp2, v, isfd)[q] = tb[v];
+    }
+}
+
+// (3) given R-bar (in tmp, the filter transpose of T-bar): the contributions of
+//     R = un + dt (...) to u-bar, F-bar, G-bar
 __global__ void k_adj_back_comb(Dev d, AdjArgs a, int sub) {
     const double dt = d.dt;
     const int gv[NG] = {0, 1, 2, 6, 7};
     const double z = 0.5 - IM_B - IM_H - IM_A;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
-        double r[NV], tb[NV], rb[NV];
-        const Field& R = sub == SUB_A ? a.R3 : a.R4;
-        for (int v = 0; v < NV; ++v) { r[v] = R.dg(v)[p]; tb[v] = a.tmp2.dg(v)[p]; }
-        solve_vjp(r, d, dt * IM_A, tb, rb);
-        for (int v = 0; v < NV; ++v) a.ubar.dg(v)[p] += rb[v];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_point(d, p, isfd, q)) continue;
+        double rb[NV];
+        for (int v = 0; v < NV; ++v) rb[v] = fp(a.tmp, v, isfd)[q];
+        for (int v = 0; v < NV; ++v) fp(a.ubar, v, isfd)[q] += rb[v];
         if (sub == SUB_B) {
             for (int v = 0; v < NV; ++v) {
-                a.F2b.dg(v)[p] += 0.25 * dt * rb[v];
-                a.F3b.dg(v)[p] += 0.25 * dt * rb[v];
+                fp(a.F2b, v, isfd)[q] += 0.25 * dt * rb[v];
+                fp(a.F3b, v, isfd)[q] += 0.25 * dt * rb[v];
             }
             for (int c = 0; c < NG; ++c) {
-                a.G1b.dg(c)[p] += dt * IM_B * rb[gv[c]];
-                a.G2b.dg(c)[p] += dt * IM_H * rb[gv[c]];
-                a.G3b.dg(c)[p] += dt * z * rb[gv[c]];
+                fp(a.G1b, c, isfd)[q] += dt * IM_B * rb[gv[c]];
+                fp(a.G2b, c, isfd)[q] += dt * IM_H * rb[gv[c]];
+                fp(a.G3b, c, isfd)[q] += dt * z * rb[gv[c]];
             }
         } else {
-            for (int v = 0; v < NV; ++v) a.F2b.dg(v)[p] += dt * rb[v];
-            for (int c = 0; c < NG; ++c) a.G2b.dg(c)[p] += dt * (1.0 - IM_A) * rb[gv[c]];
+            for (int v = 0; v < NV; ++v) fp(a.F2b, v, isfd)[q] += dt * rb[v];
+            for (int c = 0; c < NG; ++c) fp(a.G2b, c, isfd)[q] += dt * (1.0 - IM_A) * rb[gv[c]];
         }
     }
 }
@@ -506,9 +476,16 @@ __global__ void k_adj_back_comb(Dev d, AdjArgs a, int sub) {
 // (4) stages 2 and 1: U2-bar in tmp; recompute U1, R2 from un
 __global__ void k_adj_back_s12(Dev d, AdjArgs a) {
     const double dta = d.dt * IM_A;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_point(d, p, isfd, q)) {
+            // lambda_n is zero on the representation an element does not use
+            for (int v = 0; v < NV; ++v) fp(a.lam, v, isfd)[q] = 0.0;
+            continue;
+        }
         double un[NV], U1[NV], R2[NV], g1[NG], u2b[NV], r2b[NV], g1b[NG], u1b[NV], r1b[NV];
-        for (int v = 0; v < NV; ++v) { un[v] = a.un.dg(v)[p]; U1[v] = un[v]; u2b[v] = a.tmp.dg(v)[p]; }
+        for (int v = 0; v < NV; ++v) { un[v] = fp(a.un, v, isfd)[q]; U1[v] = un[v]; u2b[v] = fp(a.tmp, v, isfd)[q]; }
         stiff_solve_flat(U1, d, dta);
         implicit_G_flat(U1, d, g1);
         for (int v = 0; v < NV; ++v) R2[v] = un[v];
@@ -519,34 +496,35 @@ __global__ void k_adj_back_s12(Dev d, AdjArgs a) {
         R2[7] = fma(-dta, g1[4], R2[7]);
         solve_vjp(R2, d, dta, u2b, r2b);
         const int gv[NG] = {0, 1, 2, 6, 7};
-        for (int c = 0; c < NG; ++c) g1b[c] = a.G1b.dg(c)[p] - dta * r2b[gv[c]];
+        for (int c = 0; c < NG; ++c) g1b[c] = fp(a.G1b, c, isfd)[q] - dta * r2b[gv[c]];
         for (int v = 0; v < NV; ++v) u1b[v] = 0.0;
         G_vjp(U1, d, g1b, u1b);
         solve_vjp(un, d, dta, u1b, r1b);
-        for (int v = 0; v < NV; ++v) a.lam.dg(v)[p] = a.ubar.dg(v)[p] + r2b[v] + r1b[v];
+        for (int v = 0; v < NV; ++v) fp(a.lam, v, isfd)[q] = fp(a.ubar, v, isfd)[q] + r2b[v] + r1b[v];
     }
 }
 
 void launch_adj(const Dev& d, int which, AdjArgs a, int sub, cudaStream_t st) {
     const int grid = 152 * 8;
+    prof_begin("adj_pointwise", st);
     switch (which) {
         case 0: k_adj_s12<<<grid, 256, 0, st>>>(d, a); break;
         case 1: k_adj_comb<<<grid, 256, 0, st>>>(d, a, sub); break;
         case 2: k_adj_seed<<<grid, 256, 0, st>>>(d, a); break;
         case 3: k_adj_back_comb<<<grid, 256, 0, st>>>(d, a, sub); break;
         case 4: k_adj_back_s12<<<grid, 256, 0, st>>>(d, a); break;
+        case 5: k_adj_solve_back<<<grid, 256, 0, st>>>(d, a, sub); break;
+        case 6: k_adj_solve<<<grid, 256, 0, st>>>(d, a, sub); break;
         default: break;
     }
-    g_launch_counter += 1;
-}
-
-void launch_adj_G(const Dev& d, Field U, Field G, cudaStream_t st) {
-    k_adj_G<<<152 * 8, 256, 0, st>>>(d, U, G);
+    prof_end(st);
     g_launch_counter += 1;
 }
 
 void launch_adj_addG(const Dev& d, Field U, Field Gb, Field io, cudaStream_t st) {
+    prof_begin("adj_pointwise", st);
     k_adj_addG<<<152 * 8, 256, 0, st>>>(d, U, Gb, io);
+    prof_end(st);
     g_launch_counter += 1;
 }
 
@@ -568,12 +546,33 @@ __global__ void k_luminosity(Dev d, Field U, LumArgs la, double* out, Field grad
         const int s = t / nf, ij = t % nf;
         const int e = la.elem[s];
         const int64_t eb = (int64_t)e * d.nn;
+        const bool fde = d.mask[e] == 1;
+        const Tables& T = d.tabs[d.P];
+        const int nc = T.nc, i0 = ij % np1, j0 = ij / np1;
+        const int64_t fb = fde ? fdb(d, e) : 0;
+        // node value of variable v at (i0, j0, k): DG node, or the FD -> DG
+        // projection (6-point Lagrange per direction) of an FD element's cells
+        auto nodal = [&](int v, int k) -> double {
+            if (!fde) return U.dg(v)[eb + ij + nf * k];
+            const int lo0 = T.f2d_lo[i0], lo1 = T.f2d_lo[j0], lo2 = T.f2d_lo[k];
+            double a2 = 0.0;
+            for (int n2 = 0; n2 < 6; ++n2) {
+                double a1 = 0.0;
+                for (int n1 = 0; n1 < 6; ++n1) {
+                    const double* row = U.fd(v) + fb + lo0 + nc * ((lo1 + n1) + nc * (lo2 + n2));
+                    double a0 = 0.0;
+                    for (int n0 = 0; n0 < 6; ++n0) a0 = fma(T.F2D[i0][lo0 + n0], row[n0], a0);
+                    a1 = fma(T.F2D[j0][lo1 + n1], a0, a1);
+                }
+                a2 = fma(T.F2D[k][lo2 + n2], a1, a2);
+            }
+            return a2;
+        };
         double E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
         for (int k = 0; k < np1; ++k) {
-            const int64_t p = eb + ij + nf * k;
             for (int a = 0; a < 3; ++a) {
-                E[a] = fma(la.lk[k], U.dg(a)[p], E[a]);
-                B[a] = fma(la.lk[k], U.dg(3 + a)[p], B[a]);
+                E[a] = fma(la.lk[k], nodal(a, k), E[a]);
+                B[a] = fma(la.lk[k], nodal(3 + a, k), B[a]);
             }
         }
         const double* w = la.wn + ((int64_t)s * nf + ij) * 4;
@@ -585,12 +584,26 @@ __global__ void k_luminosity(Dev d, Field U, LumArgs la, double* out, Field grad
             const double gE[3] = {B[1] * r[2] - B[2] * r[1], B[2] * r[0] - B[0] * r[2], B[0] * r[1] - B[1] * r[0]};
             const double gB[3] = {r[1] * E[2] - r[2] * E[1], r[2] * E[0] - r[0] * E[2], r[0] * E[1] - r[1] * E[0]};
             for (int k = 0; k < np1; ++k) {
-                const int64_t p = eb + ij + nf * k;
                 const double f = scale * w[0] * la.lk[k];
-                for (int a = 0; a < 3; ++a) {
-                    grad.dg(a)[p] += f * gE[a];
-                    grad.dg(3 + a)[p] += f * gB[a];
+                if (!fde) {
+                    const int64_t p = eb + ij + nf * k;
+                    for (int a = 0; a < 3; ++a) {
+                        grad.dg(a)[p] += f * gE[a];
+                        grad.dg(3 + a)[p] += f * gB[a];
+                    }
+                    continue;
                 }
+                const int lo0 = T.f2d_lo[i0], lo1 = T.f2d_lo[j0], lo2 = T.f2d_lo[k];
+                for (int n2 = 0; n2 < 6; ++n2)
+                    for (int n1 = 0; n1 < 6; ++n1)
+                        for (int n0 = 0; n0 < 6; ++n0) {
+                            const double wgt = f * T.F2D[i0][lo0 + n0] * T.F2D[j0][lo1 + n1] * T.F2D[k][lo2 + n2];
+                            const int64_t cell = fb + lo0 + n0 + nc * ((lo1 + n1) + nc * (lo2 + n2));
+                            for (int a = 0; a < 3; ++a) {
+                                atomicAdd(grad.fd(a) + cell, wgt * gE[a]);
+                                atomicAdd(grad.fd(3 + a) + cell, wgt * gB[a]);
+                            }
+                        }
             }
         }
     }

@@ -5,8 +5,9 @@
 //           - sum_faces (|grad xi^d|_gamma / w0) (F*.n^ - F_int.n^)
 // with F^j the physical fluxes at the nodes (Sec. II.A), the inverse Jacobian
 // of the element map at each node, the Rusanov flux with lambda = alpha +
-// |beta.n^|, then the same IMEX stage, clamp, filter and indicator as the box
-// kernel.  The stiff solve, clamp and indicator use the gamma inner product.
+// |beta.n^|, then the same stage order as the box kernel (explicit part,
+// filter, stiff solve, clamp, indicator).  The stiff solve, clamp and indicator
+// use the gamma inner product.
 #include "ffe_internal.h"
 #include "physics.cuh"
 #include "physics_gen.cuh"
@@ -160,7 +161,8 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
             const double norm = sqrt(d3(nu, nl));
             const double inrm = 1.0 / norm;
             for (int i = 0; i < 3; ++i) nl[i] *= inrm;
-            double Ui[NV], Ue[NV];
+            double Ui[NV], Ue[NV], Je[3];
+            bool jx = false;   // exterior current given (FD neighbour), not J~(Ue)
             for (int v = 0; v < NV; ++v) Ui[v] = sU[v * nn + me];
             const int nb = d.nbr[e * 6 + f];
             if (nb >= 0) {
@@ -170,11 +172,15 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                     const int64_t q = (int64_t)nb * d.nn + cn[0] + np1 * (cn[1] + np1 * cn[2]);
                     for (int v = 0; v < NV; ++v) Ue[v] = a.Uin.dg(v)[q];
                 } else {
+                    // FD->DG projection (6-point stencils) of the neighbour's cells and of
+                    // their current J~ (the current of a projected state would carry its
+                    // projection error in E~.B~ amplified by eta into the q~ flux)
+                    jx = true;
                     const int nc = T.nc;
                     const int lo0 = T.f2d_lo[cn[0]], lo1 = T.f2d_lo[cn[1]], lo2 = T.f2d_lo[cn[2]];
                     const int64_t base = fdb(d, nb);
-                    for (int v = 0; v < NV; ++v) {
-                        const double* src = a.Uin.fd(v) + base;
+                    for (int v = 0; v < NV + 3; ++v) {
+                        const double* src = v < NV ? a.Uin.fd(v) + base : a.J.fd(3 + v - NV) + base;
                         double acc = 0.0;
                         for (int n2 = 0; n2 < 6; ++n2) {
                             double a2 = 0.0;
@@ -186,7 +192,8 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                             }
                             acc = fma(T.F2D[cn[2]][lo2 + n2], a2, acc);
                         }
-                        Ue[v] = acc;
+                        if (v < NV) Ue[v] = acc;
+                        else Je[v - NV] = acc;
                     }
                 }
             } else {
@@ -203,7 +210,8 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                 }
             }
             double Fe[3][NV], jde[3];
-            fluxes_at<KS>(Ue, mf, d.eta, Fe, jde);
+            if (jx) flux_gen(Ue, Je, mf, Fe);
+            else fluxes_at<KS>(Ue, mf, d.eta, Fe, jde);
             const double lam = mf.a + fabs(d3(mf.b, nl));
             const double sc = 0.5 * norm * w0inv;
             for (int v = 0; v < NV; ++v) {
@@ -234,7 +242,7 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
             if (SUB != SUB_C)
                 for (int v = 0; v < NV; ++v) a.Fout.dg(v)[eb + tid] = du[v];
             if (KS) {
-                // stage combination with the metric-aware solve and clamp
+                // explicit part of the stage (the metric-aware solve and clamp follow the filter)
                 const int gv[NG] = {0, 1, 2, 6, 7};
                 for (int v = 0; v < NV; ++v) u[v] = a.un.dg(v)[eb + tid];
                 if (SUB == SUB_A) {
@@ -251,17 +259,8 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                     for (int c = 0; c < NG; ++c)
                         u[gv[c]] = fma(dt, (a.G2.dg(c)[eb + tid] + a.G3.dg(c)[eb + tid]) * (1.0 / 6.0) + a.G4.dg(c)[eb + tid] * (2.0 / 3.0), u[gv[c]]);
                 }
-                if (SUB != SUB_C && !stiff_solve_gen(u, m, d, dt * IM_A)) atomic_status(d, 2);
-                if (d.mode != FFE_RELAX) hard_clamp_gen(u, m);
             } else {
-                substep_combine(d, SUB, du, eb + tid, false, a, dt, u);
-            }
-            if (SUB != SUB_C) {
-                // G at the solved stage value, before the filter: G_s = (U_s - R_s)/(dt a)
-                double g[NG];
-                if (KS) implicit_G_gen(u, m, d, g);
-                else implicit_G_flat(u, d, g);
-                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
+                substep_explicit(d, SUB, du, eb + tid, false, a, dt, u);
             }
         }
         __syncthreads();
@@ -283,6 +282,21 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                     }
                 }
                 __syncthreads();
+            }
+        }
+        // implicit part after the filter; G at the stage value: G_s = (U_s - R~_s)/(dt a)
+        if (act) {
+            if (KS) {
+                if (SUB != SUB_C && !stiff_solve_gen(u, m, d, dt * IM_A)) atomic_status(d, 2);
+                if (d.mode != FFE_RELAX) hard_clamp_gen(u, m);
+            } else {
+                substep_implicit(d, SUB, dt, u);
+            }
+            if (SUB != SUB_C) {
+                double g[NG];
+                if (KS) implicit_G_gen(u, m, d, g);
+                else implicit_G_flat(u, d, g);
+                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
             }
         }
         bool flagged = false;
@@ -380,9 +394,9 @@ static void curved_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_
 #undef FFE_LAUNCH_C
 }
 
-void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field un, Field F2, Field F3, Field G1, Field G2,
-                              Field G3, Field G4, Field Fout, Field Uout, Field Gout, cudaStream_t st) {
-    SubArgs a{Uin, Uin, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
+void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field J, Field un, Field F2, Field F3, Field G1,
+                              Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout, cudaStream_t st) {
+    SubArgs a{Uin, J, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
     prof_begin(sub == SUB_RHS ? "dg_rhs_curved" : "dg_substep_curved", st);
     if (d.ks) {
         switch (d.P) {

@@ -3,9 +3,13 @@
 // k_dg_substep fuses, per DG element (one CTA, one thread per LGL node):
 //   volume term  -(d xi^k/d x^j) D_k F^j  (Sec. III.A, nodal DG-SEM),
 //   the Rusanov boundary correction lifted with the lumped LGL mass (Sec. III.C.2 flux),
-//   the explicit sources, the IMEX-SSP3(4,3,3) stage update with the pointwise
-//   stiff solve (Sec. III.B), the optional algebraic clamp (Sec. II.B), the
-//   exponential filter (Sec. III.A) and the troubled-cell indicator (Sec. III.C.3).
+//   the explicit sources, the explicit part of the IMEX-SSP3(4,3,3) stage, the
+//   exponential filter (Sec. III.A) of that explicit update, the pointwise stiff
+//   solve (Sec. III.B), the optional algebraic clamp (Sec. II.B) and the
+//   troubled-cell indicator (Sec. III.C.3).  Filtering before the solve keeps
+//   every state the explicit right-hand side sees a solve output: a filter after
+//   the solve re-creates a parallel E~ that the eta-current of the q~ flux
+//   amplifies by eta (unstable for eta dt >> 1).
 #include <cstdio>
 
 #include "ffe_internal.h"
@@ -196,12 +200,14 @@ __device__ void dg_external_state(const Dev& d, const SubArgs& a, int e, int f, 
             for (int q = 0; q < 3; ++q) Je[q] = a.J.dg(3 + q)[p];
             return;
         }
-        // FD neighbour: its FD->DG projection evaluated at this node (6-point stencils)
+        // FD neighbour: its FD->DG projection evaluated at this node (6-point
+        // stencils), for the state and for its current J~ (the current of the
+        // projected state would carry the projection error of E~.B~ times eta)
         const int nc = T.nc;
         const int lo0 = T.f2d_lo[c[0]], lo1 = T.f2d_lo[c[1]], lo2 = T.f2d_lo[c[2]];
         const int64_t base = fdb(d, nb);
-        for (int v = 0; v < NV; ++v) {
-            const double* src = a.Uin.fd(v) + base;
+        for (int v = 0; v < NV + 3; ++v) {
+            const double* src = v < NV ? a.Uin.fd(v) + base : a.J.fd(3 + v - NV) + base;
             double acc = 0.0;
             for (int n2 = 0; n2 < 6; ++n2) {
                 double a2 = 0.0;
@@ -213,9 +219,9 @@ __device__ void dg_external_state(const Dev& d, const SubArgs& a, int e, int f, 
                 }
                 acc = fma(T.F2D[c[2]][lo2 + n2], a2, acc);
             }
-            Ue[v] = acc;
+            if (v < NV) Ue[v] = acc;
+            else Je[v - NV] = acc;
         }
-        current_flat(Ue, d.eta, jd, Je);
         return;
     }
     int kind = d.bc[e * 6 + f];
@@ -342,13 +348,7 @@ __global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) 
         if (act) {
             if (SUB != SUB_C)
                 for (int v = 0; v < NV; ++v) a.Fout.dg(v)[eb + tid] = du[v];
-            substep_combine(d, SUB, du, eb + tid, false, a, d.dt, u);
-            if (SUB != SUB_C) {
-                // G at the solved stage value, before the filter: G_s = (U_s - R_s)/(dt a)
-                double g[NG];
-                implicit_G_flat(u, d, g);
-                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
-            }
+            substep_explicit(d, SUB, du, eb + tid, false, a, d.dt, u);
         }
         __syncthreads();   // sU, sJ, sC are free from here on
         if (d.filter_on) {
@@ -383,6 +383,15 @@ __global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) 
                 }
             }
             __syncthreads();
+        }
+        // implicit part after the filter; G at the stage value: G_s = (U_s - R~_s)/(dt a)
+        if (act) {
+            substep_implicit(d, SUB, d.dt, u);
+            if (SUB != SUB_C) {
+                double g[NG];
+                implicit_G_flat(u, d, g);
+                for (int c = 0; c < NG; ++c) a.Gout.dg(c)[eb + tid] = g[c];
+            }
         }
         bool flagged = false;
         if (d.tci_on) {

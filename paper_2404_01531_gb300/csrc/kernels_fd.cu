@@ -16,58 +16,9 @@
 #include "physics.cuh"
 #include "shellmap.cuh"
 #include "stage.cuh"
+#include "fd_common.cuh"
 
 namespace ffe {
-
-constexpr int NQ = 12;  // reconstructed quantities: 9 evolved + J~ (3)
-
-__device__ __forceinline__ int64_t ext_size(const Dev& d) {
-    const int64_t ne = d.nc + 2 * GH;
-    return ne * ne * ne;
-}
-// ext layout: [NQ][chunk][ext_size] indexed by position in the chunk
-__device__ __forceinline__ double* ext_at(const Dev& d, int q, int wl) {
-    return d.ext + ((int64_t)q * d.chunk + wl) * ext_size(d);
-}
-__device__ __forceinline__ int64_t nface(const Dev& d) { return (int64_t)(d.nc + 1) * d.nc * d.nc; }
-// flux layout: [3][NV][chunk][nface]; curved meshes keep every physical
-// component j: [3 (k)][3 (j)][NV][chunk][nface]
-__device__ __forceinline__ double* flux_at(const Dev& d, int k, int v, int wl) {
-    return d.flux + (((int64_t)k * NV + v) * d.chunk + wl) * nface(d);
-}
-__device__ __forceinline__ double* flux_at_c(const Dev& d, int k, int j, int v, int wl) {
-    return d.flux + ((((int64_t)k * 3 + j) * NV + v) * d.chunk + wl) * nface(d);
-}
-// shell map of element e (its instance's geometry and its index inside the instance)
-__device__ __forceinline__ ShellGeo shell_for(const Dev& d, int e, int& el) {
-    ShellGeo g;
-    if (d.einst) {
-        const InstInfo& in = d.inst[d.einst[e]];
-        g.r_in = in.r_in;
-        g.c = in.c;
-        g.na = in.na;
-        g.nr = in.nr;
-        el = e - in.e0;
-    } else {
-        g.r_in = d.shell_rin;
-        g.c = d.shell_c;
-        g.na = d.shell_na;
-        g.nr = d.shell_nr;
-        el = e;
-    }
-    return g;
-}
-
-__device__ __forceinline__ void axes_of(int dd, int& t1, int& t2) {
-    t1 = dd == 0 ? 1 : 0;
-    t2 = dd == 2 ? 1 : 2;
-}
-
-// number of listed elements in this chunk
-__device__ __forceinline__ int chunk_n(const Dev& d, int ci, int w0) {
-    const int n = d.counts[ci] - w0;
-    return n < 0 ? 0 : (n > d.chunk ? d.chunk : n);
-}
 
 // ---------------------------------------------------------------------------
 __global__ void k_fd_fill_interior(Dev d, const int* list, int ci, int w0, Field U, Field J) {
@@ -97,9 +48,9 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
         const ES es = esz(d, e);
         const Tables& T = d.tabs[es.P];
         const int nc = es.nc, ne = nc + 2 * GH, np1 = es.np1, nn = es.nn;
-        double* su = sm;                          // neighbour DG block [9][nn]
-        double* t1b = su + NV * nn;               // [9][GH][np1][np1]
-        double* t2b = t1b + NV * GH * np1 * np1;  // [9][GH][np1][nc]
+        double* su = sm;                          // neighbour DG block [12][nn]: U and J~
+        double* t1b = su + NQ * nn;               // [12][GH][np1][np1]
+        double* t2b = t1b + NQ * GH * np1 * np1;  // [12][GH][np1][nc]
         const int dd = f >> 1, s = f & 1;
         int t1, t2;
         axes_of(dd, t1, t2);
@@ -133,17 +84,22 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
                 for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = J.fd(3 + k)[p];
             }
         } else if (nb >= 0) {
-            // DG neighbour: its polynomial at its own subcell centres (DG -> FD), 3 layers
+            // DG neighbour: its polynomial at its own subcell centres (DG -> FD), 3
+            // layers, for U and for its nodal current J~ (the current of the
+            // evaluated state would carry the interpolation error of E~.B~ times eta)
             const int f2 = d.nbr_face[e * 6 + f];
             const int d2 = f2 >> 1, s2 = f2 & 1;
             int u1, u2;
             axes_of(d2, u1, u2);
             const int o = d.orient[e * 6 + f];
-            for (int t = threadIdx.x; t < NV * nn; t += blockDim.x)
-                su[t] = U.dg(t / nn)[(int64_t)nb * d.nn + t % nn];
+            for (int t = threadIdx.x; t < NQ * nn; t += blockDim.x) {
+                const int qv = t / nn;
+                const int64_t pn = (int64_t)nb * d.nn + t % nn;
+                su[t] = qv < NV ? U.dg(qv)[pn] : J.dg(3 + qv - NV)[pn];
+            }
             __syncthreads();
             // contract the normal direction for the 3 layers
-            for (int t = threadIdx.x; t < NV * GH * np1 * np1; t += blockDim.x) {
+            for (int t = threadIdx.x; t < NQ * GH * np1 * np1; t += blockDim.x) {
                 const int v = t / (GH * np1 * np1), r = t % (GH * np1 * np1);
                 const int g = r / (np1 * np1), a1 = r % np1, a2 = (r / np1) % np1;
                 const int cn = s2 ? nc - 1 - g : g;
@@ -158,7 +114,7 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
                 t1b[t] = acc;
             }
             __syncthreads();
-            for (int t = threadIdx.x; t < NV * GH * nc * np1; t += blockDim.x) {
+            for (int t = threadIdx.x; t < NQ * GH * nc * np1; t += blockDim.x) {
                 const int v = t / (GH * nc * np1), r = t % (GH * nc * np1);
                 const int g = r / (nc * np1), ta = r % nc, a2 = (r / nc) % np1;
                 double acc = 0.0;
@@ -170,16 +126,12 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
                 const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
                 int a2, b2;   // the neighbour's subcell (along u1, u2) under this ghost cell
                 orient_map(o, nc, ta, tb, a2, b2);
-                double u[NV], jd[3], jf[3];
-                for (int v = 0; v < NV; ++v) {
+                const int64_t og = ghost_offset(g, ta, tb);
+                for (int v = 0; v < NQ; ++v) {
                     double acc = 0.0;
                     for (int m = 0; m < np1; ++m) acc = fma(T.P2F[b2][m], t2b[((v * GH + g) * np1 + m) * nc + a2], acc);
-                    u[v] = acc;
+                    ext_at(d, v, wl)[og] = acc;
                 }
-                current_flat(u, d.eta, jd, jf);
-                const int64_t og = ghost_offset(g, ta, tb);
-                for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[og] = u[v];
-                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = jf[k];
             }
             __syncthreads();
         } else {
@@ -238,42 +190,6 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
             }
         }
     }
-}
-
-// WENO5-Z at the face right of v2 from v0..v4 (point-value interpolation
-// candidates, ideal weights (1, 10, 5)/16, Jiang-Shu indicators, Z weights q = 2).
-// The Z weights alpha_k = d_k (1 + tau^2/b_k^2), b_k = beta_k + eps, are scaled
-// by b_0^2 b_1^2 b_2^2 so that the normalised combination needs one division:
-//   A_k = d_k (b_k^2 + tau^2) prod_{j != k} b_j^2,  value = sum A_k p_k / sum A_k.
-// With eps >= 1e-40 every A_k stays above 1e-240, inside the normal range.
-__device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
-    const double p0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
-    const double p1 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
-    const double p2 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
-    const double c13 = 13.0 / 12.0;
-    const double s0a = v0 - 2.0 * v1 + v2, s0b = v0 - 4.0 * v1 + 3.0 * v2;
-    const double s1a = v1 - 2.0 * v2 + v3, s1b = v1 - v3;
-    const double s2a = v2 - 2.0 * v3 + v4, s2b = 3.0 * v2 - 4.0 * v3 + v4;
-    const double b0 = fma(c13 * s0a, s0a, 0.25 * s0b * s0b) + eps;
-    const double b1 = fma(c13 * s1a, s1a, 0.25 * s1b * s1b) + eps;
-    const double b2 = fma(c13 * s2a, s2a, 0.25 * s2b * s2b) + eps;
-    const double t = b0 - b2;
-    const double t2 = t * t;
-    const double q0 = b0 * b0, q1 = b1 * b1, q2 = b2 * b2;
-    const double A0 = (0.0625 * (q0 + t2)) * (q1 * q2);
-    const double A1 = (0.625 * (q1 + t2)) * (q0 * q2);
-    const double A2 = (0.3125 * (q2 + t2)) * (q0 * q1);
-    return fma(A0, p0, fma(A1, p1, A2 * p2)) / (A0 + A1 + A2);
-}
-
-// face fi of direction k: position m along k, tangential (ta, tb); false past the element's faces
-__device__ __forceinline__ bool face_coords(int64_t fi, int nc, int& m, int& ta, int& tb) {
-    const int64_t nf = (int64_t)(nc + 1) * nc * nc;
-    if (fi >= nf) return false;
-    m = (int)(fi % (nc + 1));
-    ta = (int)((fi / (nc + 1)) % nc);
-    tb = (int)(fi / ((int64_t)(nc + 1) * nc));
-    return true;
 }
 
 // 12 left/right face values and the two cells either side, from the extended block
@@ -450,6 +366,18 @@ __global__ void k_fd_update(Dev d, const int* list, int ci, int w0, SubArgs a) {
 
 int fd_chunks(const Dev& d) { return (d.fd_cap + d.chunk - 1) / d.chunk; }
 
+static size_t ghost_smem(const Dev& d) {
+    return (size_t)(NQ * d.nn + NQ * GH * d.np1 * d.np1 + NQ * GH * d.nc * d.np1) * sizeof(double);
+}
+
+void launch_fd_fill(const Dev& d, const int* list, int ci, int w0, Field U, Field J, cudaStream_t st) {
+    const size_t smem = ghost_smem(d);
+    cudaFuncSetAttribute(k_fd_fill_ghosts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fd_fill_interior<<<152 * 8, 256, 0, st>>>(d, list, ci, w0, U, J);
+    k_fd_fill_ghosts<<<152 * 2, 256, smem, st>>>(d, list, ci, w0, U, J);
+    g_launch_counter += 2;
+}
+
 template <int SUB>
 static void launch_update(const Dev& d, const int* list, int ci, int w0, const SubArgs& a, cudaStream_t st) {
     if (d.curved) k_fd_update<SUB, true><<<152 * 8, 256, 0, st>>>(d, list, ci, w0, a);
@@ -461,8 +389,7 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin
                        cudaStream_t st) {
     SubArgs a{Uin, J, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
     const int grid = 152 * 8;
-    const int np1 = d.np1, nn = d.nn, nc = d.nc;
-    const size_t smem = (size_t)(NV * nn + NV * GH * np1 * np1 + NV * GH * nc * np1) * sizeof(double);
+    const size_t smem = ghost_smem(d);
     cudaFuncSetAttribute(k_fd_fill_ghosts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int k = 0, nch = fd_chunks(d); k < nch; ++k) {
         const int w0 = k * d.chunk;

@@ -15,9 +15,11 @@ __device__ __forceinline__ void atomic_status(const Dev& d, int bits) { atomicOr
 //   SUB_A: R = u_n + dt F2 + dt (1-a) G2                       -> solve -> U3
 //   SUB_B: R = u_n + dt (F2 + F3)/4 + dt (b G1 + h G2 + z G3)   -> solve -> U4
 //   SUB_C: u_{n+1} = u_n + dt ((F2 + F3)/6 + 2 F4/3 + (G2 + G3)/6 + 2 G4/3)
-// followed by the algebraic clamp when the constraint mode asks for it.
-__device__ __forceinline__ void substep_combine(const Dev& d, int sub, const double* f, int64_t p, bool isfd,
-                                                const SubArgs& a, double dt, double* u) {
+// followed by the algebraic clamp when the constraint mode asks for it.  DG
+// kernels filter R between the explicit and the implicit part.
+// Explicit part R of the substep (DG elements filter R before the implicit part).
+__device__ __forceinline__ void substep_explicit(const Dev& d, int sub, const double* f, int64_t p, bool isfd,
+                                                 const SubArgs& a, double dt, double* u) {
     auto ld = [&](const Field& F, int v) { return isfd ? F.fd(v)[p] : F.dg(v)[p]; };
     const int gv[NG] = {0, 1, 2, 6, 7};
     for (int v = 0; v < NV; ++v) u[v] = ld(a.un, v);
@@ -35,10 +37,20 @@ __device__ __forceinline__ void substep_combine(const Dev& d, int sub, const dou
         for (int c = 0; c < NG; ++c)
             u[gv[c]] = fma(dt, (ld(a.G2, c) + ld(a.G3, c)) * (1.0 / 6.0) + ld(a.G4, c) * (2.0 / 3.0), u[gv[c]]);
     }
+}
+
+// Implicit part: stiff solve (stages 3, 4) and the algebraic clamp when asked for.
+__device__ __forceinline__ void substep_implicit(const Dev& d, int sub, double dt, double* u) {
     if (sub != SUB_C) {
         if (!stiff_solve_flat(u, d, dt * IM_A)) atomic_status(d, 2);
     }
     if (d.mode != FFE_RELAX) hard_clamp_flat(u);
+}
+
+__device__ __forceinline__ void substep_combine(const Dev& d, int sub, const double* f, int64_t p, bool isfd,
+                                                const SubArgs& a, double dt, double* u) {
+    substep_explicit(d, sub, f, p, isfd, a, dt, u);
+    substep_implicit(d, sub, dt, u);
 }
 
 // A DG element the indicator flags needs an FD slot.  Contexts with a slot

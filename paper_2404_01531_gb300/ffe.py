@@ -26,7 +26,7 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
            "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
            "ffe_fd_rhs_noalloc", "ffe_create_batch", "ffe_get_layout", "ffe_set_initial_batch",
            "ffe_rhs_vjp", "ffe_adjoint_step", "ffe_luminosity", "ffe_initial_tangent",
-           "ffe_last_error", "ffe_destroy"]
+           "ffe_freeze_mask", "ffe_last_error", "ffe_destroy"]
 
 
 class Domain(ctypes.Structure):
@@ -204,12 +204,13 @@ class Context:
         self.dt, self.dxmin = inf.dt, inf.dxmin
         return inf
 
-    def set_initial(self, kind=None, params=()):
+    def set_initial(self, kind=None, params=(), keep_mask=False):
+        """Analytic initial data; keep_mask: keep the current DG/FD mask (no indicator)."""
         if kind is None:
             kind, kw = self.cfg["initial"]
             params = tuple(kw.values())
         arr = (ctypes.c_double * max(len(params), 1))(*params)
-        check(load().ffe_set_initial(self.h, ID[kind], arr, len(params), 0))
+        check(load().ffe_set_initial(self.h, ID[kind], arr, len(params), 1 if keep_mask else 0))
 
     def step(self, n=1):
         check(load().ffe_step(self.h, int(n)))
@@ -307,6 +308,10 @@ class Context:
 
     def initial_tangent(self, which, out):
         check(load().ffe_initial_tangent(self.h, int(which), ctypes.c_void_p(out.data_ptr())))
+
+    def freeze_mask(self, on=True):
+        """Freeze (or release) the DG/FD mask: no indicator, no switching."""
+        check(load().ffe_freeze_mask(self.h, int(bool(on))))
 
     def layout(self):
         """(elem_P, fd_slot, elem_inst, inst_first) as numpy arrays."""

@@ -158,3 +158,129 @@ def test_autograd_function_step(ffe):
     (U2 * w).sum().backward()
     assert torch.isfinite(U0.grad).all() and float(U0.grad.abs().sum()) > 0
     ctx.close()
+
+
+# ---- hybrid DG-FD (fixed mask) --------------------------------------------------
+
+def _active(ctx, mask):
+    """Boolean over the state vector: DG nodes of DG elements, cells of FD elements."""
+    nn, ncell = ctx.n_dg // ctx.n_elem, ctx.n_fd // ctx.n_elem
+    dg = (mask == 0).repeat_interleave(nn)
+    fd = (mask == 1).repeat_interleave(ncell)
+    return torch.cat([dg.repeat(9), fd.repeat(9)])
+
+
+def _hybrid(ffe, eta=1e5, every=3, cfg=None, inner=False):
+    """Tiny shell with every `every`-th element (or, inner=True, the radial layer
+    at the star) on FD subcells, fixed mask, and the dipole data on the LGL
+    nodes / subcell centres."""
+    cfg = cfg if cfg is not None else _tiny(eta)
+    ctx = ffe.Context(cfg)
+    U, m = ctx.state()
+    mask = torch.zeros_like(m)
+    if inner:
+        na, nr = cfg["n_ang"], cfg["n_rad"]
+        e = torch.arange(ctx.n_elem, device=m.device)
+        mask[(e // (na * na)) % nr == 0] = 1
+    else:
+        mask[::every] = 1
+    ctx.set_state(U.clone(), mask)
+    ctx.set_initial(keep_mask=True)
+    assert int(ctx.state()[1].sum()) == int(mask.sum())
+    return ctx, mask
+
+
+def _perturb(ctx, mask, seed, amp=0.02):
+    """A linearisation point without flat stretches: the data plus white noise
+    of amp * max|U| on the active points.  (WENO5-Z is not differentiable where
+    a stencil is exactly flat, e.g. zero E~ ahead of the light front.)"""
+    U = ctx.state()[0].clone()
+    act = _active(ctx, mask)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    U += amp * torch.randn(U.shape, generator=g, dtype=torch.float64).cuda() * U.abs().max() * act
+    return U, act
+
+
+def _richardson(f, h, lam):
+    """lam . (central difference of the vector map f extrapolated from steps 2h
+    and h, error O(h^4)); the vectors are differenced before the dot product."""
+    d1 = (f(2 * h) - f(-2 * h)) / (4 * h)
+    d2 = (f(h) - f(-h)) / (2 * h)
+    return float(torch.dot(lam, (4.0 * d2 - d1) / 3.0))
+
+
+def _dirs(U, act, seed):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    lam = torch.randn(U.shape, generator=g, dtype=torch.float64).cuda() * act
+    dlt = torch.randn(U.shape, generator=g, dtype=torch.float64).cuda() * U.abs().max() * act
+    return lam, dlt
+
+
+@pytest.mark.parametrize("eta", [0.0, 50.0, 1e5])
+def test_hybrid_rhs_vjp_matches_finite_differences(ffe, eta):
+    """lambda . (dF/dU) delta with a third of the elements on FD subcells: WENO5-Z,
+    Rusanov, ghosts from FD / DG neighbours and boundary states, and the DG lift
+    on FD-neighbour traces, against extrapolated central differences."""
+    ctx, mask = _hybrid(ffe, eta)
+    U, act = _perturb(ctx, mask, 11)
+    lam, dlt = _dirs(U, act, 12)
+    vjp = torch.zeros_like(U)
+    ctx.rhs_vjp(U, lam, vjp)
+    assert float(vjp[~act].abs().max()) == 0.0
+
+    def f(h):
+        F = torch.zeros_like(U)
+        ctx.rhs(U + h * dlt, F)
+        return F
+    fd = _richardson(f, 1e-8, lam)
+    ad = float(torch.dot(vjp, dlt))
+    assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+    ctx.close()
+
+
+def test_hybrid_adjoint_step_matches_finite_differences(ffe):
+    ctx, mask = _hybrid(ffe)
+    U, act = _perturb(ctx, mask, 13)
+    lam, dlt = _dirs(U, act, 14)
+    out = torch.zeros_like(U)
+    ctx.adjoint_step(U, lam, out)
+    assert float(out[~act].abs().max()) == 0.0
+
+    def f(h):
+        ctx.set_state(U + h * dlt, mask)
+        ctx.step(1)
+        return ctx.state()[0].clone()
+    fd = _richardson(f, 1e-8, lam)
+    ad = float(torch.dot(out, dlt))
+    assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+    ctx.close()
+
+
+def test_hybrid_luminosity_gradient_matches_central_differences(ffe):
+    """Frozen mask with the star-adjacent layer on FD, r = 1.5 (inside that
+    layer: the luminosity is taken from FD elements), 10 steps:
+    d Lbar/d (mu, chi, Omega) against extrapolated central differences.
+    WENO-Z with eps = 1e-40 is not differentiable where a stencil is exactly
+    flat (E~, q~, psi~ vanish ahead of the light front in the dipole data):
+    there the adjoint takes the ideal-weight branch and a difference quotient
+    sees the weights jump.  eps = 1e-6 makes the weights smooth at flat data."""
+    from paper_2404_01531_gb300.adjoint import lbar_forward, luminosity_gradient
+    cfg = _tiny()
+    cfg["params"]["weno_eps"] = 1e-6
+    nsteps, rL = 10, 1.5
+    ctx, mask = _hybrid(ffe, cfg=cfg, inner=True)
+    L, g, _ = luminosity_gradient(ctx, nsteps, r_L=rL, every=4)
+    ctx.close()
+    base = dict(mu=cfg["initial"][1]["mu"], chi=cfg["initial"][1]["chi"], omega=cfg["params"]["omega_star"])
+    for k, name in enumerate(("mu", "chi", "omega")):
+        def lb(dh):
+            c, _ = _hybrid(ffe, cfg=_with(cfg, **{name: base[name] + dh}), inner=True)
+            v = lbar_forward(c, nsteps, rL)
+            c.close()
+            return v
+        h = 1e-6 * base[name]
+        d1 = (lb(2 * h) - lb(-2 * h)) / (4 * h)
+        d2 = (lb(h) - lb(-h)) / (2 * h)
+        fd = (4.0 * d2 - d1) / 3.0
+        # difference quotients of Lbar over the hybrid evolution repeat to ~1e-6
+        assert abs(g[k] - fd) <= 3e-6 * abs(fd), (name, g[k], fd)
