@@ -199,7 +199,7 @@ ffe_status ffe_launch_count(ffe_ctx* ctx, int64_t* n);
 /* Per-kernel timing.  With on = 1, ffe_step launches eagerly (no graph) and
  * brackets every kernel with CUDA events on the context stream, synchronising
  * once per step; totals accumulate until read.  ffe_profile_read writes a JSON
- * object {"kernel": [launches, total_ms], ...} into buf (NUL-terminated,
+ * object {"kernel": [launches, total_ms, max_ms], ...} into buf (NUL-terminated,
  * truncated to cap) and clears the totals. */
 ffe_status ffe_set_profiling(ffe_ctx* ctx, int on);
 ffe_status ffe_profile_read(ffe_ctx* ctx, char* buf, size_t cap);

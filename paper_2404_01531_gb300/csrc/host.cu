@@ -206,11 +206,17 @@ struct Profiler {
     std::vector<ProfRec> pending;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
     size_t used = 0;
-    std::vector<std::pair<std::string, std::pair<long, double>>> totals;
+    struct Tot { long n; double ms, max_ms; };
+    std::vector<std::pair<std::string, Tot>> totals;
     void add(const std::string& n, double ms) {
         for (auto& t : totals)
-            if (t.first == n) { t.second.first += 1; t.second.second += ms; return; }
-        totals.push_back({n, {1, ms}});
+            if (t.first == n) {
+                t.second.n += 1;
+                t.second.ms += ms;
+                t.second.max_ms = ms > t.second.max_ms ? ms : t.second.max_ms;
+                return;
+            }
+        totals.push_back({n, {1, ms, ms}});
     }
 };
 thread_local Profiler g_prof;
@@ -1644,8 +1650,8 @@ ffe_status ffe_profile_read(ffe_ctx* c, char* buf, size_t cap) {
     std::string js = "{";
     for (size_t i = 0; i < g_prof.totals.size(); ++i) {
         char tmp[160];
-        snprintf(tmp, sizeof tmp, "%s\"%s\": [%ld, %.6f]", i ? ", " : "", g_prof.totals[i].first.c_str(),
-                 g_prof.totals[i].second.first, g_prof.totals[i].second.second);
+        snprintf(tmp, sizeof tmp, "%s\"%s\": [%ld, %.6f, %.6f]", i ? ", " : "", g_prof.totals[i].first.c_str(),
+                 g_prof.totals[i].second.n, g_prof.totals[i].second.ms, g_prof.totals[i].second.max_ms);
         js += tmp;
     }
     js += "}";
