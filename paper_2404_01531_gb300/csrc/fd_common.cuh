@@ -46,6 +46,50 @@ __device__ __forceinline__ ShellGeo shell_for(const Dev& d, int e, int& el) {
     return g;
 }
 
+// FD-point geometry of a flat-shell element from the tabulated gnomonic
+// coordinates and radii of its rows (Dev::stab): base indices of the element's
+// angular and radial rows on the half-cell grid, its wedge axes and side.
+struct ShellPts {
+    const double *tx, *tw, *tr, *tir;
+    int gx, gy, gr, pn;
+    double s, na, nr, c;
+};
+__device__ __forceinline__ ShellPts shell_pts(const Dev& d, int e, int nc) {
+    int el;
+    const ShellGeo g = shell_for(d, e, el);
+    int ia, ib, ir, w;
+    shell_elem(g, el, ia, ib, ir, w);
+    ShellPts p;
+    const double* t = d.stab + (d.einst ? d.inst[d.einst[e]].tab : 0);
+    const int nx = 2 * nc * g.na + 1, nrr = 2 * nc * g.nr + 1;
+    p.tx = t;
+    p.tw = t + nx;
+    p.tr = t + 2 * nx;
+    p.tir = t + 2 * nx + nrr;
+    p.gx = 2 * nc * ia;
+    p.gy = 2 * nc * ib;
+    p.gr = 2 * nc * ir;
+    p.pn = (w >> 1) == 0 ? 2 : ((w >> 1) == 1 ? 1 : 0);
+    p.s = (w & 1) ? -1.0 : 1.0;
+    p.na = g.na;
+    p.nr = g.nr;
+    p.c = g.c;
+    return p;
+}
+// inverse Jacobian (and the point, if x) at the centre of cell cc
+__device__ __forceinline__ void shell_cell(const ShellPts& p, const int* cc, double ij[3][3], double* x) {
+    const int hx = p.gx + 2 * cc[0] + 1, hy = p.gy + 2 * cc[1] + 1, hr = p.gr + 2 * cc[2] + 1;
+    shell_cell_closed(p.tx[hx], p.tx[hy], p.tw[hx], p.tw[hy], p.tr[hr], p.tir[hr], p.pn, p.s, p.na, p.nr, p.c, ij, x);
+}
+// unit normal grad xi^k / |grad xi^k| at face m of direction k, tangential cells (ta, tb)
+__device__ __forceinline__ void shell_face_normal(const ShellPts& p, int k, int m, int ta, int tb, double* nh) {
+    double X, Y;
+    if (k == 0) { X = p.tx[p.gx + 2 * m]; Y = 0.0; }
+    else if (k == 1) { X = 0.0; Y = p.tx[p.gy + 2 * m]; }
+    else { X = p.tx[p.gx + 2 * ta + 1]; Y = p.tx[p.gy + 2 * tb + 1]; }
+    shell_normal_closed(k, X, Y, p.pn, p.s, nh);
+}
+
 __device__ __forceinline__ void axes_of(int dd, int& t1, int& t2) {
     t1 = dd == 0 ? 1 : 0;
     t2 = dd == 2 ? 1 : 2;

@@ -45,6 +45,7 @@ struct Tables {
 struct InstInfo {
     double r_in, c, dt, omega;   // shell map r = r_in exp(c (er + 1)), time step, star rotation
     int na, nr, e0, P;           // elements per wedge side / radially, first element, order
+    int tab;                     // offset of the instance's FD-point tables in Dev::stab
 };
 
 // A field buffer in state-vector layout: [nv][n_dg] then [nv][n_fd].
@@ -84,12 +85,17 @@ struct Dev {
     const double* ijac;             // [E][3]
     // curved meshes: d xi^k / d x^i per DG node [9][ndg] (index 3 k + i), the
     // Kerr-Schild metric per DG node [NMET][ndg] (null in flat space), and the
-    // shell map for FD cells and faces (evaluated on the fly)
+    // shell map for FD cells and faces (closed form, from stab)
     int curved, ks;
     const double* geo;
     const double* met;
     double shell_rin, shell_c;
     int shell_na, shell_nr;
+    // flat shells, per instance at InstInfo::tab (single context: 0), on the
+    // half-cell grid g = 2 nc i + h of each angular / radial element row (h even:
+    // FD faces, h odd: cell centres): X_g = tan(pi/4 e_g), 1/(pi/4 (1 + X_g^2))
+    // [2 nc na + 1 each], then r_g, 1/r_g [2 nc nr + 1 each]
+    const double* stab;
     const double* xyz_dg;           // [3][ndg] node coordinates
     const double* xyz_fd;           // [3][nfd] subcell-centre coordinates
     // connectivity

@@ -782,6 +782,32 @@ ffe_status finish_create(ffe_ctx* c, int fd_cap, const std::vector<int>& orders)
     if ((s = dalloc(c, &d.near_list, 4096))) return s;
     if ((s = dalloc(c, &d.counts, 8))) return s;
     if ((s = dalloc(c, &d.units, 3))) return s;   // node updates, FD and DG element updates
+    if (d.curved && !d.ks) {
+        // FD-point tables of the shell map (Dev::stab): gnomonic coordinate
+        // X = tan(pi/4 e) and 1/(pi/4 (1 + X^2)) on the half-cell grid of the
+        // angular rows, r and 1/r on that of the radial rows
+        std::vector<double> tab;
+        auto add = [&](int P, int na, int nr, double r_in, double cc) {
+            const int off = (int)tab.size(), nc = 2 * P + 1;
+            const long double q = 0.785398163397448309615660845819875721L;
+            std::vector<double> X(2 * nc * na + 1), R(2 * nc * nr + 1);
+            for (size_t g = 0; g < X.size(); ++g) X[g] = (double)std::tan(q * (-1.0L + (long double)g / (nc * na)));
+            for (size_t g = 0; g < R.size(); ++g) R[g] = (double)(r_in * std::exp((long double)cc * g / (nc * nr)));
+            for (double x : X) tab.push_back(x);
+            for (double x : X) tab.push_back((double)(1.0L / (q * (1.0L + (long double)x * x))));
+            for (double r : R) tab.push_back(r);
+            for (double r : R) tab.push_back(1.0 / r);
+            return off;
+        };
+        if (c->batch)
+            for (auto& in : c->insts) in.tab = add(in.P, in.na, in.nr, in.r_in, in.c);
+        else
+            add(d.P, c->shell.na, c->shell.nr, c->shell.r_in, c->shell.c);
+        double* dt;
+        if ((s = dalloc(c, &dt, tab.size()))) return s;
+        CK(cudaMemcpy(dt, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+        d.stab = dt;
+    }
     if (c->batch) {
         int *eP8, *ein;
         InstInfo* dinst;

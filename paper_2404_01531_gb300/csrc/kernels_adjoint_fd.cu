@@ -31,14 +31,6 @@ __device__ __forceinline__ double* extb_at(const Dev& d, double* extb, int q, in
     return extb + ((int64_t)q * d.chunk + wl) * ext_size(d);
 }
 
-// inverse Jacobian at the centre of cell cc of element e
-__device__ __forceinline__ void cell_ijac(const Dev& d, int e, int nc, const int* cc, double ij[3][3]) {
-    double xi[3], x[3];
-    for (int q = 0; q < 3; ++q) xi[q] = -1.0 + (cc[q] + 0.5) * 2.0 / nc;
-    int el;
-    const ShellGeo sg = shell_for(d, e, el);
-    shell_map(sg, el, xi, x, ij);
-}
 
 __global__ void k_fdv_faces(Dev d, const int* list, int ci, int w0, Field L, double* extb) {
     const int n = chunk_n(d, ci, w0);
@@ -55,18 +47,9 @@ __global__ void k_fdv_faces(Dev d, const int* list, int ci, int w0, Field L, dou
         int t1, t2;
         axes_of(k, t1, t2);
         // unit normal at the face point
+        const ShellPts sp = shell_pts(d, e, nc);
         double nh[3];
-        {
-            double xi[3], x[3], ij[3][3];
-            xi[k] = -1.0 + m * 2.0 / nc;
-            xi[t1] = -1.0 + (ta + 0.5) * 2.0 / nc;
-            xi[t2] = -1.0 + (tb + 0.5) * 2.0 / nc;
-            int el;
-            const ShellGeo sg = shell_for(d, e, el);
-            shell_map(sg, el, xi, x, ij);
-            const double inrm = 1.0 / sqrt(ij[k][0] * ij[k][0] + ij[k][1] * ij[k][1] + ij[k][2] * ij[k][2]);
-            for (int j = 0; j < 3; ++j) nh[j] = ij[k][j] * inrm;
-        }
+        shell_face_normal(sp, k, m, ta, tb, nh);
         // flux adjoints: the face is the right face of cell m-1 (du -= sc F) and
         // the left face of cell m (du += sc F)
         double Fb[3][NV];
@@ -81,7 +64,7 @@ __global__ void k_fdv_faces(Dev d, const int* list, int ci, int w0, Field L, dou
             cc[t1] = ta;
             cc[t2] = tb;
             double ij[3][3];
-            cell_ijac(d, e, nc, cc, ij);
+            shell_cell(sp, cc, ij, nullptr);
             const int64_t p = fb + cc[0] + nc * (cc[1] + nc * cc[2]);
             const double sgn = side ? 0.5 * nc : -0.5 * nc;
             for (int v = 0; v < NV; ++v) {
@@ -294,24 +277,18 @@ __global__ void k_fdv_ghosts(Dev d, const int* list, int ci, int w0, Field U, Fi
                 const int64_t p = fdb(d, e) + c[0] + nc * (c[1] + nc * c[2]);
                 double ui[NV], u[NV], ub[NV], ib[NV];
                 for (int v = 0; v < NV; ++v) { ui[v] = U.fd(v)[p]; ib[v] = 0.0; }
-                int el;
-                const ShellGeo sg = shell_for(d, e, el);
+                const ShellPts sp = shell_pts(d, e, nc);
                 if (kind == FFE_BC_NO_INCOMING) {
-                    double xi[3], x[3], ij[3][3], nrm[3];
-                    xi[dd] = s ? 1.0 : -1.0;
-                    xi[t1] = -1.0 + (ta + 0.5) * 2.0 / nc;
-                    xi[t2] = -1.0 + (tb + 0.5) * 2.0 / nc;
-                    shell_map(sg, el, xi, x, ij);
-                    const double sgn = s ? 1.0 : -1.0;
-                    const double nn2 = sqrt(ij[dd][0] * ij[dd][0] + ij[dd][1] * ij[dd][1] + ij[dd][2] * ij[dd][2]);
-                    for (int qd = 0; qd < 3; ++qd) nrm[qd] = sgn * ij[dd][qd] / nn2;
+                    double nrm[3];
+                    shell_face_normal(sp, dd, s ? nc : 0, ta, tb, nrm);
+                    if (!s)
+                        for (int qd = 0; qd < 3; ++qd) nrm[qd] = -nrm[qd];
                     bc_no_incoming_flat(ui, nrm, u);
                     ghost_bar(ghost_offset(g, ta, tb), u, ub);
                     bc_no_incoming_vjp(ui, nrm, ub, ib);
                 } else {
-                    double xi[3], x[3], ij[3][3];
-                    for (int qd = 0; qd < 3; ++qd) xi[qd] = -1.0 + (c[qd] + 0.5) * 2.0 / nc;
-                    shell_map(sg, el, xi, x, ij);
+                    double x[3], ij[3][3];
+                    shell_cell(sp, c, ij, x);
                     const double om = omega_of(d, e);
                     bc_star_flat(ui, x, om, u);
                     ghost_bar(ghost_offset(g, ta, tb), u, ub);

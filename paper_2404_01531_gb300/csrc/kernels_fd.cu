@@ -156,27 +156,17 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
                         nrm[dd] = s ? 1.0 : -1.0;
                         if (d.curved) {
                             // outward unit normal at the face point of this column
-                            double xi[3], x[3], ij[3][3];
-                            xi[dd] = s ? 1.0 : -1.0;
-                            xi[t1] = -1.0 + (ta + 0.5) * 2.0 / nc;
-                            xi[t2] = -1.0 + (tb + 0.5) * 2.0 / nc;
-                            int el;
-                            const ShellGeo sg = shell_for(d, e, el);
-                            shell_map(sg, el, xi, x, ij);
-                            const double sgn = s ? 1.0 : -1.0;
-                            const double nn2 = sqrt(ij[dd][0] * ij[dd][0] + ij[dd][1] * ij[dd][1] + ij[dd][2] * ij[dd][2]);
-                            for (int q = 0; q < 3; ++q) nrm[q] = sgn * ij[dd][q] / nn2;
+                            shell_face_normal(shell_pts(d, e, nc), dd, s ? nc : 0, ta, tb, nrm);
+                            if (!s)
+                                for (int q = 0; q < 3; ++q) nrm[q] = -nrm[q];
                         }
                         bc_no_incoming_flat(ui, nrm, u);
                     } else {
                         double x[3];
                         if (d.curved) {
                             // centre of the outermost cell of this column
-                            double xi[3], ij[3][3];
-                            for (int q = 0; q < 3; ++q) xi[q] = -1.0 + (c[q] + 0.5) * 2.0 / nc;
-                            int el;
-                            const ShellGeo sg = shell_for(d, e, el);
-                            shell_map(sg, el, xi, x, ij);
+                            double ij[3][3];
+                            shell_cell(shell_pts(d, e, nc), c, ij, x);
                         } else {
                             for (int k = 0; k < 3; ++k) x[k] = d.xyz_fd[(int64_t)k * d.nfd + p];
                         }
@@ -264,19 +254,13 @@ __global__ void k_fd_flux_curved(Dev d, const int* list, int ci, int w0) {
         axes_of(k, t1, t2);
         double UL[NQ], UR[NQ], Um[NQ], Up[NQ];
         reconstruct(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
-        double xi[3], x[3], ij[3][3];
-        xi[k] = -1.0 + m * 2.0 / nc;
-        xi[t1] = -1.0 + (ta + 0.5) * 2.0 / nc;
-        xi[t2] = -1.0 + (tb + 0.5) * 2.0 / nc;
-        int el;
-        const ShellGeo sg = shell_for(d, e, el);
-        shell_map(sg, el, xi, x, ij);
-        const double inrm = 1.0 / sqrt(ij[k][0] * ij[k][0] + ij[k][1] * ij[k][1] + ij[k][2] * ij[k][2]);
+        double nh[3];
+        shell_face_normal(shell_pts(d, e, nc), k, m, ta, tb, nh);
         for (int j = 0; j < 3; ++j) {
             double FL[NV], FR[NV], Fs[NV];
             flux_dir_flat(UL, UL + NV, j, FL);
             flux_dir_flat(UR, UR + NV, j, FR);
-            const double nj = ij[k][j] * inrm;
+            const double nj = nh[j];
             for (int v = 0; v < NV; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * nj * (UR[v] - UL[v]);
             if (d.fd_corr) {
                 double Fm[NV], Fp[NV];
@@ -303,13 +287,7 @@ __global__ void k_fd_update(Dev d, const int* list, int ci, int w0, SubArgs a) {
         const int cc[3] = {c % nc, (c / nc) % nc, c / (nc * nc)};
         const int64_t p = fdb(d, e) + c;
         double ij[3][3];
-        if (CURVED) {
-            double xi[3], x[3];
-            for (int k = 0; k < 3; ++k) xi[k] = -1.0 + (cc[k] + 0.5) * 2.0 / nc;
-            int el;
-            const ShellGeo sg = shell_for(d, e, el);
-            shell_map(sg, el, xi, x, ij);
-        }
+        if (CURVED) shell_cell(shell_pts(d, e, nc), cc, ij, nullptr);
         double du[NV], u0[NV];
         for (int v = 0; v < NV; ++v) u0[v] = a.Uin.fd(v)[p];
         du[0] = -a.J.fd(0)[p];

@@ -73,6 +73,52 @@ __host__ __device__ inline void shell_map(const ShellGeo& g, int e, const double
     ijac[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
 }
 
+// Closed forms of the same map at FD points, from the gnomonic coordinates
+// X = x_a/(s x_n), Y = x_b/(s x_n) and r (pn, pa, pb: the wedge's normal and
+// tangential physical axes, s its side):
+//   grad xi^0 = na rho / (q (1 + X^2) r) (e_a - s X e_n),
+//   grad xi^1 = na rho / (q (1 + Y^2) r) (e_b - s Y e_n),
+//   grad xi^2 = nr / (c r) x^,   x^ = (s e_n + X e_a + Y e_b) / rho,
+// rho = sqrt(1 + X^2 + Y^2), q = pi/4.  wX = 1/(q (1 + X^2)), ir = 1/r.
+__host__ __device__ inline void shell_cell_closed(double X, double Y, double wX, double wY, double r, double ir,
+                                                  int pn, double s, double na, double nr, double c,
+                                                  double ijac[3][3], double x[3]) {
+    const int pa = (pn + 1) % 3, pb = (pn + 2) % 3;
+    const double rho = sqrt(1.0 + X * X + Y * Y), irho = 1.0 / rho;
+    const double fx = na * rho * ir * wX, fy = na * rho * ir * wY, fr = nr * ir / c;
+    ijac[0][pa] = fx;
+    ijac[0][pb] = 0.0;
+    ijac[0][pn] = -s * X * fx;
+    ijac[1][pa] = 0.0;
+    ijac[1][pb] = fy;
+    ijac[1][pn] = -s * Y * fy;
+    ijac[2][pn] = fr * s * irho;
+    ijac[2][pa] = fr * X * irho;
+    ijac[2][pb] = fr * Y * irho;
+    if (x) {
+        x[pn] = r * s * irho;
+        x[pa] = r * X * irho;
+        x[pb] = r * Y * irho;
+    }
+}
+
+// Unit normal grad xi^k / |grad xi^k| (k = 0, 1: T = X or Y on the face; k = 2:
+// X, Y at the point).
+__host__ __device__ inline void shell_normal_closed(int k, double X, double Y, int pn, double s, double nh[3]) {
+    const int pa = (pn + 1) % 3, pb = (pn + 2) % 3;
+    if (k == 2) {
+        const double irho = 1.0 / sqrt(1.0 + X * X + Y * Y);
+        nh[pn] = s * irho;
+        nh[pa] = X * irho;
+        nh[pb] = Y * irho;
+    } else {
+        const double T = k == 0 ? X : Y, it = 1.0 / sqrt(1.0 + T * T);
+        nh[pn] = -s * T * it;
+        nh[k == 0 ? pa : pb] = it;
+        nh[k == 0 ? pb : pa] = 0.0;
+    }
+}
+
 // Neighbour face index (a2, b2) for my face index (a, b) under orientation code
 // o: bit 0 swaps a and b, bit 1 reverses the first, bit 2 the second.
 __host__ __device__ inline void orient_map(int o, int n, int a, int b, int& a2, int& b2) {
