@@ -256,6 +256,19 @@ ffe_status ffe_rhs_vjp(ffe_ctx* ctx, const double* U_dev, const double* lam_dev,
 ffe_status ffe_adjoint_step(ffe_ctx* ctx, const double* U_dev, const double* lam_in_dev, double* lam_out_dev,
                             double* omega_bar);
 
+/* The two halves of ffe_adjoint_step, for callers that keep a segment's stages
+ * in device memory instead of recomputing them (Sec. III.B stages; checkpointed
+ * recomputation with the stage states stored):
+ * ffe_adjoint_forward recomputes the step's stages from U_n; when stages_dev is
+ * not NULL it receives them as five consecutive state vectors [U2][T3][U3][T4]
+ * [U4] (T_s the filtered explicit part of stage s), and when U_next_dev is not
+ * NULL it receives u_{n+1} (must not alias U_dev).
+ * ffe_adjoint_reverse runs the backward sweep from those stages: same result
+ * as ffe_adjoint_step(U_dev, lam_in, lam_out, omega_bar). */
+ffe_status ffe_adjoint_forward(ffe_ctx* ctx, const double* U_dev, double* stages_dev, double* U_next_dev);
+ffe_status ffe_adjoint_reverse(ffe_ctx* ctx, const double* U_dev, const double* stages_dev, const double* lam_in_dev,
+                               double* lam_out_dev, double* omega_bar);
+
 /* Spin-down luminosity through the sphere r = r_L (Sec. IV.C.2): L = closed
  * integral of (E x B).r^ dA on the radial element layer containing r_L (xi^3
  * interpolation, LGL quadrature, exact area element).  *L_host receives L;

@@ -56,19 +56,22 @@ def lbar_forward(ctx, nsteps, r_L=20.0):
     return acc / nsteps
 
 
-def luminosity_gradient(ctx, nsteps, r_L=20.0, every=25):
+def luminosity_gradient(ctx, nsteps, r_L=20.0, every=25, keep_stages=True):
     """Lbar = mean of L(u_n), n = 1..nsteps, and d Lbar/d (mu, chi, Omega).
 
     ctx: a Context holding the dipole initial data (ffe_set_initial already
     called).  Forward: nsteps steps keeping a checkpoint every `every` steps.
     Reverse: per segment, the states are recomputed from its checkpoint and
-    ffe_adjoint_step runs backward with the luminosity gradient of each state
-    added to lambda.  Returns (Lbar, [dmu, dchi, dOmega], timings)."""
+    the step adjoints run backward with the luminosity gradient of each state
+    added to lambda.  keep_stages: the recomputation keeps every step's stage
+    states (5 state vectors per step of the segment, in device memory) and the
+    backward sweep uses them (ffe_adjoint_forward / ffe_adjoint_reverse);
+    otherwise each step adjoint recomputes its stages (ffe_adjoint_step).
+    Returns (Lbar, [dmu, dchi, dOmega], timings)."""
     import time
     U0, mask0 = ctx.state()
     U0 = U0.clone()
     mask0 = mask0.clone()
-    st = torch.cuda.current_stream()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ckpt = {0: U0.clone()}
@@ -84,20 +87,33 @@ def luminosity_gradient(ctx, nsteps, r_L=20.0, every=25):
     lam = torch.zeros_like(U0)
     tmp = torch.empty_like(U0)
     om_bar = 0.0
+    stages = None
+    if keep_stages:
+        stages = torch.empty((min(every, nsteps), 5 * U0.numel()), dtype=U0.dtype, device=U0.device)
     starts = list(range(0, nsteps, every))
     for s0 in reversed(starts):
         s1 = min(s0 + every, nsteps)
-        # recompute u_{s0} .. u_{s1-1}
-        ctx.set_state(ckpt[s0], mask0)
+        # recompute u_{s0} .. u_{s1-1} (and, with keep_stages, every step's stages)
         states = [ckpt[s0]]
-        for _ in range(s1 - s0 - 1):
-            ctx.step(1)
-            states.append(ctx.state()[0].clone())
+        if keep_stages:
+            for n in range(s0, s1):
+                nxt = torch.empty_like(U0) if n + 1 < s1 else None
+                ctx.adjoint_forward(states[n - s0], stages[n - s0], nxt)
+                if nxt is not None:
+                    states.append(nxt)
+        else:
+            ctx.set_state(ckpt[s0], mask0)
+            for _ in range(s1 - s0 - 1):
+                ctx.step(1)
+                states.append(ctx.state()[0].clone())
         for n in range(s1 - 1, s0 - 1, -1):
             # lambda_{n+1} += dL(u_{n+1})/du / nsteps, then through step n
             un1 = ckpt[s1] if n + 1 == s1 else states[n + 1 - s0]
             ctx.luminosity(un1, r_L, grad=lam, scale=1.0 / nsteps)
-            om_bar += ctx.adjoint_step(states[n - s0], lam, tmp)
+            if keep_stages:
+                om_bar += ctx.adjoint_reverse(states[n - s0], stages[n - s0], lam, tmp)
+            else:
+                om_bar += ctx.adjoint_step(states[n - s0], lam, tmp)
             lam, tmp = tmp, lam
     torch.cuda.synchronize()
     t2 = time.perf_counter()

@@ -1472,21 +1472,13 @@ ffe_status ffe_rhs_vjp(ffe_ctx* c, const double* U_dev, const double* lam_dev, d
     return FFE_OK;
 }
 
-ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_in_dev, double* lam_out_dev,
-                            double* omega_bar) {
-    g_err.clear();
-    if (!c || !U_dev || !lam_in_dev || !lam_out_dev) return fail(FFE_EINVAL, "null argument");
-    ffe_status s;
-    if ((s = adjoint_ready(c))) return s;
+// Forward recomputation of a step's stages from U_n (a.un): stage s = 3, 4 is
+// R_s (explicit part) -> T_s = filter(R_s) -> U_s = S(T_s), G_s = G(U_s).  With
+// next, also u_{n+1} = filter(W), W the explicit part of the last substep.
+static ffe_status adj_forward(ffe_ctx* c, AdjArgs& a, const Field* next) {
     const Dev& d = c->d;
     cudaStream_t st = c->st;
-    AdjArgs a = c->adj;
-    a.un = Field{(double*)U_dev, NV, d.ndg, d.nfd};
-    Field lin{(double*)lam_in_dev, NV, d.ndg, d.nfd};
-    a.lam = Field{lam_out_dev, NV, d.ndg, d.nfd};
-    launch_build_lists(d, st);
-    // forward recomputation of the step's stages from U_n: stage s = 3, 4 is
-    // R_s (explicit part) -> T_s = filter(R_s) -> U_s = S(T_s), G_s = G(U_s)
+    ffe_status s;
     launch_adj(d, 0, a, 0, st);
     rhs_at(c, a.U2, a.F2);
     launch_adj(d, 1, a, SUB_A, st);
@@ -1497,7 +1489,18 @@ ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_i
     if ((s = filter_or_copy(c, a.R4, a.T4, 0))) return s;
     launch_adj(d, 6, a, SUB_B, st);
     rhs_at(c, a.U4, a.F4);
-    // reverse
+    if (next) {
+        launch_adj(d, 1, a, SUB_C, st);
+        if ((s = filter_or_copy(c, a.W, *next, 0))) return s;
+    }
+    return FFE_OK;
+}
+
+// Reverse sweep of one step given its stages (a.un, a.U2, a.T3, a.U3, a.T4, a.U4).
+static ffe_status adj_reverse(ffe_ctx* c, AdjArgs& a, Field lin, double* omega_bar) {
+    const Dev& d = c->d;
+    cudaStream_t st = c->st;
+    ffe_status s;
     CK(cudaMemsetAsync(c->d_omega_bar, 0, sizeof(double), st));
     if ((s = filter_or_copy(c, lin, a.tmp, 1))) return s;               // W-bar (u_{n+1} = filter(W))
     launch_adj(d, 2, a, 0, st);                                         // seeds
@@ -1523,6 +1526,60 @@ ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_i
     }
     CK(cudaGetLastError());
     return FFE_OK;
+}
+
+// the five stored stages of a step: [U2][T3][U3][T4][U4], state vectors
+static void point_stages(const Dev& d, AdjArgs& a, double* stages) {
+    const int64_t n = (int64_t)NV * (d.ndg + d.nfd);
+    Field* f[5] = {&a.U2, &a.T3, &a.U3, &a.T4, &a.U4};
+    for (int i = 0; i < 5; ++i) *f[i] = Field{stages + i * n, NV, d.ndg, d.nfd};
+}
+
+ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_in_dev, double* lam_out_dev,
+                            double* omega_bar) {
+    g_err.clear();
+    if (!c || !U_dev || !lam_in_dev || !lam_out_dev) return fail(FFE_EINVAL, "null argument");
+    ffe_status s;
+    if ((s = adjoint_ready(c))) return s;
+    const Dev& d = c->d;
+    AdjArgs a = c->adj;
+    a.un = Field{(double*)U_dev, NV, d.ndg, d.nfd};
+    a.lam = Field{lam_out_dev, NV, d.ndg, d.nfd};
+    launch_build_lists(d, c->st);
+    if ((s = adj_forward(c, a, nullptr))) return s;
+    return adj_reverse(c, a, Field{(double*)lam_in_dev, NV, d.ndg, d.nfd}, omega_bar);
+}
+
+ffe_status ffe_adjoint_forward(ffe_ctx* c, const double* U_dev, double* stages_dev, double* U_next_dev) {
+    g_err.clear();
+    if (!c || !U_dev) return fail(FFE_EINVAL, "null argument");
+    if (U_next_dev == U_dev) return fail(FFE_EINVAL, "U_next must not alias U");
+    ffe_status s;
+    if ((s = adjoint_ready(c))) return s;
+    const Dev& d = c->d;
+    AdjArgs a = c->adj;
+    a.un = Field{(double*)U_dev, NV, d.ndg, d.nfd};
+    if (stages_dev) point_stages(d, a, stages_dev);
+    launch_build_lists(d, c->st);
+    Field next{U_next_dev, NV, d.ndg, d.nfd};
+    if ((s = adj_forward(c, a, U_next_dev ? &next : nullptr))) return s;
+    CK(cudaGetLastError());
+    return FFE_OK;
+}
+
+ffe_status ffe_adjoint_reverse(ffe_ctx* c, const double* U_dev, const double* stages_dev, const double* lam_in_dev,
+                               double* lam_out_dev, double* omega_bar) {
+    g_err.clear();
+    if (!c || !U_dev || !stages_dev || !lam_in_dev || !lam_out_dev) return fail(FFE_EINVAL, "null argument");
+    ffe_status s;
+    if ((s = adjoint_ready(c))) return s;
+    const Dev& d = c->d;
+    AdjArgs a = c->adj;
+    a.un = Field{(double*)U_dev, NV, d.ndg, d.nfd};
+    a.lam = Field{lam_out_dev, NV, d.ndg, d.nfd};
+    point_stages(d, a, (double*)stages_dev);
+    launch_build_lists(d, c->st);
+    return adj_reverse(c, a, Field{(double*)lam_in_dev, NV, d.ndg, d.nfd}, omega_bar);
 }
 
 ffe_status ffe_luminosity(ffe_ctx* c, const double* U_dev, double r_L, double* L_host, double* grad_dev,

@@ -315,15 +315,33 @@ __device__ __forceinline__ bool act_point(const Dev& d, int64_t p, bool& isfd, i
     const int e = d.slot_elem ? d.slot_elem[sl] : sl;
     return e >= 0 && d.mask[e] == 1;
 }
+
+// The same points visited through the FD list: p < ndg is DG node p, else the
+// (p - ndg)-th cell of the listed FD elements; act_count is the range.
+__device__ __forceinline__ int64_t act_count(const Dev& d) { return d.ndg + (int64_t)d.counts[1] * d.ncell; }
+__device__ __forceinline__ bool act_listed(const Dev& d, int64_t p, bool& isfd, int64_t& q) {
+    if (p < d.ndg) {
+        isfd = false;
+        q = p;
+        return d.mask[p / d.nn] == 0;
+    }
+    isfd = true;
+    const int64_t r = p - d.ndg;
+    const int e = d.fd_list[r / d.ncell];
+    const int c = (int)(r % d.ncell);
+    q = fdb(d, e) + c;
+    return c < esz(d, e).ncell;
+}
 __device__ __forceinline__ double* fp(const Field& f, int v, bool isfd) { return isfd ? f.fd(v) : f.dg(v); }
 
 // forward recomputation: stage 1-2 (U2, G1, G2)
 __global__ void k_adj_s12(Dev d, AdjArgs a) {
     const double dt = d.dt, dta = dt * IM_A;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
         bool isfd;
         int64_t q;
-        if (!act_point(d, p, isfd, q)) continue;
+        if (!act_listed(d, p, isfd, q)) continue;
         double u[NV], U1[NV], g1[NG], g2[NG];
         for (int v = 0; v < NV; ++v) { u[v] = fp(a.un, v, isfd)[q]; U1[v] = u[v]; }
         stiff_solve_flat(U1, d, dta);
@@ -345,10 +363,11 @@ __global__ void k_adj_comb(Dev d, AdjArgs a, int sub) {
     const double dt = d.dt;
     const int gv[NG] = {0, 1, 2, 6, 7};
     const double z = 0.5 - IM_B - IM_H - IM_A;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
         bool isfd;
         int64_t q;
-        if (!act_point(d, p, isfd, q)) continue;
+        if (!act_listed(d, p, isfd, q)) continue;
         double u[NV];
         for (int v = 0; v < NV; ++v) u[v] = fp(a.un, v, isfd)[q];
         if (sub == SUB_A) {
@@ -375,10 +394,11 @@ __global__ void k_adj_solve(Dev d, AdjArgs a, int sub) {
     const Field& Tt = sub == SUB_A ? a.T3 : a.T4;
     const Field& Us = sub == SUB_A ? a.U3 : a.U4;
     const Field& Gs = sub == SUB_A ? a.G3 : a.G4;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
         bool isfd;
         int64_t q;
-        if (!act_point(d, p, isfd, q)) continue;
+        if (!act_listed(d, p, isfd, q)) continue;
         double u[NV], g[NG];
         for (int v = 0; v < NV; ++v) u[v] = fp(Tt, v, isfd)[q];
         stiff_solve_flat(u, d, dta);
@@ -393,10 +413,11 @@ __global__ void k_adj_solve(Dev d, AdjArgs a, int sub) {
 __global__ void k_adj_seed(Dev d, AdjArgs a) {
     const double dt = d.dt;
     const int gv[NG] = {0, 1, 2, 6, 7};
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
         bool isfd;
         int64_t q;
-        if (!act_point(d, p, isfd, q)) continue;
+        if (!act_listed(d, p, isfd, q)) continue;
         for (int v = 0; v < NV; ++v) {
             const double w = fp(a.tmp, v, isfd)[q];
             fp(a.ubar, v, isfd)[q] = w;
@@ -416,10 +437,11 @@ __global__ void k_adj_seed(Dev d, AdjArgs a) {
 
 // (2) tmp = U-bar of stage U_s: RHS-vjp result (in tmp) + G-vjp of Gs-bar at U_s
 __global__ void k_adj_addG(Dev d, Field U, Field Gb, Field io) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
         bool isfd;
         int64_t q;
-        if (!act_point(d, p, isfd, q)) continue;
+        if (!act_listed(d, p, isfd, q)) continue;
         double u[NV], gb[NG], ub[NV];
         for (int v = 0; v < NV; ++v) { u[v] = fp(U, v, isfd)[q]; ub[v] = fp(io, v, isfd)[q]; }
         for (int c = 0; c < NG; ++c) gb[c] = fp(Gb, c, isfd)[q];
@@ -432,10 +454,11 @@ __global__ void k_adj_addG(Dev d, Field U, Field Gb, Field io) {
 __global__ void k_adj_solve_back(Dev d, AdjArgs a, int sub) {
     const double dta = d.dt * IM_A;
     const Field& Tt = sub == SUB_A ? a.T3 : a.T4;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
         bool isfd;
         int64_t q;
-        if (!act_point(d, p, isfd, q)) continue;
+        if (!act_listed(d, p, isfd, q)) continue;
         double t[NV], ub[NV], tb[NV];
         for (int v = 0; v < NV; ++v) { t[v] = fp(Tt, v, isfd)[q]; ub[v] = fp(a.tmp, v, isfd)[q]; }
         solve_vjp(t, d, dta, ub, tb);
@@ -449,10 +472,11 @@ __global__ void k_adj_back_comb(Dev d, AdjArgs a, int sub) {
     const double dt = d.dt;
     const int gv[NG] = {0, 1, 2, 6, 7};
     const double z = 0.5 - IM_B - IM_H - IM_A;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.ndg + d.nfd; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
         bool isfd;
         int64_t q;
-        if (!act_point(d, p, isfd, q)) continue;
+        if (!act_listed(d, p, isfd, q)) continue;
         double rb[NV];
         for (int v = 0; v < NV; ++v) rb[v] = fp(a.tmp, v, isfd)[q];
         for (int v = 0; v < NV; ++v) fp(a.ubar, v, isfd)[q] += rb[v];

@@ -26,7 +26,7 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
            "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
            "ffe_fd_rhs_noalloc", "ffe_create_batch", "ffe_get_layout", "ffe_set_initial_batch",
            "ffe_rhs_vjp", "ffe_adjoint_step", "ffe_luminosity", "ffe_initial_tangent",
-           "ffe_freeze_mask", "ffe_last_error", "ffe_destroy"]
+           "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_last_error", "ffe_destroy"]
 
 
 class Domain(ctypes.Structure):
@@ -298,6 +298,21 @@ class Context:
         ob = ctypes.c_double(0.0)
         check(load().ffe_adjoint_step(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
                                       ctypes.c_void_p(lam_out.data_ptr()), ctypes.byref(ob)))
+        return ob.value
+
+    def adjoint_forward(self, U, stages=None, U_next=None):
+        """Recompute the stages of the step from U into stages (5 state vectors:
+        U2, T3, U3, T4, U4) and/or u_{n+1} into U_next."""
+        vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        check(load().ffe_adjoint_forward(self.h, vp(U), vp(stages), vp(U_next)))
+
+    def adjoint_reverse(self, U, stages, lam_in, lam_out):
+        """lam_out = lambda_n from lambda_{n+1} with the stored stages of the step
+        from U; returns dL/dOmega of the step."""
+        ob = ctypes.c_double(0.0)
+        check(load().ffe_adjoint_reverse(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(stages.data_ptr()),
+                                         ctypes.c_void_p(lam_in.data_ptr()), ctypes.c_void_p(lam_out.data_ptr()),
+                                         ctypes.byref(ob)))
         return ob.value
 
     def luminosity(self, U, r_L, grad=None, scale=1.0):

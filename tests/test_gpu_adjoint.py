@@ -284,3 +284,26 @@ def test_hybrid_luminosity_gradient_matches_central_differences(ffe):
         fd = (4.0 * d2 - d1) / 3.0
         # difference quotients of Lbar over the hybrid evolution repeat to ~1e-6
         assert abs(g[k] - fd) <= 3e-6 * abs(fd), (name, g[k], fd)
+
+
+def test_split_adjoint_matches_adjoint_step(ffe):
+    """ffe_adjoint_forward (stages kept) + ffe_adjoint_reverse = ffe_adjoint_step,
+    and the forward half's u_{n+1} is the step's result up to rounding."""
+    ctx, mask = _hybrid(ffe)
+    U, act = _perturb(ctx, mask, 21)
+    lam, _ = _dirs(U, act, 22)
+    ref = torch.zeros_like(U)
+    om_ref = ctx.adjoint_step(U, lam, ref)
+    stages = torch.empty(5 * U.numel(), dtype=U.dtype, device=U.device)
+    nxt = torch.empty_like(U)
+    ctx.adjoint_forward(U, stages, nxt)
+    out = torch.zeros_like(U)
+    om = ctx.adjoint_reverse(U, stages, lam, out)
+    scale = float(ref.abs().max())
+    assert float((out - ref).abs().max()) <= 1e-12 * scale
+    assert abs(om - om_ref) <= 1e-12 * max(abs(om_ref), 1e-300) or om == om_ref
+    ctx.set_state(U, mask)
+    ctx.step(1)
+    U1 = ctx.state()[0]
+    assert float(((nxt - U1) * act).abs().max()) <= 1e-10 * float((U1 * act).abs().max())
+    ctx.close()
