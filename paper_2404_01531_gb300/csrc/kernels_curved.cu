@@ -357,19 +357,21 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
 }
 
 
-// Persistent kernel over the DG work list: each item is dispatched on its
-// element's order (batched contexts mix P = 4 and P = 5 in one launch).
-template <int PMAX, int SUB, bool KS>
-__global__ void __launch_bounds__(DGC<PMAX>::NT, 1) k_dg_curved(Dev d, SubArgs a) {
+// Persistent kernel over the DG work list; flat metric: two CTAs per SM
+// (registers bounded accordingly; the metric-aware variant keeps one).  MIXED: each item is dispatched on its element's order
+// (batched contexts mix P = 4 and P = 5 in one launch); otherwise every element
+// has order PMAX and only that path is compiled.
+template <int PMAX, int SUB, bool KS, bool MIXED>
+__global__ void __launch_bounds__(DGC<PMAX>::NT, KS ? 1 : 2) k_dg_curved(Dev d, SubArgs a) {
     constexpr int NT = DGC<PMAX>::NT;
     extern __shared__ double sm[];
     const int nwork = d.counts[0];
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const int e = d.dg_list[w];
-        const int P = elem_P(d, e);
+        const int P = MIXED ? elem_P(d, e) : PMAX;
         if (P == PMAX) {
             dg_curved_elem<PMAX, NT, SUB, KS>(d, a, e, sm);
-        } else if constexpr (PMAX > 3) {
+        } else if constexpr (MIXED && PMAX > 3) {
             if (P == PMAX - 1) dg_curved_elem<PMAX - 1, NT, SUB, KS>(d, a, e, sm);
             else if constexpr (PMAX > 4) {
                 if (P == PMAX - 2) dg_curved_elem<PMAX - 2, NT, SUB, KS>(d, a, e, sm);
@@ -382,9 +384,14 @@ template <int P, bool KS>
 static void curved_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_t st) {
     using K = DGC<P>;
     const int grid = d.dg_grid > 0 ? d.dg_grid : 152 * 2;
-#define FFE_LAUNCH_C(S)                                                                                   \
-    cudaFuncSetAttribute(k_dg_curved<P, S, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);   \
-    k_dg_curved<P, S, KS><<<grid, K::NT, K::SMEM, st>>>(d, a);
+#define FFE_LAUNCH_C(S)                                                                                      \
+    if (d.eP) {                                                                                              \
+        cudaFuncSetAttribute(k_dg_curved<P, S, KS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM); \
+        k_dg_curved<P, S, KS, true><<<grid, K::NT, K::SMEM, st>>>(d, a);                                     \
+    } else {                                                                                                 \
+        cudaFuncSetAttribute(k_dg_curved<P, S, KS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM); \
+        k_dg_curved<P, S, KS, false><<<grid, K::NT, K::SMEM, st>>>(d, a);                                    \
+    }
     switch (sub) {
         case SUB_A: FFE_LAUNCH_C(SUB_A) break;
         case SUB_B: FFE_LAUNCH_C(SUB_B) break;

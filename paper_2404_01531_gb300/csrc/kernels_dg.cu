@@ -240,7 +240,7 @@ __device__ void dg_external_state(const Dev& d, const SubArgs& a, int e, int f, 
 }
 
 template <int P, int SUB>
-__global__ void __launch_bounds__(DGK<P>::NT, 2) k_dg_substep(Dev d, SubArgs a) {
+__global__ void __launch_bounds__(DGK<P>::NT, 3) k_dg_substep(Dev d, SubArgs a) {
     using K = DGK<P>;
     constexpr int np1 = K::np1, nn = K::nn, nf = K::nf, NT = K::NT, NW = K::NW;
     extern __shared__ double sm[];
