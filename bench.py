@@ -44,6 +44,18 @@ def _dist():
     return ws, rank, local
 
 
+def combine_ranks(ms, units, dist, device):
+    """Whole-job timing over the replicas: the slowest rank's time and the sum of
+    the units every rank advanced (one replica per rank, no exchange)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.item(), u.item()
+
+
 def cpu_oracle_rate(steps, budget_s=None):
     """Time the oracle, as it stands, on the bounded sample (1 thread)."""
     from oracle.problem import Problem
@@ -147,7 +159,7 @@ def run_reference(args):
 def run_shell(args):
     """The neutron-star shell (6 wedges x 6x6x12, P=5, eta=1e5) with its three
     innermost radial layers on FD subcells and the mask frozen: an FD-heavy
-    curved-mesh step (subcell flux with the shell map at every face)."""
+    curved-mesh step (subcell fluxes of every physical component at every face)."""
     import torch
     from paper_2404_01531_gb300 import ffe
     from paper_2404_01531_gb300.roofline import FP64_PEAK_TFLOPS, FD_FLUX_FLOPS, fd_faces_per_element
@@ -423,12 +435,7 @@ def main():
     inf = ctx.info()
     units = inf.node_updates - u0
     n_fd_end = inf.n_fd_elem
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    u = torch.tensor([float(units)], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-    ms_max, units_all = t.item(), u.item()
+    ms_max, units_all = combine_ranks(ms, units, dist, "cuda")
     value = units_all / (ms_max / 1e3)
     launches = None
     n0 = ctx.launch_count()
