@@ -28,9 +28,10 @@ import ffe_workloads as W  # noqa: E402
 
 METRIC = "RHS element-node updates/s FP64 at 1 GB300, % roofline; adjoint/forward time"
 UNIT = "element-node updates/s"
-# dram bytes (read + write) per launch of the dominant kernel from an ncu capture
-# (profiles/ summary of the same kernel); None until measured on the current kernel
-TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes (read + write) per ms of kernel time, from an ncu capture of the
+# kernel (profiles/k_fd_flux_breakdown_8x8x8.md): bytes and time of a launch
+# both scale with its FD elements (785 KB and 13.9 us each)
+DRAM_BYTES_PER_MS = {"fd_flux": 55.6e6}
 
 CPU_SAMPLE = dict(nx=16, ny=2, nz=2, x_half=0.5)
 CPU_SAMPLE_TEXT = ("oracle (numpy fp64, 1 thread) on a 16x2x2-element slab of the breakdown "
@@ -471,7 +472,8 @@ def main():
     if flops is not None:
         ach = flops / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+                "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": DRAM_BYTES_PER_MS[dom] * dom_ms / dom_launches if dom in DRAM_BYTES_PER_MS else None,
                 "kernel": dom, "peak_source": "derived: 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz",
                 "share": dom_ms / total_ms, "launches": dom_launches, "max_launch_ms": dom_max,
                 "units": {"fd_elem_updates": n_fd_upd, "dg_elem_updates": n_dg_upd}}
