@@ -127,6 +127,43 @@ __device__ __forceinline__ double weno5z(double v0, double v1, double v2, double
     return fma(A0, p0, fma(A1, p1, A2 * p2)) / (A0 + A1 + A2);
 }
 
+// Z-weighted combination of three candidates from their indicators b_k (eps
+// included); the ideal weights are taken as (1, 10, 5) (scale-free).
+__device__ __forceinline__ double weno5z_combine(double b0, double b1, double b2, double p0, double p1, double p2) {
+    const double t = b0 - b2;
+    const double t2 = t * t;
+    const double q0 = b0 * b0, q1 = b1 * b1, q2 = b2 * b2;
+    const double A0 = (q0 + t2) * (q1 * q2);
+    const double A1 = (10.0 * (q1 + t2)) * (q0 * q2);
+    const double A2 = (5.0 * (q2 + t2)) * (q0 * q1);
+    return fma(A0, p0, fma(A1, p1, A2 * p2)) / (A0 + A1 + A2);
+}
+
+// Both values at the face between v2 and v3 from the six cells v0..v5:
+// uL = weno5z(v0..v4), uR = weno5z(v5..v1).  The two share two candidates
+// (the quadratics through v1..v3 and v2..v4) and two second differences.
+__device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, double v3, double v4, double v5,
+                                            double eps, double& uL, double& uR) {
+    const double c13 = 13.0 / 12.0;
+    const double p123 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
+    const double p234 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
+    const double pL0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
+    const double pR0 = fma(0.375, v5, fma(-1.25, v4, 1.875 * v3));
+    const double a012 = v0 - 2.0 * v1 + v2, a123 = v1 - 2.0 * v2 + v3;
+    const double a234 = v2 - 2.0 * v3 + v4, a345 = v3 - 2.0 * v4 + v5;
+    const double k123 = c13 * a123 * a123, k234 = c13 * a234 * a234;
+    const double eL0 = v0 - 4.0 * v1 + 3.0 * v2, eL1 = v1 - v3, eL2 = 3.0 * v2 - 4.0 * v3 + v4;
+    const double eR0 = v5 - 4.0 * v4 + 3.0 * v3, eR1 = v4 - v2, eR2 = 3.0 * v3 - 4.0 * v2 + v1;
+    const double bL0 = fma(c13 * a012, a012, fma(0.25 * eL0, eL0, eps));
+    const double bL1 = k123 + fma(0.25 * eL1, eL1, eps);
+    const double bL2 = k234 + fma(0.25 * eL2, eL2, eps);
+    const double bR0 = fma(c13 * a345, a345, fma(0.25 * eR0, eR0, eps));
+    const double bR1 = k234 + fma(0.25 * eR1, eR1, eps);
+    const double bR2 = k123 + fma(0.25 * eR2, eR2, eps);
+    uL = weno5z_combine(bL0, bL1, bL2, pL0, p123, p234);
+    uR = weno5z_combine(bR0, bR1, bR2, pR0, p234, p123);
+}
+
 // Reverse mode of weno5z: g[i] += yb d weno5z(v0..v4)/d v_i.  The weights are
 // homogeneous of degree 0 in (b_0, b_1, b_2), so the b_k are first scaled by
 // their maximum; the A_k are then O(1) and their derivatives stay in range.

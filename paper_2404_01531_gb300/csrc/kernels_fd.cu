@@ -198,8 +198,7 @@ __device__ __forceinline__ void reconstruct(const Dev& d, int wl, int k, int m, 
         const double* src = ext_at(d, qq, wl) + base;
         const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
         const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
-        UL[qq] = weno5z(v0, v1, v2, v3, v4, d.weno_eps);
-        UR[qq] = weno5z(v5, v4, v3, v2, v1, d.weno_eps);
+        weno5z_pair(v0, v1, v2, v3, v4, v5, d.weno_eps, UL[qq], UR[qq]);
         Um[qq] = v2;
         Up[qq] = v3;
     }
