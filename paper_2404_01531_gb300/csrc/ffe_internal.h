@@ -35,6 +35,10 @@ struct Tables {
     double x[MAXNP], w[MAXNP], w0;
     double D[MAXNP][MAXNP];        // D_ij = l_j'(x_i)
     double Filt[MAXNP][MAXNP];     // V diag(sigma) V^-1
+    // Filt = I - sum_r FrV[r] FrW[r]^T over the nfr modes m the filter damps by
+    // more than 1e-20 (FrV[r][i] = P_m(x_i), FrW[r][j] = (1 - sigma_m) (V^-1)[m][j])
+    int nfr;
+    double FrV[MAXNP][MAXNP], FrW[MAXNP][MAXNP];
     double Pi[MAXNP][MAXNP];       // projection on Legendre modes p <= P - M
     double P2F[MAXNC][MAXNP];      // DG -> FD (Lagrange evaluation at subcell centres)
     double F2D[MAXNP][MAXNC];      // FD -> DG (6-point Lagrange, shifted inside)

@@ -145,6 +145,20 @@ void build_tables(int P, double fa, double fb, int M, Tables& T) {
             T.Filt[i][j] = (double)sf;
             T.Pi[i][j] = (double)sp;
         }
+    // low-rank form of the filter: modes damped by 1 - sigma_m > 1e-20 (the rest
+    // change a nodal value by less than 1e-20 of the mode's coefficient)
+    std::vector<int> damped;
+    for (int m = 0; m < np1; ++m)
+        if (-expm1l(-(ld)fa * powl((ld)m / P, 2.0L * (ld)fb)) > 1e-20L) damped.push_back(m);
+    T.nfr = (int)damped.size();
+    for (int r = 0; r < T.nfr; ++r) {
+        const int m = damped[r];
+        const ld dm = -expm1l(-(ld)fa * powl((ld)m / P, 2.0L * (ld)fb));
+        for (int i = 0; i < np1; ++i) {
+            T.FrV[r][i] = (double)V[i * np1 + m];
+            T.FrW[r][i] = (double)(dm * Vi[m * np1 + i]);
+        }
+    }
     std::vector<ld> xc(nc);
     const ld dxi = 2.0L / nc;
     for (int c = 0; c < nc; ++c) xc[c] = -1.0L + (c + 0.5L) * dxi;

@@ -8,6 +8,7 @@
 // |beta.n^|, then the same stage order as the box kernel (explicit part,
 // filter, stiff solve, clamp, indicator).  The stiff solve, clamp and indicator
 // use the gamma inner product.
+#include "dgfilter.cuh"
 #include "ffe_internal.h"
 #include "physics.cuh"
 #include "physics_gen.cuh"
@@ -268,21 +269,9 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
             if (act)
                 for (int v = 0; v < NV; ++v) sU[v * nn + tid] = u[v];
             __syncthreads();
-            for (int k = 0; k < 3; ++k) {
-                const double* src = (k == 1) ? sT : sU;
-                double* dst = (k == 1) ? sU : sT;
-                const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
-                if (act) {
-                    const int base = tid - ci[k] * stride;
-                    for (int v = 0; v < NV; ++v) {
-                        double acc = 0.0;
-                        for (int mm = 0; mm < np1; ++mm) acc = fma(T.Filt[ci[k]][mm], src[v * nn + base + mm * stride], acc);
-                        if (k < 2) dst[v * nn + tid] = acc;
-                        else u[v] = acc;
-                    }
-                }
-                __syncthreads();
-            }
+            filter_lowrank<P, NT>(T, sU, sT, act);
+            if (act)
+                for (int v = 0; v < NV; ++v) u[v] = sU[v * nn + tid];
         }
         // implicit part after the filter; G at the stage value: G_s = (U_s - R~_s)/(dt a)
         if (act) {

@@ -12,6 +12,7 @@
 //   amplifies by eta (unstable for eta dt >> 1).
 #include <cstdio>
 
+#include "dgfilter.cuh"
 #include "ffe_internal.h"
 #include "physics.cuh"
 #include "stage.cuh"
@@ -352,37 +353,12 @@ __global__ void __launch_bounds__(DGK<P>::NT, 3) k_dg_substep(Dev d, SubArgs a) 
         }
         __syncthreads();   // sU, sJ, sC are free from here on
         if (d.filter_on) {
-            // x pass sU -> sT, y pass sT -> sU, z pass sU -> sT
             if (act)
                 for (int v = 0; v < NV; ++v) sU[v * nn + tid] = u[v];
             __syncthreads();
-            if (act) {
-                const int ox = np1 * (j + np1 * k);
-                for (int v = 0; v < NV; ++v) {
-                    double acc = 0.0;
-                    for (int m = 0; m < np1; ++m) acc = fma(T.Filt[i][m], sU[v * nn + ox + m], acc);
-                    sT[v * nn + tid] = acc;
-                }
-            }
-            __syncthreads();
-            if (act) {
-                const int oy = i + np1 * np1 * k;
-                for (int v = 0; v < NV; ++v) {
-                    double acc = 0.0;
-                    for (int m = 0; m < np1; ++m) acc = fma(T.Filt[j][m], sT[v * nn + oy + np1 * m], acc);
-                    sU[v * nn + tid] = acc;
-                }
-            }
-            __syncthreads();
-            if (act) {
-                const int oz = i + np1 * j;
-                for (int v = 0; v < NV; ++v) {
-                    double acc = 0.0;
-                    for (int m = 0; m < np1; ++m) acc = fma(T.Filt[k][m], sU[v * nn + oz + np1 * np1 * m], acc);
-                    u[v] = acc;
-                }
-            }
-            __syncthreads();
+            filter_lowrank<P, NT>(T, sU, sT, act);
+            if (act)
+                for (int v = 0; v < NV; ++v) u[v] = sU[v * nn + tid];
         }
         // implicit part after the filter; G at the stage value: G_s = (U_s - R~_s)/(dt a)
         if (act) {

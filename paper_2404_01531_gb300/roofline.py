@@ -2,19 +2,27 @@
 add/mul/div/sqrt = 1), counted from the operations the method defines, not
 from the instructions the kernels happen to issue.  Used for the roofline
 fraction: achieved = count x units per launch / launch time."""
+import math
 
 # FP64 peak: 2 FMA lanes per clock per SM x 2 flops x 152 SMs x 2.07 GHz
 # (the GB300's nominal 1.25 TFLOP/s FP64 at its 2070 MHz maximum SM clock).
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 
-def dg_flops_per_node(P, sub, filter_on=True, tci_on=True, solve=True):
+def filter_rank(P, a=36.0, b=50.0):
+    """Modes the exponential filter sigma_m = exp(-a (m/P)^(2b)) damps by more
+    than 1e-20: the rank of I - F along one axis as the DG kernels apply it."""
+    return sum(1 for m in range(P + 1) if -math.expm1(-a * (m / P) ** (2 * b)) > 1e-20)
+
+
+def dg_flops_per_node(P, sub, filter_on=True, tci_on=True, solve=True, a=36.0, b=50.0):
     """One DG node through k_dg_substep: volume term (27 directional (P+1)-point
     contractions), derivative combination and explicit sources, the lifted
     Rusanov correction (6 (P+1)^2 face nodes per (P+1)^3 nodes), the IMEX stage
     combination, the pointwise stiff solve and implicit operator (substeps A, B),
-    the dense F x F x F filter of 9 variables and the indicator (|B|, 3 low-pass
-    contractions, two sums).  sub: 0 (A), 1 (B), 2 (C)."""
+    the filter of 9 variables in its low-rank form (per axis and kept mode one
+    (P+1)-point dot product per line and one FMA per node) and the indicator
+    (|B|, 3 low-pass contractions, two sums).  sub: 0 (A), 1 (B), 2 (C)."""
     n = P + 1
     f = 27 * n * 2              # volume contractions
     f += 22                     # combination + sources
@@ -23,7 +31,7 @@ def dg_flops_per_node(P, sub, filter_on=True, tci_on=True, solve=True):
     if sub != 2 and solve:
         f += 38 + 30            # stiff solve + implicit operator
     if filter_on:
-        f += 3 * n * 2 * 9
+        f += 3 * 2 * 2 * 9 * filter_rank(P, a, b)
     if tci_on:
         f += 6 + 3 * n * 2 + 5
     return f

@@ -89,3 +89,23 @@ def test_projections(N):
         assert nz.max() - nz.min() < 6
         nearest = np.argmin(np.abs(xc - x[j]))
         assert nz.min() <= nearest <= nz.max()
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7])
+def test_filter_low_rank_form(N):
+    """The DG kernels apply the filter as I - sum_m (1 - sigma_m) v_m w_m^T over
+    the modes damped by more than 1e-20 (v_m the nodal values of mode m, w_m
+    row m of V^-1).  That drops (1 - sigma_m) v_m w_m^T for the other modes, a
+    change below 1e-20 per unit coefficient: the forms agree to rounding, and
+    at the default a = 36, b = 50 only modes N-1 and N (N = 2: mode N; N = 6, 7:
+    modes N-2 .. N) are kept."""
+    x, _ = basis.lgl_nodes_weights(N)
+    V = basis.vandermonde(N, x)
+    Vi = np.linalg.inv(V)
+    sig = basis.filter_sigma(N)
+    damp = -np.expm1(-36.0 * (np.arange(N + 1) / N) ** 100)
+    kept = [m for m in range(N + 1) if damp[m] > 1e-20]
+    assert kept == list(range(N - {2: 0, 6: 2, 7: 2}.get(N, 1), N + 1))
+    low = np.eye(N + 1) - sum(damp[m] * np.outer(V[:, m], Vi[m]) for m in kept)
+    np.testing.assert_allclose(low, basis.filter_matrix(N, x), rtol=0, atol=1e-14)
+    assert np.all(np.abs(1.0 - sig[[m for m in range(N + 1) if m not in kept]]) <= 1e-20)
