@@ -280,6 +280,15 @@ ffe_status ffe_luminosity(ffe_ctx* ctx, const double* U_dev, double r_L, double*
  * parameter `which` (DIPOLE: 0 = mu, 2 = chi) at the nodes, into dU_dev. */
 ffe_status ffe_initial_tangent(ffe_ctx* ctx, int which, double* dU_dev);
 
+/* Reciprocal 1/x that the WENO5-Z weights use (the hardware approximation
+ * rcp.approx.ftz.f64 refined by two Newton-Raphson steps), evaluated
+ * elementwise: y_dev[i] = 1/x_dev[i], i < n, both device arrays of doubles
+ * (caller-owned; x_dev and y_dev may be the same).  Defined for positive
+ * normal x whose reciprocal is normal (below 2^1022); within about one ulp of
+ * the correctly rounded quotient.  For accuracy tests; enqueued on
+ * cuda_stream.  FFE_EINVAL for n < 0 or a NULL array with n > 0. */
+ffe_status ffe_eval_recip(const double* x_dev, double* y_dev, int64_t n, void* cuda_stream);
+
 /* Thread-local message of the last failed call ("" if none). */
 const char* ffe_last_error(void);
 

@@ -101,34 +101,39 @@ __device__ __forceinline__ int chunk_n(const Dev& d, int ci, int w0) {
     return n < 0 ? 0 : (n > d.chunk ? d.chunk : n);
 }
 
+// 1/d for a positive normal d whose reciprocal is normal: the hardware
+// approximation rcp.approx.ftz.f64 refined by two Newton-Raphson steps for
+// f(y) = 1/y - d, y <- y + y (1 - d y) (each squares the relative error; the
+// residual 1 - d y is exact in one FMA when y is close to 1/d).  Within about
+// one ulp of the rounded quotient (ffe_eval_recip exposes it for tests); used
+// for the WENO5-Z weight denominators, positive sums bounded away from zero
+// (for sums above 2^1022 the flushed reciprocal is 0; the quotient it
+// replaces would overflow there for candidates above 4 in magnitude).
+__device__ __forceinline__ double recip_nr(double d) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+    double r = fma(-d, y, 1.0);
+    y = fma(y, r, y);
+    r = fma(-d, y, 1.0);
+    return fma(y, r, y);
+}
+
+// 2^-floor(log2 x) for a positive normal x below 2^1022: x times it lies in
+// [1, 2) and the product is exact (integer operations on the exponent field).
+__device__ __forceinline__ double pow2_inv_scale(double x) {
+    const long long e = __double_as_longlong(x) >> 52;
+    return __longlong_as_double((2046LL - e) << 52);
+}
+
 // WENO5-Z at the face right of v2 from v0..v4 (point-value interpolation
 // candidates, ideal weights (1, 10, 5)/16, Jiang-Shu indicators, Z weights q = 2).
 // The Z weights alpha_k = d_k (1 + tau^2/b_k^2), b_k = beta_k + eps, are scaled
 // by b_0^2 b_1^2 b_2^2 so that the normalised combination needs one division:
 //   A_k = d_k (b_k^2 + tau^2) prod_{j != k} b_j^2,  value = sum A_k p_k / sum A_k.
 // With eps >= 1e-40 every A_k stays above 1e-240, inside the normal range.
-__device__ __forceinline__ double weno5z(double v0, double v1, double v2, double v3, double v4, double eps) {
-    const double p0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
-    const double p1 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
-    const double p2 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
-    const double c13 = 13.0 / 12.0;
-    const double s0a = v0 - 2.0 * v1 + v2, s0b = v0 - 4.0 * v1 + 3.0 * v2;
-    const double s1a = v1 - 2.0 * v2 + v3, s1b = v1 - v3;
-    const double s2a = v2 - 2.0 * v3 + v4, s2b = 3.0 * v2 - 4.0 * v3 + v4;
-    const double b0 = fma(c13 * s0a, s0a, 0.25 * s0b * s0b) + eps;
-    const double b1 = fma(c13 * s1a, s1a, 0.25 * s1b * s1b) + eps;
-    const double b2 = fma(c13 * s2a, s2a, 0.25 * s2b * s2b) + eps;
-    const double t = b0 - b2;
-    const double t2 = t * t;
-    const double q0 = b0 * b0, q1 = b1 * b1, q2 = b2 * b2;
-    const double A0 = (0.0625 * (q0 + t2)) * (q1 * q2);
-    const double A1 = (0.625 * (q1 + t2)) * (q0 * q2);
-    const double A2 = (0.3125 * (q2 + t2)) * (q0 * q1);
-    return fma(A0, p0, fma(A1, p1, A2 * p2)) / (A0 + A1 + A2);
-}
-
-// Z-weighted combination of three candidates from their indicators b_k (eps
-// included); the ideal weights are taken as (1, 10, 5) (scale-free).
+// weno5z_combine: the Z-weighted combination of three candidates from their
+// indicators b_k (eps included); the ideal weights are taken as (1, 10, 5)
+// (scale-free).
 __device__ __forceinline__ double weno5z_combine(double b0, double b1, double b2, double p0, double p1, double p2) {
     const double t = b0 - b2;
     const double t2 = t * t;
@@ -136,11 +141,11 @@ __device__ __forceinline__ double weno5z_combine(double b0, double b1, double b2
     const double A0 = (q0 + t2) * (q1 * q2);
     const double A1 = (10.0 * (q1 + t2)) * (q0 * q2);
     const double A2 = (5.0 * (q2 + t2)) * (q0 * q1);
-    return fma(A0, p0, fma(A1, p1, A2 * p2)) / (A0 + A1 + A2);
+    return fma(A0, p0, fma(A1, p1, A2 * p2)) * recip_nr(A0 + A1 + A2);
 }
 
-// Both values at the face between v2 and v3 from the six cells v0..v5:
-// uL = weno5z(v0..v4), uR = weno5z(v5..v1).  The two share two candidates
+// Both values at the face between v2 and v3 from the six cells v0..v5: uL the
+// WENO5-Z value from v0..v4, uR the one from v5..v1 (mirrored).  The two share two candidates
 // (the quadratics through v1..v3 and v2..v4) and two second differences.
 __device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, double v3, double v4, double v5,
                                             double eps, double& uL, double& uR) {
@@ -164,52 +169,83 @@ __device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, dou
     uR = weno5z_combine(bR0, bR1, bR2, pR0, p234, p123);
 }
 
-// Reverse mode of weno5z: g[i] += yb d weno5z(v0..v4)/d v_i.  The weights are
-// homogeneous of degree 0 in (b_0, b_1, b_2), so the b_k are first scaled by
-// their maximum; the A_k are then O(1) and their derivatives stay in range.
-__device__ __forceinline__ void weno5z_vjp(double v0, double v1, double v2, double v3, double v4, double eps,
-                                           double yb, double* g) {
-    const double p0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
-    const double p1 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
-    const double p2 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
-    const double c13 = 13.0 / 12.0;
-    const double s0a = v0 - 2.0 * v1 + v2, s0b = v0 - 4.0 * v1 + 3.0 * v2;
-    const double s1a = v1 - 2.0 * v2 + v3, s1b = v1 - v3;
-    const double s2a = v2 - 2.0 * v3 + v4, s2b = 3.0 * v2 - 4.0 * v3 + v4;
-    const double B0 = fma(c13 * s0a, s0a, 0.25 * s0b * s0b) + eps;
-    const double B1 = fma(c13 * s1a, s1a, 0.25 * s1b * s1b) + eps;
-    const double B2 = fma(c13 * s2a, s2a, 0.25 * s2b * s2b) + eps;
-    const double bm = fmax(B0, fmax(B1, B2)), ibm = 1.0 / bm;
-    const double b0 = B0 * ibm, b1 = B1 * ibm, b2 = B2 * ibm;
+// Reverse mode of weno5z_combine for indicators B_k (eps included) and
+// candidates p_k: from the value's adjoint yb, the candidates' adjoints pb_k
+// and the indicators' adjoints Bb_k.  With A_k = d_k s_k P_k, s_k = b_k^2 +
+// t^2, t = b_0 - b_2, P_k the product of the other two b_j^2, d = (1, 10, 5)
+// and W_k = d_k dL/dA_k = d_k yb (p_k - value) / sum A:
+//   dL/db_0 = 2 (t T + b_0 (W_0 P_0 + W_1 s_1 b_2^2 + W_2 s_2 b_1^2)),
+//   dL/db_1 = 2 b_1 (W_0 s_0 b_2^2 + W_1 P_1 + W_2 s_2 b_0^2),
+//   dL/db_2 = 2 (-t T + b_2 (W_0 s_0 b_1^2 + W_1 s_1 b_0^2 + W_2 P_2)),
+// T = sum_k W_k P_k.  The weights are homogeneous of degree 0 in the b_k, so
+// the B_k are first scaled exactly by the power of two of their maximum; the
+// A_k are then O(1) and their derivatives stay in range.
+__device__ __forceinline__ void weno5z_combine_vjp(double B0, double B1, double B2, double p0, double p1, double p2,
+                                                   double yb, double& pb0, double& pb1, double& pb2, double& Bb0,
+                                                   double& Bb1, double& Bb2) {
+    const double sc = pow2_inv_scale(fmax(B0, fmax(B1, B2)));
+    const double b0 = B0 * sc, b1 = B1 * sc, b2 = B2 * sc;
     const double t = b0 - b2, t2 = t * t;
     const double q0 = b0 * b0, q1 = b1 * b1, q2 = b2 * b2;
-    const double A0 = (0.0625 * (q0 + t2)) * (q1 * q2);
-    const double A1 = (0.625 * (q1 + t2)) * (q0 * q2);
-    const double A2 = (0.3125 * (q2 + t2)) * (q0 * q1);
-    const double iS = 1.0 / (A0 + A1 + A2);
+    const double s0 = q0 + t2, s1 = q1 + t2, s2 = q2 + t2;
+    const double P0 = q1 * q2, P1 = q0 * q2, P2 = q0 * q1;
+    const double A0 = s0 * P0, A1 = 10.0 * (s1 * P1), A2 = 5.0 * (s2 * P2);
+    const double iS = recip_nr(A0 + A1 + A2);
     const double val = fma(A0, p0, fma(A1, p1, A2 * p2)) * iS;
-    const double pb0 = yb * A0 * iS, pb1 = yb * A1 * iS, pb2 = yb * A2 * iS;
-    const double ab0 = yb * (p0 - val) * iS, ab1 = yb * (p1 - val) * iS, ab2 = yb * (p2 - val) * iS;
-    // A0 = d0 (q0 + t^2) q1 q2, A1 = d1 (q1 + t^2) q0 q2, A2 = d2 (q2 + t^2) q0 q1, t = b0 - b2
-    const double bb0 = ab0 * 0.0625 * (2.0 * b0 + 2.0 * t) * q1 * q2 +
-                       ab1 * 0.625 * (2.0 * t * q0 * q2 + (q1 + t2) * 2.0 * b0 * q2) +
-                       ab2 * 0.3125 * (2.0 * t * q0 * q1 + (q2 + t2) * 2.0 * b0 * q1);
-    const double bb1 = ab0 * 0.0625 * (q0 + t2) * 2.0 * b1 * q2 + ab1 * 0.625 * 2.0 * b1 * q0 * q2 +
-                       ab2 * 0.3125 * (q2 + t2) * q0 * 2.0 * b1;
-    const double bb2 = ab0 * 0.0625 * (-2.0 * t * q1 * q2 + (q0 + t2) * q1 * 2.0 * b2) +
-                       ab1 * 0.625 * (-2.0 * t * q0 * q2 + (q1 + t2) * q0 * 2.0 * b2) +
-                       ab2 * 0.3125 * (2.0 * b2 - 2.0 * t) * q0 * q1;
-    // back to the unscaled beta_k (b_k = beta_k / bm; bm is a maximum, whose own
-    // derivative cancels because the weights are scale invariant)
-    const double be0 = bb0 * ibm, be1 = bb1 * ibm, be2 = bb2 * ibm;
-    const double s0ab = be0 * 2.0 * c13 * s0a, s0bb = be0 * 0.5 * s0b;
-    const double s1ab = be1 * 2.0 * c13 * s1a, s1bb = be1 * 0.5 * s1b;
-    const double s2ab = be2 * 2.0 * c13 * s2a, s2bb = be2 * 0.5 * s2b;
-    g[0] += 0.375 * pb0 + s0ab + s0bb;
-    g[1] += -1.25 * pb0 - 0.125 * pb1 - 2.0 * s0ab - 4.0 * s0bb + s1ab + s1bb;
-    g[2] += 1.875 * pb0 + 0.75 * pb1 + 0.375 * pb2 + s0ab + 3.0 * s0bb - 2.0 * s1ab + s2ab + 3.0 * s2bb;
-    g[3] += 0.375 * pb1 + 0.75 * pb2 + s1ab - s1bb - 2.0 * s2ab - 4.0 * s2bb;
-    g[4] += -0.125 * pb2 + s2ab + s2bb;
+    const double y = yb * iS;
+    pb0 = y * A0;
+    pb1 = y * A1;
+    pb2 = y * A2;
+    const double W0 = y * (p0 - val), W1 = (10.0 * y) * (p1 - val), W2 = (5.0 * y) * (p2 - val);
+    const double W0P0 = W0 * P0, W0s0 = W0 * s0, W1s1 = W1 * s1, W2s2 = W2 * s2;
+    const double T = fma(W1, P1, fma(W2, P2, W0P0));
+    const double X0 = fma(W1s1, q2, fma(W2s2, q1, W0P0));
+    const double X1 = fma(W0s0, q2, fma(W2s2, q0, W1 * P1));
+    const double X2 = fma(W0s0, q1, fma(W1s1, q0, W2 * P2));
+    const double sc2 = 2.0 * sc;
+    Bb0 = sc2 * fma(t, T, b0 * X0);
+    Bb1 = sc2 * (b1 * X1);
+    Bb2 = sc2 * fma(-t, T, b2 * X2);
+}
+
+// Reverse mode of weno5z_pair: g[i] += ybL d uL/d v_i + ybR d uR/d v_i,
+// i = 0..5, through the shared candidates and second differences.
+__device__ __forceinline__ void weno5z_pair_vjp(double v0, double v1, double v2, double v3, double v4, double v5,
+                                                double eps, double ybL, double ybR, double* g) {
+    const double c13 = 13.0 / 12.0;
+    const double p123 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
+    const double p234 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
+    const double pL0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
+    const double pR0 = fma(0.375, v5, fma(-1.25, v4, 1.875 * v3));
+    const double a012 = v0 - 2.0 * v1 + v2, a123 = v1 - 2.0 * v2 + v3;
+    const double a234 = v2 - 2.0 * v3 + v4, a345 = v3 - 2.0 * v4 + v5;
+    const double k123 = c13 * a123 * a123, k234 = c13 * a234 * a234;
+    const double eL0 = v0 - 4.0 * v1 + 3.0 * v2, eL1 = v1 - v3, eL2 = 3.0 * v2 - 4.0 * v3 + v4;
+    const double eR0 = v5 - 4.0 * v4 + 3.0 * v3, eR1 = v4 - v2, eR2 = 3.0 * v3 - 4.0 * v2 + v1;
+    const double BL0 = fma(c13 * a012, a012, fma(0.25 * eL0, eL0, eps));
+    const double BL1 = k123 + fma(0.25 * eL1, eL1, eps);
+    const double BL2 = k234 + fma(0.25 * eL2, eL2, eps);
+    const double BR0 = fma(c13 * a345, a345, fma(0.25 * eR0, eR0, eps));
+    const double BR1 = k234 + fma(0.25 * eR1, eR1, eps);
+    const double BR2 = k123 + fma(0.25 * eR2, eR2, eps);
+    double pbL0, pbL1, pbL2, BbL0, BbL1, BbL2, pbR0, pbR1, pbR2, BbR0, BbR1, BbR2;
+    weno5z_combine_vjp(BL0, BL1, BL2, pL0, p123, p234, ybL, pbL0, pbL1, pbL2, BbL0, BbL1, BbL2);
+    weno5z_combine_vjp(BR0, BR1, BR2, pR0, p234, p123, ybR, pbR0, pbR1, pbR2, BbR0, BbR1, BbR2);
+    // adjoints of the shared and one-sided intermediates
+    const double p123b = pbL1 + pbR2, p234b = pbL2 + pbR1;
+    const double c26 = 2.0 * c13;
+    const double a012b = c26 * a012 * BbL0, a345b = c26 * a345 * BbR0;
+    const double a123b = c26 * a123 * (BbL1 + BbR2), a234b = c26 * a234 * (BbL2 + BbR1);
+    const double eL0b = 0.5 * eL0 * BbL0, eL1b = 0.5 * eL1 * BbL1, eL2b = 0.5 * eL2 * BbL2;
+    const double eR0b = 0.5 * eR0 * BbR0, eR1b = 0.5 * eR1 * BbR1, eR2b = 0.5 * eR2 * BbR2;
+    g[0] += fma(0.375, pbL0, a012b + eL0b);
+    g[1] += fma(-1.25, pbL0, fma(-0.125, p123b, fma(-2.0, a012b, fma(-4.0, eL0b, a123b + eL1b + eR2b))));
+    g[2] += fma(1.875, pbL0, fma(0.75, p123b, fma(0.375, p234b, fma(-2.0, a123b, fma(3.0, eL0b + eL2b,
+               fma(-4.0, eR2b, a012b + a234b - eR1b))))));
+    g[3] += fma(0.375, p123b, fma(0.75, p234b, fma(1.875, pbR0, fma(-2.0, a234b, fma(3.0, eR0b + eR2b,
+               fma(-4.0, eL2b, a123b + a345b - eL1b))))));
+    g[4] += fma(-0.125, p234b, fma(-1.25, pbR0, fma(-2.0, a345b, fma(-4.0, eR0b, a234b + eL2b + eR1b))));
+    g[5] += fma(0.375, pbR0, a345b + eR0b);
 }
 
 // face fi of direction k: position m along k, tangential (ta, tb); false past the element's faces

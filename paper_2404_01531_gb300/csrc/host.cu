@@ -946,6 +946,15 @@ void set_last_error(const char* msg) { g_err = msg; }
 // ------------------------------------------------------------------ C ABI ---
 extern "C" {
 
+ffe_status ffe_eval_recip(const double* x_dev, double* y_dev, int64_t n, void* cuda_stream) {
+    g_err.clear();
+    if (n < 0 || (n > 0 && (!x_dev || !y_dev))) return fail(FFE_EINVAL, "bad argument");
+    if (n == 0) return FFE_OK;
+    launch_eval_recip(x_dev, y_dev, n, (cudaStream_t)cuda_stream);
+    CK(cudaGetLastError());
+    return FFE_OK;
+}
+
 const char* ffe_last_error(void) { return g_err.c_str(); }
 
 ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, int P, const ffe_metric* metric,

@@ -103,14 +103,8 @@ __global__ void k_fdv_faces(Dev d, const int* list, int ci, int w0, Field L, dou
             const double* src = ext_at(d, qq, wl) + base;
             const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
             const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
-            double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, h[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-            if (ubL[qq] != 0.0) weno5z_vjp(v0, v1, v2, v3, v4, d.weno_eps, ubL[qq], g);
-            if (ubR[qq] != 0.0) weno5z_vjp(v5, v4, v3, v2, v1, d.weno_eps, ubR[qq], h);
-            g[5] += h[0];
-            g[4] += h[1];
-            g[3] += h[2];
-            g[2] += h[3];
-            g[1] += h[4];
+            double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            if (ubL[qq] != 0.0 || ubR[qq] != 0.0) weno5z_pair_vjp(v0, v1, v2, v3, v4, v5, d.weno_eps, ubL[qq], ubR[qq], g);
             g[2] += ubm[qq];
             g[3] += ubp[qq];
             double* dst = extb_at(d, extb, qq, wl) + base;

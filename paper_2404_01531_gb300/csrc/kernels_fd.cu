@@ -615,4 +615,17 @@ void launch_fd2dg(const Dev& d, Field un, cudaStream_t st) {
     g_launch_counter += 1;
 }
 
+// ---------------------------------------------------------------------------
+// The WENO5-Z reciprocal, elementwise (accuracy tests of recip_nr).
+__global__ void k_eval_recip(const double* x, double* y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = recip_nr(x[i]);
+}
+
+void launch_eval_recip(const double* x, double* y, int64_t n, cudaStream_t st) {
+    const int64_t blocks = (n + 255) / 256;
+    k_eval_recip<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(x, y, n);
+    g_launch_counter += 1;
+}
+
 }  // namespace ffe

@@ -26,7 +26,8 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
            "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
            "ffe_fd_rhs_noalloc", "ffe_create_batch", "ffe_get_layout", "ffe_set_initial_batch",
            "ffe_rhs_vjp", "ffe_adjoint_step", "ffe_luminosity", "ffe_initial_tangent",
-           "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_last_error", "ffe_destroy"]
+           "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_eval_recip", "ffe_last_error",
+           "ffe_destroy"]
 
 
 class Domain(ctypes.Structure):
@@ -100,6 +101,7 @@ def load():
         "ffe_adjoint_step": [P, P, P, P, ctypes.POINTER(d)],
         "ffe_luminosity": [P, P, d, ctypes.POINTER(d), P, d],
         "ffe_initial_tangent": [P, i, P],
+        "ffe_eval_recip": [P, P, ctypes.c_int64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -128,6 +130,16 @@ def fd_rhs_noalloc(P, Uext, h, eta, weno_eps, fd_corrector, out, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream()
     check(load().ffe_fd_rhs_noalloc(P, n, hh, eta, weno_eps, int(fd_corrector), ctypes.c_void_p(Uext.data_ptr()),
                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
+
+
+def eval_recip(x, y, stream=None):
+    """y = 1/x elementwise with the reciprocal the WENO5-Z kernels use (see
+    ffe_eval_recip in include/ffe.h); x, y: float64 CUDA tensors of equal size."""
+    import torch
+    assert x.dtype == torch.float64 and y.dtype == torch.float64 and x.numel() == y.numel()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    check(load().ffe_eval_recip(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
+                                ctypes.c_void_p(st.cuda_stream)))
 
 
 def check(status):
