@@ -145,26 +145,31 @@ __device__ __forceinline__ double weno5z_combine(double b0, double b1, double b2
 }
 
 // Both values at the face between v2 and v3 from the six cells v0..v5: uL the
-// WENO5-Z value from v0..v4, uR the one from v5..v1 (mirrored).  The two share two candidates
-// (the quadratics through v1..v3 and v2..v4) and two second differences.
+// WENO5-Z value from v0..v4, uR the one from v5..v1 (mirrored).  Everything is
+// built from the first differences d_i = v_{i+1} - v_i: the candidates (the
+// quadratics through v0..v2, v1..v3, v2..v4 and v3..v5 at the face), the
+// second differences a and the one-sided combinations e of the Jiang-Shu
+// indicators beta = (13/12) a^2 + (1/4) e^2, of which 4 (beta + eps) enter
+// the weights (they are invariant under a common scale of the indicators).
+// The two values share two candidates and two second differences.
 __device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, double v3, double v4, double v5,
                                             double eps, double& uL, double& uR) {
-    const double c13 = 13.0 / 12.0;
-    const double p123 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
-    const double p234 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
-    const double pL0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
-    const double pR0 = fma(0.375, v5, fma(-1.25, v4, 1.875 * v3));
-    const double a012 = v0 - 2.0 * v1 + v2, a123 = v1 - 2.0 * v2 + v3;
-    const double a234 = v2 - 2.0 * v3 + v4, a345 = v3 - 2.0 * v4 + v5;
-    const double k123 = c13 * a123 * a123, k234 = c13 * a234 * a234;
-    const double eL0 = v0 - 4.0 * v1 + 3.0 * v2, eL1 = v1 - v3, eL2 = 3.0 * v2 - 4.0 * v3 + v4;
-    const double eR0 = v5 - 4.0 * v4 + 3.0 * v3, eR1 = v4 - v2, eR2 = 3.0 * v3 - 4.0 * v2 + v1;
-    const double bL0 = fma(c13 * a012, a012, fma(0.25 * eL0, eL0, eps));
-    const double bL1 = k123 + fma(0.25 * eL1, eL1, eps);
-    const double bL2 = k234 + fma(0.25 * eL2, eL2, eps);
-    const double bR0 = fma(c13 * a345, a345, fma(0.25 * eR0, eR0, eps));
-    const double bR1 = k234 + fma(0.25 * eR1, eR1, eps);
-    const double bR2 = k123 + fma(0.25 * eR2, eR2, eps);
+    const double d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3, d45 = v5 - v4;
+    const double p123 = fma(0.125, d12, fma(0.375, d23, v2));
+    const double p234 = fma(0.625, d23, fma(-0.125, d34, v2));
+    const double pL0 = fma(-0.375, d01, fma(0.875, d12, v2));
+    const double pR0 = fma(-0.875, d34, fma(0.375, d45, v3));
+    const double a012 = d12 - d01, a123 = d23 - d12, a234 = d34 - d23, a345 = d45 - d34;
+    const double eL0 = fma(2.0, d12, a012), eL1 = d12 + d23, eL2 = fma(-2.0, d23, a234);
+    const double eR0 = fma(-2.0, d34, a345), eR1 = d23 + d34, eR2 = fma(2.0, d23, a123);
+    const double c = 13.0 / 3.0, eps4 = 4.0 * eps;
+    const double k123 = (c * a123) * a123, k234 = (c * a234) * a234;
+    const double bL0 = fma(c * a012, a012, fma(eL0, eL0, eps4));
+    const double bL1 = k123 + fma(eL1, eL1, eps4);
+    const double bL2 = k234 + fma(eL2, eL2, eps4);
+    const double bR0 = fma(c * a345, a345, fma(eR0, eR0, eps4));
+    const double bR1 = k234 + fma(eR1, eR1, eps4);
+    const double bR2 = k123 + fma(eR2, eR2, eps4);
     uL = weno5z_combine(bL0, bL1, bL2, pL0, p123, p234);
     uR = weno5z_combine(bR0, bR1, bR2, pR0, p234, p123);
 }
