@@ -214,41 +214,46 @@ __device__ __forceinline__ void weno5z_combine_vjp(double B0, double B1, double 
 }
 
 // Reverse mode of weno5z_pair: g[i] += ybL d uL/d v_i + ybR d uR/d v_i,
-// i = 0..5, through the shared candidates and second differences.
+// i = 0..5, through the shared candidates and second differences (same
+// first-difference form and 4x-scaled indicators as the forward pair).
 __device__ __forceinline__ void weno5z_pair_vjp(double v0, double v1, double v2, double v3, double v4, double v5,
                                                 double eps, double ybL, double ybR, double* g) {
-    const double c13 = 13.0 / 12.0;
-    const double p123 = fma(-0.125, v1, fma(0.75, v2, 0.375 * v3));
-    const double p234 = fma(0.375, v2, fma(0.75, v3, -0.125 * v4));
-    const double pL0 = fma(0.375, v0, fma(-1.25, v1, 1.875 * v2));
-    const double pR0 = fma(0.375, v5, fma(-1.25, v4, 1.875 * v3));
-    const double a012 = v0 - 2.0 * v1 + v2, a123 = v1 - 2.0 * v2 + v3;
-    const double a234 = v2 - 2.0 * v3 + v4, a345 = v3 - 2.0 * v4 + v5;
-    const double k123 = c13 * a123 * a123, k234 = c13 * a234 * a234;
-    const double eL0 = v0 - 4.0 * v1 + 3.0 * v2, eL1 = v1 - v3, eL2 = 3.0 * v2 - 4.0 * v3 + v4;
-    const double eR0 = v5 - 4.0 * v4 + 3.0 * v3, eR1 = v4 - v2, eR2 = 3.0 * v3 - 4.0 * v2 + v1;
-    const double BL0 = fma(c13 * a012, a012, fma(0.25 * eL0, eL0, eps));
-    const double BL1 = k123 + fma(0.25 * eL1, eL1, eps);
-    const double BL2 = k234 + fma(0.25 * eL2, eL2, eps);
-    const double BR0 = fma(c13 * a345, a345, fma(0.25 * eR0, eR0, eps));
-    const double BR1 = k234 + fma(0.25 * eR1, eR1, eps);
-    const double BR2 = k123 + fma(0.25 * eR2, eR2, eps);
+    const double d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3, d45 = v5 - v4;
+    const double p123 = fma(0.125, d12, fma(0.375, d23, v2));
+    const double p234 = fma(0.625, d23, fma(-0.125, d34, v2));
+    const double pL0 = fma(-0.375, d01, fma(0.875, d12, v2));
+    const double pR0 = fma(-0.875, d34, fma(0.375, d45, v3));
+    const double a012 = d12 - d01, a123 = d23 - d12, a234 = d34 - d23, a345 = d45 - d34;
+    const double eL0 = fma(2.0, d12, a012), eL1 = d12 + d23, eL2 = fma(-2.0, d23, a234);
+    const double eR0 = fma(-2.0, d34, a345), eR1 = d23 + d34, eR2 = fma(2.0, d23, a123);
+    const double c = 13.0 / 3.0, eps4 = 4.0 * eps;
+    const double k123 = (c * a123) * a123, k234 = (c * a234) * a234;
+    const double BL0 = fma(c * a012, a012, fma(eL0, eL0, eps4));
+    const double BL1 = k123 + fma(eL1, eL1, eps4);
+    const double BL2 = k234 + fma(eL2, eL2, eps4);
+    const double BR0 = fma(c * a345, a345, fma(eR0, eR0, eps4));
+    const double BR1 = k234 + fma(eR1, eR1, eps4);
+    const double BR2 = k123 + fma(eR2, eR2, eps4);
     double pbL0, pbL1, pbL2, BbL0, BbL1, BbL2, pbR0, pbR1, pbR2, BbR0, BbR1, BbR2;
     weno5z_combine_vjp(BL0, BL1, BL2, pL0, p123, p234, ybL, pbL0, pbL1, pbL2, BbL0, BbL1, BbL2);
     weno5z_combine_vjp(BR0, BR1, BR2, pR0, p234, p123, ybR, pbR0, pbR1, pbR2, BbR0, BbR1, BbR2);
-    // adjoints of the shared and one-sided intermediates
+    // adjoints of the shared and one-sided intermediates (B = c a^2 + e^2 + 4 eps)
     const double p123b = pbL1 + pbR2, p234b = pbL2 + pbR1;
-    const double c26 = 2.0 * c13;
-    const double a012b = c26 * a012 * BbL0, a345b = c26 * a345 * BbR0;
-    const double a123b = c26 * a123 * (BbL1 + BbR2), a234b = c26 * a234 * (BbL2 + BbR1);
-    const double eL0b = 0.5 * eL0 * BbL0, eL1b = 0.5 * eL1 * BbL1, eL2b = 0.5 * eL2 * BbL2;
-    const double eR0b = 0.5 * eR0 * BbR0, eR1b = 0.5 * eR1 * BbR1, eR2b = 0.5 * eR2 * BbR2;
+    const double c2 = 2.0 * c;
+    const double a012b = c2 * a012 * BbL0, a345b = c2 * a345 * BbR0;
+    const double a123b = c2 * a123 * (BbL1 + BbR2), a234b = c2 * a234 * (BbL2 + BbR1);
+    const double eL0b = 2.0 * eL0 * BbL0, eL1b = 2.0 * eL1 * BbL1, eL2b = 2.0 * eL2 * BbL2;
+    const double eR0b = 2.0 * eR0 * BbR0, eR1b = 2.0 * eR1 * BbR1, eR2b = 2.0 * eR2 * BbR2;
+    // to the cells: p123 = (-v1 + 6 v2 + 3 v3)/8, p234 = (3 v2 + 6 v3 - v4)/8,
+    // pL0 = (3 v0 - 10 v1 + 15 v2)/8, pR0 = (15 v3 - 10 v4 + 3 v5)/8,
+    // eL0 = v0 - 4 v1 + 3 v2, eL1 = v3 - v1, eL2 = 3 v2 - 4 v3 + v4,
+    // eR0 = 3 v3 - 4 v4 + v5, eR1 = v4 - v2, eR2 = v1 - 4 v2 + 3 v3
     g[0] += fma(0.375, pbL0, a012b + eL0b);
-    g[1] += fma(-1.25, pbL0, fma(-0.125, p123b, fma(-2.0, a012b, fma(-4.0, eL0b, a123b + eL1b + eR2b))));
+    g[1] += fma(-1.25, pbL0, fma(-0.125, p123b, fma(-2.0, a012b, fma(-4.0, eL0b, a123b - eL1b + eR2b))));
     g[2] += fma(1.875, pbL0, fma(0.75, p123b, fma(0.375, p234b, fma(-2.0, a123b, fma(3.0, eL0b + eL2b,
                fma(-4.0, eR2b, a012b + a234b - eR1b))))));
     g[3] += fma(0.375, p123b, fma(0.75, p234b, fma(1.875, pbR0, fma(-2.0, a234b, fma(3.0, eR0b + eR2b,
-               fma(-4.0, eL2b, a123b + a345b - eL1b))))));
+               fma(-4.0, eL2b, a123b + a345b + eL1b))))));
     g[4] += fma(-0.125, p234b, fma(-1.25, pbR0, fma(-2.0, a345b, fma(-4.0, eR0b, a234b + eL2b + eR1b))));
     g[5] += fma(0.375, pbR0, a345b + eR0b);
 }

@@ -205,7 +205,7 @@ __device__ __forceinline__ void reconstruct(const Dev& d, int wl, int k, int m, 
 }
 
 // One thread per (chunk position, direction, face): box elements.
-__global__ void k_fd_flux(Dev d, const int* list, int ci, int w0) {
+__global__ void __launch_bounds__(128, 4) k_fd_flux(Dev d, const int* list, int ci, int w0) {
     const int n = chunk_n(d, ci, w0);
     const int64_t nfc = nface(d);
     const int64_t total = (int64_t)n * 3 * nfc;
@@ -237,7 +237,7 @@ __global__ void k_fd_flux(Dev d, const int* list, int ci, int w0) {
 // face, Rusanov dissipation along the unit face normal n^ (lambda = 1):
 //   F^j = (F^j(L) + F^j(R))/2 - n^_j (U_R - U_L)/2,
 // optional corrector per component.
-__global__ void k_fd_flux_curved(Dev d, const int* list, int ci, int w0) {
+__global__ void __launch_bounds__(128, 4) k_fd_flux_curved(Dev d, const int* list, int ci, int w0) {
     const int n = chunk_n(d, ci, w0);
     const int64_t nfc = nface(d);
     const int64_t total = (int64_t)n * 3 * nfc;
