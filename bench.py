@@ -28,10 +28,10 @@ import ffe_workloads as W  # noqa: E402
 
 METRIC = "RHS element-node updates/s FP64 at 1 GB300, % roofline; adjoint/forward time"
 UNIT = "element-node updates/s"
-# DRAM bytes (read + write) per ms of kernel time, from an ncu capture of the
-# kernel (profiles/k_fd_flux_breakdown_8x8x8.md): bytes and time of a launch
-# both scale with its FD elements (785 KB and 13.9 us each)
-DRAM_BYTES_PER_MS = {"fd_flux": 55.6e6}
+# DRAM bytes (read + write) of k_fd_flux per FD element it processes, from an
+# ncu capture of the kernel (profiles/k_fd_flux_breakdown_8x8x8.md): a launch
+# moves this many bytes for each element of its chunk
+DRAM_BYTES_PER_FD_ELEMENT = {"fd_flux": None}
 
 CPU_SAMPLE = dict(nx=16, ny=2, nz=2, x_half=0.5)
 CPU_SAMPLE_TEXT = ("oracle (numpy fp64, 1 thread) on a 16x2x2-element slab of the breakdown "
@@ -208,6 +208,147 @@ def run_shell(args):
     print(json.dumps(line), flush=True)
 
 
+def _oned_profile(test, x):
+    """Exact or reference profile b(x) of the paper's 1-D data (App. A)."""
+    import numpy as np
+    if test == "fast_wave_kink":
+        return np.where(x < -0.1, 1.0, np.where(x > 0.1, 0.7, 0.85 - 1.5 * x))
+    if test == "alfven":
+        return np.where(x < -0.1, 1.0, np.where(x > 0.1, 1.3, 1.15 + 0.15 * np.sin(5.0 * np.pi * x)))
+    raise ValueError(test)
+
+
+def _oned_points(ctx, U, mask):
+    """Values [9][n] and x [n] of the representation each element uses (DG nodes
+    of DG elements, subcell centres of FD elements)."""
+    import numpy as np
+    xd, xf = ctx.coords()
+    dg, fd = ctx.split(U)
+    xd = xd.cpu().numpy().reshape(3, ctx.n_elem, -1)[0]
+    xf = xf.cpu().numpy().reshape(3, ctx.n_elem, -1)[0]
+    dg = dg.reshape(9, ctx.n_elem, -1)
+    fd = fd.reshape(9, ctx.n_elem, -1)
+    on_dg, on_fd = mask == 0, mask == 1
+    vals = np.concatenate([dg[:, on_dg].reshape(9, -1), fd[:, on_fd].reshape(9, -1)], axis=1)
+    xs = np.concatenate([xd[on_dg].reshape(-1), xf[on_fd].reshape(-1)])
+    return vals, xs
+
+
+def oned_measure(levels=(0, 1, 2, 3)):
+    """The paper's 1-D tests (Sec. IV.A, Table I, App. A) to their end times at
+    resolution levels n (32 2^n elements): step time, element-node update rate
+    and the errors the paper plots -- fast wave against its exact translation,
+    Alfven wave against the stationary profile, breakdown through B^2 - E^2 and
+    E.B -- plus the fast wave from the FD start."""
+    import numpy as np
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    out = []
+    runs = [(t, n, False) for t in W.ONED for n in levels] + [("fast_wave_kink", 0, True)]
+    for test, n, via in runs:
+        cfg = W.oned(test, n, via_fd=via)
+        ctx = ffe.Context(cfg)
+        ctx.set_initial()
+        fd0 = int(ctx.download()[1].sum())
+        ctx.step(2)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        i0 = ctx.info()
+        e0.record(st)
+        ctx.step(cfg["steps"] - 2)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        i1 = ctx.info()
+        U, mask = ctx.download()
+        vals, xs = _oned_points(ctx, U, mask)
+        t = cfg["steps"] * cfg["params"]["dt"]
+        r = {"test": test, "level": n, "elements_x": cfg["n"][0], "steps": cfg["steps"], "t_end": t,
+             "fd_start": via, "fd_elements_start": fd0, "fd_elements_end": int(mask.sum()),
+             "ms_per_step": ms / (cfg["steps"] - 2),
+             "node_updates_per_s": (i1.node_updates - i0.node_updates) / (ms / 1e3), "status_bits": ctx.status()}
+        if test == "fast_wave_kink":
+            b = _oned_profile(test, xs - t)
+            err = np.abs(vals[2] + b)
+            far = (np.abs(xs - t - 0.1) > 0.15) & (np.abs(xs - t + 0.1) > 0.15)
+            r.update(err_Ez_max=float(err.max()), err_Ez_mean=float(err.mean()), err_Ez_max_far_from_kinks=float(err[far].max()))
+        elif test == "alfven":
+            b = _oned_profile(test, xs)
+            r.update(dev_Bz_max=float(np.abs(vals[5] - b).max()), dev_Bz_mean=float(np.abs(vals[5] - b).mean()),
+                     dev_Ex_max=float(np.abs(vals[0] + b).max()))
+        else:
+            E, B = vals[0:3], vals[3:6]
+            r.update(min_B2_minus_E2=float(((B * B).sum(0) - (E * E).sum(0)).min()),
+                     max_abs_EdotB=float(np.abs((E * B).sum(0)).max()))
+        ctx.close()
+        out.append(r)
+    return out
+
+
+def split_measure(steps=20, warmup=3):
+    """The paper's efficiency experiment (Sec. IV.A.4): the stationary Alfven
+    wave on (8, 32, 8) elements with the elements below a y row forced onto FD
+    and the rest on DG (indicator off, mask frozen); step time against the FD
+    fraction x, the speedup over all-FD and the factor f of the model
+    1 / (x + (1 - x)/f) fitted to the mixed runs."""
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    h = 3.0 / 8
+    cfg = W.oned("alfven", 0)
+    cfg.update(lo=(-1.5, -16 * h, -4 * h), hi=(1.5, 16 * h, 4 * h), n=(8, 32, 8))
+    cfg["params"].update(tci_on=0)
+    ctx = ffe.Context(cfg)
+    U, m = ctx.state()
+    E = ctx.n_elem
+    yc = ctx.coords()[0].view(3, E, -1)[1].mean(1)   # element centres in y
+    rows = []
+    for k in (32, 16, 6, 3, 2, 1, 0):
+        mask = (yc < -16 * h + k * h).to(torch.uint8)
+        ctx.set_state(U.clone(), mask)
+        ctx.set_initial(keep_mask=True)
+        ctx.step(warmup)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        i0 = ctx.info()
+        e0.record(st)
+        ctx.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        i1 = ctx.info()
+        rows.append({"fd_rows": k, "fd_fraction": k / 32, "ms_per_step": ms,
+                     "node_updates_per_s": (i1.node_updates - i0.node_updates) / (ms * steps / 1e3),
+                     "status_bits": ctx.status()})
+        U, m = ctx.state()
+    ctx.close()
+    t_fd = rows[0]["ms_per_step"]
+    for r in rows:
+        r["speedup_over_all_fd"] = t_fd / r["ms_per_step"]
+    mixed = [r for r in rows if 0 < r["fd_fraction"] < 1]
+    # 1/s - x = (1 - x)/f, least squares in 1/f
+    num = sum((1 - r["fd_fraction"]) * (1 / r["speedup_over_all_fd"] - r["fd_fraction"]) for r in mixed)
+    den = sum((1 - r["fd_fraction"]) ** 2 for r in mixed)
+    return {"elements": E, "rows": rows, "f_all_dg": t_fd / rows[-1]["ms_per_step"], "f_fit_mixed": den / num}
+
+
+def run_oned(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    o = oned_measure()
+    sp = split_measure(steps=args.steps if args.steps != 50 else 20, warmup=max(args.warmup, 3))
+    ten = min(sp["rows"], key=lambda r: abs(r["fd_fraction"] - 0.1))
+    line = {"metric": METRIC, "value": ten["node_updates_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ten["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper's 1-D tests (Table I, levels 0-3, to their end times) and the Alfven "
+                                   "DG/FD split on (8,32,8) elements (value: the run nearest 10% FD)",
+                       "fd_fraction": ten["fd_fraction"]},
+            "oned": o, "split": sp}
+    print(json.dumps(line), flush=True)
+
+
 def run_pulsars(args):
     """Batched shells: one launch per kernel and substep for every instance,
     against the same instances advanced one context at a time."""
@@ -380,10 +521,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64,
                     help="elements along x (same width 4/64; smaller values for profiler captures)")
-    ap.add_argument("--workload", default="breakdown", choices=["breakdown", "pulsars", "adjoint", "shell"],
+    ap.add_argument("--workload", default="breakdown", choices=["breakdown", "pulsars", "adjoint", "shell", "oned"],
                     help="pulsars: the 32-shell batch, batched launch vs one context per instance; "
                          "adjoint: luminosity gradient of one neutron-star shell (--steps steps); "
-                         "shell: that shell with three FD layers, frozen mask (curved FD kernels)")
+                         "shell: that shell with three FD layers, frozen mask (curved FD kernels); "
+                         "oned: the paper's 1-D tests and its DG/FD split experiment")
     ap.add_argument("--no-adjoint", action="store_true", help="breakdown: skip the adjoint/forward timing")
     ap.add_argument("--n-inst", type=int, default=32)
     ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
@@ -396,6 +538,8 @@ def main():
         return run_shell(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "oned":
+        return run_oned(args)
 
     import numpy as np
     import torch
@@ -473,7 +617,8 @@ def main():
         ach = flops / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": DRAM_BYTES_PER_MS[dom] * dom_ms / dom_launches if dom in DRAM_BYTES_PER_MS else None,
+                "traffic": (DRAM_BYTES_PER_FD_ELEMENT[dom] * n_fd_upd / dom_launches
+                            if DRAM_BYTES_PER_FD_ELEMENT.get(dom) else None),
                 "kernel": dom, "peak_source": "derived: 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz",
                 "share": dom_ms / total_ms, "launches": dom_launches, "max_launch_ms": dom_max,
                 "units": {"fd_elem_updates": n_fd_upd, "dg_elem_updates": n_dg_upd}}

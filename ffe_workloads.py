@@ -9,6 +9,8 @@ Workloads (the five problem setups the library is exercised on):
   wald        Kerr-Schild M=1, a=0.9, shell r in [1.5, 50], 6 wedges x 8x8x16
   pulsars     32 rotating-dipole shells with seeded sizes and orders
   adjoint     one rotating-dipole shell, 6 wedges x 6x6x12, luminosity at r=20
+  oned        the paper's 1-D tests (fast wave with kinks, stationary Alfven
+              wave, FFE breakdown) at its resolutions and time steps
 """
 import math
 
@@ -54,6 +56,31 @@ def cleaning_mode(n=4, P=5, eps=1e-3, kappa=1.0, steps=20):
                 metric=("minkowski", 0.0, 0.0),
                 params=base_params(eta=0.0, cfl=0.5, kappa_psi=kappa, kappa_phi=kappa, tci_on=0),
                 initial=("cleaning_mode", dict(eps=eps)), steps=steps)
+
+
+# The paper's one-dimensional tests (Sec. IV.A, Table I, App. A): domain along
+# x, time step at the lowest resolution (halved per level n) and end time.
+ONED = {
+    "fast_wave_kink": dict(x=(-0.5, 1.5), dt=9.22e-4, t_end=0.5),
+    "alfven": dict(x=(-1.5, 1.5), dt=1.38e-3, t_end=2.0),
+    "breakdown_1d": dict(x=(-0.5, 0.5), dt=4.61e-4, t_end=0.04),
+}
+
+
+def oned(test, n=0, P=5, via_fd=False, steps=None):
+    """One of the paper's 1-D tests at resolution level n: 32 2^n elements
+    along x (Dirichlet to the initial data at both ends), one element across
+    [-0.1, 0.1] in y and z (periodic), eta = 1e6, CFL factor 0.3 with the
+    table's time step, filter, indicator and corrector on.  via_fd: start every
+    element on FD (the paper's start).  steps defaults to the test's end time."""
+    o = ONED[test]
+    dt = o["dt"] / 2 ** n
+    return dict(name="oned_" + test, kind="box", lo=(o["x"][0], -0.1, -0.1), hi=(o["x"][1], 0.1, 0.1),
+                n=(32 * 2 ** n, 1, 1), bc=(DIRICHLET, PERIODIC, PERIODIC), P=P,
+                metric=("minkowski", 0.0, 0.0),
+                params=base_params(eta=1e6, cfl=0.3, dt=dt, fd_corrector=1),
+                initial=(test, dict()), init_via_fd=via_fd,
+                steps=steps if steps is not None else int(round(o["t_end"] / dt)))
 
 
 def splitmix64(seed):

@@ -62,9 +62,13 @@ enum { FFE_DOMAIN_BOX = 0, FFE_DOMAIN_SHELL6 = 1 };
 enum { FFE_BC_PERIODIC = 1, FFE_BC_DIRICHLET = 2, FFE_BC_NO_INCOMING = 3, FFE_BC_STAR = 4 };
 enum { FFE_METRIC_MINKOWSKI = 0, FFE_METRIC_KERR_SCHILD = 1 };
 enum { FFE_ID_FAST_WAVE = 0, FFE_ID_BREAKDOWN = 1, FFE_ID_CLEANING_MODE = 2,
-       FFE_ID_WALD = 3, FFE_ID_DIPOLE = 4 };
+       FFE_ID_WALD = 3, FFE_ID_DIPOLE = 4,
+       /* the paper's one-dimensional tests (App. A): fast wave with two kinks,
+        * stationary Alfven wave, FFE breakdown */
+       FFE_ID_FAST_WAVE_KINK = 5, FFE_ID_ALFVEN = 6, FFE_ID_BREAKDOWN_1D = 7 };
 enum { FFE_RELAX = 0, FFE_HARD = 1, FFE_RELAX_THEN_HARD = 2 };
-enum { FFE_INIT_KEEP_MASK = 1 };   /* ffe_set_initial flag */
+enum { FFE_INIT_KEEP_MASK = 1,     /* ffe_set_initial flags */
+       FFE_INIT_VIA_FD = 2 };
 
 /* Domain (Sec. III.A; shell: Sec. IV.B).  BOX: [lo, hi], boundary kind per axis
  * (periodic or a physical kind applied at both ends).  SHELL6: six cubed-sphere
@@ -149,10 +153,19 @@ ffe_status ffe_set_initial_batch(ffe_ctx* ctx, int id_kind, const double* id_par
  *   CLEANING_MODE  {eps}                 B=(1+eps sin(pi x),0,0)
  *   WALD           {M, a, B0}            Wald's field (Kerr-Schild metric)
  *   DIPOLE         {mu, delta, chi}      B~ = curl[mu m x x/(r^2+delta^2)^(3/2)], m = (sin chi, 0, cos chi)
+ *   FAST_WAVE_KINK {}                    B=(1,b,0), E=(0,0,-b), b = 1 | 0.85-1.5x | 0.7 across |x|<0.1
+ *   ALFVEN         {}                    B=(1,1,b), E=(-b,0,1), b = 1 | 1.15+0.15 sin(5 pi x) | 1.3,
+ *                                        q~ = -db/dx (Gauss's law)
+ *   BREAKDOWN_1D   {}                    B=(1,b,b), E=(0,0.5,-0.5), b = 1 | -10x | -1
  * The data are set on the LGL nodes, then the troubled-cell indicator runs and
  * flagged elements take the data at their subcell centres (Sec. III.C.1/III.C.3).
  * flags & FFE_INIT_KEEP_MASK: no indicator; the context's current mask is kept
  * and its FD elements take the data at their subcell centres (fixed-mask runs).
+ * flags & FFE_INIT_VIA_FD: the paper's start (Sec. III.C.1): every element on
+ * FD with the data at its subcell centres; the FD indicator at the end of each
+ * step returns smooth elements to DG.  Needs the indicator on and a flat
+ * metric (FFE_EINVAL otherwise); excludes FFE_INIT_KEEP_MASK; not built for
+ * batches (FFE_ENOTIMPL from ffe_set_initial_batch).
  * Resets time and step counters. */
 ffe_status ffe_set_initial(ffe_ctx* ctx, int id_kind, const double* id_params, int n_params, int flags);
 
@@ -279,6 +292,13 @@ ffe_status ffe_luminosity(ffe_ctx* ctx, const double* U_dev, double r_L, double*
 /* Derivative of the initial DG state set by ffe_set_initial with respect to its
  * parameter `which` (DIPOLE: 0 = mu, 2 = chi) at the nodes, into dU_dev. */
 ffe_status ffe_initial_tangent(ffe_ctx* ctx, int which, double* dU_dev);
+
+/* Cartesian coordinates of the DG nodes [3][n_dg] and of the FD subcell
+ * centres [3][n_fd] (every element's block, in state-vector order), copied
+ * into caller-owned device arrays (either may be NULL) on the context stream.
+ * FD centres of batched contexts are not stored (FFE_ENOTIMPL when
+ * xyz_fd_dev is not NULL). */
+ffe_status ffe_get_coords(ffe_ctx* ctx, double* xyz_dg_dev, double* xyz_fd_dev);
 
 /* Reciprocal 1/x that the WENO5-Z weights use (the hardware approximation
  * rcp.approx.ftz.f64 refined by two Newton-Raphson steps), evaluated

@@ -36,8 +36,55 @@ def cleaning_mode(xyz, eps=1e-3):
     return U
 
 
-def evaluate(kind, xyz, **kw):
-    return {"fast_wave": fast_wave, "breakdown": breakdown, "cleaning_mode": cleaning_mode}[kind](xyz, **kw)
+def fast_wave_kink(xyz, t=0.0):
+    """Fast wave of the paper's 1-D tests (App. A, "Fast wave"): B = (1, b, 0),
+    E = (0, 0, -b) with b = 1 (x < -0.1), 0.85 - 1.5 x (|x| < 0.1), 0.7
+    (x > 0.1): a ramp between two kinks.  E.B = 0, B^2 - E^2 = 1, div E = 0
+    (q = 0) and J = 0: a vacuum fast mode whose exact solution is the
+    translation Q(x, t) = Q(x - t, 0) (Sec. IV.A.1)."""
+    x = xyz[0] - t
+    b = np.where(x < -0.1, 1.0, np.where(x > 0.1, 0.7, 0.85 - 1.5 * x))
+    U = np.zeros((9,) + np.shape(x))
+    U[3] = 1.0
+    U[4] = b
+    U[2] = -b
+    return U
+
+
+def alfven_stationary(xyz):
+    """Stationary Alfven wave of the paper's 1-D tests (App. A, "Stationary
+    Alfven wave"): B = (1, 1, b), E = (-b, 0, 1) with b = 1 (x < -0.1),
+    1.15 + 0.15 sin(5 pi x) (|x| < 0.1), 1.3 (x > 0.1).  E.B = 0 and
+    B^2 - E^2 = 1.  [reading] The paper lists E and B only; q~ is set by
+    Gauss's law, q = div E = -db/dx = -0.75 pi cos(5 pi x) inside the layer
+    (0 outside; continuous, since cos(+-pi/2) = 0)."""
+    x = xyz[0]
+    inside = np.abs(x) < 0.1
+    b = np.where(x < -0.1, 1.0, np.where(x > 0.1, 1.3, 1.15 + 0.15 * np.sin(5.0 * np.pi * x)))
+    U = np.zeros((9,) + np.shape(x))
+    U[0] = -b
+    U[2] = 1.0
+    U[3] = 1.0
+    U[4] = 1.0
+    U[5] = b
+    U[8] = np.where(inside, -0.75 * np.pi * np.cos(5.0 * np.pi * x), 0.0)
+    return U
+
+
+def breakdown_1d(xyz):
+    """FFE breakdown of the paper's 1-D tests (App. A, "FFE breakdown"):
+    B = (1, b, b), E = (0, 0.5, -0.5) with b = 1 (x < -0.1), -10 x (|x| < 0.1),
+    -1 (x > 0.1).  E.B = 0 and div E = 0 (q = 0); B^2 - E^2 = 0.5 + 2 b^2 falls
+    towards zero in the layer as the evolution proceeds."""
+    x = xyz[0]
+    b = np.where(x < -0.1, 1.0, np.where(x > 0.1, -1.0, -10.0 * x))
+    U = np.zeros((9,) + np.shape(x))
+    U[1] = 0.5
+    U[2] = -0.5
+    U[3] = 1.0
+    U[4] = b
+    U[5] = b
+    return U
 
 
 CS_H = 1e-30
@@ -124,8 +171,9 @@ def dipole_closed(xyz, mu=1.0, delta=0.1, chi=0.0):
 
 
 _KINDS = {"fast_wave": fast_wave, "breakdown": breakdown, "cleaning_mode": cleaning_mode,
-          "wald": wald, "dipole": dipole}
+          "wald": wald, "dipole": dipole, "fast_wave_kink": fast_wave_kink, "alfven": alfven_stationary,
+          "breakdown_1d": breakdown_1d}
 
 
-def evaluate(kind, xyz, **kw):  # noqa: F811  (extends the flat-space table above)
+def evaluate(kind, xyz, **kw):
     return _KINDS[kind](xyz, **kw)

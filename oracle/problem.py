@@ -46,18 +46,27 @@ class Problem:
                         mode=p["constraint_mode"], filter_on=p["filter_on"], tci_on=p["tci_on"],
                         tci_alpha=p["tci_alpha"], tci_M=p["tci_M"])
         self.dxmin = d.min_spacing()
-        self.dt = p["cfl"] * self.dxmin / self.lam_max * p["c_over_D"]
+        # an explicit time step (the paper's tables give one) or the CFL step (Sec. III.B)
+        self.dt = p["dt"] if p.get("dt", 0.0) > 0.0 else p["cfl"] * self.dxmin / self.lam_max * p["c_over_D"]
 
-    def initial_state(self):
+    def initial_state(self, via_fd=False):
         """Initial data on the LGL nodes, then the TCI (alpha) on every element;
         flagged elements take the initial data at their subcell centres.
         [reading] the paper initialises on the FD grid (Sec. III.C.1); here the
-        nodal start is the default, as the FD start only matters for Gibbs-prone data."""
+        nodal start is the default, as the FD start only matters for Gibbs-prone data.
+        via_fd: the paper's start, every element on FD with the initial data at
+        its subcell centres; the FD indicator at the end of each step returns
+        the smooth ones to DG."""
         from .stepper import tci_ratio, tci_threshold
         d, T = self.disc, self.T
         udg = self.initial(d.xyz.reshape(3, -1)).reshape((9,) + d.xyz.shape[1:])
         ufd = np.zeros((9, d.E, T.nc, T.nc, T.nc)) if d.has_fd else np.zeros((9, d.E, 1, 1, 1))
         mask = np.zeros(d.E, dtype=np.uint8)
+        if via_fd:
+            assert d.has_fd, "an FD start needs the FD grid (indicator on)"
+            mask[:] = 1
+            ufd[:] = self.initial(d.xyz_fd.reshape(3, -1)).reshape((9,) + d.xyz_fd.shape[1:])
+            return dict(mask=mask, udg=udg, ufd=ufd, t=0.0)
         if self.prm["tci_on"]:
             r = tci_ratio(udg[3:6], self.met["dg"], T, np.arange(d.E))
             flag = r > tci_threshold(T.N, self.prm["tci_M"], self.prm["tci_alpha"])

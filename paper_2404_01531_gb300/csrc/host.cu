@@ -197,6 +197,31 @@ void initial_point(int kind, const double* prm, int nprm, const double* X, doubl
         wald_point(X, nprm > 0 ? prm[0] : 1.0, nprm > 1 ? prm[1] : 0.0, nprm > 2 ? prm[2] : 1.0, U);
     } else if (kind == FFE_ID_DIPOLE) {
         dipole_point(X, nprm > 0 ? prm[0] : 1.0, nprm > 1 ? prm[1] : 0.1, nprm > 2 ? prm[2] : 0.0, U);
+    } else if (kind == FFE_ID_FAST_WAVE_KINK) {
+        // App. A fast wave: B = (1, b, 0), E = (0, 0, -b), b = 1 | 0.85 - 1.5 x | 0.7
+        const double b = x < -0.1 ? 1.0 : (x > 0.1 ? 0.7 : 0.85 - 1.5 * x);
+        U[3] = 1.0;
+        U[4] = b;
+        U[2] = -b;
+    } else if (kind == FFE_ID_ALFVEN) {
+        // App. A stationary Alfven wave: B = (1, 1, b), E = (-b, 0, 1),
+        // b = 1 | 1.15 + 0.15 sin(5 pi x) | 1.3; q~ = div E~ = -db/dx
+        const bool in = fabs(x) < 0.1;
+        const double b = x < -0.1 ? 1.0 : (x > 0.1 ? 1.3 : 1.15 + 0.15 * sin(5.0 * M_PI * x));
+        U[0] = -b;
+        U[2] = 1.0;
+        U[3] = 1.0;
+        U[4] = 1.0;
+        U[5] = b;
+        U[8] = in ? -0.75 * M_PI * cos(5.0 * M_PI * x) : 0.0;
+    } else if (kind == FFE_ID_BREAKDOWN_1D) {
+        // App. A FFE breakdown: B = (1, b, b), E = (0, 0.5, -0.5), b = 1 | -10 x | -1
+        const double b = x < -0.1 ? 1.0 : (x > 0.1 ? -1.0 : -10.0 * x);
+        U[1] = 0.5;
+        U[2] = -0.5;
+        U[3] = 1.0;
+        U[4] = b;
+        U[5] = b;
     }
 }
 
@@ -879,7 +904,7 @@ ffe_status init_slots(ffe_ctx* c, const std::vector<unsigned char>& mask) {
 }
 
 // Initial data for all elements (per-instance parameters in batched contexts).
-ffe_status set_initial_impl(ffe_ctx* c, int id_kind, bool keep_mask) {
+ffe_status set_initial_impl(ffe_ctx* c, int id_kind, bool keep_mask, bool via_fd) {
     const Dev& d = c->d;
     auto prm_of = [&](int e) -> const double* {
         return c->batch ? c->id_prm_inst.data() + (size_t)c->h_einst[e] * c->id_nprm : c->id_prm.data();
@@ -895,11 +920,11 @@ ffe_status set_initial_impl(ffe_ctx* c, int id_kind, bool keep_mask) {
         initial_point(id_kind, prm_of(e), nprm, X, u);
         for (int v = 0; v < NV; ++v) U[v * d.ndg + p] = u[v];
     });
-    std::vector<unsigned char> mask(d.E, 0);
+    std::vector<unsigned char> mask(d.E, via_fd ? 1 : 0);
     if (keep_mask) CK(cudaMemcpy(mask.data(), d.mask, d.E, cudaMemcpyDeviceToHost));
-    if (d.tci_on || keep_mask) {
+    if (d.tci_on || keep_mask || via_fd) {
         ffe_status s;
-        if (!keep_mask) {
+        if (!keep_mask && !via_fd) {
             double* ratio;
             if ((s = dalloc(c, &ratio, d.E))) return s;
             CK(cudaMemcpy(c->un.p, U.data(), NV * d.ndg * 8, cudaMemcpyHostToDevice));
@@ -945,6 +970,18 @@ void set_last_error(const char* msg) { g_err = msg; }
 
 // ------------------------------------------------------------------ C ABI ---
 extern "C" {
+
+ffe_status ffe_get_coords(ffe_ctx* c, double* xyz_dg_dev, double* xyz_fd_dev) {
+    g_err.clear();
+    if (!c) return fail(FFE_EINVAL, "null context");
+    const Dev& d = c->d;
+    if (xyz_fd_dev && !d.xyz_fd) return fail(FFE_ENOTIMPL, "FD centres are not stored for batched contexts");
+    if (xyz_dg_dev)
+        CK(cudaMemcpyAsync(xyz_dg_dev, d.xyz_dg, 3 * (size_t)d.ndg * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    if (xyz_fd_dev)
+        CK(cudaMemcpyAsync(xyz_fd_dev, d.xyz_fd, 3 * (size_t)d.nfd * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return FFE_OK;
+}
 
 ffe_status ffe_eval_recip(const double* x_dev, double* y_dev, int64_t n, void* cuda_stream) {
     g_err.clear();
@@ -1252,7 +1289,7 @@ ffe_status ffe_set_initial_batch(ffe_ctx* c, int id_kind, const double* id_param
     if (!c) return fail(FFE_EINVAL, "null context");
     if (id_kind < FFE_ID_FAST_WAVE || id_kind > FFE_ID_DIPOLE) return fail(FFE_EINVAL, "initial data kind %d", id_kind);
     if (n_params < 0 || (n_params > 0 && !id_params)) return fail(FFE_EINVAL, "bad initial-data parameters");
-    (void)flags;
+    if (flags & FFE_INIT_VIA_FD) return fail(FFE_ENOTIMPL, "an FD start is not built for batches (FD slot pool)");
     c->id_kind = id_kind;
     if (c->batch) {
         c->id_nprm = n_params;
@@ -1260,14 +1297,18 @@ ffe_status ffe_set_initial_batch(ffe_ctx* c, int id_kind, const double* id_param
     } else {
         c->id_prm.assign(id_params, id_params + n_params);
     }
-    return set_initial_impl(c, id_kind, (flags & FFE_INIT_KEEP_MASK) != 0);
+    return set_initial_impl(c, id_kind, (flags & FFE_INIT_KEEP_MASK) != 0, (flags & FFE_INIT_VIA_FD) != 0);
 }
 
 ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) {
     g_err.clear();
     if (!c) return fail(FFE_EINVAL, "null context");
-    if (id_kind < FFE_ID_FAST_WAVE || id_kind > FFE_ID_DIPOLE) return fail(FFE_EINVAL, "initial data kind %d", id_kind);
+    if (id_kind < FFE_ID_FAST_WAVE || id_kind > FFE_ID_BREAKDOWN_1D) return fail(FFE_EINVAL, "initial data kind %d", id_kind);
     if (n_params < 0 || (n_params > 0 && !id_params)) return fail(FFE_EINVAL, "bad initial-data parameters");
+    if ((flags & FFE_INIT_VIA_FD) && (flags & FFE_INIT_KEEP_MASK))
+        return fail(FFE_EINVAL, "FFE_INIT_VIA_FD and FFE_INIT_KEEP_MASK exclude each other");
+    if ((flags & FFE_INIT_VIA_FD) && (c->d.ks || !c->d.tci_on))
+        return fail(FFE_EINVAL, "an FD start needs the indicator on and a flat metric");
     c->id_kind = id_kind;
     c->id_prm.assign(id_params, id_params + n_params);
     if (c->batch) {
@@ -1275,7 +1316,7 @@ ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int
         c->id_prm_inst.clear();
         for (int i = 0; i < c->n_inst; ++i) c->id_prm_inst.insert(c->id_prm_inst.end(), id_params, id_params + n_params);
     }
-    return set_initial_impl(c, id_kind, (flags & FFE_INIT_KEEP_MASK) != 0);
+    return set_initial_impl(c, id_kind, (flags & FFE_INIT_KEEP_MASK) != 0, (flags & FFE_INIT_VIA_FD) != 0);
 }
 
 ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) {

@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(HERE, "libffe.so")
 
 NV = 9
 BC = {"periodic": 1, "dirichlet": 2, "no_incoming": 3, "star": 4}
-ID = {"fast_wave": 0, "breakdown": 1, "cleaning_mode": 2, "wald": 3, "dipole": 4}
+ID = {"fast_wave": 0, "breakdown": 1, "cleaning_mode": 2, "wald": 3, "dipole": 4,
+      "fast_wave_kink": 5, "alfven": 6, "breakdown_1d": 7}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
 STATUS = {0: "FFE_OK", 1: "FFE_EINVAL", 2: "FFE_ENOMEM", 3: "FFE_ECUDA", 4: "FFE_ETIMEOUT",
           5: "FFE_ENUMERIC", 6: "FFE_ESTATE", 7: "FFE_ENOTIMPL"}
@@ -26,7 +27,8 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
            "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
            "ffe_fd_rhs_noalloc", "ffe_create_batch", "ffe_get_layout", "ffe_set_initial_batch",
            "ffe_rhs_vjp", "ffe_adjoint_step", "ffe_luminosity", "ffe_initial_tangent",
-           "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_eval_recip", "ffe_last_error",
+           "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_get_coords", "ffe_eval_recip",
+           "ffe_last_error",
            "ffe_destroy"]
 
 
@@ -102,6 +104,7 @@ def load():
         "ffe_luminosity": [P, P, d, ctypes.POINTER(d), P, d],
         "ffe_initial_tangent": [P, i, P],
         "ffe_eval_recip": [P, P, ctypes.c_int64, P],
+        "ffe_get_coords": [P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -216,13 +219,18 @@ class Context:
         self.dt, self.dxmin = inf.dt, inf.dxmin
         return inf
 
-    def set_initial(self, kind=None, params=(), keep_mask=False):
-        """Analytic initial data; keep_mask: keep the current DG/FD mask (no indicator)."""
+    def set_initial(self, kind=None, params=(), keep_mask=False, via_fd=None):
+        """Analytic initial data; keep_mask: keep the current DG/FD mask (no
+        indicator); via_fd: start every element on FD (default: the workload's
+        "init_via_fd")."""
         if kind is None:
             kind, kw = self.cfg["initial"]
             params = tuple(kw.values())
+        if via_fd is None:
+            via_fd = bool(self.cfg.get("init_via_fd", False))
         arr = (ctypes.c_double * max(len(params), 1))(*params)
-        check(load().ffe_set_initial(self.h, ID[kind], arr, len(params), 1 if keep_mask else 0))
+        flags = (1 if keep_mask else 0) | (2 if via_fd else 0)
+        check(load().ffe_set_initial(self.h, ID[kind], arr, len(params), flags))
 
     def step(self, n=1):
         check(load().ffe_step(self.h, int(n)))
@@ -287,6 +295,16 @@ class Context:
         return json.loads(buf.value.decode())
 
     # layout helpers: state vector <-> (9, E, ...) blocks
+    def coords(self):
+        """(xyz_dg [3][n_dg], xyz_fd [3][n_fd]) float64 CUDA tensors: DG node and
+        FD subcell-centre coordinates in state-vector order."""
+        import torch
+        xd = torch.empty(3 * self.n_dg, dtype=torch.float64, device="cuda")
+        xf = torch.empty(3 * self.n_fd, dtype=torch.float64, device="cuda")
+        check(load().ffe_get_coords(self.h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(xf.data_ptr())))
+        torch.cuda.synchronize()
+        return xd.view(3, -1), xf.view(3, -1)
+
     def split(self, U):
         U = np.asarray(U)
         E, np1, nc = self.n_elem, self.np1, self.nc
