@@ -3,6 +3,7 @@
 // indexing, and the WENO5-Z interpolation (Sec. III.C.2).
 #pragma once
 #include "ffe_internal.h"
+#include "fp64util.cuh"
 #include "shellmap.cuh"
 
 namespace ffe {
@@ -99,30 +100,6 @@ __device__ __forceinline__ void axes_of(int dd, int& t1, int& t2) {
 __device__ __forceinline__ int chunk_n(const Dev& d, int ci, int w0) {
     const int n = d.counts[ci] - w0;
     return n < 0 ? 0 : (n > d.chunk ? d.chunk : n);
-}
-
-// 1/d for a positive normal d whose reciprocal is normal: the hardware
-// approximation rcp.approx.ftz.f64 refined by two Newton-Raphson steps for
-// f(y) = 1/y - d, y <- y + y (1 - d y) (each squares the relative error; the
-// residual 1 - d y is exact in one FMA when y is close to 1/d).  Within about
-// one ulp of the rounded quotient (ffe_eval_recip exposes it for tests); used
-// for the WENO5-Z weight denominators, positive sums bounded away from zero
-// (for sums above 2^1022 the flushed reciprocal is 0; the quotient it
-// replaces would overflow there for candidates above 4 in magnitude).
-__device__ __forceinline__ double recip_nr(double d) {
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
-    double r = fma(-d, y, 1.0);
-    y = fma(y, r, y);
-    r = fma(-d, y, 1.0);
-    return fma(y, r, y);
-}
-
-// 2^-floor(log2 x) for a positive normal x below 2^1022: x times it lies in
-// [1, 2) and the product is exact (integer operations on the exponent field).
-__device__ __forceinline__ double pow2_inv_scale(double x) {
-    const long long e = __double_as_longlong(x) >> 52;
-    return __longlong_as_double((2046LL - e) << 52);
 }
 
 // WENO5-Z at the face right of v2 from v0..v4 (point-value interpolation

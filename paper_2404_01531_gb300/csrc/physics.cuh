@@ -8,6 +8,7 @@
 //             current and the cleaning damping are the implicit operator (Sec. III.B).
 #pragma once
 #include "ffe_internal.h"
+#include "fp64util.cuh"
 
 namespace ffe {
 
@@ -25,7 +26,7 @@ __device__ __forceinline__ void current_flat(const double* U, double eta, double
         jf[0] = jf[1] = jf[2] = 0.0;
         return;
     }
-    double ib2 = 1.0 / B2;
+    double ib2 = recip_any(B2);
     double EB = dot3(E, B), E2 = dot3(E, E);
     double cx = E[1] * B[2] - E[2] * B[1];
     double cy = E[2] * B[0] - E[0] * B[2];
@@ -46,7 +47,7 @@ __device__ __forceinline__ void current_eta_flat(const double* U, double eta, do
     const double* B = U + 3;
     double B2 = dot3(B, B);
     if (B2 == 0.0 || eta == 0.0) { jp[0] = jp[1] = jp[2] = 0.0; return; }
-    double ib2 = 1.0 / B2;
+    double ib2 = recip_any(B2);
     double EB = dot3(E, B), E2 = dot3(E, E);
     double rr = E2 - B2;
     rr = rr > 0.0 ? rr : 0.0;
@@ -91,13 +92,13 @@ __device__ __forceinline__ void hard_clamp_flat(double* U) {
     const double* B = U + 3;
     double B2 = dot3(B, B);
     if (B2 == 0.0) { E[0] = E[1] = E[2] = 0.0; return; }
-    double f = dot3(E, B) / B2;
+    double f = dot3(E, B) * recip_any(B2);
     E[0] = fma(-f, B[0], E[0]);
     E[1] = fma(-f, B[1], E[1]);
     E[2] = fma(-f, B[2], E[2]);
     double E2 = dot3(E, E);
     if (E2 > B2) {
-        double s = sqrt(B2 / E2);
+        double s = sqrt(B2 * recip_any(E2));
         E[0] *= s; E[1] *= s; E[2] *= s;
     }
 }
@@ -115,17 +116,17 @@ __device__ __forceinline__ double stiff_root(double c, double p2, double a2, dou
     const double K = c * p2 * ib2;
     double s = 0.0;
     if (K > 0.0) {
-        const double ta = sqrt(K / ((c > 1.0 ? c - 1.0 : 0.0) + cbrt(K)));
+        const double ta = sqrt(K * recip_any((c > 1.0 ? c - 1.0 : 0.0) + cbrt(K)));
         s = ta > 1.0 ? ta - 1.0 : 0.0;
     }
     double step = 1.0;
     for (int it = 0; it < 100; ++it) {
-        const double a1 = 1.0 + s, b1 = 1.0 + c + s, w = 1.0 / (a1 * b1);
+        const double a1 = 1.0 + s, b1 = 1.0 + c + s, w = recip_any(a1 * b1);
         const double u = b1 * w, v = a1 * w;
         const double pu = p2 * u * u, av = a2 * v * v;
         const double g = c * ((pu + av) - B2) * ib2 - s;
         const double dg = -2.0 * c * (pu * u + av * v) * ib2 - 1.0;
-        const double sn = s - g / dg;
+        const double sn = fma(-g, recip_any(dg), s);
         step = sn - s;
         if (!(sn > s)) break;
         s = sn;
@@ -141,19 +142,19 @@ __device__ __forceinline__ double stiff_root(double c, double p2, double a2, dou
 // g(s) = c (|E(s)|^2 - B^2)/B^2 - s (stiff_root).  Returns false if Newton hit
 // its iteration cap.
 __device__ __forceinline__ bool stiff_solve_flat(double* U, const Dev& d, double dta) {
-    U[6] = U[6] / fma(d.kpsi, dta, 1.0);
-    U[7] = U[7] / fma(d.kphi, dta, 1.0);
+    U[6] *= recip_any(fma(d.kpsi, dta, 1.0));
+    U[7] *= recip_any(fma(d.kphi, dta, 1.0));
     if (d.eta == 0.0) return true;
     double* E = U;
     const double* B = U + 3;
     double B2 = dot3(B, B);
     if (B2 == 0.0) return true;
     double c = d.eta * dta;
-    double ib2 = 1.0 / B2;
+    double ib2 = recip_any(B2);
     double f = dot3(E, B) * ib2;
     double pa[3] = {f * B[0], f * B[1], f * B[2]};
     double pe[3] = {E[0] - pa[0], E[1] - pa[1], E[2] - pa[2]};
-    double i1c = 1.0 / (1.0 + c);
+    double i1c = recip_any(1.0 + c);
     double e0[3] = {fma(pa[0], i1c, pe[0]), fma(pa[1], i1c, pe[1]), fma(pa[2], i1c, pe[2])};
     if (!(dot3(e0, e0) > B2)) {
         E[0] = e0[0]; E[1] = e0[1]; E[2] = e0[2];
@@ -161,7 +162,7 @@ __device__ __forceinline__ bool stiff_solve_flat(double* U, const Dev& d, double
     }
     bool ok;
     const double s = stiff_root(c, dot3(pe, pe), dot3(pa, pa), B2, ib2, ok);
-    double u = 1.0 / (1.0 + s), v = 1.0 / (1.0 + c + s);
+    double u = recip_any(1.0 + s), v = recip_any(1.0 + c + s);
     E[0] = fma(pe[0], u, pa[0] * v);
     E[1] = fma(pe[1], u, pa[1] * v);
     E[2] = fma(pe[2], u, pa[2] * v);
