@@ -33,6 +33,8 @@ UNIT = "element-node updates/s"
 # moves this many bytes for each element of its chunk
 DRAM_BYTES_PER_FD_ELEMENT = {"fd_flux": 6.34e5}
 
+RECON = {"weno5z": 0, "mp5": 1}
+
 CPU_SAMPLE = dict(nx=16, ny=2, nz=2, x_half=0.5)
 CPU_SAMPLE_TEXT = ("oracle (numpy fp64, 1 thread) on a 16x2x2-element slab of the breakdown "
                    "workload (same element width, order and current sheet), whole hybrid steps")
@@ -163,10 +165,10 @@ def run_shell(args):
     curved-mesh step (subcell fluxes of every physical component at every face)."""
     import torch
     from paper_2404_01531_gb300 import ffe
-    from paper_2404_01531_gb300.roofline import FP64_PEAK_TFLOPS, FD_FLUX_FLOPS, fd_faces_per_element
+    from paper_2404_01531_gb300.roofline import FP64_PEAK_TFLOPS, fd_faces_per_element, fd_flux_flops
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     cfg = W.adjoint_pulsar(steps=args.steps)
-    cfg["params"].update(tci_on=0)
+    cfg["params"].update(tci_on=0, recon=RECON[args.recon])
     ctx = ffe.Context(cfg)
     U, m = ctx.state()
     e = torch.arange(ctx.n_elem, device=m.device)
@@ -192,13 +194,14 @@ def run_shell(args):
     ctx.set_profiling(False)
     prof = ctx.profile_read()
     n_fd = j1.fd_elem_updates - j0.fd_elem_updates
-    fl = n_fd * fd_faces_per_element(ctx.P) * FD_FLUX_FLOPS
+    fl = n_fd * fd_faces_per_element(ctx.P) * fd_flux_flops(RECON[args.recon])
     ach = fl / (prof["fd_flux"][1] / 1e3) / 1e12
     line = {"metric": METRIC, "value": (i1.node_updates - i0.node_updates) / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "neutron-star shell 6 wedges x 6x6x12 P=5, eta=1e5, three inner radial layers "
-                                   "on FD (frozen mask)", "elements": ctx.n_elem, "fd_elements": int(mask.sum())},
+                                   "on FD (frozen mask)", "elements": ctx.n_elem, "fd_elements": int(mask.sum()),
+                       "recon": args.recon},
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": ach / FP64_PEAK_TFLOPS, "kernel": "fd_flux (k_fd_flux_curved)",
                          "units": {"fd_elem_updates": n_fd}},
@@ -527,6 +530,8 @@ def main():
                          "shell: that shell with three FD layers, frozen mask (curved FD kernels); "
                          "oned: the paper's 1-D tests and its DG/FD split experiment")
     ap.add_argument("--no-adjoint", action="store_true", help="breakdown: skip the adjoint/forward timing")
+    ap.add_argument("--recon", default="weno5z", choices=list(RECON),
+                    help="breakdown and shell: FD reconstruction (the paper's WENO5-Z, or MP5)")
     ap.add_argument("--n-inst", type=int, default=32)
     ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
     args = ap.parse_args()
@@ -550,10 +555,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2404_01531_gb300 import ffe
-    from paper_2404_01531_gb300.roofline import (FP64_PEAK_TFLOPS, FD_FLUX_FLOPS, dg_flops_per_node,
+    from paper_2404_01531_gb300.roofline import (FP64_PEAK_TFLOPS, fd_flux_flops, dg_flops_per_node,
                                                  fd_faces_per_element)
 
     cfg = W.breakdown(nx=args.nx, x_half=2.0 * args.nx / 64)
+    cfg["params"]["recon"] = RECON[args.recon]
     stream = torch.cuda.current_stream()
     ctx = ffe.Context(cfg, stream=stream)
     ctx.set_initial()
@@ -609,7 +615,7 @@ def main():
     if dom == "dg_substep":
         flops = n_dg_upd * nn * sum(dg_flops_per_node(P, s) for s in range(3)) / 3.0
     elif dom == "fd_flux":
-        flops = n_fd_upd * fd_faces_per_element(P) * FD_FLUX_FLOPS
+        flops = n_fd_upd * fd_faces_per_element(P) * fd_flux_flops(RECON[args.recon])
     else:
         flops = None
     roof = None
@@ -665,7 +671,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"breakdown {args.nx}x8x8 P=5 (FFE breakdown / current sheet, eta=1e3)",
                        "elements": E, "P": P, "dg_nodes": E * nn, "fd_elements_end": n_fd_end,
-                       "parallelism": f"replicas x{ws}", "l2": "working set > L2 (no flush needed)"},
+                       "parallelism": f"replicas x{ws}", "l2": "working set > L2 (no flush needed)",
+                       "recon": args.recon},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
             "adjoint": adj, "status_bits": status}

@@ -97,7 +97,13 @@ typedef struct {
     double weno_eps; int fd_corrector;               /* FD subcell scheme                */
     int constraint_mode;                             /* FFE_RELAX | FFE_HARD | ...        */
     double omega_star;                               /* star rotation (FFE_BC_STAR)       */
+    int recon;                                       /* FFE_RECON_WENO5Z | FFE_RECON_MP5  */
 } ffe_params;
+
+/* FD reconstruction: WENO5-Z with q = 2 (the paper's, Sec. III.C.2) or MP5
+ * (Suresh & Huynh's monotonicity-preserving limiter on the 5-point
+ * interpolant); the adjoint is built for WENO5-Z only. */
+enum { FFE_RECON_WENO5Z = 0, FFE_RECON_MP5 = 1 };
 
 /* Sizes of the state vector. */
 typedef struct {

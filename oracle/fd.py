@@ -50,6 +50,64 @@ def weno5z(v0, v1, v2, v3, v4, eps, q=2):
     return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2)
 
 
+def _minmod(a, b):
+    """minmod(a, b) = (sign a + sign b)/2 min(|a|, |b|)."""
+    return 0.5 * (np.sign(a) + np.sign(b)) * np.minimum(np.abs(a), np.abs(b))
+
+
+def _minmod4(a, b, c, d):
+    """minmod of four values: the smallest magnitude when all four share a sign, else 0."""
+    same = (np.sign(a) == np.sign(b)) & (np.sign(a) == np.sign(c)) & (np.sign(a) == np.sign(d))
+    m = np.minimum(np.minimum(np.abs(a), np.abs(b)), np.minimum(np.abs(c), np.abs(d)))
+    return np.where(same, np.sign(a) * m, 0.0)
+
+
+def mp5(v0, v1, v2, v3, v4, alpha=4.0):
+    """MP5 value at the face between v2 and v3 from the left-biased stencil:
+    the monotonicity-preserving limiter of Suresh & Huynh (J. Comput. Phys.
+    136, 83 (1997)) applied to the five-point interpolant.
+
+    [reading] The paper reconstructs with WENO5-Z; MP5 is the alternative the
+    task names.  As for WENO5-Z (see `weno5z`) the subcell data are point
+    values, so the unlimited value is the point-value interpolant at the face,
+    (3 v0 - 20 v1 + 90 v2 + 60 v3 - 5 v4)/128 (the 5-point polynomial through
+    v0..v4), and the limiter's bounds are Suresh & Huynh's, written in the same
+    second differences:
+      v_MP = v2 + minmod(v3 - v2, alpha (v2 - v1));  if (vL - v2)(vL - v_MP) <= 0
+      the value is vL; otherwise, with d_j the second differences centred on
+      v1, v2, v3, d+ = minmod4(4 d2 - d3, 4 d3 - d2, d2, d3),
+      d- = minmod4(4 d2 - d1, 4 d1 - d2, d2, d1), v_UL = v2 + alpha (v2 - v1),
+      v_MD = (v2 + v3)/2 - d+/2, v_LC = v2 + (v2 - v1)/2 + (4/3) d-,
+      v_min = max(min(v2, v3, v_MD), min(v2, v_UL, v_LC)),
+      v_max = min(max(v2, v3, v_MD), max(v2, v_UL, v_LC)),
+      value = median(vL, v_min, v_max) = vL + minmod(v_min - vL, v_max - vL).
+    The unlimited test uses no tolerance (the median returns vL whenever it
+    lies within the bounds, so rounding-level products change nothing)."""
+    vL = (3.0 * v0 - 20.0 * v1 + 90.0 * v2 + 60.0 * v3 - 5.0 * v4) / 128.0
+    vMP = v2 + _minmod(v3 - v2, alpha * (v2 - v1))
+    d1 = v0 - 2.0 * v1 + v2
+    d2 = v1 - 2.0 * v2 + v3
+    d3 = v2 - 2.0 * v3 + v4
+    dp = _minmod4(4.0 * d2 - d3, 4.0 * d3 - d2, d2, d3)
+    dm = _minmod4(4.0 * d2 - d1, 4.0 * d1 - d2, d2, d1)
+    vUL = v2 + alpha * (v2 - v1)
+    vMD = 0.5 * (v2 + v3) - 0.5 * dp
+    vLC = v2 + 0.5 * (v2 - v1) + (4.0 / 3.0) * dm
+    vmin = np.maximum(np.minimum(np.minimum(v2, v3), vMD), np.minimum(np.minimum(v2, vUL), vLC))
+    vmax = np.minimum(np.maximum(np.maximum(v2, v3), vMD), np.maximum(np.maximum(v2, vUL), vLC))
+    lim = vL + _minmod(vmin - vL, vmax - vL)
+    return np.where((vL - v2) * (vL - vMP) <= 0.0, vL, lim)
+
+
+def reconstruct(v, prm):
+    """Left and right face values from the six cells around each face: WENO5-Z
+    (default, the paper's choice) or MP5 (prm["recon"] == 1)."""
+    if prm.get("recon", 0) == 1:
+        return mp5(v[0], v[1], v[2], v[3], v[4]), mp5(v[5], v[4], v[3], v[2], v[1])
+    eps = prm["weno_eps"]
+    return weno5z(v[0], v[1], v[2], v[3], v[4], eps), weno5z(v[5], v[4], v[3], v[2], v[1], eps)
+
+
 def fill_ghosts(st, disc, sel, met_fn, prm):
     """Extended cell arrays (9, n, Nc+6, Nc+6, Nc+6) for FD elements `sel`, the
     coordinates of every filled cell (for the metric), and the current J~ of the
@@ -149,8 +207,7 @@ def rhs_fd(st, disc, met, prm):
         # face m (0..Nc) between interior cells m-1 and m; extended index of cell c is c + NG
         # v[o+3][m] = cell m+o (o = -3..2) for each face m
         v = [W[sl(NG + o, NG + o + Nc + 1)] for o in range(-3, 3)]
-        WL = weno5z(v[0], v[1], v[2], v[3], v[4], eps)
-        WR = weno5z(v[5], v[4], v[3], v[2], v[1], eps)
+        WL, WR = reconstruct(v, prm)
         UL, UR = WL[:9], WR[:9]
         JL, JR = WL[9:], WR[9:]
         mf = _met_at(met["fdface"][k], sel, ())

@@ -41,7 +41,7 @@ class Problem:
         self.initial = lambda xyz: initial.evaluate(ikind, xyz, **ikw)
         # the algebraic-only mode has no driver current
         self.prm = dict(eta=p["eta"] if p["constraint_mode"] != 1 else 0.0, kappa_psi=p["kappa_psi"], kappa_phi=p["kappa_phi"],
-                        weno_eps=p["weno_eps"], fd_corrector=p["fd_corrector"],
+                        weno_eps=p["weno_eps"], fd_corrector=p["fd_corrector"], recon=p.get("recon", 0),
                         dirichlet=self.initial, omega=p["omega_star"],
                         mode=p["constraint_mode"], filter_on=p["filter_on"], tci_on=p["tci_on"],
                         tci_alpha=p["tci_alpha"], tci_M=p["tci_M"])

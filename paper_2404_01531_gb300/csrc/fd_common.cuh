@@ -151,6 +151,37 @@ __device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, dou
     uR = weno5z_combine(bR0, bR1, bR2, pR0, p234, p123);
 }
 
+// MP5 value at the right face of v2 from v0..v4 (point values): Suresh &
+// Huynh's monotonicity-preserving limiter (J. Comput. Phys. 136, 83 (1997))
+// on the 5-point interpolant (3 v0 - 20 v1 + 90 v2 + 60 v3 - 5 v4)/128, alpha = 4:
+// the interpolant when it lies between v2 and v_MP = v2 + minmod(v3 - v2,
+// alpha (v2 - v1)), else its median with the bounds built from v_UL, v_MD,
+// v_LC and the minmod4 curvatures of the second differences.
+__device__ __forceinline__ double minmod2(double a, double b) {
+    return a * b > 0.0 ? (fabs(a) < fabs(b) ? a : b) : 0.0;
+}
+
+__device__ __forceinline__ double minmod4(double a, double b, double c, double d) {
+    if (a > 0.0 && b > 0.0 && c > 0.0 && d > 0.0) return fmin(fmin(a, b), fmin(c, d));
+    if (a < 0.0 && b < 0.0 && c < 0.0 && d < 0.0) return fmax(fmax(a, b), fmax(c, d));
+    return 0.0;
+}
+
+__device__ __forceinline__ double mp5(double v0, double v1, double v2, double v3, double v4) {
+    const double vL = fma(0.0234375, v0, fma(-0.15625, v1, fma(0.703125, v2, fma(0.46875, v3, -0.0390625 * v4))));
+    const double vMP = v2 + minmod2(v3 - v2, 4.0 * (v2 - v1));
+    if ((vL - v2) * (vL - vMP) <= 0.0) return vL;
+    const double d1 = v0 - 2.0 * v1 + v2, d2 = v1 - 2.0 * v2 + v3, d3 = v2 - 2.0 * v3 + v4;
+    const double dp = minmod4(4.0 * d2 - d3, 4.0 * d3 - d2, d2, d3);
+    const double dm = minmod4(4.0 * d2 - d1, 4.0 * d1 - d2, d2, d1);
+    const double vUL = v2 + 4.0 * (v2 - v1);
+    const double vMD = 0.5 * (v2 + v3) - 0.5 * dp;
+    const double vLC = v2 + 0.5 * (v2 - v1) + (4.0 / 3.0) * dm;
+    const double vmin = fmax(fmin(fmin(v2, v3), vMD), fmin(fmin(v2, vUL), vLC));
+    const double vmax = fmin(fmax(fmax(v2, v3), vMD), fmax(fmax(v2, vUL), vLC));
+    return vL + minmod2(vmin - vL, vmax - vL);
+}
+
 // Reverse mode of weno5z_combine for indicators B_k (eps included) and
 // candidates p_k: from the value's adjoint yb, the candidates' adjoints pb_k
 // and the indicators' adjoints Bb_k.  With A_k = d_k s_k P_k, s_k = b_k^2 +

@@ -83,7 +83,7 @@ struct Dev {
     int dg_grid;                    // CTAs of the curved DG kernel (chosen by the autotuner; 0 = default)
     // physics and scheme parameters
     double eta, kpsi, kphi, dt, weno_eps, omega;
-    int mode, filter_on, tci_on, fd_corr;
+    int mode, filter_on, tci_on, fd_corr, recon;
     double thr_dg, thr_fd;          // (P+1-M)^-alpha and (P+1-M)^-(alpha+1)
     // geometry of the affine box: d xi / d x per element and axis
     const double* ijac;             // [E][3]

@@ -1028,6 +1028,8 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     }
     if (params->constraint_mode < FFE_RELAX || params->constraint_mode > FFE_RELAX_THEN_HARD)
         return fail(FFE_EINVAL, "constraint mode %d", params->constraint_mode);
+    if (params->recon != FFE_RECON_WENO5Z && params->recon != FFE_RECON_MP5)
+        return fail(FFE_EINVAL, "reconstruction %d", params->recon);
     if (params->eta < 0 || params->kappa_psi < 0 || params->kappa_phi < 0) return fail(FFE_EINVAL, "negative damping");
     if (params->tci_on && (params->tci_M < 1 || params->tci_M > P)) return fail(FFE_EINVAL, "tci_M=%d", params->tci_M);
     if (params->dt < 0 || (params->dt == 0 && !(params->cfl > 0 && params->c_over_D > 0)))
@@ -1064,6 +1066,7 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     d.kpsi = params->kappa_psi;
     d.kphi = params->kappa_phi;
     d.weno_eps = params->weno_eps;
+    d.recon = params->recon;
     d.omega = params->omega_star;
     d.mode = params->constraint_mode;
     d.filter_on = params->filter_on;
@@ -1102,7 +1105,7 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
         if (pi.eta != p0.eta || pi.kappa_psi != p0.kappa_psi || pi.kappa_phi != p0.kappa_phi ||
             pi.filter_on != p0.filter_on || pi.filter_a != p0.filter_a || pi.filter_b != p0.filter_b ||
             pi.tci_on != p0.tci_on || pi.tci_M != p0.tci_M || pi.tci_alpha != p0.tci_alpha ||
-            pi.weno_eps != p0.weno_eps || pi.fd_corrector != p0.fd_corrector ||
+            pi.weno_eps != p0.weno_eps || pi.fd_corrector != p0.fd_corrector || pi.recon != p0.recon ||
             pi.constraint_mode != p0.constraint_mode)
             return fail(FFE_EINVAL, "instance %d: scheme parameters differ from instance 0", i);
         if (pi.dt < 0 || (pi.dt == 0 && !(pi.cfl > 0 && pi.c_over_D > 0)))
@@ -1111,6 +1114,7 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
     }
     if (p0.constraint_mode < FFE_RELAX || p0.constraint_mode > FFE_RELAX_THEN_HARD)
         return fail(FFE_EINVAL, "constraint mode %d", p0.constraint_mode);
+    if (p0.recon != FFE_RECON_WENO5Z && p0.recon != FFE_RECON_MP5) return fail(FFE_EINVAL, "reconstruction %d", p0.recon);
     ffe_ctx* c = new ffe_ctx();
     auto bail = [&](ffe_status s) { ffe_destroy(c); return s; };
     c->batch = true;
@@ -1153,6 +1157,7 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
     d.kpsi = p0.kappa_psi;
     d.kphi = p0.kappa_phi;
     d.weno_eps = p0.weno_eps;
+    d.recon = p0.recon;
     d.omega = p0.omega_star;
     d.mode = p0.constraint_mode;
     d.filter_on = p0.filter_on;
@@ -1457,6 +1462,7 @@ static ffe_status adjoint_ready(ffe_ctx* c) {
     const Dev& d = c->d;
     if (!d.curved || d.ks || c->batch) return fail(FFE_ENOTIMPL, "the adjoint is built for flat-metric shells");
     if (d.mode == FFE_HARD || d.mode == FFE_RELAX_THEN_HARD) return fail(FFE_ENOTIMPL, "the adjoint of the clamp is not built");
+    if (d.recon != FFE_RECON_WENO5Z) return fail(FFE_ENOTIMPL, "the adjoint is built for WENO5-Z reconstruction");
     if (d.tci_on) return fail(FFE_ESTATE, "the adjoint differentiates a fixed mask: freeze it first (ffe_freeze_mask)");
     std::vector<unsigned char> m(d.E);
     CK(cudaMemcpyAsync(m.data(), d.mask, d.E, cudaMemcpyDeviceToHost, c->st));

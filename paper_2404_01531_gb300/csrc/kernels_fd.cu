@@ -182,7 +182,8 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
     }
 }
 
-// 12 left/right face values and the two cells either side, from the extended block
+// 12 left/right face values (WENO5-Z pair or MP5) and the two cells either side, from the extended block
+template <int RECON>
 __device__ __forceinline__ void reconstruct(const Dev& d, int wl, int k, int m, int ta, int tb, int nc,
                                             double* UL, double* UR, double* Um, double* Up) {
     const int ne = nc + 2 * GH;
@@ -198,13 +199,19 @@ __device__ __forceinline__ void reconstruct(const Dev& d, int wl, int k, int m, 
         const double* src = ext_at(d, qq, wl) + base;
         const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
         const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
-        weno5z_pair(v0, v1, v2, v3, v4, v5, d.weno_eps, UL[qq], UR[qq]);
+        if (RECON == FFE_RECON_MP5) {
+            UL[qq] = mp5(v0, v1, v2, v3, v4);
+            UR[qq] = mp5(v5, v4, v3, v2, v1);
+        } else {
+            weno5z_pair(v0, v1, v2, v3, v4, v5, d.weno_eps, UL[qq], UR[qq]);
+        }
         Um[qq] = v2;
         Up[qq] = v3;
     }
 }
 
 // One thread per (chunk position, direction, face): box elements.
+template <int RECON>
 __global__ void __launch_bounds__(128, 4) k_fd_flux(Dev d, const int* list, int ci, int w0) {
     const int n = chunk_n(d, ci, w0);
     const int64_t nfc = nface(d);
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(128, 4) k_fd_flux(Dev d, const int* list, int 
         int m, ta, tb;
         if (!face_coords(fi, nc, m, ta, tb)) continue;
         double UL[NQ], UR[NQ], Um[NQ], Up[NQ];
-        reconstruct(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
+        reconstruct<RECON>(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
         double FL[NV], FR[NV], Fs[NV];
         flux_dir_flat(UL, UL + NV, k, FL);
         flux_dir_flat(UR, UR + NV, k, FR);
@@ -237,6 +244,7 @@ __global__ void __launch_bounds__(128, 4) k_fd_flux(Dev d, const int* list, int 
 // face, Rusanov dissipation along the unit face normal n^ (lambda = 1):
 //   F^j = (F^j(L) + F^j(R))/2 - n^_j (U_R - U_L)/2,
 // optional corrector per component.
+template <int RECON>
 __global__ void __launch_bounds__(128, 4) k_fd_flux_curved(Dev d, const int* list, int ci, int w0) {
     const int n = chunk_n(d, ci, w0);
     const int64_t nfc = nface(d);
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(128, 4) k_fd_flux_curved(Dev d, const int* lis
         int t1, t2;
         axes_of(k, t1, t2);
         double UL[NQ], UR[NQ], Um[NQ], Up[NQ];
-        reconstruct(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
+        reconstruct<RECON>(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
         double nh[3];
         shell_face_normal(shell_pts(d, e, nc), k, m, ta, tb, nh);
         for (int j = 0; j < 3; ++j) {
@@ -377,8 +385,13 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin
         k_fd_fill_ghosts<<<152 * 2, 256, smem, st>>>(d, list, ci, w0, Uin, J);
         prof_end(st);
         prof_begin("fd_flux", st);
-        if (d.curved) k_fd_flux_curved<<<grid, 128, 0, st>>>(d, list, ci, w0);
-        else k_fd_flux<<<grid, 128, 0, st>>>(d, list, ci, w0);
+        if (d.recon == FFE_RECON_MP5) {
+            if (d.curved) k_fd_flux_curved<FFE_RECON_MP5><<<grid, 128, 0, st>>>(d, list, ci, w0);
+            else k_fd_flux<FFE_RECON_MP5><<<grid, 128, 0, st>>>(d, list, ci, w0);
+        } else {
+            if (d.curved) k_fd_flux_curved<FFE_RECON_WENO5Z><<<grid, 128, 0, st>>>(d, list, ci, w0);
+            else k_fd_flux<FFE_RECON_WENO5Z><<<grid, 128, 0, st>>>(d, list, ci, w0);
+        }
         prof_end(st);
         prof_begin("fd_update", st);
         switch (sub) {

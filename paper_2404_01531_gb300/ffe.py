@@ -52,7 +52,7 @@ class Params(ctypes.Structure):
                 ("filter_on", ctypes.c_int), ("filter_a", ctypes.c_double), ("filter_b", ctypes.c_double),
                 ("tci_on", ctypes.c_int), ("tci_M", ctypes.c_int), ("tci_alpha", ctypes.c_double),
                 ("weno_eps", ctypes.c_double), ("fd_corrector", ctypes.c_int),
-                ("constraint_mode", ctypes.c_int), ("omega_star", ctypes.c_double)]
+                ("constraint_mode", ctypes.c_int), ("omega_star", ctypes.c_double), ("recon", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -154,7 +154,7 @@ def check(status):
 def params_from(p):
     return Params(p["eta"], p["kappa_psi"], p["kappa_phi"], p["cfl"], p["c_over_D"], p.get("dt", 0.0),
                   p["filter_on"], p["filter_a"], p["filter_b"], p["tci_on"], p["tci_M"], p["tci_alpha"],
-                  p["weno_eps"], p["fd_corrector"], p["constraint_mode"], p["omega_star"])
+                  p["weno_eps"], p["fd_corrector"], p["constraint_mode"], p["omega_star"], p.get("recon", 0))
 
 
 class _DevArray:

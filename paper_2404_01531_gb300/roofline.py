@@ -39,6 +39,15 @@ def dg_flops_per_node(P, sub, filter_on=True, tci_on=True, solve=True, a=36.0, b
 
 WENO_FLOPS = 73                  # one WENO5-Z face value (3 candidates, 3 indicators, Z weights, 1 div)
 FD_FLUX_FLOPS = 24 * WENO_FLOPS + 45 + 36   # 12 quantities x (L, R) + Rusanov + corrector
+# MP5 value on its unlimited path: the 5-point interpolant (9), v_MP (4) and the
+# bracketing test (3); the limited path adds data-dependent work not counted
+MP5_FLOPS = 16
+FD_FLUX_FLOPS_MP5 = 24 * MP5_FLOPS + 45 + 36
+
+
+def fd_flux_flops(recon):
+    """Algorithmic flops of one face of the FD flux kernel for the reconstruction (0 WENO5-Z, 1 MP5)."""
+    return FD_FLUX_FLOPS_MP5 if recon == 1 else FD_FLUX_FLOPS
 
 
 def fd_faces_per_element(P):
