@@ -112,12 +112,14 @@ __device__ __forceinline__ int chunk_n(const Dev& d, int ci, int w0) {
 // indicators b_k (eps included); the ideal weights are taken as (1, 10, 5)
 // (scale-free).
 __device__ __forceinline__ double weno5z_combine(double b0, double b1, double b2, double p0, double p1, double p2) {
+    // A_k = d_k (b_k^2 + t^2) P_k with P_k the product of the other two b_j^2
+    // is d_k (X + t^2 P_k), X = b_0^2 b_1^2 b_2^2 shared by the three
     const double t = b0 - b2;
     const double t2 = t * t;
     const double q0 = b0 * b0, q1 = b1 * b1, q2 = b2 * b2;
-    const double A0 = (q0 + t2) * (q1 * q2);
-    const double A1 = (10.0 * (q1 + t2)) * (q0 * q2);
-    const double A2 = (5.0 * (q2 + t2)) * (q0 * q1);
+    const double P0 = q1 * q2, P1 = q0 * q2, P2 = q0 * q1;
+    const double X = q0 * P0;
+    const double A0 = fma(t2, P0, X), A1 = 10.0 * fma(t2, P1, X), A2 = 5.0 * fma(t2, P2, X);
     return fma(A0, p0, fma(A1, p1, A2 * p2)) * recip_nr(A0 + A1 + A2);
 }
 

@@ -226,15 +226,18 @@ __global__ void __launch_bounds__(128, 4) k_fd_flux(Dev d, const int* list, int 
         if (!face_coords(fi, nc, m, ta, tb)) continue;
         double UL[NQ], UR[NQ], Um[NQ], Up[NQ];
         reconstruct<RECON>(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
-        double FL[NV], FR[NV], Fs[NV];
-        flux_dir_flat(UL, UL + NV, k, FL);
-        flux_dir_flat(UR, UR + NV, k, FR);
-        for (int v = 0; v < NV; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * (UR[v] - UL[v]);
+        // the flat flux is linear in (U, J~): (F(UL) + F(UR))/2 = F((UL + UR)/2)
+        // and the corrector's F(Um) + F(Up) = F(Um + Up)
+        double hS[NQ], Fh[NV], Fs[NV];
+        for (int qq = 0; qq < NQ; ++qq) hS[qq] = 0.5 * (UL[qq] + UR[qq]);
+        flux_dir_flat(hS, hS + NV, k, Fh);
+        for (int v = 0; v < NV; ++v) Fs[v] = fma(-0.5, UR[v] - UL[v], Fh[v]);
         if (d.fd_corr) {
-            double Fm[NV], Fp[NV];
-            flux_dir_flat(Um, Um + NV, k, Fm);
-            flux_dir_flat(Up, Up + NV, k, Fp);
-            for (int v = 0; v < NV; ++v) Fs[v] = Fs[v] - (1.0 / 6.0) * (Fm[v] - 2.0 * Fs[v] + Fp[v]);
+            double Sm[NQ], Fm[NV];
+            for (int qq = 0; qq < NQ; ++qq) Sm[qq] = Um[qq] + Up[qq];
+            flux_dir_flat(Sm, Sm + NV, k, Fm);
+            // F - (Fm - 2 F + Fp)/6 = (4/3) F - (Fm + Fp)/6
+            for (int v = 0; v < NV; ++v) Fs[v] = fma(-1.0 / 6.0, Fm[v], (4.0 / 3.0) * Fs[v]);
         }
         for (int v = 0; v < NV; ++v) flux_at(d, k, v, wl)[fi] = Fs[v];
     }
@@ -263,17 +266,22 @@ __global__ void __launch_bounds__(128, 4) k_fd_flux_curved(Dev d, const int* lis
         reconstruct<RECON>(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
         double nh[3];
         shell_face_normal(shell_pts(d, e, nc), k, m, ta, tb, nh);
+        // the flat flux is linear in (U, J~): (F^j(L) + F^j(R))/2 = F^j((UL + UR)/2),
+        // and the corrector's F(Um) + F(Up) = F(Um + Up)
+        double hS[NQ], dU[NV], Sm[NQ];
+        for (int qq = 0; qq < NQ; ++qq) hS[qq] = 0.5 * (UL[qq] + UR[qq]);
+        for (int v = 0; v < NV; ++v) dU[v] = UR[v] - UL[v];
+        if (d.fd_corr)
+            for (int qq = 0; qq < NQ; ++qq) Sm[qq] = Um[qq] + Up[qq];
         for (int j = 0; j < 3; ++j) {
-            double FL[NV], FR[NV], Fs[NV];
-            flux_dir_flat(UL, UL + NV, j, FL);
-            flux_dir_flat(UR, UR + NV, j, FR);
-            const double nj = nh[j];
-            for (int v = 0; v < NV; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * nj * (UR[v] - UL[v]);
+            double Fh[NV], Fs[NV];
+            flux_dir_flat(hS, hS + NV, j, Fh);
+            const double hn = -0.5 * nh[j];
+            for (int v = 0; v < NV; ++v) Fs[v] = fma(hn, dU[v], Fh[v]);
             if (d.fd_corr) {
-                double Fm[NV], Fp[NV];
-                flux_dir_flat(Um, Um + NV, j, Fm);
-                flux_dir_flat(Up, Up + NV, j, Fp);
-                for (int v = 0; v < NV; ++v) Fs[v] = Fs[v] - (1.0 / 6.0) * (Fm[v] - 2.0 * Fs[v] + Fp[v]);
+                double Fm[NV];
+                flux_dir_flat(Sm, Sm + NV, j, Fm);
+                for (int v = 0; v < NV; ++v) Fs[v] = fma(-1.0 / 6.0, Fm[v], (4.0 / 3.0) * Fs[v]);
             }
             for (int v = 0; v < NV; ++v) flux_at_c(d, k, j, v, wl)[fi] = Fs[v];
         }
