@@ -299,6 +299,27 @@ ffe_status ffe_luminosity(ffe_ctx* ctx, const double* U_dev, double r_L, double*
  * parameter `which` (DIPOLE: 0 = mu, 2 = chi) at the nodes, into dU_dev. */
 ffe_status ffe_initial_tangent(ffe_ctx* ctx, int which, double* dU_dev);
 
+/* Checkpoint / resume.  ffe_save writes the context's evolving state to a
+ * caller-owned host buffer: time, step count, initial-data kind and
+ * parameters (the boundary data are rebuilt from them), the state vector, the
+ * DG/FD mask, the FD slot pool of a batched context and the update counters.
+ * With host_buf = NULL it only stores the size needed in *bytes; otherwise
+ * *bytes is the buffer's size on entry (FFE_EINVAL if too small) and the
+ * bytes written on return; synchronises the context stream.  ffe_load
+ * restores such a checkpoint into a context created with the same domain,
+ * elements, orders, metric and FD pool (FFE_EINVAL otherwise); stepping on
+ * from it gives the same results as the saved context would.  Adjoint
+ * work fields are not part of a checkpoint. */
+ffe_status ffe_save(ffe_ctx* ctx, void* host_buf, size_t* bytes);
+ffe_status ffe_load(ffe_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Pointwise constraint diagnostics (flat metric; FFE_ENOTIMPL on
+ * Kerr-Schild) of a state vector U_dev (NULL: the context's state), over the
+ * DG nodes of DG elements and the subcells of FD elements: out_host[0] =
+ * max |E~.B~|, [1] = min (B~^2 - E~^2), [2] = max |psi~|, [3] = max |phi~|.
+ * Synchronises the context stream. */
+ffe_status ffe_constraints(ffe_ctx* ctx, const double* U_dev, double* out_host);
+
 /* Cartesian coordinates of the DG nodes [3][n_dg] and of the FD subcell
  * centres [3][n_fd] (every element's block, in state-vector order), copied
  * into caller-owned device arrays (either may be NULL) on the context stream.

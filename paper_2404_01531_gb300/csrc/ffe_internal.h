@@ -158,6 +158,7 @@ int fd_chunks(const Dev& d);
 // extended blocks (U, J~ with ghosts) of the listed FD elements of one chunk
 void launch_fd_fill(const Dev& d, const int* list, int count_index, int w0, Field U, Field J, cudaStream_t st);
 void launch_eval_recip(const double* x, double* y, int64_t n, cudaStream_t st);
+void launch_constraints(const Dev& d, Field U, double* part, int blocks, cudaStream_t st);
 // out += (d RHS_FD/dU)^T L (kernels_adjoint_fd.cu); extb: scratch of the size of d.ext
 void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, double* extb, double* omega_bar,
                        cudaStream_t st);

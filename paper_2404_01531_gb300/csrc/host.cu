@@ -338,6 +338,7 @@ struct ffe_ctx {
     bool adj_fd = false;             // the current mask has FD elements
     double* d_extb = nullptr;        // extended-block adjoint of one FD chunk
     double* d_omega_bar = nullptr;
+    double* d_cons = nullptr;        // per-block partials of ffe_constraints
     double* d_partial = nullptr;
     // luminosity surface (cached per radius)
     double lum_r = -1.0;
@@ -970,6 +971,150 @@ void set_last_error(const char* msg) { g_err = msg; }
 
 // ------------------------------------------------------------------ C ABI ---
 extern "C" {
+
+// ---- checkpoint / resume ---------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];                    // "FFECKPT1"
+    int64_t E, ndg, nfd, fd_cap, n_inst;
+    int64_t steps, id_kind, id_nprm_total;
+    double t;
+    unsigned long long units[3];
+    int64_t free_count;
+};
+
+size_t ckpt_size(const ffe_ctx* c) {
+    const Dev& d = c->d;
+    const size_t nprm = c->batch ? c->id_prm_inst.size() : c->id_prm.size();
+    size_t b = sizeof(CkptHeader) + nprm * sizeof(double) + NV * (size_t)(d.ndg + d.nfd) * sizeof(double) + d.E;
+    if (d.fd_slot) b += sizeof(int) * ((size_t)d.E + 2 * (size_t)d.fd_cap);
+    return b;
+}
+}  // namespace
+
+ffe_status ffe_save(ffe_ctx* c, void* host_buf, size_t* bytes) {
+    g_err.clear();
+    if (!c || !bytes) return fail(FFE_EINVAL, "null argument");
+    const Dev& d = c->d;
+    const size_t need = ckpt_size(c);
+    if (!host_buf) {
+        *bytes = need;
+        return FFE_OK;
+    }
+    if (*bytes < need) return fail(FFE_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", *bytes, need);
+    if (c->id_kind < 0) return fail(FFE_ESTATE, "no initial data set");
+    CkptHeader h{};
+    memcpy(h.magic, "FFECKPT1", 8);
+    h.E = d.E;
+    h.ndg = d.ndg;
+    h.nfd = d.nfd;
+    h.fd_cap = d.fd_slot ? d.fd_cap : 0;
+    h.n_inst = c->n_inst;
+    h.steps = c->steps;
+    h.t = c->t;
+    h.id_kind = c->id_kind;
+    const std::vector<double>& prm = c->batch ? c->id_prm_inst : c->id_prm;
+    h.id_nprm_total = (int64_t)prm.size();
+    char* p = (char*)host_buf;
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpy(h.units, d.units, sizeof h.units, cudaMemcpyDeviceToHost));
+    int fc = 0;
+    if (d.fd_slot) CK(cudaMemcpy(&fc, &d.counts[5], sizeof(int), cudaMemcpyDeviceToHost));
+    h.free_count = fc;
+    memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    if (!prm.empty()) memcpy(p, prm.data(), prm.size() * sizeof(double));
+    p += prm.size() * sizeof(double);
+    CK(cudaMemcpy(p, c->un.p, NV * (size_t)(d.ndg + d.nfd) * sizeof(double), cudaMemcpyDeviceToHost));
+    p += NV * (size_t)(d.ndg + d.nfd) * sizeof(double);
+    CK(cudaMemcpy(p, d.mask, d.E, cudaMemcpyDeviceToHost));
+    p += d.E;
+    if (d.fd_slot) {
+        CK(cudaMemcpy(p, d.fd_slot, sizeof(int) * d.E, cudaMemcpyDeviceToHost));
+        p += sizeof(int) * d.E;
+        CK(cudaMemcpy(p, d.slot_elem, sizeof(int) * d.fd_cap, cudaMemcpyDeviceToHost));
+        p += sizeof(int) * d.fd_cap;
+        CK(cudaMemcpy(p, d.free_slots, sizeof(int) * d.fd_cap, cudaMemcpyDeviceToHost));
+    }
+    *bytes = need;
+    return FFE_OK;
+}
+
+ffe_status ffe_load(ffe_ctx* c, const void* host_buf, size_t bytes) {
+    g_err.clear();
+    if (!c || !host_buf) return fail(FFE_EINVAL, "null argument");
+    Dev& d = c->d;
+    CkptHeader h;
+    if (bytes < sizeof h) return fail(FFE_EINVAL, "checkpoint of %zu bytes is truncated", bytes);
+    memcpy(&h, host_buf, sizeof h);
+    if (memcmp(h.magic, "FFECKPT1", 8) != 0) return fail(FFE_EINVAL, "not a checkpoint of this library");
+    if (h.E != d.E || h.ndg != d.ndg || h.nfd != d.nfd || h.fd_cap != (d.fd_slot ? d.fd_cap : 0) ||
+        h.n_inst != c->n_inst)
+        return fail(FFE_EINVAL, "checkpoint of a different mesh, order or FD pool");
+    if (h.id_kind < FFE_ID_FAST_WAVE || h.id_kind > FFE_ID_BREAKDOWN_1D || h.id_nprm_total < 0)
+        return fail(FFE_EINVAL, "corrupt checkpoint header");
+    const char* p = (const char*)host_buf + sizeof h;
+    std::vector<double> prm((size_t)h.id_nprm_total);
+    const size_t need = sizeof h + prm.size() * sizeof(double) + NV * (size_t)(d.ndg + d.nfd) * sizeof(double) + d.E +
+                        (d.fd_slot ? sizeof(int) * ((size_t)d.E + 2 * (size_t)d.fd_cap) : 0);
+    if (bytes < need) return fail(FFE_EINVAL, "checkpoint of %zu bytes, %zu expected", bytes, need);
+    if (!prm.empty()) memcpy(prm.data(), p, prm.size() * sizeof(double));
+    p += prm.size() * sizeof(double);
+    c->id_kind = (int)h.id_kind;
+    if (c->batch) {
+        c->id_prm_inst = prm;
+        c->id_nprm = c->n_inst > 0 ? (int)(prm.size() / c->n_inst) : 0;
+    } else {
+        c->id_prm = prm;
+    }
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpy(c->un.p, p, NV * (size_t)(d.ndg + d.nfd) * sizeof(double), cudaMemcpyHostToDevice));
+    p += NV * (size_t)(d.ndg + d.nfd) * sizeof(double);
+    CK(cudaMemcpy(d.mask, p, d.E, cudaMemcpyHostToDevice));
+    p += d.E;
+    if (d.fd_slot) {
+        std::vector<int> slot(d.E);
+        memcpy(slot.data(), p, sizeof(int) * d.E);
+        CK(cudaMemcpy(d.fd_slot, p, sizeof(int) * d.E, cudaMemcpyHostToDevice));
+        p += sizeof(int) * d.E;
+        CK(cudaMemcpy(d.slot_elem, p, sizeof(int) * d.fd_cap, cudaMemcpyHostToDevice));
+        p += sizeof(int) * d.fd_cap;
+        CK(cudaMemcpy(d.free_slots, p, sizeof(int) * d.fd_cap, cudaMemcpyHostToDevice));
+        const int fc = (int)h.free_count;
+        CK(cudaMemcpy(&d.counts[5], &fc, sizeof(int), cudaMemcpyHostToDevice));
+        c->h_fd_slot = slot;
+    }
+    CK(cudaMemcpy(d.units, h.units, sizeof h.units, cudaMemcpyHostToDevice));
+    c->t = h.t;
+    c->steps = h.steps;
+    return fill_dirichlet(c);
+}
+
+ffe_status ffe_constraints(ffe_ctx* c, const double* U_dev, double* out_host) {
+    g_err.clear();
+    if (!c || !out_host) return fail(FFE_EINVAL, "null argument");
+    const Dev& d = c->d;
+    if (d.ks) return fail(FFE_ENOTIMPL, "constraint diagnostics are built for the flat metric");
+    const int blocks = 152 * 4;
+    ffe_status s;
+    if (!c->d_cons && (s = dalloc(c, &c->d_cons, 4 * (size_t)blocks))) return s;
+    double* part = c->d_cons;
+    Field U{U_dev ? (double*)U_dev : c->un.p, NV, d.ndg, d.nfd};
+    launch_constraints(d, U, part, blocks, c->st);
+    std::vector<double> h(4 * (size_t)blocks);
+    CK(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    out_host[0] = 0.0;
+    out_host[1] = 1.0e308;
+    out_host[2] = out_host[3] = 0.0;
+    for (int b = 0; b < blocks; ++b) {
+        out_host[0] = fmax(out_host[0], h[4 * b]);
+        out_host[1] = fmin(out_host[1], h[4 * b + 1]);
+        out_host[2] = fmax(out_host[2], h[4 * b + 2]);
+        out_host[3] = fmax(out_host[3], h[4 * b + 3]);
+    }
+    return FFE_OK;
+}
 
 ffe_status ffe_get_coords(ffe_ctx* c, double* xyz_dg_dev, double* xyz_fd_dev) {
     g_err.clear();

@@ -523,4 +523,53 @@ void launch_tci_ratio(const Dev& d, const double* Udg, double* ratio, cudaStream
     g_launch_counter += 1;
 }
 
+// ---------------------------------------------------------------------------
+// Pointwise constraint diagnostics of a state (flat metric, densitised fields):
+// per block max |E~.B~|, min (B~^2 - E~^2), max |psi~|, max |phi~| over the DG
+// nodes of DG elements and the cells of FD elements.
+__device__ __forceinline__ void cons_point(const Field& U, bool fd, int64_t p, double* r) {
+    double u[8];
+    for (int v = 0; v < 8; ++v) u[v] = fd ? U.fd(v)[p] : U.dg(v)[p];
+    const double EB = fma(u[2], u[5], fma(u[1], u[4], u[0] * u[3]));
+    const double D = fma(u[5], u[5], fma(u[4], u[4], u[3] * u[3])) - fma(u[2], u[2], fma(u[1], u[1], u[0] * u[0]));
+    r[0] = fmax(r[0], fabs(EB));
+    r[1] = fmin(r[1], D);
+    r[2] = fmax(r[2], fabs(u[6]));
+    r[3] = fmax(r[3], fabs(u[7]));
+}
+
+__global__ void k_constraints(Dev d, Field U, double* part) {
+    __shared__ double sr[4][256];
+    double r[4] = {0.0, 1.0e308, 0.0, 0.0};
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = tid; p < d.ndg; p += stride) {
+        const int e = (int)(p / d.nn);
+        if (d.mask[e] == 0 && (int)(p % d.nn) < esz(d, e).nn) cons_point(U, false, p, r);
+    }
+    for (int64_t p = tid; p < d.nfd; p += stride) {
+        const int sl = (int)(p / d.ncell);
+        const int e = d.slot_elem ? d.slot_elem[sl] : sl;
+        if (e >= 0 && d.mask[e] == 1 && (int)(p % d.ncell) < esz(d, e).ncell) cons_point(U, true, p, r);
+    }
+    for (int i = 0; i < 4; ++i) sr[i][threadIdx.x] = r[i];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sr[0][threadIdx.x] = fmax(sr[0][threadIdx.x], sr[0][threadIdx.x + o]);
+            sr[1][threadIdx.x] = fmin(sr[1][threadIdx.x], sr[1][threadIdx.x + o]);
+            sr[2][threadIdx.x] = fmax(sr[2][threadIdx.x], sr[2][threadIdx.x + o]);
+            sr[3][threadIdx.x] = fmax(sr[3][threadIdx.x], sr[3][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) part[4 * blockIdx.x + i] = sr[i][0];
+}
+
+void launch_constraints(const Dev& d, Field U, double* part, int blocks, cudaStream_t st) {
+    k_constraints<<<blocks, 256, 0, st>>>(d, U, part);
+    g_launch_counter += 1;
+}
+
 }  // namespace ffe

@@ -195,18 +195,26 @@ __device__ __forceinline__ void reconstruct(const Dev& d, int wl, int k, int m, 
     c[t2] = tb + GH;
     const int64_t base = c[0] + (int64_t)ne * (c[1] + (int64_t)ne * c[2]);
     const int64_t stride = k == 0 ? 1 : (k == 1 ? ne : (int64_t)ne * ne);
-    for (int qq = 0; qq < NQ; ++qq) {
-        const double* src = ext_at(d, qq, wl) + base;
-        const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
-        const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
-        if (RECON == FFE_RECON_MP5) {
+    if constexpr (RECON == FFE_RECON_MP5) {
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) {
+            const double* src = ext_at(d, qq, wl) + base;
+            const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
+            const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
             UL[qq] = mp5(v0, v1, v2, v3, v4);
             UR[qq] = mp5(v5, v4, v3, v2, v1);
-        } else {
-            weno5z_pair(v0, v1, v2, v3, v4, v5, d.weno_eps, UL[qq], UR[qq]);
+            Um[qq] = v2;
+            Up[qq] = v3;
         }
-        Um[qq] = v2;
-        Up[qq] = v3;
+    } else {
+        for (int qq = 0; qq < NQ; ++qq) {
+            const double* src = ext_at(d, qq, wl) + base;
+            const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
+            const double v3 = src[3 * stride], v4 = src[4 * stride], v5 = src[5 * stride];
+            weno5z_pair(v0, v1, v2, v3, v4, v5, d.weno_eps, UL[qq], UR[qq]);
+            Um[qq] = v2;
+            Up[qq] = v3;
+        }
     }
 }
 

@@ -27,7 +27,8 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
            "ffe_near_threshold", "ffe_launch_count", "ffe_set_profiling", "ffe_profile_read",
            "ffe_fd_rhs_noalloc", "ffe_create_batch", "ffe_get_layout", "ffe_set_initial_batch",
            "ffe_rhs_vjp", "ffe_adjoint_step", "ffe_luminosity", "ffe_initial_tangent",
-           "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_get_coords", "ffe_eval_recip",
+           "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_save", "ffe_load",
+           "ffe_constraints", "ffe_get_coords", "ffe_eval_recip",
            "ffe_last_error",
            "ffe_destroy"]
 
@@ -105,6 +106,9 @@ def load():
         "ffe_initial_tangent": [P, i, P],
         "ffe_eval_recip": [P, P, ctypes.c_int64, P],
         "ffe_get_coords": [P, P, P],
+        "ffe_save": [P, P, ctypes.POINTER(ctypes.c_size_t)],
+        "ffe_load": [P, P, ctypes.c_size_t],
+        "ffe_constraints": [P, P, ctypes.POINTER(d)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -295,6 +299,25 @@ class Context:
         return json.loads(buf.value.decode())
 
     # layout helpers: state vector <-> (9, E, ...) blocks
+    def save(self):
+        """Checkpoint of the context (bytes; see ffe_save in include/ffe.h)."""
+        n = ctypes.c_size_t(0)
+        check(load().ffe_save(self.h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        check(load().ffe_save(self.h, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def load_checkpoint(self, blob):
+        """Restore a checkpoint made by save() on a context of the same mesh."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        check(load().ffe_load(self.h, buf, len(blob)))
+
+    def constraints(self, U=None):
+        """(max |E.B|, min (B^2 - E^2), max |psi|, max |phi|) of U (default: the state)."""
+        out = (ctypes.c_double * 4)()
+        check(load().ffe_constraints(self.h, ctypes.c_void_p(U.data_ptr()) if U is not None else None, out))
+        return tuple(out)
+
     def coords(self):
         """(xyz_dg [3][n_dg], xyz_fd [3][n_fd]) float64 CUDA tensors: DG node and
         FD subcell-centre coordinates in state-vector order."""
