@@ -46,17 +46,17 @@ def test_resume_from_checkpoint_is_exact(ffe):
 
 
 def test_resume_batch_with_fd_pool(ffe):
-    """A batched context with an FD slot pool: the pool (slots, free list) is
-    part of the checkpoint."""
+    """A batched context (its FD slots come from a pool, one slot per element
+    by default): the slot map and free list are part of the checkpoint."""
     cfgs = [W.pulsar(r_lc=3.0, chi=0.4, n_ang=1, n_rad=4, P=5, r_out=4.0),
             W.pulsar(r_lc=3.5, chi=0.2, n_ang=1, n_rad=6, P=4, r_out=6.0)]
-    a = ffe.BatchContext(cfgs, fd_capacity=40)
+    a = ffe.BatchContext(cfgs)
     a.set_initial()
     a.step(3)
     blob = a.save()
     a.step(3)
     Ua, ma = a.download()
-    b = ffe.BatchContext(cfgs, fd_capacity=40)
+    b = ffe.BatchContext(cfgs)
     b.set_initial()
     b.load_checkpoint(blob)
     b.step(3)
