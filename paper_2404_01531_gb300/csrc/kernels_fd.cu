@@ -196,7 +196,6 @@ __device__ __forceinline__ void reconstruct(const Dev& d, int wl, int k, int m, 
     const int64_t base = c[0] + (int64_t)ne * (c[1] + (int64_t)ne * c[2]);
     const int64_t stride = k == 0 ? 1 : (k == 1 ? ne : (int64_t)ne * ne);
     if constexpr (RECON == FFE_RECON_MP5) {
-#pragma unroll
         for (int qq = 0; qq < NQ; ++qq) {
             const double* src = ext_at(d, qq, wl) + base;
             const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride];
