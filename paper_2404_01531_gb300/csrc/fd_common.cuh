@@ -142,13 +142,13 @@ __device__ __forceinline__ void weno5z_pair(double v0, double v1, double v2, dou
     const double eL0 = fma(2.0, d12, a012), eL1 = d12 + d23, eL2 = fma(-2.0, d23, a234);
     const double eR0 = fma(-2.0, d34, a345), eR1 = d23 + d34, eR2 = fma(2.0, d23, a123);
     const double c = 13.0 / 3.0, eps4 = 4.0 * eps;
-    const double k123 = (c * a123) * a123, k234 = (c * a234) * a234;
+    const double c123 = c * a123, c234 = c * a234;
     const double bL0 = fma(c * a012, a012, fma(eL0, eL0, eps4));
-    const double bL1 = k123 + fma(eL1, eL1, eps4);
-    const double bL2 = k234 + fma(eL2, eL2, eps4);
+    const double bL1 = fma(c123, a123, fma(eL1, eL1, eps4));
+    const double bL2 = fma(c234, a234, fma(eL2, eL2, eps4));
     const double bR0 = fma(c * a345, a345, fma(eR0, eR0, eps4));
-    const double bR1 = k234 + fma(eR1, eR1, eps4);
-    const double bR2 = k123 + fma(eR2, eR2, eps4);
+    const double bR1 = fma(c234, a234, fma(eR1, eR1, eps4));
+    const double bR2 = fma(c123, a123, fma(eR2, eR2, eps4));
     uL = weno5z_combine(bL0, bL1, bL2, pL0, p123, p234);
     uR = weno5z_combine(bR0, bR1, bR2, pR0, p234, p123);
 }
