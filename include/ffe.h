@@ -252,9 +252,11 @@ ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host, double et
  * discrete decision frozen as the forward pass took it (piecewise
  * differentiability): the DG/FD mask (which must be frozen, ffe_freeze_mask:
  * FFE_ESTATE otherwise), the rectifier max(E^2-B^2,0), the stiff-solve branch
- * and the sign of S.n at a no-incoming-Poynting face.  WENO5-Z weights are
+ * and the sign of S.n at a no-incoming-Poynting face, and in the HARD modes
+ * the clamp's branch (E^2 > B^2 after the projection).  WENO5-Z weights are
  * differentiated (they are smooth).  Flat-metric shells (FFE_DOMAIN_SHELL6),
- * RELAX constraint mode.  All buffers are device state vectors; lambda and the
+ * every constraint mode, WENO5-Z reconstruction (FFE_ENOTIMPL for MP5, the
+ * Kerr-Schild metric and batches).  All buffers are device state vectors; lambda and the
  * outputs live on the representation each element uses (DG nodes of DG
  * elements, cells of FD elements) and are zero on the other one. */
 
@@ -283,7 +285,9 @@ ffe_status ffe_adjoint_step(ffe_ctx* ctx, const double* U_dev, const double* lam
  * [U4] (T_s the filtered explicit part of stage s), and when U_next_dev is not
  * NULL it receives u_{n+1} (must not alias U_dev).
  * ffe_adjoint_reverse runs the backward sweep from those stages: same result
- * as ffe_adjoint_step(U_dev, lam_in, lam_out, omega_bar). */
+ * as ffe_adjoint_step(U_dev, lam_in, lam_out, omega_bar).  In the HARD modes
+ * the clamp at the step's end needs the pre-clamp state, which the stages do
+ * not hold, so the reverse recomputes the step (as ffe_adjoint_step does). */
 ffe_status ffe_adjoint_forward(ffe_ctx* ctx, const double* U_dev, double* stages_dev, double* U_next_dev);
 ffe_status ffe_adjoint_reverse(ffe_ctx* ctx, const double* U_dev, const double* stages_dev, const double* lam_in_dev,
                                double* lam_out_dev, double* omega_bar);

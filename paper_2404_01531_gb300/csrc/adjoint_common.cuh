@@ -115,6 +115,43 @@ __device__ __forceinline__ void solve_vjp(const double* R, const Dev& d, double 
     }
 }
 
+// Reverse mode of the algebraic clamp Y = hard_clamp(X) (Sec. II.B, HARD
+// modes): E1 = E - (E.B/B^2) B, then E1 |B|/|E1| where |E1| > |B|; B, psi,
+// phi, q pass through.  Ub holds Y-bar on entry and X-bar on return; the
+// branch is the one the forward clamp took at X.
+__device__ __forceinline__ void clamp_vjp(const double* X, double* Ub) {
+    const double* E = X;
+    const double* B = X + 3;
+    const double B2 = dot3(B, B);
+    if (B2 == 0.0) {   // the forward set E to zero
+        Ub[0] = Ub[1] = Ub[2] = 0.0;
+        return;
+    }
+    const double ib2 = 1.0 / B2;
+    const double f = dot3(E, B) * ib2;
+    double E1[3], e1b[3];
+    for (int a = 0; a < 3; ++a) E1[a] = fma(-f, B[a], E[a]);
+    const double E12 = dot3(E1, E1);
+    const double eb[3] = {Ub[0], Ub[1], Ub[2]};
+    if (E12 > B2) {
+        // Y = s E1, s = |B|/|E1|: E1-bar = s (eb - (eb.E1) E1/|E1|^2), B-bar += (eb.E1) s B/B^2
+        const double s = sqrt(B2 / E12), ebE1 = dot3(eb, E1);
+        for (int a = 0; a < 3; ++a) {
+            e1b[a] = s * (eb[a] - ebE1 / E12 * E1[a]);
+            Ub[3 + a] += ebE1 * s * ib2 * B[a];
+        }
+    } else {
+        for (int a = 0; a < 3; ++a) e1b[a] = eb[a];
+    }
+    // E1 = E - f B, f = E.B/B^2: E-bar = e1b - (e1b.B) B/B^2,
+    // B-bar += -f e1b - (e1b.B)/B^2 (E - 2 f B)
+    const double g = dot3(e1b, B) * ib2;
+    for (int a = 0; a < 3; ++a) {
+        Ub[a] = fma(-g, B[a], e1b[a]);
+        Ub[3 + a] += -f * e1b[a] - g * fma(-2.0 * f, B[a], E[a]);
+    }
+}
+
 // Ub += (dG/dU)^T Gb, G = (-J~_eta, -kpsi psi, -kphi phi)
 __device__ __forceinline__ void G_vjp(const double* U, const Dev& d, const double* Gb, double* Ub) {
     const double zero[3] = {0.0, 0.0, 0.0};

@@ -179,6 +179,8 @@ void launch_rhs_vjp(const Dev& d, Field U, Field L, Field out, double* omega_bar
 void launch_filter(const Dev& d, Field in, Field out, int nv, int transpose, cudaStream_t st);
 void launch_adj(const Dev& d, int which, AdjArgs a, int sub, cudaStream_t st);
 void launch_adj_addG(const Dev& d, Field U, Field Gb, Field io, cudaStream_t st);
+void launch_adj_clamp(const Dev& d, Field io, cudaStream_t st);
+void launch_adj_clamp_back(const Dev& d, Field X, Field yb, Field out, cudaStream_t st);
 void launch_luminosity(const Dev& d, Field U, const int* elem, const double* lk, const double* wn, int ns,
                        double* partial, int nblocks, Field grad, double scale, cudaStream_t st);
 

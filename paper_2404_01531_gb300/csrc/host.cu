@@ -1606,7 +1606,6 @@ ffe_status ffe_freeze_mask(ffe_ctx* c, int on) {
 static ffe_status adjoint_ready(ffe_ctx* c) {
     const Dev& d = c->d;
     if (!d.curved || d.ks || c->batch) return fail(FFE_ENOTIMPL, "the adjoint is built for flat-metric shells");
-    if (d.mode == FFE_HARD || d.mode == FFE_RELAX_THEN_HARD) return fail(FFE_ENOTIMPL, "the adjoint of the clamp is not built");
     if (d.recon != FFE_RECON_WENO5Z) return fail(FFE_ENOTIMPL, "the adjoint is built for WENO5-Z reconstruction");
     if (d.tci_on) return fail(FFE_ESTATE, "the adjoint differentiates a fixed mask: freeze it first (ffe_freeze_mask)");
     std::vector<unsigned char> m(d.E);
@@ -1707,6 +1706,7 @@ static ffe_status adj_forward(ffe_ctx* c, AdjArgs& a, const Field* next) {
     if (next) {
         launch_adj(d, 1, a, SUB_C, st);
         if ((s = filter_or_copy(c, a.W, *next, 0))) return s;
+        if (d.mode != FFE_RELAX) launch_adj_clamp(d, *next, st);
     }
     return FFE_OK;
 }
@@ -1717,7 +1717,15 @@ static ffe_status adj_reverse(ffe_ctx* c, AdjArgs& a, Field lin, double* omega_b
     cudaStream_t st = c->st;
     ffe_status s;
     CK(cudaMemsetAsync(c->d_omega_bar, 0, sizeof(double), st));
-    if ((s = filter_or_copy(c, lin, a.tmp, 1))) return s;               // W-bar (u_{n+1} = filter(W))
+    if (d.mode != FFE_RELAX) {
+        // u_{n+1} = clamp(X), X = filter(W): back through the clamp at X
+        launch_adj(d, 1, a, SUB_C, st);                                 // W
+        if ((s = filter_or_copy(c, a.W, a.tmp2, 0))) return s;          // X
+        launch_adj_clamp_back(d, a.tmp2, lin, a.ubar, st);              // X-bar (ubar is free until the seeds)
+        if ((s = filter_or_copy(c, a.ubar, a.tmp, 1))) return s;        // W-bar
+    } else if ((s = filter_or_copy(c, lin, a.tmp, 1))) {                // W-bar (u_{n+1} = filter(W))
+        return s;
+    }
     launch_adj(d, 2, a, 0, st);                                         // seeds
     rhs_vjp_at(c, a.U4, a.F4b, a.tmp);                                  // U4-bar from F4
     launch_adj_addG(d, a.U4, a.G4b, a.tmp, st);                         // + G4 = G(U4)
@@ -1792,8 +1800,15 @@ ffe_status ffe_adjoint_reverse(ffe_ctx* c, const double* U_dev, const double* st
     AdjArgs a = c->adj;
     a.un = Field{(double*)U_dev, NV, d.ndg, d.nfd};
     a.lam = Field{lam_out_dev, NV, d.ndg, d.nfd};
-    point_stages(d, a, (double*)stages_dev);
     launch_build_lists(d, c->st);
+    if (d.mode != FFE_RELAX) {
+        // the clamp at the step's end needs the pre-clamp state, built from the
+        // step's right-hand sides, which the stored stages do not hold: recompute
+        // the step in the context's own stage fields (the stored ones stay untouched)
+        if ((s = adj_forward(c, a, nullptr))) return s;
+    } else {
+        point_stages(d, a, (double*)stages_dev);
+    }
     return adj_reverse(c, a, Field{(double*)lam_in_dev, NV, d.ndg, d.nfd}, omega_bar);
 }
 

@@ -345,6 +345,7 @@ __global__ void k_adj_s12(Dev d, AdjArgs a) {
         double u[NV], U1[NV], g1[NG], g2[NG];
         for (int v = 0; v < NV; ++v) { u[v] = fp(a.un, v, isfd)[q]; U1[v] = u[v]; }
         stiff_solve_flat(U1, d, dta);
+        if (d.mode != FFE_RELAX) hard_clamp_flat(U1);
         implicit_G_flat(U1, d, g1);
         u[0] = fma(-dta, g1[0], u[0]);
         u[1] = fma(-dta, g1[1], u[1]);
@@ -352,6 +353,7 @@ __global__ void k_adj_s12(Dev d, AdjArgs a) {
         u[6] = fma(-dta, g1[3], u[6]);
         u[7] = fma(-dta, g1[4], u[7]);
         stiff_solve_flat(u, d, dta);
+        if (d.mode != FFE_RELAX) hard_clamp_flat(u);
         implicit_G_flat(u, d, g2);
         for (int v = 0; v < NV; ++v) fp(a.U2, v, isfd)[q] = u[v];
         for (int c = 0; c < NG; ++c) { fp(a.G1, c, isfd)[q] = g1[c]; fp(a.G2, c, isfd)[q] = g2[c]; }
@@ -402,6 +404,7 @@ __global__ void k_adj_solve(Dev d, AdjArgs a, int sub) {
         double u[NV], g[NG];
         for (int v = 0; v < NV; ++v) u[v] = fp(Tt, v, isfd)[q];
         stiff_solve_flat(u, d, dta);
+        if (d.mode != FFE_RELAX) hard_clamp_flat(u);
         implicit_G_flat(u, d, g);
         for (int v = 0; v < NV; ++v) fp(Us, v, isfd)[q] = u[v];
         for (int c = 0; c < NG; ++c) fp(Gs, c, isfd)[q] = g[c];
@@ -461,6 +464,13 @@ __global__ void k_adj_solve_back(Dev d, AdjArgs a, int sub) {
         if (!act_listed(d, p, isfd, q)) continue;
         double t[NV], ub[NV], tb[NV];
         for (int v = 0; v < NV; ++v) { t[v] = fp(Tt, v, isfd)[q]; ub[v] = fp(a.tmp, v, isfd)[q]; }
+        if (d.mode != FFE_RELAX) {
+            // U_s = clamp(S(T_s)): back through the clamp at S(T_s) first
+            double x[NV];
+            for (int v = 0; v < NV; ++v) x[v] = t[v];
+            stiff_solve_flat(x, d, dta);
+            clamp_vjp(x, ub);
+        }
         solve_vjp(t, d, dta, ub, tb);
         for (int v = 0; v < NV; ++v) fp(a.tmp2, v, isfd)[q] = tb[v];
     }
@@ -509,8 +519,12 @@ __global__ void k_adj_back_s12(Dev d, AdjArgs a) {
             continue;
         }
         double un[NV], U1[NV], R2[NV], g1[NG], u2b[NV], r2b[NV], g1b[NG], u1b[NV], r1b[NV];
+        const bool clamp = d.mode != FFE_RELAX;
+        double V1[NV], V2[NV];   // the solve outputs before the clamp (HARD modes)
         for (int v = 0; v < NV; ++v) { un[v] = fp(a.un, v, isfd)[q]; U1[v] = un[v]; u2b[v] = fp(a.tmp, v, isfd)[q]; }
         stiff_solve_flat(U1, d, dta);
+        for (int v = 0; v < NV; ++v) V1[v] = U1[v];
+        if (clamp) hard_clamp_flat(U1);
         implicit_G_flat(U1, d, g1);
         for (int v = 0; v < NV; ++v) R2[v] = un[v];
         R2[0] = fma(-dta, g1[0], R2[0]);
@@ -518,14 +532,63 @@ __global__ void k_adj_back_s12(Dev d, AdjArgs a) {
         R2[2] = fma(-dta, g1[2], R2[2]);
         R2[6] = fma(-dta, g1[3], R2[6]);
         R2[7] = fma(-dta, g1[4], R2[7]);
+        if (clamp) {
+            for (int v = 0; v < NV; ++v) V2[v] = R2[v];
+            stiff_solve_flat(V2, d, dta);
+            clamp_vjp(V2, u2b);
+        }
         solve_vjp(R2, d, dta, u2b, r2b);
         const int gv[NG] = {0, 1, 2, 6, 7};
         for (int c = 0; c < NG; ++c) g1b[c] = fp(a.G1b, c, isfd)[q] - dta * r2b[gv[c]];
         for (int v = 0; v < NV; ++v) u1b[v] = 0.0;
         G_vjp(U1, d, g1b, u1b);
+        if (clamp) clamp_vjp(V1, u1b);
         solve_vjp(un, d, dta, u1b, r1b);
         for (int v = 0; v < NV; ++v) fp(a.lam, v, isfd)[q] = fp(a.ubar, v, isfd)[q] + r2b[v] + r1b[v];
     }
+}
+
+// HARD modes, the step's end: u_{n+1} = clamp(X), X = filter(W).
+// (7) in place: io = clamp(io)
+__global__ void k_adj_clamp(Dev d, Field io) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_listed(d, p, isfd, q)) continue;
+        double u[NV];
+        for (int v = 0; v < NV; ++v) u[v] = fp(io, v, isfd)[q];
+        hard_clamp_flat(u);
+        for (int v = 0; v < 3; ++v) fp(io, v, isfd)[q] = u[v];
+    }
+}
+
+// (8) out = (d clamp/dX at X)^T yb
+__global__ void k_adj_clamp_back(Dev d, Field X, Field yb, Field out) {
+    const int64_t np_ = act_count(d);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np_; p += (int64_t)gridDim.x * blockDim.x) {
+        bool isfd;
+        int64_t q;
+        if (!act_listed(d, p, isfd, q)) continue;
+        double x[NV], ub[NV];
+        for (int v = 0; v < NV; ++v) { x[v] = fp(X, v, isfd)[q]; ub[v] = fp(yb, v, isfd)[q]; }
+        clamp_vjp(x, ub);
+        for (int v = 0; v < NV; ++v) fp(out, v, isfd)[q] = ub[v];
+    }
+}
+
+void launch_adj_clamp(const Dev& d, Field io, cudaStream_t st) {
+    prof_begin("adj_pointwise", st);
+    k_adj_clamp<<<152 * 8, 256, 0, st>>>(d, io);
+    prof_end(st);
+    g_launch_counter += 1;
+}
+
+void launch_adj_clamp_back(const Dev& d, Field X, Field yb, Field out, cudaStream_t st) {
+    prof_begin("adj_pointwise", st);
+    k_adj_clamp_back<<<152 * 8, 256, 0, st>>>(d, X, yb, out);
+    prof_end(st);
+    g_launch_counter += 1;
 }
 
 void launch_adj(const Dev& d, int which, AdjArgs a, int sub, cudaStream_t st) {

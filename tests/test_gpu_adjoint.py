@@ -310,3 +310,38 @@ def test_split_adjoint_matches_adjoint_step(ffe):
     U1 = ctx.state()[0]
     assert float(((nxt - U1) * act).abs().max()) <= 1e-10 * float((U1 * act).abs().max())
     ctx.close()
+
+
+@pytest.mark.parametrize("mode", [W.HARD, W.RELAX_THEN_HARD])
+def test_hard_mode_adjoint_step_matches_finite_differences(ffe, mode):
+    """The algebraic clamp (HARD: clamp only, eta off; RELAX_THEN_HARD: stiff
+    solve then clamp) in the hybrid step: adjoint step against extrapolated
+    central differences of the forward step, and the split forward/reverse
+    against the one-call adjoint step."""
+    cfg = _tiny(1e5)
+    cfg["params"]["constraint_mode"] = mode
+    ctx, mask = _hybrid(ffe, cfg=cfg)
+    U, act = _perturb(ctx, mask, 31)
+    lam, dlt = _dirs(U, act, 32)
+    out = torch.zeros_like(U)
+    ctx.adjoint_step(U, lam, out)
+    assert float(out[~act].abs().max()) == 0.0
+
+    def f(h):
+        ctx.set_state(U + h * dlt, mask)
+        ctx.step(1)
+        return ctx.state()[0].clone()
+    fd = _richardson(f, 1e-8, lam)
+    ad = float(torch.dot(out, dlt))
+    assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+    stages = torch.empty(5 * U.numel(), dtype=U.dtype, device=U.device)
+    nxt = torch.empty_like(U)
+    ctx.adjoint_forward(U, stages, nxt)
+    out2 = torch.zeros_like(U)
+    ctx.adjoint_reverse(U, stages, lam, out2)
+    assert float((out2 - out).abs().max()) <= 1e-12 * float(out.abs().max())
+    ctx.set_state(U, mask)
+    ctx.step(1)
+    U1 = ctx.state()[0]
+    assert float(((nxt - U1) * act).abs().max()) <= 1e-10 * float((U1 * act).abs().max())
+    ctx.close()
