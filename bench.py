@@ -31,7 +31,7 @@ UNIT = "element-node updates/s"
 # DRAM bytes (read + write) of k_fd_flux per FD element it processes, from an
 # ncu capture of the kernel (profiles/k_fd_flux_breakdown_8x8x8.md): a launch
 # moves this many bytes for each element of its chunk
-DRAM_BYTES_PER_FD_ELEMENT = {"fd_flux": 6.34e5}
+DRAM_BYTES_PER_FD_ELEMENT = {"fd_flux": 5.535e5}
 
 RECON = {"weno5z": 0, "mp5": 1}
 
