@@ -336,6 +336,35 @@ def split_measure(steps=20, warmup=3):
     return {"elements": E, "rows": rows, "f_all_dg": t_fd / rows[-1]["ms_per_step"], "f_fit_mixed": den / num}
 
 
+def run_dg_phases(args):
+    """Cost of the optional phases of the box DG substep kernel: the smooth fast
+    wave on 16^3 elements (all DG, nothing flagged), the kernel's average launch
+    time with the filter, the indicator and the driver current each switched
+    off through ffe_params (physics changed; timing only)."""
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rows = {}
+    for label, prm in (("all_on", {}), ("indicator_off", dict(tci_on=0)), ("filter_off", dict(filter_on=0)),
+                       ("eta_0", dict(eta=0.0)), ("all_off", dict(tci_on=0, filter_on=0, eta=0.0))):
+        cfg = W.fast_wave(n=16)
+        cfg["params"].update(prm)
+        ctx = ffe.Context(cfg)
+        ctx.set_initial()
+        ctx.step(max(args.warmup, 3))
+        torch.cuda.synchronize()
+        ctx.set_profiling(True)
+        ctx.step(6)
+        ctx.set_profiling(False)
+        p = ctx.profile_read()
+        rows[label] = p["dg_substep"][1] / p["dg_substep"][0]
+        ctx.close()
+    line = {"metric": "k_dg_substep average launch time", "value": rows["all_on"], "unit": "ms",
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fast wave, periodic 16^3 elements, P=5, all DG"}, "dg_substep_ms": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_oned(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -524,11 +553,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64,
                     help="elements along x (same width 4/64; smaller values for profiler captures)")
-    ap.add_argument("--workload", default="breakdown", choices=["breakdown", "pulsars", "adjoint", "shell", "oned"],
+    ap.add_argument("--workload", default="breakdown", choices=["breakdown", "pulsars", "adjoint", "shell", "oned", "dgphases"],
                     help="pulsars: the 32-shell batch, batched launch vs one context per instance; "
                          "adjoint: luminosity gradient of one neutron-star shell (--steps steps); "
                          "shell: that shell with three FD layers, frozen mask (curved FD kernels); "
-                         "oned: the paper's 1-D tests and its DG/FD split experiment")
+                         "oned: the paper's 1-D tests and its DG/FD split experiment; "
+                         "dgphases: cost of the DG kernel's filter, indicator and stiff-current phases")
     ap.add_argument("--no-adjoint", action="store_true", help="breakdown: skip the adjoint/forward timing")
     ap.add_argument("--recon", default="weno5z", choices=list(RECON),
                     help="breakdown and shell: FD reconstruction (the paper's WENO5-Z, or MP5)")
@@ -545,6 +575,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "oned":
         return run_oned(args)
+    if args.workload == "dgphases":
+        return run_dg_phases(args)
 
     import numpy as np
     import torch
