@@ -116,17 +116,17 @@ __device__ __forceinline__ double stiff_root(double c, double p2, double a2, dou
     const double K = c * p2 * ib2;
     double s = 0.0;
     if (K > 0.0) {
-        const double ta = sqrt(K * recip_any((c > 1.0 ? c - 1.0 : 0.0) + cbrt(K)));
+        const double ta = sqrt(K / ((c > 1.0 ? c - 1.0 : 0.0) + cbrt(K)));
         s = ta > 1.0 ? ta - 1.0 : 0.0;
     }
     double step = 1.0;
     for (int it = 0; it < 100; ++it) {
-        const double a1 = 1.0 + s, b1 = 1.0 + c + s, w = recip_any(a1 * b1);
+        const double a1 = 1.0 + s, b1 = 1.0 + c + s, w = 1.0 / (a1 * b1);
         const double u = b1 * w, v = a1 * w;
         const double pu = p2 * u * u, av = a2 * v * v;
         const double g = c * ((pu + av) - B2) * ib2 - s;
         const double dg = -2.0 * c * (pu * u + av * v) * ib2 - 1.0;
-        const double sn = fma(-g, recip_any(dg), s);
+        const double sn = s - g / dg;
         step = sn - s;
         if (!(sn > s)) break;
         s = sn;
