@@ -59,11 +59,13 @@ def test_rhs_kerr_schild_shell(ffe, P):
     assert _rhs_parity(ffe, cfg, st, pr) <= 1e-11
 
 
-def test_rhs_star_shell_mixed_dg_fd(ffe):
+@pytest.mark.parametrize("corr", [0, 1])
+def test_rhs_star_shell_mixed_dg_fd(ffe, corr):
     """Flat rotating-star shell, random data, random DG/FD mask: curved FD flux
-    and update, ghost fills across wedges, star and no-incoming-Poynting states."""
+    and update (with and without the corrector applied per physical flux
+    component), ghost fills across wedges, star and no-incoming-Poynting states."""
     cfg = W.pulsar(r_lc=3.0, n_ang=2, n_rad=3, P=5)
-    cfg["params"].update(eta=50.0)
+    cfg["params"].update(eta=50.0, fd_corrector=corr)
     pr = Problem(cfg)
     rng = np.random.default_rng(11)
     E = pr.disc.E
