@@ -115,6 +115,8 @@ struct Dev {
     unsigned char* mask;            // [E] 0 = DG, 1 = FD
     unsigned char* switched;        // [E] switched to FD during the current step
     int* dg_list; int* fd_list; int* flag_list; int* near_list;
+    int* dg_list_lo;   // batches: DG elements of order P-1 (count in counts[6]); null otherwise
+    int* dg_list_lo2;  // batches: DG elements of order P-2 (count in counts[7]); null otherwise
     int* counts;                    // [0] n_dg, [1] n_fd, [2] n_flag, [3] n_near, [4] status bits, [5] free slots
     unsigned long long* units;      // [0] node updates (DG nodes + FD cells per substep), [1] FD and [2] DG element updates
     // FD scratch per chunk of listed FD elements: extended cells [12][chunk][(nc+6)^3],

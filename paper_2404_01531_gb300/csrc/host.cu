@@ -863,6 +863,9 @@ ffe_status finish_create(ffe_ctx* c, int fd_cap, const std::vector<int>& orders)
         d.einst = ein;
         d.inst = dinst;
         (void)eP8;
+        // DG elements of the lower orders get their own work lists (own launches)
+        if ((s = dalloc(c, &d.dg_list_lo, d.E))) return s;
+        if ((s = dalloc(c, &d.dg_list_lo2, d.E))) return s;
         // FD slot pool: every slot free until ffe_set_initial assigns some
         if ((s = dalloc(c, &d.fd_slot, d.E))) return s;
         if ((s = dalloc(c, &d.slot_elem, fd_cap))) return s;

@@ -346,48 +346,49 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
 }
 
 
-// Persistent kernel over the DG work list; flat metric: two CTAs per SM
-// (registers bounded accordingly; the metric-aware variant keeps one).  MIXED: each item is dispatched on its element's order
-// (batched contexts mix P = 4 and P = 5 in one launch); otherwise every element
-// has order PMAX and only that path is compiled.
-template <int PMAX, int SUB, bool KS, bool MIXED>
-__global__ void __launch_bounds__(DGC<PMAX>::NT, KS ? 1 : 2) k_dg_curved(Dev d, SubArgs a) {
-    constexpr int NT = DGC<PMAX>::NT;
+// Persistent kernel over a DG work list of order-P elements (list, count in
+// d.counts[ci]); flat metric: two CTAs per SM (four for the 128-thread CTAs of
+// orders <= 4; registers bounded accordingly), the metric-aware variant one.
+// Batched contexts launch each order's elements separately, in CTAs sized for
+// that order (one kernel dispatching on the order would keep every order's
+// registers live and spill).
+template <int P, int SUB, bool KS>
+__global__ void __launch_bounds__(DGC<P>::NT, KS ? 1 : (DGC<P>::NT <= 128 ? 4 : 2))
+    k_dg_curved(Dev d, SubArgs a, const int* list, int ci) {
     extern __shared__ double sm[];
-    const int nwork = d.counts[0];
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-        const int e = d.dg_list[w];
-        const int P = MIXED ? elem_P(d, e) : PMAX;
-        if (P == PMAX) {
-            dg_curved_elem<PMAX, NT, SUB, KS>(d, a, e, sm);
-        } else if constexpr (MIXED && PMAX > 3) {
-            if (P == PMAX - 1) dg_curved_elem<PMAX - 1, NT, SUB, KS>(d, a, e, sm);
-            else if constexpr (PMAX > 4) {
-                if (P == PMAX - 2) dg_curved_elem<PMAX - 2, NT, SUB, KS>(d, a, e, sm);
-            }
-        }
+    const int nwork = d.counts[ci];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) dg_curved_elem<P, DGC<P>::NT, SUB, KS>(d, a, list[w], sm);
+}
+
+template <int P, bool KS, int SUB>
+static void curved_launch(const Dev& d, const SubArgs& a, const int* list, int ci, int grid, cudaStream_t st) {
+    using K = DGC<P>;
+    cudaFuncSetAttribute(k_dg_curved<P, SUB, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    k_dg_curved<P, SUB, KS><<<grid, K::NT, K::SMEM, st>>>(d, a, list, ci);
+    g_launch_counter += 1;
+}
+
+template <int P, bool KS, int SUB>
+static void curved_dispatch_sub(const Dev& d, const SubArgs& a, cudaStream_t st) {
+    const int grid = d.dg_grid > 0 ? d.dg_grid : 152 * 2;
+    curved_launch<P, KS, SUB>(d, a, d.dg_list, 0, grid, st);
+    // batches: the elements of orders P-1 and P-2, each in CTAs sized for their order
+    if constexpr (P > 3) {
+        if (d.dg_list_lo) curved_launch<P - 1, KS, SUB>(d, a, d.dg_list_lo, 6, 152 * 4, st);
+    }
+    if constexpr (P > 4) {
+        if (d.dg_list_lo2) curved_launch<P - 2, KS, SUB>(d, a, d.dg_list_lo2, 7, 152 * 4, st);
     }
 }
 
 template <int P, bool KS>
 static void curved_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_t st) {
-    using K = DGC<P>;
-    const int grid = d.dg_grid > 0 ? d.dg_grid : 152 * 2;
-#define FFE_LAUNCH_C(S)                                                                                      \
-    if (d.eP) {                                                                                              \
-        cudaFuncSetAttribute(k_dg_curved<P, S, KS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM); \
-        k_dg_curved<P, S, KS, true><<<grid, K::NT, K::SMEM, st>>>(d, a);                                     \
-    } else {                                                                                                 \
-        cudaFuncSetAttribute(k_dg_curved<P, S, KS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM); \
-        k_dg_curved<P, S, KS, false><<<grid, K::NT, K::SMEM, st>>>(d, a);                                    \
-    }
     switch (sub) {
-        case SUB_A: FFE_LAUNCH_C(SUB_A) break;
-        case SUB_B: FFE_LAUNCH_C(SUB_B) break;
-        case SUB_C: FFE_LAUNCH_C(SUB_C) break;
-        default: FFE_LAUNCH_C(SUB_RHS) break;
+        case SUB_A: curved_dispatch_sub<P, KS, SUB_A>(d, a, st); break;
+        case SUB_B: curved_dispatch_sub<P, KS, SUB_B>(d, a, st); break;
+        case SUB_C: curved_dispatch_sub<P, KS, SUB_C>(d, a, st); break;
+        default: curved_dispatch_sub<P, KS, SUB_RHS>(d, a, st); break;
     }
-#undef FFE_LAUNCH_C
 }
 
 void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field J, Field un, Field F2, Field F3, Field G1,
@@ -410,7 +411,6 @@ void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field J, Field u
         }
     }
     prof_end(st);
-    g_launch_counter += 1;
 }
 
 // Stages 1 and 2 at DG nodes with the Kerr-Schild metric (FD is flat-only).

@@ -37,12 +37,15 @@ struct DGK {
 __global__ void k_build_lists(Dev d) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= d.E) return;
-    if (d.mask[e] == 0) d.dg_list[atomicAdd(&d.counts[0], 1)] = e;
-    else d.fd_list[atomicAdd(&d.counts[1], 1)] = e;
+    if (d.mask[e] != 0) d.fd_list[atomicAdd(&d.counts[1], 1)] = e;
+    else if (!d.dg_list_lo || elem_P(d, e) == d.P) d.dg_list[atomicAdd(&d.counts[0], 1)] = e;
+    else if (elem_P(d, e) == d.P - 1) d.dg_list_lo[atomicAdd(&d.counts[6], 1)] = e;
+    else d.dg_list_lo2[atomicAdd(&d.counts[7], 1)] = e;
 }
 
 void launch_build_lists(const Dev& d, cudaStream_t st) {
     cudaMemsetAsync(d.counts, 0, 2 * sizeof(int), st);
+    if (d.dg_list_lo) cudaMemsetAsync(d.counts + 6, 0, 2 * sizeof(int), st);
     prof_begin("build_lists", st);
     k_build_lists<<<(d.E + 255) / 256, 256, 0, st>>>(d);
     prof_end(st);
