@@ -106,15 +106,69 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
             node_metric<KS>(d, eb + tid, m);
             for (int k = 0; k < 3; ++k)
                 for (int i = 0; i < 3; ++i) ij[k][i] = d.geo[(int64_t)(3 * k + i) * d.ndg + eb + tid];
-            double u[NV], F[3][NV];
+            double u[NV];
             for (int v = 0; v < NV; ++v) u[v] = sU[v * nn + tid];
-            fluxes_at<KS>(u, m, d.eta, F, jd);
-            for (int j = 0; j < 3; ++j)
-                for (int v = 0; v < NV; ++v) sF[(j * NV + v) * nn + tid] = F[j][v];
+            if (KS) {
+                double F[3][NV];
+                fluxes_at<KS>(u, m, d.eta, F, jd);
+                for (int j = 0; j < 3; ++j)
+                    for (int v = 0; v < NV; ++v) sF[(j * NV + v) * nn + tid] = F[j][v];
+            } else {
+                // flat metric: the fluxes are fixed linear combinations of E~, B~,
+                // psi~, phi~ and J~, so only J~ (full) is stored beside U
+                double jf[3];
+                current_flat(u, d.eta, jd, jf);
+                for (int i = 0; i < 3; ++i) sF[i * nn + tid] = jf[i];
+            }
         }
         __syncthreads();
         double du[NV];
-        if (act) {
+        if (act && !KS) {
+            // flat metric: D_k F^j = +-D_k of one field (D_k is linear), so the
+            // volume term is built from the reference derivatives R = D_k X of the
+            // 11 fields X = E~, B~, psi~, phi~, J~ and the node's d xi^k/d x^j:
+            //   E~: curl B~ - grad psi~,  B~: -curl E~ - grad phi~,
+            //   psi~: -div E~,  phi~: -div B~,  q~: -div J~
+            for (int v = 0; v < NV; ++v) du[v] = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
+                const int base = tid - ci[k] * stride;
+                double Dk[np1];
+                for (int mm = 0; mm < np1; ++mm) Dk[mm] = T.D[ci[k]][mm];
+                auto R = [&](const double* f) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int mm = 0; mm < np1; ++mm) acc = fma(Dk[mm], f[base + mm * stride], acc);
+                    return acc;
+                };
+                const double ka = ij[k][0], kb = ij[k][1], kc = ij[k][2];
+                double r;
+                r = R(sU + 0 * nn);   // E0
+                du[4] = fma(-kc, r, du[4]); du[5] = fma(kb, r, du[5]); du[6] = fma(-ka, r, du[6]);
+                r = R(sU + 1 * nn);   // E1
+                du[3] = fma(kc, r, du[3]); du[5] = fma(-ka, r, du[5]); du[6] = fma(-kb, r, du[6]);
+                r = R(sU + 2 * nn);   // E2
+                du[3] = fma(-kb, r, du[3]); du[4] = fma(ka, r, du[4]); du[6] = fma(-kc, r, du[6]);
+                r = R(sU + 3 * nn);   // B0
+                du[1] = fma(kc, r, du[1]); du[2] = fma(-kb, r, du[2]); du[7] = fma(-ka, r, du[7]);
+                r = R(sU + 4 * nn);   // B1
+                du[0] = fma(-kc, r, du[0]); du[2] = fma(ka, r, du[2]); du[7] = fma(-kb, r, du[7]);
+                r = R(sU + 5 * nn);   // B2
+                du[0] = fma(kb, r, du[0]); du[1] = fma(-ka, r, du[1]); du[7] = fma(-kc, r, du[7]);
+                r = R(sU + 6 * nn);   // psi
+                du[0] = fma(-ka, r, du[0]); du[1] = fma(-kb, r, du[1]); du[2] = fma(-kc, r, du[2]);
+                r = R(sU + 7 * nn);   // phi
+                du[3] = fma(-ka, r, du[3]); du[4] = fma(-kb, r, du[4]); du[5] = fma(-kc, r, du[5]);
+                r = R(sF + 0 * nn);   // J0
+                du[8] = fma(-ka, r, du[8]);
+                r = R(sF + 1 * nn);   // J1
+                du[8] = fma(-kb, r, du[8]);
+                r = R(sF + 2 * nn);   // J2
+                du[8] = fma(-kc, r, du[8]);
+            }
+        }
+        if (act && KS) {
             for (int v = 0; v < NV; ++v) du[v] = 0.0;
             for (int k = 0; k < 3; ++k) {
                 const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
@@ -132,6 +186,8 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                     }
                 }
             }
+        }
+        if (act) {
             double u[NV], S[NV];
             for (int v = 0; v < NV; ++v) u[v] = sU[v * nn + tid];
             if (KS) {
@@ -215,10 +271,22 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
             else fluxes_at<KS>(Ue, mf, d.eta, Fe, jde);
             const double lam = mf.a + fabs(d3(mf.b, nl));
             const double sc = 0.5 * norm * w0inv;
-            for (int v = 0; v < NV; ++v) {
-                double dfn = 0.0;
-                for (int j = 0; j < 3; ++j) dfn = fma(nl[j], Fe[j][v] - sF[(j * NV + v) * nn + me], dfn);
-                sC[(f * NV + v) * nf + ab] = sc * fma(-lam, Ue[v] - Ui[v], dfn);
+            if (KS) {
+                for (int v = 0; v < NV; ++v) {
+                    double dfn = 0.0;
+                    for (int j = 0; j < 3; ++j) dfn = fma(nl[j], Fe[j][v] - sF[(j * NV + v) * nn + me], dfn);
+                    sC[(f * NV + v) * nf + ab] = sc * fma(-lam, Ue[v] - Ui[v], dfn);
+                }
+            } else {
+                // interior flux from the node's state and its stored current J~
+                double Fi[3][NV];
+                const double Ji[3] = {sF[me], sF[nn + me], sF[2 * nn + me]};
+                flux_gen(Ui, Ji, mf, Fi);
+                for (int v = 0; v < NV; ++v) {
+                    double dfn = 0.0;
+                    for (int j = 0; j < 3; ++j) dfn = fma(nl[j], Fe[j][v] - Fi[j][v], dfn);
+                    sC[(f * NV + v) * nf + ab] = sc * fma(-lam, Ue[v] - Ui[v], dfn);
+                }
             }
         }
         __syncthreads();
