@@ -266,26 +266,31 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                     bc_star_flat(Ui, xn, omega_of(d, e), Ue);
                 }
             }
-            double Fe[3][NV], jde[3];
-            if (jx) flux_gen(Ue, Je, mf, Fe);
-            else fluxes_at<KS>(Ue, mf, d.eta, Fe, jde);
             const double lam = mf.a + fabs(d3(mf.b, nl));
             const double sc = 0.5 * norm * w0inv;
             if (KS) {
+                double Fe[3][NV], jde[3];
+                if (jx) flux_gen(Ue, Je, mf, Fe);
+                else fluxes_at<KS>(Ue, mf, d.eta, Fe, jde);
                 for (int v = 0; v < NV; ++v) {
                     double dfn = 0.0;
                     for (int j = 0; j < 3; ++j) dfn = fma(nl[j], Fe[j][v] - sF[(j * NV + v) * nn + me], dfn);
                     sC[(f * NV + v) * nf + ab] = sc * fma(-lam, Ue[v] - Ui[v], dfn);
                 }
             } else {
-                // interior flux from the node's state and its stored current J~
-                double Fi[3][NV];
-                const double Ji[3] = {sF[me], sF[nn + me], sF[2 * nn + me]};
-                flux_gen(Ui, Ji, mf, Fi);
+                // the flat flux is linear in (U, J~): F(Ue) - F(Ui) = F(Ue - Ui, Je - Ji),
+                // Ji the node's stored current, Je the exterior one
+                if (!jx) {
+                    double jde[3];
+                    current_flat(Ue, d.eta, jde, Je);
+                }
+                double dUv[NV], dJv[3], Fd[3][NV];
+                for (int v = 0; v < NV; ++v) dUv[v] = Ue[v] - Ui[v];
+                for (int i = 0; i < 3; ++i) dJv[i] = Je[i] - sF[i * nn + me];
+                flux_gen(dUv, dJv, mf, Fd);
                 for (int v = 0; v < NV; ++v) {
-                    double dfn = 0.0;
-                    for (int j = 0; j < 3; ++j) dfn = fma(nl[j], Fe[j][v] - Fi[j][v], dfn);
-                    sC[(f * NV + v) * nf + ab] = sc * fma(-lam, Ue[v] - Ui[v], dfn);
+                    const double dfn = fma(nl[2], Fd[2][v], fma(nl[1], Fd[1][v], nl[0] * Fd[0][v]));
+                    sC[(f * NV + v) * nf + ab] = sc * fma(-lam, dUv[v], dfn);
                 }
             }
         }
