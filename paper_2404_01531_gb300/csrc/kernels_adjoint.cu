@@ -8,7 +8,7 @@
 //   solve_vjp       U = R + dt a G(U) (Sec. III.B): analytic branch and the
 //                   scalar root s of the nonlinear branch by implicit differentiation
 //   k_rhs_vjp       lambda^T dF/dU of the DG right-hand side: transposed
-//                   derivative contractions, flux Jacobians, sources, the lifted
+//                   derivative contractions of the 11 field weights, sources, the lifted
 //                   Rusanov terms of my faces and of my neighbours' faces, the
 //                   star / no-incoming boundary states, and d/d Omega at the star
 //   k_filter_t      transpose of the exponential filter
@@ -24,8 +24,8 @@ namespace ffe {
 template <int P>
 struct AVJ {
     static constexpr int np1 = P + 1, nn = np1 * np1 * np1, nf = np1 * np1, NT = ((nn + 31) / 32) * 32;
-    // shared doubles: lambda [9][nn] | Y [27][nn] | C [6][9][nf]
-    static constexpr int SMEM = (9 * nn + 27 * nn + 54 * nf) * 8;
+    // shared doubles: lambda [9][nn] | Y [11][nn] | C [6][9][nf]
+    static constexpr int SMEM = (9 * nn + 11 * nn + 54 * nf) * 8;
 };
 
 __device__ __forceinline__ void unit_normal(const Dev& d, int64_t p, int dd, int s, double* n, double& norm) {
@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(AVJ<P>::NT) k_rhs_vjp(Dev d, Field U, Field L,
     constexpr int np1 = K::np1, nn = K::nn, nf = K::nf, NT = K::NT;
     extern __shared__ double sm[];
     double* sL = sm;              // [9][nn]
-    double* sY = sL + 9 * nn;     // [27][nn]
-    double* sC = sY + 27 * nn;    // [6][9][nf]
+    double* sY = sL + 9 * nn;     // [11][nn]
+    double* sC = sY + 11 * nn;    // [6][9][nf]
     __shared__ double s_om[NT];
     const Tables& T = d.tabs[P];
     const int tid = threadIdx.x;
@@ -74,44 +74,60 @@ __global__ void __launch_bounds__(AVJ<P>::NT) k_rhs_vjp(Dev d, Field U, Field L,
         const double om = omega_of(d, e);
         double om_acc = 0.0;
         for (int t = tid; t < NV * nn; t += NT) sL[t] = L.dg(t / nn)[eb + t % nn];
-        double lam[NV], u[NV], ij[3][3], mu[3][NV];
+        double lam[NV], u[NV], ij[3][3];
         if (act) {
             for (int v = 0; v < NV; ++v) { lam[v] = L.dg(v)[eb + tid]; u[v] = U.dg(v)[eb + tid]; }
             for (int k = 0; k < 3; ++k)
                 for (int i = 0; i < 3; ++i) ij[k][i] = d.geo[(int64_t)(3 * k + i) * d.ndg + eb + tid];
         }
-        for (int j = 0; j < 3; ++j)
-            for (int v = 0; v < NV; ++v) mu[j][v] = 0.0;
-        // volume: mu^j_m = sum_k sum_n D_k[n][m] ij_n[k][j] lambda_n  (transposed contraction)
+        // volume (flat metric): the forward builds curl, gradient and divergence
+        // from the reference derivatives D_k X of the 11 fields X = E~, B~, psi~,
+        // phi~, J~; its transpose gathers per axis k the weights Y_k,X(n) that
+        // multiply D_k X at node n (lambda and the node's d xi^k/d x^j) and
+        // contracts them with D_k^T:  Xbar(m) = sum_k sum_n D_k[n][m] Y_k,X(n)
+        double xb[11];
+        for (int w = 0; w < 11; ++w) xb[w] = 0.0;
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
             __syncthreads();
-            if (act)
-                for (int j = 0; j < 3; ++j)
-                    for (int v = 0; v < NV; ++v) sY[(j * NV + v) * nn + tid] = ij[k][j] * lam[v];
+            if (act) {
+                const double ka = ij[k][0], kb = ij[k][1], kc = ij[k][2];
+                double* y = sY + tid;
+                y[0 * nn] = fma(-kc, lam[4], fma(kb, lam[5], -ka * lam[6]));    // E0
+                y[1 * nn] = fma(kc, lam[3], fma(-ka, lam[5], -kb * lam[6]));    // E1
+                y[2 * nn] = fma(-kb, lam[3], fma(ka, lam[4], -kc * lam[6]));    // E2
+                y[3 * nn] = fma(kc, lam[1], fma(-kb, lam[2], -ka * lam[7]));    // B0
+                y[4 * nn] = fma(-kc, lam[0], fma(ka, lam[2], -kb * lam[7]));    // B1
+                y[5 * nn] = fma(kb, lam[0], fma(-ka, lam[1], -kc * lam[7]));    // B2
+                y[6 * nn] = -fma(ka, lam[0], fma(kb, lam[1], kc * lam[2]));     // psi
+                y[7 * nn] = -fma(ka, lam[3], fma(kb, lam[4], kc * lam[5]));     // phi
+                y[8 * nn] = -ka * lam[8];                                       // J0
+                y[9 * nn] = -kb * lam[8];                                       // J1
+                y[10 * nn] = -kc * lam[8];                                      // J2
+            }
             __syncthreads();
             if (act) {
                 const int stride = k == 0 ? 1 : (k == 1 ? np1 : np1 * np1);
                 const int base = tid - ci[k] * stride;
                 double Dt[np1];
                 for (int m = 0; m < np1; ++m) Dt[m] = T.D[m][ci[k]];
-                for (int j = 0; j < 3; ++j)
-                    for (int v = 0; v < NV; ++v) {
-                        const double* src = sY + (j * NV + v) * nn + base;
-                        double acc = mu[j][v];
 #pragma unroll
-                        for (int m = 0; m < np1; ++m) acc = fma(Dt[m], src[m * stride], acc);
-                        mu[j][v] = acc;
-                    }
+                for (int w = 0; w < 11; ++w) {
+                    const double* src = sY + w * nn + base;
+                    double acc = xb[w];
+#pragma unroll
+                    for (int m = 0; m < np1; ++m) acc = fma(Dt[m], src[m * stride], acc);
+                    xb[w] = acc;
+                }
             }
         }
         double ub[NV];
         for (int v = 0; v < NV; ++v) ub[v] = 0.0;
         if (act) {
-            // dU_n = - sum (...) F^j(U_m) + S(U_n): volume and explicit sources
-            double neg[3][NV];
-            for (int j = 0; j < 3; ++j)
-                for (int v = 0; v < NV; ++v) neg[j][v] = -mu[j][v];
-            flux_t(u, d.eta, neg, ub);
+            // fields directly; J~ (the q~ flux) through the current's Jacobian
+            for (int v = 0; v < 8; ++v) ub[v] = xb[v];
+            const double jb[3] = {xb[8], xb[9], xb[10]};
+            current_vjp(u, d.eta, jb, jb, ub);
             const double wd[3] = {-lam[0], -lam[1], -lam[2]}, zero[3] = {0.0, 0.0, 0.0};
             current_vjp(u, d.eta, wd, zero, ub);
             ub[8] += lam[6];
