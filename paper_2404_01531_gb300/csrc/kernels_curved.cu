@@ -87,7 +87,6 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
     constexpr int np1 = K::np1, nn = K::nn, nf = K::nf, NW = NT / 32;
     double* sU = sm;                 // [9][nn]
     double* sF = sU + 9 * nn;        // [3][9][nn]
-    double* sT = sF;                 // filter buffer [9][nn]
     double* sC = sF + 27 * nn;       // [6][9][nf]
     double* red = sC + 54 * nf;
     const Tables& T = d.tabs[P];
@@ -342,7 +341,7 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
             if (act)
                 for (int v = 0; v < NV; ++v) sU[v * nn + tid] = u[v];
             __syncthreads();
-            filter_lowrank<P, NT>(T, sU, sT, act);
+            filter_lowrank<P, NT>(T, sU);
             if (act)
                 for (int v = 0; v < NV; ++v) u[v] = sU[v * nn + tid];
         }

@@ -251,7 +251,6 @@ __global__ void __launch_bounds__(DGK<P>::NT, 3) k_dg_substep(Dev d, SubArgs a) 
     double* sU = sm;                 // [9][nn]
     double* sJ = sU + 9 * nn;        // [6][nn]
     double* sC = sJ + 6 * nn;        // [6][9][nf]
-    double* sT = sJ;                 // [9][nn] filter buffer (after the lift phase)
     double* red = sU + 9 * nn + K::AUX;
     __shared__ int s_flag;
     const Tables& T = *d.tab;
@@ -359,7 +358,7 @@ __global__ void __launch_bounds__(DGK<P>::NT, 3) k_dg_substep(Dev d, SubArgs a) 
             if (act)
                 for (int v = 0; v < NV; ++v) sU[v * nn + tid] = u[v];
             __syncthreads();
-            filter_lowrank<P, NT>(T, sU, sT, act);
+            filter_lowrank<P, NT>(T, sU);
             if (act)
                 for (int v = 0; v < NV; ++v) u[v] = sU[v * nn + tid];
         }
