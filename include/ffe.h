@@ -312,8 +312,11 @@ ffe_status ffe_initial_tangent(ffe_ctx* ctx, int which, double* dU_dev);
  * bytes written on return; synchronises the context stream.  ffe_load
  * restores such a checkpoint into a context created with the same domain,
  * elements, orders, metric and FD pool (FFE_EINVAL otherwise); stepping on
- * from it gives the same results as the saved context would.  Adjoint
- * work fields are not part of a checkpoint. */
+ * from it gives the same results as the saved context would.  Every count
+ * and index of the buffer (parameter count, mask bytes 0/1, the FD pool's
+ * element <-> slot maps and free list) is checked on the host first: a
+ * truncated, foreign or corrupt buffer is FFE_EINVAL and leaves the context
+ * unchanged.  Adjoint work fields are not part of a checkpoint. */
 ffe_status ffe_save(ffe_ctx* ctx, void* host_buf, size_t* bytes);
 ffe_status ffe_load(ffe_ctx* ctx, const void* host_buf, size_t bytes);
 

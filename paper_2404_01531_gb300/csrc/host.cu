@@ -1054,15 +1054,57 @@ ffe_status ffe_load(ffe_ctx* c, const void* host_buf, size_t bytes) {
     if (h.E != d.E || h.ndg != d.ndg || h.nfd != d.nfd || h.fd_cap != (d.fd_slot ? d.fd_cap : 0) ||
         h.n_inst != c->n_inst)
         return fail(FFE_EINVAL, "checkpoint of a different mesh, order or FD pool");
-    if (h.id_kind < FFE_ID_FAST_WAVE || h.id_kind > FFE_ID_BREAKDOWN_1D || h.id_nprm_total < 0)
+    // sizes first (no allocation or arithmetic on an unchecked count), then every
+    // index the kernels will follow; the context is changed only once all hold
+    const size_t body = NV * (size_t)(d.ndg + d.nfd) * sizeof(double) + d.E +
+                        (d.fd_slot ? sizeof(int) * ((size_t)d.E + 2 * (size_t)d.fd_cap) : 0);
+    if (h.id_kind < FFE_ID_FAST_WAVE || h.id_kind > FFE_ID_BREAKDOWN_1D || h.id_nprm_total < 0 ||
+        (size_t)h.id_nprm_total > (bytes - sizeof h) / sizeof(double) || h.steps < 0 || !std::isfinite(h.t) ||
+        (c->batch && c->n_inst > 0 && h.id_nprm_total % c->n_inst != 0))
         return fail(FFE_EINVAL, "corrupt checkpoint header");
+    const size_t need = sizeof h + (size_t)h.id_nprm_total * sizeof(double) + body;
+    if (bytes < need) return fail(FFE_EINVAL, "checkpoint of %zu bytes, %zu expected", bytes, need);
     const char* p = (const char*)host_buf + sizeof h;
     std::vector<double> prm((size_t)h.id_nprm_total);
-    const size_t need = sizeof h + prm.size() * sizeof(double) + NV * (size_t)(d.ndg + d.nfd) * sizeof(double) + d.E +
-                        (d.fd_slot ? sizeof(int) * ((size_t)d.E + 2 * (size_t)d.fd_cap) : 0);
-    if (bytes < need) return fail(FFE_EINVAL, "checkpoint of %zu bytes, %zu expected", bytes, need);
     if (!prm.empty()) memcpy(prm.data(), p, prm.size() * sizeof(double));
     p += prm.size() * sizeof(double);
+    const char* state = p;
+    p += NV * (size_t)(d.ndg + d.nfd) * sizeof(double);
+    const unsigned char* mask = (const unsigned char*)p;
+    p += d.E;
+    for (int64_t e = 0; e < d.E; ++e)
+        if (mask[e] > 1) return fail(FFE_EINVAL, "corrupt checkpoint: mask of element %lld is %d", (long long)e, mask[e]);
+    std::vector<int> slot, selem, freel;
+    if (d.fd_slot) {
+        // the FD slot pool: an element is on FD exactly when it holds a slot,
+        // slot <-> element both ways, and the free list holds the other slots once
+        slot.resize(d.E);
+        selem.resize(d.fd_cap);
+        freel.resize(d.fd_cap);
+        memcpy(slot.data(), p, sizeof(int) * d.E);
+        memcpy(selem.data(), p + sizeof(int) * d.E, sizeof(int) * d.fd_cap);
+        memcpy(freel.data(), p + sizeof(int) * ((size_t)d.E + d.fd_cap), sizeof(int) * d.fd_cap);
+        int held = 0;
+        for (int e = 0; e < d.E; ++e) {
+            const int sl = slot[e];
+            if (sl < -1 || sl >= d.fd_cap || (sl >= 0) != (mask[e] == 1) || (sl >= 0 && selem[sl] != e))
+                return fail(FFE_EINVAL, "corrupt checkpoint: FD slot of element %d", e);
+            held += sl >= 0;
+        }
+        for (int sl = 0; sl < d.fd_cap; ++sl) {
+            const int e = selem[sl];
+            if (e < -1 || e >= d.E || (e >= 0 && slot[e] != sl))
+                return fail(FFE_EINVAL, "corrupt checkpoint: element of FD slot %d", sl);
+        }
+        if (h.free_count != d.fd_cap - held) return fail(FFE_EINVAL, "corrupt checkpoint: free FD slot count");
+        std::vector<unsigned char> seen(d.fd_cap, 0);
+        for (int64_t i = 0; i < h.free_count; ++i) {
+            const int sl = freel[i];
+            if (sl < 0 || sl >= d.fd_cap || selem[sl] != -1 || seen[sl])
+                return fail(FFE_EINVAL, "corrupt checkpoint: free FD slot list");
+            seen[sl] = 1;
+        }
+    }
     c->id_kind = (int)h.id_kind;
     if (c->batch) {
         c->id_prm_inst = prm;
@@ -1071,18 +1113,12 @@ ffe_status ffe_load(ffe_ctx* c, const void* host_buf, size_t bytes) {
         c->id_prm = prm;
     }
     CK(cudaStreamSynchronize(c->st));
-    CK(cudaMemcpy(c->un.p, p, NV * (size_t)(d.ndg + d.nfd) * sizeof(double), cudaMemcpyHostToDevice));
-    p += NV * (size_t)(d.ndg + d.nfd) * sizeof(double);
-    CK(cudaMemcpy(d.mask, p, d.E, cudaMemcpyHostToDevice));
-    p += d.E;
+    CK(cudaMemcpy(c->un.p, state, NV * (size_t)(d.ndg + d.nfd) * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.mask, mask, d.E, cudaMemcpyHostToDevice));
     if (d.fd_slot) {
-        std::vector<int> slot(d.E);
-        memcpy(slot.data(), p, sizeof(int) * d.E);
-        CK(cudaMemcpy(d.fd_slot, p, sizeof(int) * d.E, cudaMemcpyHostToDevice));
-        p += sizeof(int) * d.E;
-        CK(cudaMemcpy(d.slot_elem, p, sizeof(int) * d.fd_cap, cudaMemcpyHostToDevice));
-        p += sizeof(int) * d.fd_cap;
-        CK(cudaMemcpy(d.free_slots, p, sizeof(int) * d.fd_cap, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d.fd_slot, slot.data(), sizeof(int) * d.E, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d.slot_elem, selem.data(), sizeof(int) * d.fd_cap, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d.free_slots, freel.data(), sizeof(int) * d.fd_cap, cudaMemcpyHostToDevice));
         const int fc = (int)h.free_count;
         CK(cudaMemcpy(&d.counts[5], &fc, sizeof(int), cudaMemcpyHostToDevice));
         c->h_fd_slot = slot;

@@ -100,3 +100,70 @@ def test_constraints_match_the_state(ffe):
     assert mask.sum() > 0
     np.testing.assert_allclose(got, (EB, D, np.abs(u[6]).max(), np.abs(u[7]).max()), rtol=1e-12, atol=1e-15)
     ctx.close()
+
+
+def _ckpt_parts(blob, n_elem):
+    """Offsets of the checkpoint's sections (the layout ffe_save writes):
+    header, initial-data parameters, state, mask, then for FD slot pools the
+    element->slot map, the slot->element map and the free list."""
+    import struct
+    fmt = "<8s5q3qd3Qq"
+    hdr = struct.unpack_from(fmt, blob, 0)
+    E, ndg, nfd, fd_cap = hdr[1:5]
+    nprm = hdr[8]
+    off = {"nprm": 64, "free_count": 104}
+    off["state"] = struct.calcsize(fmt) + 8 * nprm
+    off["mask"] = off["state"] + 8 * 9 * (ndg + nfd)
+    off["slot"] = off["mask"] + E
+    off["free"] = off["slot"] + 4 * (E + fd_cap)
+    assert E == n_elem
+    return off, fd_cap
+
+
+def test_corrupt_checkpoint_is_rejected_and_leaves_the_context_unchanged(ffe):
+    """ffe_load checks every count and index of a checkpoint on the host before
+    it touches the context: an absurd parameter count, a mask byte other than
+    0/1, an FD slot outside the pool and a wrong free-slot count are each
+    FFE_EINVAL, and the context keeps its state, mask and counters."""
+    import struct
+    cfg = W.breakdown(nx=16, ny=2, nz=1, x_half=0.5)
+    a = ffe.Context(cfg)
+    a.set_initial()
+    a.step(3)
+    blob = bytearray(a.save())
+    off, _ = _ckpt_parts(blob, a.n_elem)
+    a.step(2)
+    U0, m0 = a.download()
+    i0 = a.info()
+    bad_count = bytearray(blob)
+    struct.pack_into("<q", bad_count, off["nprm"], 1 << 60)
+    bad_mask = bytearray(blob)
+    bad_mask[off["mask"] + 3] = 7
+    for bad in (bad_count, bad_mask):
+        with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
+            a.load_checkpoint(bytes(bad))
+    U1, m1 = a.download()
+    i1 = a.info()
+    assert np.array_equal(U0, U1) and np.array_equal(m0, m1)
+    assert (i0.t, i0.steps) == (i1.t, i1.steps)
+    a.load_checkpoint(bytes(blob))   # the intact checkpoint still loads
+    assert a.info().steps == 3
+    a.close()
+
+    cfgs = [W.pulsar(r_lc=3.0, chi=0.4, n_ang=1, n_rad=4, P=5, r_out=4.0),
+            W.pulsar(r_lc=3.5, chi=0.2, n_ang=1, n_rad=6, P=4, r_out=6.0)]
+    b = ffe.BatchContext(cfgs)
+    b.set_initial()
+    b.step(2)
+    blob = bytearray(b.save())
+    off, fd_cap = _ckpt_parts(blob, b.n_elem)
+    bad_slot = bytearray(blob)
+    struct.pack_into("<i", bad_slot, off["slot"], fd_cap)
+    bad_free = bytearray(blob)
+    (fc,) = struct.unpack_from("<q", blob, off["free_count"])
+    struct.pack_into("<q", bad_free, off["free_count"], fc + 1)
+    for bad in (bad_slot, bad_free):
+        with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
+            b.load_checkpoint(bytes(bad))
+    b.load_checkpoint(bytes(blob))
+    b.close()
