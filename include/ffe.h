@@ -185,10 +185,18 @@ ffe_status ffe_rhs(ffe_ctx* ctx, const double* U_dev, double* dUdt_dev);
 ffe_status ffe_step(ffe_ctx* ctx, int nsteps);
 
 /* Borrowed device view of the current state vector and mask (uint8 per element,
- * 0 = DG, 1 = FD); valid until the next mutating call. */
+ * 0 = DG, 1 = FD); valid until the next mutating call.  Writes through the
+ * view are not checked: a mask written there must hold 0 and 1 only (and, in
+ * a batched context, match its FD slot map, see ffe_set_state). */
 ffe_status ffe_get_state(ffe_ctx* ctx, double** U_dev, unsigned char** mask_dev);
 
-/* Replace the state and mask from caller device buffers (state-vector layout). */
+/* Replace the state and mask from caller device buffers (state-vector layout);
+ * either pointer may be NULL.  The mask is checked on the host first (one
+ * E-byte copy, synchronising the context stream): bytes other than 0 and 1,
+ * or, in a batched context, an element on FD without an FD pool slot or on DG
+ * while holding one (pool slots change only through the indicator's
+ * switches), give FFE_EINVAL with nothing replaced.  ffe_upload applies the
+ * same check to its host mask. */
 ffe_status ffe_set_state(ffe_ctx* ctx, const double* U_dev, const unsigned char* mask_dev);
 
 /* Host copies of the state (synchronising); either pointer may be NULL. */

@@ -1541,9 +1541,36 @@ ffe_status ffe_get_state(ffe_ctx* c, double** U_dev, unsigned char** mask_dev) {
     return FFE_OK;
 }
 
+namespace {
+// A caller's mask (host copy) before it replaces the context's: bytes 0 (DG)
+// or 1 (FD) only, and in an FD slot pool exactly the elements that hold a slot
+// on FD (elements change pool slots only through the indicator's switches).
+ffe_status check_mask(ffe_ctx* c, const unsigned char* m) {
+    const Dev& d = c->d;
+    for (int e = 0; e < d.E; ++e)
+        if (m[e] > 1) return fail(FFE_EINVAL, "mask of element %d is %d (0 = DG, 1 = FD)", e, m[e]);
+    if (d.fd_slot) {
+        std::vector<int> slot(d.E);
+        CK(cudaMemcpyAsync(slot.data(), d.fd_slot, sizeof(int) * d.E, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int e = 0; e < d.E; ++e)
+            if ((slot[e] >= 0) != (m[e] == 1))
+                return fail(FFE_EINVAL, "mask of element %d does not match the FD slot pool", e);
+    }
+    return FFE_OK;
+}
+}  // namespace
+
 ffe_status ffe_set_state(ffe_ctx* c, const double* U_dev, const unsigned char* mask_dev) {
     if (!c) return fail(FFE_EINVAL, "null context");
     const Dev& d = c->d;
+    if (mask_dev) {
+        std::vector<unsigned char> m(d.E);
+        CK(cudaMemcpyAsync(m.data(), mask_dev, d.E, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        ffe_status s;
+        if ((s = check_mask(c, m.data()))) return s;
+    }
     if (U_dev) CK(cudaMemcpyAsync(c->un.p, U_dev, NV * (d.ndg + d.nfd) * 8, cudaMemcpyDeviceToDevice, c->st));
     if (mask_dev) CK(cudaMemcpyAsync(d.mask, mask_dev, d.E, cudaMemcpyDeviceToDevice, c->st));
     return FFE_OK;
@@ -1561,6 +1588,8 @@ ffe_status ffe_download(ffe_ctx* c, double* U_host, unsigned char* mask_host) {
 ffe_status ffe_upload(ffe_ctx* c, const double* U_host, const unsigned char* mask_host) {
     if (!c) return fail(FFE_EINVAL, "null context");
     const Dev& d = c->d;
+    ffe_status s;
+    if (mask_host && (s = check_mask(c, mask_host))) return s;
     if (U_host) CK(cudaMemcpyAsync(c->un.p, U_host, NV * (d.ndg + d.nfd) * 8, cudaMemcpyHostToDevice, c->st));
     if (mask_host) CK(cudaMemcpyAsync(d.mask, mask_host, d.E, cudaMemcpyHostToDevice, c->st));
     return FFE_OK;

@@ -167,3 +167,41 @@ def test_corrupt_checkpoint_is_rejected_and_leaves_the_context_unchanged(ffe):
             b.load_checkpoint(bytes(bad))
     b.load_checkpoint(bytes(blob))
     b.close()
+
+
+def test_state_replacement_checks_the_mask(ffe):
+    """ffe_set_state and ffe_upload refuse a mask byte other than 0/1 and, in a
+    batched context, a mask that disagrees with the FD slot pool; nothing is
+    replaced.  A consistent mask is accepted."""
+    cfg = W.breakdown(nx=16, ny=2, nz=1, x_half=0.5)
+    a = ffe.Context(cfg)
+    a.set_initial()
+    a.step(2)
+    U, m = (t.clone() for t in a.state())
+    U0, m0 = a.download()
+    bad = m.clone()
+    bad[5] = 2
+    with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
+        a.set_state(U * 2.0, bad)
+    U1, m1 = a.download()
+    assert np.array_equal(U0, U1) and np.array_equal(m0, m1)
+    hm = torch.from_numpy(m0.copy()).pin_memory()
+    hm[0] = 9
+    hU = torch.from_numpy(U0).pin_memory()
+    with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
+        a.upload_from(hU.data_ptr(), hm.data_ptr())
+    flipped = m.clone()
+    flipped[0] = 1 - flipped[0]   # any 0/1 mask is valid without a slot pool
+    a.set_state(U, flipped)
+    a.close()
+
+    cfgs = [W.pulsar(r_lc=3.0, chi=0.4, n_ang=1, n_rad=4, P=5, r_out=4.0)]
+    b = ffe.BatchContext(cfgs)
+    b.set_initial()
+    U, m = (t.clone() for t in b.state())
+    b.set_state(U, m)                     # the pool's own mask
+    flipped = m.clone()
+    flipped[0] = 1 - flipped[0]
+    with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
+        b.set_state(U, flipped)
+    b.close()
