@@ -1178,6 +1178,39 @@ ffe_status ffe_eval_recip(const double* x_dev, double* y_dev, int64_t n, void* c
 
 const char* ffe_last_error(void) { return g_err.c_str(); }
 
+namespace {
+// Every node and FD cell index of a context fits a 32-bit int: at most
+// INT_MAX / (2 Pmax + 1)^3 elements (1.6 M at P = 5, beyond what fits in HBM).
+ffe_status check_count(int64_t E, int Pmax, const char* who) {
+    const int64_t per = (int64_t)(2 * Pmax + 1) * (2 * Pmax + 1) * (2 * Pmax + 1);
+    if (E < 1 || E > INT32_MAX / per)
+        return fail(FFE_EINVAL, "%s: %lld elements (1 to %lld at P = %d)", who, (long long)E, (long long)(INT32_MAX / per), Pmax);
+    return FFE_OK;
+}
+
+// Scheme parameters: finite, damping and filter strengths non-negative, a
+// positive step or CFL data, indicator and WENO constants positive where used,
+// known constraint mode and reconstruction.
+ffe_status check_scheme(const ffe_params& p, const char* who) {
+    const double v[] = {p.eta, p.kappa_psi, p.kappa_phi, p.cfl, p.c_over_D, p.dt, p.filter_a, p.filter_b,
+                        p.tci_alpha, p.weno_eps, p.omega_star};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(FFE_EINVAL, "%s: a scheme parameter is not finite", who);
+    if (p.eta < 0 || p.kappa_psi < 0 || p.kappa_phi < 0) return fail(FFE_EINVAL, "%s: negative damping", who);
+    if (p.dt < 0 || (p.dt == 0 && !(p.cfl > 0 && p.c_over_D > 0)))
+        return fail(FFE_EINVAL, "%s: need dt > 0 or cfl > 0 and c_over_D > 0", who);
+    if (p.filter_on && (p.filter_a < 0 || !(p.filter_b > 0)))
+        return fail(FFE_EINVAL, "%s: filter needs a >= 0 and b > 0", who);
+    if (p.constraint_mode < FFE_RELAX || p.constraint_mode > FFE_RELAX_THEN_HARD)
+        return fail(FFE_EINVAL, "%s: constraint mode %d", who, p.constraint_mode);
+    if (p.recon != FFE_RECON_WENO5Z && p.recon != FFE_RECON_MP5) return fail(FFE_EINVAL, "%s: reconstruction %d", who, p.recon);
+    if (p.tci_on && !(p.tci_alpha > 0)) return fail(FFE_EINVAL, "%s: indicator needs alpha > 0", who);
+    if (p.tci_on && p.recon == FFE_RECON_WENO5Z && !(p.weno_eps > 0))
+        return fail(FFE_EINVAL, "%s: WENO5-Z needs eps > 0", who);
+    return FFE_OK;
+}
+}  // namespace
+
 ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, int P, const ffe_metric* metric,
                       const ffe_params* params, void* cuda_stream, ffe_ctx** out) {
     g_err.clear();
@@ -1210,14 +1243,20 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
         if ((domain->bc_lo[dd] == FFE_BC_PERIODIC) != (domain->bc_hi[dd] == FFE_BC_PERIODIC))
             return fail(FFE_EINVAL, "periodic axis %d needs periodic at both ends", dd);
     }
-    if (params->constraint_mode < FFE_RELAX || params->constraint_mode > FFE_RELAX_THEN_HARD)
-        return fail(FFE_EINVAL, "constraint mode %d", params->constraint_mode);
-    if (params->recon != FFE_RECON_WENO5Z && params->recon != FFE_RECON_MP5)
-        return fail(FFE_EINVAL, "reconstruction %d", params->recon);
-    if (params->eta < 0 || params->kappa_psi < 0 || params->kappa_phi < 0) return fail(FFE_EINVAL, "negative damping");
     if (params->tci_on && (params->tci_M < 1 || params->tci_M > P)) return fail(FFE_EINVAL, "tci_M=%d", params->tci_M);
-    if (params->dt < 0 || (params->dt == 0 && !(params->cfl > 0 && params->c_over_D > 0)))
-        return fail(FFE_EINVAL, "need dt > 0 or cfl > 0 and c_over_D > 0");
+    ffe_status st0;
+    if ((st0 = check_scheme(*params, "parameters"))) return st0;
+    if (domain->kind == FFE_DOMAIN_SHELL6) {
+        if (!std::isfinite(domain->r_out)) return fail(FFE_EINVAL, "need a finite r_out");
+        st0 = check_count(6 * (int64_t)elements->n[0] * elements->n[0] * elements->n[2], P, "shell");
+    } else {
+        for (int dd = 0; dd < 3; ++dd)
+            if (!std::isfinite(domain->lo[dd]) || !std::isfinite(domain->hi[dd]))
+                return fail(FFE_EINVAL, "box bounds along axis %d are not finite", dd);
+        st0 = check_count((int64_t)elements->n[0] * elements->n[1] * elements->n[2], P, "box");
+    }
+    if (st0) return st0;
+    if (metric->kind == FFE_METRIC_KERR_SCHILD && !std::isfinite(metric->M)) return fail(FFE_EINVAL, "need a finite M");
 
     ffe_ctx* c = new ffe_ctx();
     c->dom = *domain;
@@ -1277,9 +1316,14 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
     if (metric->kind != FFE_METRIC_MINKOWSKI) return fail(FFE_ENOTIMPL, "batched contexts are flat-space shells");
     if (fd_capacity < 0) return fail(FFE_EINVAL, "fd_capacity < 0");
     const ffe_params& p0 = params[0];
+    int64_t n_all = 0;
     for (int i = 0; i < n_inst; ++i) {
         const ffe_domain& dm = doms[i];
         const ffe_params& pi = params[i];
+        char who[32];
+        snprintf(who, sizeof who, "instance %d", i);
+        ffe_status st0;
+        if ((st0 = check_scheme(pi, who))) return st0;
         if (dm.kind != FFE_DOMAIN_SHELL6) return fail(FFE_EINVAL, "instance %d: batched instances are shells", i);
         if (!(dm.r_in > 0) || !(dm.r_out > dm.r_in)) return fail(FFE_EINVAL, "instance %d: need 0 < r_in < r_out", i);
         if (els[i].n[0] < 1 || els[i].n[2] < 1) return fail(FFE_EINVAL, "instance %d: element counts", i);
@@ -1292,13 +1336,11 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
             pi.weno_eps != p0.weno_eps || pi.fd_corrector != p0.fd_corrector || pi.recon != p0.recon ||
             pi.constraint_mode != p0.constraint_mode)
             return fail(FFE_EINVAL, "instance %d: scheme parameters differ from instance 0", i);
-        if (pi.dt < 0 || (pi.dt == 0 && !(pi.cfl > 0 && pi.c_over_D > 0)))
-            return fail(FFE_EINVAL, "instance %d: need dt > 0 or cfl > 0 and c_over_D > 0", i);
+        if (!std::isfinite(dm.r_out)) return fail(FFE_EINVAL, "instance %d: need a finite r_out", i);
         if (p0.tci_on && (p0.tci_M < 1 || p0.tci_M > Ps[i])) return fail(FFE_EINVAL, "tci_M=%d", p0.tci_M);
+        n_all += 6 * (int64_t)els[i].n[0] * els[i].n[0] * els[i].n[2];
+        if ((st0 = check_count(n_all, 5, "batch"))) return st0;
     }
-    if (p0.constraint_mode < FFE_RELAX || p0.constraint_mode > FFE_RELAX_THEN_HARD)
-        return fail(FFE_EINVAL, "constraint mode %d", p0.constraint_mode);
-    if (p0.recon != FFE_RECON_WENO5Z && p0.recon != FFE_RECON_MP5) return fail(FFE_EINVAL, "reconstruction %d", p0.recon);
     ffe_ctx* c = new ffe_ctx();
     auto bail = [&](ffe_status s) { ffe_destroy(c); return s; };
     c->batch = true;

@@ -46,6 +46,114 @@ def test_library_is_device_code_for_sm_103a(lib_path):
     assert "sm_103a" in out.stdout
 
 
-def test_last_error_starts_empty(lib_path):
+def test_last_error_reports_the_last_failure(lib_path):
+    """A failing call leaves its reason in ffe_last_error (thread-local),
+    whatever ran before in the process."""
+    import ctypes
     from paper_2404_01531_gb300 import ffe
-    assert ffe.load().ffe_last_error() == b""
+    lib = ffe.load()
+    h = ctypes.c_void_p()
+    assert lib.ffe_create(None, None, 5, None, None, None, ctypes.byref(h)) == 1
+    assert lib.ffe_last_error() == b"null argument"
+    assert h.value is None
+
+
+def _create(ffe, cfg):
+    """ffe_create on a configuration, with no CUDA stream: status and message."""
+    import ctypes
+    lib = ffe.load()
+    dom, el = ffe.domain_of(cfg)
+    mk, M, spin = cfg["metric"]
+    met = ffe.Metric(ffe.METRIC[mk], M, spin)
+    prm = ffe.params_from(cfg["params"])
+    h = ctypes.c_void_p()
+    st = lib.ffe_create(ctypes.byref(dom), ctypes.byref(el), cfg["P"], ctypes.byref(met), ctypes.byref(prm),
+                        None, ctypes.byref(h))
+    return st, lib.ffe_last_error().decode(), h.value
+
+
+PARAM_KEYS = {"eta", "kappa_psi", "kappa_phi", "cfl", "c_over_D", "dt", "filter_on", "filter_a", "filter_b",
+              "tci_on", "tci_M", "tci_alpha", "weno_eps", "fd_corrector", "constraint_mode", "omega_star", "recon"}
+
+
+def _bad(cfg, **kw):
+    """A copy of cfg with some scheme parameters or mesh entries replaced."""
+    import copy
+    c = copy.deepcopy(cfg)
+    for k, v in kw.items():
+        (c["params"] if k in PARAM_KEYS else c)[k] = v
+    return c
+
+
+def test_create_rejects_invalid_configurations(lib_path):
+    """ffe_create checks its whole configuration on the host before any CUDA
+    call (so this runs without a GPU): each bad value is FFE_EINVAL with a
+    message naming it, and no context is returned."""
+    import ffe_workloads as W
+    from paper_2404_01531_gb300 import ffe
+    nan, inf = float("nan"), float("inf")
+    box = W.breakdown(nx=4, ny=2, nz=1, x_half=0.5)
+    shell = W.pulsar(r_lc=3.0, chi=0.4, n_ang=1, n_rad=4, P=5, r_out=4.0)
+    cases = [
+        (_bad(box, P=7), "order"),
+        (_bad(box, eta=nan), "not finite"),
+        (_bad(box, kappa_psi=inf), "not finite"),
+        (_bad(box, eta=-1.0), "negative damping"),
+        (_bad(box, dt=0.0, cfl=0.0), "need dt"),
+        (_bad(box, dt=-1e-3), "need dt"),
+        (_bad(box, filter_b=0.0), "filter"),
+        (_bad(box, tci_alpha=0.0), "alpha"),
+        (_bad(box, weno_eps=0.0), "eps"),
+        (_bad(box, tci_M=9), "tci_M"),
+        (_bad(box, constraint_mode=5), "constraint mode"),
+        (_bad(box, recon=3), "reconstruction"),
+        (_bad(box, n=[2000, 2000, 2000]), "elements"),
+        (_bad(box, n=[4, 0, 1]), "elements"),
+        (_bad(box, hi=[inf, 1.0, 1.0]), "not finite"),
+        (_bad(box, lo=[1.0, 0.0, 0.0], hi=[1.0, 1.0, 1.0]), "empty box"),
+        (_bad(shell, r_out=inf), "r_out"),
+        (_bad(shell, r_in=2.0, r_out=1.0), "r_in < r_out"),
+        (_bad(shell, P=6), "3 <= P <= 5"),
+        (_bad(shell, n_ang=3000, n_rad=3000), "elements"),
+    ]
+    for cfg, what in cases:
+        st, msg, h = _create(ffe, cfg)
+        assert st == 1, (what, st, msg)
+        assert h is None
+        assert what in msg, (what, msg)
+
+
+def test_create_batch_rejects_invalid_configurations(lib_path):
+    """ffe_create_batch: host checks per instance before any CUDA call."""
+    import ctypes
+    import ffe_workloads as W
+    from paper_2404_01531_gb300 import ffe
+    lib = ffe.load()
+
+    def create(cfgs, fd_capacity=0):
+        n = len(cfgs)
+        doms, els, prms = (ffe.Domain * max(n, 1))(), (ffe.Elements * max(n, 1))(), (ffe.Params * max(n, 1))()
+        Ps = (ctypes.c_int * max(n, 1))(*[c["P"] for c in cfgs])
+        for i, c in enumerate(cfgs):
+            doms[i], els[i] = ffe.domain_of(c)
+            prms[i] = ffe.params_from(c["params"])
+        met = ffe.Metric(0, 0.0, 0.0)
+        h = ctypes.c_void_p()
+        st = lib.ffe_create_batch(n, doms, els, Ps, ctypes.byref(met), prms, fd_capacity, None, ctypes.byref(h))
+        return st, lib.ffe_last_error().decode(), h.value
+
+    a = W.pulsar(r_lc=3.0, chi=0.4, n_ang=1, n_rad=4, P=5, r_out=4.0)
+    b = W.pulsar(r_lc=3.5, chi=0.2, n_ang=1, n_rad=6, P=4, r_out=6.0)
+    for cfgs, fd_cap, what in [
+        ([], 0, "bad argument"),
+        ([a, b], -1, "fd_capacity"),
+        ([a, _bad(b, eta=a["params"]["eta"] + 1.0)], 0, "differ"),
+        ([_bad(a, eta=float("nan")), b], 0, "not finite"),
+        ([a, _bad(b, P=6)], 0, "order"),
+        ([a, _bad(b, r_out=float("inf"))], 0, "r_out"),
+        ([a, _bad(b, n_ang=200, n_rad=200)], 0, "elements"),
+    ]:
+        st, msg, h = create(cfgs, fd_cap)
+        assert st == 1, (what, st, msg)
+        assert h is None
+        assert what in msg, (what, msg)
