@@ -157,3 +157,34 @@ def test_create_batch_rejects_invalid_configurations(lib_path):
         assert st == 1, (what, st, msg)
         assert h is None
         assert what in msg, (what, msg)
+
+
+def test_workload_configurations_pass_the_host_checks(lib_path):
+    """Every workload the tests and the benchmark build gets past ffe_create's
+    host checks: here (no GPU) it stops at the first device allocation, on a
+    GPU the context is created and destroyed again."""
+    import ctypes
+    import ffe_workloads as W
+    from paper_2404_01531_gb300 import ffe
+    lib = ffe.load()
+    wald = W.wald(n_ang=2, n_rad=2)
+    wald["params"]["tci_on"] = 0
+    cfgs = [W.fast_wave(), W.breakdown(nx=8, ny=2, nz=1), W.cleaning_mode(), wald, W.pulsar(n_ang=1, n_rad=2),
+            W.adjoint_pulsar(tiny=True)] + [W.oned(t) for t in ("fast_wave_kink", "alfven", "breakdown_1d")]
+    for cfg in cfgs:
+        st, msg, h = _create(ffe, cfg)
+        assert st != 1, (cfg["name"] if "name" in cfg else cfg["kind"], msg)
+        if st == 0:
+            lib.ffe_destroy(ctypes.c_void_p(h))
+    ps = W.pulsars(n_inst=32)
+    n = len(ps)
+    doms, els, prms = (ffe.Domain * n)(), (ffe.Elements * n)(), (ffe.Params * n)()
+    Ps = (ctypes.c_int * n)(*[c["P"] for c in ps])
+    for i, c in enumerate(ps):
+        doms[i], els[i] = ffe.domain_of(c)
+        prms[i] = ffe.params_from(c["params"])
+    h = ctypes.c_void_p()
+    st = lib.ffe_create_batch(n, doms, els, Ps, ctypes.byref(ffe.Metric(0, 0.0, 0.0)), prms, 0, None, ctypes.byref(h))
+    assert st != 1, lib.ffe_last_error()
+    if st == 0:
+        lib.ffe_destroy(h)
