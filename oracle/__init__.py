@@ -19,7 +19,10 @@ silent are marked ``[reading]`` in the docstrings.
 
 Parity unpinned (no value from the paper or mathematics fixes them; they are
 checked only by GPU-vs-oracle agreement, conservation and convergence):
-  * the flux at a face shared by a DG and an FD element (`dg.external_state`
-    with an FD neighbour, `fd.fill_ghosts` with a DG neighbour);
+  * at a face shared by a DG and an FD element, the exterior current
+    (`dg.external_fd_current`, `fd.fill_ghosts` for J~: the projection of the
+    current, a reading); the exterior state there (`dg.external_dg_state` with
+    an FD neighbour, `fd.fill_ghosts` with a DG neighbour) is pinned by the
+    exactness of the mixed DG/FD right-hand side on linear fields;
   * the rollback bookkeeping of a substep redone on FD (`stepper`).
 """

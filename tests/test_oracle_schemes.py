@@ -45,6 +45,43 @@ def test_dg_rhs_exact_on_linear_fields_matches_maxwell():
     np.testing.assert_allclose(r.reshape(9, -1), np.broadcast_to(exp[:, None], (9, r[0].size)), atol=1e-11)
 
 
+@pytest.mark.parametrize("recon,corr", [(0, 1), (1, 0)])
+def test_mixed_dg_fd_rhs_exact_on_linear_fields(recon, corr):
+    """Linear fields, eta = 0, q = 0 on a box with DG and FD elements side by
+    side (Dirichlet to the same fields): every piece of the hybrid scheme is
+    exact on them (DG; WENO5-Z / MP5 point-value interpolation; Rusanov with
+    equal states; the corrector; the DG polynomial at an FD neighbour's ghost
+    centres and the 6-point FD->DG extrapolation at a DG face), so the
+    right-hand side at every DG node and FD cell is the flat Maxwell one.  Pins
+    the DG/FD interface treatment (Sec. III.C.2, ghost cells and the DG
+    element's exterior state) against a closed form."""
+    rng = np.random.default_rng(21)
+    A = rng.normal(size=(9, 3))
+    A[8] = 0
+    U0 = rng.normal(size=9)
+    U0[8] = 0
+    fn = lambda xyz: U0.reshape((9,) + (1,) * (xyz.ndim - 1)) + np.einsum('vd,d...->v...', A, xyz)
+    cfg = _box((3, 2, 1), bc="dirichlet", eta=0.0, recon=recon, fd_corrector=corr)
+    pr = Problem(cfg)   # indicator on: builds the subcell geometry (the mask is set below)
+    pr.prm["dirichlet"] = fn
+    E = pr.disc.E
+    mask = np.zeros(E, np.uint8)
+    mask[[0, 2, 4]] = 1     # elements on FD, each with DG neighbours across faces
+    Nc = pr.T.nc
+    st = dict(mask=mask,
+              udg=fn(pr.disc.xyz.reshape(3, -1)).reshape((9,) + pr.disc.xyz.shape[1:]),
+              ufd=fn(pr.disc.xyz_fd.reshape(3, -1)).reshape((9, E, Nc, Nc, Nc)))
+    dE, dB = A[0:3], A[3:6]
+    curl = lambda g: np.array([g[2, 1] - g[1, 2], g[0, 2] - g[2, 0], g[1, 0] - g[0, 1]])
+    exp = np.concatenate([curl(dB) - A[6], -curl(dE) - A[7], [-np.trace(dE), -np.trace(dB), 0.0]])
+    rdg = rhs_dg(st, pr.disc, pr.met, pr.prm)[:, mask == 0]
+    rfd = rhs_fd(st, pr.disc, pr.met, pr.prm)[:, mask == 1]
+    scale = np.abs(exp).max()
+    for r in (rdg, rfd):
+        np.testing.assert_allclose(r.reshape(9, -1), np.broadcast_to(exp[:, None], (9, r[0].size)),
+                                   atol=1e-10 * scale)
+
+
 @pytest.mark.parametrize("which", ["dg", "fd"])
 def test_conservation_periodic(which):
     """Linear Maxwell (eta = 0, q = 0) on a periodic box: the LGL-quadrature
