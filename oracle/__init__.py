@@ -23,6 +23,8 @@ checked only by GPU-vs-oracle agreement, conservation and convergence):
     (`dg.external_fd_current`, `fd.fill_ghosts` for J~: the projection of the
     current, a reading); the exterior state there (`dg.external_dg_state` with
     an FD neighbour, `fd.fill_ghosts` with a DG neighbour) is pinned by the
-    exactness of the mixed DG/FD right-hand side on linear fields;
-  * the rollback bookkeeping of a substep redone on FD (`stepper`).
+    exactness of the mixed DG/FD right-hand side on linear fields.
+The rollback bookkeeping of a substep redone on FD (`stepper`) is pinned the
+same way: on fields linear in x a step with switches after substeps A, B and C
+equals the step without them.
 """

@@ -292,3 +292,60 @@ def test_breakdown_hard_mode_invariants_and_switching():
     E, B = U[0:3], U[3:6]
     assert np.abs(np.sum(E * B, 0)).max() < 1e-12
     assert (np.sum(E * E, 0) - np.sum(B * B, 0)).max() < 1e-12
+
+
+def test_rollback_bookkeeping_is_exact_on_linear_fields(monkeypatch):
+    """A substep redone on FD (Sec. III.C.1: the substep's inputs u_n, earlier
+    F and G and its stage state projected to the element's subcells, the RHS
+    recomputed by the FD operator, the result rebuilt) against the same step
+    without any switch.  Fields linear in x with eta = 0 and q = 0 stay linear
+    in x through the IMEX stages (kappa psi~ and kappa phi~ make G nonzero), DG
+    and FD are exact on them and the projections are exact, so elements 3, 4, 5
+    of a 9 x 1 x 1 box (out of reach of the x boundary's fixed exterior state
+    within three right-hand sides) must agree whether they switch to FD after
+    substep A, B or C or not at all.  The indicator is replaced by a fake that
+    flags the chosen element after each substep."""
+    import oracle.stepper as stepper
+    from oracle.ops import apply_3d
+    rng = np.random.default_rng(31)
+    A = np.zeros((9, 3))
+    A[:8, 0] = rng.normal(size=8)
+    U0 = rng.normal(size=9)
+    U0[8] = 0
+    fn = lambda xyz: U0.reshape((9,) + (1,) * (xyz.ndim - 1)) + np.einsum('vd,d...->v...', A, xyz)
+    cfg = _box((9, 1, 1), eta=0.0, kappa_psi=1.0, kappa_phi=1.0)
+    cfg["bc"] = ("dirichlet", "periodic", "periodic")
+    pr = Problem(cfg)
+    pr.prm["dirichlet"] = fn
+    E = pr.disc.E
+    xc = pr.disc.xyz.mean(axis=(2, 3, 4))[0]
+    order = np.argsort(xc)                     # elements along x
+    targets = [int(order[3]), int(order[4]), int(order[5])]
+    st0 = dict(mask=np.zeros(E, np.uint8), udg=fn(pr.disc.xyz.reshape(3, -1)).reshape((9,) + pr.disc.xyz.shape[1:]),
+               ufd=np.zeros((9, E) + (pr.T.nc,) * 3), t=0.0)
+
+    def run(flags):
+        calls = {"n": 0}
+
+        def fake(B, met_dg, T, sel):
+            k = calls["n"]
+            calls["n"] += 1
+            r = np.zeros(len(sel))
+            if k < len(flags) and flags[k] is not None:
+                r[sel == flags[k]] = 1.0
+            return r
+        monkeypatch.setattr(stepper, "tci_ratio", fake)
+        S = Stepper(pr)
+        out = S.step({k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st0.items()})
+        return out, S.last_switched
+
+    ref, sw0 = run([None, None, None])
+    got, sw1 = run(targets)
+    assert sw0 == [] and sw1 == sorted(targets)
+    assert all(got["mask"][e] == 1 for e in targets)
+    scale = np.abs(ref["udg"][:, targets]).max()
+    for e in targets:
+        want = apply_3d(pr.T.P, ref["udg"][:, e])      # exact on the linear-in-x step result
+        np.testing.assert_allclose(got["ufd"][:, e], want, atol=1e-11 * scale)
+    # the reference really moved: the step changed the state by more than rounding
+    assert np.abs(ref["udg"][:, targets] - st0["udg"][:, targets]).max() > 1e-3 * scale
