@@ -19,7 +19,8 @@
  * Conventions for every entry point:
  *   - Every function returns ffe_status.  FFE_OK = 0.  On error a thread-local
  *     message is available from ffe_last_error(); no exception, longjmp or
- *     device trap crosses the ABI.
+ *     device trap crosses the ABI (a host allocation or thread start that
+ *     fails inside the library is FFE_ENOMEM).
  *   - Arguments are validated before anything is enqueued (FFE_EINVAL).
  *   - "_dev" pointers are device pointers owned by the caller (for example a
  *     torch tensor's data_ptr()); "_host" pointers are host memory owned by the

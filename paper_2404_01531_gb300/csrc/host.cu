@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <string>
 #include <thread>
 #include <vector>
@@ -28,6 +29,20 @@ ffe_status fail(ffe_status s, const char* fmt, ...) {
     va_end(ap);
     g_err = buf;
     return s;
+}
+
+// Every entry point's body is a function-try-block ending here, so that no C++
+// exception (a failed host allocation, a host thread that cannot be started)
+// crosses the C ABI: it becomes FFE_ENOMEM with its description.  A context
+// being created when that happens is not released.
+ffe_status host_failure() {
+    try {
+        throw;
+    } catch (const std::exception& ex) {
+        return fail(FFE_ENOMEM, "host resources exhausted: %s", ex.what());
+    } catch (...) {
+        return fail(FFE_ENOMEM, "host resources exhausted");
+    }
 }
 
 #define CK(call)                                                                          \
@@ -225,16 +240,24 @@ void initial_point(int kind, const double* prm, int nprm, const double* X, doubl
     }
 }
 
-// run fn(i) for i in [0, n) on all host cores
+// run fn(i) for i in [0, n) on all host cores; a share whose thread cannot be
+// started runs on the calling thread (the started ones are always joined)
 template <typename F>
 void parallel_for(int64_t n, F fn) {
     unsigned nt = std::thread::hardware_concurrency();
     nt = nt == 0 ? 1 : (nt > 64 ? 64 : nt);
     std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t)
-        th.emplace_back([&, t]() {
+    th.reserve(nt);
+    for (unsigned t = 0; t < nt; ++t) {
+        auto share = [&, t]() {
             for (int64_t i = t; i < n; i += nt) fn(i);
-        });
+        };
+        try {
+            th.emplace_back(share);
+        } catch (...) {
+            share();
+        }
+    }
     for (auto& x : th) x.join();
 }
 
@@ -995,7 +1018,7 @@ size_t ckpt_size(const ffe_ctx* c) {
 }
 }  // namespace
 
-ffe_status ffe_save(ffe_ctx* c, void* host_buf, size_t* bytes) {
+ffe_status ffe_save(ffe_ctx* c, void* host_buf, size_t* bytes) try {
     g_err.clear();
     if (!c || !bytes) return fail(FFE_EINVAL, "null argument");
     const Dev& d = c->d;
@@ -1041,9 +1064,11 @@ ffe_status ffe_save(ffe_ctx* c, void* host_buf, size_t* bytes) {
     }
     *bytes = need;
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_load(ffe_ctx* c, const void* host_buf, size_t bytes) {
+ffe_status ffe_load(ffe_ctx* c, const void* host_buf, size_t bytes) try {
     g_err.clear();
     if (!c || !host_buf) return fail(FFE_EINVAL, "null argument");
     Dev& d = c->d;
@@ -1127,9 +1152,11 @@ ffe_status ffe_load(ffe_ctx* c, const void* host_buf, size_t bytes) {
     c->t = h.t;
     c->steps = h.steps;
     return fill_dirichlet(c);
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_constraints(ffe_ctx* c, const double* U_dev, double* out_host) {
+ffe_status ffe_constraints(ffe_ctx* c, const double* U_dev, double* out_host) try {
     g_err.clear();
     if (!c || !out_host) return fail(FFE_EINVAL, "null argument");
     const Dev& d = c->d;
@@ -1153,9 +1180,11 @@ ffe_status ffe_constraints(ffe_ctx* c, const double* U_dev, double* out_host) {
         out_host[3] = fmax(out_host[3], h[4 * b + 3]);
     }
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_get_coords(ffe_ctx* c, double* xyz_dg_dev, double* xyz_fd_dev) {
+ffe_status ffe_get_coords(ffe_ctx* c, double* xyz_dg_dev, double* xyz_fd_dev) try {
     g_err.clear();
     if (!c) return fail(FFE_EINVAL, "null context");
     const Dev& d = c->d;
@@ -1165,15 +1194,19 @@ ffe_status ffe_get_coords(ffe_ctx* c, double* xyz_dg_dev, double* xyz_fd_dev) {
     if (xyz_fd_dev)
         CK(cudaMemcpyAsync(xyz_fd_dev, d.xyz_fd, 3 * (size_t)d.nfd * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_eval_recip(const double* x_dev, double* y_dev, int64_t n, void* cuda_stream) {
+ffe_status ffe_eval_recip(const double* x_dev, double* y_dev, int64_t n, void* cuda_stream) try {
     g_err.clear();
     if (n < 0 || (n > 0 && (!x_dev || !y_dev))) return fail(FFE_EINVAL, "bad argument");
     if (n == 0) return FFE_OK;
     launch_eval_recip(x_dev, y_dev, n, (cudaStream_t)cuda_stream);
     CK(cudaGetLastError());
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
 const char* ffe_last_error(void) { return g_err.c_str(); }
@@ -1212,7 +1245,7 @@ ffe_status check_scheme(const ffe_params& p, const char* who) {
 }  // namespace
 
 ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, int P, const ffe_metric* metric,
-                      const ffe_params* params, void* cuda_stream, ffe_ctx** out) {
+                      const ffe_params* params, void* cuda_stream, ffe_ctx** out) try {
     g_err.clear();
     if (!domain || !elements || !metric || !params || !out) return fail(FFE_EINVAL, "null argument");
     *out = nullptr;
@@ -1305,11 +1338,13 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     if ((s = finish_create(c, d.E, {P}))) return bail(s);
     *out = c;
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
 ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elements* els, const int* Ps,
                             const ffe_metric* metric, const ffe_params* params, int fd_capacity, void* cuda_stream,
-                            ffe_ctx** out) {
+                            ffe_ctx** out) try {
     g_err.clear();
     if (n_inst < 1 || !doms || !els || !Ps || !metric || !params || !out) return fail(FFE_EINVAL, "bad argument");
     *out = nullptr;
@@ -1492,9 +1527,11 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
     if ((s = finish_create(c, cap, orders))) return bail(s);
     *out = c;
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_get_layout(ffe_ctx* c, int* elem_P, int* fd_slot, int* elem_inst, int* inst_first, int* n_inst) {
+ffe_status ffe_get_layout(ffe_ctx* c, int* elem_P, int* fd_slot, int* elem_inst, int* inst_first, int* n_inst) try {
     if (!c) return fail(FFE_EINVAL, "null context");
     const Dev& d = c->d;
     CK(cudaStreamSynchronize(c->st));
@@ -1513,9 +1550,11 @@ ffe_status ffe_get_layout(ffe_ctx* c, int* elem_P, int* fd_slot, int* elem_inst,
     }
     if (n_inst) *n_inst = c->n_inst;
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_set_initial_batch(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) {
+ffe_status ffe_set_initial_batch(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) try {
     g_err.clear();
     if (!c) return fail(FFE_EINVAL, "null context");
     if (id_kind < FFE_ID_FAST_WAVE || id_kind > FFE_ID_DIPOLE) return fail(FFE_EINVAL, "initial data kind %d", id_kind);
@@ -1529,9 +1568,11 @@ ffe_status ffe_set_initial_batch(ffe_ctx* c, int id_kind, const double* id_param
         c->id_prm.assign(id_params, id_params + n_params);
     }
     return set_initial_impl(c, id_kind, (flags & FFE_INIT_KEEP_MASK) != 0, (flags & FFE_INIT_VIA_FD) != 0);
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) {
+ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int n_params, int flags) try {
     g_err.clear();
     if (!c) return fail(FFE_EINVAL, "null context");
     if (id_kind < FFE_ID_FAST_WAVE || id_kind > FFE_ID_BREAKDOWN_1D) return fail(FFE_EINVAL, "initial data kind %d", id_kind);
@@ -1548,9 +1589,11 @@ ffe_status ffe_set_initial(ffe_ctx* c, int id_kind, const double* id_params, int
         for (int i = 0; i < c->n_inst; ++i) c->id_prm_inst.insert(c->id_prm_inst.end(), id_params, id_params + n_params);
     }
     return set_initial_impl(c, id_kind, (flags & FFE_INIT_KEEP_MASK) != 0, (flags & FFE_INIT_VIA_FD) != 0);
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) {
+ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) try {
     g_err.clear();
     if (!c || !U_dev || !dUdt_dev) return fail(FFE_EINVAL, "null argument");
     if (c->id_kind < 0) return fail(FFE_ESTATE, "no initial data set (boundary data undefined)");
@@ -1567,20 +1610,26 @@ ffe_status ffe_rhs(ffe_ctx* c, const double* U_dev, double* dUdt_dev) {
                       c->G1, c->st);
     CK(cudaGetLastError());
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_step(ffe_ctx* c, int nsteps) {
+ffe_status ffe_step(ffe_ctx* c, int nsteps) try {
     g_err.clear();
     if (!c || nsteps < 0) return fail(FFE_EINVAL, "bad argument");
     if (c->id_kind < 0) return fail(FFE_ESTATE, "no initial data set");
     return run_steps(c, nsteps);
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_get_state(ffe_ctx* c, double** U_dev, unsigned char** mask_dev) {
+ffe_status ffe_get_state(ffe_ctx* c, double** U_dev, unsigned char** mask_dev) try {
     if (!c) return fail(FFE_EINVAL, "null context");
     if (U_dev) *U_dev = c->un.p;
     if (mask_dev) *mask_dev = c->d.mask;
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
 namespace {
@@ -1603,7 +1652,7 @@ ffe_status check_mask(ffe_ctx* c, const unsigned char* m) {
 }
 }  // namespace
 
-ffe_status ffe_set_state(ffe_ctx* c, const double* U_dev, const unsigned char* mask_dev) {
+ffe_status ffe_set_state(ffe_ctx* c, const double* U_dev, const unsigned char* mask_dev) try {
     if (!c) return fail(FFE_EINVAL, "null context");
     const Dev& d = c->d;
     if (mask_dev) {
@@ -1616,18 +1665,22 @@ ffe_status ffe_set_state(ffe_ctx* c, const double* U_dev, const unsigned char* m
     if (U_dev) CK(cudaMemcpyAsync(c->un.p, U_dev, NV * (d.ndg + d.nfd) * 8, cudaMemcpyDeviceToDevice, c->st));
     if (mask_dev) CK(cudaMemcpyAsync(d.mask, mask_dev, d.E, cudaMemcpyDeviceToDevice, c->st));
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_download(ffe_ctx* c, double* U_host, unsigned char* mask_host) {
+ffe_status ffe_download(ffe_ctx* c, double* U_host, unsigned char* mask_host) try {
     if (!c) return fail(FFE_EINVAL, "null context");
     const Dev& d = c->d;
     if (U_host) CK(cudaMemcpyAsync(U_host, c->un.p, NV * (d.ndg + d.nfd) * 8, cudaMemcpyDeviceToHost, c->st));
     if (mask_host) CK(cudaMemcpyAsync(mask_host, d.mask, d.E, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_upload(ffe_ctx* c, const double* U_host, const unsigned char* mask_host) {
+ffe_status ffe_upload(ffe_ctx* c, const double* U_host, const unsigned char* mask_host) try {
     if (!c) return fail(FFE_EINVAL, "null context");
     const Dev& d = c->d;
     ffe_status s;
@@ -1635,9 +1688,11 @@ ffe_status ffe_upload(ffe_ctx* c, const double* U_host, const unsigned char* mas
     if (U_host) CK(cudaMemcpyAsync(c->un.p, U_host, NV * (d.ndg + d.nfd) * 8, cudaMemcpyHostToDevice, c->st));
     if (mask_host) CK(cudaMemcpyAsync(d.mask, mask_host, d.E, cudaMemcpyHostToDevice, c->st));
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_get_info(ffe_ctx* c, ffe_info* info) {
+ffe_status ffe_get_info(ffe_ctx* c, ffe_info* info) try {
     if (!c || !info) return fail(FFE_EINVAL, "null argument");
     const Dev& d = c->d;
     info->n_elem = d.E;
@@ -1663,24 +1718,30 @@ ffe_status ffe_get_info(ffe_ctx* c, ffe_info* info) {
     info->fd_elem_updates = (int64_t)u[1];
     info->dg_elem_updates = (int64_t)u[2];
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_get_status(ffe_ctx* c, int* bits) {
+ffe_status ffe_get_status(ffe_ctx* c, int* bits) try {
     if (!c || !bits) return fail(FFE_EINVAL, "null argument");
     CK(cudaMemcpyAsync(bits, c->d.counts + 4, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemsetAsync(c->d.counts + 4, 0, sizeof(int), c->st));
     CK(cudaStreamSynchronize(c->st));
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_tci_ratio(ffe_ctx* c, const double* U_dev, double* ratio_dev) {
+ffe_status ffe_tci_ratio(ffe_ctx* c, const double* U_dev, double* ratio_dev) try {
     if (!c || !U_dev || !ratio_dev) return fail(FFE_EINVAL, "null argument");
     launch_tci_ratio(c->d, U_dev, ratio_dev, c->st);
     CK(cudaGetLastError());
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_near_threshold(ffe_ctx* c, int* idx, int cap, int* n) {
+ffe_status ffe_near_threshold(ffe_ctx* c, int* idx, int cap, int* n) try {
     if (!c || !n || (cap > 0 && !idx)) return fail(FFE_EINVAL, "bad argument");
     int cnt = 0;
     CK(cudaMemcpyAsync(&cnt, c->d.counts + 3, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1690,15 +1751,19 @@ ffe_status ffe_near_threshold(ffe_ctx* c, int* idx, int cap, int* n) {
     if (cap > 0 && cnt > 0)
         CK(cudaMemcpy(idx, c->d.near_list, (size_t)(cnt < cap ? cnt : cap) * sizeof(int), cudaMemcpyDeviceToHost));
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_launch_count(ffe_ctx* c, int64_t* n) {
+ffe_status ffe_launch_count(ffe_ctx* c, int64_t* n) try {
     if (!c || !n) return fail(FFE_EINVAL, "null argument");
     *n = g_launch_counter;
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_freeze_mask(ffe_ctx* c, int on) {
+ffe_status ffe_freeze_mask(ffe_ctx* c, int on) try {
     g_err.clear();
     if (!c) return fail(FFE_EINVAL, "null context");
     CK(cudaStreamSynchronize(c->st));
@@ -1711,6 +1776,8 @@ ffe_status ffe_freeze_mask(ffe_ctx* c, int on) {
         c->graph = nullptr;
     }
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
 static ffe_status adjoint_ready(ffe_ctx* c) {
@@ -1775,7 +1842,7 @@ static void rhs_vjp_at(ffe_ctx* c, Field U, Field L, Field out) {
     }
 }
 
-ffe_status ffe_rhs_vjp(ffe_ctx* c, const double* U_dev, const double* lam_dev, double* out_dev, double* omega_bar) {
+ffe_status ffe_rhs_vjp(ffe_ctx* c, const double* U_dev, const double* lam_dev, double* out_dev, double* omega_bar) try {
     g_err.clear();
     if (!c || !U_dev || !lam_dev || !out_dev) return fail(FFE_EINVAL, "null argument");
     ffe_status s;
@@ -1794,6 +1861,8 @@ ffe_status ffe_rhs_vjp(ffe_ctx* c, const double* U_dev, const double* lam_dev, d
     }
     CK(cudaGetLastError());
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
 // Forward recomputation of a step's stages from U_n (a.un): stage s = 3, 4 is
@@ -1869,7 +1938,7 @@ static void point_stages(const Dev& d, AdjArgs& a, double* stages) {
 }
 
 ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_in_dev, double* lam_out_dev,
-                            double* omega_bar) {
+                            double* omega_bar) try {
     g_err.clear();
     if (!c || !U_dev || !lam_in_dev || !lam_out_dev) return fail(FFE_EINVAL, "null argument");
     ffe_status s;
@@ -1881,9 +1950,11 @@ ffe_status ffe_adjoint_step(ffe_ctx* c, const double* U_dev, const double* lam_i
     launch_build_lists(d, c->st);
     if ((s = adj_forward(c, a, nullptr))) return s;
     return adj_reverse(c, a, Field{(double*)lam_in_dev, NV, d.ndg, d.nfd}, omega_bar);
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_adjoint_forward(ffe_ctx* c, const double* U_dev, double* stages_dev, double* U_next_dev) {
+ffe_status ffe_adjoint_forward(ffe_ctx* c, const double* U_dev, double* stages_dev, double* U_next_dev) try {
     g_err.clear();
     if (!c || !U_dev) return fail(FFE_EINVAL, "null argument");
     if (U_next_dev == U_dev) return fail(FFE_EINVAL, "U_next must not alias U");
@@ -1898,10 +1969,12 @@ ffe_status ffe_adjoint_forward(ffe_ctx* c, const double* U_dev, double* stages_d
     if ((s = adj_forward(c, a, U_next_dev ? &next : nullptr))) return s;
     CK(cudaGetLastError());
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
 ffe_status ffe_adjoint_reverse(ffe_ctx* c, const double* U_dev, const double* stages_dev, const double* lam_in_dev,
-                               double* lam_out_dev, double* omega_bar) {
+                               double* lam_out_dev, double* omega_bar) try {
     g_err.clear();
     if (!c || !U_dev || !stages_dev || !lam_in_dev || !lam_out_dev) return fail(FFE_EINVAL, "null argument");
     ffe_status s;
@@ -1920,10 +1993,12 @@ ffe_status ffe_adjoint_reverse(ffe_ctx* c, const double* U_dev, const double* st
         point_stages(d, a, (double*)stages_dev);
     }
     return adj_reverse(c, a, Field{(double*)lam_in_dev, NV, d.ndg, d.nfd}, omega_bar);
+} catch (...) {
+    return host_failure();
 }
 
 ffe_status ffe_luminosity(ffe_ctx* c, const double* U_dev, double r_L, double* L_host, double* grad_dev,
-                          double scale) {
+                          double scale) try {
     g_err.clear();
     if (!c || !U_dev) return fail(FFE_EINVAL, "null argument");
     const Dev& d = c->d;
@@ -2007,9 +2082,11 @@ ffe_status ffe_luminosity(ffe_ctx* c, const double* U_dev, double r_L, double* L
     }
     CK(cudaGetLastError());
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_initial_tangent(ffe_ctx* c, int which, double* dU_dev) {
+ffe_status ffe_initial_tangent(ffe_ctx* c, int which, double* dU_dev) try {
     g_err.clear();
     if (!c || !dU_dev) return fail(FFE_EINVAL, "null argument");
     if (c->id_kind != FFE_ID_DIPOLE || c->batch) return fail(FFE_ENOTIMPL, "tangents are built for the dipole data");
@@ -2057,18 +2134,22 @@ ffe_status ffe_initial_tangent(ffe_ctx* c, int which, double* dU_dev) {
     });
     CK(cudaMemcpy(dU_dev, T.data(), T.size() * 8, cudaMemcpyHostToDevice));
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_set_profiling(ffe_ctx* c, int on) {
+ffe_status ffe_set_profiling(ffe_ctx* c, int on) try {
     if (!c) return fail(FFE_EINVAL, "null context");
     CK(cudaStreamSynchronize(c->st));
     g_prof.on = on != 0;
     g_prof.pending.clear();
     g_prof.used = 0;
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
-ffe_status ffe_profile_read(ffe_ctx* c, char* buf, size_t cap) {
+ffe_status ffe_profile_read(ffe_ctx* c, char* buf, size_t cap) try {
     if (!c || !buf || cap == 0) return fail(FFE_EINVAL, "bad argument");
     std::string js = "{";
     for (size_t i = 0; i < g_prof.totals.size(); ++i) {
@@ -2081,6 +2162,8 @@ ffe_status ffe_profile_read(ffe_ctx* c, char* buf, size_t cap) {
     g_prof.totals.clear();
     snprintf(buf, cap, "%s", js.c_str());
     return FFE_OK;
+} catch (...) {
+    return host_failure();
 }
 
 void ffe_destroy(ffe_ctx* c) {
