@@ -248,7 +248,10 @@ ffe_status ffe_profile_read(ffe_ctx* ctx, char* buf, size_t cap);
  * in one fixed device array of 2^20 doubles (8 MiB) that every GPU loading the
  * library holds until exit; calls needing more (per element 3 (2P+7)^3 +
  * 27 (2P+2)(2P+1)^2 doubles, e.g. at most 19 elements at P = 5) are rejected
- * with FFE_EINVAL.  The first call on a device looks up the array's device
+ * with FFE_EINVAL, as are P outside [3, 6], n_elem < 0, NULL buffers, widths that
+ * are not positive and finite, eta < 0 or weno_eps <= 0 (non-finite values
+ * included); these checks make no CUDA call, and n_elem = 0 returns FFE_OK
+ * without one.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current, so make it before
  * any stream capture.  All calls share the array and each overwrites every
  * entry it reads (nothing needs clearing), so calls that overlap on the GPU

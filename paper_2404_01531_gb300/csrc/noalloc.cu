@@ -10,6 +10,7 @@
 // extended cell and the face fluxes) in one file-scope device array of fixed
 // size, FFE_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB).  Every GPU that loads the
 // library holds that array until the process exits.
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 
@@ -151,10 +152,14 @@ extern "C" ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host
         return FFE_EINVAL;
     }
     for (int k = 0; k < 3; ++k)
-        if (!(h_host[k] > 0.0)) {
-            ffe::set_last_error("ffe_fd_rhs_noalloc: element widths must be positive");
+        if (!(h_host[k] > 0.0) || !std::isfinite(h_host[k])) {
+            ffe::set_last_error("ffe_fd_rhs_noalloc: element widths must be positive and finite");
             return FFE_EINVAL;
         }
+    if (!(eta >= 0.0) || !std::isfinite(eta) || !(weno_eps > 0.0) || !std::isfinite(weno_eps)) {
+        ffe::set_last_error("ffe_fd_rhs_noalloc: need finite eta >= 0 and weno_eps > 0");
+        return FFE_EINVAL;
+    }
     const int nc = 2 * P + 1, ne = nc + 2 * GH;
     const long long per_elem = 3LL * ne * ne * ne + 3LL * NV * (nc + 1) * nc * nc;
     const long long cap = kScratchDoubles / per_elem;

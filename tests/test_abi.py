@@ -188,3 +188,28 @@ def test_workload_configurations_pass_the_host_checks(lib_path):
     assert st != 1, lib.ffe_last_error()
     if st == 0:
         lib.ffe_destroy(h)
+
+
+def test_fd_rhs_noalloc_argument_checks(lib_path):
+    """ffe_fd_rhs_noalloc rejects bad orders, counts, widths, parameters and
+    NULL buffers (and over-sized calls) before any CUDA call; n_elem = 0 is a
+    no-op.  Runs without a GPU."""
+    import ctypes
+    from paper_2404_01531_gb300 import ffe
+    lib = ffe.load()
+    h = (ctypes.c_double * 3)(0.5, 0.5, 0.5)
+    buf = ctypes.c_void_p(16)   # never dereferenced: every case below fails before a launch
+
+    def call(P=5, n=1, hh=h, eta=0.0, eps=1e-40, U=buf, out=buf):
+        return lib.ffe_fd_rhs_noalloc(P, n, hh, eta, eps, 1, U, out, None), lib.ffe_last_error().decode()
+
+    nan = float("nan")
+    cases = [dict(P=2), dict(P=7), dict(n=-1), dict(hh=None), dict(U=None), dict(out=None),
+             dict(hh=(ctypes.c_double * 3)(0.5, 0.0, 0.5)), dict(hh=(ctypes.c_double * 3)(0.5, nan, 0.5)),
+             dict(hh=(ctypes.c_double * 3)(float("inf"), 0.5, 0.5)), dict(eta=-1.0), dict(eta=nan),
+             dict(eps=0.0), dict(eps=nan), dict(n=1000)]
+    for kw in cases:
+        st, msg = call(**kw)
+        assert st == 1, (kw, st, msg)
+        assert msg.startswith("ffe_fd_rhs_noalloc"), msg
+    assert call(n=0, U=None, out=None)[0] == 0
