@@ -3,6 +3,7 @@ App. B, App. C) against closed forms, identities and convergence."""
 import math
 
 import numpy as np
+import pytest
 
 import ffe_workloads as W
 from oracle import initial
@@ -118,3 +119,60 @@ def test_wald_stationarity_converges():
         st = pr.initial_state()
         res.append(np.abs(rhs_dg(st, pr.disc, pr.met, pr.prm)[:8]).max())
     assert res[1] < 2e-3 and res[0] / res[1] > 5, res
+
+
+@pytest.fixture(scope="module")
+def wald_fd_residuals():
+    """The FD right-hand side of the exact (stationary) Wald field, every
+    element on FD subcells, P = 5, on two shells (1 x 1 x 2 and 2 x 2 x 4
+    elements per wedge): max |dU/dt| over element interiors (3 cells from every
+    face) and over the face-centre cells next to radial-boundary faces, faces
+    between elements of one wedge, and faces between wedges."""
+    import warnings
+    from oracle.fd import rhs_fd
+    out = []
+    for na, nr in ((1, 2), (2, 4)):
+        cfg = W.wald(n_ang=na, n_rad=nr, P=5, r_in=2.0, r_out=6.0)
+        cfg["params"]["fd_corrector"] = 0
+        pr = Problem(cfg)
+        st = pr.initial_state(via_fd=True)
+        st["mask"][:] = 1
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")   # metric at the never-read corner ghost cells
+            r = np.abs(rhs_fd(st, pr.disc, pr.met, pr.prm)[:8]).max(axis=0)
+        d, Nc = pr.disc, pr.T.nc
+        cen = d.xyz_fd.mean(axis=(2, 3, 4))
+        wedge = [(int(np.argmax(np.abs(cen[:, e]))), bool(cen[np.argmax(np.abs(cen[:, e])), e] > 0)) for e in range(d.E)]
+        res = {"interior": r[:, 3:Nc - 3, 3:Nc - 3, 3:Nc - 3].max(), "boundary": 0.0, "wedge": 0.0, "between_wedges": 0.0}
+        for e in range(d.E):
+            for f in range(6):
+                ax = 2 - f // 2
+                idx = [slice(3, Nc - 3)] * 3
+                idx[ax] = slice(0, 1) if f % 2 == 0 else slice(Nc - 1, Nc)
+                nb = d.nbr[e, f]
+                k = "boundary" if nb < 0 else ("wedge" if wedge[nb] == wedge[e] else "between_wedges")
+                res[k] = max(res[k], r[e][tuple(idx)].max())
+        out.append(res)
+    return out
+
+
+def test_fd_wald_residual_converges_within_wedges(wald_fd_residuals):
+    """The metric-general FD operator (Sec. III.C.2 on the Kerr-Schild
+    background, a = 0.9) is consistent inside the wedges: the residual of the
+    exact stationary field falls under refinement in element interiors and at
+    the radial boundaries (ghosts from the exact field)."""
+    c, f = wald_fd_residuals
+    assert f["interior"] < c["interior"] / 4, (c, f)
+    assert f["boundary"] < c["boundary"] / 4, (c, f)
+    assert f["wedge"] < 2e-3, (c, f)
+
+
+@pytest.mark.xfail(strict=True, reason="ghost cells across cubed-sphere wedge boundaries are the neighbour "
+                                       "wedge's own cells, not values on the extension of the local grid")
+def test_fd_wald_residual_converges_between_wedges(wald_fd_residuals):
+    """At faces between wedges the neighbour's cells do not continue the local
+    grid lines, and copying them as ghosts is inconsistent: the residual there
+    does not fall under refinement (1.7e-2 -> 3.0e-2).  Interpolating the
+    neighbour's data to the local grid's ghost centres would make it fall."""
+    c, f = wald_fd_residuals
+    assert f["between_wedges"] < c["between_wedges"] / 4, (c, f)
