@@ -24,6 +24,10 @@ checked only by GPU-vs-oracle agreement, conservation and convergence):
     current, a reading); the exterior state there (`dg.external_dg_state` with
     an FD neighbour, `fd.fill_ghosts` with a DG neighbour) is pinned by the
     exactness of the mixed DG/FD right-hand side on linear fields.
+FD ghosts across a neighbour's face: copied from its cells (the default, the
+reading the CUDA path implements) or, with prm["ghost_interp"], interpolated to
+this element's grid extension; only the latter converges between cubed-sphere
+wedges (tests/test_oracle_curved.py).
 The rollback bookkeeping of a substep redone on FD (`stepper`) is pinned the
 same way: on fields linear in x a step with switches after substeps A, B and C
 equals the step without them.

@@ -108,6 +108,48 @@ def reconstruct(v, prm):
     return weno5z(v[0], v[1], v[2], v[3], v[4], eps), weno5z(v[5], v[4], v[3], v[2], v[1], eps)
 
 
+def _lagrange_weights(nodes, t):
+    """w[..., m]: the Lagrange basis through `nodes` (last axis) evaluated at t
+    (the shape of nodes without its last axis, or broadcastable to it)."""
+    n = nodes.shape[-1]
+    t = np.asarray(t)[..., None]
+    w = np.ones(np.broadcast_shapes(t.shape[:-1], nodes.shape[:-1]) + (n,))
+    for m in range(n):
+        for k in range(n):
+            if k != m:
+                w[..., m] *= (t[..., 0] - nodes[..., k]) / (nodes[..., m] - nodes[..., k])
+    return w
+
+
+def _interp_dg(u, xi, x_lgl):
+    """The nodal polynomial u (q, k, j, i) of an element at reference points
+    xi (3, npts): tensor Lagrange interpolation at its LGL nodes."""
+    L = [_lagrange_weights(x_lgl, xi[d]) for d in range(3)]    # (npts, P+1) each
+    return np.einsum('pa,pb,pc,qcba->qp', L[0], L[1], L[2], u)
+
+
+def _interp_fd(u, xi, xc, npt=6):
+    """Cell values u (q, z, y, x) of an FD element at reference points xi
+    (3, npts): tensor Lagrange interpolation through the `npt` cell centres
+    nearest each point along every axis (sixth order for npt = 6), the stencil
+    kept inside the element."""
+    Nc = len(xc)
+    dxi = 2.0 / Nc
+    starts, ws = [], []
+    for d in range(3):
+        pos = (xi[d] + 1.0) / dxi - 0.5
+        st0 = np.clip(np.floor(pos).astype(np.int64) - (npt // 2 - 1), 0, Nc - npt)
+        nodes = xc[st0[:, None] + np.arange(npt)[None, :]]
+        starts.append(st0)
+        ws.append(_lagrange_weights(nodes, xi[d]))
+    a = np.arange(npt)
+    iz = (starts[2][:, None] + a)[:, :, None, None]
+    iy = (starts[1][:, None] + a)[:, None, :, None]
+    ix = (starts[0][:, None] + a)[:, None, None, :]
+    g = u[:, iz, iy, ix]                                        # (q, npts, c, b, a)
+    return np.einsum('pa,pb,pc,qpcba->qp', ws[0], ws[1], ws[2], g)
+
+
 def fill_ghosts(st, disc, sel, met_fn, prm):
     """Extended cell arrays (9, n, Nc+6, Nc+6, Nc+6) for FD elements `sel`, the
     coordinates of every filled cell (for the metric), and the current J~ of the
@@ -115,7 +157,16 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
     regions are never read by the dimension-split scheme and stay NaN.
     [reading] A DG neighbour's ghost cells take its polynomial at its subcell
     centres for U and, for J~, the same evaluation of its nodal current (not the
-    current of the evaluated state; see dg.external_fd_current)."""
+    current of the evaluated state; see dg.external_fd_current).
+    prm["ghost_interp"] (default off, the reading the CUDA path implements):
+    ghosts across a neighbour's face are the neighbour's data at the ghost
+    centres of this element's grid extended past the face -- a DG neighbour's
+    polynomial evaluated there, an FD neighbour's cells interpolated there
+    (6-point tensor Lagrange in its reference coordinates, the paper's
+    sixth-order transfer, Sec. III.C.1).  Where the grids continue each other
+    (inside a cubed-sphere wedge, on boxes) both readings give the same
+    ghosts up to rounding; between wedges only the interpolated ghosts are
+    consistent."""
     T = disc.T
     Nc = T.nc
     n = len(sel)
@@ -136,7 +187,18 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
                 idx = [slice(NG, NG + Nc)] * 3
                 idx[2 - d] = pos
                 tgt = (slice(None), a) + tuple(idx)
-                if nb >= 0:
+                if nb >= 0 and prm.get("ghost_interp", False):
+                    gx = _ghost_centres(disc, e, d, s, g, dxi)
+                    xi_nb = disc.mesh.inv_map(nb, gx.reshape(3, -1) - disc.mesh.period_shift(e, f)[:, None])
+                    if st["mask"][nb] == FD:
+                        ext[tgt] = _interp_fd(st["ufd"][:, nb], xi_nb, T.xc).reshape(ext[tgt].shape)
+                    else:
+                        ext[tgt] = _interp_dg(st["udg"][:, nb], xi_nb, T.x).reshape(ext[tgt].shape)
+                        m = _met_at(met_fn["dg"], np.array([nb]), ())
+                        jd, jp = ph.current(st["udg"][:, nb:nb + 1], m, prm["eta"])
+                        jgh[(slice(None),) + tgt[1:]] = _interp_dg((jd + jp)[:, 0], xi_nb, T.x).reshape((3,) + ext[tgt].shape[1:])
+                    xyz[tgt] = gx
+                elif nb >= 0:
                     src = st["ufd"][:, nb] if st["mask"][nb] == FD else apply_3d(T.P, st["udg"][:, nb])
                     ext[tgt] = src.reshape(9, -1)[:, disc.fd_map[e, f, g]]
                     if st["mask"][nb] == DG:
@@ -147,13 +209,8 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
                     xyz[tgt] = disc.xyz_fd[:, nb].reshape(3, -1)[:, disc.fd_map[e, f, g]]
                 else:
                     # ghost centre from the element map continued past the face
-                    xi_n = -(1 + (g + 0.5) * dxi) if s == 0 else 1 + (g + 0.5) * dxi
-                    Z, Y, X = np.meshgrid(T.xc, T.xc, T.xc, indexing="ij")
-                    pts = np.stack([X, Y, Z])
                     lay = layer_slice(d, s, Nc, 0)
-                    pts = pts[(slice(None),) + lay].copy()
-                    pts[d] = xi_n
-                    gx = disc.mesh.map(e, pts)
+                    gx = _ghost_centres(disc, e, d, s, g, dxi)
                     xyz[tgt] = gx
                     outer = st["ufd"][:, e][(slice(None),) + lay]
                     if kind == BC_DIRICHLET:
@@ -171,6 +228,19 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
                     else:
                         raise ValueError("face without neighbour or boundary condition")
     return ext, xyz, jgh
+
+
+def _ghost_centres(disc, e, d, s, g, dxi):
+    """Physical centres (3, Nc, Nc) of ghost layer g past face (d, s) of element
+    e: its reference grid continued past the face, mapped by its own map."""
+    T = disc.T
+    Nc = T.nc
+    xi_n = -(1 + (g + 0.5) * dxi) if s == 0 else 1 + (g + 0.5) * dxi
+    Z, Y, X = np.meshgrid(T.xc, T.xc, T.xc, indexing="ij")
+    pts = np.stack([X, Y, Z])
+    pts = pts[(slice(None),) + layer_slice(d, s, Nc, 0)].copy()
+    pts[d] = xi_n
+    return disc.mesh.map(e, pts)
 
 
 def rhs_fd(st, disc, met, prm):

@@ -60,6 +60,11 @@ class BoxMesh:
             out.append(self.lo[d] + (c[d] + 0.5 * (xi[d] + 1.0)) * self.h[d])
         return np.stack(out)
 
+    def inv_map(self, e, x):
+        """xi(x) for element e (the affine map inverted); x is (3, ...)."""
+        c = np.asarray(self.eidx(e))
+        return np.stack([2.0 * ((x[d] - self.lo[d]) / self.h[d] - c[d]) - 1.0 for d in range(3)])
+
     def inv_jac(self, e, xi):
         """d xi^k / d x^j = diag(2/h)."""
         shape = np.shape(xi)[1:]
@@ -240,6 +245,26 @@ class ShellMesh:
         out[t1] = r * X / rho
         out[t2] = r * Y / rho
         return np.stack(out)
+
+    def inv_map(self, e, x):
+        """xi(x) for element e, the map above inverted in closed form: in the
+        element's wedge X = x_t1 / (sigma x_n), Y = x_t2 / (sigma x_n),
+        eta_a = (4/pi) atan X, eta_b = (4/pi) atan Y,
+        eta_r = 2 log(r / r_in) / log(r_out / r_in) - 1, then the element's
+        affine piece of the logical cube.  Valid wherever sigma x_n > 0 (within
+        45 degrees of the wedge axis and somewhat beyond)."""
+        ia, ib, ir, w = self.eidx(e)
+        n_ax, sg = WEDGES[w]
+        t1, t2 = (n_ax + 1) % 3, (n_ax + 2) % 3
+        xn = sg * x[n_ax]
+        ea = 4.0 / np.pi * np.arctan(x[t1] / xn)
+        eb = 4.0 / np.pi * np.arctan(x[t2] / xn)
+        r = np.sqrt(x[0] ** 2 + x[1] ** 2 + x[2] ** 2)
+        er = 2.0 * np.log(r / self.r_in) / np.log(self.r_out / self.r_in) - 1.0
+        xi0 = 2.0 * ((ea + 1.0) * self.na / 2.0 - ia) - 1.0
+        xi1 = 2.0 * ((eb + 1.0) * self.na / 2.0 - ib) - 1.0
+        xi2 = 2.0 * ((er + 1.0) * self.nr / 2.0 - ir) - 1.0
+        return np.stack([xi0, xi1, xi2])
 
     def inv_jac(self, e, xi):
         J = complex_step_jacobian(lambda p: self.map(e, p), xi)
