@@ -105,3 +105,18 @@ def test_lbar_forward_matches(monkeypatch):
     ctx = FakeContext()
     L_ref, _ = forward_mode(ctx, 4)
     assert adjoint.lbar_forward(ctx, 4) == pytest.approx(L_ref, rel=1e-13)
+
+
+def test_autograd_step_wiring():
+    """adjoint.Step: forward = one step of the context from U, backward = the
+    step adjoint at the saved input U (not at the output)."""
+    from paper_2404_01531_gb300 import adjoint
+    ctx = FakeContext()
+    U = ctx.initial().clone().requires_grad_(True)
+    out = adjoint.Step.apply(U, ctx)
+    assert torch.allclose(out, ctx.f(U.detach()))
+    w = torch.linspace(-1.0, 1.0, U.numel(), dtype=torch.float64)
+    (out * w).sum().backward()
+    z = ctx.A @ U.detach()
+    want = ctx.A.T @ ((1.0 - torch.tanh(z) ** 2) * w)
+    assert torch.allclose(U.grad, want, rtol=1e-14, atol=1e-15)
