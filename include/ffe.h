@@ -234,16 +234,20 @@ ffe_status ffe_profile_read(ffe_ctx* ctx, char* buf, size_t cap);
 
 /* FD-subcell right-hand side that allocates no memory.  The paper has no
  * counterpart: this is a service for callers that cannot call cudaMalloc --
- * code running inside a CUDA-graph capture, hosts that own all device memory
- * and forbid allocations behind their back, latency-critical paths where an
- * allocation would stall.  ffe_create allocates a whole context, so those
- * callers cannot reach ffe_rhs; this entry point computes the same explicit
- * FD right-hand side (flat metric, affine element of widths h_host[0..2])
- * from caller-owned buffers:
+ * host applications that own all device memory and forbid allocations behind
+ * their back, latency-critical paths where an allocation would stall.
+ * ffe_create allocates a whole context, so those callers cannot reach
+ * ffe_rhs; this entry point computes the explicit FD right-hand side (flat
+ * metric, affine element of widths h_host[0..2]) of caller-built extended
+ * blocks from caller-owned buffers:
  *   Uext_dev  [9][n_elem][(2P+7)^3]  the 9 evolved variables on each element's
  *             (2P+1)^3 subcells plus 3 ghost layers on every face (edge and
  *             corner ghost regions are never read), x fastest;
  *   dUdt_dev  [9][n_elem][(2P+1)^3]  output, same cell order as the FD block.
+ * The current J~ of every cell, ghosts included, is computed from that cell's
+ * state.  This is what ffe_rhs does for ghosts that hold an FD neighbour's
+ * data or a boundary state; ghosts across a DG neighbour's face get that
+ * neighbour's nodal current from ffe_rhs instead, so for them the two differ.
  * Its intermediate data (J~ at every extended cell and the face fluxes) live
  * in one fixed device array of 2^20 doubles (8 MiB) that every GPU loading the
  * library holds until exit; calls needing more (per element 3 (2P+7)^3 +
@@ -251,11 +255,14 @@ ffe_status ffe_profile_read(ffe_ctx* ctx, char* buf, size_t cap);
  * with FFE_EINVAL, as are P outside [3, 6], n_elem < 0, NULL buffers, widths that
  * are not positive and finite, eta < 0 or weno_eps <= 0 (non-finite values
  * included); these checks make no CUDA call, and n_elem = 0 returns FFE_OK
- * without one.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current, so make it before
- * any stream capture.  All calls share the array and each overwrites every
- * entry it reads (nothing needs clearing), so calls that overlap on the GPU
- * (different streams, no ordering between them) race.  Enqueued on cuda_stream. */
+ * without one.  Devices 0 to 63 are served (FFE_EINVAL on a higher index).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process: after a cudaDeviceReset of that device the kept address is
+ * stale, so do not call this entry point again after such a reset.  All
+ * calls share the array and each overwrites every entry it reads (nothing
+ * needs clearing), so calls that overlap on the GPU (different streams, no
+ * ordering between them) race.  Enqueued on cuda_stream. */
 ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host, double eta, double weno_eps,
                               int fd_corrector, const double* Uext_dev, double* dUdt_dev, void* cuda_stream);
 
@@ -338,6 +345,38 @@ ffe_status ffe_load(ffe_ctx* ctx, const void* host_buf, size_t bytes);
  * max |E~.B~|, [1] = min (B~^2 - E~^2), [2] = max |psi~|, [3] = max |phi~|.
  * Synchronises the context stream. */
 ffe_status ffe_constraints(ffe_ctx* ctx, const double* U_dev, double* out_host);
+
+/* Borrowed device view of the DG/FD mask (uint8 per element, 0 = DG,
+ * 1 = FD; Sec. III.C.3) and, when n_elem is not NULL, the element count;
+ * valid until the context is destroyed, contents current after the context
+ * stream reaches the point of the call. */
+ffe_status ffe_get_mask(ffe_ctx* ctx, const unsigned char** mask_dev, int* n_elem);
+
+/* Same as ffe_freeze_mask (declared with the adjoint below): on != 0 replays
+ * the current mask, with no troubled-cell indicator and no switching, in
+ * every following step (the frozen-branch runs of finite-difference and
+ * complex-step checks); on = 0 restores the indicator setting of ffe_create. */
+ffe_status ffe_set_frozen_masks(ffe_ctx* ctx, int on);
+
+/* Diagnostics of the context's current state, written to out_host
+ * (synchronising the context stream):
+ *   FFE_DIAG_L2_ERR      the L2 error norm of Sec. IV.B.1 (Table II),
+ *                        L2 = sqrt((1/n) sum_k sum_v (U_v,k - R_v,k)^2) over the
+ *                        n points k (DG nodes of DG elements, subcells of FD
+ *                        elements) and the variables v0 <= v < v0 + nv, where
+ *                        R is the analytic initial data of ffe_set_initial at
+ *                        those points (the exact solution of a stationary
+ *                        problem such as the Wald field); args = {v0, nv}
+ *                        (NULL: {3, 3}, the magnetic field B~); out_host[0] = L2,
+ *                        out_host[1] = n.  FFE_ESTATE before ffe_set_initial.
+ *                        The reference is evaluated on the host and kept on the
+ *                        device until the mask or the initial data change; the
+ *                        sum is reduced on the device (deterministic).
+ *   FFE_DIAG_LUMINOSITY  args[0] = r_L: out_host[0] = the luminosity of
+ *                        ffe_luminosity through r = r_L (shells).
+ *   FFE_DIAG_CONSTRAINTS out_host[0..3] as ffe_constraints (flat metric). */
+enum { FFE_DIAG_L2_ERR = 0, FFE_DIAG_LUMINOSITY = 1, FFE_DIAG_CONSTRAINTS = 2 };
+ffe_status ffe_diagnostic(ffe_ctx* ctx, int kind, const double* args, double* out_host);
 
 /* Cartesian coordinates of the DG nodes [3][n_dg] and of the FD subcell
  * centres [3][n_fd] (every element's block, in state-vector order), copied

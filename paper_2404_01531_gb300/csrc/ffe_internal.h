@@ -68,6 +68,7 @@ struct Dev {
     // of their slot); uniform contexts have one order.
     int E, P, np1, nn, nc, ncell;
     int64_t ndg, nfd;
+    int nsm;                        // streaming multiprocessors of the device (launch shapes)
     const unsigned char* eP;        // [E] order of each element (null: all P)
     const int* einst;               // [E] instance of each element (null: one instance)
     const InstInfo* inst;           // [n_inst]
@@ -161,6 +162,7 @@ int fd_chunks(const Dev& d);
 void launch_fd_fill(const Dev& d, const int* list, int count_index, int w0, Field U, Field J, cudaStream_t st);
 void launch_eval_recip(const double* x, double* y, int64_t n, cudaStream_t st);
 void launch_constraints(const Dev& d, Field U, double* part, int blocks, cudaStream_t st);
+void launch_l2_err(const Dev& d, Field U, Field R, int v0, int nv, double* part, int blocks, cudaStream_t st);
 // out += (d RHS_FD/dU)^T L (kernels_adjoint_fd.cu); extb: scratch of the size of d.ext
 void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, double* extb, double* omega_bar,
                        cudaStream_t st);

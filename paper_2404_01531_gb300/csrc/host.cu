@@ -362,6 +362,10 @@ struct ffe_ctx {
     double* d_extb = nullptr;        // extended-block adjoint of one FD chunk
     double* d_omega_bar = nullptr;
     double* d_cons = nullptr;        // per-block partials of ffe_constraints
+    double* d_ref = nullptr;         // analytic initial data (reference of the L2 error), state layout
+    bool ref_valid = false;          // d_ref matches the current mask, FD slots and initial data
+    std::vector<unsigned char> ref_mask;
+    std::vector<int> ref_slot;
     double* d_partial = nullptr;
     // luminosity surface (cached per radius)
     double lum_r = -1.0;
@@ -732,7 +736,7 @@ ffe_status autotune(ffe_ctx* c) {
     if (!d.ks) launch_current(d, c->un, c->J, nullptr, 0, c->st);
     float best = 1e30f;
     int best_g = 0;
-    for (int g : {152, 304, 456, 608}) {
+    for (int g : {d.nsm, 2 * d.nsm, 3 * d.nsm, 4 * d.nsm}) {
         d.dg_grid = g;
         float tot = 0.0f;
         for (int rep = 0; rep < 3; ++rep) {
@@ -984,6 +988,62 @@ ffe_status set_initial_impl(ffe_ctx* c, int id_kind, bool keep_mask, bool via_fd
     CK(cudaMemset(d.units, 0, 3 * sizeof(unsigned long long)));
     c->t = 0.0;
     c->steps = 0;
+    c->ref_valid = false;
+    return FFE_OK;
+}
+
+
+// The analytic initial data of the context at the DG nodes of its DG elements
+// and the subcells of its FD elements (state-vector layout, in d_ref): the
+// exact solution of a stationary problem such as the Wald field.  Rebuilt
+// when the mask, the FD slots or the initial data changed since the last build.
+ffe_status build_reference(ffe_ctx* c) {
+    const Dev& d = c->d;
+    std::vector<unsigned char> mask(d.E);
+    std::vector<int> slot;
+    CK(cudaMemcpyAsync(mask.data(), d.mask, d.E, cudaMemcpyDeviceToHost, c->st));
+    if (d.fd_slot) {
+        slot.resize(d.E);
+        CK(cudaMemcpyAsync(slot.data(), d.fd_slot, d.E * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    if (c->ref_valid && mask == c->ref_mask && slot == c->ref_slot) return FFE_OK;
+    ffe_status s;
+    const size_t n = (size_t)NV * (d.ndg + d.nfd);
+    if (!c->d_ref && (s = dalloc(c, &c->d_ref, n))) return s;
+    auto prm_of = [&](int e) -> const double* {
+        return c->batch ? c->id_prm_inst.data() + (size_t)c->h_einst[e] * c->id_nprm : c->id_prm.data();
+    };
+    const int nprm = c->batch ? c->id_nprm : (int)c->id_prm.size();
+    std::vector<double> xdg(3 * (size_t)d.ndg), R(n, 0.0);
+    CK(cudaMemcpy(xdg.data(), d.xyz_dg, xdg.size() * 8, cudaMemcpyDeviceToHost));
+    parallel_for(d.ndg, [&](int64_t p) {
+        const int e = (int)(p / d.nn);
+        const int P = host_P(c, e);
+        if (mask[e] || (int)(p % d.nn) >= (P + 1) * (P + 1) * (P + 1)) return;
+        double X[3] = {xdg[p], xdg[d.ndg + p], xdg[2 * d.ndg + p]}, u[NV];
+        initial_point(c->id_kind, prm_of(e), nprm, X, u);
+        for (int v = 0; v < NV; ++v) R[v * d.ndg + p] = u[v];
+    });
+    MapFn map = ctx_map(c);
+    parallel_for(d.E, [&](int64_t e) {
+        if (!mask[e]) return;
+        const int P = host_P(c, (int)e), nc = 2 * P + 1;
+        const int64_t base = (int64_t)(d.fd_slot ? slot[e] : e) * d.ncell;
+        if (base < 0) return;
+        for (int q = 0; q < nc * nc * nc; ++q) {
+            const int cc[3] = {q % nc, (q / nc) % nc, q / (nc * nc)};
+            double xi[3], X[3], ij[3][3], u[NV];
+            for (int a = 0; a < 3; ++a) xi[a] = -1.0 + (cc[a] + 0.5) * 2.0 / nc;
+            map((int)e, xi, X, ij);
+            initial_point(c->id_kind, prm_of((int)e), nprm, X, u);
+            for (int v = 0; v < NV; ++v) R[NV * d.ndg + v * d.nfd + base + q] = u[v];
+        }
+    });
+    CK(cudaMemcpy(c->d_ref, R.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    c->ref_mask = mask;
+    c->ref_slot = slot;
+    c->ref_valid = true;
     return FFE_OK;
 }
 
@@ -1161,7 +1221,7 @@ ffe_status ffe_constraints(ffe_ctx* c, const double* U_dev, double* out_host) tr
     if (!c || !out_host) return fail(FFE_EINVAL, "null argument");
     const Dev& d = c->d;
     if (d.ks) return fail(FFE_ENOTIMPL, "constraint diagnostics are built for the flat metric");
-    const int blocks = 152 * 4;
+    const int blocks = d.nsm * 4;
     ffe_status s;
     if (!c->d_cons && (s = dalloc(c, &c->d_cons, 4 * (size_t)blocks))) return s;
     double* part = c->d_cons;
@@ -1179,6 +1239,60 @@ ffe_status ffe_constraints(ffe_ctx* c, const double* U_dev, double* out_host) tr
         out_host[2] = fmax(out_host[2], h[4 * b + 2]);
         out_host[3] = fmax(out_host[3], h[4 * b + 3]);
     }
+    return FFE_OK;
+} catch (...) {
+    return host_failure();
+}
+
+ffe_status ffe_get_mask(ffe_ctx* c, const unsigned char** mask_dev, int* n_elem) try {
+    g_err.clear();
+    if (!c || !mask_dev) return fail(FFE_EINVAL, "null argument");
+    *mask_dev = c->d.mask;
+    if (n_elem) *n_elem = c->d.E;
+    return FFE_OK;
+} catch (...) {
+    return host_failure();
+}
+
+ffe_status ffe_set_frozen_masks(ffe_ctx* c, int on) { return ffe_freeze_mask(c, on); }
+
+ffe_status ffe_diagnostic(ffe_ctx* c, int kind, const double* args, double* out_host) try {
+    g_err.clear();
+    if (!c || !out_host) return fail(FFE_EINVAL, "null argument");
+    const Dev& d = c->d;
+    if (kind == FFE_DIAG_CONSTRAINTS) return ffe_constraints(c, nullptr, out_host);
+    if (kind == FFE_DIAG_LUMINOSITY) {
+        if (!args) return fail(FFE_EINVAL, "the luminosity needs args[0] = r_L");
+        return ffe_luminosity(c, c->un.p, args[0], out_host, nullptr, 0.0);
+    }
+    if (kind != FFE_DIAG_L2_ERR) return fail(FFE_EINVAL, "diagnostic kind %d", kind);
+    int v0 = 3, nv = 3;
+    if (args) {
+        if (!(args[0] >= 0 && args[0] <= NV - 1 && args[1] >= 1 && args[0] + args[1] <= NV) ||
+            args[0] != std::floor(args[0]) || args[1] != std::floor(args[1]))
+            return fail(FFE_EINVAL, "L2 error: variables [%g, %g + %g) outside [0, 9)", args[0], args[0], args[1]);
+        v0 = (int)args[0];
+        nv = (int)args[1];
+    }
+    if (c->id_kind < 0) return fail(FFE_ESTATE, "L2 error: no initial data set");
+    ffe_status s;
+    if ((s = build_reference(c))) return s;
+    const int blocks = d.nsm * 4;
+    if (!c->d_cons && (s = dalloc(c, &c->d_cons, 4 * (size_t)blocks))) return s;
+    Field R{c->d_ref, NV, d.ndg, d.nfd};
+    launch_l2_err(d, c->un, R, v0, nv, c->d_cons, blocks, c->st);
+    std::vector<double> h(blocks);
+    CK(cudaMemcpyAsync(h.data(), c->d_cons, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double sum = 0.0;
+    for (double x : h) sum += x;
+    int64_t npts = 0;
+    for (int e = 0; e < d.E; ++e) {
+        const int P = host_P(c, e);
+        npts += c->ref_mask[e] ? (int64_t)(2 * P + 1) * (2 * P + 1) * (2 * P + 1) : (int64_t)(P + 1) * (P + 1) * (P + 1);
+    }
+    out_host[0] = std::sqrt(sum / (double)npts);
+    out_host[1] = (double)npts;
     return FFE_OK;
 } catch (...) {
     return host_failure();
@@ -1242,6 +1356,15 @@ ffe_status check_scheme(const ffe_params& p, const char* who) {
         return fail(FFE_EINVAL, "%s: WENO5-Z needs eps > 0", who);
     return FFE_OK;
 }
+// Streaming multiprocessors of the current device: launch shapes (persistent
+// grids, grid-stride loops) are multiples of it.
+ffe_status query_sms(ffe_ctx* c) {
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    c->d.nsm = nsm > 0 ? nsm : 1;
+    return FFE_OK;
+}
 }  // namespace
 
 ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, int P, const ffe_metric* metric,
@@ -1292,6 +1415,10 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     if (metric->kind == FFE_METRIC_KERR_SCHILD && !std::isfinite(metric->M)) return fail(FFE_EINVAL, "need a finite M");
 
     ffe_ctx* c = new ffe_ctx();
+    if (ffe_status sq = query_sms(c)) {
+        delete c;
+        return sq;
+    }
     c->dom = *domain;
     c->el = *elements;
     c->met = *metric;
@@ -1377,6 +1504,10 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
         if ((st0 = check_count(n_all, 5, "batch"))) return st0;
     }
     ffe_ctx* c = new ffe_ctx();
+    if (ffe_status sq = query_sms(c)) {
+        delete c;
+        return sq;
+    }
     auto bail = [&](ffe_status s) { ffe_destroy(c); return s; };
     c->batch = true;
     c->n_inst = n_inst;
@@ -2070,7 +2201,7 @@ ffe_status ffe_luminosity(ffe_ctx* c, const double* U_dev, double r_L, double* L
     }
     if (!c->d_partial && (s = dalloc(c, &c->d_partial, 1024))) return s;
     Field U{(double*)U_dev, NV, d.ndg, d.nfd}, G{grad_dev, NV, d.ndg, d.nfd};
-    const int nb = 152;
+    const int nb = d.nsm;
     launch_luminosity(d, U, c->d_lum_elem, c->d_lum_lk, c->d_lum_w, c->lum_ns, c->d_partial, nb, G, scale, c->st);
     if (L_host) {
         std::vector<double> part(nb);

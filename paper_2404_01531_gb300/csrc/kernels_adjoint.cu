@@ -262,7 +262,7 @@ void launch_rhs_vjp(const Dev& d, Field U, Field L, Field out, double* omega_bar
 #define FFE_VJP(PP)                                                                                        \
     case PP:                                                                                               \
         cudaFuncSetAttribute(k_rhs_vjp<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, AVJ<PP>::SMEM);  \
-        k_rhs_vjp<PP><<<152 * 2, AVJ<PP>::NT, AVJ<PP>::SMEM, st>>>(d, U, L, out, omega_bar);            \
+        k_rhs_vjp<PP><<<d.nsm * 2, AVJ<PP>::NT, AVJ<PP>::SMEM, st>>>(d, U, L, out, omega_bar);            \
         break;
         FFE_VJP(3)
         FFE_VJP(4)
@@ -308,7 +308,7 @@ __global__ void k_filter(Dev d, Field in, Field outf, int nv, int transpose) {
 
 void launch_filter(const Dev& d, Field in, Field out, int nv, int transpose, cudaStream_t st) {
     prof_begin("filter", st);
-    k_filter<<<152 * 4, 128, 2 * d.nn * sizeof(double), st>>>(d, in, out, nv, transpose);
+    k_filter<<<d.nsm * 4, 128, 2 * d.nn * sizeof(double), st>>>(d, in, out, nv, transpose);
     prof_end(st);
     g_launch_counter += 1;
 }
@@ -595,20 +595,20 @@ __global__ void k_adj_clamp_back(Dev d, Field X, Field yb, Field out) {
 
 void launch_adj_clamp(const Dev& d, Field io, cudaStream_t st) {
     prof_begin("adj_pointwise", st);
-    k_adj_clamp<<<152 * 8, 256, 0, st>>>(d, io);
+    k_adj_clamp<<<d.nsm * 8, 256, 0, st>>>(d, io);
     prof_end(st);
     g_launch_counter += 1;
 }
 
 void launch_adj_clamp_back(const Dev& d, Field X, Field yb, Field out, cudaStream_t st) {
     prof_begin("adj_pointwise", st);
-    k_adj_clamp_back<<<152 * 8, 256, 0, st>>>(d, X, yb, out);
+    k_adj_clamp_back<<<d.nsm * 8, 256, 0, st>>>(d, X, yb, out);
     prof_end(st);
     g_launch_counter += 1;
 }
 
 void launch_adj(const Dev& d, int which, AdjArgs a, int sub, cudaStream_t st) {
-    const int grid = 152 * 8;
+    const int grid = d.nsm * 8;
     prof_begin("adj_pointwise", st);
     switch (which) {
         case 0: k_adj_s12<<<grid, 256, 0, st>>>(d, a); break;
@@ -626,7 +626,7 @@ void launch_adj(const Dev& d, int which, AdjArgs a, int sub, cudaStream_t st) {
 
 void launch_adj_addG(const Dev& d, Field U, Field Gb, Field io, cudaStream_t st) {
     prof_begin("adj_pointwise", st);
-    k_adj_addG<<<152 * 8, 256, 0, st>>>(d, U, Gb, io);
+    k_adj_addG<<<d.nsm * 8, 256, 0, st>>>(d, U, Gb, io);
     prof_end(st);
     g_launch_counter += 1;
 }

@@ -316,9 +316,9 @@ void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, doubl
         const int w0 = k * d.chunk;
         launch_fd_fill(d, d.fd_list, 1, w0, U, J, st);
         cudaMemsetAsync(extb, 0, extb_bytes, st);
-        k_fdv_faces<<<152 * 8, 128, 0, st>>>(d, d.fd_list, 1, w0, L, extb);
-        k_fdv_cells<<<152 * 8, 256, 0, st>>>(d, d.fd_list, 1, w0, U, L, out, extb);
-        k_fdv_ghosts<<<152 * 2, 256, smem, st>>>(d, d.fd_list, 1, w0, U, J, out, extb, omega_bar);
+        k_fdv_faces<<<d.nsm * 8, 128, 0, st>>>(d, d.fd_list, 1, w0, L, extb);
+        k_fdv_cells<<<d.nsm * 8, 256, 0, st>>>(d, d.fd_list, 1, w0, U, L, out, extb);
+        k_fdv_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, d.fd_list, 1, w0, U, J, out, extb, omega_bar);
         g_launch_counter += 3;
     }
     prof_end(st);

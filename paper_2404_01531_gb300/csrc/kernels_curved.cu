@@ -442,14 +442,14 @@ static void curved_launch(const Dev& d, const SubArgs& a, const int* list, int c
 
 template <int P, bool KS, int SUB>
 static void curved_dispatch_sub(const Dev& d, const SubArgs& a, cudaStream_t st) {
-    const int grid = d.dg_grid > 0 ? d.dg_grid : 152 * 2;
+    const int grid = d.dg_grid > 0 ? d.dg_grid : d.nsm * 2;
     curved_launch<P, KS, SUB>(d, a, d.dg_list, 0, grid, st);
     // batches: the elements of orders P-1 and P-2, each in CTAs sized for their order
     if constexpr (P > 3) {
-        if (d.dg_list_lo) curved_launch<P - 1, KS, SUB>(d, a, d.dg_list_lo, 6, 152 * 4, st);
+        if (d.dg_list_lo) curved_launch<P - 1, KS, SUB>(d, a, d.dg_list_lo, 6, d.nsm * 4, st);
     }
     if constexpr (P > 4) {
-        if (d.dg_list_lo2) curved_launch<P - 2, KS, SUB>(d, a, d.dg_list_lo2, 7, 152 * 4, st);
+        if (d.dg_list_lo2) curved_launch<P - 2, KS, SUB>(d, a, d.dg_list_lo2, 7, d.nsm * 4, st);
     }
 }
 
@@ -514,7 +514,7 @@ __global__ void k_stage12_ks(Dev d, Field un, Field Ua, Field G1, Field G2) {
 
 void launch_stage12_ks(const Dev& d, Field un, Field Ua, Field G1, Field G2, cudaStream_t st) {
     prof_begin("stage12", st);
-    k_stage12_ks<<<152 * 8, 256, 0, st>>>(d, un, Ua, G1, G2);
+    k_stage12_ks<<<d.nsm * 8, 256, 0, st>>>(d, un, Ua, G1, G2);
     prof_end(st);
     g_launch_counter += 1;
 }

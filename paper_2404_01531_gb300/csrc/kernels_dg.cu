@@ -93,7 +93,7 @@ __global__ void k_current(Dev d, Field U, Field J, const int* list, int count_in
 
 void launch_current(const Dev& d, Field U, Field J, const int* list, int count_index, cudaStream_t st) {
     prof_begin("current", st);
-    k_current<<<152 * 8, 256, 0, st>>>(d, U, J, list, count_index);
+    k_current<<<d.nsm * 8, 256, 0, st>>>(d, U, J, list, count_index);
     prof_end(st);
     g_launch_counter += 1;
 }
@@ -143,7 +143,7 @@ __global__ void k_stage12(Dev d, Field un, Field Ua, Field G1, Field G2) {
 
 void launch_stage12(const Dev& d, Field un, Field Ua, Field G1, Field G2, cudaStream_t st) {
     prof_begin("stage12", st);
-    k_stage12<<<152 * 8, 256, 0, st>>>(d, un, Ua, G1, G2);
+    k_stage12<<<d.nsm * 8, 256, 0, st>>>(d, un, Ua, G1, G2);
     prof_end(st);
     g_launch_counter += 1;
 }
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(DGK<P>::NT, 3) k_dg_substep(Dev d, SubArgs a) 
 template <int P>
 static void dg_sub_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_t st) {
     using K = DGK<P>;
-    const int grid = d.dg_grid > 0 ? d.dg_grid : 152 * 4;
+    const int grid = d.dg_grid > 0 ? d.dg_grid : d.nsm * 4;
     switch (sub) {
         case SUB_A:
             cudaFuncSetAttribute(k_dg_substep<P, SUB_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
@@ -520,7 +520,7 @@ __global__ void k_tci_ratio(Dev d, const double* Udg, double* ratio) {
 
 void launch_tci_ratio(const Dev& d, const double* Udg, double* ratio, cudaStream_t st) {
     prof_begin("tci_ratio", st);
-    k_tci_ratio<<<152 * 4, 128, 0, st>>>(d, Udg, ratio);
+    k_tci_ratio<<<d.nsm * 4, 128, 0, st>>>(d, Udg, ratio);
     prof_end(st);
     g_launch_counter += 1;
 }
@@ -571,6 +571,46 @@ __global__ void k_constraints(Dev d, Field U, double* part) {
 
 void launch_constraints(const Dev& d, Field U, double* part, int blocks, cudaStream_t st) {
     k_constraints<<<blocks, 256, 0, st>>>(d, U, part);
+    g_launch_counter += 1;
+}
+
+// L2 error norm of Sec. IV.B.1 (Table II), sum part: per block the sum over
+// the DG nodes of DG elements and the cells of FD elements of
+// sum_{v0 <= v < v0 + nv} (U_v - R_v)^2, accumulated per thread in index
+// order and reduced by a fixed tree (deterministic for a fixed grid).
+__global__ void k_l2_err(Dev d, Field U, Field R, int v0, int nv, double* part) {
+    __shared__ double sr[256];
+    double acc = 0.0;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = tid; p < d.ndg; p += stride) {
+        const int e = (int)(p / d.nn);
+        if (d.mask[e] == 0 && (int)(p % d.nn) < esz(d, e).nn)
+            for (int v = v0; v < v0 + nv; ++v) {
+                const double df = U.dg(v)[p] - R.dg(v)[p];
+                acc = fma(df, df, acc);
+            }
+    }
+    for (int64_t p = tid; p < d.nfd; p += stride) {
+        const int sl = (int)(p / d.ncell);
+        const int e = d.slot_elem ? d.slot_elem[sl] : sl;
+        if (e >= 0 && d.mask[e] == 1 && (int)(p % d.ncell) < esz(d, e).ncell)
+            for (int v = v0; v < v0 + nv; ++v) {
+                const double df = U.fd(v)[p] - R.fd(v)[p];
+                acc = fma(df, df, acc);
+            }
+    }
+    sr[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sr[threadIdx.x] += sr[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sr[0];
+}
+
+void launch_l2_err(const Dev& d, Field U, Field R, int v0, int nv, double* part, int blocks, cudaStream_t st) {
+    k_l2_err<<<blocks, 256, 0, st>>>(d, U, R, v0, nv, part);
     g_launch_counter += 1;
 }
 

@@ -373,22 +373,22 @@ static size_t ghost_smem(const Dev& d) {
 void launch_fd_fill(const Dev& d, const int* list, int ci, int w0, Field U, Field J, cudaStream_t st) {
     const size_t smem = ghost_smem(d);
     cudaFuncSetAttribute(k_fd_fill_ghosts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fd_fill_interior<<<152 * 8, 256, 0, st>>>(d, list, ci, w0, U, J);
-    k_fd_fill_ghosts<<<152 * 2, 256, smem, st>>>(d, list, ci, w0, U, J);
+    k_fd_fill_interior<<<d.nsm * 8, 256, 0, st>>>(d, list, ci, w0, U, J);
+    k_fd_fill_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, list, ci, w0, U, J);
     g_launch_counter += 2;
 }
 
 template <int SUB>
 static void launch_update(const Dev& d, const int* list, int ci, int w0, const SubArgs& a, cudaStream_t st) {
-    if (d.curved) k_fd_update<SUB, true><<<152 * 8, 256, 0, st>>>(d, list, ci, w0, a);
-    else k_fd_update<SUB, false><<<152 * 8, 256, 0, st>>>(d, list, ci, w0, a);
+    if (d.curved) k_fd_update<SUB, true><<<d.nsm * 8, 256, 0, st>>>(d, list, ci, w0, a);
+    else k_fd_update<SUB, false><<<d.nsm * 8, 256, 0, st>>>(d, list, ci, w0, a);
 }
 
 void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin, Field J, Field un, Field F2,
                        Field F3, Field G1, Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout,
                        cudaStream_t st) {
     SubArgs a{Uin, J, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
-    const int grid = 152 * 8;
+    const int grid = d.nsm * 8;
     const size_t smem = ghost_smem(d);
     cudaFuncSetAttribute(k_fd_fill_ghosts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int k = 0, nch = fd_chunks(d); k < nch; ++k) {
@@ -397,7 +397,7 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin
         k_fd_fill_interior<<<grid, 256, 0, st>>>(d, list, ci, w0, Uin, J);
         prof_end(st);
         prof_begin("fd_fill_ghosts", st);
-        k_fd_fill_ghosts<<<152 * 2, 256, smem, st>>>(d, list, ci, w0, Uin, J);
+        k_fd_fill_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, list, ci, w0, Uin, J);
         prof_end(st);
         prof_begin("fd_flux", st);
         if (d.recon == FFE_RECON_MP5) {
@@ -512,7 +512,7 @@ void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F
     const int np1 = d.np1, nn = d.nn, nc = d.nc;
     const size_t smem = (size_t)(nn + nc * np1 * np1 + nc * nc * np1) * sizeof(double);
     prof_begin("rollback_project", st);
-    k_rollback_project<<<152, 256, smem, st>>>(d, r);
+    k_rollback_project<<<d.nsm, 256, smem, st>>>(d, r);
     prof_end(st);
     g_launch_counter += 1;
 }
@@ -638,7 +638,7 @@ void launch_fd2dg(const Dev& d, Field un, cudaStream_t st) {
     const size_t smem = (size_t)(d.ncell + nc * nc * np1 + nc * np1 * np1 + NV * nn + 3 * nn + 2 * 256) * sizeof(double);
     cudaFuncSetAttribute(k_fd2dg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin("fd2dg", st);
-    k_fd2dg<<<152, 256, smem, st>>>(d, un);
+    k_fd2dg<<<d.nsm, 256, smem, st>>>(d, un);
     prof_end(st);
     g_launch_counter += 1;
 }
@@ -652,7 +652,12 @@ __global__ void k_eval_recip(const double* x, double* y, int64_t n) {
 
 void launch_eval_recip(const double* x, double* y, int64_t n, cudaStream_t st) {
     const int64_t blocks = (n + 255) / 256;
-    k_eval_recip<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(x, y, n);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        nsm < 1)
+        nsm = 1;
+    const int cap = nsm * 16;
+    k_eval_recip<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(x, y, n);
     g_launch_counter += 1;
 }
 

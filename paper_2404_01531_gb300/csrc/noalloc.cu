@@ -1,15 +1,20 @@
 // FD-subcell right-hand side without any device allocation.
 //
-// Who needs this: callers that cannot call cudaMalloc -- for example code that
-// runs while a CUDA graph is being captured, a host that hands the library
-// memory from its own pool and forbids allocations behind its back, or a tight
-// latency path where a first-touch allocation would stall.  ffe_create
-// allocates everything a context needs, so those callers cannot use ffe_rhs;
-// this entry point computes the same FD right-hand side from caller-owned
-// inputs and outputs, and keeps its intermediate data (the current J~ at every
-// extended cell and the face fluxes) in one file-scope device array of fixed
-// size, FFE_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB).  Every GPU that loads the
+// Who needs this: callers that cannot call cudaMalloc -- a host application
+// that hands the library memory from its own pool and forbids allocations
+// behind its back, or a latency-critical path where a first-touch allocation
+// would stall.  ffe_create allocates everything a context needs, so those
+// callers cannot use ffe_rhs; this entry point computes the FD right-hand side
+// of caller-built extended blocks from caller-owned inputs and outputs, and
+// keeps its intermediate data (the current J~ at every extended cell and the
+// face fluxes) in one file-scope device array of fixed size,
+// FFE_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB).  Every GPU that loads the
 // library holds that array until the process exits.
+//
+// Unlike the context path, the current J~ of every ghost cell is computed here
+// from that cell's state: a context gives the ghosts across a DG neighbour's
+// face that neighbour's nodal current instead (evaluated like its state), so
+// the two agree on ghosts from FD neighbours and boundary states only.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -145,7 +150,7 @@ void set_last_error(const char* msg);
 
 extern "C" ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host, double eta, double weno_eps,
                                          int fd_corrector, const double* Uext_dev, double* dUdt_dev,
-                                         void* cuda_stream) {
+                                         void* cuda_stream) try {
     char msg[256];
     if (P < 3 || P > 6 || n_elem < 0 || !h_host || (n_elem > 0 && (!Uext_dev || !dUdt_dev))) {
         ffe::set_last_error("ffe_fd_rhs_noalloc: need 3 <= P <= 6, n_elem >= 0, h and buffers non-null");
@@ -174,10 +179,16 @@ extern "C" ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host
     if (n_elem == 0) return FFE_OK;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         snprintf(msg, sizeof msg, "ffe_fd_rhs_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
         ffe::set_last_error(msg);
         return FFE_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        snprintf(msg, sizeof msg, "ffe_fd_rhs_noalloc: device %d is beyond the %d devices this entry point serves",
+                 dev, kMaxDevices);
+        ffe::set_last_error(msg);
+        return FFE_EINVAL;
     }
     double* scratch = nullptr;
     {
@@ -210,9 +221,11 @@ extern "C" ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host
     a.F = scratch + 3LL * n_elem * a.ext;            // likewise: nothing needs clearing
     a.out = dUdt_dev;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    k_na_current<<<152 * 4, 256, 0, st>>>(a);
-    k_na_flux<<<152 * 8, 128, 0, st>>>(a);
-    k_na_update<<<152 * 4, 256, 0, st>>>(a);
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+    k_na_current<<<nsm * 4, 256, 0, st>>>(a);
+    k_na_flux<<<nsm * 8, 128, 0, st>>>(a);
+    k_na_update<<<nsm * 4, 256, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(msg, sizeof msg, "ffe_fd_rhs_noalloc: launch: %s", cudaGetErrorString(e));
@@ -220,4 +233,9 @@ extern "C" ffe_status ffe_fd_rhs_noalloc(int P, int n_elem, const double* h_host
         return FFE_ECUDA;
     }
     return FFE_OK;
+} catch (...) {
+    // a host exception (the mutex, an allocation inside the runtime) must not
+    // cross the C ABI
+    ffe::set_last_error("ffe_fd_rhs_noalloc: host resources exhausted");
+    return FFE_ENOMEM;
 }

@@ -18,6 +18,7 @@ BC = {"periodic": 1, "dirichlet": 2, "no_incoming": 3, "star": 4}
 ID = {"fast_wave": 0, "breakdown": 1, "cleaning_mode": 2, "wald": 3, "dipole": 4,
       "fast_wave_kink": 5, "alfven": 6, "breakdown_1d": 7}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
+DIAG = {"l2_err": 0, "luminosity": 1, "constraints": 2}
 STATUS = {0: "FFE_OK", 1: "FFE_EINVAL", 2: "FFE_ENOMEM", 3: "FFE_ECUDA", 4: "FFE_ETIMEOUT",
           5: "FFE_ENUMERIC", 6: "FFE_ESTATE", 7: "FFE_ENOTIMPL"}
 
@@ -28,7 +29,8 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
            "ffe_fd_rhs_noalloc", "ffe_create_batch", "ffe_get_layout", "ffe_set_initial_batch",
            "ffe_rhs_vjp", "ffe_adjoint_step", "ffe_luminosity", "ffe_initial_tangent",
            "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_save", "ffe_load",
-           "ffe_constraints", "ffe_get_coords", "ffe_eval_recip",
+           "ffe_constraints", "ffe_get_coords", "ffe_eval_recip", "ffe_get_mask", "ffe_set_frozen_masks",
+           "ffe_diagnostic",
            "ffe_last_error",
            "ffe_destroy"]
 
@@ -109,6 +111,9 @@ def load():
         "ffe_save": [P, P, ctypes.POINTER(ctypes.c_size_t)],
         "ffe_load": [P, P, ctypes.c_size_t],
         "ffe_constraints": [P, P, ctypes.POINTER(d)],
+        "ffe_get_mask": [P, ctypes.POINTER(P), ctypes.POINTER(i)],
+        "ffe_set_frozen_masks": [P, i],
+        "ffe_diagnostic": [P, i, ctypes.POINTER(d), ctypes.POINTER(d)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -128,11 +133,28 @@ class FFEError(RuntimeError):
 
 def fd_rhs_noalloc(P, Uext, h, eta, weno_eps, fd_corrector, out, stream=None):
     """FD right-hand side of caller-built extended blocks without any device
-    allocation (see ffe_fd_rhs_noalloc in include/ffe.h).  Uext: float64 CUDA
-    tensor [9][n][(2P+7)^3]; out: float64 CUDA tensor [9][n][(2P+1)^3]."""
+    allocation (see ffe_fd_rhs_noalloc in include/ffe.h).  Uext: contiguous
+    float64 CUDA tensor [9][n][(2P+7)^3]; out: contiguous float64 CUDA tensor
+    [9][n][(2P+1)^3], both on the current device (where the library resolves
+    its fixed scratch array).  Sizes, types and placement are checked here,
+    before the library is called, since a wrong size would make its kernels
+    read or write past the buffers."""
     import torch
-    ne = 2 * P + 7
+    ne, nc = 2 * P + 7, 2 * P + 1
+    for name, t in (("Uext", Uext), ("out", out)):
+        if t.dtype != torch.float64:
+            raise ValueError(f"fd_rhs_noalloc: {name} must be float64, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"fd_rhs_noalloc: {name} must be contiguous")
+    if Uext.numel() % (9 * ne ** 3) != 0:
+        raise ValueError(f"fd_rhs_noalloc: Uext has {Uext.numel()} elements, not a multiple of 9 (2P+7)^3 = {9 * ne ** 3}")
     n = Uext.numel() // (9 * ne ** 3)
+    if out.numel() != 9 * n * nc ** 3:
+        raise ValueError(f"fd_rhs_noalloc: out has {out.numel()} elements, {n} blocks need 9 n (2P+1)^3 = {9 * n * nc ** 3}")
+    dev = torch.cuda.current_device()
+    for name, t in (("Uext", Uext), ("out", out)):
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"fd_rhs_noalloc: {name} must be a CUDA tensor on the current device cuda:{dev}")
     hh = (ctypes.c_double * 3)(*h)
     st = stream if stream is not None else torch.cuda.current_stream()
     check(load().ffe_fd_rhs_noalloc(P, n, hh, eta, weno_eps, int(fd_corrector), ctypes.c_void_p(Uext.data_ptr()),
@@ -317,6 +339,24 @@ class Context:
         out = (ctypes.c_double * 4)()
         check(load().ffe_constraints(self.h, ctypes.c_void_p(U.data_ptr()) if U is not None else None, out))
         return tuple(out)
+
+    def mask(self):
+        """Zero-copy torch view (uint8, n_elem) of the library's DG/FD mask."""
+        import torch
+        pm, n = ctypes.c_void_p(), ctypes.c_int()
+        check(load().ffe_get_mask(self.h, ctypes.byref(pm), ctypes.byref(n)))
+        return torch.as_tensor(_DevArray(pm.value, (n.value,), "|u1"), device="cuda")
+
+    def set_frozen_masks(self, on=True):
+        check(load().ffe_set_frozen_masks(self.h, int(bool(on))))
+
+    def diagnostic(self, kind, args=None):
+        """ffe_diagnostic: "l2_err" (args (v0, nv), default B~) -> (L2, n points),
+        "luminosity" (args (r_L,)) -> (L,), "constraints" -> the 4 values of constraints()."""
+        out = (ctypes.c_double * 4)()
+        a = (ctypes.c_double * len(args))(*args) if args else None
+        check(load().ffe_diagnostic(self.h, DIAG[kind], a, out))
+        return {"l2_err": tuple(out[:2]), "luminosity": (out[0],), "constraints": tuple(out)}[kind]
 
     def coords(self):
         """(xyz_dg [3][n_dg], xyz_fd [3][n_fd]) float64 CUDA tensors: DG node and

@@ -213,3 +213,27 @@ def test_fd_rhs_noalloc_argument_checks(lib_path):
         assert st == 1, (kw, st, msg)
         assert msg.startswith("ffe_fd_rhs_noalloc"), msg
     assert call(n=0, U=None, out=None)[0] == 0
+
+
+def test_fd_rhs_noalloc_wrapper_checks_buffers_before_the_call():
+    """The Python wrapper of ffe_fd_rhs_noalloc refuses, before calling the
+    library, buffers whose type, layout or size would let its kernels read or
+    write past them (checked here with host tensors; the size and type checks
+    come before the device check)."""
+    torch = pytest.importorskip("torch")
+    from paper_2404_01531_gb300 import ffe
+    P = 3
+    ne, nc = 2 * P + 7, 2 * P + 1
+    ext = torch.zeros(9 * 2 * ne ** 3, dtype=torch.float64)
+    good = torch.zeros(9 * 2 * nc ** 3, dtype=torch.float64)
+    with pytest.raises(ValueError, match="out has"):
+        ffe.fd_rhs_noalloc(P, ext, [0.1] * 3, 0.0, 1e-40, 1, good[:-1])
+    with pytest.raises(ValueError, match="not a multiple"):
+        ffe.fd_rhs_noalloc(P, ext[:-1], [0.1] * 3, 0.0, 1e-40, 1, good)
+    with pytest.raises(ValueError, match="float64"):
+        ffe.fd_rhs_noalloc(P, ext.float(), [0.1] * 3, 0.0, 1e-40, 1, good)
+    with pytest.raises(ValueError, match="contiguous"):
+        ffe.fd_rhs_noalloc(P, ext, [0.1] * 3, 0.0, 1e-40, 1, torch.zeros(2 * 9 * 2 * nc ** 3, dtype=torch.float64)[::2])
+    if not torch.cuda.is_available():
+        with pytest.raises((ValueError, RuntimeError, AssertionError)):
+            ffe.fd_rhs_noalloc(P, ext, [0.1] * 3, 0.0, 1e-40, 1, good)

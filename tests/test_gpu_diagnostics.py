@@ -1,0 +1,88 @@
+"""The diagnostics entry point (ffe_diagnostic) and the mask view
+(ffe_get_mask, ffe_set_frozen_masks) on the GPU, against the oracle's data.
+
+The L2 error norm is the paper's (Sec. IV.B.1, Table II):
+L2 = sqrt((1/n) sum_k |U_k - U_exact,k|^2) over the n grid points, here against
+the analytic initial data, which is the exact solution of the stationary Wald
+problem."""
+import numpy as np
+import pytest
+
+import ffe_workloads as W
+from oracle.problem import Problem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ffe():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2404_01531_gb300 import ffe
+    ffe.load()
+    return ffe
+
+
+def _l2_host(ctx, U, pr, v0, nv):
+    """The same norm from the downloaded state and the oracle's initial data
+    at the DG nodes of DG elements and the subcells of FD elements."""
+    dg, fd = ctx.split(U)
+    _, mask = ctx.download()
+    d = pr.disc
+    rdg = pr.initial(d.xyz.reshape(3, -1)).reshape((9,) + d.xyz.shape[1:])
+    s, n = 0.0, 0
+    for e in range(ctx.n_elem):
+        if mask[e] == 0:
+            s += ((dg[v0:v0 + nv, e] - rdg[v0:v0 + nv, e]) ** 2).sum()
+            n += ctx.np1 ** 3
+        else:
+            rfd = pr.initial(d.xyz_fd[:, e].reshape(3, -1)).reshape((9,) + d.xyz_fd.shape[2:])
+            s += ((fd[v0:v0 + nv, e] - rfd[v0:v0 + nv]) ** 2).sum()
+            n += ctx.nc ** 3
+    return np.sqrt(s / n), n
+
+
+def test_l2_error_of_the_wald_field(ffe):
+    """Kerr-Schild a = 0.9 shell: zero at the initial data, then the device
+    reduction equals the host norm against the oracle's exact field."""
+    cfg = W.wald(n_ang=2, n_rad=2, P=5, r_in=2.0, r_out=6.0)
+    cfg["params"]["tci_on"] = 0
+    pr = Problem(cfg)
+    ctx = ffe.Context(cfg)
+    ctx.set_initial()
+    l2, n = ctx.diagnostic("l2_err")
+    assert n == ctx.n_elem * 216 and l2 < 1e-14, (l2, n)
+    ctx.step(20)
+    U, _ = ctx.download()
+    l2, n = ctx.diagnostic("l2_err")
+    ref, nh = _l2_host(ctx, U, pr, 3, 3)
+    assert n == nh and 0 < l2 and abs(l2 - ref) <= 1e-10 * ref, (l2, ref)
+    l2e, _ = ctx.diagnostic("l2_err", (0, 3))
+    refe, _ = _l2_host(ctx, U, pr, 0, 3)
+    assert abs(l2e - refe) <= 1e-10 * refe, (l2e, refe)
+    with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
+        ctx.diagnostic("l2_err", (7, 3))
+    ctx.close()
+
+
+def test_l2_error_with_fd_elements_and_the_mask_view(ffe):
+    """Breakdown box with FD elements (all nine variables), the borrowed mask
+    view, the frozen-mask alias and the constraints through ffe_diagnostic."""
+    cfg = W.breakdown(nx=16, ny=1, nz=1, x_half=0.5, steps=3)
+    pr = Problem(cfg)
+    ctx = ffe.Context(cfg)
+    ctx.set_initial()
+    ctx.step(3)
+    U, mask = ctx.download()
+    assert mask.any() and not mask.all()
+    assert np.array_equal(ctx.mask().cpu().numpy(), mask)
+    l2, n = ctx.diagnostic("l2_err", (0, 9))
+    ref, nh = _l2_host(ctx, U, pr, 0, 9)
+    assert n == nh and abs(l2 - ref) <= 1e-10 * ref, (l2, ref)
+    assert np.allclose(ctx.diagnostic("constraints"), ctx.constraints(), rtol=0, atol=0)
+    ctx.set_frozen_masks(True)
+    ctx.step(2)
+    assert np.array_equal(ctx.mask().cpu().numpy(), mask)
+    ctx.set_frozen_masks(False)
+    ctx.close()

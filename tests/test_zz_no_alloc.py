@@ -1,10 +1,14 @@
 """The allocation-free FD right-hand side (ffe_fd_rhs_noalloc) against the
-context path (ffe_rhs) on the same data, two calls in a row.
+context path (ffe_rhs) and against the oracle's FD operator on the same data,
+two calls in a row, with and without the derivative corrector.
 
-It exists for callers that cannot call cudaMalloc (graph capture, hosts that
-own all device memory); its scratch is a fixed static device array shared by
-all calls.  This file is collected last so that a run stopping at the first
-failure has already run every other test."""
+It exists for callers that cannot call cudaMalloc (host applications that own
+all device memory, latency-critical paths); its scratch is a fixed static
+device array shared by all calls.  Every element of the periodic test box is
+on FD, so every ghost holds an FD neighbour's cells, the case in which the
+entry point and the context path take the ghost currents the same way.  This
+file is collected last so that a run stopping at the first failure has already
+run every other test."""
 import numpy as np
 import pytest
 
@@ -36,13 +40,17 @@ def extended_blocks(ufd, n):
     return out
 
 
-def test_noalloc_fd_rhs_matches_context_path_twice():
+@pytest.mark.parametrize("corr", [1, 0])
+def test_noalloc_fd_rhs_matches_context_path_twice(corr):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from paper_2404_01531_gb300 import ffe
+    from oracle.fd import rhs_fd
+    from oracle.problem import Problem
     cfg = W.fast_wave(n=3, P=5)
     cfg["n"] = (3, 2, 1)
-    cfg["params"].update(eta=50.0, fd_corrector=1)
+    cfg["params"].update(eta=50.0, fd_corrector=corr)
+    pr = Problem(cfg)
     ctx = ffe.Context(cfg)
     ctx.set_initial()
     E, P = ctx.n_elem, ctx.P
@@ -59,13 +67,16 @@ def test_noalloc_fd_rhs_matches_context_path_twice():
         ctx.rhs(U, ref)
         ext = torch.from_numpy(np.ascontiguousarray(extended_blocks(ufd, cfg["n"]))).cuda()
         out = torch.full((9, E, nc, nc, nc), float("nan"), dtype=torch.float64, device="cuda")
-        ffe.fd_rhs_noalloc(P, ext, h, cfg["params"]["eta"], cfg["params"]["weno_eps"], 1, out)
+        ffe.fd_rhs_noalloc(P, ext, h, cfg["params"]["eta"], cfg["params"]["weno_eps"], corr, out)
         torch.cuda.synchronize()
         _, rfd = ctx.split(ref.cpu().numpy())
         got = out.cpu().numpy()
         sel_dg = np.zeros(E, dtype=bool)
         err = rel_err_split(udg, udg, got, rfd, sel_dg).max()
         assert err <= 1e-11, (call, err)
+        ofd = rhs_fd(dict(mask=np.ones(E, dtype=np.uint8), udg=udg, ufd=ufd), pr.disc, pr.met, pr.prm)
+        err_o = rel_err_split(udg, udg, got, ofd, sel_dg).max()
+        assert err_o <= 1e-11, (call, err_o)
     ctx.close()
 
 
