@@ -29,9 +29,12 @@ import ffe_workloads as W  # noqa: E402
 METRIC = "RHS element-node updates/s FP64 at 1 GB300, % roofline; adjoint/forward time"
 UNIT = "element-node updates/s"
 # DRAM bytes (read + write) of k_fd_flux per FD element it processes, from an
-# ncu capture of the kernel (profiles/k_fd_flux_breakdown_8x8x8.md): a launch
-# moves this many bytes for each element of its chunk
+# ncu capture of the kernel on the 8x8x8 breakdown box: a launch moves this
+# many bytes for each element of its chunk (scaled to a launch of this run by
+# its FD element count)
 DRAM_BYTES_PER_FD_ELEMENT = {"fd_flux": 5.535e5}
+TRAFFIC_SOURCE = ("scaled: 553.5 KB of DRAM traffic per FD element (ncu dram__bytes_read.sum + "
+                  "dram__bytes_write.sum of k_fd_flux on the 8x8x8 breakdown box) x FD elements per launch")
 
 RECON = {"weno5z": 0, "mp5": 1}
 
@@ -81,17 +84,43 @@ def cpu_oracle_rate(steps, budget_s=None):
     return units / dt, dt, done
 
 
-def cpu_baseline_subprocess(steps, budget_s):
-    """Run the oracle timing in a fresh single-threaded interpreter (spawned, no CUDA)."""
+def _oracle_procs(n_proc, steps, budget_s):
+    """Start n_proc fresh single-threaded interpreters (no CUDA), each timing
+    the oracle on its own copy of the sample."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
             "r, dt, n = bench.cpu_oracle_rate(%d, %r); print(json.dumps([r, dt, n]))" % (ROOT, steps, budget_s))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    r, dt, n = json.loads(out.stdout.strip().splitlines()[-1])
+    return [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                             text=True) for _ in range(n_proc)]
+
+
+def _collect(procs):
+    res = []
+    for p in procs:
+        out, err = p.communicate(timeout=900)
+        if p.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    return res
+
+
+def cpu_baseline_subprocess(steps, budget_s):
+    """Run the oracle timing in a fresh single-threaded interpreter (spawned, no CUDA)."""
+    r, dt, n = _collect(_oracle_procs(1, steps, budget_s))[0]
     return r, dt, n
+
+
+def cpu_baseline_all_cores(steps, budget_s):
+    """The oracle on every host core: one single-threaded interpreter per core
+    (os.cpu_count()), each advancing its own copy of the sample (independent
+    slabs, like elements split over cores); rate = all their element-node
+    updates / the longest wall time."""
+    n = os.cpu_count() or 1
+    res = _collect(_oracle_procs(n, steps, budget_s))
+    units = sum(r * dt for r, dt, _ in res)
+    wall = max(dt for _, dt, _ in res)
+    return units / wall, wall, min(k for _, _, k in res), n
 
 
 class Clocks:
@@ -587,7 +616,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2404_01531_gb300 import ffe
-    from paper_2404_01531_gb300.roofline import (FP64_PEAK_TFLOPS, fd_flux_flops, dg_flops_per_node,
+    from paper_2404_01531_gb300.roofline import (fp64_peak_tflops, fd_flux_flops, dg_flops_per_node,
                                                  fd_faces_per_element)
 
     cfg = W.breakdown(nx=args.nx, x_half=2.0 * args.nx / 64)
@@ -597,12 +626,15 @@ def main():
     ctx.set_initial()
     ctx.step(max(args.warmup, 3))
     torch.cuda.synchronize()
+    # the state before the timed window: the profiled pass below replays the
+    # same steps from it
+    ckpt = ctx.save()
 
     # ---- timed region: graph replays, inputs resident in HBM (working set >> L2)
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    u0 = ctx.info().node_updates
+    i_t0 = ctx.info()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -616,50 +648,63 @@ def main():
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     inf = ctx.info()
-    units = inf.node_updates - u0
+    units = inf.node_updates - i_t0.node_updates
     n_fd_end = inf.n_fd_elem
     ms_max, units_all = combine_ranks(ms, units, dist, "cuda")
     value = units_all / (ms_max / 1e3)
-    launches = None
     n0 = ctx.launch_count()
     ctx.step(1)
     torch.cuda.synchronize()
     per_step_launches = ctx.launch_count() - n0
     launches = per_step_launches * args.steps
 
-    # ---- per-kernel event timing of the same steps (eager launches)
-    # algorithmic work of the window from the library's element-update counters
-    # (every FD element update is one pass of fd_flux over it, every DG element
-    # update one pass of dg_substep); per-launch work = total / launches
+    # ---- per-kernel event timing of the same steps (eager launches) from the
+    # same starting state; algorithmic work of the window from the library's
+    # element-update counters (every FD element update is one pass of fd_flux
+    # over it, every DG element update one pass of dg_substep)
+    ctx.load_checkpoint(ckpt)
     i0 = ctx.info()
     ctx.set_profiling(True)
     ctx.step(args.steps)
     ctx.set_profiling(False)
     i1 = ctx.info()
     prof = ctx.profile_read()
+    same_window = (i1.node_updates - i0.node_updates == units and
+                   i1.fd_elem_updates - i0.fd_elem_updates == inf.fd_elem_updates - i_t0.fd_elem_updates)
     total_ms = sum(v[1] for v in prof.values())
-    dom = max(prof, key=lambda k: prof[k][1])
-    dom_launches, dom_ms, dom_max = prof[dom]
     E, P = ctx.n_elem, ctx.P
     nn = (P + 1) ** 3
     n_fd_upd = i1.fd_elem_updates - i0.fd_elem_updates
     n_dg_upd = i1.dg_elem_updates - i0.dg_elem_updates
-    if dom == "dg_substep":
-        flops = n_dg_upd * nn * sum(dg_flops_per_node(P, s) for s in range(3)) / 3.0
-    elif dom == "fd_flux":
-        flops = n_fd_upd * fd_faces_per_element(P) * fd_flux_flops(RECON[args.recon])
-    else:
-        flops = None
-    roof = None
-    if flops is not None:
-        ach = flops / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": (DRAM_BYTES_PER_FD_ELEMENT[dom] * n_fd_upd / dom_launches
-                            if DRAM_BYTES_PER_FD_ELEMENT.get(dom) else None),
-                "kernel": dom, "peak_source": "derived: 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz",
-                "share": dom_ms / total_ms, "launches": dom_launches, "max_launch_ms": dom_max,
-                "units": {"fd_elem_updates": n_fd_upd, "dg_elem_updates": n_dg_upd}}
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    f_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = fp64_peak_tflops(props.multi_processor_count, f_max)
+    peak_src = (f"derived: 2 FP64 FMA lanes/clk/SM x {props.multi_processor_count} SMs (device) x "
+                f"{f_max / 1e3:.3f} GHz (max SM clock, nvidia-smi)")
+    fma_measured = ffe.fp64_fma_rate(stream)
+
+    def kernel_roof(name, flops):
+        if name not in prof or flops is None:
+            return None
+        launches_k, ms_k, max_k = prof[name]
+        ach = flops / (ms_k / 1e3) / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "traffic": (DRAM_BYTES_PER_FD_ELEMENT[name] * n_fd_upd / launches_k
+                         if DRAM_BYTES_PER_FD_ELEMENT.get(name) else None),
+             "kernel": name, "peak_source": peak_src, "peak_measured_fma": fma_measured,
+             "frac_of_measured_fma": ach / fma_measured, "share": ms_k / total_ms, "launches": launches_k,
+             "ms_per_step": ms_k / args.steps, "max_launch_ms": max_k,
+             "profiled_window": "the timed steps replayed from the same state" if same_window else "differs",
+             "units": {"fd_elem_updates": n_fd_upd, "dg_elem_updates": n_dg_upd}}
+        if r["traffic"] is not None:
+            r["traffic_source"] = TRAFFIC_SOURCE
+        return r
+    dg_fl = n_dg_upd * nn * sum(dg_flops_per_node(P, s) for s in range(3)) / 3.0
+    fd_fl = n_fd_upd * fd_faces_per_element(P) * fd_flux_flops(RECON[args.recon])
+    roofs = {"fd_flux": kernel_roof("fd_flux", fd_fl), "dg_substep": kernel_roof("dg_substep", dg_fl)}
+    dom = max((k for k in roofs if roofs[k]), key=lambda k: prof[k][1])
+    roof = roofs[dom]
+    roof_dg = roofs["dg_substep"]
 
     # ---- end to end through the C ABI with host buffers
     pin = torch.empty(ctx.n_state, dtype=torch.float64, pin_memory=True)
@@ -693,9 +738,14 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         try:
-            r, dt, n = cpu_baseline_subprocess(40, 20.0)
-            cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": CPU_SAMPLE_TEXT + f", {n} steps in {dt:.1f} s"}
+            r1, dt1, n1 = cpu_baseline_subprocess(40, 15.0)
+            ra, dta, na, ncores = cpu_baseline_all_cores(40, 15.0)
+            cpu = {"value": ra, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                   "sample": (f"oracle (numpy fp64) on a 16x2x2-element slab of the breakdown workload (same "
+                              f"element width, order and current sheet), whole hybrid steps: {ncores} "
+                              f"single-threaded processes, one per host core, each on its own copy of the slab, "
+                              f"at least {na} steps each in {dta:.1f} s"),
+                   "one_core": {"value": r1, "cores": 1, "sample": CPU_SAMPLE_TEXT + f", {n1} steps in {dt1:.1f} s"}}
         except Exception as ex:  # reported, not fatal
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -705,7 +755,7 @@ def main():
                        "elements": E, "P": P, "dg_nodes": E * nn, "fd_elements_end": n_fd_end,
                        "parallelism": f"replicas x{ws}", "l2": "working set > L2 (no flush needed)",
                        "recon": args.recon},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "roofline_dg": roof_dg, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
             "adjoint": adj, "status_bits": status}
     print(json.dumps(line), flush=True)

@@ -99,6 +99,19 @@ typedef struct {
     int constraint_mode;                             /* FFE_RELAX | FFE_HARD | ...        */
     double omega_star;                               /* star rotation (FFE_BC_STAR)       */
     int recon;                                       /* FFE_RECON_WENO5Z | FFE_RECON_MP5  */
+    int fd_chunk;                                    /* FD elements per scratch chunk: the FD
+                                                        kernels walk the FD list in chunks of this
+                                                        many elements (0 = 2048); bounds the FD
+                                                        scratch whatever the FD population      */
+    int fd_capacity;                                 /* ffe_create: FD slots of the context's
+                                                        FD block (0 or >= elements: one per
+                                                        element, FD block of element e at slot e);
+                                                        fewer: a pool of slots that elements take
+                                                        when they switch to FD and return when they
+                                                        switch back (see ffe_get_layout); an element
+                                                        flagged when none is free stays on DG and
+                                                        status bit 2 is raised.  Ignored by
+                                                        ffe_create_batch (its own argument)      */
 } ffe_params;
 
 /* FD reconstruction: WENO5-Z with q = 2 (the paper's, Sec. III.C.2) or MP5
@@ -393,6 +406,15 @@ ffe_status ffe_get_coords(ffe_ctx* ctx, double* xyz_dg_dev, double* xyz_fd_dev);
  * the correctly rounded quotient.  For accuracy tests; enqueued on
  * cuda_stream.  FFE_EINVAL for n < 0 or a NULL array with n > 0. */
 ffe_status ffe_eval_recip(const double* x_dev, double* y_dev, int64_t n, void* cuda_stream);
+
+/* FP64 FMA throughput of the current device, measured: a register-only
+ * loop of independent fused multiply-adds (4 CTAs of 256 threads per SM, 8
+ * chains per thread, 2^16 steps each, no memory traffic) timed with CUDA
+ * events on cuda_stream (synchronising it); *tflops_host receives the rate in
+ * TFLOP/s (an FMA counts 2).  The measured denominator of the FP64 roofline
+ * reported beside the one derived from the SM count and clock.  Not part of
+ * the method. */
+ffe_status ffe_fp64_fma_rate(void* cuda_stream, double* tflops_host);
 
 /* Thread-local message of the last failed call ("" if none). */
 const char* ffe_last_error(void);

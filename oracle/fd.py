@@ -158,15 +158,17 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
     [reading] A DG neighbour's ghost cells take its polynomial at its subcell
     centres for U and, for J~, the same evaluation of its nodal current (not the
     current of the evaluated state; see dg.external_fd_current).
-    prm["ghost_interp"] (default off, the reading the CUDA path implements):
-    ghosts across a neighbour's face are the neighbour's data at the ghost
-    centres of this element's grid extended past the face -- a DG neighbour's
-    polynomial evaluated there, an FD neighbour's cells interpolated there
-    (6-point tensor Lagrange in its reference coordinates, the paper's
-    sixth-order transfer, Sec. III.C.1).  Where the grids continue each other
-    (inside a cubed-sphere wedge, on boxes) both readings give the same
-    ghosts up to rounding; between wedges only the interpolated ghosts are
-    consistent."""
+    prm["ghost_interp"] (the default reading, Problem sets it): ghosts across
+    a neighbour's face are the neighbour's data at the ghost centres of this
+    element's grid extended past the face -- a DG neighbour's polynomial
+    evaluated there, an FD neighbour's cells interpolated there (6-point
+    tensor Lagrange in its reference coordinates, the paper's sixth-order
+    transfer, Sec. III.C.1).  Off: the neighbour's own cells (its polynomial
+    at its own subcell centres).  Where the grids continue each other (inside
+    a cubed-sphere wedge, on boxes) both readings give the same ghosts up to
+    rounding; between wedges only the interpolated ghosts are consistent
+    (the residual of an exact stationary field converges there with them and
+    not with the copies)."""
     T = disc.T
     Nc = T.nc
     n = len(sel)

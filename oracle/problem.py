@@ -44,7 +44,11 @@ class Problem:
                         weno_eps=p["weno_eps"], fd_corrector=p["fd_corrector"], recon=p.get("recon", 0),
                         dirichlet=self.initial, omega=p["omega_star"],
                         mode=p["constraint_mode"], filter_on=p["filter_on"], tci_on=p["tci_on"],
-                        tci_alpha=p["tci_alpha"], tci_M=p["tci_M"])
+                        tci_alpha=p["tci_alpha"], tci_M=p["tci_M"],
+                        # [reading] FD ghosts across a neighbour's face are the neighbour's
+                        # data at the ghost centres of this element's grid continued past
+                        # the face (Sec. III.C.1's sixth-order transfer); see fd.fill_ghosts
+                        ghost_interp=bool(p.get("ghost_interp", True)))
         self.dxmin = d.min_spacing()
         # an explicit time step (the paper's tables give one) or the CFL step (Sec. III.B)
         self.dt = p["dt"] if p.get("dt", 0.0) > 0.0 else p["cfl"] * self.dxmin / self.lam_max * p["c_over_D"]

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libffe.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["host.cu", "host_geom.cu", "kernels_dg.cu", "kernels_fd.cu", "kernels_curved.cu", "kernels_adjoint.cu", "kernels_adjoint_fd.cu",
-           "noalloc.cu"]
+           "kernels_fd_interp.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -102,12 +102,16 @@ struct Dev {
     // [2 nc na + 1 each], then r_g, 1/r_g [2 nc nr + 1 each]
     const double* stab;
     const double* xyz_dg;           // [3][ndg] node coordinates
-    const double* xyz_fd;           // [3][nfd] subcell-centre coordinates
+    const double* xyz_fd;           // [3][xfd_n] subcell-centre coordinates of every element
+                                    // (element e's cells at e ncell; null in batches)
+    int64_t xfd_n;
     // connectivity
     const int* nbr;                 // [E][6] neighbour element or -1
     const int* nbr_face;            // [E][6] the neighbour's face touching mine
     const int* orient;              // [E][6] orientation code of the shared face (shellmap.cuh)
     const int* bc;                  // [E][6] boundary kind when nbr < 0
+    const unsigned char* ginterp;   // [E][6] 1: face between cubed-sphere wedges, FD ghosts
+                                    // interpolated to the extended grid (null: none)
     const int* bface;               // [E][6] boundary-face slot (Dirichlet data) or -1
     const double* bdg;              // [nbf][9][np1*np1] Dirichlet states at face nodes
     const double* bfd;              // [nbf][9][GH][nc*nc] Dirichlet states in ghost cells
@@ -161,6 +165,12 @@ int fd_chunks(const Dev& d);
 // extended blocks (U, J~ with ghosts) of the listed FD elements of one chunk
 void launch_fd_fill(const Dev& d, const int* list, int count_index, int w0, Field U, Field J, cudaStream_t st);
 void launch_eval_recip(const double* x, double* y, int64_t n, cudaStream_t st);
+// register-only DFMA loop: returns its flops, *ms its event-timed duration
+double launch_fma_probe(int nsm, int iters, cudaStream_t st, float* ms);
+// ghosts of the faces between cubed-sphere wedges (kernels_fd_interp.cu)
+void launch_fd_fill_interp(const Dev& d, const int* list, int ci, int w0, Field U, Field J, cudaStream_t st);
+void launch_fdv_ghosts_interp(const Dev& d, const int* list, int ci, int w0, Field U, Field out, const double* extb,
+                              cudaStream_t st);
 void launch_constraints(const Dev& d, Field U, double* part, int blocks, cudaStream_t st);
 void launch_l2_err(const Dev& d, Field U, Field R, int v0, int nv, double* part, int blocks, cudaStream_t st);
 // out += (d RHS_FD/dU)^T L (kernels_adjoint_fd.cu); extb: scratch of the size of d.ext

@@ -472,6 +472,7 @@ ffe_status build_box(ffe_ctx* c) {
     c->d.ijac = d_ijac;
     c->d.xyz_dg = d_xdg;
     c->d.xyz_fd = d_xfd;
+    c->d.xfd_n = (int64_t)c->d.E * c->d.ncell;
     c->d.nbr = d_nbr;
     c->d.nbr_face = d_nbf;
     c->d.bc = d_bc;
@@ -513,6 +514,37 @@ MapFn ctx_map(ffe_ctx* c) {
 }
 
 int host_P(const ffe_ctx* c, int e) { return c->batch ? c->h_eP[e] : c->d.P; }
+
+// Faces between cubed-sphere wedges: there the FD ghosts are the neighbour's
+// data interpolated to this element's grid continued past the face
+// (k_fd_fill_ghosts_interp).  nbr: neighbour of every element face.
+ffe_status set_ginterp(ffe_ctx* c, const std::vector<int>& nbr) {
+    Dev& d = c->d;
+    auto wedge = [&](int e) {
+        if (c->batch) {
+            const InstInfo& in = c->insts[c->h_einst[e]];
+            return (e - in.e0) / (in.na * in.na * in.nr);
+        }
+        return e / (c->shell.na * c->shell.na * c->shell.nr);
+    };
+    std::vector<unsigned char> gi(6 * (size_t)d.E, 0);
+    bool any = false;
+    for (int e = 0; e < d.E; ++e)
+        for (int f = 0; f < 6; ++f) {
+            const int nb = nbr[6 * (size_t)e + f];
+            if (nb >= 0 && wedge(nb) != wedge(e)) {
+                gi[6 * (size_t)e + f] = 1;
+                any = true;
+            }
+        }
+    if (!any) return FFE_OK;
+    unsigned char* p;
+    ffe_status s;
+    if ((s = dalloc(c, &p, gi.size()))) return s;
+    CK(cudaMemcpy(p, gi.data(), gi.size(), cudaMemcpyHostToDevice));
+    d.ginterp = p;
+    return FFE_OK;
+}
 
 // Six-wedge shell: coordinates, per-node inverse Jacobians, connectivity with
 // orientation, boundary kinds, Kerr-Schild metric arrays and (dx)_min.
@@ -560,6 +592,7 @@ ffe_status build_shell(ffe_ctx* c) {
         }
     c->nbf = nbfd;
     c->h_bface = bface;
+    if (ffe_status sg = set_ginterp(c, nbr)) return sg;
     // (dx)_min along element grid lines
     double dmin = 1e300;
     for (int64_t e = 0; e < E; ++e)
@@ -602,6 +635,7 @@ ffe_status build_shell(ffe_ctx* c) {
     Dev& d = c->d;
     d.xyz_dg = d_xdg;
     d.xyz_fd = d_xfd;
+    d.xfd_n = (int64_t)d.E * d.ncell;
     d.geo = d_geo;
     d.ijac = d_ijac;
     d.nbr = d_nbr;
@@ -840,7 +874,8 @@ ffe_status finish_create(ffe_ctx* c, int fd_cap, const std::vector<int>& orders)
     d.thr_fd = d.thr_fdP[d.P];
     d.fd_cap = fd_cap;
     d.nfd = (int64_t)fd_cap * d.ncell;
-    d.chunk = fd_cap < 2048 ? (fd_cap > 0 ? fd_cap : 1) : 2048;
+    const int chunk = params->fd_chunk > 0 ? params->fd_chunk : 2048;
+    d.chunk = fd_cap < chunk ? (fd_cap > 0 ? fd_cap : 1) : chunk;
     if ((s = dalloc(c, &d.mask, d.E))) return s;
     if ((s = dalloc(c, &d.switched, d.E))) return s;
     if ((s = dalloc(c, &d.dg_list, d.E))) return s;
@@ -893,6 +928,8 @@ ffe_status finish_create(ffe_ctx* c, int fd_cap, const std::vector<int>& orders)
         // DG elements of the lower orders get their own work lists (own launches)
         if ((s = dalloc(c, &d.dg_list_lo, d.E))) return s;
         if ((s = dalloc(c, &d.dg_list_lo2, d.E))) return s;
+    }
+    if (c->batch || fd_cap < d.E) {
         // FD slot pool: every slot free until ffe_set_initial assigns some
         if ((s = dalloc(c, &d.fd_slot, d.E))) return s;
         if ((s = dalloc(c, &d.slot_elem, fd_cap))) return s;
@@ -1302,7 +1339,8 @@ ffe_status ffe_get_coords(ffe_ctx* c, double* xyz_dg_dev, double* xyz_fd_dev) tr
     g_err.clear();
     if (!c) return fail(FFE_EINVAL, "null context");
     const Dev& d = c->d;
-    if (xyz_fd_dev && !d.xyz_fd) return fail(FFE_ENOTIMPL, "FD centres are not stored for batched contexts");
+    if (xyz_fd_dev && (!d.xyz_fd || d.fd_slot))
+        return fail(FFE_ENOTIMPL, "FD centres in state-vector order need one FD slot per element (no FD slot pool)");
     if (xyz_dg_dev)
         CK(cudaMemcpyAsync(xyz_dg_dev, d.xyz_dg, 3 * (size_t)d.ndg * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     if (xyz_fd_dev)
@@ -1318,6 +1356,22 @@ ffe_status ffe_eval_recip(const double* x_dev, double* y_dev, int64_t n, void* c
     if (n == 0) return FFE_OK;
     launch_eval_recip(x_dev, y_dev, n, (cudaStream_t)cuda_stream);
     CK(cudaGetLastError());
+    return FFE_OK;
+} catch (...) {
+    return host_failure();
+}
+
+ffe_status ffe_fp64_fma_rate(void* cuda_stream, double* tflops_host) try {
+    g_err.clear();
+    if (!tflops_host) return fail(FFE_EINVAL, "null argument");
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    float ms = 0.0f;
+    const double flops = launch_fma_probe(nsm, 1 << 16, (cudaStream_t)cuda_stream, &ms);
+    CK(cudaGetLastError());
+    if (!(ms > 0.0f)) return fail(FFE_ECUDA, "the probe's events gave no duration");
+    *tflops_host = flops / (ms * 1e-3) / 1e12;
     return FFE_OK;
 } catch (...) {
     return host_failure();
@@ -1351,6 +1405,8 @@ ffe_status check_scheme(const ffe_params& p, const char* who) {
     if (p.constraint_mode < FFE_RELAX || p.constraint_mode > FFE_RELAX_THEN_HARD)
         return fail(FFE_EINVAL, "%s: constraint mode %d", who, p.constraint_mode);
     if (p.recon != FFE_RECON_WENO5Z && p.recon != FFE_RECON_MP5) return fail(FFE_EINVAL, "%s: reconstruction %d", who, p.recon);
+    if (p.fd_chunk < 0) return fail(FFE_EINVAL, "%s: fd_chunk %d < 0", who, p.fd_chunk);
+    if (p.fd_capacity < 0) return fail(FFE_EINVAL, "%s: fd_capacity %d < 0", who, p.fd_capacity);
     if (p.tci_on && !(p.tci_alpha > 0)) return fail(FFE_EINVAL, "%s: indicator needs alpha > 0", who);
     if (p.tci_on && p.recon == FFE_RECON_WENO5Z && !(p.weno_eps > 0))
         return fail(FFE_EINVAL, "%s: WENO5-Z needs eps > 0", who);
@@ -1462,7 +1518,8 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
     c->tab = c->tabs_h[P];
     if ((s = (domain->kind == FFE_DOMAIN_SHELL6 ? build_shell(c) : build_box(c)))) return bail(s);
     d.dt = params->dt > 0 ? params->dt : params->cfl * c->dxmin / c->lam_max * params->c_over_D;
-    if ((s = finish_create(c, d.E, {P}))) return bail(s);
+    const int cap = params->fd_capacity > 0 && params->fd_capacity < d.E ? params->fd_capacity : d.E;
+    if ((s = finish_create(c, cap, {P}))) return bail(s);
     *out = c;
     return FFE_OK;
 } catch (...) {
@@ -1496,7 +1553,7 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
             pi.filter_on != p0.filter_on || pi.filter_a != p0.filter_a || pi.filter_b != p0.filter_b ||
             pi.tci_on != p0.tci_on || pi.tci_M != p0.tci_M || pi.tci_alpha != p0.tci_alpha ||
             pi.weno_eps != p0.weno_eps || pi.fd_corrector != p0.fd_corrector || pi.recon != p0.recon ||
-            pi.constraint_mode != p0.constraint_mode)
+            pi.constraint_mode != p0.constraint_mode || pi.fd_chunk != p0.fd_chunk)
             return fail(FFE_EINVAL, "instance %d: scheme parameters differ from instance 0", i);
         if (!std::isfinite(dm.r_out)) return fail(FFE_EINVAL, "instance %d: need a finite r_out", i);
         if (p0.tci_on && (p0.tci_M < 1 || p0.tci_M > Ps[i])) return fail(FFE_EINVAL, "tci_M=%d", p0.tci_M);
@@ -1621,6 +1678,7 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
     }
     c->nbf = nbfd;
     c->h_bface = bface;
+    if (ffe_status sg = set_ginterp(c, nbr)) return bail(sg);
     d.dt = c->insts[0].dt;
     ffe_status s;
     double *d_xdg, *d_geo, *d_bdg, *d_bfd, *d_ijac;

@@ -3,7 +3,7 @@
 //   out += (d RHS_FD / d U)^T lambda  over every listed FD element.
 // The forward operator of an FD element is: extended block of the 12
 // quantities (U and J~ = J~(U)) with 3 ghost layers from FD neighbours
-// (copies), DG neighbours (their polynomials of U and of the nodal J~ at the
+// (copies; interpolated across faces between wedges, k_fdv_ghosts_interp), DG neighbours (their polynomials of U and of the nodal J~ at the
 // ghost subcell centres) or the boundary states; WENO5-Z left/right values at every face; Rusanov flux
 // of every physical component with the unit face normal; optional 4th-order
 // corrector with the cell-centred fluxes; flux difference with the inverse
@@ -156,6 +156,7 @@ __global__ void k_fdv_ghosts(Dev d, const int* list, int ci, int w0, Field U, Fi
     for (int item = blockIdx.x; item < n * 6; item += gridDim.x) {
         const int wl = item / 6, f = item % 6;
         const int e = list[w0 + wl];
+        if (d.ginterp && d.ginterp[e * 6 + f]) continue;   // k_fdv_ghosts_interp
         const ES es = esz(d, e);
         const Tables& T = d.tabs[es.P];
         const int nc = es.nc, ne = nc + 2 * GH, np1 = es.np1, nn = es.nn;
@@ -320,6 +321,7 @@ void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, doubl
         k_fdv_cells<<<d.nsm * 8, 256, 0, st>>>(d, d.fd_list, 1, w0, U, L, out, extb);
         k_fdv_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, d.fd_list, 1, w0, U, J, out, extb, omega_bar);
         g_launch_counter += 3;
+        launch_fdv_ghosts_interp(d, d.fd_list, 1, w0, U, out, extb, st);
     }
     prof_end(st);
 }

@@ -53,8 +53,9 @@ void launch_build_lists(const Dev& d, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// J~ (drift, full) at every DG node of DG elements and FD cell of FD elements;
-// with a list, only the FD cells of the listed elements.
+// J~ (drift, full) at every DG node of DG elements and at the cells of the FD
+// list (counts[1], as built by k_build_lists); with a list, only the FD cells
+// of the listed elements.
 __global__ void k_current(Dev d, Field U, Field J, const int* list, int count_index) {
     int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -67,17 +68,11 @@ __global__ void k_current(Dev d, Field U, Field J, const int* list, int count_in
             current_flat(u, d.eta, jd, jf);
             for (int c = 0; c < 3; ++c) { J.dg(c)[p] = jd[c]; J.dg(3 + c)[p] = jf[c]; }
         }
-        for (int64_t p = tid; p < d.nfd; p += stride) {
-            const int sl = (int)(p / d.ncell);
-            const int e = d.slot_elem ? d.slot_elem[sl] : sl;
-            if (e < 0 || d.mask[e] != 1 || (int)(p % d.ncell) >= esz(d, e).ncell) continue;
-            double u[NV], jd[3], jf[3];
-            for (int v = 0; v < NV; ++v) u[v] = U.fd(v)[p];
-            current_flat(u, d.eta, jd, jf);
-            for (int c = 0; c < 3; ++c) { J.fd(c)[p] = jd[c]; J.fd(3 + c)[p] = jf[c]; }
-        }
-    } else {
-        int n = d.counts[count_index];
+        list = d.fd_list;
+        count_index = 1;
+    }
+    {
+        const int n = d.counts[count_index];
         for (int64_t q = tid; q < (int64_t)n * d.ncell; q += stride) {
             const int e = list[q / d.ncell];
             const int c = (int)(q % d.ncell);
@@ -100,6 +95,7 @@ void launch_current(const Dev& d, Field U, Field J, const int* list, int count_i
 
 // ---------------------------------------------------------------------------
 // Stages 1 and 2 are pointwise: U1 = solve(u_n), G1 = G(U1); U2 = solve(u_n - dt a G1), G2 = G(U2).
+// Over the DG nodes of DG elements and the cells of the FD list (built first).
 __device__ __forceinline__ void stage12_point(const Dev& d, double dt, double* u, double* g1, double* g2) {
     const double dta = dt * IM_A;
     double U1[NV];
@@ -129,10 +125,13 @@ __global__ void k_stage12(Dev d, Field un, Field Ua, Field G1, Field G2) {
         for (int v = 0; v < NV; ++v) Ua.dg(v)[p] = u[v];
         for (int c = 0; c < NG; ++c) { G1.dg(c)[p] = g1[c]; G2.dg(c)[p] = g2[c]; }
     }
-    for (int64_t p = tid; p < d.nfd; p += stride) {
-        const int sl = (int)(p / d.ncell);
-        const int e = d.slot_elem ? d.slot_elem[sl] : sl;
-        if (e < 0 || d.mask[e] != 1 || (int)(p % d.ncell) >= esz(d, e).ncell) continue;
+    // FD cells: the elements of the FD list only (an FD slot pool may be mostly empty)
+    const int64_t nfdq = (int64_t)d.counts[1] * d.ncell;
+    for (int64_t q = tid; q < nfdq; q += stride) {
+        const int e = d.fd_list[q / d.ncell];
+        const int c = (int)(q % d.ncell);
+        if (c >= esz(d, e).ncell) continue;
+        const int64_t p = fdb(d, e) + c;
         double u[NV], g1[NG], g2[NG];
         for (int v = 0; v < NV; ++v) u[v] = un.fd(v)[p];
         stage12_point(d, dt_of(d, e), u, g1, g2);

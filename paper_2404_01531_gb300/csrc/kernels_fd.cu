@@ -7,6 +7,8 @@
 //   k_fd_update  one thread per cell: flux difference, sources, IMEX stage;
 //   k_rollback_project  DG -> FD projection of a flagged element's substep inputs;
 //   k_fd2dg      end-of-step FD -> DG check with alpha' = alpha + 1 (Sec. III.C.3).
+// Ghosts across faces between cubed-sphere wedges are filled by
+// k_fd_fill_ghosts_interp (kernels_fd_interp.cu).
 // Listed FD elements are processed in chunks of d.chunk so that the scratch
 // (extended blocks, face fluxes) is bounded whatever the number of FD elements.
 // Elements may have different orders (batched contexts): every size below is
@@ -45,6 +47,7 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
     for (int item = blockIdx.x; item < n * 6; item += gridDim.x) {
         const int wl = item / 6, f = item % 6;
         const int e = list[w0 + wl];
+        if (d.ginterp && d.ginterp[e * 6 + f]) continue;   // k_fd_fill_ghosts_interp
         const ES es = esz(d, e);
         const Tables& T = d.tabs[es.P];
         const int nc = es.nc, ne = nc + 2 * GH, np1 = es.np1, nn = es.nn;
@@ -168,7 +171,8 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
                             double ij[3][3];
                             shell_cell(shell_pts(d, e, nc), c, ij, x);
                         } else {
-                            for (int k = 0; k < 3; ++k) x[k] = d.xyz_fd[(int64_t)k * d.nfd + p];
+                            for (int k = 0; k < 3; ++k)
+                                x[k] = d.xyz_fd[(int64_t)k * d.xfd_n + (int64_t)e * d.ncell + (p - fdb(d, e))];
                         }
                         bc_star_flat(ui, x, omega_of(d, e), u);
                     }
@@ -376,6 +380,7 @@ void launch_fd_fill(const Dev& d, const int* list, int ci, int w0, Field U, Fiel
     k_fd_fill_interior<<<d.nsm * 8, 256, 0, st>>>(d, list, ci, w0, U, J);
     k_fd_fill_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, list, ci, w0, U, J);
     g_launch_counter += 2;
+    launch_fd_fill_interp(d, list, ci, w0, U, J, st);
 }
 
 template <int SUB>
@@ -399,6 +404,7 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin
         prof_begin("fd_fill_ghosts", st);
         k_fd_fill_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, list, ci, w0, Uin, J);
         prof_end(st);
+        launch_fd_fill_interp(d, list, ci, w0, Uin, J, st);
         prof_begin("fd_flux", st);
         if (d.recon == FFE_RECON_MP5) {
             if (d.curved) k_fd_flux_curved<FFE_RECON_MP5><<<grid, 128, 0, st>>>(d, list, ci, w0);
@@ -659,6 +665,41 @@ void launch_eval_recip(const double* x, double* y, int64_t n, cudaStream_t st) {
     const int cap = nsm * 16;
     k_eval_recip<<<(int)(blocks < cap ? blocks : cap), 256, 0, st>>>(x, y, n);
     g_launch_counter += 1;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe (the measured denominator of the FP64 roofline):
+// every thread runs 8 independent DFMA chains in registers, no memory traffic;
+// the chains stay live through a store that the data never trigger.
+__device__ double g_fma_sink;
+
+__global__ void k_fma_probe(int iters, double a, double b) {
+    double x[8];
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    double acc = 0.0;
+    for (int k = 0; k < 8; ++k) acc += x[k];
+    if (acc == -1.0) g_fma_sink = acc;
+}
+
+double launch_fma_probe(int nsm, int iters, cudaStream_t st, float* ms) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = nsm * 4, threads = 256;
+    k_fma_probe<<<blocks, threads, 0, st>>>(iters / 8 + 1, 0.999999, 1e-7);   // warm-up
+    cudaEventRecord(e0, st);
+    k_fma_probe<<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-7);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_launch_counter += 2;
+    return 2.0 * 8.0 * (double)iters * blocks * threads;
 }
 
 }  // namespace ffe

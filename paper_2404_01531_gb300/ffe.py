@@ -30,7 +30,7 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
            "ffe_rhs_vjp", "ffe_adjoint_step", "ffe_luminosity", "ffe_initial_tangent",
            "ffe_freeze_mask", "ffe_adjoint_forward", "ffe_adjoint_reverse", "ffe_save", "ffe_load",
            "ffe_constraints", "ffe_get_coords", "ffe_eval_recip", "ffe_get_mask", "ffe_set_frozen_masks",
-           "ffe_diagnostic",
+           "ffe_diagnostic", "ffe_fp64_fma_rate",
            "ffe_last_error",
            "ffe_destroy"]
 
@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
                 ("filter_on", ctypes.c_int), ("filter_a", ctypes.c_double), ("filter_b", ctypes.c_double),
                 ("tci_on", ctypes.c_int), ("tci_M", ctypes.c_int), ("tci_alpha", ctypes.c_double),
                 ("weno_eps", ctypes.c_double), ("fd_corrector", ctypes.c_int),
-                ("constraint_mode", ctypes.c_int), ("omega_star", ctypes.c_double), ("recon", ctypes.c_int)]
+                ("constraint_mode", ctypes.c_int), ("omega_star", ctypes.c_double), ("recon", ctypes.c_int),
+                ("fd_chunk", ctypes.c_int), ("fd_capacity", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -114,6 +115,7 @@ def load():
         "ffe_get_mask": [P, ctypes.POINTER(P), ctypes.POINTER(i)],
         "ffe_set_frozen_masks": [P, i],
         "ffe_diagnostic": [P, i, ctypes.POINTER(d), ctypes.POINTER(d)],
+        "ffe_fp64_fma_rate": [P, ctypes.POINTER(d)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -171,6 +173,16 @@ def eval_recip(x, y, stream=None):
                                 ctypes.c_void_p(st.cuda_stream)))
 
 
+def fp64_fma_rate(stream=None):
+    """Measured FP64 FMA throughput of the current device in TFLOP/s (see
+    ffe_fp64_fma_rate in include/ffe.h)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    r = ctypes.c_double(0.0)
+    check(load().ffe_fp64_fma_rate(ctypes.c_void_p(st.cuda_stream), ctypes.byref(r)))
+    return r.value
+
+
 def check(status):
     if status != 0:
         msg = load().ffe_last_error().decode()
@@ -180,7 +192,8 @@ def check(status):
 def params_from(p):
     return Params(p["eta"], p["kappa_psi"], p["kappa_phi"], p["cfl"], p["c_over_D"], p.get("dt", 0.0),
                   p["filter_on"], p["filter_a"], p["filter_b"], p["tci_on"], p["tci_M"], p["tci_alpha"],
-                  p["weno_eps"], p["fd_corrector"], p["constraint_mode"], p["omega_star"], p.get("recon", 0))
+                  p["weno_eps"], p["fd_corrector"], p["constraint_mode"], p["omega_star"], p.get("recon", 0),
+                  p.get("fd_chunk", 0), p.get("fd_capacity", 0))
 
 
 class _DevArray:
@@ -369,10 +382,18 @@ class Context:
         return xd.view(3, -1), xf.view(3, -1)
 
     def split(self, U):
+        """(DG blocks [9][E][np1^3], FD blocks [9][E][nc^3]) of a state vector;
+        with an FD slot pool the FD block of an element without a slot is zero."""
         U = np.asarray(U)
         E, np1, nc = self.n_elem, self.np1, self.nc
         dg = U[:NV * self.n_dg].reshape(NV, E, np1, np1, np1)
-        fd = U[NV * self.n_dg:].reshape(NV, E, nc, nc, nc)
+        if self.n_fd == E * nc ** 3:
+            fd = U[NV * self.n_dg:].reshape(NV, E, nc, nc, nc)
+        else:
+            sl = self.layout()[1]
+            pool = U[NV * self.n_dg:].reshape(NV, -1, nc, nc, nc)
+            fd = np.zeros((NV, E, nc, nc, nc))
+            fd[:, sl >= 0] = pool[:, sl[sl >= 0]]
         return dg, fd
 
     def join(self, udg, ufd):

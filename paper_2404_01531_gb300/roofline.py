@@ -4,9 +4,15 @@ from the instructions the kernels happen to issue.  Used for the roofline
 fraction: achieved = count x units per launch / launch time."""
 import math
 
-# FP64 peak: 2 FMA lanes per clock per SM x 2 flops x 152 SMs x 2.07 GHz
-# (the GB300's nominal 1.25 TFLOP/s FP64 at its 2070 MHz maximum SM clock).
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+def fp64_peak_tflops(n_sm, sm_mhz):
+    """FP64 peak from the unit counts and the clock: 2 FMA lanes per clock per
+    SM x 2 flops x SMs x clock (152 SMs at 2070 MHz: the GB300's nominal
+    1.25 TFLOP/s FP64)."""
+    return 2 * 2 * n_sm * sm_mhz * 1e6 / 1e12
+
+
+FP64_PEAK_TFLOPS = fp64_peak_tflops(152, 2070.0)   # the GB300's nominal figure
 
 
 def filter_rank(P, a=36.0, b=50.0):

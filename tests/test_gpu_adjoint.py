@@ -241,6 +241,44 @@ def test_hybrid_rhs_vjp_matches_finite_differences(ffe, eta):
     ctx.close()
 
 
+@pytest.mark.parametrize("pattern", ["all_fd_chunked", "checker"])
+def test_hybrid_rhs_vjp_ghosts_between_wedges(ffe, pattern):
+    """The reverse mode of the FD ghosts interpolated across faces between
+    cubed-sphere wedges: every element on FD (FD neighbours across every wedge
+    face; the FD list walked in chunks of 5 elements), and a checkerboard of
+    DG and FD elements (DG neighbours across wedge faces), against
+    extrapolated central differences of the right-hand side."""
+    cfg = _tiny(50.0)
+    if pattern == "all_fd_chunked":
+        cfg["params"]["fd_chunk"] = 5
+    ctx = ffe.Context(cfg)
+    U0, m = ctx.state()
+    E = ctx.n_elem
+    e = torch.arange(E, device=m.device)
+    if pattern == "all_fd_chunked":
+        mask = torch.ones_like(m)
+    else:
+        na, nr = cfg["n_ang"], cfg["n_rad"]
+        mask = ((e % na + (e // na) % na + (e // (na * na)) % nr + e // (na * na * nr)) % 2).to(torch.uint8)
+    ctx.set_state(U0.clone(), mask)
+    ctx.set_initial(keep_mask=True)
+    ctx.freeze_mask(True)
+    U, act = _perturb(ctx, mask, 21)
+    lam, dlt = _dirs(U, act, 22)
+    vjp = torch.zeros_like(U)
+    ctx.rhs_vjp(U, lam, vjp)
+    assert float(vjp[~act].abs().max()) == 0.0
+
+    def f(h):
+        F = torch.zeros_like(U)
+        ctx.rhs(U + h * dlt, F)
+        return F
+    fd = _richardson(f, 1e-8, lam)
+    ad = float(torch.dot(vjp, dlt))
+    assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+    ctx.close()
+
+
 def test_hybrid_adjoint_step_matches_finite_differences(ffe):
     ctx, mask = _hybrid(ffe)
     U, act = _perturb(ctx, mask, 13)

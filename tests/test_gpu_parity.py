@@ -144,3 +144,58 @@ def test_step_cleaning_mode_single_element_periodic(ffe):
     cfg = W.cleaning_mode(n=1)
     U, mask, st, ctx = _run_both(ffe, cfg, 20)
     compare_state(ctx, U, st, 1e-8)
+
+
+def test_rhs_mixed_dg_fd_dirichlet_small_chunks(ffe):
+    """The mixed box with the FD list walked in chunks of 5 elements (the
+    chunk offsets w0 > 0 of the ghost fill, flux and update kernels)."""
+    cfg = W.breakdown(nx=6, ny=2, nz=2, x_half=0.1875)
+    cfg["params"]["fd_chunk"] = 5
+    pr = Problem(cfg)
+    rng = np.random.default_rng(8)
+    E = pr.disc.E
+    mask = (rng.random(E) < 0.6).astype(np.uint8)
+    assert mask.sum() > 10
+    st = dict(mask=mask, udg=rng.normal(size=(9, E, 6, 6, 6)) + 1.0, ufd=rng.normal(size=(9, E, 11, 11, 11)) + 1.0)
+    assert _rhs_parity(ffe, cfg, st, pr) <= 1e-11
+
+
+def test_step_breakdown_slab_100_steps_chunked(ffe):
+    """The breakdown workload's element width and x extent (64 elements along
+    x, one across y and z), 100 steps with the indicator switching elements,
+    the FD list walked one element per chunk."""
+    cfg = W.breakdown(nx=64, ny=1, nz=1, x_half=2.0)
+    cfg["params"]["fd_chunk"] = 1
+    U, mask, st, ctx = _run_both(ffe, cfg, 100)
+    assert mask.sum() >= 2
+    compare_state(ctx, U, st, 1e-8)
+
+
+def test_step_breakdown_with_an_fd_slot_pool(ffe):
+    """A single context whose FD block is a pool of 6 slots (fewer than its 32
+    elements): elements take a slot when they switch to FD and return it at
+    FD -> DG; the steps equal the oracle's as with one slot per element, and
+    the state vector is smaller by the unused FD blocks."""
+    cfg = W.breakdown(nx=16, ny=2, nz=1, x_half=0.5)
+    cfg["params"]["fd_capacity"] = 6
+    ctx0 = ffe.Context(W.breakdown(nx=16, ny=2, nz=1, x_half=0.5))
+    n_full = ctx0.n_state
+    ctx0.close()
+    ctx = ffe.Context(cfg)
+    ctx.set_initial()
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    S = Stepper(pr)
+    near = set()
+    for _ in range(30):
+        st = S.step(st)
+        near |= set(S.near)
+    ctx.step(30)
+    U, mask = ctx.download()
+    near |= set(ctx.near_threshold())
+    assert ctx.status() == 0
+    assert set(np.nonzero(mask != st["mask"])[0].tolist()) <= near
+    assert 0 < mask.sum() <= 6
+    assert ctx.n_state == 9 * (ctx.n_dg + 6 * ctx.nc ** 3) < n_full
+    compare_state(ctx, U, st, 1e-8)
+    ctx.close()

@@ -12,6 +12,7 @@ from oracle.geometry import ShellMesh, Discretisation, BC_DIRICHLET
 from oracle.metric import ks_metric
 from oracle.ops import deriv
 from oracle.problem import Problem
+from oracle.stepper import Stepper
 from oracle.basis import Tables
 
 
@@ -176,14 +177,13 @@ def test_fd_wald_residual_converges_within_wedges():
     assert f["wedge"] < 2e-3, (c, f)
 
 
-@pytest.mark.xfail(strict=True, reason="ghost cells across cubed-sphere wedge boundaries are the neighbour "
-                                       "wedge's own cells, not values on the extension of the local grid")
-def test_fd_wald_residual_converges_between_wedges_with_copied_ghosts():
-    """At faces between wedges the neighbour's cells do not continue the local
-    grid lines, and copying them as ghosts is inconsistent: the residual there
+def test_fd_wald_residual_does_not_converge_between_wedges_with_copied_ghosts():
+    """Why the ghosts are interpolated: at faces between wedges the
+    neighbour's cells do not continue the local grid lines, and copying them
+    as ghosts (prm["ghost_interp"] off) is inconsistent -- the residual there
     does not fall under refinement (1.7e-2 -> 3.0e-2)."""
     c, f = _wald_fd_residuals(False)
-    assert f["between_wedges"] < c["between_wedges"] / 3, (c, f)
+    assert f["between_wedges"] > c["between_wedges"] / 3, (c, f)
 
 
 def test_fd_wald_residual_converges_between_wedges_with_interpolated_ghosts():
@@ -209,7 +209,50 @@ def test_interpolated_ghosts_equal_copied_ghosts_on_aligned_grids():
     pr = Problem(cfg)
     st = pr.initial_state()
     st["mask"][[0, 3]] = 1
+    pr.prm["ghost_interp"] = False
     a = rhs_fd(st, pr.disc, pr.met, pr.prm)
     pr.prm["ghost_interp"] = True
     b = rhs_fd(st, pr.disc, pr.met, pr.prm)
     assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+
+
+def _table2():
+    """Rows (P, N_r, N_Omega, dt, error) of tests/golden/table2_wald.txt (the
+    paper's Table II, Sec. IV.B.1)."""
+    import os
+    rows = []
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table2_wald.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        P, res, dt, err = line.split()
+        nr, nom = (int(x) for x in res.split("x"))
+        rows.append((int(P), nr, nom, float(dt), float(err)))
+    return rows
+
+
+def test_exact_wald_l2_error_in_the_band_of_table2():
+    """The paper's exact-Wald convergence test (Sec. IV.B.1, Table II): a = 0,
+    r in [1.99 M, 20 M], eta = 0, DG-P5 at the low resolution (1 radial x 6
+    angular elements, one per wedge), the table's time step, evolved to
+    t = 5 M; L2 = sqrt((1/n) sum_k |B~_k - B~_exact,k|^2) over the n nodes.
+    The paper imposes nothing at the inner surface (inside the horizon) and
+    a Dirichlet state at the outer one; here both surfaces take the exact
+    state, so the error is compared with the table's within a factor of 2
+    (measured 7.4e-4 against 8.71e-4)."""
+    P, nr, nom, dt, err = _table2()[0]
+    assert (P, nr, nom) == (5, 1, 6)
+    na = int(round(np.sqrt(nom / 6)))
+    cfg = W.wald(n_ang=na, n_rad=nr, P=P, r_in=1.99, r_out=20.0, spin=0.0)
+    cfg["params"].update(tci_on=0, dt=dt)
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    S = Stepper(pr)
+    n = int(round(5.0 / dt))
+    for _ in range(n):
+        st = S.step(st)
+    d = pr.disc
+    ex = pr.initial(d.xyz.reshape(3, -1)).reshape((9,) + d.xyz.shape[1:])
+    v = st["udg"][3:6] - ex[3:6]
+    l2 = np.sqrt((v ** 2).sum() / v[0].size)
+    assert err / 2 < l2 < 2 * err, (l2, err)

@@ -82,6 +82,71 @@ def test_mixed_dg_fd_rhs_exact_on_linear_fields(recon, corr):
                                    atol=1e-10 * scale)
 
 
+@pytest.mark.parametrize("recon,corr", [(0, 1), (1, 0)])
+def test_mixed_dg_fd_rhs_exact_with_a_linear_current(recon, corr):
+    """Currents across DG/FD interfaces (Sec. II.B current, Sec. III.C.2
+    interfaces): a constant B~ (so B~^2 is constant), E~ linear in x with
+    E~^2 < B~^2 in the box, a constant charge q~ and eta > 0 make the drift
+    current q~ (E~ x B~)/B~^2 and the parallel current eta (E~.B~) B~/B~^2
+    linear in x.  Every piece of the hybrid scheme is exact on them: the
+    nodal current of a DG neighbour evaluated at an FD element's ghost
+    centres, the 6-point FD->DG projection of an FD neighbour's cell currents
+    at a DG element's face, the reconstruction of J~ and the q~ flux.  So at
+    every DG node and FD cell
+      dE/dt = -J_drift(x),  dB/dt = -curl E,  dpsi/dt = -div E + q,
+      dphi/dt = 0,          dq/dt = -div J  (a constant).
+    A current dropped, taken from the wrong neighbour or oriented wrongly at an
+    interface fails it."""
+    rng = np.random.default_rng(31)
+    B = np.array([1.3, -0.7, 0.9])
+    AE = 0.1 * rng.normal(size=(3, 3))        # AE[i, j] = d_j E^i
+    E0 = 0.2 * rng.normal(size=3)
+    q0, eta = 0.8, 3.0
+    B2 = B @ B
+
+    def fn(xyz):
+        sh = (1,) * (xyz.ndim - 1)
+        U = np.zeros((9,) + xyz.shape[1:])
+        U[0:3] = E0.reshape((3,) + sh) + np.einsum('ij,j...->i...', AE, xyz)
+        U[3:6] = B.reshape((3,) + sh)
+        U[8] = q0
+        return U
+    cfg = _box((3, 2, 1), bc="dirichlet", eta=eta, recon=recon, fd_corrector=corr)
+    pr = Problem(cfg)
+    pr.prm["dirichlet"] = fn
+    E = pr.disc.E
+    mask = np.zeros(E, np.uint8)
+    mask[[0, 2, 4]] = 1
+    Nc = pr.T.nc
+    udg = fn(pr.disc.xyz.reshape(3, -1)).reshape((9,) + pr.disc.xyz.shape[1:])
+    ufd = fn(pr.disc.xyz_fd.reshape(3, -1)).reshape((9, E, Nc, Nc, Nc))
+    Emax = max(np.sqrt((udg[0:3] ** 2).sum(axis=0)).max(), np.sqrt((ufd[0:3] ** 2).sum(axis=0)).max())
+    assert Emax ** 2 < B2          # the rectifier max(E^2 - B^2, 0) is off
+    st = dict(mask=mask, udg=udg, ufd=ufd)
+    curl = lambda g: np.array([g[2, 1] - g[1, 2], g[0, 2] - g[2, 0], g[1, 0] - g[0, 1]])
+    # d_j J^i of J = q (E x B)/B^2 + eta (E.B) B/B^2
+    dJ = np.stack([q0 * np.cross(AE[:, j], B) / B2 + eta * (AE[:, j] @ B) * B / B2 for j in range(3)], axis=1)
+    divJ = np.trace(dJ)
+
+    def expected(U):
+        Ev = U[0:3]
+        jd = q0 * np.cross(Ev, B, axis=0) / B2
+        ex = np.zeros_like(U)
+        ex[0:3] = -jd
+        ex[3:6] = -curl(AE).reshape((3,) + (1,) * (U.ndim - 1))
+        ex[6] = -np.trace(AE) + q0
+        ex[8] = -divJ
+        return ex
+    rdg = rhs_dg(st, pr.disc, pr.met, pr.prm)[:, mask == 0]
+    rfd = rhs_fd(st, pr.disc, pr.met, pr.prm)[:, mask == 1]
+    edg = expected(udg[:, mask == 0])
+    efd = expected(ufd[:, mask == 1])
+    scale = max(np.abs(edg).max(), abs(divJ))
+    np.testing.assert_allclose(rdg, edg, atol=1e-10 * scale)
+    np.testing.assert_allclose(rfd, efd, atol=1e-10 * scale)
+    assert abs(divJ) > 0.05 and np.abs(edg[0:3]).max() > 0.05
+
+
 @pytest.mark.parametrize("which", ["dg", "fd"])
 def test_conservation_periodic(which):
     """Linear Maxwell (eta = 0, q = 0) on a periodic box: the LGL-quadrature
@@ -349,3 +414,40 @@ def test_rollback_bookkeeping_is_exact_on_linear_fields(monkeypatch):
         np.testing.assert_allclose(got["ufd"][:, e], want, atol=1e-11 * scale)
     # the reference really moved: the step changed the state by more than rounding
     assert np.abs(ref["udg"][:, targets] - st0["udg"][:, targets]).max() > 1e-3 * scale
+
+
+def _fast_wave_error_with(stepper_cls, eta, steps=10):
+    from oracle import initial as ini
+    cfg = W.fast_wave(n=2, P=5)
+    cfg["params"].update(eta=eta, tci_on=0)
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    S = stepper_cls(pr)
+    for _ in range(steps):
+        st = S.step(st)
+    ex = ini.fast_wave(pr.disc.xyz.reshape(3, -1), t=steps * pr.dt).reshape((9,) + pr.disc.xyz.shape[1:])
+    return np.abs(st["udg"] - ex).max()
+
+
+def test_filter_before_the_stiff_solve_keeps_the_smooth_wave_independent_of_eta():
+    """The order inside a substep (explicit part -> filter -> stiff solve,
+    reading of Sec. III.A/III.B): the smooth fast wave is force-free (E.B = 0,
+    E^2 < B^2), so the driver current must leave it alone at any
+    conductivity: its error after 10 steps is the same at eta = 1e5 and 1e7 as
+    at eta = 0.  Swapping the order (solve, then filter; planted below in a
+    copy of the oracle's stepper) leaves a parallel E~ of the size of the
+    filtered top mode in every stage state, which the q~ flux carries
+    amplified by eta: the error grows by orders of magnitude (measured 45 at
+    eta = 1e5 against 4.4e-3)."""
+    import types
+    import oracle.stepper as SM
+    base = _fast_wave_error_with(Stepper, 0.0)
+    for eta in (1e5, 1e7):
+        assert abs(_fast_wave_error_with(Stepper, eta) - base) <= 1e-9 * base, eta
+    src = open(SM.__file__).read()
+    planted = src.replace("return self.solve(self.filt(R, mk), mk)", "return self.filt(self.solve(R, mk), mk)")
+    assert planted.count("self.filt(self.solve(R, mk), mk)") == 2
+    mod = types.ModuleType("oracle.stepper_swapped")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(planted, "stepper_swapped", "exec"), mod.__dict__)
+    assert _fast_wave_error_with(mod.Stepper, 1e5) > 100 * base
