@@ -188,6 +188,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_wald(args):
+    """The Wald workload (Kerr-Schild a = 0.9, 6 wedges x 8x8x16, P = 5,
+    r in [1.5, 50], exact Wald field, Dirichlet at both ends) for 1000 steps
+    with the troubled-cell indicator on: step time and rate, the paper's L2
+    error of B~ against the exact field (Sec. IV.B.1) at steps 100, 500 and
+    1000, the RMS of the divergence-cleaning fields psi~, phi~ (constraint
+    monitors) and the FD population."""
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = W.wald()
+    cfg["params"]["tci_on"] = 1
+    ctx = ffe.Context(cfg)
+    ctx.set_initial()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows, done, ms_total, u0 = [], 0, 0.0, ctx.info().node_updates
+    for target in (100, 500, 1000):
+        torch.cuda.synchronize()
+        e0.record(st)
+        ctx.step(target - done)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        done = target
+        l2, n = ctx.diagnostic("l2_err")
+        rows.append({"step": target, "t": ctx.info().t, "l2_B": l2, "rms_psi": ctx.diagnostic("l2_err", (6, 1))[0],
+                     "rms_phi": ctx.diagnostic("l2_err", (7, 1))[0], "fd_elements": ctx.info().n_fd_elem})
+    units = ctx.info().node_updates - u0
+    line = {"metric": METRIC, "value": units / (ms_total / 1e3), "unit": UNIT, "n_gpus": 1, "steps": done,
+            "warmup": 0, "ms_per_step": ms_total / done, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Wald field, Kerr-Schild M=1 a=0.9, 6 wedges x 8x8x16, P=5, r in [1.5, 50], eta=0, "
+                                   "indicator on", "elements": ctx.n_elem},
+            "wald": rows, "status_bits": ctx.status()}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_shell(args):
     """The neutron-star shell (6 wedges x 6x6x12, P=5, eta=1e5) with its three
     innermost radial layers on FD subcells and the mask frozen: an FD-heavy
@@ -412,12 +451,25 @@ def run_oned(args):
 
 def run_pulsars(args):
     """Batched shells: one launch per kernel and substep for every instance,
-    against the same instances advanced one context at a time."""
+    against the same instances advanced one context at a time.  Under
+    torchrun the batch is split by whole instances over the ranks
+    (partition.assign_instances; no exchange on the data path): each rank
+    advances its own batched context, the timing is the slowest rank's and the
+    units are summed (fixed total work: strong scaling)."""
     import torch
     from paper_2404_01531_gb300 import ffe
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    cfgs = W.pulsars(n_inst=args.n_inst)
+    from paper_2404_01531_gb300.partition import instances_of
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfgs_all = W.pulsars(n_inst=args.n_inst)
+    mine = instances_of(cfgs_all, ws, rank)
+    cfgs = [cfgs_all[i] for i in mine]
     E = sum(6 * c["n_ang"] ** 2 * c["n_rad"] for c in cfgs)
+    E_all = sum(6 * c["n_ang"] ** 2 * c["n_rad"] for c in cfgs_all)
     b = ffe.BatchContext(cfgs, fd_capacity=int(args.fd_capacity * E))
     b.set_initial()
     b.step(max(args.warmup, 3))
@@ -425,13 +477,19 @@ def run_pulsars(args):
     st = torch.cuda.current_stream()
     u0 = b.info().node_updates
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     e0.record(st)
     b.step(args.steps)
     e1.record(st)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     ms_b = e0.elapsed_time(e1)
     inf = b.info()
     units_b = inf.node_updates - u0
+    ms_max, units_all = combine_ranks(ms_b, units_b, dist, "cuda")
     fd_end = inf.n_fd_elem
     status = b.status()
     b.set_profiling(True)
@@ -439,31 +497,40 @@ def run_pulsars(args):
     b.set_profiling(False)
     prof = b.profile_read()
     b.close()
-    # one context per instance, same steps, timed one after the other
-    ms_s, units_s = 0.0, 0
-    for c in cfgs:
-        s = ffe.Context(c)
-        s.set_initial()
-        s.step(max(args.warmup, 3))
-        torch.cuda.synchronize()
-        u0 = s.info().node_updates
-        e0.record(st)
-        s.step(args.steps)
-        e1.record(st)
-        torch.cuda.synchronize()
-        ms_s += e0.elapsed_time(e1)
-        units_s += s.info().node_updates - u0
-        s.close()
-    vb, vs = units_b / (ms_b / 1e3), units_s / (ms_s / 1e3)
-    line = {"metric": METRIC, "value": vb, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"pulsars: {len(cfgs)} rotating-dipole shells (seed 1531), P in {{4,5}}",
-                       "elements": E, "fd_elements_end": fd_end, "fd_capacity": int(args.fd_capacity * E)},
-            "one_instance_per_launch": {"value": vs, "ms_per_step": ms_s / args.steps},
-            "batched_over_single": vb / vs, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
-            "status_bits": status}
-    print(json.dumps(line), flush=True)
+    vb = units_all / (ms_max / 1e3)
+    single = None
+    if ws == 1:
+        # one context per instance, same steps, timed one after the other
+        ms_s, units_s = 0.0, 0
+        for c in cfgs:
+            s1 = ffe.Context(c)
+            s1.set_initial()
+            s1.step(max(args.warmup, 3))
+            torch.cuda.synchronize()
+            u0 = s1.info().node_updates
+            e0.record(st)
+            s1.step(args.steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms_s += e0.elapsed_time(e1)
+            units_s += s1.info().node_updates - u0
+            s1.close()
+        vs = units_s / (ms_s / 1e3)
+        single = {"value": vs, "ms_per_step": ms_s / args.steps}
+    if rank == 0:
+        line = {"metric": METRIC, "value": vb, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"pulsars: {len(cfgs_all)} rotating-dipole shells (seed 1531), P in {{4,5}}",
+                           "elements": E_all, "fd_elements_end_rank0": fd_end,
+                           "fd_capacity": int(args.fd_capacity * E),
+                           "parallelism": f"whole instances over {ws} ranks" if ws > 1 else "one batched context"},
+                "one_instance_per_launch": single,
+                "batched_over_single": vb / single["value"] if single else None,
+                "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()}, "status_bits": status}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def adjoint_measure(steps=500, every=25, r_L=20.0, fd_check=False):
@@ -519,6 +586,11 @@ def adjoint_measure(steps=500, every=25, r_L=20.0, fd_check=False):
     e1.record(st)
     torch.cuda.synchronize()
     rev_ms = e0.elapsed_time(e1) / k
+    # where the backward sweep's time goes (eager, per-kernel events)
+    ctx.set_profiling(True)
+    ctx.adjoint_reverse(U0, stages, lam, out)
+    ctx.set_profiling(False)
+    rev_prof = {kk: v[1] for kk, v in ctx.profile_read().items()}
     del stages
     ctx.set_state(U0, m0)
     L, g, tm = luminosity_gradient(ctx, steps, r_L=r_L, every=every)
@@ -530,6 +602,7 @@ def adjoint_measure(steps=500, every=25, r_L=20.0, fd_check=False):
            "forward_ms_per_step": fwd_ms / steps, "adjoint_step_ms": adj_ms,
            "adjoint_step_over_forward_step": adj_ms / (fwd_ms / steps),
            "adjoint_reverse_ms": rev_ms, "adjoint_reverse_over_forward_step": rev_ms / (fwd_ms / steps),
+           "reverse_kernel_ms": rev_prof,
            "gradient_s": tm["forward_s"] + tm["adjoint_s"], "forward_s": fwd_ms / 1e3,
            "gradient_over_forward": (tm["forward_s"] + tm["adjoint_s"]) / (fwd_ms / 1e3),
            "Lbar": L, "grad": g}
@@ -582,17 +655,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64,
                     help="elements along x (same width 4/64; smaller values for profiler captures)")
-    ap.add_argument("--workload", default="breakdown", choices=["breakdown", "pulsars", "adjoint", "shell", "oned", "dgphases"],
+    ap.add_argument("--workload", default="breakdown",
+                    choices=["breakdown", "pulsars", "adjoint", "shell", "oned", "dgphases", "wald"],
                     help="pulsars: the 32-shell batch, batched launch vs one context per instance; "
                          "adjoint: luminosity gradient of one neutron-star shell (--steps steps); "
                          "shell: that shell with three FD layers, frozen mask (curved FD kernels); "
                          "oned: the paper's 1-D tests and its DG/FD split experiment; "
-                         "dgphases: cost of the DG kernel's filter, indicator and stiff-current phases")
+                         "dgphases: cost of the DG kernel's filter, indicator and stiff-current phases; "
+                         "wald: the Kerr-Schild Wald shell, 1000 steps, indicator on")
     ap.add_argument("--no-adjoint", action="store_true", help="breakdown: skip the adjoint/forward timing")
     ap.add_argument("--recon", default="weno5z", choices=list(RECON),
                     help="breakdown and shell: FD reconstruction (the paper's WENO5-Z, or MP5)")
     ap.add_argument("--n-inst", type=int, default=32)
     ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
+    ap.add_argument("--fd-slots", type=float, default=0.25,
+                    help="breakdown: FD slot pool as a fraction of the elements (1 = one FD block per element)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -600,6 +677,8 @@ def main():
         return run_pulsars(args)
     if args.workload == "shell":
         return run_shell(args)
+    if args.workload == "wald":
+        return run_wald(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
     if args.workload == "oned":
@@ -621,6 +700,9 @@ def main():
 
     cfg = W.breakdown(nx=args.nx, x_half=2.0 * args.nx / 64)
     cfg["params"]["recon"] = RECON[args.recon]
+    n_elem = args.nx * 8 * 8
+    fd_slots = min(n_elem, max(1, int(round(args.fd_slots * n_elem))))
+    cfg["params"]["fd_capacity"] = fd_slots
     stream = torch.cuda.current_stream()
     ctx = ffe.Context(cfg, stream=stream)
     ctx.set_initial()
@@ -754,7 +836,7 @@ def main():
             "config": {"workload": f"breakdown {args.nx}x8x8 P=5 (FFE breakdown / current sheet, eta=1e3)",
                        "elements": E, "P": P, "dg_nodes": E * nn, "fd_elements_end": n_fd_end,
                        "parallelism": f"replicas x{ws}", "l2": "working set > L2 (no flush needed)",
-                       "recon": args.recon},
+                       "recon": args.recon, "fd_slots": fd_slots},
             "roofline": roof, "roofline_dg": roof_dg, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
             "adjoint": adj, "status_bits": status}

@@ -13,6 +13,7 @@ import numpy as np
 
 from . import initial, physics as ph
 from .basis import lagrange_matrix
+from .ops import apply_3d
 from .problem import Problem
 from .stepper import Stepper
 
@@ -53,9 +54,12 @@ def luminosity(pr, udg, lw):
     return np.sum(np.sum(S * np.moveaxis(nrm, 1, 0), axis=0) * W)
 
 
-def lbar(cfg, nsteps, params=None, r_L=20.0):
+def lbar(cfg, nsteps, params=None, r_L=20.0, mask=None):
     """Mean luminosity over steps 1..nsteps for dipole (mu, chi) and star Omega;
-    params = (mu, chi, Omega) may be complex (complex-step)."""
+    params = (mu, chi, Omega) may be complex (complex-step).  mask (optional,
+    uint8 per element): a fixed DG/FD mask -- its FD elements start with the
+    initial data at their subcell centres, no element switches, and an FD
+    element enters the luminosity through its FD -> DG projection."""
     cfg = dict(cfg)
     cfg["params"] = dict(cfg["params"])
     kind, kw = cfg["initial"]
@@ -63,30 +67,46 @@ def lbar(cfg, nsteps, params=None, r_L=20.0):
     mu, chi, om = params if params is not None else (kw["mu"], kw["chi"], cfg["params"]["omega_star"])
     kw.update(mu=mu, chi=chi)
     cfg["initial"] = (kind, kw)
+    if mask is not None:
+        cfg["params"]["tci_on"] = 1        # the subcell grid is built; the mask is frozen below
     pr = Problem(cfg)
     pr.prm["omega"] = om
     pr.initial = lambda xyz: initial.evaluate(kind, xyz, **kw)
     pr.prm["dirichlet"] = pr.initial
     d = pr.disc
     udg = initial.evaluate(kind, d.xyz.reshape(3, -1), **kw).reshape((9,) + d.xyz.shape[1:])
-    st = dict(mask=np.zeros(d.E, np.uint8), udg=udg, ufd=np.zeros((9, d.E, 1, 1, 1), dtype=udg.dtype), t=0.0)
+    if mask is None:
+        st = dict(mask=np.zeros(d.E, np.uint8), udg=udg, ufd=np.zeros((9, d.E, 1, 1, 1), dtype=udg.dtype), t=0.0)
+    else:
+        pr.prm["tci_on"] = 0
+        nc = pr.T.nc
+        ufd = np.zeros((9, d.E, nc, nc, nc), dtype=udg.dtype)
+        for e in np.nonzero(mask)[0]:
+            ufd[:, e] = initial.evaluate(kind, d.xyz_fd[:, e].reshape(3, -1), **kw).reshape((9, nc, nc, nc))
+        st = dict(mask=np.asarray(mask, dtype=np.uint8).copy(), udg=udg, ufd=ufd, t=0.0)
     S = Stepper(pr)
     lw = luminosity_weights(pr, r_L)
     acc = 0.0
     for _ in range(nsteps):
         st = S.step(st)
-        acc = acc + luminosity(pr, st["udg"], lw)
+        u = st["udg"]
+        if mask is not None and mask.any():
+            u = u.copy()
+            fd = np.nonzero(st["mask"])[0]
+            u[:, fd] = apply_3d(pr.T.R, st["ufd"][:, fd])
+        acc = acc + luminosity(pr, u, lw)
     return acc / nsteps
 
 
-def lbar_gradient_complex_step(cfg, nsteps, h=1e-30, r_L=20.0):
+def lbar_gradient_complex_step(cfg, nsteps, h=1e-30, r_L=20.0, mask=None):
     """d Lbar / d (mu, chi, Omega) by complex step (exact to rounding for the
-    frozen-branch map: every branch is taken on the real part)."""
+    frozen-branch map: every branch is taken on the real part); mask: a fixed
+    DG/FD mask (see lbar)."""
     kw = cfg["initial"][1]
     base = [kw["mu"], kw["chi"], cfg["params"]["omega_star"]]
     g = []
     for k in range(3):
         p = [complex(v) for v in base]
         p[k] += 1j * h
-        g.append(np.imag(lbar(cfg, nsteps, p, r_L)) / h)
+        g.append(np.imag(lbar(cfg, nsteps, p, r_L, mask)) / h)
     return np.array(g)

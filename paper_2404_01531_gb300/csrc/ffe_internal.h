@@ -20,6 +20,7 @@ constexpr int GH = 3;          // FD ghost layers
 // d_j alpha, d_j beta^i (index 3 j + i), gamma^jk Gamma^i_jk, K.
 enum MetIdx : int { M_ALPHA = 0, M_BETA = 1, M_GL = 4, M_GU = 10, M_SQRTG = 16, M_DALPHA = 17,
                     M_DBETA = 20, M_GTRACE = 29, M_K = 32, NMET = 33 };
+constexpr int NPM = 17;        // the pointwise part (alpha .. sqrt(gamma)), without derivatives
 
 // IMEX-SSP3(4,3,3) coefficients (Pareschi & Russo 2005).
 constexpr double IM_A = 0.24169426078821;
@@ -94,6 +95,15 @@ struct Dev {
     int curved, ks;
     const double* geo;
     const double* met;
+    // Kerr-Schild metric at FD points (null in flat space): subcell centres
+    // [NMET][E ncell]; face points [3][NPM][E (nc+1) nc^2]; ghost centres across
+    // Dirichlet faces [nbf][NPM][GH nc^2] and across faces between wedges
+    // [slot][NPM][GH nc^2] with slot gislot[e 6 + f]
+    const double* metfd;
+    const double* metff;
+    const double* metgb;
+    const double* metgi;
+    const int* gislot;
     double shell_rin, shell_c;
     int shell_na, shell_nr;
     // flat shells, per instance at InstInfo::tab (single context: 0), on the
@@ -128,6 +138,9 @@ struct Dev {
     // face fluxes [3 (x3 curved)][9][chunk][(nc+1) nc^2]
     double* ext;
     double* flux;
+    // FD->DG face traces of FD elements for their DG neighbours, per FD slot
+    // [6][12][np1^2] (k_fd_traces; null: none)
+    double* ftr;
 };
 
 // sizes of one element
@@ -148,6 +161,7 @@ __device__ __forceinline__ ES esz(const Dev& d, int e) { return es_of(elem_P(d, 
 __device__ __forceinline__ int64_t fdb(const Dev& d, int e) {
     return (int64_t)(d.fd_slot ? d.fd_slot[e] : e) * d.ncell;
 }
+__device__ __forceinline__ int fd_slot_of(const Dev& d, int e) { return d.fd_slot ? d.fd_slot[e] : e; }
 __device__ __forceinline__ double dt_of(const Dev& d, int e) { return d.einst ? d.inst[d.einst[e]].dt : d.dt; }
 __device__ __forceinline__ double omega_of(const Dev& d, int e) { return d.einst ? d.inst[d.einst[e]].omega : d.omega; }
 
@@ -162,6 +176,8 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int count_index, 
                        Field un, Field F2, Field F3, Field G1, Field G2, Field G3, Field G4,
                        Field Fout, Field Uout, Field Gout, cudaStream_t st);
 int fd_chunks(const Dev& d);
+// FD->DG face traces of the listed FD elements for their DG neighbours (Dev::ftr)
+void launch_fd_traces(const Dev& d, Field U, Field J, cudaStream_t st);
 // extended blocks (U, J~ with ghosts) of the listed FD elements of one chunk
 void launch_fd_fill(const Dev& d, const int* list, int count_index, int w0, Field U, Field J, cudaStream_t st);
 void launch_eval_recip(const double* x, double* y, int64_t n, cudaStream_t st);

@@ -341,6 +341,7 @@ struct ffe_ctx {
     int graph_kernels = 0;
     int nbf = 0;                     // boundary faces with Dirichlet data
     std::vector<int> h_bface;
+    std::vector<unsigned char> h_ginterp;   // [E][6] faces between cubed-sphere wedges
     ShellGeo shell{};
     double lam_max = 1.0;
     // batched contexts
@@ -515,6 +516,108 @@ MapFn ctx_map(ffe_ctx* c) {
 
 int host_P(const ffe_ctx* c, int e) { return c->batch ? c->h_eP[e] : c->d.P; }
 
+// Kerr-Schild metric at the FD points of every element (the FD kernels read
+// it there as the DG kernels read it at their nodes): subcell centres with the
+// derivative terms of the sources, [NMET][E ncell] (Dev::metfd); face points
+// of the three directions, [3][NPM][E nface] (Dev::metff; face m between cells
+// m-1 and m, tangential cell centres ta, tb along axes_of); ghost centres
+// across Dirichlet faces, [nbf][NPM][GH nc^2] (Dev::metgb, indexed like the
+// Dirichlet ghost states), and across faces between wedges,
+// [slot][NPM][GH nc^2] (Dev::metgi, slot Dev::gislot[e 6 + f]).  NPM: alpha,
+// beta^i, gamma_ij, gamma^ij, sqrt(gamma), the first NPM entries of NMET.
+ffe_status build_ks_fd_tables(ffe_ctx* c, const std::vector<double>& xfd) {
+    Dev& d = c->d;
+    const int E = d.E, nc = d.nc, ncell = d.ncell;
+    const int64_t nfc = (int64_t)(nc + 1) * nc * nc, ncells = (int64_t)E * ncell, nfaces = (int64_t)E * nfc;
+    const double M = c->met.M, a = c->met.a, dxi = 2.0 / nc;
+    MapFn map = ctx_map(c);
+    ffe_status s;
+    std::vector<double> mc((size_t)NMET * ncells);
+    parallel_for(ncells, [&](int64_t p) {
+        double x[3] = {xfd[p], xfd[ncells + p], xfd[2 * ncells + p]}, out[NMET];
+        ks_point(x, M, a, out);
+        for (int q = 0; q < NMET; ++q) mc[q * ncells + p] = out[q];
+    });
+    double* d_mc;
+    if ((s = dalloc(c, &d_mc, mc.size()))) return s;
+    CK(cudaMemcpy(d_mc, mc.data(), mc.size() * 8, cudaMemcpyHostToDevice));
+    std::vector<double>().swap(mc);
+    d.metfd = d_mc;
+    std::vector<double> mf((size_t)3 * NPM * nfaces);
+    parallel_for(E, [&](int64_t e) {
+        for (int k = 0; k < 3; ++k) {
+            const int t1 = k == 0 ? 1 : 0, t2 = k == 2 ? 1 : 2;
+            for (int64_t fi = 0; fi < nfc; ++fi) {
+                const int m = (int)(fi % (nc + 1)), ta = (int)((fi / (nc + 1)) % nc), tb = (int)(fi / ((nc + 1) * nc));
+                double xi[3], x[3], ij[3][3], out[NMET];
+                xi[k] = -1.0 + m * dxi;
+                xi[t1] = -1.0 + (ta + 0.5) * dxi;
+                xi[t2] = -1.0 + (tb + 0.5) * dxi;
+                map((int)e, xi, x, ij);
+                ks_point(x, M, a, out);
+                for (int q = 0; q < NPM; ++q) mf[((size_t)k * NPM + q) * nfaces + e * nfc + fi] = out[q];
+            }
+        }
+    });
+    double* d_mf;
+    if ((s = dalloc(c, &d_mf, mf.size()))) return s;
+    CK(cudaMemcpy(d_mf, mf.data(), mf.size() * 8, cudaMemcpyHostToDevice));
+    std::vector<double>().swap(mf);
+    d.metff = d_mf;
+    // ghost centres: the element's reference grid continued past the face
+    auto ghosts = [&](int e, int f, double* dst, int64_t stride) {
+        const int dd = f >> 1, sd = f & 1;
+        const int t1 = dd == 0 ? 1 : 0, t2 = dd == 2 ? 1 : 2;
+        for (int g = 0; g < GH; ++g)
+            for (int b = 0; b < nc; ++b)
+                for (int aa = 0; aa < nc; ++aa) {
+                    double xi[3], x[3], ij[3][3], out[NMET];
+                    xi[dd] = sd ? 1.0 + (g + 0.5) * dxi : -(1.0 + (g + 0.5) * dxi);
+                    xi[t1] = -1.0 + (aa + 0.5) * dxi;
+                    xi[t2] = -1.0 + (b + 0.5) * dxi;
+                    map(e, xi, x, ij);
+                    ks_point(x, M, a, out);
+                    for (int q = 0; q < NPM; ++q) dst[q * stride + (int64_t)g * nc * nc + aa + nc * b] = out[q];
+                }
+    };
+    const int64_t per = (int64_t)NPM * GH * nc * nc;
+    if (c->nbf > 0) {
+        std::vector<double> mg((size_t)c->nbf * per);
+        parallel_for(E, [&](int64_t e) {
+            for (int f = 0; f < 6; ++f) {
+                const int sl = c->h_bface[6 * e + f];
+                if (sl >= 0) ghosts((int)e, f, mg.data() + sl * per, (int64_t)GH * nc * nc);
+            }
+        });
+        double* d_mg;
+        if ((s = dalloc(c, &d_mg, mg.size()))) return s;
+        CK(cudaMemcpy(d_mg, mg.data(), mg.size() * 8, cudaMemcpyHostToDevice));
+        d.metgb = d_mg;
+    }
+    std::vector<int> gslot(6 * (size_t)E, -1);
+    int ng = 0;
+    for (size_t i = 0; i < c->h_ginterp.size(); ++i)
+        if (c->h_ginterp[i]) gslot[i] = ng++;
+    if (ng > 0) {
+        std::vector<double> mg((size_t)ng * per);
+        parallel_for(E, [&](int64_t e) {
+            for (int f = 0; f < 6; ++f) {
+                const int sl = gslot[6 * e + f];
+                if (sl >= 0) ghosts((int)e, f, mg.data() + sl * per, (int64_t)GH * nc * nc);
+            }
+        });
+        double* d_mg;
+        int* d_gs;
+        if ((s = dalloc(c, &d_mg, mg.size()))) return s;
+        if ((s = dalloc(c, &d_gs, gslot.size()))) return s;
+        CK(cudaMemcpy(d_mg, mg.data(), mg.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d_gs, gslot.data(), gslot.size() * sizeof(int), cudaMemcpyHostToDevice));
+        d.metgi = d_mg;
+        d.gislot = d_gs;
+    }
+    return FFE_OK;
+}
+
 // Faces between cubed-sphere wedges: there the FD ghosts are the neighbour's
 // data interpolated to this element's grid continued past the face
 // (k_fd_fill_ghosts_interp).  nbr: neighbour of every element face.
@@ -537,6 +640,7 @@ ffe_status set_ginterp(ffe_ctx* c, const std::vector<int>& nbr) {
                 any = true;
             }
         }
+    c->h_ginterp = gi;
     if (!any) return FFE_OK;
     unsigned char* p;
     ffe_status s;
@@ -672,6 +776,7 @@ ffe_status build_shell(ffe_ctx* c) {
         d.ks = 1;
         c->lam_max = 0.0;
         for (double v : lam) c->lam_max = fmax(c->lam_max, v);
+        if (c->prm.tci_on && (s = build_ks_fd_tables(c, xfd))) return s;
     }
     return FFE_OK;
 }
@@ -738,7 +843,7 @@ void enqueue_step(ffe_ctx* c) {
                        {SUB_B, c->Ub, c->F3, c->Ua, c->G4},
                        {SUB_C, c->Ua, c->Fs, c->un, c->G4}};
     for (const S& s : subs) {
-        if (!d.ks) launch_current(d, s.Uin, c->J, nullptr, 0, st);
+        if (!d.ks || d.metfd) launch_current(d, s.Uin, c->J, nullptr, 0, st);
         if (d.curved)
             launch_dg_substep_curved(d, s.sub, s.Uin, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, s.Fout,
                                      s.Uout, s.Gout, st);
@@ -767,7 +872,7 @@ ffe_status autotune(ffe_ctx* c) {
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     launch_build_lists(d, c->st);
-    if (!d.ks) launch_current(d, c->un, c->J, nullptr, 0, c->st);
+    if (!d.ks || d.metfd) launch_current(d, c->un, c->J, nullptr, 0, c->st);
     float best = 1e30f;
     int best_g = 0;
     for (int g : {d.nsm, 2 * d.nsm, 3 * d.nsm, 4 * d.nsm}) {
@@ -884,7 +989,7 @@ ffe_status finish_create(ffe_ctx* c, int fd_cap, const std::vector<int>& orders)
     if ((s = dalloc(c, &d.near_list, 4096))) return s;
     if ((s = dalloc(c, &d.counts, 8))) return s;
     if ((s = dalloc(c, &d.units, 3))) return s;   // node updates, FD and DG element updates
-    if (d.curved && !d.ks) {
+    if (d.curved) {
         // FD-point tables of the shell map (Dev::stab): gnomonic coordinate
         // X = tan(pi/4 e) and 1/(pi/4 (1 + X^2)) on the half-cell grid of the
         // angular rows, r and 1/r on that of the radial rows
@@ -943,6 +1048,7 @@ ffe_status finish_create(ffe_ctx* c, int fd_cap, const std::vector<int>& orders)
     const int64_t ne = d.nc + 2 * GH;
     if ((s = dalloc(c, &d.ext, (size_t)12 * d.chunk * ne * ne * ne))) return s;
     if ((s = dalloc(c, &d.flux, (size_t)(d.curved ? 9 : 3) * NV * d.chunk * (d.nc + 1) * d.nc * d.nc))) return s;
+    if ((s = dalloc(c, &d.ftr, (size_t)fd_cap * 6 * 12 * d.np1 * d.np1))) return s;
     return FFE_OK;
 }
 
@@ -1436,7 +1542,10 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
         return fail(FFE_EINVAL, "metric kind %d", metric->kind);
     if (metric->kind == FFE_METRIC_KERR_SCHILD) {
         if (domain->kind != FFE_DOMAIN_SHELL6) return fail(FFE_EINVAL, "Kerr-Schild needs a shell domain");
-        if (params->tci_on) return fail(FFE_ENOTIMPL, "FD subcells on the Kerr-Schild background are not built");
+        if (params->tci_on && params->fd_corrector)
+            return fail(FFE_ENOTIMPL, "the FD flux corrector is defined for Cartesian meshes, not the Kerr-Schild background");
+        if (params->tci_on && (domain->bc_lo[0] != FFE_BC_DIRICHLET || domain->bc_hi[0] != FFE_BC_DIRICHLET))
+            return fail(FFE_ENOTIMPL, "FD subcells on the Kerr-Schild background take Dirichlet shell boundaries");
         if (!(metric->M > 0) || !(fabs(metric->a) < 1)) return fail(FFE_EINVAL, "need M > 0 and |a| < 1");
         if (P < 3 || P > 5) return fail(FFE_EINVAL, "curved elements support 3 <= P <= 5");
     }
@@ -1827,8 +1936,12 @@ namespace {
 // on FD (elements change pool slots only through the indicator's switches).
 ffe_status check_mask(ffe_ctx* c, const unsigned char* m) {
     const Dev& d = c->d;
-    for (int e = 0; e < d.E; ++e)
+    for (int e = 0; e < d.E; ++e) {
         if (m[e] > 1) return fail(FFE_EINVAL, "mask of element %d is %d (0 = DG, 1 = FD)", e, m[e]);
+        if (m[e] == 1 && d.ks && !d.metfd)
+            return fail(FFE_ENOTIMPL, "FD elements on the Kerr-Schild background need a context created with the "
+                                      "indicator on (the metric at the FD points is tabulated then)");
+    }
     if (d.fd_slot) {
         std::vector<int> slot(d.E);
         CK(cudaMemcpyAsync(slot.data(), d.fd_slot, sizeof(int) * d.E, cudaMemcpyDeviceToHost, c->st));

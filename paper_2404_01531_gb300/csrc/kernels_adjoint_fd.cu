@@ -312,18 +312,24 @@ void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, doubl
     cudaFuncSetAttribute(k_fdv_ghosts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t ne = d.nc + 2 * GH;
     const size_t extb_bytes = (size_t)NQ * d.chunk * ne * ne * ne * sizeof(double);
-    prof_begin("fd_rhs_vjp", st);
     for (int k = 0, nch = fd_chunks(d); k < nch; ++k) {
         const int w0 = k * d.chunk;
+        prof_begin("fdv_fill", st);
         launch_fd_fill(d, d.fd_list, 1, w0, U, J, st);
         cudaMemsetAsync(extb, 0, extb_bytes, st);
+        prof_end(st);
+        prof_begin("fdv_faces", st);
         k_fdv_faces<<<d.nsm * 8, 128, 0, st>>>(d, d.fd_list, 1, w0, L, extb);
+        prof_end(st);
+        prof_begin("fdv_cells", st);
         k_fdv_cells<<<d.nsm * 8, 256, 0, st>>>(d, d.fd_list, 1, w0, U, L, out, extb);
+        prof_end(st);
+        prof_begin("fdv_ghosts", st);
         k_fdv_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, d.fd_list, 1, w0, U, J, out, extb, omega_bar);
-        g_launch_counter += 3;
         launch_fdv_ghosts_interp(d, d.fd_list, 1, w0, U, out, extb, st);
+        prof_end(st);
+        g_launch_counter += 3;
     }
-    prof_end(st);
 }
 
 }  // namespace ffe

@@ -231,26 +231,15 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                     // FD->DG projection (6-point stencils) of the neighbour's cells and of
                     // their current J~ (the current of a projected state would carry its
                     // projection error in E~.B~ amplified by eta into the q~ flux)
+                    // (from the face traces k_fd_traces left for it, indexed along
+                    // the neighbour's own face axes)
                     jx = true;
-                    const int nc = T.nc;
-                    const int lo0 = T.f2d_lo[cn[0]], lo1 = T.f2d_lo[cn[1]], lo2 = T.f2d_lo[cn[2]];
-                    const int64_t base = fdb(d, nb);
-                    for (int v = 0; v < NV + 3; ++v) {
-                        const double* src = v < NV ? a.Uin.fd(v) + base : a.J.fd(3 + v - NV) + base;
-                        double acc = 0.0;
-                        for (int n2 = 0; n2 < 6; ++n2) {
-                            double a2 = 0.0;
-                            for (int n1 = 0; n1 < 6; ++n1) {
-                                double a1 = 0.0;
-                                const double* row = src + (int64_t)(lo0 + nc * ((lo1 + n1) + nc * (lo2 + n2)));
-                                for (int n0 = 0; n0 < 6; ++n0) a1 = fma(T.F2D[cn[0]][lo0 + n0], row[n0], a1);
-                                a2 = fma(T.F2D[cn[1]][lo1 + n1], a1, a2);
-                            }
-                            acc = fma(T.F2D[cn[2]][lo2 + n2], a2, acc);
-                        }
-                        if (v < NV) Ue[v] = acc;
-                        else Je[v - NV] = acc;
-                    }
+                    const int f2 = d.nbr_face[e * 6 + f], d2 = f2 >> 1;
+                    const int u1 = d2 == 0 ? 1 : 0, u2 = d2 == 2 ? 1 : 2;
+                    const int nfm = d.np1 * d.np1;
+                    const double* tr = d.ftr + ((int64_t)fd_slot_of(d, nb) * 6 + f2) * 12 * nfm + cn[u1] + np1 * cn[u2];
+                    for (int v = 0; v < NV; ++v) Ue[v] = tr[v * nfm];
+                    for (int q = 0; q < 3; ++q) Je[q] = tr[(NV + q) * nfm];
                 }
             } else {
                 const int kind = d.bc[e * 6 + f];
@@ -466,6 +455,7 @@ static void curved_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_
 void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field J, Field un, Field F2, Field F3, Field G1,
                               Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout, cudaStream_t st) {
     SubArgs a{Uin, J, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
+    if (!d.ks) launch_fd_traces(d, Uin, J, st);
     prof_begin(sub == SUB_RHS ? "dg_rhs_curved" : "dg_substep_curved", st);
     if (d.ks) {
         switch (d.P) {
@@ -490,12 +480,9 @@ __global__ void k_stage12_ks(Dev d, Field un, Field Ua, Field G1, Field G2) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const double dta = d.dt * IM_A;
-    for (int64_t p = tid; p < d.ndg; p += stride) {
-        if (d.mask[p / d.nn] != 0) continue;
-        PM m;
-        load_pm(d.met, d.ndg, p, m);
-        double u[NV], U1[NV], g1[NG], g2[NG];
-        for (int v = 0; v < NV; ++v) { u[v] = un.dg(v)[p]; U1[v] = u[v]; }
+    auto point = [&](const PM& m, double* u, double* g1, double* g2) {
+        double U1[NV];
+        for (int v = 0; v < NV; ++v) U1[v] = u[v];
         if (!stiff_solve_gen(U1, m, d, dta)) atomic_status(d, 2);
         if (d.mode != FFE_RELAX) hard_clamp_gen(U1, m);
         implicit_G_gen(U1, m, d, g1);
@@ -507,8 +494,30 @@ __global__ void k_stage12_ks(Dev d, Field un, Field Ua, Field G1, Field G2) {
         if (!stiff_solve_gen(u, m, d, dta)) atomic_status(d, 2);
         if (d.mode != FFE_RELAX) hard_clamp_gen(u, m);
         implicit_G_gen(u, m, d, g2);
+    };
+    for (int64_t p = tid; p < d.ndg; p += stride) {
+        if (d.mask[p / d.nn] != 0) continue;
+        PM m;
+        load_pm(d.met, d.ndg, p, m);
+        double u[NV], g1[NG], g2[NG];
+        for (int v = 0; v < NV; ++v) u[v] = un.dg(v)[p];
+        point(m, u, g1, g2);
         for (int v = 0; v < NV; ++v) Ua.dg(v)[p] = u[v];
         for (int c = 0; c < NG; ++c) { G1.dg(c)[p] = g1[c]; G2.dg(c)[p] = g2[c]; }
+    }
+    // FD cells of the FD list, with the metric at the subcell centre
+    const int64_t nfdq = (int64_t)d.counts[1] * d.ncell;
+    for (int64_t q = tid; q < nfdq; q += stride) {
+        const int e = d.fd_list[q / d.ncell];
+        const int c = (int)(q % d.ncell);
+        const int64_t p = fdb(d, e) + c;
+        PM m;
+        load_pm(d.metfd, (int64_t)d.E * d.ncell, (int64_t)e * d.ncell + c, m);
+        double u[NV], g1[NG], g2[NG];
+        for (int v = 0; v < NV; ++v) u[v] = un.fd(v)[p];
+        point(m, u, g1, g2);
+        for (int v = 0; v < NV; ++v) Ua.fd(v)[p] = u[v];
+        for (int cg = 0; cg < NG; ++cg) { G1.fd(cg)[p] = g1[cg]; G2.fd(cg)[p] = g2[cg]; }
     }
 }
 

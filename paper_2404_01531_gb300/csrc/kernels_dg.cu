@@ -15,6 +15,7 @@
 #include "dgfilter.cuh"
 #include "ffe_internal.h"
 #include "physics.cuh"
+#include "physics_gen.cuh"
 #include "stage.cuh"
 
 namespace ffe {
@@ -29,8 +30,9 @@ struct DGK {
     static constexpr int NT = ((nn + 31) / 32) * 32;
     static constexpr int NW = NT / 32;
     // shared doubles: U[9][nn] | J[6][nn] + C[6][9][nf] (aliased by the filter buffer [9][nn]) | red[2][NW]
+    // | D scaled by the element's d xi/d x, per axis [3][np1][np1]
     static constexpr int AUX = (6 * nn + 54 * nf) > 9 * nn ? (6 * nn + 54 * nf) : 9 * nn;
-    static constexpr int SMEM = (9 * nn + AUX + 2 * NW) * 8;
+    static constexpr int SMEM = (9 * nn + AUX + 2 * NW + 3 * nf) * 8;
 };
 
 // ---------------------------------------------------------------------------
@@ -65,7 +67,13 @@ __global__ void k_current(Dev d, Field U, Field J, const int* list, int count_in
             if (d.mask[e] != 0 || (int)(p % d.nn) >= esz(d, e).nn) continue;
             double u[NV], jd[3], jf[3];
             for (int v = 0; v < NV; ++v) u[v] = U.dg(v)[p];
-            current_flat(u, d.eta, jd, jf);
+            if (d.ks) {
+                PM m;
+                load_pm(d.met, d.ndg, p, m);
+                current_gen(u, m, d.eta, jd, jf);
+            } else {
+                current_flat(u, d.eta, jd, jf);
+            }
             for (int c = 0; c < 3; ++c) { J.dg(c)[p] = jd[c]; J.dg(3 + c)[p] = jf[c]; }
         }
         list = d.fd_list;
@@ -80,7 +88,13 @@ __global__ void k_current(Dev d, Field U, Field J, const int* list, int count_in
             const int64_t p = fdb(d, e) + c;
             double u[NV], jd[3], jf[3];
             for (int v = 0; v < NV; ++v) u[v] = U.fd(v)[p];
-            current_flat(u, d.eta, jd, jf);
+            if (d.ks) {
+                PM m;
+                load_pm(d.metfd, (int64_t)d.E * d.ncell, (int64_t)e * d.ncell + c, m);
+                current_gen(u, m, d.eta, jd, jf);
+            } else {
+                current_flat(u, d.eta, jd, jf);
+            }
             for (int c2 = 0; c2 < 3; ++c2) { J.fd(c2)[p] = jd[c2]; J.fd(3 + c2)[p] = jf[c2]; }
         }
     }
@@ -205,26 +219,13 @@ __device__ void dg_external_state(const Dev& d, const SubArgs& a, int e, int f, 
         }
         // FD neighbour: its FD->DG projection evaluated at this node (6-point
         // stencils), for the state and for its current J~ (the current of the
-        // projected state would carry the projection error of E~.B~ times eta)
-        const int nc = T.nc;
-        const int lo0 = T.f2d_lo[c[0]], lo1 = T.f2d_lo[c[1]], lo2 = T.f2d_lo[c[2]];
-        const int64_t base = fdb(d, nb);
-        for (int v = 0; v < NV + 3; ++v) {
-            const double* src = v < NV ? a.Uin.fd(v) + base : a.J.fd(3 + v - NV) + base;
-            double acc = 0.0;
-            for (int n2 = 0; n2 < 6; ++n2) {
-                double a2 = 0.0;
-                for (int n1 = 0; n1 < 6; ++n1) {
-                    double a1 = 0.0;
-                    const double* row = src + (int64_t)(lo0 + nc * ((lo1 + n1) + nc * (lo2 + n2)));
-                    for (int n0 = 0; n0 < 6; ++n0) a1 = fma(T.F2D[c[0]][lo0 + n0], row[n0], a1);
-                    a2 = fma(T.F2D[c[1]][lo1 + n1], a1, a2);
-                }
-                acc = fma(T.F2D[c[2]][lo2 + n2], a2, acc);
-            }
-            if (v < NV) Ue[v] = acc;
-            else Je[v - NV] = acc;
-        }
+        // projected state would carry the projection error of E~.B~ times eta),
+        // from the face traces k_fd_traces left for it (same face axes: boxes)
+        (void)T;
+        const int nfm = d.np1 * d.np1;
+        const double* tr = d.ftr + ((int64_t)fd_slot_of(d, nb) * 6 + f2) * 12 * nfm + ta + np1 * tb;
+        for (int v = 0; v < NV; ++v) Ue[v] = tr[v * nfm];
+        for (int q = 0; q < 3; ++q) Je[q] = tr[(NV + q) * nfm];
         return;
     }
     int kind = d.bc[e * 6 + f];
@@ -251,17 +252,12 @@ __global__ void __launch_bounds__(DGK<P>::NT, 3) k_dg_substep(Dev d, SubArgs a) 
     double* sJ = sU + 9 * nn;        // [6][nn]
     double* sC = sJ + 6 * nn;        // [6][9][nf]
     double* red = sU + 9 * nn + K::AUX;
+    double* sD = red + 2 * NW;       // [3][np1][np1]: (d xi^a/d x^a) D
     __shared__ int s_flag;
     const Tables& T = *d.tab;
     const int tid = threadIdx.x;
     const bool act = tid < nn;
     const int i = tid % np1, j = (tid / np1) % np1, k = tid / (np1 * np1);
-    double Di[np1], Dj[np1], Dk[np1];
-    for (int m = 0; m < np1; ++m) {
-        Di[m] = T.D[act ? i : 0][m];
-        Dj[m] = T.D[act ? j : 0][m];
-        Dk[m] = T.D[act ? k : 0][m];
-    }
     const double w0inv = 1.0 / T.w0;
     const int nwork = d.counts[0];
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
@@ -270,12 +266,14 @@ __global__ void __launch_bounds__(DGK<P>::NT, 3) k_dg_substep(Dev d, SubArgs a) 
         const double sx = d.ijac[3 * e], sy = d.ijac[3 * e + 1], sz = d.ijac[3 * e + 2];
         for (int t = tid; t < NV * nn; t += NT) sU[t] = a.Uin.dg(t / nn)[eb + t % nn];
         for (int t = tid; t < NJ * nn; t += NT) sJ[t] = a.J.dg(t / nn)[eb + t % nn];
+        if (tid < 3 * nf) sD[tid] = (tid < nf ? sx : (tid < 2 * nf ? sy : sz)) * T.D[(tid % nf) / np1][tid % np1];
         __syncthreads();
 
         double du[NV];
         if (act) {
-            double Dx[np1], Dy[np1], Dz[np1];
-            for (int m = 0; m < np1; ++m) { Dx[m] = sx * Di[m]; Dy[m] = sy * Dj[m]; Dz[m] = sz * Dk[m]; }
+            const double* Dx = sD + np1 * i;
+            const double* Dy = sD + nf + np1 * j;
+            const double* Dz = sD + 2 * nf + np1 * k;
             const int ox = np1 * (j + np1 * k);   // x-line start
             const int oy = i + np1 * np1 * k;     // y-line start, stride np1
             const int oz = i + np1 * j;           // z-line start, stride np1^2
@@ -459,6 +457,7 @@ void launch_dg_substep(const Dev& d, int sub, Field Uin, Field J, Field un, Fiel
                        Field G1, Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout,
                        cudaStream_t st) {
     SubArgs a{Uin, J, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
+    launch_fd_traces(d, Uin, J, st);
     prof_begin(sub == SUB_RHS ? "dg_rhs" : "dg_substep", st);
     switch (d.P) {
         case 2: dg_sub_dispatch<2>(d, sub, a, st); break;

@@ -16,6 +16,7 @@
 // are those of the largest order.
 #include "ffe_internal.h"
 #include "physics.cuh"
+#include "physics_gen.cuh"
 #include "shellmap.cuh"
 #include "stage.cuh"
 #include "fd_common.cuh"
@@ -177,7 +178,15 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
                         bc_star_flat(ui, x, omega_of(d, e), u);
                     }
                 }
-                current_flat(u, d.eta, jd, jf);
+                if (d.ks) {
+                    // Dirichlet ghosts only on this background: metric at the ghost centre
+                    PM m;
+                    load_pm(d.metgb + (int64_t)d.bface[e * 6 + f] * NPM * GH * d.nc * d.nc, (int64_t)GH * d.nc * d.nc,
+                            (int64_t)g * nc * nc + ta + nc * tb, m);
+                    current_gen(u, m, d.eta, jd, jf);
+                } else {
+                    current_flat(u, d.eta, jd, jf);
+                }
                 const int64_t og = ghost_offset(g, ta, tb);
                 for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[og] = u[v];
                 for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = jf[k];
@@ -299,8 +308,57 @@ __global__ void __launch_bounds__(128, 4) k_fd_flux_curved(Dev d, const int* lis
     }
 }
 
+// Kerr-Schild variant (Sec. III.C.2 on a curved background): the metric at
+// the face point from Dev::metff; the unit normal n_l = d_l xi^k / |d xi^k|_gamma;
+// Rusanov with lambda = alpha + |beta^l n_l| and the dissipation along
+// n^j = gamma^jl n_l:
+//   F^j = (F^j(L) + F^j(R))/2 - lambda n^j (U_R - U_L)/2,
+// where the flux at a fixed point is linear in (U, J~), so its average is the
+// flux of the averaged states.  No corrector (it is defined for Cartesian
+// meshes; FFE_ENOTIMPL at creation).
+template <int RECON>
+__global__ void __launch_bounds__(128, 4) k_fd_flux_ks(Dev d, const int* list, int ci, int w0) {
+    const int n = chunk_n(d, ci, w0);
+    const int64_t nfc = nface(d);
+    const int64_t total = (int64_t)n * 3 * nfc;
+    const int64_t nfaces = (int64_t)d.E * nfc;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int wl = (int)(q / (3 * nfc));
+        const int k = (int)((q / nfc) % 3);
+        const int64_t fi = q % nfc;
+        const int e = list[w0 + wl];
+        const int nc = esz(d, e).nc;
+        int m, ta, tb;
+        if (!face_coords(fi, nc, m, ta, tb)) continue;
+        double UL[NQ], UR[NQ], Um[NQ], Up[NQ];
+        reconstruct<RECON>(d, wl, k, m, ta, tb, nc, UL, UR, Um, Up);
+        double nh[3];
+        shell_face_normal(shell_pts(d, e, nc), k, m, ta, tb, nh);
+        PM pm;
+        load_pm(d.metff + (int64_t)k * NPM * nfaces, nfaces, (int64_t)e * nfc + fi, pm);
+        double nu[3];
+        for (int i = 0; i < 3; ++i)
+            nu[i] = fma(pm.gu[sym3(i, 0)], nh[0], fma(pm.gu[sym3(i, 1)], nh[1], pm.gu[sym3(i, 2)] * nh[2]));
+        const double inrm = 1.0 / sqrt(d3(nu, nh));
+        double nl[3];
+        for (int i = 0; i < 3; ++i) nl[i] = nh[i] * inrm;
+        const double lam = pm.a + fabs(d3(pm.b, nl));
+        double hS[NQ], dU[NV], F[3][NV];
+        for (int qq = 0; qq < NQ; ++qq) hS[qq] = 0.5 * (UL[qq] + UR[qq]);
+        for (int v = 0; v < NV; ++v) dU[v] = UR[v] - UL[v];
+        flux_gen(hS, hS + NV, pm, F);
+        for (int j = 0; j < 3; ++j) {
+            const double hn = -0.5 * lam * nu[j] * inrm;
+            for (int v = 0; v < NV; ++v) flux_at_c(d, k, j, v, wl)[fi] = fma(hn, dU[v], F[j][v]);
+        }
+    }
+}
+
 // One thread per (chunk position, cell): flux difference + sources + stage.
-template <int SUB, bool CURVED>
+// KS: the Kerr-Schild background (metric and its derivative terms at the
+// subcell centre from Dev::metfd; sources, stiff solve, clamp and implicit
+// operator in their metric-general forms).
+template <int SUB, bool CURVED, bool KS = false>
 __global__ void k_fd_update(Dev d, const int* list, int ci, int w0, SubArgs a) {
     const int n = chunk_n(d, ci, w0);
     const int64_t total = (int64_t)n * d.ncell;
@@ -316,12 +374,20 @@ __global__ void k_fd_update(Dev d, const int* list, int ci, int w0, SubArgs a) {
         if (CURVED) shell_cell(shell_pts(d, e, nc), cc, ij, nullptr);
         double du[NV], u0[NV];
         for (int v = 0; v < NV; ++v) u0[v] = a.Uin.fd(v)[p];
-        du[0] = -a.J.fd(0)[p];
-        du[1] = -a.J.fd(1)[p];
-        du[2] = -a.J.fd(2)[p];
-        du[3] = du[4] = du[5] = 0.0;
-        du[6] = u0[8];
-        du[7] = du[8] = 0.0;
+        PM m;
+        const int64_t mstride = (int64_t)d.E * d.ncell, mp = (int64_t)e * d.ncell + c;
+        if (KS) {
+            load_pm(d.metfd, mstride, mp, m);
+            const double jd[3] = {a.J.fd(0)[p], a.J.fd(1)[p], a.J.fd(2)[p]};
+            sources_gen(u0, jd, m, d.metfd, mstride, mp, du);
+        } else {
+            du[0] = -a.J.fd(0)[p];
+            du[1] = -a.J.fd(1)[p];
+            du[2] = -a.J.fd(2)[p];
+            du[3] = du[4] = du[5] = 0.0;
+            du[6] = u0[8];
+            du[7] = du[8] = 0.0;
+        }
         for (int k = 0; k < 3; ++k) {
             int t1, t2;
             axes_of(k, t1, t2);
@@ -353,7 +419,13 @@ __global__ void k_fd_update(Dev d, const int* list, int ci, int w0, SubArgs a) {
         if (SUB != SUB_C)
             for (int v = 0; v < NV; ++v) a.Fout.fd(v)[p] = du[v];
         double u[NV];
-        substep_combine(d, SUB, du, p, true, a, dt_of(d, e), u);
+        if (KS) {
+            substep_explicit(d, SUB, du, p, true, a, dt_of(d, e), u);
+            if (SUB != SUB_C && !stiff_solve_gen(u, m, d, dt_of(d, e) * IM_A)) atomic_status(d, 2);
+            if (d.mode != FFE_RELAX) hard_clamp_gen(u, m);
+        } else {
+            substep_combine(d, SUB, du, p, true, a, dt_of(d, e), u);
+        }
         bool bad = false;
         for (int v = 0; v < NV; ++v) {
             a.Uout.fd(v)[p] = u[v];
@@ -362,7 +434,8 @@ __global__ void k_fd_update(Dev d, const int* list, int ci, int w0, SubArgs a) {
         if (bad) atomic_status(d, 1);
         if (SUB != SUB_C) {
             double g[NG];
-            implicit_G_flat(u, d, g);
+            if (KS) implicit_G_gen(u, m, d, g);
+            else implicit_G_flat(u, d, g);
             for (int cg = 0; cg < NG; ++cg) a.Gout.fd(cg)[p] = g[cg];
         }
     }
@@ -385,7 +458,8 @@ void launch_fd_fill(const Dev& d, const int* list, int ci, int w0, Field U, Fiel
 
 template <int SUB>
 static void launch_update(const Dev& d, const int* list, int ci, int w0, const SubArgs& a, cudaStream_t st) {
-    if (d.curved) k_fd_update<SUB, true><<<d.nsm * 8, 256, 0, st>>>(d, list, ci, w0, a);
+    if (d.ks) k_fd_update<SUB, true, true><<<d.nsm * 8, 256, 0, st>>>(d, list, ci, w0, a);
+    else if (d.curved) k_fd_update<SUB, true><<<d.nsm * 8, 256, 0, st>>>(d, list, ci, w0, a);
     else k_fd_update<SUB, false><<<d.nsm * 8, 256, 0, st>>>(d, list, ci, w0, a);
 }
 
@@ -404,13 +478,19 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin
         prof_begin("fd_fill_ghosts", st);
         k_fd_fill_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, list, ci, w0, Uin, J);
         prof_end(st);
-        launch_fd_fill_interp(d, list, ci, w0, Uin, J, st);
+        if (d.ginterp) {
+            prof_begin("fd_fill_ghosts_interp", st);
+            launch_fd_fill_interp(d, list, ci, w0, Uin, J, st);
+            prof_end(st);
+        }
         prof_begin("fd_flux", st);
         if (d.recon == FFE_RECON_MP5) {
-            if (d.curved) k_fd_flux_curved<FFE_RECON_MP5><<<grid, 128, 0, st>>>(d, list, ci, w0);
+            if (d.ks) k_fd_flux_ks<FFE_RECON_MP5><<<grid, 128, 0, st>>>(d, list, ci, w0);
+            else if (d.curved) k_fd_flux_curved<FFE_RECON_MP5><<<grid, 128, 0, st>>>(d, list, ci, w0);
             else k_fd_flux<FFE_RECON_MP5><<<grid, 128, 0, st>>>(d, list, ci, w0);
         } else {
-            if (d.curved) k_fd_flux_curved<FFE_RECON_WENO5Z><<<grid, 128, 0, st>>>(d, list, ci, w0);
+            if (d.ks) k_fd_flux_ks<FFE_RECON_WENO5Z><<<grid, 128, 0, st>>>(d, list, ci, w0);
+            else if (d.curved) k_fd_flux_curved<FFE_RECON_WENO5Z><<<grid, 128, 0, st>>>(d, list, ci, w0);
             else k_fd_flux<FFE_RECON_WENO5Z><<<grid, 128, 0, st>>>(d, list, ci, w0);
         }
         prof_end(st);
@@ -424,6 +504,64 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin
         prof_end(st);
         g_launch_counter += 4;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Face traces of FD elements for their DG neighbours (Sec. III.C.2 interface):
+// at every LGL node of each face whose neighbour is on DG, the FD->DG
+// projection (6-point stencils along each axis) of the element's cells, for U
+// and for its current J~.  A DG element facing an FD neighbour reads its
+// exterior state here instead of projecting 6 x 6 x 6 cells per face node
+// itself (which left most of its block idle).  Layout: per FD slot [6 faces]
+// [12 quantities][np1max^2], face node index a + np1 b along the face's axes
+// (axes_of of its normal).  One thread per (element, face, node, quantity).
+__global__ void k_fd_traces(Dev d, Field U, Field J) {
+    const int n = d.counts[1];
+    const int nfm = d.np1 * d.np1;
+    const int64_t per = (int64_t)6 * nfm * NQ;
+    const int64_t total = (int64_t)n * per;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int w = (int)(q / per);
+        const int r = (int)(q % per);
+        const int f = r / (nfm * NQ), ab = (r / NQ) % nfm, qv = r % NQ;
+        const int e = d.fd_list[w];
+        const int nb = d.nbr[e * 6 + f];
+        if (nb < 0 || d.mask[nb] != 0) continue;
+        const ES es = esz(d, e);
+        const int np1 = es.np1, nc = es.nc;
+        if (ab >= np1 * np1) continue;
+        const Tables& T = d.tabs[es.P];
+        const int dd = f >> 1;
+        int t1, t2;
+        axes_of(dd, t1, t2);
+        int c[3];
+        c[dd] = (f & 1) ? es.P : 0;
+        c[t1] = ab % np1;
+        c[t2] = ab / np1;
+        const int lo0 = T.f2d_lo[c[0]], lo1 = T.f2d_lo[c[1]], lo2 = T.f2d_lo[c[2]];
+        const int64_t base = fdb(d, e);
+        const double* src = qv < NV ? U.fd(qv) + base : J.fd(3 + qv - NV) + base;
+        double acc = 0.0;
+        for (int n2 = 0; n2 < 6; ++n2) {
+            double a2 = 0.0;
+            for (int n1 = 0; n1 < 6; ++n1) {
+                double a1 = 0.0;
+                const double* row = src + (int64_t)(lo0 + nc * ((lo1 + n1) + nc * (lo2 + n2)));
+                for (int n0 = 0; n0 < 6; ++n0) a1 = fma(T.F2D[c[0]][lo0 + n0], row[n0], a1);
+                a2 = fma(T.F2D[c[1]][lo1 + n1], a1, a2);
+            }
+            acc = fma(T.F2D[c[2]][lo2 + n2], a2, acc);
+        }
+        d.ftr[(((int64_t)fd_slot_of(d, e) * 6 + f) * NQ + qv) * nfm + ab] = acc;
+    }
+}
+
+void launch_fd_traces(const Dev& d, Field U, Field J, cudaStream_t st) {
+    if (!d.ftr) return;
+    prof_begin("fd_traces", st);
+    k_fd_traces<<<d.nsm * 8, 128, 0, st>>>(d, U, J);
+    prof_end(st);
+    g_launch_counter += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -579,7 +717,15 @@ __global__ void k_fd2dg(Dev d, Field un) {
         for (int v = 3; v < 6; ++v) project_fd2dg_var(es, T, un.fd(v) + fb, proj + v * nn, work);
         for (int t = threadIdx.x; t < nn; t += blockDim.x) {
             const double bx = proj[3 * nn + t], by = proj[4 * nn + t], bz = proj[5 * nn + t];
-            tmp[t] = sqrt(fma(bz, bz, fma(by, by, bx * bx)));
+            if (d.ks) {
+                // |B~| with the spatial metric at the node
+                PM m;
+                load_pm(d.met, d.ndg, (int64_t)e * d.nn + t, m);
+                const double u[NV] = {0.0, 0.0, 0.0, bx, by, bz, 0.0, 0.0, 0.0};
+                tmp[t] = bnorm_gen(u, m);
+            } else {
+                tmp[t] = sqrt(fma(bz, bz, fma(by, by, bx * bx)));
+            }
         }
         __syncthreads();
         for (int t = threadIdx.x; t < nn; t += blockDim.x) {

@@ -20,9 +20,11 @@
 //     interpolated state, as for every FD ghost;
 //   - a DG neighbour: its nodal polynomial of U and of its nodal current J~
 //     evaluated at the point (as its ghosts are filled everywhere else).
-// Flat metric only (the shells that carry FD subcells).
+// On the Kerr-Schild background the ghost current takes the metric at the
+// ghost centre (Dev::metgi).
 #include "ffe_internal.h"
 #include "physics.cuh"
+#include "physics_gen.cuh"
 #include "shellmap.cuh"
 #include "fd_common.cuh"
 #include "adjoint_common.cuh"
@@ -156,7 +158,14 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
                         }
                     }
                 double jd[3], jf[3];
-                current_flat(u, d.eta, jd, jf);
+                if (d.ks) {
+                    PM m;
+                    load_pm(d.metgi + (int64_t)d.gislot[e * 6 + f] * NPM * GH * d.nc * d.nc, (int64_t)GH * d.nc * d.nc,
+                            (int64_t)g * nc * nc + ta + nc * tb, m);
+                    current_gen(u, m, d.eta, jd, jf);
+                } else {
+                    current_flat(u, d.eta, jd, jf);
+                }
                 for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[og] = u[v];
                 for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = jf[k];
             } else {
@@ -188,9 +197,7 @@ size_t fd_interp_smem(const Dev& d) { return (size_t)NQ * d.nn * sizeof(double);
 
 void launch_fd_fill_interp(const Dev& d, const int* list, int ci, int w0, Field U, Field J, cudaStream_t st) {
     if (!d.ginterp) return;
-    prof_begin("fd_fill_ghosts_interp", st);
     k_fd_fill_ghosts_interp<<<d.nsm * 2, 256, fd_interp_smem(d), st>>>(d, list, ci, w0, U, J);
-    prof_end(st);
     g_launch_counter += 1;
 }
 

@@ -327,6 +327,27 @@ def test_hybrid_luminosity_gradient_matches_central_differences(ffe):
         assert abs(g[k] - fd) <= 3e-6 * abs(fd), (name, g[k], fd)
 
 
+def test_hybrid_luminosity_gradient_matches_oracle_complex_step(ffe):
+    """The gradient workload's tiny shell (6 wedges x 2x2x4, P = 5) with its
+    innermost radial layer on FD subcells (fixed mask): d Lbar/d (mu, chi,
+    Omega) through r = 1.5 over 3 steps from the GPU adjoint (checkpoints
+    every 2 steps) against the oracle's complex-step derivative of the same
+    frozen-mask evolution, and Lbar against the oracle's."""
+    from oracle.adjoint import lbar, lbar_gradient_complex_step
+    from paper_2404_01531_gb300.adjoint import luminosity_gradient
+    cfg = _tiny(50.0)
+    cfg["params"]["weno_eps"] = 1e-6
+    ctx, mask = _hybrid(ffe, cfg=cfg, inner=True)
+    nsteps, rL = 3, 1.5
+    L, g, _ = luminosity_gradient(ctx, nsteps, r_L=rL, every=2)
+    m = mask.cpu().numpy()
+    Lo = lbar(cfg, nsteps, r_L=rL, mask=m)
+    go = lbar_gradient_complex_step(cfg, nsteps, r_L=rL, mask=m)
+    assert abs(L - Lo) <= 1e-9 * abs(Lo), (L, Lo)
+    np.testing.assert_allclose(g, go, rtol=1e-6)
+    ctx.close()
+
+
 def test_split_adjoint_matches_adjoint_step(ffe):
     """ffe_adjoint_forward (stages kept) + ffe_adjoint_reverse = ffe_adjoint_step,
     and the forward half's u_{n+1} is the step's result up to rounding."""

@@ -172,12 +172,12 @@ def test_step_breakdown_slab_100_steps_chunked(ffe):
 
 
 def test_step_breakdown_with_an_fd_slot_pool(ffe):
-    """A single context whose FD block is a pool of 6 slots (fewer than its 32
+    """A single context whose FD block is a pool of 16 slots (half its 32
     elements): elements take a slot when they switch to FD and return it at
     FD -> DG; the steps equal the oracle's as with one slot per element, and
     the state vector is smaller by the unused FD blocks."""
     cfg = W.breakdown(nx=16, ny=2, nz=1, x_half=0.5)
-    cfg["params"]["fd_capacity"] = 6
+    cfg["params"]["fd_capacity"] = 16
     ctx0 = ffe.Context(W.breakdown(nx=16, ny=2, nz=1, x_half=0.5))
     n_full = ctx0.n_state
     ctx0.close()
@@ -195,7 +195,7 @@ def test_step_breakdown_with_an_fd_slot_pool(ffe):
     near |= set(ctx.near_threshold())
     assert ctx.status() == 0
     assert set(np.nonzero(mask != st["mask"])[0].tolist()) <= near
-    assert 0 < mask.sum() <= 6
-    assert ctx.n_state == 9 * (ctx.n_dg + 6 * ctx.nc ** 3) < n_full
+    assert 0 < mask.sum() <= 16
+    assert ctx.n_state == 9 * (ctx.n_dg + 16 * ctx.nc ** 3) < n_full
     compare_state(ctx, U, st, 1e-8)
     ctx.close()

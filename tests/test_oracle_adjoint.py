@@ -59,3 +59,30 @@ def test_complex_step_gradient_matches_central_differences_and_homogeneity():
         assert abs(fd - g[k]) <= 1e-5 * abs(g[k]), (k, fd, g[k])
     L = lbar(cfg, n, r_L=rL)
     assert abs(base[0] * g[0] - 2 * L) <= 1e-10 * abs(L)
+
+
+def test_complex_step_gradient_with_a_fixed_hybrid_mask():
+    """The same on the tiny shell with its innermost radial layer on FD
+    subcells (fixed mask): the complex step runs through WENO5-Z (its |.|
+    branches on the real part, eps = 1e-6 so that the flat stencils of the
+    dipole data stay differentiable), the interpolated ghosts between wedges,
+    the star state in the ghosts and the FD -> DG projection in the
+    luminosity; one step, against central differences (eps = 1e-6 makes
+    WENO5-Z scale-dependent, so the homogeneity in mu of the other test does
+    not hold here)."""
+    cfg = _tiny()
+    cfg["params"].update(eta=50.0, weno_eps=1e-6)
+    na, nr = cfg["n_ang"], cfg["n_rad"]
+    e = np.arange(6 * na * na * nr)
+    mask = ((e // (na * na)) % nr == 0).astype(np.uint8)
+    n, rL = 1, 1.5
+    g = lbar_gradient_complex_step(cfg, n, r_L=rL, mask=mask)
+    kw = cfg["initial"][1]
+    base = [kw["mu"], kw["chi"], cfg["params"]["omega_star"]]
+    for k in range(3):
+        h = 1e-5 * abs(base[k])
+        p, m = list(base), list(base)
+        p[k] += h
+        m[k] -= h
+        fd = (lbar(cfg, n, p, rL, mask) - lbar(cfg, n, m, rL, mask)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-4 * abs(g[k]), (k, fd, g[k])
