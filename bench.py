@@ -533,6 +533,52 @@ def run_pulsars(args):
         dist.destroy_process_group()
 
 
+def batch_measure(n_inst=32, steps=3, warmup=2, fd_capacity=0.5):
+    """The batched workload (n_inst rotating-dipole shells, seed 1531) for a
+    few steps: one batched context (one launch per kernel and substep for every
+    instance) against one context per instance advanced one after the other;
+    node updates per second of each and their ratio."""
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    cfgs = W.pulsars(n_inst=n_inst)
+    E = sum(6 * c["n_ang"] ** 2 * c["n_rad"] for c in cfgs)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b = ffe.BatchContext(cfgs, fd_capacity=int(fd_capacity * E))
+    b.set_initial()
+    b.step(warmup)
+    torch.cuda.synchronize()
+    u0 = b.info().node_updates
+    e0.record(st)
+    b.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    units_b = b.info().node_updates - u0
+    tuned = list(b.info().dg_ctas_per_sm)
+    status = b.status()
+    b.close()
+    ms_s, units_s = 0.0, 0
+    for c in cfgs:
+        s1 = ffe.Context(c)
+        s1.set_initial()
+        s1.step(warmup)
+        torch.cuda.synchronize()
+        u0 = s1.info().node_updates
+        e0.record(st)
+        s1.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_s += e0.elapsed_time(e1)
+        units_s += s1.info().node_updates - u0
+        s1.close()
+    vb, vs = units_b / (ms_b / 1e3), units_s / (ms_s / 1e3)
+    return {"workload": f"{n_inst} rotating-dipole shells (seed 1531), {E} elements, P in {{4,5}}, {steps} steps",
+            "batched_value": vb, "batched_ms_per_step": ms_b / steps, "single_value": vs,
+            "single_ms_per_step": ms_s / steps, "batched_over_single": vb / vs,
+            "dg_ctas_per_sm_by_order": dict(zip(("P5", "P4", "P3"), tuned)), "status_bits": status}
+
+
 def adjoint_measure(steps=500, every=25, r_L=20.0, fd_check=False):
     """Neutron-star shell 6 wedges x 6x6x12 at P=5: time of `steps` forward steps
     (graph replays) against the checkpointed gradient of the time-averaged
@@ -664,6 +710,8 @@ def main():
                          "dgphases: cost of the DG kernel's filter, indicator and stiff-current phases; "
                          "wald: the Kerr-Schild Wald shell, 1000 steps, indicator on")
     ap.add_argument("--no-adjoint", action="store_true", help="breakdown: skip the adjoint/forward timing")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="breakdown: skip the batched-against-single timing of the 32-shell batch")
     ap.add_argument("--recon", default="weno5z", choices=list(RECON),
                     help="breakdown and shell: FD reconstruction (the paper's WENO5-Z, or MP5)")
     ap.add_argument("--n-inst", type=int, default=32)
@@ -817,6 +865,12 @@ def main():
             adj = adjoint_measure()
         except Exception as ex:  # reported, not fatal
             adj = {"failed": str(ex)}
+    batched = None
+    if not args.no_batch and ws == 1:
+        try:
+            batched = batch_measure(args.n_inst, 3, 2, args.fd_capacity)
+        except Exception as ex:  # reported, not fatal
+            batched = {"failed": str(ex)}
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -839,7 +893,8 @@ def main():
                        "recon": args.recon, "fd_slots": fd_slots},
             "roofline": roof, "roofline_dg": roof_dg, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
-            "adjoint": adj, "status_bits": status}
+            "adjoint": adj, "batched_over_single": (batched or {}).get("batched_over_single"),
+            "batch": batched, "status_bits": status}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

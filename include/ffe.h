@@ -132,6 +132,9 @@ typedef struct {
     int64_t fd_elem_updates;      /* FD elements advanced through an RHS and stage update
                                      (rollback redos included), since ffe_set_initial      */
     int64_t dg_elem_updates;      /* DG elements advanced likewise                         */
+    int dg_ctas_per_sm[3];        /* persistent DG launch shapes the autotuner chose (CTAs per
+                                     SM) for the highest order and, in a batch, the next two
+                                     lower orders; 0 = not tuned (the first ffe_step tunes)   */
 } ffe_info;
 
 /* Create a context: builds the mesh, operator tables and geometry, allocates

@@ -108,6 +108,10 @@ __device__ __forceinline__ int chunk_n(const Dev& d, int ci, int w0) {
 // by b_0^2 b_1^2 b_2^2 so that the normalised combination needs one division:
 //   A_k = d_k (b_k^2 + tau^2) prod_{j != k} b_j^2,  value = sum A_k p_k / sum A_k.
 // With eps >= 1e-40 every A_k stays above 1e-240, inside the normal range.
+// At the other end the products of six indicators overflow once an indicator
+// exceeds about 1e51 (stencil differences of about 1e25): the weights then
+// become Inf/NaN and the status word reports it.  Field values that large are
+// far outside any state of this system (the fields are of order one).
 // weno5z_combine: the Z-weighted combination of three candidates from their
 // indicators b_k (eps included); the ideal weights are taken as (1, 10, 5)
 // (scale-free).

@@ -82,7 +82,8 @@ struct Dev {
     int* free_slots;
     int fd_cap;                     // FD slots
     int chunk;                      // FD elements per scratch chunk
-    int dg_grid;                    // CTAs of the curved DG kernel (chosen by the autotuner; 0 = default)
+    int dg_grid;                    // CTAs of the DG kernel of the highest order (autotuner; 0 = default)
+    int dg_grid_lo, dg_grid_lo2;    // batches: CTAs of the DG kernels of orders P-1, P-2 (autotuner; 0 = default)
     // physics and scheme parameters
     double eta, kpsi, kphi, dt, weno_eps, omega;
     int mode, filter_on, tci_on, fd_corr, recon;
@@ -103,7 +104,15 @@ struct Dev {
     const double* metff;
     const double* metgb;
     const double* metgi;
+    // faces between cubed-sphere wedges: ghost-table slot of each element face
+    // ([E][6], -1 elsewhere) and per ghost (slot, g, ta, tb) of the slot's face,
+    // [slot][GH nc^2]: the first neighbour cell of its 6-point stencil along each
+    // axis [3] with the stencil weights [3][6], and the Lagrange weights of the
+    // neighbour's LGL nodes along each axis [3][MAXNP]
     const int* gislot;
+    const int* gst;
+    const double* gwf;
+    const double* gwl;
     double shell_rin, shell_c;
     int shell_na, shell_nr;
     // flat shells, per instance at InstInfo::tab (single context: 0), on the
@@ -190,8 +199,11 @@ void launch_fdv_ghosts_interp(const Dev& d, const int* list, int ci, int w0, Fie
 void launch_constraints(const Dev& d, Field U, double* part, int blocks, cudaStream_t st);
 void launch_l2_err(const Dev& d, Field U, Field R, int v0, int nv, double* part, int blocks, cudaStream_t st);
 // out += (d RHS_FD/dU)^T L (kernels_adjoint_fd.cu); extb: scratch of the size of d.ext
-void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, double* extb, double* omega_bar,
-                       cudaStream_t st);
+// FD elements per chunk of the FD reverse mode (its per-face buffer gb holds
+// [3][12][FDV_CHUNK][(nc+1) nc^2][6] doubles)
+constexpr int FDV_CHUNK = 256;
+void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, double* extb, double* gb,
+                       double* omega_bar, cudaStream_t st);
 void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F2, Field F3,
                              Field G1, Field G2, Field G3, Field G4, cudaStream_t st);
 void launch_fd2dg(const Dev& d, Field un, cudaStream_t st);

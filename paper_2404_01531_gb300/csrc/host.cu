@@ -342,6 +342,7 @@ struct ffe_ctx {
     int nbf = 0;                     // boundary faces with Dirichlet data
     std::vector<int> h_bface;
     std::vector<unsigned char> h_ginterp;   // [E][6] faces between cubed-sphere wedges
+    std::vector<int> h_gislot;              // [E][6] their ghost-table slot (-1 elsewhere)
     ShellGeo shell{};
     double lam_max = 1.0;
     // batched contexts
@@ -361,6 +362,7 @@ struct ffe_ctx {
     AdjArgs adj{};
     bool adj_fd = false;             // the current mask has FD elements
     double* d_extb = nullptr;        // extended-block adjoint of one FD chunk
+    double* d_gbuf = nullptr;        // per-face contributions to it (FD reverse mode)
     double* d_omega_bar = nullptr;
     double* d_cons = nullptr;        // per-block partials of ffe_constraints
     double* d_ref = nullptr;         // analytic initial data (reference of the L2 error), state layout
@@ -594,10 +596,9 @@ ffe_status build_ks_fd_tables(ffe_ctx* c, const std::vector<double>& xfd) {
         CK(cudaMemcpy(d_mg, mg.data(), mg.size() * 8, cudaMemcpyHostToDevice));
         d.metgb = d_mg;
     }
-    std::vector<int> gslot(6 * (size_t)E, -1);
+    const std::vector<int>& gslot = c->h_gislot;
     int ng = 0;
-    for (size_t i = 0; i < c->h_ginterp.size(); ++i)
-        if (c->h_ginterp[i]) gslot[i] = ng++;
+    for (int v : gslot) ng = v + 1 > ng ? v + 1 : ng;
     if (ng > 0) {
         std::vector<double> mg((size_t)ng * per);
         parallel_for(E, [&](int64_t e) {
@@ -607,13 +608,9 @@ ffe_status build_ks_fd_tables(ffe_ctx* c, const std::vector<double>& xfd) {
             }
         });
         double* d_mg;
-        int* d_gs;
         if ((s = dalloc(c, &d_mg, mg.size()))) return s;
-        if ((s = dalloc(c, &d_gs, gslot.size()))) return s;
         CK(cudaMemcpy(d_mg, mg.data(), mg.size() * 8, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(d_gs, gslot.data(), gslot.size() * sizeof(int), cudaMemcpyHostToDevice));
         d.metgi = d_mg;
-        d.gislot = d_gs;
     }
     return FFE_OK;
 }
@@ -647,6 +644,64 @@ ffe_status set_ginterp(ffe_ctx* c, const std::vector<int>& nbr) {
     if ((s = dalloc(c, &p, gi.size()))) return s;
     CK(cudaMemcpy(p, gi.data(), gi.size(), cudaMemcpyHostToDevice));
     d.ginterp = p;
+    // per ghost of those faces: its reference coordinates in the neighbour
+    // (closed-form inverse of the neighbour's wedge map) turned into the
+    // interpolation data the kernels use -- the first cell and the 6-point
+    // Lagrange weights of the stencil through the neighbour's subcell centres
+    // along each axis, and the Lagrange weights of its LGL nodes along each
+    // axis -- so that the kernels do no transcendental or division work
+    std::vector<int> slot(gi.size(), -1);
+    int ns = 0;
+    for (size_t i = 0; i < gi.size(); ++i)
+        if (gi[i]) slot[i] = ns++;
+    const int ncm = d.nc, ghn = GH * ncm * ncm;
+    std::vector<int> gst((size_t)ns * ghn * 3, 0);
+    std::vector<double> gwf((size_t)ns * ghn * 18, 0.0), gwl((size_t)ns * ghn * 3 * MAXNP, 0.0);
+    auto geo_of = [&](int e, int& el) {
+        if (c->batch) {
+            const InstInfo& in = c->insts[c->h_einst[e]];
+            el = e - in.e0;
+            return ShellGeo{in.r_in, in.c, in.na, in.nr};
+        }
+        el = e;
+        return c->shell;
+    };
+    parallel_for(d.E, [&](int64_t e) {
+        for (int f = 0; f < 6; ++f) {
+            const int sl = slot[6 * e + f];
+            if (sl < 0) continue;
+            const int nb = nbr[6 * (size_t)e + f];
+            const int P = host_P(c, (int)e), nc = 2 * P + 1, np1 = P + 1;
+            const Tables& T = c->tabs_h[P];
+            int el, eln;
+            const ShellGeo ge = geo_of((int)e, el), gn = geo_of(nb, eln);
+            for (int t = 0; t < GH * nc * nc; ++t) {
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                double xn[3];
+                shell_ghost_ref(ge, el, gn, eln, f >> 1, f & 1, g, ta, tb, nc, xn);
+                const size_t gi3 = ((size_t)sl * ghn + t) * 3;
+                for (int a = 0; a < 3; ++a) {
+                    gst[gi3 + a] = fd6_stencil(nc, xn[a], &gwf[((size_t)sl * ghn + t) * 18 + 6 * a]);
+                    lagrange_at(T.x, np1, xn[a], &gwl[(gi3 + a) * MAXNP]);
+                }
+            }
+        }
+    });
+    int *d_sl, *d_st;
+    double *d_wf, *d_wl;
+    if ((s = dalloc(c, &d_sl, slot.size()))) return s;
+    if ((s = dalloc(c, &d_st, gst.size()))) return s;
+    if ((s = dalloc(c, &d_wf, gwf.size()))) return s;
+    if ((s = dalloc(c, &d_wl, gwl.size()))) return s;
+    CK(cudaMemcpy(d_sl, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_st, gst.data(), gst.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_wf, gwf.data(), gwf.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_wl, gwl.data(), gwl.size() * 8, cudaMemcpyHostToDevice));
+    d.gislot = d_sl;
+    d.gst = d_st;
+    d.gwf = d_wf;
+    d.gwl = d_wl;
+    c->h_gislot = slot;
     return FFE_OK;
 }
 
@@ -864,8 +919,13 @@ void enqueue_step(ffe_ctx* c) {
     if (d.tci_on) launch_fd2dg(d, c->un, st);
 }
 
-// Launch-shape autotuner: times the DG right-hand side (no state change)
-// with persistent grids of 1, 2, 3 and 4 CTAs per SM and keeps the fastest.
+// Launch-shape autotuner: times the DG right-hand side (no state change) with
+// persistent grids of 1, 2, 3, 4, 6 and 8 CTAs per SM and keeps the fastest,
+// for the highest order and, in a batch, separately for the elements of each
+// lower order (each order runs its own kernel in CTAs sized for it, so each
+// has its own best grid: elements per CTA per order).  The whole right-hand
+// side is timed each time, one order's grid varied, the others at their best
+// so far.
 ffe_status autotune(ffe_ctx* c) {
     Dev& d = c->d;
     cudaEvent_t a, b;
@@ -873,28 +933,34 @@ ffe_status autotune(ffe_ctx* c) {
     CK(cudaEventCreate(&b));
     launch_build_lists(d, c->st);
     if (!d.ks || d.metfd) launch_current(d, c->un, c->J, nullptr, 0, c->st);
-    float best = 1e30f;
-    int best_g = 0;
-    for (int g : {d.nsm, 2 * d.nsm, 3 * d.nsm, 4 * d.nsm}) {
-        d.dg_grid = g;
-        float tot = 0.0f;
-        for (int rep = 0; rep < 3; ++rep) {
-            CK(cudaEventRecord(a, c->st));
-            if (d.curved)
-                launch_dg_substep_curved(d, SUB_RHS, c->un, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, c->Fs,
-                                         c->Fs, c->G1, c->st);
-            else
-                launch_dg_substep(d, SUB_RHS, c->un, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, c->Fs,
-                                  c->Fs, c->G1, c->st);
-            CK(cudaEventRecord(b, c->st));
-            CK(cudaEventSynchronize(b));
-            float ms = 0.0f;
-            CK(cudaEventElapsedTime(&ms, a, b));
-            if (rep > 0) tot += ms;
+    int* slots[3] = {&d.dg_grid, &d.dg_grid_lo, &d.dg_grid_lo2};
+    const int nord = c->batch ? 3 : 1;
+    for (int o = 0; o < nord; ++o) {
+        if (o == 1 && !d.dg_list_lo) continue;
+        if (o == 2 && !d.dg_list_lo2) continue;
+        float best = 1e30f;
+        int best_g = 0;
+        for (int k : {1, 2, 3, 4, 6, 8}) {
+            *slots[o] = k * d.nsm;
+            float tot = 0.0f;
+            for (int rep = 0; rep < 3; ++rep) {
+                CK(cudaEventRecord(a, c->st));
+                if (d.curved)
+                    launch_dg_substep_curved(d, SUB_RHS, c->un, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4,
+                                             c->Fs, c->Fs, c->G1, c->st);
+                else
+                    launch_dg_substep(d, SUB_RHS, c->un, c->J, c->un, c->F2, c->F3, c->G1, c->G2, c->G3, c->G4, c->Fs,
+                                      c->Fs, c->G1, c->st);
+                CK(cudaEventRecord(b, c->st));
+                CK(cudaEventSynchronize(b));
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, a, b));
+                if (rep > 0) tot += ms;
+            }
+            if (tot < best) { best = tot; best_g = k * d.nsm; }
         }
-        if (tot < best) { best = tot; best_g = g; }
+        *slots[o] = best_g;
     }
-    d.dg_grid = best_g;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     c->tuned = true;
@@ -2019,6 +2085,9 @@ ffe_status ffe_get_info(ffe_ctx* c, ffe_info* info) try {
     info->node_updates = (int64_t)u[0];
     info->fd_elem_updates = (int64_t)u[1];
     info->dg_elem_updates = (int64_t)u[2];
+    info->dg_ctas_per_sm[0] = d.dg_grid / d.nsm;
+    info->dg_ctas_per_sm[1] = d.dg_grid_lo / d.nsm;
+    info->dg_ctas_per_sm[2] = d.dg_grid_lo2 / d.nsm;
     return FFE_OK;
 } catch (...) {
     return host_failure();
@@ -2104,6 +2173,8 @@ static ffe_status adjoint_ready(ffe_ctx* c) {
     if ((s = dalloc(c, &c->d_partial, 1024))) return s;
     const size_t ne = (size_t)d.nc + 2 * GH;
     if ((s = dalloc(c, &c->d_extb, (size_t)12 * d.chunk * ne * ne * ne))) return s;
+    const size_t fch = (size_t)(d.chunk < FDV_CHUNK ? d.chunk : FDV_CHUNK);
+    if ((s = dalloc(c, &c->d_gbuf, (size_t)3 * 12 * fch * (d.nc + 1) * d.nc * d.nc * 6))) return s;
     c->adj_ready = true;
     return FFE_OK;
 }
@@ -2140,7 +2211,7 @@ static void rhs_vjp_at(ffe_ctx* c, Field U, Field L, Field out) {
     launch_rhs_vjp(d, U, L, out, c->d_omega_bar, c->st);
     if (c->adj_fd) {
         launch_current(d, U, c->J, nullptr, 0, c->st);
-        launch_fd_rhs_vjp(d, U, c->J, L, out, c->d_extb, c->d_omega_bar, c->st);
+        launch_fd_rhs_vjp(d, U, c->J, L, out, c->d_extb, c->d_gbuf, c->d_omega_bar, c->st);
     }
 }
 

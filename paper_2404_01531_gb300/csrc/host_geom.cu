@@ -256,4 +256,55 @@ void match_faces(int E, const MapFn& map, const std::vector<double>& xnodes, int
     }
 }
 
+void shell_ghost_ref(const ShellGeo& ge, int el, const ShellGeo& gn, int eln, int dd, int s, int g, int ta, int tb,
+                     int nc, double xn[3]) {
+    int ia, ib, ir, w, ja, jb, jr, wn;
+    shell_elem(ge, el, ia, ib, ir, w);
+    shell_elem(gn, eln, ja, jb, jr, wn);
+    const double dxi = 2.0 / nc;
+    const int t1 = dd == 0 ? 1 : 0, t2 = dd == 2 ? 1 : 2;
+    double xi[3];
+    xi[dd] = s ? 1.0 + (g + 0.5) * dxi : -1.0 - (g + 0.5) * dxi;
+    xi[t1] = -1.0 + (ta + 0.5) * dxi;
+    xi[t2] = -1.0 + (tb + 0.5) * dxi;
+    const long double q = 0.785398163397448309615660845819875721L;   // pi/4
+    const long double ea = -1.0L + (ia + 0.5L * (xi[0] + 1.0L)) * 2.0L / ge.na;
+    const long double eb = -1.0L + (ib + 0.5L * (xi[1] + 1.0L)) * 2.0L / ge.na;
+    const long double er = -1.0L + (ir + 0.5L * (xi[2] + 1.0L)) * 2.0L / ge.nr;
+    // wedge axes: normal n = (2, 1, 0) for w >> 1 = (0, 1, 2), side s = +-1 by w & 1
+    auto axis = [](int ww) { return (ww >> 1) == 0 ? 2 : ((ww >> 1) == 1 ? 1 : 0); };
+    auto side = [](int ww) { return (ww & 1) ? -1.0L : 1.0L; };
+    long double u[3];
+    const int n1 = axis(w);
+    u[n1] = side(w);
+    u[(n1 + 1) % 3] = std::tan(q * ea);
+    u[(n1 + 2) % 3] = std::tan(q * eb);
+    const int n2 = axis(wn);
+    const long double un = side(wn) * u[n2];
+    const long double ean = std::atan(u[(n2 + 1) % 3] / un) / q;
+    const long double ebn = std::atan(u[(n2 + 2) % 3] / un) / q;
+    xn[0] = (double)(2.0L * ((ean + 1.0L) * 0.5L * gn.na - ja) - 1.0L);
+    xn[1] = (double)(2.0L * ((ebn + 1.0L) * 0.5L * gn.na - jb) - 1.0L);
+    xn[2] = (double)(2.0L * ((er + 1.0L) * 0.5L * gn.nr - jr) - 1.0L);
+}
+
+int fd6_stencil(int nc, double t, double* w) {
+    const double dxi = 2.0 / nc;
+    int st = (int)std::floor((t + 1.0) / dxi - 0.5) - 2;
+    st = st < 0 ? 0 : (st > nc - 6 ? nc - 6 : st);
+    double x[6];
+    for (int j = 0; j < 6; ++j) x[j] = -1.0 + (st + j + 0.5) * dxi;
+    lagrange_at(x, 6, t, w);
+    return st;
+}
+
+void lagrange_at(const double* x, int n, double t, double* w) {
+    for (int m = 0; m < n; ++m) {
+        long double v = 1.0L;
+        for (int k = 0; k < n; ++k)
+            if (k != m) v *= ((long double)t - x[k]) / ((long double)x[m] - x[k]);
+        w[m] = (double)v;
+    }
+}
+
 }  // namespace ffe

@@ -16,9 +16,11 @@
 //                 transposed DG -> FD evaluation (of U and of the nodal J~) into
 //                 the DG neighbour's nodes, or through the boundary state into my
 //                 outermost cells
-// Contributions from several faces and elements meet in out and in the
-// extended-block adjoint; they are summed with FP64 atomics (the order of the
-// additions, hence the last bits, may differ between runs).
+// The faces' contributions to the extended-block adjoint are written per face
+// (k_fdv_faces) and summed per cell in a fixed order (k_fdv_gather); where
+// several elements meet in out (an element's cells, a neighbour's cells or
+// nodes reached through ghosts) they are summed with FP64 atomics (the order
+// of those additions, hence the last bits, may differ between runs).
 #include "ffe_internal.h"
 #include "physics.cuh"
 #include "shellmap.cuh"
@@ -32,7 +34,14 @@ __device__ __forceinline__ double* extb_at(const Dev& d, double* extb, int q, in
 }
 
 
-__global__ void k_fdv_faces(Dev d, const int* list, int ci, int w0, Field L, double* extb) {
+// Per-face contributions to the extended-block adjoint: for face fi of
+// direction k the adjoints of its 6 stencil cells, gb[k][q][wl][fi][0..5] (the
+// stencil starts at extended index m along k); k_fdv_gather sums them per cell.
+__device__ __forceinline__ double* gbuf_at(const Dev& d, double* gb, int k, int q, int wl) {
+    return gb + (((int64_t)k * NQ + q) * d.chunk + wl) * nface(d) * 6;
+}
+
+__global__ void k_fdv_faces(Dev d, const int* list, int ci, int w0, Field L, double* gb) {
     const int n = chunk_n(d, ci, w0);
     const int64_t nfc = nface(d);
     const int64_t total = (int64_t)n * 3 * nfc;
@@ -107,10 +116,44 @@ __global__ void k_fdv_faces(Dev d, const int* list, int ci, int w0, Field L, dou
             if (ubL[qq] != 0.0 || ubR[qq] != 0.0) weno5z_pair_vjp(v0, v1, v2, v3, v4, v5, d.weno_eps, ubL[qq], ubR[qq], g);
             g[2] += ubm[qq];
             g[3] += ubp[qq];
-            double* dst = extb_at(d, extb, qq, wl) + base;
-            for (int s = 0; s < 6; ++s)
-                if (g[s] != 0.0) atomicAdd(dst + s * stride, g[s]);
+            double* dst = gbuf_at(d, gb, k, qq, wl) + fi * 6;
+            for (int s = 0; s < 6; ++s) dst[s] = g[s];
         }
+    }
+}
+
+// Extended-block adjoint of cell (x, y, z) and quantity q: the sum, over the
+// three directions, of the contributions of the faces whose 6-cell stencil
+// along that direction holds it (faces m = c_k - 5 .. c_k of the cell's line,
+// the cell being stencil entry c_k - m); every position is written, no
+// clearing, no atomics, a fixed order.
+__global__ void k_fdv_gather(Dev d, const int* list, int ci, int w0, const double* gb, double* extb) {
+    const int n = chunk_n(d, ci, w0);
+    const int64_t ext = ext_size(d);
+    const int64_t total = (int64_t)n * NQ * ext;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int wl = (int)(t / (NQ * ext));
+        const int qq = (int)((t / ext) % NQ);
+        const int64_t o = t % ext;
+        const int e = list[w0 + wl];
+        const int nc = esz(d, e).nc, ne = nc + 2 * GH;
+        if (o >= (int64_t)ne * ne * ne) continue;
+        const int c3[3] = {(int)(o % ne), (int)((o / ne) % ne), (int)(o / ((int64_t)ne * ne))};
+        double acc = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            int t1, t2;
+            axes_of(k, t1, t2);
+            const int ta = c3[t1] - GH, tb = c3[t2] - GH;
+            if (ta < 0 || ta >= nc || tb < 0 || tb >= nc) continue;
+            const double* g = gb + (((int64_t)k * NQ + qq) * d.chunk + wl) * nface(d) * 6;
+            for (int sI = 0; sI < 6; ++sI) {
+                const int m = c3[k] - sI;
+                if (m < 0 || m > nc) continue;
+                const int64_t fi = m + (int64_t)(nc + 1) * (ta + (int64_t)nc * tb);
+                acc += g[fi * 6 + sI];
+            }
+        }
+        extb_at(d, extb, qq, wl)[o] = acc;
     }
 }
 
@@ -306,20 +349,24 @@ __global__ void k_fdv_ghosts(Dev d, const int* list, int ci, int w0, Field U, Fi
 
 // out (FD block) must be zeroed and the DG right-hand-side adjoint already
 // written by the caller; J holds J~(U) at the FD cells (launch_current).
-void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, double* extb, double* omega_bar,
-                       cudaStream_t st) {
+void launch_fd_rhs_vjp(const Dev& dc, Field U, Field J, Field L, Field out, double* extb, double* gb,
+                       double* omega_bar, cudaStream_t st) {
+    // chunks of at most FDV_CHUNK elements: the per-face contribution buffer gb
+    // holds [3][12][FDV_CHUNK][faces][6] doubles
+    Dev d = dc;
+    d.chunk = d.chunk < FDV_CHUNK ? d.chunk : FDV_CHUNK;
     const size_t smem = fdv_ghost_smem(d);
     cudaFuncSetAttribute(k_fdv_ghosts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t ne = d.nc + 2 * GH;
-    const size_t extb_bytes = (size_t)NQ * d.chunk * ne * ne * ne * sizeof(double);
     for (int k = 0, nch = fd_chunks(d); k < nch; ++k) {
         const int w0 = k * d.chunk;
         prof_begin("fdv_fill", st);
         launch_fd_fill(d, d.fd_list, 1, w0, U, J, st);
-        cudaMemsetAsync(extb, 0, extb_bytes, st);
         prof_end(st);
         prof_begin("fdv_faces", st);
-        k_fdv_faces<<<d.nsm * 8, 128, 0, st>>>(d, d.fd_list, 1, w0, L, extb);
+        k_fdv_faces<<<d.nsm * 8, 128, 0, st>>>(d, d.fd_list, 1, w0, L, gb);
+        prof_end(st);
+        prof_begin("fdv_gather", st);
+        k_fdv_gather<<<d.nsm * 8, 256, 0, st>>>(d, d.fd_list, 1, w0, gb, extb);
         prof_end(st);
         prof_begin("fdv_cells", st);
         k_fdv_cells<<<d.nsm * 8, 256, 0, st>>>(d, d.fd_list, 1, w0, U, L, out, extb);
@@ -328,7 +375,7 @@ void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, doubl
         k_fdv_ghosts<<<d.nsm * 2, 256, smem, st>>>(d, d.fd_list, 1, w0, U, J, out, extb, omega_bar);
         launch_fdv_ghosts_interp(d, d.fd_list, 1, w0, U, out, extb, st);
         prof_end(st);
-        g_launch_counter += 3;
+        g_launch_counter += 4;
     }
 }
 

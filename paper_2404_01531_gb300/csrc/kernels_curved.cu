@@ -435,10 +435,12 @@ static void curved_dispatch_sub(const Dev& d, const SubArgs& a, cudaStream_t st)
     curved_launch<P, KS, SUB>(d, a, d.dg_list, 0, grid, st);
     // batches: the elements of orders P-1 and P-2, each in CTAs sized for their order
     if constexpr (P > 3) {
-        if (d.dg_list_lo) curved_launch<P - 1, KS, SUB>(d, a, d.dg_list_lo, 6, d.nsm * 4, st);
+        if (d.dg_list_lo)
+            curved_launch<P - 1, KS, SUB>(d, a, d.dg_list_lo, 6, d.dg_grid_lo > 0 ? d.dg_grid_lo : d.nsm * 4, st);
     }
     if constexpr (P > 4) {
-        if (d.dg_list_lo2) curved_launch<P - 2, KS, SUB>(d, a, d.dg_list_lo2, 7, d.nsm * 4, st);
+        if (d.dg_list_lo2)
+            curved_launch<P - 2, KS, SUB>(d, a, d.dg_list_lo2, 7, d.dg_grid_lo2 > 0 ? d.dg_grid_lo2 : d.nsm * 4, st);
     }
 }
 
@@ -455,7 +457,7 @@ static void curved_dispatch(const Dev& d, int sub, const SubArgs& a, cudaStream_
 void launch_dg_substep_curved(const Dev& d, int sub, Field Uin, Field J, Field un, Field F2, Field F3, Field G1,
                               Field G2, Field G3, Field G4, Field Fout, Field Uout, Field Gout, cudaStream_t st) {
     SubArgs a{Uin, J, un, F2, F3, G1, G2, G3, G4, Fout, Uout, Gout};
-    if (!d.ks) launch_fd_traces(d, Uin, J, st);
+    if (!d.ks || d.metfd) launch_fd_traces(d, Uin, J, st);
     prof_begin(sub == SUB_RHS ? "dg_rhs_curved" : "dg_substep_curved", st);
     if (d.ks) {
         switch (d.P) {

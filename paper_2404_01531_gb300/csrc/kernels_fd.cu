@@ -514,52 +514,78 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int ci, Field Uin
 // exterior state here instead of projecting 6 x 6 x 6 cells per face node
 // itself (which left most of its block idle).  Layout: per FD slot [6 faces]
 // [12 quantities][np1max^2], face node index a + np1 b along the face's axes
-// (axes_of of its normal).  One thread per (element, face, node, quantity).
+// (axes_of of its normal).  One CTA per (element, face): the 6 cell layers
+// next to the face (the normal stencil of a face node) go to shared memory and
+// the projection is sum-factorised -- normal direction, then the two
+// tangential ones -- 6 (nc^2 + nc np1 + np1^2) FMAs per quantity instead of
+// 216 per face node.
 __global__ void k_fd_traces(Dev d, Field U, Field J) {
+    extern __shared__ double sm[];
     const int n = d.counts[1];
     const int nfm = d.np1 * d.np1;
-    const int64_t per = (int64_t)6 * nfm * NQ;
-    const int64_t total = (int64_t)n * per;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(q / per);
-        const int r = (int)(q % per);
-        const int f = r / (nfm * NQ), ab = (r / NQ) % nfm, qv = r % NQ;
+    for (int item = blockIdx.x; item < n * 6; item += gridDim.x) {
+        const int w = item / 6, f = item % 6;
         const int e = d.fd_list[w];
         const int nb = d.nbr[e * 6 + f];
         if (nb < 0 || d.mask[nb] != 0) continue;
         const ES es = esz(d, e);
-        const int np1 = es.np1, nc = es.nc;
-        if (ab >= np1 * np1) continue;
+        const int np1 = es.np1, nc = es.nc, nc2 = nc * nc;
         const Tables& T = d.tabs[es.P];
         const int dd = f >> 1;
         int t1, t2;
         axes_of(dd, t1, t2);
-        int c[3];
-        c[dd] = (f & 1) ? es.P : 0;
-        c[t1] = ab % np1;
-        c[t2] = ab / np1;
-        const int lo0 = T.f2d_lo[c[0]], lo1 = T.f2d_lo[c[1]], lo2 = T.f2d_lo[c[2]];
+        const int cn = (f & 1) ? es.P : 0;       // the face's LGL index along the normal
+        const int lo = T.f2d_lo[cn];
+        double* L = sm;                            // [12][6][nc (t2)][nc (t1)]
+        double* A = L + NQ * 6 * nc2;              // [12][nc (t2)][nc (t1)]
+        double* B = A + NQ * nc2;                  // [12][nc (t2)][np1 (t1)]
         const int64_t base = fdb(d, e);
-        const double* src = qv < NV ? U.fd(qv) + base : J.fd(3 + qv - NV) + base;
-        double acc = 0.0;
-        for (int n2 = 0; n2 < 6; ++n2) {
-            double a2 = 0.0;
-            for (int n1 = 0; n1 < 6; ++n1) {
-                double a1 = 0.0;
-                const double* row = src + (int64_t)(lo0 + nc * ((lo1 + n1) + nc * (lo2 + n2)));
-                for (int n0 = 0; n0 < 6; ++n0) a1 = fma(T.F2D[c[0]][lo0 + n0], row[n0], a1);
-                a2 = fma(T.F2D[c[1]][lo1 + n1], a1, a2);
-            }
-            acc = fma(T.F2D[c[2]][lo2 + n2], a2, acc);
+        for (int t = threadIdx.x; t < NQ * 6 * nc2; t += blockDim.x) {
+            const int q = t / (6 * nc2), r = t % (6 * nc2);
+            const int nn = r / nc2, ab = r % nc2;
+            int c[3];
+            c[dd] = lo + nn;
+            c[t1] = ab % nc;
+            c[t2] = ab / nc;
+            const double* src = q < NV ? U.fd(q) : J.fd(3 + q - NV);
+            L[t] = src[base + c[0] + nc * (c[1] + nc * c[2])];
         }
-        d.ftr[(((int64_t)fd_slot_of(d, e) * 6 + f) * NQ + qv) * nfm + ab] = acc;
+        __syncthreads();
+        for (int t = threadIdx.x; t < NQ * nc2; t += blockDim.x) {
+            const int q = t / nc2, ab = t % nc2;
+            double acc = 0.0;
+            for (int m = 0; m < 6; ++m) acc = fma(T.F2D[cn][lo + m], L[(q * 6 + m) * nc2 + ab], acc);
+            A[t] = acc;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < NQ * nc * np1; t += blockDim.x) {
+            const int q = t / (nc * np1), r = t % (nc * np1);
+            const int b = r / np1, i = r % np1;
+            const int li = T.f2d_lo[i];
+            double acc = 0.0;
+            for (int m = 0; m < 6; ++m) acc = fma(T.F2D[i][li + m], A[(q * nc + b) * nc + li + m], acc);
+            B[t] = acc;
+        }
+        __syncthreads();
+        double* dst = d.ftr + ((int64_t)fd_slot_of(d, e) * 6 + f) * NQ * nfm;
+        for (int t = threadIdx.x; t < NQ * np1 * np1; t += blockDim.x) {
+            const int q = t / (np1 * np1), r = t % (np1 * np1);
+            const int j = r / np1, i = r % np1;
+            const int lj = T.f2d_lo[j];
+            double acc = 0.0;
+            for (int m = 0; m < 6; ++m) acc = fma(T.F2D[j][lj + m], B[(q * nc + lj + m) * np1 + i], acc);
+            dst[q * nfm + i + np1 * j] = acc;
+        }
+        __syncthreads();
     }
 }
 
 void launch_fd_traces(const Dev& d, Field U, Field J, cudaStream_t st) {
     if (!d.ftr) return;
+    const size_t smem = (size_t)(NQ * 6 * d.nc * d.nc + NQ * d.nc * d.nc + NQ * d.nc * d.np1) * sizeof(double);
+    cudaFuncSetAttribute(k_fd_traces, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin("fd_traces", st);
-    k_fd_traces<<<d.nsm * 8, 128, 0, st>>>(d, U, J);
+    k_fd_traces<<<d.nsm * 2, 256, smem, st>>>(d, U, J);
     prof_end(st);
     g_launch_counter += 1;
 }

@@ -20,8 +20,10 @@
 //     interpolated state, as for every FD ghost;
 //   - a DG neighbour: its nodal polynomial of U and of its nodal current J~
 //     evaluated at the point (as its ghosts are filled everywhere else).
-// On the Kerr-Schild background the ghost current takes the metric at the
-// ghost centre (Dev::metgi).
+// The geometry is static, so the host tabulates, per ghost, the stencils'
+// first cells and weights and the LGL Lagrange weights (Dev::gst, gwf, gwl);
+// the kernels only gather and multiply.  On the Kerr-Schild background the
+// ghost current takes the metric at the ghost centre (Dev::metgi).
 #include "ffe_internal.h"
 #include "physics.cuh"
 #include "physics_gen.cuh"
@@ -32,73 +34,6 @@
 namespace ffe {
 
 namespace {
-
-// normal axis and side of wedge w (the numbering of shell_map)
-__device__ __forceinline__ int wedge_axis(int w) { return (w >> 1) == 0 ? 2 : ((w >> 1) == 1 ? 1 : 0); }
-__device__ __forceinline__ double wedge_side(int w) { return (w & 1) ? -1.0 : 1.0; }
-
-// Reference coordinates in element nb of the centre of ghost cell (g, ta, tb)
-// past face (dd, s) of element e (e and nb in one shell).
-__device__ void ghost_ref_in_nb(const Dev& d, int e, int nb, int dd, int s, int g, int ta, int tb, int nc,
-                                double xn[3]) {
-    int el, eln;
-    const ShellGeo ge = shell_for(d, e, el);
-    const ShellGeo gn = shell_for(d, nb, eln);
-    int ia, ib, ir, w, ja, jb, jr, wn;
-    shell_elem(ge, el, ia, ib, ir, w);
-    shell_elem(gn, eln, ja, jb, jr, wn);
-    const double dxi = 2.0 / nc;
-    int t1, t2;
-    axes_of(dd, t1, t2);
-    double xi[3];
-    xi[dd] = s ? 1.0 + (g + 0.5) * dxi : -1.0 - (g + 0.5) * dxi;
-    xi[t1] = -1.0 + (ta + 0.5) * dxi;
-    xi[t2] = -1.0 + (tb + 0.5) * dxi;
-    const double q = 0.78539816339744830962;   // pi/4
-    const double ea = -1.0 + (ia + 0.5 * (xi[0] + 1.0)) * 2.0 / ge.na;
-    const double eb = -1.0 + (ib + 0.5 * (xi[1] + 1.0)) * 2.0 / ge.na;
-    const double er = -1.0 + (ir + 0.5 * (xi[2] + 1.0)) * 2.0 / ge.nr;
-    // direction of the point, scaled so that its wedge-axis component is the side
-    double u[3];
-    const int n1 = wedge_axis(w);
-    u[n1] = wedge_side(w);
-    u[(n1 + 1) % 3] = tan(q * ea);
-    u[(n1 + 2) % 3] = tan(q * eb);
-    const int n2 = wedge_axis(wn);
-    const double un = wedge_side(wn) * u[n2];
-    const double ean = atan(u[(n2 + 1) % 3] / un) / q;
-    const double ebn = atan(u[(n2 + 2) % 3] / un) / q;
-    xn[0] = 2.0 * ((ean + 1.0) * 0.5 * gn.na - ja) - 1.0;
-    xn[1] = 2.0 * ((ebn + 1.0) * 0.5 * gn.na - jb) - 1.0;
-    xn[2] = 2.0 * ((er + 1.0) * 0.5 * gn.nr - jr) - 1.0;
-}
-
-// Lagrange basis through the np1 LGL nodes of T at t.
-__device__ __forceinline__ void lgl_weights(const Tables& T, int np1, double t, double* w) {
-    for (int m = 0; m < np1; ++m) {
-        double v = 1.0;
-        for (int k = 0; k < np1; ++k)
-            if (k != m) v *= (t - T.x[k]) / (T.x[m] - T.x[k]);
-        w[m] = v;
-    }
-}
-
-// Lagrange basis through the 6 subcell centres nearest t (stencil kept inside
-// the element of nc cells); returns the first cell of the stencil.
-__device__ __forceinline__ int fd6_weights(int nc, double t, double* w) {
-    const double dxi = 2.0 / nc;
-    int st = (int)floor((t + 1.0) / dxi - 0.5) - 2;
-    st = st < 0 ? 0 : (st > nc - 6 ? nc - 6 : st);
-    double x[6];
-    for (int j = 0; j < 6; ++j) x[j] = -1.0 + (st + j + 0.5) * dxi;
-    for (int m = 0; m < 6; ++m) {
-        double v = 1.0;
-        for (int k = 0; k < 6; ++k)
-            if (k != m) v *= (t - x[k]) / (x[m] - x[k]);
-        w[m] = v;
-    }
-    return st;
-}
 
 __device__ __forceinline__ int64_t ghost_off(int dd, int s, int nc, int g, int ta, int tb) {
     const int ne = nc + 2 * GH;
@@ -124,7 +59,6 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
         if (!d.ginterp[e * 6 + f]) continue;
         const int nb = d.nbr[e * 6 + f];
         const ES es = esz(d, e);
-        const Tables& T = d.tabs[es.P];
         const int nc = es.nc, np1 = es.np1, nn = es.nn;
         const int dd = f >> 1, s = f & 1;
         const bool fdnb = d.mask[nb] == 1;
@@ -136,31 +70,32 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
             }
             __syncthreads();
         }
-        const int nper = GH * nc * nc;
+        const int nper = GH * nc * nc, ghn = GH * d.nc * d.nc;
+        const int sl = d.gislot[e * 6 + f];
         for (int t = threadIdx.x; t < nper; t += blockDim.x) {
             const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
-            double xn[3];
-            ghost_ref_in_nb(d, e, nb, dd, s, g, ta, tb, nc, xn);
             const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
+            const int64_t gi = (int64_t)sl * ghn + t;
             if (fdnb) {
-                double wa[6], wb[6], wc[6];
-                const int sa = fd6_weights(nc, xn[0], wa), sb = fd6_weights(nc, xn[1], wb), sc = fd6_weights(nc, xn[2], wc);
+                const int* st3 = d.gst + gi * 3;
+                const double* wf = d.gwf + gi * 18;
+                const int sa = st3[0], sb = st3[1], sc = st3[2];
                 const int64_t base = fdb(d, nb);
                 double u[NV];
                 for (int v = 0; v < NV; ++v) u[v] = 0.0;
                 for (int cz = 0; cz < 6; ++cz)
                     for (int cy = 0; cy < 6; ++cy) {
-                        const double wzy = wc[cz] * wb[cy];
+                        const double wzy = wf[12 + cz] * wf[6 + cy];
                         const int64_t row = base + sa + (int64_t)nc * ((sb + cy) + (int64_t)nc * (sc + cz));
                         for (int cx = 0; cx < 6; ++cx) {
-                            const double w = wzy * wa[cx];
+                            const double w = wzy * wf[cx];
                             for (int v = 0; v < NV; ++v) u[v] = fma(w, U.fd(v)[row + cx], u[v]);
                         }
                     }
                 double jd[3], jf[3];
                 if (d.ks) {
                     PM m;
-                    load_pm(d.metgi + (int64_t)d.gislot[e * 6 + f] * NPM * GH * d.nc * d.nc, (int64_t)GH * d.nc * d.nc,
+                    load_pm(d.metgi + (int64_t)sl * NPM * GH * d.nc * d.nc, (int64_t)GH * d.nc * d.nc,
                             (int64_t)g * nc * nc + ta + nc * tb, m);
                     current_gen(u, m, d.eta, jd, jf);
                 } else {
@@ -169,10 +104,9 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
                 for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[og] = u[v];
                 for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = jf[k];
             } else {
-                double la[MAXNP], lb[MAXNP], lc[MAXNP];
-                lgl_weights(T, np1, xn[0], la);
-                lgl_weights(T, np1, xn[1], lb);
-                lgl_weights(T, np1, xn[2], lc);
+                const double* la = d.gwl + gi * 3 * MAXNP;
+                const double* lb = la + MAXNP;
+                const double* lc = lb + MAXNP;
                 for (int qv = 0; qv < NQ; ++qv) {
                     const double* a = su + qv * nn;
                     double acc = 0.0;
@@ -233,7 +167,6 @@ __global__ void k_fdv_ghosts_interp(Dev d, const int* list, int ci, int w0, Fiel
         if (!d.ginterp[e * 6 + f]) continue;
         const int nb = d.nbr[e * 6 + f];
         const ES es = esz(d, e);
-        const Tables& T = d.tabs[es.P];
         const int nc = es.nc, np1 = es.np1, nn = es.nn;
         const int dd = f >> 1, s = f & 1;
         const bool fdnb = d.mask[nb] == 1;
@@ -243,17 +176,18 @@ __global__ void k_fdv_ghosts_interp(Dev d, const int* list, int ci, int w0, Fiel
             box[3 + threadIdx.x] = -1;
         }
         __syncthreads();
+        const int sl = d.gislot[e * 6 + f], ghn = GH * d.nc * d.nc;
         for (int t = threadIdx.x; t < nper; t += blockDim.x) {
             const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
-            double xn[3];
-            ghost_ref_in_nb(d, e, nb, dd, s, g, ta, tb, nc, xn);
             const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
+            const int64_t gi = (int64_t)sl * ghn + t;
             double gq[NQ];
             for (int qv = 0; qv < NQ; ++qv) gq[qv] = extb_ptr(d, extb, qv, wl)[og];
             double* w = wts + (size_t)t * 3 * MAXNP;
             if (fdnb) {
                 for (int a = 0; a < 3; ++a) {
-                    const int st = fd6_weights(nc, xn[a], w + a * MAXNP);
+                    const int st = d.gst[gi * 3 + a];
+                    for (int m = 0; m < 6; ++m) w[a * MAXNP + m] = d.gwf[gi * 18 + 6 * a + m];
                     sti[3 * t + a] = st;
                     atomicMin(box + a, st);
                     atomicMax(box + 3 + a, st);
@@ -267,7 +201,7 @@ __global__ void k_fdv_ghosts_interp(Dev d, const int* list, int ci, int w0, Fiel
                 current_vjp(u, d.eta, gq + NV, gq + NV, ub);
                 for (int v = 0; v < NV; ++v) gb[v * nperm + t] = ub[v];
             } else {
-                for (int a = 0; a < 3; ++a) lgl_weights(T, np1, xn[a], w + a * MAXNP);
+                for (int a = 0; a < 3 * MAXNP; ++a) w[a] = d.gwl[gi * 3 * MAXNP + a];
                 for (int qv = 0; qv < NQ; ++qv) gb[qv * nperm + t] = gq[qv];
             }
         }

@@ -64,7 +64,8 @@ class Info(ctypes.Structure):
                 ("n_dg", ctypes.c_int64), ("n_fd", ctypes.c_int64), ("n_state", ctypes.c_int64),
                 ("dt", ctypes.c_double), ("dxmin", ctypes.c_double), ("t", ctypes.c_double),
                 ("steps", ctypes.c_int64), ("n_fd_elem", ctypes.c_int), ("node_updates", ctypes.c_int64),
-                ("fd_elem_updates", ctypes.c_int64), ("dg_elem_updates", ctypes.c_int64)]
+                ("fd_elem_updates", ctypes.c_int64), ("dg_elem_updates", ctypes.c_int64),
+                ("dg_ctas_per_sm", ctypes.c_int * 3)]
 
 
 _lib = None

@@ -77,3 +77,33 @@ def test_batch_layout(ffe):
     for i, c in enumerate(CFGS):
         assert np.all(eP[first[i]:first[i + 1]] == c["P"]) and np.all(ei[first[i]:first[i + 1]] == i)
     b.close()
+
+
+def test_full_batch_equals_single_contexts_over_ten_steps(ffe):
+    """The batched workload at its stated size (32 rotating-dipole shells,
+    seed 1531, 99,990 elements, P 4 and 5, FD slot pool of half the elements)
+    advanced 10 steps in one batched context equals each instance advanced
+    alone (the single contexts are held to the oracle by the tests above):
+    same masks, states equal to rounding."""
+    cfgs = W.pulsars()
+    E = sum(6 * c["n_ang"] ** 2 * c["n_rad"] for c in cfgs)
+    b = ffe.BatchContext(cfgs, fd_capacity=E // 2)
+    b.set_initial()
+    b.step(10)
+    Ub, mb = b.download()
+    assert b.status() == 0
+    for i, cfg in enumerate(cfgs):
+        udg_b, ufd_b = b.split_instance(Ub, i)
+        m_b = _instance_mask(b, i, mb)
+        s = ffe.Context(cfg)
+        s.set_initial()
+        s.step(10)
+        Us, ms = s.download()
+        dgs, fds = s.split(Us)
+        near = set(s.near_threshold())
+        assert set(np.nonzero(ms != m_b)[0].tolist()) <= near, i
+        same = ms == m_b
+        if same.all():
+            assert rel_err_split(udg_b, dgs, ufd_b, fds, ms == 0).max() <= 1e-10, i
+        s.close()
+    b.close()
