@@ -227,6 +227,52 @@ def run_wald(args):
     print(json.dumps(line), flush=True)
 
 
+def run_wald_vacuum(args):
+    """The paper's vacuum Wald problem (Sec. IV.B.2) at its grid (16 x 96
+    elements, P = 5, spherical Kerr-Schild radius r in [M, 125 M]): Wald's
+    magnetic field with E~ = 0 at t = 0, eta = 0, evolved to t = 125 M for
+    several spins; the flux of B~ through the upper half of the outer horizon
+    (FFE_DIAG_BFLUX_UPPER on the coordinate surface r = r+) at t = 25, 50, 75,
+    100, 125 M against the closed form pi r+^2 B0 (1 - a^4/r+^4) of the
+    stationary state (King et al.), and the RMS of psi~ and phi~."""
+    import math
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rows = []
+    for a in args.spins:
+        cfg = W.wald_vacuum(spin=a)
+        ctx = ffe.Context(cfg)
+        ctx.set_initial()
+        dt = ctx.dt
+        rp = 1.0 + math.sqrt(1.0 - a * a)
+        king = math.pi * rp * rp * (1.0 - a ** 4 / rp ** 4)
+        flux0 = ctx.diagnostic("bflux_upper", (rp,))[0]
+        series, done = [], 0
+        t0 = time.perf_counter()
+        for tt in (25.0, 50.0, 75.0, 100.0, cfg["t_end"]):
+            n = int(round(tt / dt))
+            ctx.step(n - done)
+            done = n
+            series.append({"t": n * dt, "flux": ctx.diagnostic("bflux_upper", (rp,))[0],
+                           "rms_psi": ctx.diagnostic("l2_err", (6, 1))[0],
+                           "rms_phi": ctx.diagnostic("l2_err", (7, 1))[0]})
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        rows.append({"spin": a, "r_plus": rp, "dt": dt, "steps": done, "king": king, "flux_t0": flux0,
+                     "series": series, "rel_err_end": series[-1]["flux"] / king - 1.0, "wall_s": wall,
+                     "status_bits": ctx.status()})
+        ctx.close()
+    line = {"metric": "horizon magnetic flux / closed form, vacuum Wald (Sec. IV.B.2)",
+            "value": max(abs(r["rel_err_end"]) for r in rows), "unit": "max relative deviation at t_end",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "vacuum Wald: Kerr-Schild M=1, Wald B with E=0 at t=0, eta=0, 6 wedges x 4x4x16, "
+                                   "P=5, spherical Kerr-Schild r in [1, 125], outflow between the horizons, no "
+                                   "incoming Poynting flux outside, t_end = 125"},
+            "runs": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_shell(args):
     """The neutron-star shell (6 wedges x 6x6x12, P=5, eta=1e5) with its three
     innermost radial layers on FD subcells and the mask frozen: an FD-heavy
@@ -702,19 +748,24 @@ def main():
     ap.add_argument("--nx", type=int, default=64,
                     help="elements along x (same width 4/64; smaller values for profiler captures)")
     ap.add_argument("--workload", default="breakdown",
-                    choices=["breakdown", "pulsars", "adjoint", "shell", "oned", "dgphases", "wald"],
+                    choices=["breakdown", "pulsars", "adjoint", "shell", "oned", "dgphases", "wald", "wald_vacuum"],
                     help="pulsars: the 32-shell batch, batched launch vs one context per instance; "
                          "adjoint: luminosity gradient of one neutron-star shell (--steps steps); "
                          "shell: that shell with three FD layers, frozen mask (curved FD kernels); "
                          "oned: the paper's 1-D tests and its DG/FD split experiment; "
                          "dgphases: cost of the DG kernel's filter, indicator and stiff-current phases; "
-                         "wald: the Kerr-Schild Wald shell, 1000 steps, indicator on")
+                         "wald: the Kerr-Schild Wald shell, 1000 steps, indicator on; "
+                         "wald_vacuum: horizon flux against spin (Sec. IV.B.2)")
     ap.add_argument("--no-adjoint", action="store_true", help="breakdown: skip the adjoint/forward timing")
     ap.add_argument("--no-batch", action="store_true",
                     help="breakdown: skip the batched-against-single timing of the 32-shell batch")
+    ap.add_argument("--no-split", action="store_true",
+                    help="breakdown: skip the DG/FD split experiment (Alfven wave on (8,32,8) elements)")
     ap.add_argument("--recon", default="weno5z", choices=list(RECON),
                     help="breakdown and shell: FD reconstruction (the paper's WENO5-Z, or MP5)")
     ap.add_argument("--n-inst", type=int, default=32)
+    ap.add_argument("--spins", type=float, nargs="+", default=[0.0, 0.5, 0.9, 0.999],
+                    help="wald_vacuum: black-hole spins")
     ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
     ap.add_argument("--fd-slots", type=float, default=0.25,
                     help="breakdown: FD slot pool as a fraction of the elements (1 = one FD block per element)")
@@ -727,6 +778,8 @@ def main():
         return run_shell(args)
     if args.workload == "wald":
         return run_wald(args)
+    if args.workload == "wald_vacuum":
+        return run_wald_vacuum(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
     if args.workload == "oned":
@@ -871,6 +924,12 @@ def main():
             batched = batch_measure(args.n_inst, 3, 2, args.fd_capacity)
         except Exception as ex:  # reported, not fatal
             batched = {"failed": str(ex)}
+    split = None
+    if not args.no_split and ws == 1:
+        try:
+            split = split_measure(steps=5, warmup=3)
+        except Exception as ex:  # reported, not fatal
+            split = {"failed": str(ex)}
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -894,7 +953,7 @@ def main():
             "roofline": roof, "roofline_dg": roof_dg, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
             "adjoint": adj, "batched_over_single": (batched or {}).get("batched_over_single"),
-            "batch": batched, "status_bits": status}
+            "batch": batched, "split": split, "status_bits": status}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -15,7 +15,7 @@ Workloads (the five problem setups the library is exercised on):
 import math
 
 # boundary kinds and enumerations (mirrored by integer codes of the C ABI)
-PERIODIC, DIRICHLET, NO_INCOMING, STAR = "periodic", "dirichlet", "no_incoming", "star"
+PERIODIC, DIRICHLET, NO_INCOMING, STAR, OUTFLOW = "periodic", "dirichlet", "no_incoming", "star", "outflow"
 RELAX, HARD, RELAX_THEN_HARD = 0, 1, 2
 
 
@@ -143,3 +143,17 @@ def adjoint_pulsar(tiny=False, steps=500):
     if tiny:
         return pulsar(r_lc=6.0, chi=math.pi / 4, n_ang=2, n_rad=4, r_out=24.0, steps=steps)
     return pulsar(r_lc=6.0, chi=math.pi / 4, n_ang=6, n_rad=12, r_out=24.0, steps=steps)
+
+
+def wald_vacuum(spin=0.9, n_ang=4, n_rad=16, P=5, r_in=1.0, r_out=125.0, t_end=125.0):
+    """The paper's vacuum Wald problem (Sec. IV.B.2): Kerr-Schild M = 1, spin a,
+    Wald's magnetic field with E~ = 0 at t = 0, eta = 0, on a shell in the
+    spherical Kerr-Schild radius (App. B) whose inner surface r_in = M lies
+    between the two horizons, where nothing is imposed (outflow); no incoming
+    Poynting flux at r_out = 125 M; 16 x 96 elements (n_rad x 6 n_ang^2) at
+    P = 5, CFL factor 0.25, evolved to t_end = 125 M (a stationary state after
+    t ~ 80 M).  All elements stay DG (indicator off)."""
+    return dict(name="wald_vacuum", kind="shell", r_in=r_in, r_out=r_out, n_ang=n_ang, n_rad=n_rad,
+                bc_inner=OUTFLOW, bc_outer=NO_INCOMING, P=P, metric=("kerr_schild", 1.0, spin),
+                shell_ks=True, params=base_params(eta=0.0, cfl=0.25, tci_on=0),
+                initial=("wald", dict(M=1.0, a=spin, B0=1.0, e=0.0)), t_end=t_end)

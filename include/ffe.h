@@ -60,7 +60,9 @@ typedef struct ffe_ctx ffe_ctx;
 
 /* domain kinds, boundary kinds, metric kinds, initial data, constraint modes */
 enum { FFE_DOMAIN_BOX = 0, FFE_DOMAIN_SHELL6 = 1 };
-enum { FFE_BC_PERIODIC = 1, FFE_BC_DIRICHLET = 2, FFE_BC_NO_INCOMING = 3, FFE_BC_STAR = 4 };
+enum { FFE_BC_PERIODIC = 1, FFE_BC_DIRICHLET = 2, FFE_BC_NO_INCOMING = 3, FFE_BC_STAR = 4,
+       FFE_BC_OUTFLOW = 5   /* exterior state = interior state: an excision surface inside a
+                               horizon, where the paper imposes no condition (Sec. IV.B.2) */ };
 enum { FFE_METRIC_MINKOWSKI = 0, FFE_METRIC_KERR_SCHILD = 1 };
 enum { FFE_ID_FAST_WAVE = 0, FFE_ID_BREAKDOWN = 1, FFE_ID_CLEANING_MODE = 2,
        FFE_ID_WALD = 3, FFE_ID_DIPOLE = 4,
@@ -80,6 +82,16 @@ typedef struct {
     double lo[3], hi[3];
     int bc_lo[3], bc_hi[3];
     double r_in, r_out;
+    int shell_ks;   /* SHELL6 on FFE_METRIC_KERR_SCHILD: 1 = r_in, r_out and the
+                       logarithmic radial map are in the spherical Kerr-Schild
+                       radius r of the metric's spin a (App. B), the point of
+                       unit direction v at radius r being x = r v + a (z^ x v),
+                       so r = const is the spheroid (x^2+y^2)/(r^2+a^2) + z^2/r^2 = 1
+                       (r_in between the horizons puts the whole inner surface
+                       where every characteristic leaves the domain); 0 = the
+                       sphere |x| = r.  With 1, FD subcells are FFE_ENOTIMPL
+                       (tci_on must be 0; FFE_INIT_VIA_FD and FD masks are refused).
+                       FFE_EINVAL on a box or a Minkowski metric. */
 } ffe_domain;
 
 /* Elements: BOX n[0] x n[1] x n[2]; SHELL6 n[0] = n[1] angular, n[2] radial per wedge. */
@@ -174,7 +186,8 @@ ffe_status ffe_set_initial_batch(ffe_ctx* ctx, int id_kind, const double* id_par
  *   FAST_WAVE      {amp}                 B=(1,b,0), E=(0,0,-b), b = 1 + amp sin(pi x)
  *   BREAKDOWN      {}                    current sheet of the breakdown workload
  *   CLEANING_MODE  {eps}                 B=(1+eps sin(pi x),0,0)
- *   WALD           {M, a, B0}            Wald's field (Kerr-Schild metric)
+ *   WALD           {M, a, B0[, e]}       Wald's field (Kerr-Schild metric); E~ times e (default
+ *                                        1; e = 0: the vacuum Wald problem's start, Sec. IV.B.2)
  *   DIPOLE         {mu, delta, chi}      B~ = curl[mu m x x/(r^2+delta^2)^(3/2)], m = (sin chi, 0, cos chi)
  *   FAST_WAVE_KINK {}                    B=(1,b,0), E=(0,0,-b), b = 1 | 0.85-1.5x | 0.7 across |x|<0.1
  *   ALFVEN         {}                    B=(1,1,b), E=(-b,0,1), b = 1 | 1.15+0.15 sin(5 pi x) | 1.3,
@@ -327,9 +340,10 @@ ffe_status ffe_adjoint_forward(ffe_ctx* ctx, const double* U_dev, double* stages
 ffe_status ffe_adjoint_reverse(ffe_ctx* ctx, const double* U_dev, const double* stages_dev, const double* lam_in_dev,
                                double* lam_out_dev, double* omega_bar);
 
-/* Spin-down luminosity through the sphere r = r_L (Sec. IV.C.2): L = closed
- * integral of (E x B).r^ dA on the radial element layer containing r_L (xi^3
- * interpolation, LGL quadrature, exact area element).  *L_host receives L;
+/* Spin-down luminosity through the shell's coordinate surface r = r_L (Sec.
+ * IV.C.2; the sphere |x| = r_L unless shell_ks): L = closed integral of
+ * (E x B).n^ dA on the radial element layer containing r_L (xi^3
+ * interpolation, LGL quadrature, exact area element and outward normal).  *L_host receives L;
  * when grad_dev is not NULL, scale * dL/dU is added to it. */
 ffe_status ffe_luminosity(ffe_ctx* ctx, const double* U_dev, double r_L, double* L_host, double* grad_dev,
                           double scale);
@@ -390,8 +404,20 @@ ffe_status ffe_set_frozen_masks(ffe_ctx* ctx, int on);
  *                        sum is reduced on the device (deterministic).
  *   FFE_DIAG_LUMINOSITY  args[0] = r_L: out_host[0] = the luminosity of
  *                        ffe_luminosity through r = r_L (shells).
- *   FFE_DIAG_CONSTRAINTS out_host[0..3] as ffe_constraints (flat metric). */
-enum { FFE_DIAG_L2_ERR = 0, FFE_DIAG_LUMINOSITY = 1, FFE_DIAG_CONSTRAINTS = 2 };
+ *   FFE_DIAG_CONSTRAINTS out_host[0..3] as ffe_constraints (flat metric).
+ *   FFE_DIAG_BFLUX_UPPER args[0] = R: out_host[0] = the magnetic flux of B~
+ *                        through the upper half (z > 0) of the shell's
+ *                        coordinate surface of radius R (the sphere |x| = R;
+ *                        with shell_ks the spheroid of Kerr-Schild radius R, so
+ *                        R = r+ is the outer horizon itself), on the radial
+ *                        element layer containing R (xi^3 interpolation, LGL
+ *                        quadrature, exact area element and outward normal).
+ *                        B~ has zero coordinate divergence, so on a shell
+ *                        of spheres R = sqrt(r+^2 + a^2) gives the same flux
+ *                        (same equator), the quantity of Sec. IV.B.2.
+ *                        Shells with n[0] even
+ *                        (the equator on element boundaries), FFE_EINVAL else. */
+enum { FFE_DIAG_L2_ERR = 0, FFE_DIAG_LUMINOSITY = 1, FFE_DIAG_CONSTRAINTS = 2, FFE_DIAG_BFLUX_UPPER = 3 };
 ffe_status ffe_diagnostic(ffe_ctx* ctx, int kind, const double* args, double* out_host);
 
 /* Cartesian coordinates of the DG nodes [3][n_dg] and of the FD subcell

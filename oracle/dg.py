@@ -14,7 +14,7 @@ part.
 import numpy as np
 
 from . import physics as ph
-from .geometry import BC_DIRICHLET, BC_NO_INCOMING, BC_STAR, face_slice
+from .geometry import BC_DIRICHLET, BC_NO_INCOMING, BC_OUTFLOW, BC_STAR, face_slice
 from .ops import apply_3d, deriv
 
 DG, FD = 0, 1
@@ -105,6 +105,11 @@ def rhs_dg(st, disc, met, prm):
                 Ue[:, a] = ph.bc_no_incoming_poynting(Ui[:, a:a + 1], mfa, nhat[:, a:a + 1])[:, 0]
             elif kind == BC_STAR:
                 Ue[:, a] = ph.bc_star(Ui[:, a], disc.xyz[:, e][(slice(None),) + fs], prm["omega"])
+            elif kind == BC_OUTFLOW:
+                # [reading] an excision surface inside a horizon (Sec. IV.B.2: no
+                # condition imposed there): the exterior state is the interior one,
+                # so the Rusanov flux is the interior flux
+                Ue[:, a] = Ui[:, a]
             else:
                 raise ValueError("face without neighbour or boundary condition")
         jdi, jpi = ph.current(Ui, mf, prm["eta"])

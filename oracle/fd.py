@@ -16,7 +16,7 @@ import numpy as np
 
 from . import physics as ph
 from .dg import DG, FD, _met_at
-from .geometry import BC_DIRICHLET, BC_NO_INCOMING, BC_STAR, layer_slice, axis_of
+from .geometry import BC_DIRICHLET, BC_NO_INCOMING, BC_OUTFLOW, BC_STAR, layer_slice, axis_of
 from .ops import apply_3d
 
 NG = 3
@@ -227,6 +227,8 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
                         ext[tgt] = ph.bc_no_incoming_poynting(outer[:, None], mo, nrm[:, None])[:, 0]
                     elif kind == BC_STAR:
                         ext[tgt] = ph.bc_star(outer, disc.xyz_fd[:, e][(slice(None),) + lay], prm["omega"])
+                    elif kind == BC_OUTFLOW:
+                        ext[tgt] = outer
                     else:
                         raise ValueError("face without neighbour or boundary condition")
     return ext, xyz, jgh

@@ -13,7 +13,7 @@ fastest); face f = 2 d + s, d the reference direction (0: xi^1, 1: xi^2,
 """
 import numpy as np
 
-BC_NONE, BC_PERIODIC, BC_DIRICHLET, BC_NO_INCOMING, BC_STAR = 0, 1, 2, 3, 4
+BC_NONE, BC_PERIODIC, BC_DIRICHLET, BC_NO_INCOMING, BC_STAR, BC_OUTFLOW = 0, 1, 2, 3, 4, 5
 
 
 def axis_of(d):
@@ -216,9 +216,20 @@ class ShellMesh:
     r (sigma e_n + X e_t1 + Y e_t2) / sqrt(1 + X^2 + Y^2); elements split the
     logical cube uniformly.  Element e = ia + na (ib + na (ir + nr w)); the
     reference direction xi^3 is radial; face 4 of ir = 0 lies on r_in, face 5
-    of ir = nr-1 on r_out."""
+    of ir = nr-1 on r_out.
 
-    def __init__(self, r_in, r_out, n_ang, n_rad, bc_inner, bc_outer):
+    spin = a != 0: the shell of the black-hole tests lives in spherical
+    Kerr-Schild coordinates (App. B), so r is the Kerr-Schild radius and the
+    unit vector v = (sin th cos ph, sin th sin ph, cos th) of the cubed-sphere
+    map gives the Cartesian Kerr-Schild point by App. B's transformation,
+    x = (r cos ph - a sin ph) sin th, y = (r sin ph + a cos ph) sin th,
+    z = r cos th, i.e. x = r v + a (z^ x v).  Every surface r = const is then an
+    oblate spheroid (x^2 + y^2)/(r^2 + a^2) + z^2/r^2 = 1, so a boundary at
+    r_in between the two horizons lies wholly in the region that every
+    characteristic leaves."""
+
+    def __init__(self, r_in, r_out, n_ang, n_rad, bc_inner, bc_outer, spin=0.0):
+        self.spin = float(spin)
         self.r_in, self.r_out = float(r_in), float(r_out)
         self.na, self.nr = int(n_ang), int(n_rad)
         self.bc_inner, self.bc_outer = bc_inner, bc_outer
@@ -240,11 +251,14 @@ class ShellMesh:
         X, Y = np.tan(np.pi * ea / 4.0), np.tan(np.pi * eb / 4.0)
         r = self.r_in * (self.r_out / self.r_in) ** ((er + 1.0) / 2.0)
         rho = np.sqrt(1.0 + X * X + Y * Y)
-        out = [None, None, None]
-        out[n_ax] = sg * r / rho
-        out[t1] = r * X / rho
-        out[t2] = r * Y / rho
-        return np.stack(out)
+        v = [None, None, None]
+        v[n_ax] = sg / rho
+        v[t1] = X / rho
+        v[t2] = Y / rho
+        if self.spin == 0.0:
+            return np.stack([r * v[0], r * v[1], r * v[2]])
+        a = self.spin
+        return np.stack([r * v[0] - a * v[1], r * v[1] + a * v[0], r * v[2]])
 
     def inv_map(self, e, x):
         """xi(x) for element e, the map above inverted in closed form: in the
@@ -256,10 +270,22 @@ class ShellMesh:
         ia, ib, ir, w = self.eidx(e)
         n_ax, sg = WEDGES[w]
         t1, t2 = (n_ax + 1) % 3, (n_ax + 2) % 3
+        if self.spin != 0.0:
+            # undo App. B's transformation: r from the spheroid relation
+            # (x^2 + y^2)/(r^2 + a^2) + z^2/r^2 = 1 (the root with r^2 > 0), then
+            # (v_x, v_y) from [x; y] = [[r, -a], [a, r]] [v_x; v_y], v_z = z / r;
+            # r v has the direction of v, which is all the angular part needs
+            a = self.spin
+            R2 = x[0] ** 2 + x[1] ** 2 + x[2] ** 2
+            b = R2 - a * a
+            r = np.sqrt(0.5 * (b + np.sqrt(b * b + 4.0 * a * a * x[2] ** 2)))
+            q = 1.0 / (r * r + a * a)
+            x = np.stack([(r * x[0] + a * x[1]) * q * r, (r * x[1] - a * x[0]) * q * r, x[2]])
+        else:
+            r = np.sqrt(x[0] ** 2 + x[1] ** 2 + x[2] ** 2)
         xn = sg * x[n_ax]
         ea = 4.0 / np.pi * np.arctan(x[t1] / xn)
         eb = 4.0 / np.pi * np.arctan(x[t2] / xn)
-        r = np.sqrt(x[0] ** 2 + x[1] ** 2 + x[2] ** 2)
         er = 2.0 * np.log(r / self.r_in) / np.log(self.r_out / self.r_in) - 1.0
         xi0 = 2.0 * ((ea + 1.0) * self.na / 2.0 - ia) - 1.0
         xi1 = 2.0 * ((eb + 1.0) * self.na / 2.0 - ib) - 1.0

@@ -101,12 +101,13 @@ def _cs_grad(fn, xyz):
     return np.stack(out)
 
 
-def wald(xyz, M=1.0, a=0.9, B0=1.0):
+def wald(xyz, M=1.0, a=0.9, B0=1.0, e=1.0):
     """Wald's stationary vacuum field (Sec. IV.B.1): A_b = (B0/2)[(d_phi)_b + 2a (d_t)_b]
     with the Killing vectors d_t = (1,0,0,0) and d_phi = (0,-y,x,0) of the
     Kerr-Schild chart, F_ab = d_a A_b - d_b A_a (stationary: d_t A = 0),
     E^i = F^{ib} n_b = -alpha F^{i0}, B~^i = sqrt(gamma) B^i = [ijk] d_j A_k,
-    E~ = sqrt(gamma) E; q~ = 0 (vacuum)."""
+    E~ = sqrt(gamma) E; q~ = 0 (vacuum).  e multiplies E~ (e = 0: the vacuum
+    Wald problem's start, Wald's magnetic field with E~ = 0, Sec. IV.B.2)."""
     from .metric import ks_four_metric, adm_from_four
 
     def A(p):
@@ -128,7 +129,7 @@ def wald(xyz, M=1.0, a=0.9, B0=1.0):
     sqrtg = np.sqrt(np.linalg.det(np.moveaxis(gl, (0, 1), (-2, -1))))
     Fup0 = np.einsum('im...,n...,mn...->i...', gi[1:, :], gi[0, :], F)   # F^{i0}
     U = np.zeros((9,) + shape)
-    U[0:3] = -alpha * sqrtg * Fup0
+    U[0:3] = -e * alpha * sqrtg * Fup0
     U[3] = dA[1, 3] - dA[2, 2]
     U[4] = dA[2, 1] - dA[0, 3]
     U[5] = dA[0, 2] - dA[1, 1]

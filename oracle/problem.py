@@ -4,9 +4,11 @@ import numpy as np
 from . import initial, physics as ph
 from .metric import ks_metric
 from .basis import Tables
-from .geometry import BoxMesh, ShellMesh, Discretisation, BC_PERIODIC, BC_DIRICHLET, BC_NO_INCOMING, BC_STAR
+from .geometry import (BoxMesh, ShellMesh, Discretisation, BC_PERIODIC, BC_DIRICHLET, BC_NO_INCOMING, BC_STAR,
+                       BC_OUTFLOW)
 
-_BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "no_incoming": BC_NO_INCOMING, "star": BC_STAR}
+_BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "no_incoming": BC_NO_INCOMING, "star": BC_STAR,
+       "outflow": BC_OUTFLOW}
 
 
 class Problem:
@@ -17,8 +19,11 @@ class Problem:
         if cfg["kind"] == "box":
             self.mesh = BoxMesh(cfg["lo"], cfg["hi"], cfg["n"], [_BC[b] for b in cfg["bc"]])
         else:
+            # shell_ks: the shell's radius is the spherical Kerr-Schild r of the
+            # metric's spin (App. B)
+            spin = cfg["metric"][2] if cfg.get("shell_ks") else 0.0
             self.mesh = ShellMesh(cfg["r_in"], cfg["r_out"], cfg["n_ang"], cfg["n_rad"],
-                                  _BC[cfg["bc_inner"]], _BC[cfg["bc_outer"]])
+                                  _BC[cfg["bc_inner"]], _BC[cfg["bc_outer"]], spin=spin)
         self.disc = Discretisation(self.mesh, self.T, fd=bool(p["tci_on"]))
         mkind, M, spin = cfg["metric"]
         d = self.disc

@@ -30,6 +30,7 @@ __device__ __forceinline__ double* flux_at_c(const Dev& d, int k, int j, int v, 
 // shell map of element e (its instance's geometry and its index inside the instance)
 __device__ __forceinline__ ShellGeo shell_for(const Dev& d, int e, int& el) {
     ShellGeo g;
+    g.a = 0.0;   // FD subcells run on shells with x = r v only
     if (d.einst) {
         const InstInfo& in = d.inst[d.einst[e]];
         g.r_in = in.r_in;

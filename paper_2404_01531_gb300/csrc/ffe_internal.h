@@ -113,6 +113,8 @@ struct Dev {
     const int* gst;
     const double* gwf;
     const double* gwl;
+    const int* gbox;                // [slot][6]: first neighbour cell and extent of the stencils' box per axis
+    int gbox_max;                   // largest box volume (cells)
     double shell_rin, shell_c;
     int shell_na, shell_nr;
     // flat shells, per instance at InstInfo::tab (single context: 0), on the
@@ -148,8 +150,10 @@ struct Dev {
     double* ext;
     double* flux;
     // FD->DG face traces of FD elements for their DG neighbours, per FD slot
-    // [6][12][np1^2] (k_fd_traces; null: none)
+    // [6][12][np1^2] (k_fd_traces; null: none), and their adjoints in the
+    // reverse mode (written by the DG reverse kernel, allocated with the adjoint)
     double* ftr;
+    double* ftr_b;
 };
 
 // sizes of one element
@@ -187,6 +191,8 @@ void launch_fd_substep(const Dev& d, int sub, const int* list, int count_index, 
 int fd_chunks(const Dev& d);
 // FD->DG face traces of the listed FD elements for their DG neighbours (Dev::ftr)
 void launch_fd_traces(const Dev& d, Field U, Field J, cudaStream_t st);
+// out += the FD cells' share of the trace adjoints (Dev::ftr_b), reverse of k_fd_traces
+void launch_fd_traces_vjp(const Dev& d, Field U, Field out, cudaStream_t st);
 // extended blocks (U, J~ with ghosts) of the listed FD elements of one chunk
 void launch_fd_fill(const Dev& d, const int* list, int count_index, int w0, Field U, Field J, cudaStream_t st);
 void launch_eval_recip(const double* x, double* y, int64_t n, cudaStream_t st);
@@ -201,7 +207,7 @@ void launch_l2_err(const Dev& d, Field U, Field R, int v0, int nv, double* part,
 // out += (d RHS_FD/dU)^T L (kernels_adjoint_fd.cu); extb: scratch of the size of d.ext
 // FD elements per chunk of the FD reverse mode (its per-face buffer gb holds
 // [3][12][FDV_CHUNK][(nc+1) nc^2][6] doubles)
-constexpr int FDV_CHUNK = 256;
+constexpr int FDV_CHUNK = 1024;
 void launch_fd_rhs_vjp(const Dev& d, Field U, Field J, Field L, Field out, double* extb, double* gb,
                        double* omega_bar, cudaStream_t st);
 void launch_rollback_project(const Dev& d, int sub, Field un, Field Uin, Field F2, Field F3,
@@ -224,7 +230,7 @@ void launch_adj_addG(const Dev& d, Field U, Field Gb, Field io, cudaStream_t st)
 void launch_adj_clamp(const Dev& d, Field io, cudaStream_t st);
 void launch_adj_clamp_back(const Dev& d, Field X, Field yb, Field out, cudaStream_t st);
 void launch_luminosity(const Dev& d, Field U, const int* elem, const double* lk, const double* wn, int ns,
-                       double* partial, int nblocks, Field grad, double scale, cudaStream_t st);
+                       double* partial, int nblocks, Field grad, double scale, cudaStream_t st, int bflux = 0);
 
 extern thread_local int64_t g_launch_counter;
 

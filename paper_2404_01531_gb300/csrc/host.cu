@@ -210,6 +210,10 @@ void initial_point(int kind, const double* prm, int nprm, const double* X, doubl
         U[3] = 1.0 + eps * sin(M_PI * x);
     } else if (kind == FFE_ID_WALD) {
         wald_point(X, nprm > 0 ? prm[0] : 1.0, nprm > 1 ? prm[1] : 0.0, nprm > 2 ? prm[2] : 1.0, U);
+        // optional fourth parameter: a factor on E~ (0: the vacuum Wald problem's
+        // start, Wald's B~ with E~ = 0, Sec. IV.B.2)
+        if (nprm > 3)
+            for (int v = 0; v < 3; ++v) U[v] *= prm[3];
     } else if (kind == FFE_ID_DIPOLE) {
         dipole_point(X, nprm > 0 ? prm[0] : 1.0, nprm > 1 ? prm[1] : 0.1, nprm > 2 ? prm[2] : 0.0, U);
     } else if (kind == FFE_ID_FAST_WAVE_KINK) {
@@ -376,6 +380,12 @@ struct ffe_ctx {
     int* d_lum_elem = nullptr;
     double* d_lum_lk = nullptr;
     double* d_lum_w = nullptr;
+    // upper-hemisphere magnetic flux surface (cached per radius)
+    double flux_r = -1.0;
+    int flux_ns = 0;
+    int* d_flux_elem = nullptr;
+    double* d_flux_lk = nullptr;
+    double* d_flux_w = nullptr;
 };
 
 namespace {
@@ -687,8 +697,32 @@ ffe_status set_ginterp(ffe_ctx* c, const std::vector<int>& nbr) {
             }
         }
     });
-    int *d_sl, *d_st;
+    // per slot the box of neighbour cells its stencils cover (first cell and
+    // extent along each axis): the kernels stage it in shared memory
+    std::vector<int> box((size_t)ns * 6, 0);
+    int vmax = 0;
+    for (int sl = 0; sl < ns; ++sl) {
+        int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+        for (int t = 0; t < ghn; ++t)
+            for (int a = 0; a < 3; ++a) {
+                const int v = gst[((size_t)sl * ghn + t) * 3 + a];
+                lo[a] = v < lo[a] ? v : lo[a];
+                hi[a] = v > hi[a] ? v : hi[a];
+            }
+        int vol = 1;
+        for (int a = 0; a < 3; ++a) {
+            box[6 * sl + a] = lo[a];
+            box[6 * sl + 3 + a] = hi[a] + 6 - lo[a];
+            vol *= hi[a] + 6 - lo[a];
+        }
+        vmax = vol > vmax ? vol : vmax;
+    }
+    int *d_sl, *d_st, *d_box;
     double *d_wf, *d_wl;
+    if ((s = dalloc(c, &d_box, box.size()))) return s;
+    CK(cudaMemcpy(d_box, box.data(), box.size() * sizeof(int), cudaMemcpyHostToDevice));
+    d.gbox = d_box;
+    d.gbox_max = vmax;
     if ((s = dalloc(c, &d_sl, slot.size()))) return s;
     if ((s = dalloc(c, &d_st, gst.size()))) return s;
     if ((s = dalloc(c, &d_wf, gwf.size()))) return s;
@@ -1256,6 +1290,75 @@ ffe_status build_reference(ffe_ctx* c) {
     return FFE_OK;
 }
 
+
+// Surface quadrature on the shell's coordinate surface of radius r (the sphere
+// |x| = r; on a spherical Kerr-Schild shell the spheroid of Kerr-Schild radius
+// r) -- the luminosity of Sec. IV.C.2 and the horizon flux of Sec. IV.B.2: the
+// radial element layer that contains r, the Lagrange weights lk[np1] of xi^3
+// at r (closed-form inverse of the logarithmic radial map), and per surface
+// node (i, j) of each element of the layer the LGL weights times the exact
+// area element and the outward unit normal, wn[4] = (w_i w_j |a1 x a2|,
+// (a1 x a2)/|a1 x a2|), a_k = dx/dxi^k (on a sphere the normal is r^).  upper:
+// only the elements whose centre has z > 0 (the equator must then lie on
+// element boundaries).
+void surface_setup(ffe_ctx* c, double r, bool upper, std::vector<int>& elem, std::vector<double>& lk,
+                   std::vector<double>& wn) {
+    const Dev& d = c->d;
+    const ShellGeo g = c->shell;
+    const double er = std::log(r / g.r_in) / g.c - 1.0;
+    const double pos = (er + 1.0) / 2.0 * g.nr;
+    int ir = (int)std::floor(pos);
+    ir = ir > g.nr - 1 ? g.nr - 1 : ir;
+    const double xr = 2.0 * (pos - ir) - 1.0;
+    const int np1 = d.np1;
+    lk.assign(np1, 0.0);
+    for (int k = 0; k < np1; ++k) {
+        double v = 1.0;
+        for (int m = 0; m < np1; ++m)
+            if (m != k) v *= (xr - c->tab.x[m]) / (c->tab.x[k] - c->tab.x[m]);
+        lk[k] = v;
+    }
+    for (int e = 0; e < d.E; ++e) {
+        int ia, ib, irr, w;
+        shell_elem(g, e, ia, ib, irr, w);
+        if (irr != ir) continue;
+        if (upper) {
+            const double xi0[3] = {0.0, 0.0, xr};
+            double x0[3], ij0[3][3];
+            shell_map(g, e, xi0, x0, ij0);
+            if (!(x0[2] > 0.0)) continue;
+        }
+        elem.push_back(e);
+        for (int j = 0; j < np1; ++j)
+            for (int i = 0; i < np1; ++i) {
+                const double xi[3] = {c->tab.x[i], c->tab.x[j], xr};
+                double x[3], ij[3][3];
+                shell_map(g, e, xi, x, ij);
+                // area element |dx/dxi1 x dx/dxi2| from the Jacobian (inverse of ij)
+                double J[3][3];
+                const double det = ij[0][0] * (ij[1][1] * ij[2][2] - ij[1][2] * ij[2][1]) -
+                                   ij[0][1] * (ij[1][0] * ij[2][2] - ij[1][2] * ij[2][0]) +
+                                   ij[0][2] * (ij[1][0] * ij[2][1] - ij[1][1] * ij[2][0]);
+                J[0][0] = (ij[1][1] * ij[2][2] - ij[1][2] * ij[2][1]) / det;
+                J[0][1] = (ij[0][2] * ij[2][1] - ij[0][1] * ij[2][2]) / det;
+                J[1][0] = (ij[1][2] * ij[2][0] - ij[1][0] * ij[2][2]) / det;
+                J[1][1] = (ij[0][0] * ij[2][2] - ij[0][2] * ij[2][0]) / det;
+                J[2][0] = (ij[1][0] * ij[2][1] - ij[1][1] * ij[2][0]) / det;
+                J[2][1] = (ij[0][1] * ij[2][0] - ij[0][0] * ij[2][1]) / det;
+                const double a1[3] = {J[0][0], J[1][0], J[2][0]}, a2[3] = {J[0][1], J[1][1], J[2][1]};
+                const double cr[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
+                // a1 x a2 points to increasing xi^3 (outward) where the map keeps
+                // orientation (det > 0); flip it otherwise
+                const double area = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+                const double sg = det > 0.0 ? 1.0 : -1.0;
+                wn.push_back(c->tab.w[i] * c->tab.w[j] * area);
+                wn.push_back(sg * cr[0] / area);
+                wn.push_back(sg * cr[1] / area);
+                wn.push_back(sg * cr[2] / area);
+            }
+    }
+}
+
 }  // namespace
 
 
@@ -1470,6 +1573,39 @@ ffe_status ffe_diagnostic(ffe_ctx* c, int kind, const double* args, double* out_
     if (!c || !out_host) return fail(FFE_EINVAL, "null argument");
     const Dev& d = c->d;
     if (kind == FFE_DIAG_CONSTRAINTS) return ffe_constraints(c, nullptr, out_host);
+    if (kind == FFE_DIAG_BFLUX_UPPER) {
+        if (!args) return fail(FFE_EINVAL, "the flux needs args[0] = R");
+        const double R = args[0];
+        if (!d.curved || c->batch || c->dom.kind != FFE_DOMAIN_SHELL6) return fail(FFE_ENOTIMPL, "the flux needs a shell");
+        if (!(R > c->dom.r_in && R < c->dom.r_out)) return fail(FFE_EINVAL, "R outside the shell");
+        if (c->shell.na % 2) return fail(FFE_EINVAL, "the equator lies on element boundaries only for even n_ang");
+        ffe_status s;
+        if (c->flux_r != R) {
+            std::vector<int> elem;
+            std::vector<double> lk, wn;
+            surface_setup(c, R, true, elem, lk, wn);
+            if ((s = dalloc(c, &c->d_flux_elem, elem.size()))) return s;
+            if ((s = dalloc(c, &c->d_flux_lk, lk.size()))) return s;
+            if ((s = dalloc(c, &c->d_flux_w, wn.size()))) return s;
+            CK(cudaMemcpy(c->d_flux_elem, elem.data(), elem.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->d_flux_lk, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->d_flux_w, wn.data(), wn.size() * 8, cudaMemcpyHostToDevice));
+            c->flux_ns = (int)elem.size();
+            c->flux_r = R;
+        }
+        if (!c->d_partial && (s = dalloc(c, &c->d_partial, 1024))) return s;
+        const int nb = d.nsm;
+        Field U{c->un.p, NV, d.ndg, d.nfd}, G{nullptr, NV, d.ndg, d.nfd};
+        launch_luminosity(d, U, c->d_flux_elem, c->d_flux_lk, c->d_flux_w, c->flux_ns, c->d_partial, nb, G, 0.0,
+                          c->st, 1);
+        std::vector<double> part(nb);
+        CK(cudaMemcpyAsync(part.data(), c->d_partial, nb * 8, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        double sum = 0.0;
+        for (double v : part) sum += v;
+        out_host[0] = sum;
+        return FFE_OK;
+    }
     if (kind == FFE_DIAG_LUMINOSITY) {
         if (!args) return fail(FFE_EINVAL, "the luminosity needs args[0] = r_L");
         return ffe_luminosity(c, c->un.p, args[0], out_host, nullptr, 0.0);
@@ -1615,18 +1751,25 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
         if (!(metric->M > 0) || !(fabs(metric->a) < 1)) return fail(FFE_EINVAL, "need M > 0 and |a| < 1");
         if (P < 3 || P > 5) return fail(FFE_EINVAL, "curved elements support 3 <= P <= 5");
     }
+    if (domain->shell_ks != 0) {
+        if (domain->shell_ks != 1) return fail(FFE_EINVAL, "shell_ks = %d (0 or 1)", domain->shell_ks);
+        if (domain->kind != FFE_DOMAIN_SHELL6 || metric->kind != FFE_METRIC_KERR_SCHILD)
+            return fail(FFE_EINVAL, "shell_ks needs a shell on the Kerr-Schild metric");
+        if (params->tci_on)
+            return fail(FFE_ENOTIMPL, "FD subcells are not built for the spherical Kerr-Schild shell (tci_on = 0)");
+    }
     if (domain->kind == FFE_DOMAIN_SHELL6) {
         if (!(domain->r_in > 0) || !(domain->r_out > domain->r_in)) return fail(FFE_EINVAL, "need 0 < r_in < r_out");
         if (elements->n[0] < 1 || elements->n[2] < 1) return fail(FFE_EINVAL, "shell needs n[0], n[2] >= 1");
         if (P < 3 || P > 5) return fail(FFE_EINVAL, "curved elements support 3 <= P <= 5");
         for (int k : {domain->bc_lo[0], domain->bc_hi[0]})
-            if (k < FFE_BC_DIRICHLET || k > FFE_BC_STAR) return fail(FFE_EINVAL, "shell boundary kind %d", k);
+            if (k < FFE_BC_DIRICHLET || k > FFE_BC_OUTFLOW) return fail(FFE_EINVAL, "shell boundary kind %d", k);
     }
     for (int dd = 0; dd < 3 && domain->kind == FFE_DOMAIN_BOX; ++dd) {
         if (elements->n[dd] < 1) return fail(FFE_EINVAL, "elements n[%d] = %d", dd, elements->n[dd]);
         if (!(domain->hi[dd] > domain->lo[dd])) return fail(FFE_EINVAL, "empty box along axis %d", dd);
         for (int k : {domain->bc_lo[dd], domain->bc_hi[dd]})
-            if (k < FFE_BC_PERIODIC || k > FFE_BC_STAR) return fail(FFE_EINVAL, "boundary kind %d", k);
+            if (k < FFE_BC_PERIODIC || k > FFE_BC_OUTFLOW) return fail(FFE_EINVAL, "boundary kind %d", k);
         if ((domain->bc_lo[dd] == FFE_BC_PERIODIC) != (domain->bc_hi[dd] == FFE_BC_PERIODIC))
             return fail(FFE_EINVAL, "periodic axis %d needs periodic at both ends", dd);
     }
@@ -1661,6 +1804,7 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
         c->shell.c = 0.5 * log(domain->r_out / domain->r_in);
         c->shell.na = elements->n[0];
         c->shell.nr = elements->n[2];
+        c->shell.a = domain->shell_ks ? metric->a : 0.0;
         d.E = 6 * elements->n[0] * elements->n[0] * elements->n[2];
     } else {
         c->nx = elements->n[0];
@@ -1719,11 +1863,12 @@ ffe_status ffe_create_batch(int n_inst, const ffe_domain* doms, const ffe_elemen
         ffe_status st0;
         if ((st0 = check_scheme(pi, who))) return st0;
         if (dm.kind != FFE_DOMAIN_SHELL6) return fail(FFE_EINVAL, "instance %d: batched instances are shells", i);
+        if (dm.shell_ks) return fail(FFE_EINVAL, "instance %d: shell_ks needs the Kerr-Schild metric", i);
         if (!(dm.r_in > 0) || !(dm.r_out > dm.r_in)) return fail(FFE_EINVAL, "instance %d: need 0 < r_in < r_out", i);
         if (els[i].n[0] < 1 || els[i].n[2] < 1) return fail(FFE_EINVAL, "instance %d: element counts", i);
         if (Ps[i] < 3 || Ps[i] > 5) return fail(FFE_EINVAL, "instance %d: order %d outside [3, 5]", i, Ps[i]);
         for (int k : {dm.bc_lo[0], dm.bc_hi[0]})
-            if (k < FFE_BC_DIRICHLET || k > FFE_BC_STAR) return fail(FFE_EINVAL, "instance %d: boundary kind %d", i, k);
+            if (k < FFE_BC_DIRICHLET || k > FFE_BC_OUTFLOW) return fail(FFE_EINVAL, "instance %d: boundary kind %d", i, k);
         if (pi.eta != p0.eta || pi.kappa_psi != p0.kappa_psi || pi.kappa_phi != p0.kappa_phi ||
             pi.filter_on != p0.filter_on || pi.filter_a != p0.filter_a || pi.filter_b != p0.filter_b ||
             pi.tci_on != p0.tci_on || pi.tci_M != p0.tci_M || pi.tci_alpha != p0.tci_alpha ||
@@ -2154,6 +2299,8 @@ ffe_status ffe_freeze_mask(ffe_ctx* c, int on) try {
 static ffe_status adjoint_ready(ffe_ctx* c) {
     const Dev& d = c->d;
     if (!d.curved || d.ks || c->batch) return fail(FFE_ENOTIMPL, "the adjoint is built for flat-metric shells");
+    if (c->dom.bc_lo[0] == FFE_BC_OUTFLOW || c->dom.bc_hi[0] == FFE_BC_OUTFLOW)
+        return fail(FFE_ENOTIMPL, "the adjoint is not built for outflow boundaries");
     if (d.recon != FFE_RECON_WENO5Z) return fail(FFE_ENOTIMPL, "the adjoint is built for WENO5-Z reconstruction");
     if (d.tci_on) return fail(FFE_ESTATE, "the adjoint differentiates a fixed mask: freeze it first (ffe_freeze_mask)");
     std::vector<unsigned char> m(d.E);
@@ -2173,6 +2320,7 @@ static ffe_status adjoint_ready(ffe_ctx* c) {
     if ((s = dalloc(c, &c->d_partial, 1024))) return s;
     const size_t ne = (size_t)d.nc + 2 * GH;
     if ((s = dalloc(c, &c->d_extb, (size_t)12 * d.chunk * ne * ne * ne))) return s;
+    if ((s = dalloc(c, &c->d.ftr_b, (size_t)d.fd_cap * 6 * 12 * d.np1 * d.np1))) return s;
     const size_t fch = (size_t)(d.chunk < FDV_CHUNK ? d.chunk : FDV_CHUNK);
     if ((s = dalloc(c, &c->d_gbuf, (size_t)3 * 12 * fch * (d.nc + 1) * d.nc * d.nc * 6))) return s;
     c->adj_ready = true;
@@ -2210,6 +2358,7 @@ static void rhs_vjp_at(ffe_ctx* c, Field U, Field L, Field out) {
     cudaMemsetAsync(out.fd(0), 0, (size_t)NV * d.nfd * sizeof(double), c->st);
     launch_rhs_vjp(d, U, L, out, c->d_omega_bar, c->st);
     if (c->adj_fd) {
+        launch_fd_traces_vjp(d, U, out, c->st);
         launch_current(d, U, c->J, nullptr, 0, c->st);
         launch_fd_rhs_vjp(d, U, c->J, L, out, c->d_extb, c->d_gbuf, c->d_omega_bar, c->st);
     }
@@ -2379,59 +2528,9 @@ ffe_status ffe_luminosity(ffe_ctx* c, const double* U_dev, double r_L, double* L
     if (!(r_L > c->dom.r_in && r_L < c->dom.r_out)) return fail(FFE_EINVAL, "r_L outside the shell");
     ffe_status s;
     if (c->lum_r != r_L) {
-        // surface layer, interpolation weights and quadrature weights (host)
-        const ShellGeo g = c->shell;
-        const double er = std::log(r_L / g.r_in) / g.c - 1.0;
-        const double pos = (er + 1.0) / 2.0 * g.nr;
-        int ir = (int)std::floor(pos);
-        ir = ir > g.nr - 1 ? g.nr - 1 : ir;
-        const double xr = 2.0 * (pos - ir) - 1.0;
-        const int np1 = d.np1, nf = np1 * np1;
-        std::vector<double> lk(np1);
-        for (int k = 0; k < np1; ++k) {
-            double v = 1.0;
-            for (int m = 0; m < np1; ++m)
-                if (m != k) v *= (xr - c->tab.x[m]) / (c->tab.x[k] - c->tab.x[m]);
-            lk[k] = v;
-        }
         std::vector<int> elem;
-        std::vector<double> wn;
-        for (int e = 0; e < d.E; ++e) {
-            int ia, ib, irr, w;
-            shell_elem(g, e, ia, ib, irr, w);
-            if (irr != ir) continue;
-            elem.push_back(e);
-            for (int j = 0; j < np1; ++j)
-                for (int i = 0; i < np1; ++i) {
-                    const double xi[3] = {c->tab.x[i], c->tab.x[j], xr};
-                    double x[3], ij[3][3];
-                    shell_map(g, e, xi, x, ij);
-                    // area element |dx/dxi1 x dx/dxi2| from the Jacobian (inverse of ij)
-                    double J[3][3];
-                    const double det = ij[0][0] * (ij[1][1] * ij[2][2] - ij[1][2] * ij[2][1]) -
-                                       ij[0][1] * (ij[1][0] * ij[2][2] - ij[1][2] * ij[2][0]) +
-                                       ij[0][2] * (ij[1][0] * ij[2][1] - ij[1][1] * ij[2][0]);
-                    J[0][0] = (ij[1][1] * ij[2][2] - ij[1][2] * ij[2][1]) / det;
-                    J[0][1] = (ij[0][2] * ij[2][1] - ij[0][1] * ij[2][2]) / det;
-                    J[0][2] = (ij[0][1] * ij[1][2] - ij[0][2] * ij[1][1]) / det;
-                    J[1][0] = (ij[1][2] * ij[2][0] - ij[1][0] * ij[2][2]) / det;
-                    J[1][1] = (ij[0][0] * ij[2][2] - ij[0][2] * ij[2][0]) / det;
-                    J[1][2] = (ij[0][2] * ij[1][0] - ij[0][0] * ij[1][2]) / det;
-                    J[2][0] = (ij[1][0] * ij[2][1] - ij[1][1] * ij[2][0]) / det;
-                    J[2][1] = (ij[0][1] * ij[2][0] - ij[0][0] * ij[2][1]) / det;
-                    J[2][2] = (ij[0][0] * ij[1][1] - ij[0][1] * ij[1][0]) / det;
-                    const double a1[3] = {J[0][0], J[1][0], J[2][0]}, a2[3] = {J[0][1], J[1][1], J[2][1]};
-                    const double cr[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
-                    const double rr = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-                    const double rh[3] = {x[0] / rr, x[1] / rr, x[2] / rr};
-                    const double area = std::fabs(cr[0] * rh[0] + cr[1] * rh[1] + cr[2] * rh[2]);
-                    wn.push_back(c->tab.w[i] * c->tab.w[j] * area);
-                    wn.push_back(rh[0]);
-                    wn.push_back(rh[1]);
-                    wn.push_back(rh[2]);
-                }
-        }
-        (void)nf;
+        std::vector<double> lk, wn;
+        surface_setup(c, r_L, false, elem, lk, wn);
         if ((s = dalloc(c, &c->d_lum_elem, elem.size()))) return s;
         if ((s = dalloc(c, &c->d_lum_lk, lk.size()))) return s;
         if ((s = dalloc(c, &c->d_lum_w, wn.size()))) return s;

@@ -196,24 +196,15 @@ __global__ void __launch_bounds__(AVJ<P>::NT) k_rhs_vjp(Dev d, Field U, Field L,
                 cn[d2] = s2 ? P : 0;
                 cn[u1] = a2;
                 cn[u2] = b2;
-                const int nc = T.nc;
-                const int lo0 = T.f2d_lo[cn[0]], lo1 = T.f2d_lo[cn[1]], lo2 = T.f2d_lo[cn[2]];
-                const int64_t base = fdb(d, nb);
+                // the exterior current is the projection of the cells' J~(U): (dC/d(Ue, Je))^T lambda;
+                // the adjoint of the trace node goes to the neighbour's trace adjoint (one
+                // writer per node), k_fd_traces_vjp takes it back to the cells
                 double z[NV], zJ[3];
-                // the exterior current is the projection of the cells' J~(U): (dC/d(Ue, Je))^T lambda
                 lift_ext_tJ(n, sc, lm, z, zJ);   // dU -= C
-                for (int n2 = 0; n2 < 6; ++n2)
-                    for (int n1 = 0; n1 < 6; ++n1)
-                        for (int n0 = 0; n0 < 6; ++n0) {
-                            const double wgt = T.F2D[cn[0]][lo0 + n0] * T.F2D[cn[1]][lo1 + n1] * T.F2D[cn[2]][lo2 + n2];
-                            const int64_t cell = base + (lo0 + n0) + nc * ((lo1 + n1) + nc * (lo2 + n2));
-                            double uc[NV], ub[NV], jb[3];
-                            for (int v = 0; v < NV; ++v) { uc[v] = U.fd(v)[cell]; ub[v] = -wgt * z[v]; }
-                            for (int k = 0; k < 3; ++k) jb[k] = -wgt * zJ[k];
-                            current_vjp(uc, d.eta, jb, jb, ub);
-                            for (int v = 0; v < NV; ++v)
-                                if (ub[v] != 0.0) atomicAdd(out.fd(v) + cell, ub[v]);
-                        }
+                const int nfm = d.np1 * d.np1;
+                double* tb = d.ftr_b + ((int64_t)fd_slot_of(d, nb) * 6 + f2) * 12 * nfm + cn[u1] + np1 * cn[u2];
+                for (int v = 0; v < NV; ++v) tb[v * nfm] = -z[v];
+                for (int k = 0; k < 3; ++k) tb[(NV + k) * nfm] = -zJ[k];
             } else {
                 // (c) the neighbour's lift term at its node used my U as its exterior state
                 const int f2 = d.nbr_face[e * 6 + f], d2 = f2 >> 1, s2 = f2 & 1;
@@ -639,6 +630,7 @@ struct LumArgs {
     const double* lk;       // [np1] interpolation weights along xi^3
     const double* wn;       // [ns][np1^2][4]: weight, rhat (3) at (i, j)
     int ns;
+    int bflux;              // 1: integrate B~.rhat (magnetic flux) instead of (E x B).rhat
 };
 
 __global__ void k_luminosity(Dev d, Field U, LumArgs la, double* out, Field grad, double scale) {
@@ -681,8 +673,8 @@ __global__ void k_luminosity(Dev d, Field U, LumArgs la, double* out, Field grad
         const double* w = la.wn + ((int64_t)s * nf + ij) * 4;
         const double r[3] = {w[1], w[2], w[3]};
         const double S[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
-        acc = fma(w[0], dot3(S, r), acc);
-        if (grad.p) {
+        acc = fma(w[0], la.bflux ? dot3(B, r) : dot3(S, r), acc);
+        if (grad.p && !la.bflux) {
             // d/dE = W (B x r), d/dB = W (r x E), spread with l_k
             const double gE[3] = {B[1] * r[2] - B[2] * r[1], B[2] * r[0] - B[0] * r[2], B[0] * r[1] - B[1] * r[0]};
             const double gB[3] = {r[1] * E[2] - r[2] * E[1], r[2] * E[0] - r[0] * E[2], r[0] * E[1] - r[1] * E[0]};
@@ -720,8 +712,8 @@ __global__ void k_luminosity(Dev d, Field U, LumArgs la, double* out, Field grad
 }
 
 void launch_luminosity(const Dev& d, Field U, const int* elem, const double* lk, const double* wn, int ns,
-                       double* partial, int nblocks, Field grad, double scale, cudaStream_t st) {
-    LumArgs la{elem, lk, wn, ns};
+                       double* partial, int nblocks, Field grad, double scale, cudaStream_t st, int bflux) {
+    LumArgs la{elem, lk, wn, ns, bflux};
     k_luminosity<<<nblocks, 256, 0, st>>>(d, U, la, partial, grad, scale);
     g_launch_counter += 1;
 }

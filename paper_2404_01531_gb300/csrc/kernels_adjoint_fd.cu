@@ -347,6 +347,91 @@ __global__ void k_fdv_ghosts(Dev d, const int* list, int ci, int w0, Field U, Fi
     }
 }
 
+// Reverse of k_fd_traces: the adjoints the DG reverse mode left at the trace
+// nodes of FD faces with a DG neighbour (Dev::ftr_b, [slot][6][12][np1^2]) go
+// back through the transposed sum-factorised FD->DG projection -- the two
+// tangential directions, then the normal one -- to the 6 cell layers next to
+// the face, and through J~(U) at each of those cells, into out.  One CTA per
+// (element, face); cells shared by two faces of one element or reached by the
+// other FD terms meet in out through FP64 atomics.
+__global__ void k_fd_traces_vjp(Dev d, Field U, Field out) {
+    extern __shared__ double sm[];
+    const int n = d.counts[1];
+    const int nfm = d.np1 * d.np1;
+    for (int item = blockIdx.x; item < n * 6; item += gridDim.x) {
+        const int w = item / 6, f = item % 6;
+        const int e = d.fd_list[w];
+        const int nb = d.nbr[e * 6 + f];
+        if (nb < 0 || d.mask[nb] != 0) continue;
+        const ES es = esz(d, e);
+        const int np1 = es.np1, nc = es.nc, nc2 = nc * nc;
+        const Tables& T = d.tabs[es.P];
+        const int dd = f >> 1;
+        int t1, t2;
+        axes_of(dd, t1, t2);
+        const int cn = (f & 1) ? es.P : 0;
+        const int lo = T.f2d_lo[cn];
+        double* Ob = sm;                          // [12][np1 (t2)][np1 (t1)]
+        double* Bb = Ob + NQ * np1 * np1;         // [12][nc (t2)][np1 (t1)]
+        double* Ab = Bb + NQ * nc * np1;          // [12][nc (t2)][nc (t1)]
+        const double* src = d.ftr_b + ((int64_t)fd_slot_of(d, e) * 6 + f) * NQ * nfm;
+        for (int t = threadIdx.x; t < NQ * np1 * np1; t += blockDim.x) {
+            const int q = t / (np1 * np1), r = t % (np1 * np1);
+            Ob[t] = src[q * nfm + r];
+        }
+        __syncthreads();
+        // t2 direction: Bb[q][b][i] = sum_j F2D[j][b] Ob[q][j][i] (F2D is zero off the stencils)
+        for (int t = threadIdx.x; t < NQ * nc * np1; t += blockDim.x) {
+            const int q = t / (nc * np1), r = t % (nc * np1);
+            const int b = r / np1, i = r % np1;
+            double acc = 0.0;
+            for (int j = 0; j < np1; ++j) acc = fma(T.F2D[j][b], Ob[(q * np1 + j) * np1 + i], acc);
+            Bb[t] = acc;
+        }
+        __syncthreads();
+        // t1 direction: Ab[q][b][a] = sum_i F2D[i][a] Bb[q][b][i]
+        for (int t = threadIdx.x; t < NQ * nc2; t += blockDim.x) {
+            const int q = t / nc2, r = t % nc2;
+            const int b = r / nc, a = r % nc;
+            double acc = 0.0;
+            for (int i = 0; i < np1; ++i) acc = fma(T.F2D[i][a], Bb[(q * nc + b) * np1 + i], acc);
+            Ab[t] = acc;
+        }
+        __syncthreads();
+        // normal direction and the current's chain rule, per cell of the 6 layers
+        const int64_t base = fdb(d, e);
+        for (int t = threadIdx.x; t < 6 * nc2; t += blockDim.x) {
+            const int m = t / nc2, r = t % nc2;
+            const double wn = T.F2D[cn][lo + m];
+            int c[3];
+            c[dd] = lo + m;
+            c[t1] = r % nc;
+            c[t2] = r / nc;
+            const int64_t p = base + c[0] + nc * (c[1] + nc * c[2]);
+            double u[NV], ub[NV], jb[3];
+            for (int v = 0; v < NV; ++v) {
+                u[v] = U.fd(v)[p];
+                ub[v] = wn * Ab[v * nc2 + r];
+            }
+            for (int k = 0; k < 3; ++k) jb[k] = wn * Ab[(NV + k) * nc2 + r];
+            current_vjp(u, d.eta, jb, jb, ub);
+            for (int v = 0; v < NV; ++v)
+                if (ub[v] != 0.0) atomicAdd(out.fd(v) + p, ub[v]);
+        }
+        __syncthreads();
+    }
+}
+
+void launch_fd_traces_vjp(const Dev& d, Field U, Field out, cudaStream_t st) {
+    if (!d.ftr_b) return;
+    const size_t smem = (size_t)(NQ * d.np1 * d.np1 + NQ * d.nc * d.np1 + NQ * d.nc * d.nc) * sizeof(double);
+    cudaFuncSetAttribute(k_fd_traces_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prof_begin("fd_traces_vjp", st);
+    k_fd_traces_vjp<<<d.nsm * 2, 256, smem, st>>>(d, U, out);
+    prof_end(st);
+    g_launch_counter += 1;
+}
+
 // out (FD block) must be zeroed and the DG right-hand-side adjoint already
 // written by the caller; J holds J~(U) at the FD cells (launch_current).
 void launch_fd_rhs_vjp(const Dev& dc, Field U, Field J, Field L, Field out, double* extb, double* gb,

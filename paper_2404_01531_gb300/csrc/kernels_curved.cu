@@ -247,7 +247,10 @@ __device__ __forceinline__ void dg_curved_elem(const Dev& d, const SubArgs& a, i
                     const double* src = d.bdg + (int64_t)d.bface[e * 6 + f] * NV * nf;
                     for (int v = 0; v < NV; ++v) Ue[v] = src[v * nf + ta + np1 * tb];
                 } else if (kind == FFE_BC_NO_INCOMING) {
-                    bc_no_incoming_flat(Ui, nl, Ue);
+                    if (KS) bc_no_incoming_gen(Ui, mf, nl, Ue);
+                    else bc_no_incoming_flat(Ui, nl, Ue);
+                } else if (kind == FFE_BC_OUTFLOW) {
+                    for (int v = 0; v < NV; ++v) Ue[v] = Ui[v];
                 } else {
                     double xn[3];
                     for (int q = 0; q < 3; ++q) xn[q] = d.xyz_dg[(int64_t)q * d.ndg + p];

@@ -237,6 +237,8 @@ __device__ void dg_external_state(const Dev& d, const SubArgs& a, int e, int f, 
         double n[3] = {0.0, 0.0, 0.0};
         n[dd] = s ? 1.0 : -1.0;
         bc_no_incoming_flat(Ui, n, Ue);
+    } else if (kind == FFE_BC_OUTFLOW) {
+        for (int v = 0; v < NV; ++v) Ue[v] = Ui[v];
     } else {
         bc_star_flat(Ui, xnode, d.omega, Ue);
     }

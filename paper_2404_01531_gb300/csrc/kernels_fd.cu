@@ -165,6 +165,8 @@ __global__ void k_fd_fill_ghosts(Dev d, const int* list, int ci, int w0, Field U
                                 for (int q = 0; q < 3; ++q) nrm[q] = -nrm[q];
                         }
                         bc_no_incoming_flat(ui, nrm, u);
+                    } else if (kind == FFE_BC_OUTFLOW) {
+                        for (int v = 0; v < NV; ++v) u[v] = ui[v];
                     } else {
                         double x[3];
                         if (d.curved) {

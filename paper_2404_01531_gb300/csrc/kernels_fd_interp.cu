@@ -49,7 +49,8 @@ __device__ __forceinline__ int64_t ghost_off(int dd, int s, int nc, int g, int t
 }  // namespace
 
 // One CTA per (chunk position, face between wedges); other faces are left to
-// k_fd_fill_ghosts.  Dynamic shared memory: a DG neighbour's U and J~ [12][nn].
+// k_fd_fill_ghosts.  Dynamic shared memory: a DG neighbour's U and J~ [12][nn],
+// or the box of an FD neighbour's cells that the face's stencils reach [9][box].
 __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, Field U, Field J) {
     const int n = chunk_n(d, ci, w0);
     extern __shared__ double su[];
@@ -62,37 +63,61 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
         const int nc = es.nc, np1 = es.np1, nn = es.nn;
         const int dd = f >> 1, s = f & 1;
         const bool fdnb = d.mask[nb] == 1;
+        const int nper = GH * nc * nc, ghn = GH * d.nc * d.nc;
+        const int sl = d.gislot[e * 6 + f];
+        const int* bx = d.gbox + 6 * sl;   // the neighbour cells the stencils reach
+        const int bx0 = bx[3], bxy = bx[3] * bx[4], bvol = bx[3] * bx[4] * bx[5];
         if (!fdnb) {
             for (int t = threadIdx.x; t < NQ * nn; t += blockDim.x) {
                 const int qv = t / nn;
                 const int64_t pn = (int64_t)nb * d.nn + t % nn;
                 su[t] = qv < NV ? U.dg(qv)[pn] : J.dg(3 + qv - NV)[pn];
             }
-            __syncthreads();
+        } else {
+            const int64_t base = fdb(d, nb);
+            for (int t = threadIdx.x; t < NV * bvol; t += blockDim.x) {
+                const int v = t / bvol, r = t % bvol;
+                const int cx = bx[0] + r % bx0, cy = bx[1] + (r / bx0) % bx[4], cz = bx[2] + r / bxy;
+                su[t] = U.fd(v)[base + cx + (int64_t)nc * (cy + (int64_t)nc * cz)];
+            }
         }
-        const int nper = GH * nc * nc, ghn = GH * d.nc * d.nc;
-        const int sl = d.gislot[e * 6 + f];
-        for (int t = threadIdx.x; t < nper; t += blockDim.x) {
-            const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
-            const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
-            const int64_t gi = (int64_t)sl * ghn + t;
-            if (fdnb) {
+        __syncthreads();
+        if (fdnb) {
+            // one thread per (ghost, group of three variables): 216 FMAs per variable
+            for (int it = threadIdx.x; it < 3 * nper; it += blockDim.x) {
+                const int t = it / 3, grp = it % 3;
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
+                const int64_t gi = (int64_t)sl * ghn + t;
                 const int* st3 = d.gst + gi * 3;
-                const double* wf = d.gwf + gi * 18;
-                const int sa = st3[0], sb = st3[1], sc = st3[2];
-                const int64_t base = fdb(d, nb);
-                double u[NV];
-                for (int v = 0; v < NV; ++v) u[v] = 0.0;
+                double wf[18];
+                for (int m = 0; m < 18; ++m) wf[m] = d.gwf[gi * 18 + m];
+                const int sa = st3[0] - bx[0], sb = st3[1] - bx[1], sc = st3[2] - bx[2];
+                const double* s0 = su + (3 * grp) * bvol;
+                double u0 = 0.0, u1 = 0.0, u2 = 0.0;
                 for (int cz = 0; cz < 6; ++cz)
                     for (int cy = 0; cy < 6; ++cy) {
                         const double wzy = wf[12 + cz] * wf[6 + cy];
-                        const int64_t row = base + sa + (int64_t)nc * ((sb + cy) + (int64_t)nc * (sc + cz));
+                        const int row = sa + bx0 * (sb + cy) + bxy * (sc + cz);
+#pragma unroll
                         for (int cx = 0; cx < 6; ++cx) {
                             const double w = wzy * wf[cx];
-                            for (int v = 0; v < NV; ++v) u[v] = fma(w, U.fd(v)[row + cx], u[v]);
+                            u0 = fma(w, s0[row + cx], u0);
+                            u1 = fma(w, s0[bvol + row + cx], u1);
+                            u2 = fma(w, s0[2 * bvol + row + cx], u2);
                         }
                     }
-                double jd[3], jf[3];
+                ext_at(d, 3 * grp, wl)[og] = u0;
+                ext_at(d, 3 * grp + 1, wl)[og] = u1;
+                ext_at(d, 3 * grp + 2, wl)[og] = u2;
+            }
+            __syncthreads();
+            // the ghost current: J~ of the interpolated state (metric at the ghost centre)
+            for (int t = threadIdx.x; t < nper; t += blockDim.x) {
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
+                double u[NV], jd[3], jf[3];
+                for (int v = 0; v < NV; ++v) u[v] = ext_at(d, v, wl)[og];
                 if (d.ks) {
                     PM m;
                     load_pm(d.metgi + (int64_t)sl * NPM * GH * d.nc * d.nc, (int64_t)GH * d.nc * d.nc,
@@ -101,9 +126,13 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
                 } else {
                     current_flat(u, d.eta, jd, jf);
                 }
-                for (int v = 0; v < NV; ++v) ext_at(d, v, wl)[og] = u[v];
                 for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = jf[k];
-            } else {
+            }
+        } else {
+            for (int t = threadIdx.x; t < nper; t += blockDim.x) {
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
+                const int64_t gi = (int64_t)sl * ghn + t;
                 const double* la = d.gwl + gi * 3 * MAXNP;
                 const double* lb = la + MAXNP;
                 const double* lc = lb + MAXNP;
@@ -127,26 +156,35 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
     }
 }
 
-size_t fd_interp_smem(const Dev& d) { return (size_t)NQ * d.nn * sizeof(double); }
+size_t fd_interp_smem(const Dev& d) {
+    const size_t a = (size_t)NQ * d.nn, b = (size_t)NV * d.gbox_max;
+    return (a > b ? a : b) * sizeof(double);
+}
 
 void launch_fd_fill_interp(const Dev& d, const int* list, int ci, int w0, Field U, Field J, cudaStream_t st) {
     if (!d.ginterp) return;
-    k_fd_fill_ghosts_interp<<<d.nsm * 2, 256, fd_interp_smem(d), st>>>(d, list, ci, w0, U, J);
+    const size_t smem = fd_interp_smem(d);
+    cudaFuncSetAttribute(k_fd_fill_ghosts_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fd_fill_ghosts_interp<<<d.nsm * 2, 256, smem, st>>>(d, list, ci, w0, U, J);
     g_launch_counter += 1;
 }
 
 // ---------------------------------------------------------------------------
 // Reverse mode.  The ghosts of a face between wedges are linear in the
 // neighbour's data: an FD neighbour's cells (then J~ = J~(ghost state)), or a
-// DG neighbour's nodal U and J~ (then J~(U) at each node).  Per face, the
-// ghost adjoints and the interpolation weights go to shared memory, and each
-// neighbour cell (or node) gathers its share from every ghost whose stencil
-// holds it, in ghost order (deterministic within the face); faces and
-// elements meeting at one cell are summed with FP64 atomics.
-// Shared layout: gb [12][nper] | wts [nper][3][MAXNP] | st [nper][3] ints | box [6] ints
+// DG neighbour's nodal U and J~ (then J~(U) at each node).  FD neighbour: the
+// ghost adjoints go to shared memory, then one warp per ghost scatters its
+// adjoint times its stencil weights into a shared-memory copy of the box of
+// cells the face's stencils reach (its lanes on distinct entries, so no
+// collisions within a warp), and the box is added to the neighbour's cells once.  DG neighbour: the ghost
+// adjoints and LGL weights go to shared memory and each node gathers its
+// share from every ghost, in ghost order.  Faces and elements meeting at one
+// cell or node are summed with FP64 atomics.
+// Shared layout: FD neighbour acc [9][box max] | ghost adjoints [9][nper]; DG neighbour gb [12][nper] | wts [nper][3][MAXNP].
 size_t fdv_interp_smem(const Dev& d) {
     const size_t nper = (size_t)GH * d.nc * d.nc;
-    return (NQ * nper + nper * 3 * MAXNP) * sizeof(double) + (nper * 3 + 6) * sizeof(int);
+    const size_t dg = NQ * nper + nper * 3 * MAXNP, fd = (size_t)NV * d.gbox_max + NV * nper;
+    return (dg > fd ? dg : fd) * sizeof(double);
 }
 
 __device__ __forceinline__ double* extb_ptr(const Dev& d, const double* extb, int q, int wl) {
@@ -157,10 +195,6 @@ __global__ void k_fdv_ghosts_interp(Dev d, const int* list, int ci, int w0, Fiel
     const int n = chunk_n(d, ci, w0);
     extern __shared__ double sm[];
     const int nperm = GH * d.nc * d.nc;
-    double* gb = sm;                                   // [NQ][nper]
-    double* wts = gb + NQ * nperm;                     // [nper][3][MAXNP]
-    int* sti = (int*)(wts + (size_t)nperm * 3 * MAXNP);  // [nper][3]
-    int* box = sti + 3 * nperm;                        // lo[3], hi[3] of the stencil starts
     for (int item = blockIdx.x; item < n * 6; item += gridDim.x) {
         const int wl = item / 6, f = item % 6;
         const int e = list[w0 + wl];
@@ -171,61 +205,63 @@ __global__ void k_fdv_ghosts_interp(Dev d, const int* list, int ci, int w0, Fiel
         const int dd = f >> 1, s = f & 1;
         const bool fdnb = d.mask[nb] == 1;
         const int nper = GH * nc * nc;
-        if (threadIdx.x < 3) {
-            box[threadIdx.x] = nc;
-            box[3 + threadIdx.x] = -1;
-        }
-        __syncthreads();
         const int sl = d.gislot[e * 6 + f], ghn = GH * d.nc * d.nc;
-        for (int t = threadIdx.x; t < nper; t += blockDim.x) {
-            const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
-            const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
-            const int64_t gi = (int64_t)sl * ghn + t;
-            double gq[NQ];
-            for (int qv = 0; qv < NQ; ++qv) gq[qv] = extb_ptr(d, extb, qv, wl)[og];
-            double* w = wts + (size_t)t * 3 * MAXNP;
-            if (fdnb) {
-                for (int a = 0; a < 3; ++a) {
-                    const int st = d.gst[gi * 3 + a];
-                    for (int m = 0; m < 6; ++m) w[a * MAXNP + m] = d.gwf[gi * 18 + 6 * a + m];
-                    sti[3 * t + a] = st;
-                    atomicMin(box + a, st);
-                    atomicMax(box + 3 + a, st);
-                }
+        if (fdnb) {
+            const int* bx = d.gbox + 6 * sl;
+            const int bx0 = bx[3], bxy = bx[3] * bx[4], bvol = bx[3] * bx[4] * bx[5];
+            double* acc = sm;                    // [9][bvol]
+            double* gbv = acc + NV * d.gbox_max;   // [9][nper]
+            for (int t = threadIdx.x; t < NV * bvol; t += blockDim.x) acc[t] = 0.0;
+            for (int t = threadIdx.x; t < nper; t += blockDim.x) {
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
                 // the ghost current is J~ of the ghost state: chain rule at the ghost
-                double u[NV], ub[NV];
+                double u[NV], ub[NV], jb[3];
                 for (int v = 0; v < NV; ++v) {
                     u[v] = ext_at(d, v, wl)[og];
-                    ub[v] = gq[v];
+                    ub[v] = extb_ptr(d, extb, v, wl)[og];
                 }
-                current_vjp(u, d.eta, gq + NV, gq + NV, ub);
-                for (int v = 0; v < NV; ++v) gb[v * nperm + t] = ub[v];
-            } else {
-                for (int a = 0; a < 3 * MAXNP; ++a) w[a] = d.gwl[gi * 3 * MAXNP + a];
-                for (int qv = 0; qv < NQ; ++qv) gb[qv * nperm + t] = gq[qv];
+                for (int k = 0; k < 3; ++k) jb[k] = extb_ptr(d, extb, NV + k, wl)[og];
+                current_vjp(u, d.eta, jb, jb, ub);
+                for (int v = 0; v < NV; ++v) gbv[v * nperm + t] = ub[v];
             }
-        }
-        __syncthreads();
-        if (fdnb) {
-            const int lo0 = box[0], lo1 = box[1], lo2 = box[2];
-            const int nx = box[3] + 6 - lo0, ny = box[4] + 6 - lo1, nz = box[5] + 6 - lo2;
-            const int64_t base = fdb(d, nb);
-            for (int c = threadIdx.x; c < nx * ny * nz; c += blockDim.x) {
-                const int cx = lo0 + c % nx, cy = lo1 + (c / nx) % ny, cz = lo2 + c / (nx * ny);
-                double acc[NV];
-                for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-                for (int t = 0; t < nper; ++t) {
-                    const int ox = cx - sti[3 * t], oy = cy - sti[3 * t + 1], oz = cz - sti[3 * t + 2];
-                    if ((unsigned)ox >= 6u || (unsigned)oy >= 6u || (unsigned)oz >= 6u) continue;
-                    const double* w = wts + (size_t)t * 3 * MAXNP;
-                    const double wt = w[2 * MAXNP + oz] * w[MAXNP + oy] * w[ox];
-                    for (int v = 0; v < NV; ++v) acc[v] = fma(wt, gb[v * nperm + t], acc[v]);
+            __syncthreads();
+            // one warp per ghost: its lanes take distinct (cell, variable) entries of
+            // the stencil, so the shared-memory additions of a warp never collide
+            const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+            for (int t = threadIdx.x >> 5; t < nper; t += nwarp) {
+                const int64_t gi = (int64_t)sl * ghn + t;
+                const int* st3 = d.gst + gi * 3;
+                const double* wf = d.gwf + gi * 18;
+                const int sa = st3[0] - bx[0], sb = st3[1] - bx[1], sc = st3[2] - bx[2];
+                for (int en = lane; en < NV * 216; en += 32) {
+                    const int v = en / 216, k = en % 216;
+                    const int cx = k % 6, cy = (k / 6) % 6, cz = k / 36;
+                    const double w = wf[12 + cz] * wf[6 + cy] * wf[cx];
+                    atomicAdd(acc + v * bvol + sa + cx + bx0 * (sb + cy) + bxy * (sc + cz), w * gbv[v * nperm + t]);
                 }
-                const int64_t p = base + cx + (int64_t)nc * (cy + (int64_t)nc * cz);
-                for (int v = 0; v < NV; ++v)
-                    if (acc[v] != 0.0) atomicAdd(out.fd(v) + p, acc[v]);
+            }
+            __syncthreads();
+            const int64_t base = fdb(d, nb);
+            for (int t = threadIdx.x; t < NV * bvol; t += blockDim.x) {
+                const double a = acc[t];
+                if (a == 0.0) continue;
+                const int v = t / bvol, r = t % bvol;
+                const int cx = bx[0] + r % bx0, cy = bx[1] + (r / bx0) % bx[4], cz = bx[2] + r / bxy;
+                atomicAdd(out.fd(v) + base + cx + (int64_t)nc * (cy + (int64_t)nc * cz), a);
             }
         } else {
+            double* gb = sm;                                   // [NQ][nper]
+            double* wts = gb + NQ * nperm;                     // [nper][3][MAXNP]
+            for (int t = threadIdx.x; t < nper; t += blockDim.x) {
+                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
+                const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
+                const int64_t gi = (int64_t)sl * ghn + t;
+                double* w = wts + (size_t)t * 3 * MAXNP;
+                for (int a2 = 0; a2 < 3 * MAXNP; ++a2) w[a2] = d.gwl[gi * 3 * MAXNP + a2];
+                for (int qv = 0; qv < NQ; ++qv) gb[qv * nperm + t] = extb_ptr(d, extb, qv, wl)[og];
+            }
+            __syncthreads();
             for (int node = threadIdx.x; node < nn; node += blockDim.x) {
                 const int i = node % np1, j = (node / np1) % np1, k = node / (np1 * np1);
                 double acc[NQ];

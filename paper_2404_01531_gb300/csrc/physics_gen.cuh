@@ -169,6 +169,20 @@ __device__ __forceinline__ bool stiff_solve_gen(double* U, const PM& m, const De
     return ok;
 }
 
+// No-incoming-Poynting outer state (Sec. III.D) with the metric: S.n with
+// S_i proportional to [ijk] E_j B_k of the lowered fields and the outward
+// unit normal nl (lower index); E~ -> 0 where S.n < 0, psi~ = phi~ = 0.
+__device__ __forceinline__ void bc_no_incoming_gen(const double* Ui, const PM& m, const double* nl, double* Uo) {
+    for (int v = 0; v < NV; ++v) Uo[v] = Ui[v];
+    double El[3], Bl[3];
+    lowr(m, Ui, El);
+    lowr(m, Ui + 3, Bl);
+    const double S[3] = {El[1] * Bl[2] - El[2] * Bl[1], El[2] * Bl[0] - El[0] * Bl[2], El[0] * Bl[1] - El[1] * Bl[0]};
+    if (d3(S, nl) < 0.0) { Uo[0] = Uo[1] = Uo[2] = 0.0; }
+    Uo[6] = 0.0;
+    Uo[7] = 0.0;
+}
+
 __device__ __forceinline__ double bnorm_gen(const double* U, const PM& m) {
     double Bl[3];
     lowr(m, U + 3, Bl);

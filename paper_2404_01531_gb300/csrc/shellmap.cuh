@@ -12,6 +12,12 @@
 //   dx/dea = r (pi/4)(1 + X^2) [e_t1/rho - X v/rho^2],
 //   dx/deb = r (pi/4)(1 + Y^2) [e_t2/rho - Y v/rho^2],   (d rho/dX = X/rho)
 //   dx/der = c r v.
+// Spherical Kerr-Schild shell (a != 0, App. B): r is the Kerr-Schild radius and
+// the Cartesian Kerr-Schild point is x = r v + a (z^ x v), i.e.
+// x = (r cos ph - a sin ph) sin th, y = (r sin ph + a cos ph) sin th, z = r cos th
+// for v = (sin th cos ph, sin th sin ph, cos th); the angular columns become
+// r dv + a (z^ x dv), the radial column stays c r v.  Only shell_map carries
+// this; the closed forms below are for a = 0.
 #pragma once
 #include <cmath>
 
@@ -20,6 +26,7 @@ namespace ffe {
 struct ShellGeo {
     double r_in, c;     // r = r_in exp(c (er + 1))
     int na, nr;         // elements per wedge: angular, radial
+    double a;           // spherical Kerr-Schild spin of the map (0: x = r v)
 };
 
 __host__ __device__ inline void shell_elem(const ShellGeo& g, int e, int& ia, int& ib, int& ir, int& w) {
@@ -50,12 +57,23 @@ __host__ __device__ inline void shell_map(const ShellGeo& g, int e, const double
     v[t2] = Y / rho;
     for (int i = 0; i < 3; ++i) x[i] = r * v[i];
     double J[3][3];   // J[i][k] = d x^i / d xi^k
-    const double fa = r * q * (1.0 + X * X) / g.na, fb = r * q * (1.0 + Y * Y) / g.na, fr = g.c * r / g.nr;
+    const double fa = q * (1.0 + X * X) / g.na, fb = q * (1.0 + Y * Y) / g.na, fr = g.c * r / g.nr;
+    double dva[3], dvb[3];   // d v / d xi^1, d v / d xi^2
     for (int i = 0; i < 3; ++i) {
         const double et1 = i == t1 ? 1.0 : 0.0, et2 = i == t2 ? 1.0 : 0.0;
-        J[i][0] = fa * (et1 / rho - X * v[i] / (rho * rho));
-        J[i][1] = fb * (et2 / rho - Y * v[i] / (rho * rho));
+        dva[i] = fa * (et1 / rho - X * v[i] / (rho * rho));
+        dvb[i] = fb * (et2 / rho - Y * v[i] / (rho * rho));
+        J[i][0] = r * dva[i];
+        J[i][1] = r * dvb[i];
         J[i][2] = fr * v[i];
+    }
+    if (g.a != 0.0) {   // + a (z^ x .): (u_x, u_y) -> (-u_y, u_x)
+        x[0] -= g.a * v[1];
+        x[1] += g.a * v[0];
+        J[0][0] -= g.a * dva[1];
+        J[1][0] += g.a * dva[0];
+        J[0][1] -= g.a * dvb[1];
+        J[1][1] += g.a * dvb[0];
     }
     // inverse by cofactors
     const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -

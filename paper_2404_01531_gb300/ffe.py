@@ -14,11 +14,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libffe.so")
 
 NV = 9
-BC = {"periodic": 1, "dirichlet": 2, "no_incoming": 3, "star": 4}
+BC = {"periodic": 1, "dirichlet": 2, "no_incoming": 3, "star": 4, "outflow": 5}
 ID = {"fast_wave": 0, "breakdown": 1, "cleaning_mode": 2, "wald": 3, "dipole": 4,
       "fast_wave_kink": 5, "alfven": 6, "breakdown_1d": 7}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
-DIAG = {"l2_err": 0, "luminosity": 1, "constraints": 2}
+DIAG = {"l2_err": 0, "luminosity": 1, "constraints": 2, "bflux_upper": 3}
 STATUS = {0: "FFE_OK", 1: "FFE_EINVAL", 2: "FFE_ENOMEM", 3: "FFE_ECUDA", 4: "FFE_ETIMEOUT",
           5: "FFE_ENUMERIC", 6: "FFE_ESTATE", 7: "FFE_ENOTIMPL"}
 
@@ -38,7 +38,7 @@ EXPORTS = ["ffe_create", "ffe_set_initial", "ffe_rhs", "ffe_step", "ffe_get_stat
 class Domain(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
-                ("r_in", ctypes.c_double), ("r_out", ctypes.c_double)]
+                ("r_in", ctypes.c_double), ("r_out", ctypes.c_double), ("shell_ks", ctypes.c_int)]
 
 
 class Elements(ctypes.Structure):
@@ -219,6 +219,7 @@ def domain_of(cfg):
         dom.bc_lo[0], dom.bc_hi[0] = BC[cfg["bc_inner"]], BC[cfg["bc_outer"]]
         el.n[0] = el.n[1] = cfg["n_ang"]
         el.n[2] = cfg["n_rad"]
+        dom.shell_ks = 1 if cfg.get("shell_ks") else 0
     return dom, el
 
 
@@ -370,7 +371,8 @@ class Context:
         out = (ctypes.c_double * 4)()
         a = (ctypes.c_double * len(args))(*args) if args else None
         check(load().ffe_diagnostic(self.h, DIAG[kind], a, out))
-        return {"l2_err": tuple(out[:2]), "luminosity": (out[0],), "constraints": tuple(out)}[kind]
+        return {"l2_err": tuple(out[:2]), "luminosity": (out[0],), "constraints": tuple(out),
+                "bflux_upper": (out[0],)}[kind]
 
     def coords(self):
         """(xyz_dg [3][n_dg], xyz_fd [3][n_fd]) float64 CUDA tensors: DG node and

@@ -258,3 +258,37 @@ def test_wald_full_size_1000_steps_stationary_with_the_indicator_on(ffe):
     assert l2_1000 < 1e-3 and l2_1000 < 10 * l2_100, (l2_100, l2_1000)
     assert psi < 1e-3 and phi < 1e-3, (psi, phi)
     ctx.close()
+
+
+@pytest.mark.parametrize("spin,shell_ks", [(0.9, True), (0.999, True), (0.9, False)])
+def test_rhs_kerr_schild_shell_outflow_inner_boundary(ffe, spin, shell_ks):
+    """The vacuum Wald setup's shell (inner surface r = M, outflow there, no
+    incoming Poynting flux outside) on perturbed Wald data with E~ = 0: the
+    right-hand side against the oracle, on the spherical Kerr-Schild shell of
+    App. B (nodes, Jacobians and face normals of x = r v + a z^ x v) and on the
+    shell of spheres |x| = r."""
+    cfg = W.wald_vacuum(spin=spin, n_ang=2, n_rad=2, r_out=6.0)
+    cfg["shell_ks"] = shell_ks
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    rng = np.random.default_rng(77)
+    st["udg"] = st["udg"] + 0.05 * rng.normal(size=st["udg"].shape)
+    assert _rhs_parity(ffe, cfg, st, pr) <= 1e-11
+
+
+def test_step_vacuum_wald_on_the_spherical_kerr_schild_shell(ffe):
+    """The vacuum Wald problem (a = 0.999, Wald's B with E~ = 0, eta = 0) on a
+    small spherical Kerr-Schild shell (6 wedges x 2 x 2 x 3, r in [M, 8 M],
+    P = 5): 20 steps against the oracle, and the coordinates of the nodes on
+    the Kerr-Schild spheroids r = r_in, r_out."""
+    cfg = W.wald_vacuum(spin=0.999, n_ang=2, n_rad=3, r_out=8.0)
+    _run_both(ffe, cfg, 20, 1e-8)
+    ctx = ffe.Context(cfg)
+    x = ctx.coords()[0].cpu().numpy().reshape(3, ctx.n_elem, 6, 6, 6)
+    a = 0.999
+    for k, r in ((0, 1.0), (5, 8.0)):
+        layer = np.arange(ctx.n_elem) // 4 % 3 == (0 if k == 0 else 2)
+        p = x[:, layer, k]
+        rel = (p[0] ** 2 + p[1] ** 2) / (r * r + a * a) + p[2] ** 2 / (r * r)
+        assert np.abs(rel - 1.0).max() < 1e-13
+    ctx.close()

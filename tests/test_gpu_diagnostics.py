@@ -86,3 +86,36 @@ def test_l2_error_with_fd_elements_and_the_mask_view(ffe):
     assert np.array_equal(ctx.mask().cpu().numpy(), mask)
     ctx.set_frozen_masks(False)
     ctx.close()
+
+
+@pytest.mark.parametrize("a,shell_ks", [(0.9, True), (0.999, True), (0.9, False)])
+def test_horizon_flux_of_the_exact_wald_field(ffe, a, shell_ks):
+    """FFE_DIAG_BFLUX_UPPER on the exact Wald field (Kerr-Schild, the vacuum
+    Wald grid: 16 x 96 elements, P = 5).  On the spherical Kerr-Schild shell
+    the surface r = r+ is the outer horizon itself; on the shell of spheres
+    the sphere of radius sqrt(r+^2 + a^2) has the horizon's equator (B~ has zero
+    coordinate divergence, so the flux is the same).  The device quadrature
+    equals the oracle's quadrature of the same nodal field (interpolated to the
+    surface along xi^3, LGL weights, oriented area vectors) to rounding, and
+    the closed form pi r+^2 B0 (1 - a^4/r+^4) of Sec. IV.B.2 to the accuracy
+    of that quadrature (the oracle's tests pin it: spectral convergence on
+    the horizon)."""
+    import math
+    from oracle.surface import flux as surface_flux, surface_weights
+    cfg = W.wald_vacuum(spin=a)
+    cfg["shell_ks"] = shell_ks
+    cfg["initial"] = ("wald", dict(M=1.0, a=a, B0=1.0))
+    ctx = ffe.Context(cfg)
+    ctx.set_initial()
+    rp = 1.0 + math.sqrt(1.0 - a * a)
+    R = rp if shell_ks else math.sqrt(rp * rp + a * a)
+    (flux,) = ctx.diagnostic("bflux_upper", (R,))
+    pr = Problem(cfg)
+    udg = pr.initial_state()["udg"]
+    ref = surface_flux(udg, surface_weights(pr, R, upper=True))
+    assert abs(flux - ref) <= 1e-12 * abs(ref), (flux, ref)
+    king = math.pi * rp * rp * (1.0 - a ** 4 / rp ** 4)
+    assert abs(flux - king) <= (1e-6 if shell_ks else 1e-4) * king, (flux, king)
+    with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
+        ctx.diagnostic("bflux_upper", (0.5,))
+    ctx.close()

@@ -71,3 +71,38 @@ def test_fd_start_needs_the_indicator(ffe):
     with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
         ctx.set_initial(via_fd=True)
     ctx.close()
+
+
+def test_forced_split_alfven_wave(ffe):
+    """The paper's DG/FD split experiment (Sec. IV.A.4) on a small version of
+    its grid: the stationary Alfven wave on 4 x 8 x 1 cubic elements of width
+    3/8 (periodic in y and z), the elements below y = 0 forced onto FD (the
+    indicator off, the mask frozen), 10 steps against the oracle."""
+    h = 3.0 / 8
+    cfg = W.oned("alfven", 0)
+    cfg.update(lo=(-0.75, -4 * h, -0.5 * h), hi=(0.75, 4 * h, 0.5 * h), n=(4, 8, 1))
+    pr = Problem(cfg)
+    E = pr.disc.E
+    yc = pr.disc.xyz[1].reshape(E, -1).mean(axis=1)
+    mask = (yc < 0).astype(np.uint8)
+    assert 0 < mask.sum() < E
+    ctx = ffe.Context(cfg)
+    ctx.set_initial()
+    U0, _ = ctx.state()
+    ctx.set_state(U0.clone(), torch.from_numpy(mask).cuda())
+    ctx.set_initial(keep_mask=True)
+    ctx.freeze_mask(True)
+    st = pr.initial_state()
+    st["mask"] = mask.copy()
+    for e in np.nonzero(mask)[0]:
+        st["ufd"][:, e] = pr.initial(pr.disc.xyz_fd[:, e].reshape(3, -1)).reshape((9,) + pr.disc.xyz_fd.shape[2:])
+    pr.prm["tci_on"] = 0
+    S = Stepper(pr)
+    for _ in range(10):
+        st = S.step(st)
+    ctx.step(10)
+    U, m = ctx.download()
+    assert np.array_equal(m, mask)
+    assert ctx.status() == 0
+    compare_state(ctx, U, st, 1e-8)
+    ctx.close()

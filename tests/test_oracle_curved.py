@@ -256,3 +256,110 @@ def test_exact_wald_l2_error_in_the_band_of_table2():
     v = st["udg"][3:6] - ex[3:6]
     l2 = np.sqrt((v ** 2).sum() / v[0].size)
     assert err / 2 < l2 < 2 * err, (l2, err)
+
+
+def test_wald_field_horizon_flux_is_kings():
+    """The magnetic flux of the exact Wald field through the upper half of
+    the outer horizon has the closed form pi r+^2 B0 (1 - a^4/r+^4) (Sec.
+    IV.B.2, King et al.), r+ = M (1 + sqrt(1 - a^2)).  In Cartesian Kerr-Schild
+    coordinates the horizon r = r+ is a spheroid whose equator is the circle
+    x^2 + y^2 = r+^2 + a^2, z = 0, and the densitised B~ has zero coordinate
+    divergence, so the flux through the upper half of the coordinate sphere of
+    radius sqrt(r+^2 + a^2) (same boundary circle) is the same: the oracle's
+    Wald field integrated there (Gauss-Legendre in theta, uniform in phi)
+    reproduces the closed form to rounding for a = 0 ... 0.999.  This is the
+    reading the flux diagnostic and the vacuum Wald runs use."""
+    for a in (0.0, 0.5, 0.9, 0.999):
+        M, B0 = 1.0, 1.0
+        rp = M * (1 + np.sqrt(1 - a * a))
+        R0 = np.sqrt(rp ** 2 + a ** 2)
+        xg, wg = np.polynomial.legendre.leggauss(48)
+        th, wth = (xg + 1) * np.pi / 4, wg * np.pi / 4
+        nph = 64
+        ph = np.arange(nph) * 2 * np.pi / nph
+        T, Pp = np.meshgrid(th, ph, indexing="ij")
+        x = np.stack([R0 * np.sin(T) * np.cos(Pp), R0 * np.sin(T) * np.sin(Pp), R0 * np.cos(T)])
+        U = initial.wald(x.reshape(3, -1), M=M, a=a, B0=B0).reshape((9,) + T.shape)
+        Br = (U[3:6] * (x / R0)).sum(axis=0)
+        flux = (Br * R0 ** 2 * np.sin(T) * wth[:, None] * (2 * np.pi / nph)).sum()
+        king = np.pi * rp ** 2 * B0 * (1 - a ** 4 / rp ** 4)
+        assert abs(flux - king) <= 1e-12 * king, (a, flux, king)
+
+
+def test_spherical_kerr_schild_shell_geometry():
+    """The shell in the spherical Kerr-Schild radius (App. B): the boundary
+    layers' nodes lie on the spheroids (x^2 + y^2)/(r^2 + a^2) + z^2/r^2 = 1 of
+    r = r_in and r_out (the relation that defines r), every point agrees with
+    App. B's transformation written in (r, theta, phi), the closed-form inverse
+    map undoes the map, every angular face is matched, and the chain-rule
+    gradient of a linear function converges spectrally."""
+    a = 0.9
+    errs = []
+    for P in (4, 7):
+        mesh = ShellMesh(1.0, 4.0, 2, 2, BC_DIRICHLET, BC_DIRICHLET, spin=a)
+        T = Tables(P)
+        d = Discretisation(mesh, T)
+        x = d.xyz
+        for k, r, layer in ((0, 1.0, 0), (-1, 4.0, 1)):
+            sel = np.array([mesh.eidx(e)[2] == layer for e in range(mesh.E)])
+            p = x[:, sel][:, :, k]
+            rel = (p[0] ** 2 + p[1] ** 2) / (r * r + a * a) + p[2] ** 2 / (r * r)
+            assert np.abs(rel - 1.0).max() < 1e-13
+        # App. B in spherical form: theta, phi of the unit vector v of the
+        # cubed-sphere map at the same reference point (the a = 0 mesh)
+        m0 = ShellMesh(1.0, 4.0, 2, 2, BC_DIRICHLET, BC_DIRICHLET)
+        x0 = np.stack([m0.map(e, np.stack(np.meshgrid(T.x, T.x, T.x, indexing="ij")[::-1]))
+                       for e in range(mesh.E)], axis=1)
+        r = np.linalg.norm(x0, axis=0)
+        th, ph = np.arccos(x0[2] / r), np.arctan2(x0[1], x0[0])
+        xb = np.stack([(r * np.cos(ph) - a * np.sin(ph)) * np.sin(th),
+                       (r * np.sin(ph) + a * np.cos(ph)) * np.sin(th), r * np.cos(th)])
+        assert np.abs(xb - x).max() < 1e-13
+        rng = np.random.default_rng(P)
+        for e in rng.integers(0, mesh.E, 6):
+            xi = rng.uniform(-1, 1, size=(3, 5))
+            assert np.abs(mesh.inv_map(e, mesh.map(e, xi)) - xi).max() < 1e-12
+        assert np.all(d.nbr[:, :4] >= 0)
+        assert (d.nbr[:, 4] < 0).sum() == 6 * 2 * 2 and (d.nbr[:, 5] < 0).sum() == 6 * 2 * 2
+        f = 0.3 * x[0] - 1.1 * x[1] + 2.0 * x[2]
+        e = 0.0
+        for j, c in enumerate((0.3, -1.1, 2.0)):
+            g = sum(d.ijac[k, j] * deriv(T.D, f, k) for k in range(3))
+            e = max(e, np.abs(g - c).max())
+        errs.append(e)
+    assert errs[0] < 1e-2 and errs[1] < errs[0] / 20, errs
+
+
+def test_horizon_flux_on_the_spherical_kerr_schild_horizon_converges_to_kings():
+    """The coordinate-surface flux of the oracle (oracle.surface) of the exact
+    Wald field through the upper half of the outer horizon, which is the
+    inner surface r_in = r+ of a spherical Kerr-Schild shell: spectral
+    convergence to pi r+^2 B0 (1 - a^4/r+^4) (Sec. IV.B.2) as the angular
+    elements are refined (no interpolation in xi^3 there), and on the vacuum
+    Wald grid (r+ inside a layer, 16 x 96 elements, P = 5) within 1e-6."""
+    from oracle.surface import flux, surface_weights
+    for a in (0.9, 0.999):
+        rp = 1.0 + math.sqrt(1.0 - a * a)
+        king = math.pi * rp * rp * (1.0 - a ** 4 / rp ** 4)
+        errs = []
+        for na in (2, 4, 6):
+            cfg = W.wald_vacuum(spin=a, n_ang=na, n_rad=1, r_in=rp, r_out=2.0 * rp)
+            cfg["initial"] = ("wald", dict(M=1.0, a=a, B0=1.0))
+            pr = Problem(cfg)
+            errs.append(abs(flux(pr.initial_state()["udg"], surface_weights(pr, rp, upper=True)) / king - 1.0))
+        assert errs[1] < errs[0] / 50 and errs[2] < errs[1] / 10 and errs[2] < 1e-10, (a, errs)
+    cfg = W.wald_vacuum(spin=0.9)
+    cfg["initial"] = ("wald", dict(M=1.0, a=0.9, B0=1.0))
+    pr = Problem(cfg)
+    rp = 1.0 + math.sqrt(1.0 - 0.81)
+    king = math.pi * rp * rp * (1.0 - 0.81 ** 2 / rp ** 4)
+    assert abs(flux(pr.initial_state()["udg"], surface_weights(pr, rp, upper=True)) / king - 1.0) < 1e-6
+
+
+def test_vacuum_wald_grid_time_step_is_the_papers():
+    """The vacuum Wald grid (spherical Kerr-Schild r in [M, 125 M], 16 x 96
+    elements, P = 5, CFL factor 0.25) gives the time step that Sec. IV.B.2
+    quotes, 1.97e-3 M, for a = 0.999 -- a check of the mesh reading (radius in
+    the spherical Kerr-Schild coordinate, innermost layer at r = M)."""
+    pr = Problem(W.wald_vacuum(spin=0.999))
+    assert abs(pr.dt - 1.97e-3) < 0.005e-3, pr.dt
