@@ -273,6 +273,87 @@ def run_wald_vacuum(args):
     print(json.dumps(line), flush=True)
 
 
+def run_inclination(args):
+    """The oblique rotator's spin-down luminosity against inclination (Sec.
+    IV.C.2): rotating conducting star of radius R = 1 with the regularised
+    dipole (mu = 1, delta = 0.1 R), Omega = 1/(5 R), eta = 1e5 / R, on a
+    6-wedge shell r in [R, 20 R] (n_ang x n_ang x n_rad per wedge, P = 5, CFL
+    0.25, indicator on); one context per inclination chi, all advanced
+    together on their own CUDA streams, for two rotation periods; L through
+    r = 6 R (FFE_DIAG_LUMINOSITY) every eighth of a period.  Fits
+    L = L0 (k1 + k2 sin^2 chi) with L0 = L(chi = 0) (least squares over the
+    inclinations, on the mean of L over the last half period) and reports
+    L0 / (mu^2 Omega^4), the force-free aligned rotator's value in units of
+    the vacuum dipole's scale."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2404_01531_gb300 import ffe
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    r_lc, mu, r_L = 5.0, 1.0, 6.0
+    period = 2.0 * math.pi * r_lc
+    ctxs, streams = [], []
+    for chi in args.chis:
+        cfg = W.pulsar(r_lc=r_lc, chi=math.radians(chi), n_ang=args.n_ang, n_rad=args.n_rad, P=5, mu=mu,
+                       r_out=4.0 * r_lc)
+        s = torch.cuda.Stream()
+        ctx = ffe.Context(cfg, stream=s)
+        ctx.set_initial()
+        ctx.step(1)            # first step: launch-shape tuning, alone on the GPU
+        torch.cuda.synchronize()
+        ctxs.append(ctx)
+        streams.append(s)
+    dt = ctxs[0].dt
+    n_total = int(round(args.periods * period / dt))
+    marks = [int(round(k * period / 8 / dt)) for k in range(1, int(round(8 * args.periods)) + 1)]
+    series = [[] for _ in ctxs]
+    done, t0 = 1, time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream())
+    for m in marks:
+        # interleave the contexts in short runs of steps so that every stream
+        # has work queued while the host enqueues the others
+        for k in range(done, m, 16):
+            for ctx in ctxs:
+                ctx.step(min(16, m - k))
+        done = m
+        for i, ctx in enumerate(ctxs):
+            inf = ctx.info()
+            series[i].append({"t": inf.t, "L": ctx.diagnostic("luminosity", (r_L,))[0],
+                              "fd_elements": inf.n_fd_elem})
+    for s in streams:
+        torch.cuda.current_stream().wait_stream(s)
+    e1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    wall = time.perf_counter() - t0
+    rows = []
+    for chi, ctx, ser in zip(args.chis, ctxs, series):
+        tail = [p["L"] for p in ser if p["t"] >= (args.periods - 0.5) * period - 1e-9]
+        rows.append({"chi_deg": chi, "L_end": ser[-1]["L"], "L_mean_last_half_period": float(np.mean(tail)),
+                     "fd_elements_end": ser[-1]["fd_elements"], "status_bits": ctx.status(), "series": ser})
+    L = np.array([r["L_mean_last_half_period"] for r in rows])
+    chis = np.radians(np.array(args.chis))
+    i0 = int(np.argmin(np.abs(chis)))
+    A = np.stack([np.ones_like(chis), np.sin(chis) ** 2], axis=1)
+    k1, k2 = np.linalg.lstsq(A, L / L[i0], rcond=None)[0]
+    units = sum(c.info().node_updates for c in ctxs)
+    line = {"metric": "oblique rotator spin-down luminosity vs inclination (Sec. IV.C.2)",
+            "value": float(k2), "unit": "k2 of L = L0 (k1 + k2 sin^2 chi)", "k1": float(k1), "k2": float(k2),
+            "L0_over_mu2_omega4": float(L[i0] / (mu ** 2 * (1.0 / r_lc) ** 4)),
+            "n_gpus": 1, "higher_is_better": None, "dtype": "f64", "data": "synthetic",
+            "steps": n_total, "dt": dt, "ms_per_step_all_contexts": ms / max(done - 1, 1), "wall_s": wall,
+            "node_updates_per_s": units / (ms / 1e3),
+            "config": {"workload": f"oblique rotator: star R=1, mu=1, delta=0.1, Omega=1/5, eta=1e5, 6 wedges x "
+                                   f"{args.n_ang}x{args.n_ang}x{args.n_rad}, P=5, r in [1, 20], CFL 0.25, "
+                                   f"indicator on, {args.periods} periods, L at r=6",
+                       "inclinations_deg": args.chis, "contexts": "one per inclination, concurrent streams"},
+            "runs": rows}
+    for c in ctxs:
+        c.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_shell(args):
     """The neutron-star shell (6 wedges x 6x6x12, P=5, eta=1e5) with its three
     innermost radial layers on FD subcells and the mask frozen: an FD-heavy
@@ -748,14 +829,16 @@ def main():
     ap.add_argument("--nx", type=int, default=64,
                     help="elements along x (same width 4/64; smaller values for profiler captures)")
     ap.add_argument("--workload", default="breakdown",
-                    choices=["breakdown", "pulsars", "adjoint", "shell", "oned", "dgphases", "wald", "wald_vacuum"],
+                    choices=["breakdown", "pulsars", "adjoint", "shell", "oned", "dgphases", "wald", "wald_vacuum",
+                             "inclination"],
                     help="pulsars: the 32-shell batch, batched launch vs one context per instance; "
                          "adjoint: luminosity gradient of one neutron-star shell (--steps steps); "
                          "shell: that shell with three FD layers, frozen mask (curved FD kernels); "
                          "oned: the paper's 1-D tests and its DG/FD split experiment; "
                          "dgphases: cost of the DG kernel's filter, indicator and stiff-current phases; "
                          "wald: the Kerr-Schild Wald shell, 1000 steps, indicator on; "
-                         "wald_vacuum: horizon flux against spin (Sec. IV.B.2)")
+                         "wald_vacuum: horizon flux against spin (Sec. IV.B.2); "
+                         "inclination: oblique rotator luminosity against inclination (Sec. IV.C.2)")
     ap.add_argument("--no-adjoint", action="store_true", help="breakdown: skip the adjoint/forward timing")
     ap.add_argument("--no-batch", action="store_true",
                     help="breakdown: skip the batched-against-single timing of the 32-shell batch")
@@ -766,6 +849,11 @@ def main():
     ap.add_argument("--n-inst", type=int, default=32)
     ap.add_argument("--spins", type=float, nargs="+", default=[0.0, 0.5, 0.9, 0.999],
                     help="wald_vacuum: black-hole spins")
+    ap.add_argument("--chis", type=float, nargs="+", default=[0.0, 30.0, 60.0, 90.0],
+                    help="inclination: magnetic inclinations in degrees")
+    ap.add_argument("--periods", type=float, default=2.0, help="inclination: rotation periods to evolve")
+    ap.add_argument("--n-ang", type=int, default=4, help="inclination: angular elements per wedge side")
+    ap.add_argument("--n-rad", type=int, default=8, help="inclination: radial elements per wedge")
     ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
     ap.add_argument("--fd-slots", type=float, default=0.25,
                     help="breakdown: FD slot pool as a fraction of the elements (1 = one FD block per element)")
@@ -780,6 +868,8 @@ def main():
         return run_wald(args)
     if args.workload == "wald_vacuum":
         return run_wald_vacuum(args)
+    if args.workload == "inclination":
+        return run_inclination(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
     if args.workload == "oned":

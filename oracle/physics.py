@@ -270,13 +270,19 @@ def bc_no_incoming_poynting(Uint, m, nlow):
 def bc_star(Uint, xyz, omega):
     """Perfect-conductor rotating star as an inner boundary state (Sec. IV.C,
     ideal-MHD condition), flat space: B~_out = B~_int, E~_out = -v x B~ with
-    v = Omega z^ x x, psi~_out = q~_out = 0, phi~_out = phi~_int.  [reading]
-    the paper overwrites E inside r <= R; here r = R is the inner boundary."""
+    v = Omega z^ x x, psi~_out = q~_out = 0 (fixed inside the paper's star),
+    phi~_out = 0.  [reading] the paper overwrites E inside r <= R and lets B
+    and phi evolve there; here r = R is the inner boundary, and its state sets
+    the cleaning scalars to zero as the paper's outer boundary state does
+    (Sec. III.D): taken from the interior, phi~ leaves the incoming
+    divergence-cleaning wave of B without data, and a static dipole then
+    grows at the star."""
     U = Uint.copy()
     x, y = xyz[0], xyz[1]
     v = np.stack([-omega * y, omega * x, 0 * x])
     B = Uint[3:6]
     U[0:3] = -cross_lower(v, B)
     U[6] = 0 * U[6]
+    U[7] = 0 * U[7]
     U[8] = 0 * U[8]
     return U

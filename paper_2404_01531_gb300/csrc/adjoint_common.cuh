@@ -193,7 +193,7 @@ __device__ __forceinline__ void lift_ext_tJ(const double* n, double sc, const do
     for (int k = 0; k < 3; ++k) zJ[k] = sc * ub[NV + k];
 }
 
-// Ui-bar from Uo-bar through the star state Uo = (-v x B, B, 0, phi, 0),
+// Ui-bar from Uo-bar through the star state Uo = (-v x B, B, 0, 0, 0),
 // v = Omega (-y, x, 0) at x; returns the Omega derivative Uo-bar . dUo/dOmega.
 __device__ __forceinline__ double bc_star_vjp(const double* Ui, const double* x, double omega, const double* ob,
                                               double* ib) {
@@ -203,7 +203,6 @@ __device__ __forceinline__ double bc_star_vjp(const double* Ui, const double* x,
     ib[4] += vv[2] * ob[0] - vv[0] * ob[2];
     ib[5] += vv[0] * ob[1] - vv[1] * ob[0];
     ib[3] += ob[3]; ib[4] += ob[4]; ib[5] += ob[5];
-    ib[7] += ob[7];
     const double dv[3] = {-x[1], x[0], 0.0};
     const double* B = Ui + 3;
     const double dE[3] = {B[1] * dv[2] - B[2] * dv[1], B[2] * dv[0] - B[0] * dv[2], B[0] * dv[1] - B[1] * dv[0]};

@@ -628,9 +628,9 @@ void launch_adj_addG(const Dev& d, Field U, Field Gb, Field io, cudaStream_t st)
 struct LumArgs {
     const int* elem;        // [ns] element of surface column s
     const double* lk;       // [np1] interpolation weights along xi^3
-    const double* wn;       // [ns][np1^2][4]: weight, rhat (3) at (i, j)
+    const double* wn;       // [ns][np1^2][4]: weight, outward unit normal (3) at (i, j)
     int ns;
-    int bflux;              // 1: integrate B~.rhat (magnetic flux) instead of (E x B).rhat
+    int bflux;              // 1: integrate B~.n (magnetic flux) instead of (E x B).n
 };
 
 __global__ void k_luminosity(Dev d, Field U, LumArgs la, double* out, Field grad, double scale) {

@@ -183,7 +183,10 @@ __device__ __forceinline__ void bc_no_incoming_flat(const double* Ui, const doub
     Uo[7] = 0.0;
 }
 
-// Rotating perfect-conductor star state (Sec. IV.C): E = -v x B, v = Omega z x x.
+// Rotating perfect-conductor star state (Sec. IV.C): E = -v x B, v = Omega z x x,
+// B from the interior, psi = q = 0 (as inside the paper's star) and phi = 0 (as
+// in the paper's outer boundary states: the incoming divergence-cleaning wave
+// of B then has data; taking phi from the interior lets it grow at the star).
 __device__ __forceinline__ void bc_star_flat(const double* Ui, const double* x, double omega, double* Uo) {
     for (int v = 0; v < NV; ++v) Uo[v] = Ui[v];
     double vx = -omega * x[1], vy = omega * x[0];
@@ -192,6 +195,7 @@ __device__ __forceinline__ void bc_star_flat(const double* Ui, const double* x, 
     Uo[1] = -(-vx * B[2]);
     Uo[2] = -(vx * B[1] - vy * B[0]);
     Uo[6] = 0.0;
+    Uo[7] = 0.0;
     Uo[8] = 0.0;
 }
 

@@ -128,3 +128,27 @@ def test_star_state_is_ideal_mhd():
     v = np.stack([-0.3 * xyz[1], 0.3 * xyz[0], 0 * xyz[0]])
     np.testing.assert_allclose(out[0:3] + np.cross(v.T, U[3:6].T).T, 0, atol=1e-14)
     assert np.abs(np.sum(out[0:3] * U[3:6], 0)).max() < 1e-13
+    assert np.all(out[3:6] == U[3:6]) and np.all(out[6:9] == 0)
+
+
+def test_static_dipole_stays_put_with_the_star_boundary_state():
+    """A non-rotating star (Omega = 0) with its dipole and eta = 0 is a
+    vacuum field (the delta-regularised dipole is curl-free to O(delta^2) at
+    r >= R): 150 steps of the 2 x 2 x 4 shell keep max|B~| within 2% of the
+    initial field and the cleaning scalar phi~ below 1e-2.  The boundary state
+    that takes phi~ from the interior fails it (at step 150 max|phi~| = 1.6
+    and max|B~| has fallen to 0.3 of the initial maximum: the incoming
+    cleaning wave of B~ has no data at r = R)."""
+    import ffe_workloads as W
+    from oracle.problem import Problem
+    from oracle.stepper import Stepper
+    cfg = W.pulsar(r_lc=5.0, chi=0.0, n_ang=2, n_rad=4, P=5, r_out=20.0)
+    cfg["params"].update(tci_on=0, omega_star=0.0, eta=0.0)
+    pr = Problem(cfg)
+    st = pr.initial_state()
+    b0 = np.abs(st["udg"][3:6]).max()
+    S = Stepper(pr)
+    for _ in range(150):
+        st = S.step(st)
+    assert abs(np.abs(st["udg"][3:6]).max() / b0 - 1.0) < 0.02
+    assert np.abs(st["udg"][7]).max() < 1e-2
