@@ -163,7 +163,9 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
     element's grid extended past the face -- a DG neighbour's polynomial
     evaluated there, an FD neighbour's cells interpolated there (6-point
     tensor Lagrange in its reference coordinates, the paper's sixth-order
-    transfer, Sec. III.C.1).  Off: the neighbour's own cells (its polynomial
+    transfer, Sec. III.C.1); either way the ghost current is the neighbour's
+    current transferred the same way, not the current of the transferred
+    state.  Off: the neighbour's own cells (its polynomial
     at its own subcell centres).  Where the grids continue each other (inside
     a cubed-sphere wedge, on boxes) both readings give the same ghosts up to
     rounding; between wedges only the interpolated ghosts are consistent
@@ -194,6 +196,14 @@ def fill_ghosts(st, disc, sel, met_fn, prm):
                     xi_nb = disc.mesh.inv_map(nb, gx.reshape(3, -1) - disc.mesh.period_shift(e, f)[:, None])
                     if st["mask"][nb] == FD:
                         ext[tgt] = _interp_fd(st["ufd"][:, nb], xi_nb, T.xc).reshape(ext[tgt].shape)
+                        # the neighbour's current J~ transferred with the state (as
+                        # from a DG neighbour): J~ of the interpolated state carries
+                        # eta (E.B) of the interpolation error, which the stiff
+                        # eta = 1e5 amplifies into a growing charge at wedge faces
+                        m = _met_at(met_fn["fd"], np.array([nb]), ())
+                        jd, jp = ph.current(st["ufd"][:, nb:nb + 1], m, prm["eta"])
+                        jgh[(slice(None),) + tgt[1:]] = _interp_fd((jd + jp)[:, 0], xi_nb, T.xc).reshape(
+                            (3,) + ext[tgt].shape[1:])
                     else:
                         ext[tgt] = _interp_dg(st["udg"][:, nb], xi_nb, T.x).reshape(ext[tgt].shape)
                         m = _met_at(met_fn["dg"], np.array([nb]), ())

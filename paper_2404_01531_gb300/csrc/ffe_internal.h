@@ -98,12 +98,10 @@ struct Dev {
     const double* met;
     // Kerr-Schild metric at FD points (null in flat space): subcell centres
     // [NMET][E ncell]; face points [3][NPM][E (nc+1) nc^2]; ghost centres across
-    // Dirichlet faces [nbf][NPM][GH nc^2] and across faces between wedges
-    // [slot][NPM][GH nc^2] with slot gislot[e 6 + f]
+    // Dirichlet faces [nbf][NPM][GH nc^2]
     const double* metfd;
     const double* metff;
     const double* metgb;
-    const double* metgi;
     // faces between cubed-sphere wedges: ghost-table slot of each element face
     // ([E][6], -1 elsewhere) and per ghost (slot, g, ta, tb) of the slot's face,
     // [slot][GH nc^2]: the first neighbour cell of its 6-point stencil along each

@@ -534,9 +534,9 @@ int host_P(const ffe_ctx* c, int e) { return c->batch ? c->h_eP[e] : c->d.P; }
 // of the three directions, [3][NPM][E nface] (Dev::metff; face m between cells
 // m-1 and m, tangential cell centres ta, tb along axes_of); ghost centres
 // across Dirichlet faces, [nbf][NPM][GH nc^2] (Dev::metgb, indexed like the
-// Dirichlet ghost states), and across faces between wedges,
-// [slot][NPM][GH nc^2] (Dev::metgi, slot Dev::gislot[e 6 + f]).  NPM: alpha,
-// beta^i, gamma_ij, gamma^ij, sqrt(gamma), the first NPM entries of NMET.
+// Dirichlet ghost states).  Ghosts across faces between wedges need no metric:
+// they take the neighbour's transferred current.  NPM: alpha, beta^i,
+// gamma_ij, gamma^ij, sqrt(gamma), the first NPM entries of NMET.
 ffe_status build_ks_fd_tables(ffe_ctx* c, const std::vector<double>& xfd) {
     Dev& d = c->d;
     const int E = d.E, nc = d.nc, ncell = d.ncell;
@@ -605,22 +605,6 @@ ffe_status build_ks_fd_tables(ffe_ctx* c, const std::vector<double>& xfd) {
         if ((s = dalloc(c, &d_mg, mg.size()))) return s;
         CK(cudaMemcpy(d_mg, mg.data(), mg.size() * 8, cudaMemcpyHostToDevice));
         d.metgb = d_mg;
-    }
-    const std::vector<int>& gslot = c->h_gislot;
-    int ng = 0;
-    for (int v : gslot) ng = v + 1 > ng ? v + 1 : ng;
-    if (ng > 0) {
-        std::vector<double> mg((size_t)ng * per);
-        parallel_for(E, [&](int64_t e) {
-            for (int f = 0; f < 6; ++f) {
-                const int sl = gslot[6 * e + f];
-                if (sl >= 0) ghosts((int)e, f, mg.data() + sl * per, (int64_t)GH * nc * nc);
-            }
-        });
-        double* d_mg;
-        if ((s = dalloc(c, &d_mg, mg.size()))) return s;
-        CK(cudaMemcpy(d_mg, mg.data(), mg.size() * 8, cudaMemcpyHostToDevice));
-        d.metgi = d_mg;
     }
     return FFE_OK;
 }

@@ -165,13 +165,12 @@ __global__ void __launch_bounds__(AVJ<P>::NT) k_rhs_vjp(Dev d, Field U, Field L,
                     else bc_no_incoming_flat(Ui, n, Ue);
                     lift_ext_t(Ue, d.eta, n, sc, lm, z);   // (dC/dUe)^T lambda
                     if (kind == FFE_BC_STAR) {
-                        // Ue: E = B x v, v = Omega (-y, x, 0); B = B_i; phi = phi_i; psi = q = 0
+                        // Ue: E = B x v, v = Omega (-y, x, 0); B = B_i; psi = phi = q = 0
                         const double vv[3] = {-om * xn[1], om * xn[0], 0.0};
                         acc[3] -= vv[1] * z[2] - vv[2] * z[1];
                         acc[4] -= vv[2] * z[0] - vv[0] * z[2];
                         acc[5] -= vv[0] * z[1] - vv[1] * z[0];
                         acc[3] -= z[3]; acc[4] -= z[4]; acc[5] -= z[5];
-                        acc[7] -= z[7];
                         // d Ue_E / d Omega = B x (z^ x x) = B x (-y, x, 0)
                         const double dv[3] = {-xn[1], xn[0], 0.0};
                         const double* B = Ui + 3;

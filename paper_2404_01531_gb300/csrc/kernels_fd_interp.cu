@@ -16,14 +16,17 @@
 //     wedges of one shell, keeps its logical coordinate);
 //   - an FD neighbour: tensor-product 6-point Lagrange interpolation through
 //     the 6 subcell centres nearest the point along each axis (the stencil
-//     kept inside the element); the ghost current J~ is the current of the
-//     interpolated state, as for every FD ghost;
+//     kept inside the element), of its state and of its cell currents J~ (the
+//     current is transferred, as from a DG neighbour: the current of the
+//     interpolated state would carry eta (E.B) of the interpolation error,
+//     which a stiff eta = 1e5 turns into a charge that grows at wedge faces);
 //   - a DG neighbour: its nodal polynomial of U and of its nodal current J~
 //     evaluated at the point (as its ghosts are filled everywhere else).
 // The geometry is static, so the host tabulates, per ghost, the stencils'
 // first cells and weights and the LGL Lagrange weights (Dev::gst, gwf, gwl);
-// the kernels only gather and multiply.  On the Kerr-Schild background the
-// ghost current takes the metric at the ghost centre (Dev::metgi).
+// the kernels only gather and multiply.  The cell currents are those of
+// k_current (J.fd(3..5)), on the Kerr-Schild background with the metric at
+// the neighbour's cell centres.
 #include "ffe_internal.h"
 #include "physics.cuh"
 #include "physics_gen.cuh"
@@ -50,7 +53,8 @@ __device__ __forceinline__ int64_t ghost_off(int dd, int s, int nc, int g, int t
 
 // One CTA per (chunk position, face between wedges); other faces are left to
 // k_fd_fill_ghosts.  Dynamic shared memory: a DG neighbour's U and J~ [12][nn],
-// or the box of an FD neighbour's cells that the face's stencils reach [9][box].
+// or the box of an FD neighbour's cells that the face's stencils reach, with
+// their U and J~ [12][box].
 __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, Field U, Field J) {
     const int n = chunk_n(d, ci, w0);
     extern __shared__ double su[];
@@ -74,18 +78,21 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
                 su[t] = qv < NV ? U.dg(qv)[pn] : J.dg(3 + qv - NV)[pn];
             }
         } else {
+            // the box of the neighbour's cells: state [9] and cell current J~ [3]
             const int64_t base = fdb(d, nb);
-            for (int t = threadIdx.x; t < NV * bvol; t += blockDim.x) {
-                const int v = t / bvol, r = t % bvol;
+            for (int t = threadIdx.x; t < NQ * bvol; t += blockDim.x) {
+                const int qv = t / bvol, r = t % bvol;
                 const int cx = bx[0] + r % bx0, cy = bx[1] + (r / bx0) % bx[4], cz = bx[2] + r / bxy;
-                su[t] = U.fd(v)[base + cx + (int64_t)nc * (cy + (int64_t)nc * cz)];
+                const int64_t pc = base + cx + (int64_t)nc * (cy + (int64_t)nc * cz);
+                su[t] = qv < NV ? U.fd(qv)[pc] : J.fd(3 + qv - NV)[pc];
             }
         }
         __syncthreads();
         if (fdnb) {
-            // one thread per (ghost, group of three variables): 216 FMAs per variable
-            for (int it = threadIdx.x; it < 3 * nper; it += blockDim.x) {
-                const int t = it / 3, grp = it % 3;
+            // one thread per (ghost, group of three quantities: E~, B~, (psi~, phi~, q~),
+            // J~): 216 FMAs per quantity
+            for (int it = threadIdx.x; it < 4 * nper; it += blockDim.x) {
+                const int t = it / 4, grp = it % 4;
                 const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
                 const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
                 const int64_t gi = (int64_t)sl * ghn + t;
@@ -110,23 +117,6 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
                 ext_at(d, 3 * grp, wl)[og] = u0;
                 ext_at(d, 3 * grp + 1, wl)[og] = u1;
                 ext_at(d, 3 * grp + 2, wl)[og] = u2;
-            }
-            __syncthreads();
-            // the ghost current: J~ of the interpolated state (metric at the ghost centre)
-            for (int t = threadIdx.x; t < nper; t += blockDim.x) {
-                const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
-                const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
-                double u[NV], jd[3], jf[3];
-                for (int v = 0; v < NV; ++v) u[v] = ext_at(d, v, wl)[og];
-                if (d.ks) {
-                    PM m;
-                    load_pm(d.metgi + (int64_t)sl * NPM * GH * d.nc * d.nc, (int64_t)GH * d.nc * d.nc,
-                            (int64_t)g * nc * nc + ta + nc * tb, m);
-                    current_gen(u, m, d.eta, jd, jf);
-                } else {
-                    current_flat(u, d.eta, jd, jf);
-                }
-                for (int k = 0; k < 3; ++k) ext_at(d, NV + k, wl)[og] = jf[k];
             }
         } else {
             for (int t = threadIdx.x; t < nper; t += blockDim.x) {
@@ -157,7 +147,7 @@ __global__ void k_fd_fill_ghosts_interp(Dev d, const int* list, int ci, int w0, 
 }
 
 size_t fd_interp_smem(const Dev& d) {
-    const size_t a = (size_t)NQ * d.nn, b = (size_t)NV * d.gbox_max;
+    const size_t a = (size_t)NQ * d.nn, b = (size_t)NQ * d.gbox_max;
     return (a > b ? a : b) * sizeof(double);
 }
 
@@ -171,19 +161,20 @@ void launch_fd_fill_interp(const Dev& d, const int* list, int ci, int w0, Field 
 
 // ---------------------------------------------------------------------------
 // Reverse mode.  The ghosts of a face between wedges are linear in the
-// neighbour's data: an FD neighbour's cells (then J~ = J~(ghost state)), or a
-// DG neighbour's nodal U and J~ (then J~(U) at each node).  FD neighbour: the
-// ghost adjoints go to shared memory, then one warp per ghost scatters its
-// adjoint times its stencil weights into a shared-memory copy of the box of
-// cells the face's stencils reach (its lanes on distinct entries, so no
-// collisions within a warp), and the box is added to the neighbour's cells once.  DG neighbour: the ghost
+// neighbour's data U and J~: an FD neighbour's cells, or a DG neighbour's
+// nodes (then J~(U) at each cell or node).  FD neighbour: the ghost adjoints
+// go to shared memory, then one warp per ghost scatters its adjoint times its
+// stencil weights into a shared-memory copy of the box of cells the face's
+// stencils reach (its lanes on distinct entries, so no collisions within a
+// warp); each cell of the box takes its J~ adjoint through J~(U) of that cell
+// and is added to the neighbour's cells once.  DG neighbour: the ghost
 // adjoints and LGL weights go to shared memory and each node gathers its
 // share from every ghost, in ghost order.  Faces and elements meeting at one
 // cell or node are summed with FP64 atomics.
-// Shared layout: FD neighbour acc [9][box max] | ghost adjoints [9][nper]; DG neighbour gb [12][nper] | wts [nper][3][MAXNP].
+// Shared layout: FD neighbour acc [12][box max] | ghost adjoints [12][nper]; DG neighbour gb [12][nper] | wts [nper][3][MAXNP].
 size_t fdv_interp_smem(const Dev& d) {
     const size_t nper = (size_t)GH * d.nc * d.nc;
-    const size_t dg = NQ * nper + nper * 3 * MAXNP, fd = (size_t)NV * d.gbox_max + NV * nper;
+    const size_t dg = NQ * nper + nper * 3 * MAXNP, fd = (size_t)NQ * d.gbox_max + NQ * nper;
     return (dg > fd ? dg : fd) * sizeof(double);
 }
 
@@ -209,21 +200,13 @@ __global__ void k_fdv_ghosts_interp(Dev d, const int* list, int ci, int w0, Fiel
         if (fdnb) {
             const int* bx = d.gbox + 6 * sl;
             const int bx0 = bx[3], bxy = bx[3] * bx[4], bvol = bx[3] * bx[4] * bx[5];
-            double* acc = sm;                    // [9][bvol]
-            double* gbv = acc + NV * d.gbox_max;   // [9][nper]
-            for (int t = threadIdx.x; t < NV * bvol; t += blockDim.x) acc[t] = 0.0;
+            double* acc = sm;                      // [12][bvol]
+            double* gbv = acc + NQ * d.gbox_max;   // [12][nper]
+            for (int t = threadIdx.x; t < NQ * bvol; t += blockDim.x) acc[t] = 0.0;
             for (int t = threadIdx.x; t < nper; t += blockDim.x) {
                 const int g = t / (nc * nc), ta = t % nc, tb = (t / nc) % nc;
                 const int64_t og = ghost_off(dd, s, nc, g, ta, tb);
-                // the ghost current is J~ of the ghost state: chain rule at the ghost
-                double u[NV], ub[NV], jb[3];
-                for (int v = 0; v < NV; ++v) {
-                    u[v] = ext_at(d, v, wl)[og];
-                    ub[v] = extb_ptr(d, extb, v, wl)[og];
-                }
-                for (int k = 0; k < 3; ++k) jb[k] = extb_ptr(d, extb, NV + k, wl)[og];
-                current_vjp(u, d.eta, jb, jb, ub);
-                for (int v = 0; v < NV; ++v) gbv[v * nperm + t] = ub[v];
+                for (int qv = 0; qv < NQ; ++qv) gbv[qv * nperm + t] = extb_ptr(d, extb, qv, wl)[og];
             }
             __syncthreads();
             // one warp per ghost: its lanes take distinct (cell, variable) entries of
@@ -234,21 +217,35 @@ __global__ void k_fdv_ghosts_interp(Dev d, const int* list, int ci, int w0, Fiel
                 const int* st3 = d.gst + gi * 3;
                 const double* wf = d.gwf + gi * 18;
                 const int sa = st3[0] - bx[0], sb = st3[1] - bx[1], sc = st3[2] - bx[2];
-                for (int en = lane; en < NV * 216; en += 32) {
-                    const int v = en / 216, k = en % 216;
+                for (int en = lane; en < NQ * 216; en += 32) {
+                    const int qv = en / 216, k = en % 216;
                     const int cx = k % 6, cy = (k / 6) % 6, cz = k / 36;
                     const double w = wf[12 + cz] * wf[6 + cy] * wf[cx];
-                    atomicAdd(acc + v * bvol + sa + cx + bx0 * (sb + cy) + bxy * (sc + cz), w * gbv[v * nperm + t]);
+                    atomicAdd(acc + qv * bvol + sa + cx + bx0 * (sb + cy) + bxy * (sc + cz), w * gbv[qv * nperm + t]);
                 }
             }
             __syncthreads();
+            // per box cell: the J~ adjoint through J~(U) of the cell, then into the neighbour
             const int64_t base = fdb(d, nb);
-            for (int t = threadIdx.x; t < NV * bvol; t += blockDim.x) {
-                const double a = acc[t];
-                if (a == 0.0) continue;
-                const int v = t / bvol, r = t % bvol;
+            for (int r = threadIdx.x; r < bvol; r += blockDim.x) {
+                double ub[NV], jb[3];
+                bool any = false;
+                for (int v = 0; v < NV; ++v) {
+                    ub[v] = acc[v * bvol + r];
+                    any |= ub[v] != 0.0;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    jb[k] = acc[(NV + k) * bvol + r];
+                    any |= jb[k] != 0.0;
+                }
+                if (!any) continue;
                 const int cx = bx[0] + r % bx0, cy = bx[1] + (r / bx0) % bx[4], cz = bx[2] + r / bxy;
-                atomicAdd(out.fd(v) + base + cx + (int64_t)nc * (cy + (int64_t)nc * cz), a);
+                const int64_t pc = base + cx + (int64_t)nc * (cy + (int64_t)nc * cz);
+                double u[NV];
+                for (int v = 0; v < NV; ++v) u[v] = U.fd(v)[pc];
+                current_vjp(u, d.eta, jb, jb, ub);
+                for (int v = 0; v < NV; ++v)
+                    if (ub[v] != 0.0) atomicAdd(out.fd(v) + pc, ub[v]);
             }
         } else {
             double* gb = sm;                                   // [NQ][nper]
