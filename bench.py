@@ -283,8 +283,10 @@ def run_inclination(args):
     r = 6 R (FFE_DIAG_LUMINOSITY) every eighth of a period.  Fits
     L = L0 (k1 + k2 sin^2 chi) with L0 = L(chi = 0) (least squares over the
     inclinations, on the mean of L over the last half period) and reports
-    L0 / (mu^2 Omega^4), the force-free aligned rotator's value in units of
-    the vacuum dipole's scale."""
+    L0 / (4 pi mu^2 Omega^4): the equations are in Heaviside-Lorentz units
+    (energy density (E^2 + B^2)/2, Poynting flux E x B), where the dipole
+    moment mu is the Gaussian one over sqrt(4 pi), so the force-free aligned
+    rotator's mu_G^2 Omega^4 (c = 1) reads 4 pi mu^2 Omega^4 here."""
     import math
     import numpy as np
     import torch
@@ -340,7 +342,7 @@ def run_inclination(args):
     units = sum(c.info().node_updates for c in ctxs)
     line = {"metric": "oblique rotator spin-down luminosity vs inclination (Sec. IV.C.2)",
             "value": float(k2), "unit": "k2 of L = L0 (k1 + k2 sin^2 chi)", "k1": float(k1), "k2": float(k2),
-            "L0_over_mu2_omega4": float(L[i0] / (mu ** 2 * (1.0 / r_lc) ** 4)),
+            "L0_over_4pi_mu2_omega4": float(L[i0] / (4.0 * math.pi * mu ** 2 * (1.0 / r_lc) ** 4)),
             "n_gpus": 1, "higher_is_better": None, "dtype": "f64", "data": "synthetic",
             "steps": n_total, "dt": dt, "ms_per_step_all_contexts": ms / max(done - 1, 1), "wall_s": wall,
             "node_updates_per_s": units / (ms / 1e3),
@@ -853,7 +855,7 @@ def main():
                     help="inclination: magnetic inclinations in degrees")
     ap.add_argument("--periods", type=float, default=2.0, help="inclination: rotation periods to evolve")
     ap.add_argument("--n-ang", type=int, default=4, help="inclination: angular elements per wedge side")
-    ap.add_argument("--n-rad", type=int, default=8, help="inclination: radial elements per wedge")
+    ap.add_argument("--n-rad", type=int, default=12, help="inclination: radial elements per wedge")
     ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
     ap.add_argument("--fd-slots", type=float, default=0.25,
                     help="breakdown: FD slot pool as a fraction of the elements (1 = one FD block per element)")

@@ -323,8 +323,13 @@ def test_hybrid_luminosity_gradient_matches_central_differences(ffe):
         d1 = (lb(2 * h) - lb(-2 * h)) / (4 * h)
         d2 = (lb(h) - lb(-h)) / (2 * h)
         fd = (4.0 * d2 - d1) / 3.0
-        # difference quotients of Lbar over the hybrid evolution repeat to ~1e-6
-        assert abs(g[k] - fd) <= 3e-6 * abs(fd), (name, g[k], fd)
+        # difference quotients of Lbar over the hybrid evolution repeat to
+        # ~1e-6; where the map has kinks within 2h (WENO weights, stiff-solve
+        # branches) the two quotients disagree, and their spread bounds the
+        # error of the extrapolated one (the exact frozen-map derivative is the
+        # oracle's complex step, next test)
+        tol = max(3e-6 * abs(fd), 3.0 * abs(d2 - d1))
+        assert abs(g[k] - fd) <= tol, (name, g[k], fd, d1, d2)
 
 
 def test_hybrid_luminosity_gradient_matches_oracle_complex_step(ffe):
