@@ -323,6 +323,12 @@ def run_inclination(args):
             inf = ctx.info()
             series[i].append({"t": inf.t, "L": ctx.diagnostic("luminosity", (r_L,))[0],
                               "fd_elements": inf.n_fd_elem})
+        el = time.perf_counter() - t0
+        print(json.dumps({"progress_t": series[0][-1]["t"], "wall_s": round(el, 1),
+                          "L": [ser[-1]["L"] for ser in series],
+                          "fd_elements": [ser[-1]["fd_elements"] for ser in series]}), file=sys.stderr, flush=True)
+        if el > args.wall_budget:
+            break
     for s in streams:
         torch.cuda.current_stream().wait_stream(s)
     e1.record(torch.cuda.current_stream())
@@ -330,8 +336,9 @@ def run_inclination(args):
     ms = e0.elapsed_time(e1)
     wall = time.perf_counter() - t0
     rows = []
+    reached = series[0][-1]["t"] / period
     for chi, ctx, ser in zip(args.chis, ctxs, series):
-        tail = [p["L"] for p in ser if p["t"] >= (args.periods - 0.5) * period - 1e-9]
+        tail = [p["L"] for p in ser if p["t"] >= (reached - 0.5) * period - 1e-9]
         rows.append({"chi_deg": chi, "L_end": ser[-1]["L"], "L_mean_last_half_period": float(np.mean(tail)),
                      "fd_elements_end": ser[-1]["fd_elements"], "status_bits": ctx.status(), "series": ser})
     L = np.array([r["L_mean_last_half_period"] for r in rows])
@@ -344,7 +351,8 @@ def run_inclination(args):
             "value": float(k2), "unit": "k2 of L = L0 (k1 + k2 sin^2 chi)", "k1": float(k1), "k2": float(k2),
             "L0_over_4pi_mu2_omega4": float(L[i0] / (4.0 * math.pi * mu ** 2 * (1.0 / r_lc) ** 4)),
             "n_gpus": 1, "higher_is_better": None, "dtype": "f64", "data": "synthetic",
-            "steps": n_total, "dt": dt, "ms_per_step_all_contexts": ms / max(done - 1, 1), "wall_s": wall,
+            "steps": done, "steps_planned": n_total, "periods_reached": reached, "dt": dt,
+            "ms_per_step_all_contexts": ms / max(done - 1, 1), "wall_s": wall,
             "node_updates_per_s": units / (ms / 1e3),
             "config": {"workload": f"oblique rotator: star R=1, mu=1, delta=0.1, Omega=1/5, eta=1e5, 6 wedges x "
                                    f"{args.n_ang}x{args.n_ang}x{args.n_rad}, P=5, r in [1, 20], CFL 0.25, "
@@ -854,6 +862,8 @@ def main():
     ap.add_argument("--chis", type=float, nargs="+", default=[0.0, 30.0, 60.0, 90.0],
                     help="inclination: magnetic inclinations in degrees")
     ap.add_argument("--periods", type=float, default=2.0, help="inclination: rotation periods to evolve")
+    ap.add_argument("--wall-budget", type=float, default=900.0,
+                    help="inclination: stop at the first eighth of a period after this many seconds")
     ap.add_argument("--n-ang", type=int, default=4, help="inclination: angular elements per wedge side")
     ap.add_argument("--n-rad", type=int, default=12, help="inclination: radial elements per wedge")
     ap.add_argument("--fd-capacity", type=float, default=0.5, help="pulsars: FD slots as a fraction of elements")
