@@ -278,7 +278,7 @@ def run_inclination(args):
     IV.C.2): rotating conducting star of radius R = 1 with the regularised
     dipole (mu = 1, delta = 0.1 R), Omega = 1/(5 R), eta = 1e5 / R, on a
     6-wedge shell r in [R, 20 R] (n_ang x n_ang x n_rad per wedge, P = 5, CFL
-    0.25, indicator on); one context per inclination chi, all advanced
+    0.25, indicator on unless --no-tci); one context per inclination chi, all advanced
     together on their own CUDA streams, for two rotation periods; L through
     r = 6 R (FFE_DIAG_LUMINOSITY) every eighth of a period.  Fits
     L = L0 (k1 + k2 sin^2 chi) with L0 = L(chi = 0) (least squares over the
@@ -298,6 +298,8 @@ def run_inclination(args):
     for chi in args.chis:
         cfg = W.pulsar(r_lc=r_lc, chi=math.radians(chi), n_ang=args.n_ang, n_rad=args.n_rad, P=5, mu=mu,
                        r_out=4.0 * r_lc)
+        if args.no_tci:
+            cfg["params"]["tci_on"] = 0
         s = torch.cuda.Stream()
         ctx = ffe.Context(cfg, stream=s)
         ctx.set_initial()
@@ -356,7 +358,8 @@ def run_inclination(args):
             "node_updates_per_s": units / (ms / 1e3),
             "config": {"workload": f"oblique rotator: star R=1, mu=1, delta=0.1, Omega=1/5, eta=1e5, 6 wedges x "
                                    f"{args.n_ang}x{args.n_ang}x{args.n_rad}, P=5, r in [1, 20], CFL 0.25, "
-                                   f"indicator on, {args.periods} periods, L at r=6",
+                                   f"indicator {'off (DG and filter only)' if args.no_tci else 'on'}, "
+                                   f"{args.periods} periods, L at r=6",
                        "inclinations_deg": args.chis, "contexts": "one per inclination, concurrent streams"},
             "runs": rows}
     for c in ctxs:
@@ -862,6 +865,8 @@ def main():
     ap.add_argument("--chis", type=float, nargs="+", default=[0.0, 30.0, 60.0, 90.0],
                     help="inclination: magnetic inclinations in degrees")
     ap.add_argument("--periods", type=float, default=2.0, help="inclination: rotation periods to evolve")
+    ap.add_argument("--no-tci", action="store_true",
+                    help="inclination: indicator off, every element on DG (with the filter)")
     ap.add_argument("--wall-budget", type=float, default=900.0,
                     help="inclination: stop at the first eighth of a period after this many seconds")
     ap.add_argument("--n-ang", type=int, default=4, help="inclination: angular elements per wedge side")
