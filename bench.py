@@ -294,23 +294,45 @@ def run_inclination(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     r_lc, mu, r_L = 5.0, 1.0, 6.0
     period = 2.0 * math.pi * r_lc
-    ctxs, streams = [], []
+    cfgs = []
     for chi in args.chis:
         cfg = W.pulsar(r_lc=r_lc, chi=math.radians(chi), n_ang=args.n_ang, n_rad=args.n_rad, P=5, mu=mu,
                        r_out=4.0 * r_lc)
         if args.no_tci:
             cfg["params"]["tci_on"] = 0
-        s = torch.cuda.Stream()
-        ctx = ffe.Context(cfg, stream=s)
-        ctx.set_initial()
-        ctx.step(1)            # first step: launch-shape tuning, alone on the GPU
+        cfgs.append(cfg)
+    ctxs, streams = [], []
+    if args.batch:
+        # every inclination an instance of one batched context: one launch per
+        # kernel and substep for all of them
+        b = ffe.BatchContext(cfgs, fd_capacity=1 if args.no_tci else 0)
+        b.set_initial()
+        b.step(1)
         torch.cuda.synchronize()
-        ctxs.append(ctx)
-        streams.append(s)
-    dt = ctxs[0].dt
+        ctxs.append(b)
+        streams.append(b.stream)
+        first = b.layout()[3]
+
+        def sample(i):
+            L_i = b.diagnostic("luminosity", (r_L, i))[0]   # synchronises the batch's stream
+            m = b.mask().cpu().numpy()
+            return L_i, int(m[first[i]:first[i + 1]].sum())
+    else:
+        for cfg in cfgs:
+            s = torch.cuda.Stream()
+            ctx = ffe.Context(cfg, stream=s)
+            ctx.set_initial()
+            ctx.step(1)            # first step: launch-shape tuning, alone on the GPU
+            torch.cuda.synchronize()
+            ctxs.append(ctx)
+            streams.append(s)
+
+        def sample(i):
+            return ctxs[i].diagnostic("luminosity", (r_L,))[0], ctxs[i].info().n_fd_elem
+    dt = ctxs[0].dt   # the instances differ only in chi: one grid, one time step
     n_total = int(round(args.periods * period / dt))
     marks = [int(round(k * period / 8 / dt)) for k in range(1, int(round(8 * args.periods)) + 1)]
-    series = [[] for _ in ctxs]
+    series = [[] for _ in cfgs]
     done, t0 = 1, time.perf_counter()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(torch.cuda.current_stream())
@@ -321,10 +343,10 @@ def run_inclination(args):
             for ctx in ctxs:
                 ctx.step(min(16, m - k))
         done = m
-        for i, ctx in enumerate(ctxs):
-            inf = ctx.info()
-            series[i].append({"t": inf.t, "L": ctx.diagnostic("luminosity", (r_L,))[0],
-                              "fd_elements": inf.n_fd_elem})
+        t_now = ctxs[0].info().t
+        for i in range(len(cfgs)):
+            L_i, nfd_i = sample(i)
+            series[i].append({"t": t_now, "L": L_i, "fd_elements": nfd_i})
         el = time.perf_counter() - t0
         print(json.dumps({"progress_t": series[0][-1]["t"], "wall_s": round(el, 1),
                           "L": [ser[-1]["L"] for ser in series],
@@ -339,10 +361,12 @@ def run_inclination(args):
     wall = time.perf_counter() - t0
     rows = []
     reached = series[0][-1]["t"] / period
-    for chi, ctx, ser in zip(args.chis, ctxs, series):
+    status = [c.status() for c in ctxs]
+    for i, (chi, ser) in enumerate(zip(args.chis, series)):
         tail = [p["L"] for p in ser if p["t"] >= (reached - 0.5) * period - 1e-9]
         rows.append({"chi_deg": chi, "L_end": ser[-1]["L"], "L_mean_last_half_period": float(np.mean(tail)),
-                     "fd_elements_end": ser[-1]["fd_elements"], "status_bits": ctx.status(), "series": ser})
+                     "fd_elements_end": ser[-1]["fd_elements"],
+                     "status_bits": status[0] if args.batch else status[i], "series": ser})
     L = np.array([r["L_mean_last_half_period"] for r in rows])
     chis = np.radians(np.array(args.chis))
     i0 = int(np.argmin(np.abs(chis)))
@@ -360,7 +384,9 @@ def run_inclination(args):
                                    f"{args.n_ang}x{args.n_ang}x{args.n_rad}, P=5, r in [1, 20], CFL 0.25, "
                                    f"indicator {'off (DG and filter only)' if args.no_tci else 'on'}, "
                                    f"{args.periods} periods, L at r=6",
-                       "inclinations_deg": args.chis, "contexts": "one per inclination, concurrent streams"},
+                       "inclinations_deg": args.chis,
+                       "contexts": "one batched context, an instance per inclination" if args.batch
+                       else "one per inclination, concurrent streams"},
             "runs": rows}
     for c in ctxs:
         c.close()
@@ -865,6 +891,8 @@ def main():
     ap.add_argument("--chis", type=float, nargs="+", default=[0.0, 30.0, 60.0, 90.0],
                     help="inclination: magnetic inclinations in degrees")
     ap.add_argument("--periods", type=float, default=2.0, help="inclination: rotation periods to evolve")
+    ap.add_argument("--batch", action="store_true",
+                    help="inclination: all inclinations as instances of one batched context")
     ap.add_argument("--no-tci", action="store_true",
                     help="inclination: indicator off, every element on DG (with the filter)")
     ap.add_argument("--wall-budget", type=float, default=900.0,

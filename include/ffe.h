@@ -162,7 +162,8 @@ ffe_status ffe_create(const ffe_domain* domain, const ffe_elements* elements, in
  * P[i] in {3, 4, 5} and parameters params[i] (time step from its own CFL
  * condition, star rotation omega_star); every other scheme parameter must
  * equal params[0].  All instances advance together: one launch per kernel and
- * substep covers every element of every instance, whatever its order.
+ * substep covers every element of every instance (the DG substep kernel: one
+ * launch per element order present, each in CTAs sized for its order).
  * fd_capacity bounds the number of elements on FD subcells at any time
  * (0 = every element); an element the indicator flags when no FD slot is left
  * stays on DG and status bit 2 is raised.  State layout: every element owns a
@@ -344,7 +345,8 @@ ffe_status ffe_adjoint_reverse(ffe_ctx* ctx, const double* U_dev, const double* 
  * IV.C.2; the sphere |x| = r_L unless shell_ks): L = closed integral of
  * (E x B).n^ dA on the radial element layer containing r_L (xi^3
  * interpolation, LGL quadrature, exact area element and outward normal).  *L_host receives L;
- * when grad_dev is not NULL, scale * dL/dU is added to it. */
+ * when grad_dev is not NULL, scale * dL/dU is added to it.  Single contexts
+ * (batches: FFE_DIAG_LUMINOSITY with an instance index). */
 ffe_status ffe_luminosity(ffe_ctx* ctx, const double* U_dev, double r_L, double* L_host, double* grad_dev,
                           double scale);
 
@@ -403,7 +405,12 @@ ffe_status ffe_set_frozen_masks(ffe_ctx* ctx, int on);
  *                        device until the mask or the initial data change; the
  *                        sum is reduced on the device (deterministic).
  *   FFE_DIAG_LUMINOSITY  args[0] = r_L: out_host[0] = the luminosity of
- *                        ffe_luminosity through r = r_L (shells).
+ *                        ffe_luminosity through r = r_L (shells).  Batched
+ *                        contexts: args[1] = the instance (an integer index),
+ *                        whose shell and elements the surface covers; the
+ *                        instance must have the batch's top order
+ *                        (FFE_ENOTIMPL else).  A radius outside the shell is
+ *                        FFE_EINVAL.
  *   FFE_DIAG_CONSTRAINTS out_host[0..3] as ffe_constraints (flat metric).
  *   FFE_DIAG_BFLUX_UPPER args[0] = R: out_host[0] = the magnetic flux of B~
  *                        through the upper half (z > 0) of the shell's
@@ -416,7 +423,8 @@ ffe_status ffe_set_frozen_masks(ffe_ctx* ctx, int on);
  *                        of spheres R = sqrt(r+^2 + a^2) gives the same flux
  *                        (same equator), the quantity of Sec. IV.B.2.
  *                        Shells with n[0] even
- *                        (the equator on element boundaries), FFE_EINVAL else. */
+ *                        (the equator on element boundaries), FFE_EINVAL else;
+ *                        batched contexts take args[1] as for the luminosity. */
 enum { FFE_DIAG_L2_ERR = 0, FFE_DIAG_LUMINOSITY = 1, FFE_DIAG_CONSTRAINTS = 2, FFE_DIAG_BFLUX_UPPER = 3 };
 ffe_status ffe_diagnostic(ffe_ctx* ctx, int kind, const double* args, double* out_host);
 

@@ -7,7 +7,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <exception>
+#include <map>
 #include <string>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -374,18 +376,15 @@ struct ffe_ctx {
     std::vector<unsigned char> ref_mask;
     std::vector<int> ref_slot;
     double* d_partial = nullptr;
-    // luminosity surface (cached per radius)
-    double lum_r = -1.0;
-    int lum_ns = 0;
-    int* d_lum_elem = nullptr;
-    double* d_lum_lk = nullptr;
-    double* d_lum_w = nullptr;
-    // upper-hemisphere magnetic flux surface (cached per radius)
-    double flux_r = -1.0;
-    int flux_ns = 0;
-    int* d_flux_elem = nullptr;
-    double* d_flux_lk = nullptr;
-    double* d_flux_w = nullptr;
+    // surface quadratures of the luminosity and the upper-half magnetic flux,
+    // cached per (radius, upper half only, instance of a batch or -1)
+    struct Surf {
+        int ns = 0;
+        int* elem = nullptr;
+        double* lk = nullptr;
+        double* w = nullptr;
+    };
+    std::map<std::tuple<double, int, int>, Surf> surf;
 };
 
 namespace {
@@ -1284,11 +1283,22 @@ ffe_status build_reference(ffe_ctx* c) {
 // area element and the outward unit normal, wn[4] = (w_i w_j |a1 x a2|,
 // (a1 x a2)/|a1 x a2|), a_k = dx/dxi^k (on a sphere the normal is r^).  upper:
 // only the elements whose centre has z > 0 (the equator must then lie on
-// element boundaries).
-void surface_setup(ffe_ctx* c, double r, bool upper, std::vector<int>& elem, std::vector<double>& lk,
+// element boundaries).  inst >= 0: the shell of that instance of a batch (its
+// elements e0 .. e0 + 6 na^2 nr - 1, at the batch's top order).
+void surface_setup(ffe_ctx* c, double r, bool upper, int inst, std::vector<int>& elem, std::vector<double>& lk,
                    std::vector<double>& wn) {
     const Dev& d = c->d;
-    const ShellGeo g = c->shell;
+    ShellGeo g = c->shell;
+    int e0 = 0, ne = d.E;
+    const Tables* tb = &c->tab;
+    if (inst >= 0) {
+        const InstInfo& in = c->insts[inst];
+        g = ShellGeo{in.r_in, in.c, in.na, in.nr};
+        e0 = in.e0;
+        ne = 6 * in.na * in.na * in.nr;
+        tb = &c->tabs_h[in.P];
+    }
+    const Tables& T = *tb;
     const double er = std::log(r / g.r_in) / g.c - 1.0;
     const double pos = (er + 1.0) / 2.0 * g.nr;
     int ir = (int)std::floor(pos);
@@ -1299,10 +1309,10 @@ void surface_setup(ffe_ctx* c, double r, bool upper, std::vector<int>& elem, std
     for (int k = 0; k < np1; ++k) {
         double v = 1.0;
         for (int m = 0; m < np1; ++m)
-            if (m != k) v *= (xr - c->tab.x[m]) / (c->tab.x[k] - c->tab.x[m]);
+            if (m != k) v *= (xr - T.x[m]) / (T.x[k] - T.x[m]);
         lk[k] = v;
     }
-    for (int e = 0; e < d.E; ++e) {
+    for (int e = 0; e < ne; ++e) {
         int ia, ib, irr, w;
         shell_elem(g, e, ia, ib, irr, w);
         if (irr != ir) continue;
@@ -1312,10 +1322,10 @@ void surface_setup(ffe_ctx* c, double r, bool upper, std::vector<int>& elem, std
             shell_map(g, e, xi0, x0, ij0);
             if (!(x0[2] > 0.0)) continue;
         }
-        elem.push_back(e);
+        elem.push_back(e0 + e);
         for (int j = 0; j < np1; ++j)
             for (int i = 0; i < np1; ++i) {
-                const double xi[3] = {c->tab.x[i], c->tab.x[j], xr};
+                const double xi[3] = {T.x[i], T.x[j], xr};
                 double x[3], ij[3][3];
                 shell_map(g, e, xi, x, ij);
                 // area element |dx/dxi1 x dx/dxi2| from the Jacobian (inverse of ij)
@@ -1335,12 +1345,83 @@ void surface_setup(ffe_ctx* c, double r, bool upper, std::vector<int>& elem, std
                 // orientation (det > 0); flip it otherwise
                 const double area = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
                 const double sg = det > 0.0 ? 1.0 : -1.0;
-                wn.push_back(c->tab.w[i] * c->tab.w[j] * area);
+                wn.push_back(T.w[i] * T.w[j] * area);
                 wn.push_back(sg * cr[0] / area);
                 wn.push_back(sg * cr[1] / area);
                 wn.push_back(sg * cr[2] / area);
             }
     }
+}
+
+// The quadrature of surface_setup on the device, built once per (r, upper, inst).
+ffe_status surface_get(ffe_ctx* c, double r, bool upper, int inst, const ffe_ctx::Surf** out) {
+    const auto key = std::make_tuple(r, upper ? 1 : 0, inst);
+    auto it = c->surf.find(key);
+    if (it == c->surf.end()) {
+        std::vector<int> elem;
+        std::vector<double> lk, wn;
+        surface_setup(c, r, upper, inst, elem, lk, wn);
+        ffe_ctx::Surf sf;
+        ffe_status s;
+        if ((s = dalloc(c, &sf.elem, elem.size()))) return s;
+        if ((s = dalloc(c, &sf.lk, lk.size()))) return s;
+        if ((s = dalloc(c, &sf.w, wn.size()))) return s;
+        CK(cudaMemcpy(sf.elem, elem.data(), elem.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(sf.lk, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(sf.w, wn.data(), wn.size() * 8, cudaMemcpyHostToDevice));
+        sf.ns = (int)elem.size();
+        it = c->surf.emplace(key, sf).first;
+    }
+    *out = &it->second;
+    return FFE_OK;
+}
+
+// Sum of the surface integrand (bflux = 1: B~.n, else (E~ x B~).n) of U over
+// sf, into *out_host when it is not NULL (synchronising the context stream);
+// grad_dev (may be NULL) receives scale * d(sum)/dU.
+ffe_status surface_sum(ffe_ctx* c, const ffe_ctx::Surf& sf, const double* U_dev, int bflux, double* grad_dev,
+                       double scale, double* out_host) {
+    const Dev& d = c->d;
+    ffe_status s;
+    if (!c->d_partial && (s = dalloc(c, &c->d_partial, 1024))) return s;
+    Field U{(double*)U_dev, NV, d.ndg, d.nfd}, G{grad_dev, NV, d.ndg, d.nfd};
+    const int nb = d.nsm;
+    launch_luminosity(d, U, sf.elem, sf.lk, sf.w, sf.ns, c->d_partial, nb, G, scale, c->st, bflux);
+    if (out_host) {
+        std::vector<double> part(nb);
+        CK(cudaMemcpyAsync(part.data(), c->d_partial, nb * 8, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        double sum = 0.0;
+        for (double v : part) sum += v;
+        *out_host = sum;
+    }
+    CK(cudaGetLastError());
+    return FFE_OK;
+}
+
+// The shell a surface diagnostic integrates over: the context's, or with a
+// batch the instance args[1] (an integer index, required), which must run at
+// the batch's top order; r must lie strictly inside that shell.
+ffe_status surface_target(ffe_ctx* c, const double* args, double r, int* inst, int* na) {
+    const Dev& d = c->d;
+    if (!d.curved || (!c->batch && c->dom.kind != FFE_DOMAIN_SHELL6))
+        return fail(FFE_ENOTIMPL, "surface diagnostics need a shell");
+    double r_in = c->dom.r_in, r_out = c->dom.r_out;
+    *inst = -1;
+    *na = c->shell.na;
+    if (c->batch) {
+        const double a1 = args[1];
+        if (!(a1 >= 0 && a1 < (double)c->insts.size()) || a1 != std::floor(a1))
+            return fail(FFE_EINVAL, "a batched context needs args[1] = an instance index in [0, %d)", (int)c->insts.size());
+        const InstInfo& in = c->insts[(int)a1];
+        if (in.P != d.P) return fail(FFE_ENOTIMPL, "surface diagnostics of instances below the batch's top order P = %d", d.P);
+        *inst = (int)a1;
+        *na = in.na;
+        r_in = in.r_in;
+        r_out = in.r_in * std::exp(2.0 * in.c);
+    }
+    if (!(r > r_in && r < r_out)) return fail(FFE_EINVAL, "radius %g outside the shell (%g, %g)", r, r_in, r_out);
+    return FFE_OK;
 }
 
 }  // namespace
@@ -1557,42 +1638,17 @@ ffe_status ffe_diagnostic(ffe_ctx* c, int kind, const double* args, double* out_
     if (!c || !out_host) return fail(FFE_EINVAL, "null argument");
     const Dev& d = c->d;
     if (kind == FFE_DIAG_CONSTRAINTS) return ffe_constraints(c, nullptr, out_host);
-    if (kind == FFE_DIAG_BFLUX_UPPER) {
-        if (!args) return fail(FFE_EINVAL, "the flux needs args[0] = R");
+    if (kind == FFE_DIAG_BFLUX_UPPER || kind == FFE_DIAG_LUMINOSITY) {
+        if (!args) return fail(FFE_EINVAL, "surface diagnostics need args[0] = the radius");
         const double R = args[0];
-        if (!d.curved || c->batch || c->dom.kind != FFE_DOMAIN_SHELL6) return fail(FFE_ENOTIMPL, "the flux needs a shell");
-        if (!(R > c->dom.r_in && R < c->dom.r_out)) return fail(FFE_EINVAL, "R outside the shell");
-        if (c->shell.na % 2) return fail(FFE_EINVAL, "the equator lies on element boundaries only for even n_ang");
+        int inst, na;
         ffe_status s;
-        if (c->flux_r != R) {
-            std::vector<int> elem;
-            std::vector<double> lk, wn;
-            surface_setup(c, R, true, elem, lk, wn);
-            if ((s = dalloc(c, &c->d_flux_elem, elem.size()))) return s;
-            if ((s = dalloc(c, &c->d_flux_lk, lk.size()))) return s;
-            if ((s = dalloc(c, &c->d_flux_w, wn.size()))) return s;
-            CK(cudaMemcpy(c->d_flux_elem, elem.data(), elem.size() * sizeof(int), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(c->d_flux_lk, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(c->d_flux_w, wn.data(), wn.size() * 8, cudaMemcpyHostToDevice));
-            c->flux_ns = (int)elem.size();
-            c->flux_r = R;
-        }
-        if (!c->d_partial && (s = dalloc(c, &c->d_partial, 1024))) return s;
-        const int nb = d.nsm;
-        Field U{c->un.p, NV, d.ndg, d.nfd}, G{nullptr, NV, d.ndg, d.nfd};
-        launch_luminosity(d, U, c->d_flux_elem, c->d_flux_lk, c->d_flux_w, c->flux_ns, c->d_partial, nb, G, 0.0,
-                          c->st, 1);
-        std::vector<double> part(nb);
-        CK(cudaMemcpyAsync(part.data(), c->d_partial, nb * 8, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        double sum = 0.0;
-        for (double v : part) sum += v;
-        out_host[0] = sum;
-        return FFE_OK;
-    }
-    if (kind == FFE_DIAG_LUMINOSITY) {
-        if (!args) return fail(FFE_EINVAL, "the luminosity needs args[0] = r_L");
-        return ffe_luminosity(c, c->un.p, args[0], out_host, nullptr, 0.0);
+        if ((s = surface_target(c, args, R, &inst, &na))) return s;
+        const bool upper = kind == FFE_DIAG_BFLUX_UPPER;
+        if (upper && na % 2) return fail(FFE_EINVAL, "the equator lies on element boundaries only for even n_ang");
+        const ffe_ctx::Surf* sf;
+        if ((s = surface_get(c, R, upper, inst, &sf))) return s;
+        return surface_sum(c, *sf, c->un.p, upper ? 1 : 0, nullptr, 0.0, out_host);
     }
     if (kind != FFE_DIAG_L2_ERR) return fail(FFE_EINVAL, "diagnostic kind %d", kind);
     int v0 = 3, nv = 3;
@@ -2507,37 +2563,13 @@ ffe_status ffe_luminosity(ffe_ctx* c, const double* U_dev, double r_L, double* L
                           double scale) try {
     g_err.clear();
     if (!c || !U_dev) return fail(FFE_EINVAL, "null argument");
-    const Dev& d = c->d;
-    if (!d.curved || c->batch || c->dom.kind != FFE_DOMAIN_SHELL6) return fail(FFE_ENOTIMPL, "luminosity needs a shell");
-    if (!(r_L > c->dom.r_in && r_L < c->dom.r_out)) return fail(FFE_EINVAL, "r_L outside the shell");
+    if (c->batch) return fail(FFE_ENOTIMPL, "ffe_luminosity takes single contexts (batches: ffe_diagnostic)");
+    int inst, na;
     ffe_status s;
-    if (c->lum_r != r_L) {
-        std::vector<int> elem;
-        std::vector<double> lk, wn;
-        surface_setup(c, r_L, false, elem, lk, wn);
-        if ((s = dalloc(c, &c->d_lum_elem, elem.size()))) return s;
-        if ((s = dalloc(c, &c->d_lum_lk, lk.size()))) return s;
-        if ((s = dalloc(c, &c->d_lum_w, wn.size()))) return s;
-        CK(cudaMemcpy(c->d_lum_elem, elem.data(), elem.size() * sizeof(int), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c->d_lum_lk, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c->d_lum_w, wn.data(), wn.size() * 8, cudaMemcpyHostToDevice));
-        c->lum_ns = (int)elem.size();
-        c->lum_r = r_L;
-    }
-    if (!c->d_partial && (s = dalloc(c, &c->d_partial, 1024))) return s;
-    Field U{(double*)U_dev, NV, d.ndg, d.nfd}, G{grad_dev, NV, d.ndg, d.nfd};
-    const int nb = d.nsm;
-    launch_luminosity(d, U, c->d_lum_elem, c->d_lum_lk, c->d_lum_w, c->lum_ns, c->d_partial, nb, G, scale, c->st);
-    if (L_host) {
-        std::vector<double> part(nb);
-        CK(cudaMemcpyAsync(part.data(), c->d_partial, nb * 8, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        double sum = 0.0;
-        for (double v : part) sum += v;
-        *L_host = sum;
-    }
-    CK(cudaGetLastError());
-    return FFE_OK;
+    if ((s = surface_target(c, nullptr, r_L, &inst, &na))) return s;
+    const ffe_ctx::Surf* sf;
+    if ((s = surface_get(c, r_L, false, -1, &sf))) return s;
+    return surface_sum(c, *sf, U_dev, 0, grad_dev, scale, L_host);
 } catch (...) {
     return host_failure();
 }

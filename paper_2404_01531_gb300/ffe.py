@@ -367,7 +367,15 @@ class Context:
 
     def diagnostic(self, kind, args=None):
         """ffe_diagnostic: "l2_err" (args (v0, nv), default B~) -> (L2, n points),
-        "luminosity" (args (r_L,)) -> (L,), "constraints" -> the 4 values of constraints()."""
+        "luminosity" (args (r_L,)) -> (L,), "bflux_upper" (args (R,)) -> (flux,),
+        "constraints" -> the 4 values of constraints().  A batched context's
+        luminosity and flux take (radius, instance index)."""
+        if isinstance(self, BatchContext) and kind in ("luminosity", "bflux_upper") and (not args or len(args) != 2):
+            raise ValueError("a batched context's surface diagnostic takes (radius, instance)")
+        if kind == "l2_err" and args is not None and len(args) != 2:
+            raise ValueError("l2_err takes (v0, nv)")
+        if kind in ("luminosity", "bflux_upper") and not args:
+            raise ValueError(kind + " takes (radius,)")
         out = (ctypes.c_double * 4)()
         a = (ctypes.c_double * len(args))(*args) if args else None
         check(load().ffe_diagnostic(self.h, DIAG[kind], a, out))

@@ -107,3 +107,31 @@ def test_full_batch_equals_single_contexts_over_ten_steps(ffe):
             assert rel_err_split(udg_b, dgs, ufd_b, fds, ms == 0).max() <= 1e-10, i
         s.close()
     b.close()
+
+
+def test_surface_diagnostics_of_a_batch_instance_equal_the_single_context(ffe):
+    """FFE_DIAG_LUMINOSITY and FFE_DIAG_BFLUX_UPPER on instance 0 of the batch
+    (a P = 5 shell; instance 1 has P = 4) after 3 steps equal those of the same shell advanced
+    alone; instances below the batch's top order, a missing or foreign
+    instance index and a radius outside the instance's shell are refused."""
+    cfgs = [W.pulsar(r_lc=3.0, chi=0.4, n_ang=2, n_rad=4, P=5, r_out=6.0),
+            W.pulsar(r_lc=3.5, chi=0.2, n_ang=1, n_rad=4, P=4, r_out=5.0)]
+    b = ffe.BatchContext(cfgs)
+    b.set_initial()
+    b.step(3)
+    s = ffe.Context(cfgs[0])
+    s.set_initial()
+    s.step(3)
+    for kind, r in (("luminosity", 2.5), ("luminosity", 3.7), ("bflux_upper", 2.0)):
+        (vb,) = b.diagnostic(kind, (r, 0))
+        (vs,) = s.diagnostic(kind, (r,))
+        assert abs(vb - vs) <= 1e-10 * abs(vs) + 1e-300, (kind, r, vb, vs)
+    with pytest.raises(ffe.FFEError, match="FFE_ENOTIMPL"):
+        b.diagnostic("luminosity", (2.5, 1))
+    with pytest.raises(ValueError):
+        b.diagnostic("luminosity", (2.5,))
+    for bad in ((2.5, 7), (2.5, 0.5), (9.0, 0)):
+        with pytest.raises(ffe.FFEError, match="FFE_EINVAL"):
+            b.diagnostic("luminosity", bad)
+    s.close()
+    b.close()
