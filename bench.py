@@ -239,47 +239,37 @@ def run_wald_vacuum(args):
     import torch
     from paper_2404_01531_gb300 import ffe
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    # one context per spin, each on its own CUDA stream, advanced together
-    runs = []
+    rows = []
     for a in args.spins:
         cfg = W.wald_vacuum(spin=a)
-        ctx = ffe.Context(cfg, stream=torch.cuda.Stream())
+        ctx = ffe.Context(cfg)
         ctx.set_initial()
+        dt = ctx.dt
         rp = 1.0 + math.sqrt(1.0 - a * a)
+        king = math.pi * rp * rp * (1.0 - a ** 4 / rp ** 4)
         flux0 = ctx.diagnostic("bflux_upper", (rp,))[0]
-        ctx.step(1)            # first step: launch-shape tuning, alone on the GPU
+        series, done = [], 0
+        t0 = time.perf_counter()
+        for tt in (25.0, 50.0, 75.0, 100.0, cfg["t_end"]):
+            n = int(round(tt / dt))
+            ctx.step(n - done)
+            done = n
+            series.append({"t": n * dt, "flux": ctx.diagnostic("bflux_upper", (rp,))[0],
+                           "rms_psi": ctx.diagnostic("l2_err", (6, 1))[0],
+                           "rms_phi": ctx.diagnostic("l2_err", (7, 1))[0]})
         torch.cuda.synchronize()
-        runs.append(dict(a=a, cfg=cfg, ctx=ctx, rp=rp, done=1, series=[],
-                         king=math.pi * rp * rp * (1.0 - a ** 4 / rp ** 4), flux0=flux0))
-    t0 = time.perf_counter()
-    for tt in (25.0, 50.0, 75.0, 100.0, runs[0]["cfg"]["t_end"]):
-        targets = [int(round(tt / r["ctx"].dt)) for r in runs]
-        while any(r["done"] < n for r, n in zip(runs, targets)):
-            for r, n in zip(runs, targets):
-                k = min(16, n - r["done"])
-                if k > 0:
-                    r["ctx"].step(k)
-                    r["done"] += k
-        for r in runs:
-            ctx, rp = r["ctx"], r["rp"]
-            r["series"].append({"t": r["done"] * ctx.dt, "flux": ctx.diagnostic("bflux_upper", (rp,))[0],
-                                "rms_psi": ctx.diagnostic("l2_err", (6, 1))[0],
-                                "rms_phi": ctx.diagnostic("l2_err", (7, 1))[0]})
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    rows = []
-    for r in runs:
-        rows.append({"spin": r["a"], "r_plus": r["rp"], "dt": r["ctx"].dt, "steps": r["done"], "king": r["king"],
-                     "flux_t0": r["flux0"], "series": r["series"],
-                     "rel_err_end": r["series"][-1]["flux"] / r["king"] - 1.0, "status_bits": r["ctx"].status()})
-        r["ctx"].close()
+        wall = time.perf_counter() - t0
+        rows.append({"spin": a, "r_plus": rp, "dt": dt, "steps": done, "king": king, "flux_t0": flux0,
+                     "series": series, "rel_err_end": series[-1]["flux"] / king - 1.0, "wall_s": wall,
+                     "status_bits": ctx.status()})
+        ctx.close()
     line = {"metric": "horizon magnetic flux / closed form, vacuum Wald (Sec. IV.B.2)",
             "value": max(abs(r["rel_err_end"]) for r in rows), "unit": "max relative deviation at t_end",
             "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "vacuum Wald: Kerr-Schild M=1, Wald B with E=0 at t=0, eta=0, 6 wedges x 4x4x16, "
                                    "P=5, spherical Kerr-Schild r in [1, 125], outflow between the horizons, no "
                                    "incoming Poynting flux outside, t_end = 125"},
-            "wall_s": wall, "contexts": "one per spin, concurrent streams", "runs": rows}
+            "runs": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -896,7 +886,7 @@ def main():
     ap.add_argument("--recon", default="weno5z", choices=list(RECON),
                     help="breakdown and shell: FD reconstruction (the paper's WENO5-Z, or MP5)")
     ap.add_argument("--n-inst", type=int, default=32)
-    ap.add_argument("--spins", type=float, nargs="+", default=[0.0, 0.3, 0.5, 0.7, 0.8, 0.9, 0.95, 0.99, 0.999],
+    ap.add_argument("--spins", type=float, nargs="+", default=[0.0, 0.5, 0.7, 0.9, 0.999],
                     help="wald_vacuum: black-hole spins")
     ap.add_argument("--chis", type=float, nargs="+", default=[0.0, 30.0, 60.0, 90.0],
                     help="inclination: magnetic inclinations in degrees")
