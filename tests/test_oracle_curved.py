@@ -363,3 +363,47 @@ def test_vacuum_wald_grid_time_step_is_the_papers():
     the spherical Kerr-Schild coordinate, innermost layer at r = M)."""
     pr = Problem(W.wald_vacuum(spin=0.999))
     assert abs(pr.dt - 1.97e-3) < 0.005e-3, pr.dt
+
+
+def test_wedge_face_ghosts_transfer_the_current_so_a_force_free_state_is_eta_independent():
+    """Reading 14 at faces between wedges: an FD neighbour's ghosts carry its
+    cells' current interpolated like its state.  Pin: on an all-FD shell
+    (6 wedges x 1 x 1 x 2, every element touching wedge faces), a state with
+    E~ = -v x B~ (v = 0.1 z^ x x, sub-luminal: E.B = 0 and E^2 < B^2 at every
+    point) has no parallel current anywhere, so its right-hand side must not
+    depend on eta; it agrees at eta = 1e2 and 1e6 to rounding times eta.  The
+    current of the interpolated state instead (planted below in a copy of
+    the oracle's FD operator) takes eta (E.B) of the interpolation error at
+    those ghosts and moves the q~ right-hand side by O(1) at eta = 1e6."""
+    import types
+    import oracle.fd as FD
+    from oracle import physics as ph
+    cfg = W.pulsar(r_lc=3.0, chi=0.3, n_ang=1, n_rad=2, P=5, r_out=4.0)
+    cfg["bc_inner"] = cfg["bc_outer"] = "dirichlet"
+    pr = Problem(cfg)
+    d = pr.disc
+    x = d.xyz_fd
+    U = pr.initial(x.reshape(3, -1)).reshape((9,) + x.shape[1:])
+    v = np.stack([-0.1 * x[1], 0.1 * x[0], 0 * x[0]])
+    U[0:3] = -ph.cross_lower(v, U[3:6])
+    st = dict(mask=np.ones(d.E, dtype=np.uint8), udg=np.zeros((9,) + d.xyz.shape[1:]), ufd=U, t=0.0)
+
+    def spread(mod):
+        out = []
+        for eta in (1e2, 1e6):
+            pr.prm["eta"] = eta
+            out.append(mod.rhs_fd(st, d, pr.met, pr.prm))
+        return np.abs(out[1] - out[0]).max()
+
+    assert spread(FD) < 1e-8
+    src = open(FD.__file__).read()
+    transfer = """                        m = _met_at(met_fn["fd"], np.array([nb]), ())
+                        jd, jp = ph.current(st["ufd"][:, nb:nb + 1], m, prm["eta"])
+                        jgh[(slice(None),) + tgt[1:]] = _interp_fd((jd + jp)[:, 0], xi_nb, T.xc).reshape(
+                            (3,) + ext[tgt].shape[1:])
+"""
+    assert src.count(transfer) == 1
+    mod = types.ModuleType("oracle.fd_state_current")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(src.replace(transfer, ""), "fd_state_current", "exec"), mod.__dict__)
+    assert spread(mod) > 1e-2
