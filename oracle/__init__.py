@@ -17,18 +17,26 @@ links or calls anything here, and nothing here imports the CUDA package.
 Every function cites the passage it follows.  Readings taken where the paper is
 silent are marked ``[reading]`` in the docstrings.
 
-Parity unpinned (no value from the paper or mathematics fixes them; they are
-checked only by GPU-vs-oracle agreement, conservation and convergence):
-  * at a face shared by a DG and an FD element, the exterior current
-    (`dg.external_fd_current`, `fd.fill_ghosts` for J~: the projection of the
-    current, a reading); the exterior state there (`dg.external_dg_state` with
-    an FD neighbour, `fd.fill_ghosts` with a DG neighbour) is pinned by the
-    exactness of the mixed DG/FD right-hand side on linear fields.
-FD ghosts across a neighbour's face: copied from its cells (the default, the
-reading the CUDA path implements) or, with prm["ghost_interp"], interpolated to
-this element's grid extension; only the latter converges between cubed-sphere
-wedges (tests/test_oracle_curved.py).
-The rollback bookkeeping of a substep redone on FD (`stepper`) is pinned the
-same way: on fields linear in x a step with switches after substeps A, B and C
-equals the step without them.
+Parity unpinned in part (no value from the paper fixes which of two
+consistent readings is taken; stability chose, and the implementation of the
+reading is pinned):
+  * the exterior current at an interface (`dg.external_fd_current`,
+    `fd.fill_ghosts` for J~): the neighbour's current transferred like its
+    state, not the current of the transferred state.  Pinned at DG-FD faces
+    by the exactness of the mixed right-hand side with a linear current, and
+    at faces between wedges by the eta-independence of a force-free state
+    (tests/test_oracle_curved.py, tests/test_oracle_schemes.py).
+FD ghosts across a neighbour's face are, by default (prm["ghost_interp"], set
+by Problem, the reading the CUDA path implements), the neighbour's data
+interpolated to this element's grid extension; the neighbour's own cells
+(ghost_interp off) agree inside a wedge and on boxes and are inconsistent
+between cubed-sphere wedges (tests/test_oracle_curved.py).
+The rollback bookkeeping of a substep redone on FD (`stepper`) is pinned on
+fields linear in x: a step with switches after substeps A, B and C equals the
+step without them.  The star boundary state (`physics.bc_star`) is pinned by a
+static dipole that stays put; the shells of the black-hole tests may live in
+spherical Kerr-Schild coordinates (`geometry.ShellMesh(spin=a)`, App. B),
+pinned by the spheroid relation, the paper's time step on the vacuum Wald grid
+and King's horizon flux (`surface`); the exact-Wald errors of Table II are
+reproduced with the outflow face inside the horizon.
 """
