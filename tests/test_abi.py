@@ -237,3 +237,41 @@ def test_fd_rhs_noalloc_wrapper_checks_buffers_before_the_call():
     if not torch.cuda.is_available():
         with pytest.raises((ValueError, RuntimeError, AssertionError)):
             ffe.fd_rhs_noalloc(P, ext, [0.1] * 3, 0.0, 1e-40, 1, good)
+
+
+def test_spherical_kerr_schild_shell_host_checks(lib_path):
+    """shell_ks (the shell in the spherical Kerr-Schild radius, App. B) is a
+    flag of a Kerr-Schild shell only: on a box or a flat shell it is
+    FFE_EINVAL, values other than 0 and 1 are FFE_EINVAL, with the indicator
+    on (FD subcells) FFE_ENOTIMPL; the vacuum Wald workload itself passes the
+    host checks.  Runs without a GPU."""
+    import copy
+    import ctypes
+    import ffe_workloads as W
+    from paper_2404_01531_gb300 import ffe
+    lib = ffe.load()
+    ok = W.wald_vacuum(spin=0.999, n_ang=2, n_rad=2)
+    st, msg, h = _create(ffe, ok)
+    assert st not in (1, 7), msg
+    if st == 0:
+        lib.ffe_destroy(ctypes.c_void_p(h))
+    flat = W.pulsar(n_ang=1, n_rad=2)
+    flat["shell_ks"] = True
+    assert _create(ffe, flat)[0] == 1
+    box = W.fast_wave()
+    box["shell_ks"] = True
+    dom, el = ffe.domain_of(box)
+    dom.shell_ks = 1
+    met = ffe.Metric(ffe.METRIC["kerr_schild"], 1.0, 0.5)
+    prm = ffe.params_from(box["params"])
+    hh = ctypes.c_void_p()
+    assert lib.ffe_create(ctypes.byref(dom), ctypes.byref(el), 5, ctypes.byref(met), ctypes.byref(prm), None,
+                          ctypes.byref(hh)) == 1
+    tci = copy.deepcopy(ok)
+    tci["params"]["tci_on"] = 1
+    assert _create(ffe, tci)[0] == 7
+    dom2, el2 = ffe.domain_of(ok)
+    dom2.shell_ks = 2
+    mk, M, a = ok["metric"]
+    assert lib.ffe_create(ctypes.byref(dom2), ctypes.byref(el2), 5, ctypes.byref(ffe.Metric(ffe.METRIC[mk], M, a)),
+                          ctypes.byref(ffe.params_from(ok["params"])), None, ctypes.byref(hh)) == 1
